@@ -1,0 +1,245 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws and lays out inputs (lattices, jitter, velocities,
+random disk packings, replica plans). It holds none of the method's
+arithmetic: no displacement, energy, force or integration code lives here.
+Both the FP64 oracle (``oracle/``) and the CUDA path read their inputs from
+these generators, so the two sides see bit-identical starting data.
+
+Conventions shared with every consumer:
+  * positions / velocities are float32 arrays of shape [N, 4] (x, y, z, w);
+    in 2-D the z column is 0.  ``w`` of a position holds the particle
+    diameter for soft spheres and 0 otherwise; ``w`` of a velocity is 0;
+  * box lengths are returned as Python floats that are exactly
+    representable in float32, so that the FP32 kernels and the FP64 oracle
+    integrate in exactly the same box;
+  * all randomness comes from ``numpy.random.Generator(PCG64(seed))``.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "f32", "box_for_density", "sc_lattice", "fcc_lattice", "diamond_lattice",
+    "jitter_wrap", "thermal_velocities", "LJFluid", "lj_fluid",
+    "Packing2D", "packing_2d", "packing_box", "SWSilicon", "sw_silicon",
+    "ReplicaSpec", "replica_plan", "uniform_box_positions",
+]
+
+
+def f32(x: float) -> float:
+    """Round a double to the nearest float32 value and return it as a double."""
+    return float(np.float32(x))
+
+
+def box_for_density(n: int, rho: float, dim: int = 3) -> float:
+    """Cubic (square) box edge for ``n`` particles at number density ``rho``,
+    rounded to float32 (the box both sides use)."""
+    return f32((n / rho) ** (1.0 / dim))
+
+
+def _to4(r: np.ndarray) -> np.ndarray:
+    out = np.zeros((r.shape[0], 4), dtype=np.float32)
+    out[:, : r.shape[1]] = r
+    return out
+
+
+def sc_lattice(n_side: int, L: float, dim: int = 3) -> np.ndarray:
+    """Simple-cubic (square) lattice, n_side**dim sites at (k + 1/2) L / n_side."""
+    a = L / n_side
+    g = (np.arange(n_side, dtype=np.float64) + 0.5) * a
+    mesh = np.meshgrid(*([g] * dim), indexing="ij")
+    return np.stack([m.reshape(-1) for m in mesh], axis=1)
+
+
+def fcc_lattice(n_side: int, L: float) -> np.ndarray:
+    """Face-centred cubic lattice of 4 n_side^3 sites in a cube of edge L."""
+    a = L / n_side
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]]) + 0.25
+    g = np.arange(n_side, dtype=np.float64)
+    cells = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    return ((cells[:, None, :] + basis[None, :, :]) * a).reshape(-1, 3)
+
+
+def diamond_lattice(n_side: int, a: float) -> np.ndarray:
+    """Diamond-cubic lattice (8 n_side^3 sites) with cubic lattice constant a."""
+    fcc = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    basis = np.concatenate([fcc, fcc + 0.25]) + 0.125
+    g = np.arange(n_side, dtype=np.float64)
+    cells = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    return ((cells[:, None, :] + basis[None, :, :]) * a).reshape(-1, 3)
+
+
+def jitter_wrap(r: np.ndarray, L: float, amp: float, rng: np.random.Generator) -> np.ndarray:
+    """Add uniform noise in [-amp, amp) per component, fold into [0, L) and
+    round to float32 (a value that rounds up to L is folded to 0)."""
+    r = r + rng.uniform(-amp, amp, size=r.shape)
+    r = np.mod(r, L).astype(np.float32)
+    r[r >= np.float32(L)] = 0.0
+    r[r < 0] = 0.0
+    return r
+
+
+def thermal_velocities(n: int, dim: int, T: float, mass: float,
+                       rng: np.random.Generator) -> np.ndarray:
+    """Gaussian velocities at temperature T with zero net momentum, rescaled
+    so the kinetic energy is exactly (dim*n - dim) T / 2 (k_B = 1)."""
+    v = rng.normal(0.0, math.sqrt(T / mass), size=(n, dim))
+    v -= v.mean(axis=0, keepdims=True)
+    ke = 0.5 * mass * float((v * v).sum())
+    target = 0.5 * (dim * n - dim) * T
+    v *= math.sqrt(target / ke)
+    return v.astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# Lennard-Jones fluid (Table 1 benchmark shape: N particles, cutoff, skin)
+# --------------------------------------------------------------------------
+@dataclass
+class LJFluid:
+    N: int
+    L: float
+    r: np.ndarray           # [N,4] float32
+    v: np.ndarray           # [N,4] float32
+    eps: float = 1.0
+    sigma: float = 1.0
+    r_cut: float = 2.5
+    skin: float = 0.3
+    dt: float = 0.005
+    mass: float = 1.0
+    steps: int = 100
+    name: str = ""
+
+
+def lj_fluid(lattice: str = "sc", n_side: int = 16, rho: float = 0.84, T: float = 1.0,
+             jitter: float = 0.05, seed: int = 0, steps: int = 100) -> LJFluid:
+    """3-D LJ fluid: a jittered lattice at density ``rho`` and T velocities.
+
+    ``lattice='sc'`` with n_side=16 gives N = 4096;
+    ``lattice='fcc'`` with n_side=40 gives N = 256,000.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = n_side ** 3 if lattice == "sc" else 4 * n_side ** 3
+    L = box_for_density(n, rho, 3)
+    sites = sc_lattice(n_side, L, 3) if lattice == "sc" else fcc_lattice(n_side, L)
+    r = _to4(jitter_wrap(sites, L, jitter, rng))
+    v = _to4(thermal_velocities(n, 3, T, 1.0, rng))
+    return LJFluid(N=n, L=L, r=r, v=v, steps=steps, name=f"lj_{lattice}{n_side}_N{n}")
+
+
+def lj_small(seed: int = 0) -> LJFluid:
+    """N = 4,096 LJ fluid (simple-cubic 16^3 start), 100 steps."""
+    return lj_fluid("sc", 16, seed=seed, steps=100)
+
+
+def lj_large(seed: int = 0) -> LJFluid:
+    """N = 256,000 LJ fluid (FCC 4*40^3 start), 1,000 steps."""
+    return lj_fluid("fcc", 40, seed=seed, steps=1000)
+
+
+# --------------------------------------------------------------------------
+# 2-D bidisperse soft-sphere packing (Sec. 4.2)
+# --------------------------------------------------------------------------
+def packing_box(N: int, D: float, phi: float) -> float:
+    """Square box edge keeping packing fraction ``phi`` for N/2 disks of
+    diameter D and N/2 of diameter 1 (FP64; the packing keeps FP64 L(D))."""
+    return math.sqrt((N // 2) * math.pi * (D * D + 1.0) / 4.0 / phi)
+
+
+@dataclass
+class Packing2D:
+    N: int
+    D: float
+    phi: float
+    s0: np.ndarray          # [N,2] float64 fractional coordinates in [0,1)
+    diam: np.ndarray        # [N] float64: D for the first N/2, 1 for the rest
+    step: float = 0.05
+    steps: int = 2000
+    eps: float = 1.0
+    alpha: float = 2.0
+    skin: float = 0.3
+
+
+def packing_2d(N: int = 1024, D: float = 1.2, phi: float = 0.90, seed: int = 0,
+               steps: int = 2000, step: float = 0.05) -> Packing2D:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s0 = rng.uniform(0.0, 1.0, size=(N, 2))
+    diam = np.ones(N)
+    diam[: N // 2] = D
+    return Packing2D(N=N, D=D, phi=phi, s0=s0, diam=diam, steps=steps, step=step)
+
+
+# --------------------------------------------------------------------------
+# Stillinger-Weber silicon (learned-potential workload)
+# --------------------------------------------------------------------------
+@dataclass
+class SWSilicon:
+    N: int
+    L: float
+    r: np.ndarray
+    v: np.ndarray
+    a: float
+    T_K: float
+    mass_amu: float = 28.0855
+
+
+KB_EV = 8.617333262e-5          # Boltzmann constant, eV / K
+AMU_A2_FS2_TO_EV = 103.6427     # 1 amu A^2 fs^-2 = 103.6427 eV
+
+
+def sw_silicon(n_side: int = 4, a: float = 5.431, T_K: float = 1000.0, seed: int = 0,
+               jitter: float = 0.0) -> SWSilicon:
+    """Diamond-cubic Si, 8 n_side^3 atoms, velocities at T_K in A/fs."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = f32(n_side * a)
+    sites = diamond_lattice(n_side, a)
+    r = _to4(jitter_wrap(sites, L, jitter, rng) if jitter > 0 else
+             np.mod(sites, L).astype(np.float32))
+    n = sites.shape[0]
+    # kT / m in (A/fs)^2: (eV) / (amu) -> divide by 103.6427
+    kT_over_m = KB_EV * T_K / 28.0855 / AMU_A2_FS2_TO_EV
+    v = thermal_velocities(n, 3, kT_over_m, 1.0, rng) if T_K > 0 else np.zeros((n, 3), np.float32)
+    return SWSilicon(N=n, L=L, r=r, v=_to4(v), a=a, T_K=T_K)
+
+
+# --------------------------------------------------------------------------
+# Batched replicas (vmap over independent systems, Sec. 4.2)
+# --------------------------------------------------------------------------
+@dataclass
+class ReplicaSpec:
+    kind: str               # "lj" or "soft"
+    N: int
+    rho: float
+    L: float
+    seed: int
+    dt: float
+    extras: dict = field(default_factory=dict)
+
+
+def replica_plan(R: int = 512, n_max: int = 8192, seed: int = 0,
+                 lj_rlist: float = 2.8, soft_rlist: float = 1.7) -> list[ReplicaSpec]:
+    """Half LJ, half 3-D soft-sphere replicas with log-uniform N and uniform
+    density in [0.7, 0.95].  N has a lower clamp so that every box holds the
+    interaction range twice over (minimum image stays valid)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(R):
+        kind = "lj" if k < R // 2 else "soft"
+        rho = float(rng.uniform(0.7, 0.95))
+        rl = lj_rlist if kind == "lj" else soft_rlist
+        n_min = max(64, int(math.ceil(rho * (2.0 * rl) ** 3)) + 1)
+        N = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        N = max(N, n_min)
+        out.append(ReplicaSpec(kind=kind, N=N, rho=rho, L=box_for_density(N, rho, 3),
+                               seed=seed * 100003 + k, dt=0.005 if kind == "lj" else 0.01))
+    return out
+
+
+def uniform_box_positions(N: int, L: float, dim: int, rng: np.random.Generator) -> np.ndarray:
+    """N uniform random positions in [0, L)^dim as float32."""
+    r = np.mod(rng.uniform(0.0, L, size=(N, dim)), L).astype(np.float32)
+    r[r >= np.float32(L)] = 0.0
+    return r
