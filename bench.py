@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark: Lennard-Jones NVE particle-steps/s on one B300 (per rank).
+
+A bench step is one whole LJ NVE job of the N = 256,000 workload (FCC
+4*40^3 start at density 0.84, T* = 1, r_c = 2.5 shifted, skin 0.3,
+dt = 0.005): neighbor-list build, initial forces and 1,000 velocity-Verlet
+steps with device-side rebuild decisions, all inside libjmd (one CUDA graph
+with a device-controlled WHILE loop).  `value` = particle-steps per second
+over K timed bench steps (inputs resident in HBM; L2 flushed between bench
+steps), summed over ranks (weak scaling: each rank runs its own seeded
+replica, no data-path collective).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl jmd|reference]
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (LJ N=256k); learned vs plain SW at stated force RMSE"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="jmd", choices=["jmd", "reference"])
+    ap.add_argument("--workload", default="lj256k", choices=["lj256k", "lj4096"])
+    ap.add_argument("--md-steps", type=int, default=None, help="MD steps per bench step (default: the workload's)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tpp", type=int, default=0)
+    return ap.parse_args()
+
+
+def workload(name, seed):
+    import workloads as W
+    return W.lj_large(seed) if name == "lj256k" else W.lj_small(seed)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if p[5 + k].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(name, md_steps, seed=0):
+    """Time the FP64 oracle on `md_steps` NVE steps of the workload (all host
+    threads).  Returns (particle-steps/s, threads, seconds)."""
+    import oracle as O
+    c = workload(name, seed)
+    t0 = time.perf_counter()
+    O.nve(c.r, c.v, c.L, "lj", dt=c.dt, nsteps=md_steps)
+    dt = time.perf_counter() - t0
+    return c.N * md_steps / dt, O.num_threads(), dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    md = 5 if args.workload == "lj256k" else 50
+    times = []
+    N = workload(args.workload, 0).N
+    thr = 1
+    for k in range(args.warmup + args.steps):
+        _, thr, dt = oracle_sample(args.workload, md)
+        if k >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    val = N * md * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "lj_fcc40_N256000" if N == 256000 else "lj_sc16_N4096", "N": N,
+                   "md_steps_per_step": md},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": f"{md} FP64 velocity-Verlet steps of the N={N} LJ workload per step"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _source_sha():
+    h = hashlib.sha256()
+    for p in ("paper_1912_04232_b300/csrc/pair.cu", "paper_1912_04232_b300/csrc/common.cuh"):
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    # CPU baseline first (before any CUDA work), rank 0 at N=1 only
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        md = 20 if args.workload == "lj256k" else 200
+        val, thr, dt = oracle_sample(args.workload, md)
+        Nw = workload(args.workload, 0).N
+        cpu_baseline = {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
+                        "sample": f"{md} FP64 NVE steps of the N={Nw} LJ workload ({dt:.1f} s)"}
+
+    import torch
+    import paper_1912_04232_b300 as P
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    c = workload(args.workload, seed=rank)
+    md_steps = args.md_steps or c.steps
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    if args.tpp:
+        P.md_set_pair_tpp(args.tpp)
+    s = P.md_space_periodic(3, [c.L] * 3)
+    nl = P.NeighborList(s, c.N, c.r_cut, c.skin, 128)
+    pot = P.lj_pot(c.eps, c.sigma, c.r_cut, True)
+    r0 = torch.from_numpy(c.r).to(dev)
+    v0 = torch.from_numpy(c.v).to(dev)
+    r = torch.empty_like(r0)
+    v = torch.empty_like(v0)
+    f = torch.zeros_like(r0)
+    PE = torch.zeros(md_steps, dtype=torch.float64, device=dev)
+    KE = torch.zeros(md_steps, dtype=torch.float64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
+
+    def job():
+        nl.build(r, st)
+        P.md_energy_forces(s, pot, r, nl.plan, f, None, st)
+        P.md_integrate_nve(s, pot, r, v, f, c.mass, c.dt, md_steps, nl.plan, PE, KE, True, st)
+
+    def one_step():
+        r.copy_(r0)
+        v.copy_(v0)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        job()
+        e1.record(stream)
+        return e0, e1
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    code = P.md_status_poll(st)
+    if code != 0:
+        raise SystemExit(f"device status {code} after warm-up")
+    b0, _ = nl.stats()
+    launches0 = P.md_launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [one_step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    launches = P.md_launch_count() - launches0
+    builds = nl.stats()[0] - b0
+    code = P.md_status_poll(st)
+    if code != 0:
+        raise SystemExit(f"device status {code} in the timed region")
+    E = (PE + KE).cpu().numpy()
+    drift = float(np.abs(E - E[0]).max() / c.N)
+
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    total_ps = c.N * md_steps * args.steps * world
+    value = total_ps / (t_max * 1e-3)
+
+    # end to end: host buffers in, energies out, every step
+    e2e = None
+    if not args.no_e2e:
+        hr = torch.from_numpy(c.r).pin_memory()
+        hv = torch.from_numpy(c.v).pin_memory()
+        hpe = torch.empty(md_steps, dtype=torch.float64).pin_memory()
+        hke = torch.empty(md_steps, dtype=torch.float64).pin_memory()
+        tt = []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r.copy_(hr, non_blocking=True)
+            v.copy_(hv, non_blocking=True)
+            job()
+            hpe.copy_(PE, non_blocking=True)
+            hke.copy_(KE, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= args.warmup:
+                tt.append(e0.elapsed_time(e1))
+        e2e_ms = sum(tt)
+        if dist:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": total_ps / (e2e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(hr.numel() * 4 + hv.numel() * 4),
+               "d2h_bytes_per_step": int(hpe.numel() * 8 + hke.numel() * 8)}
+
+    # roofline of the dominant kernel (pair forces), launched alone with events
+    mean_cnt = float(nl.cnt.float().clamp(max=nl.cap).mean().item())
+    bytes_per_particle = 4.0 * mean_cnt + 4 + 16 + 16 + 16   # row, count, own r, f write, gathered r once
+    fe = []
+    for _ in range(30):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.md_energy_forces(s, pot, r, nl.plan, f, None, st)
+        e1.record(stream)
+        fe.append((e0, e1))
+    torch.cuda.synchronize()
+    kt = statistics.median(a.elapsed_time(b) for a, b in fe[5:]) * 1e-3
+    try:
+        peak, peak_src = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        peak, peak_src = 6400.0, "fallback"
+    achieved = bytes_per_particle * c.N / kt / 1e9
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        ent = tr.get("k_pair_lj", {})
+        if ent.get("source_sha") == _source_sha() and ent.get("N") == c.N:
+            traffic = ent.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"lj_fcc40_N{c.N}" if c.N == 256000 else f"lj_sc16_N{c.N}", "N": c.N,
+                       "md_steps_per_step": md_steps, "density": 0.84, "T": 1.0, "r_cut": c.r_cut, "skin": c.skin,
+                       "dt": c.dt, "neighbor_cap": nl.cap, "rebuilds_per_step": builds / args.steps,
+                       "max_energy_drift_per_particle": drift, "l2": "flushed between bench steps",
+                       "parallelism": f"replicas{world}", "pair_tpp": args.tpp or 8},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_pair<LJ> (md_energy_forces)",
+                         "bytes_per_particle": bytes_per_particle, "kernel_ms": kt * 1e3,
+                         "peak_source": peak_src},
+            "cpu_baseline": cpu_baseline,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

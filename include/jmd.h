@@ -1,0 +1,200 @@
+/*
+ * jmd.h -- C ABI of libjmd, the B300 (sm_103a) molecular-dynamics hot path.
+ *
+ * The calls follow the problem statement of "JAX, M.D.: A Framework for
+ * Differentiable Physics" (Schoenholz & Cubuk, arXiv:1912.04232):
+ *   periodic spaces                         Sec. 3.2.1
+ *   pair interactions U = 1/2 sum u(r_ij)   Sec. 3.2.2
+ *   cell lists and neighbor lists           Sec. 3.2.3
+ *   NVE / NVT / minimisation                Sec. 3.3.1
+ *   LJ, soft-sphere, Stillinger-Weber       Sec. 3.3.2
+ *   neural-network potentials               Sec. 3.2.4, 4.1
+ *   differentiating a minimisation          Sec. 4.2, App. A
+ *
+ * Conventions (every call):
+ *   - Every call returns md_status.  Argument errors found on the host are
+ *     returned synchronously and nothing is enqueued.  Errors that only the
+ *     device can see (neighbor overflow, non-finite values, bounds, timeouts)
+ *     are OR-ed into a caller-provided device word `uint32_t* d_status`; read
+ *     it with md_status_poll().
+ *   - All device arrays are owned by the caller.  The library never
+ *     allocates or frees device memory.  Scratch comes from a caller buffer
+ *     whose size the matching *_plan call reports.
+ *   - Positions, velocities and forces are float[N][4] (16-byte aligned):
+ *       positions  (x, y, z, w): w = particle diameter for soft spheres,
+ *                   0 otherwise; z = 0 in 2-D;
+ *       velocities (vx, vy, vz, 0);
+ *       forces     (fx, fy, fz, e_i) where e_i is the per-particle energy,
+ *                   so that sum_i e_i = U.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *     is asynchronous on that stream unless stated otherwise.
+ */
+#ifndef JMD_H
+#define JMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define JMD_API __attribute__((visibility("default")))
+#else
+#define JMD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *md_stream_t; /* == cudaStream_t */
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_INVALID = 1,        /* bad argument (host) */
+    MD_ERR_BOX_TOO_SMALL = 2,  /* box edge < 2 * interaction range: minimum image invalid */
+    MD_ERR_NBR_OVERFLOW = 4,   /* a neighbor row needed more than `cap` slots (device) */
+    MD_ERR_NONFINITE = 8,      /* a NaN / Inf reached a reduction (device) */
+    MD_ERR_TIMEOUT = 16,       /* a bounded device wait ran out (device) */
+    MD_ERR_BOUNDS = 32,        /* an index failed a bounds check (device) */
+    MD_ERR_CUDA = 64           /* a CUDA runtime call failed (host) */
+} md_status;
+
+/* ------------------------------------------------------------------------ */
+/* Periodic space (Sec. 3.2.1): the box [0,L_x) x [0,L_y) (x [0,L_z)) with   */
+/* r ~ r + n L.  The displacement of a from b is the nearest-image vector    */
+/*   t = a - b;  d = t - L * rint(t * Linv)                                  */
+/* and the shift r + dr is wrapped back as r - L * floor(r * Linv).          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int dim;          /* 2 or 3 */
+    float L[3];       /* box edges in FP32 (unused axes = 1) */
+    float Linv[3];    /* 1/L evaluated in FP64, rounded to FP32 */
+    double L64[3];    /* box edges as given */
+} md_space;
+
+/* box: double[dim].  Fails with MD_ERR_INVALID for dim not in {2,3} or a
+ * non-positive edge. */
+JMD_API md_status md_space_periodic(int dim, const double *box, md_space *out);
+
+/* ------------------------------------------------------------------------ */
+/* Neighbor list (Sec. 3.2.3): for every i, the j != i with r_ij < r_list,   */
+/* r_list = r_cut + skin, found through a cell list with cells of side       */
+/* >= r_list.  Rows are sorted ascending and padded with N; cnt[i] is the    */
+/* true count even when it exceeds cap (then MD_ERR_NBR_OVERFLOW is raised   */
+/* and the row is truncated).  Membership is decided in FP32 as              */
+/*   r2 = (dx*dx + dy*dy) + dz*dz < fl32(r_list)^2                           */
+/* with every operation rounded separately (no FMA).                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int dim, N, cap;
+    int ncell[3];          /* cells per axis (>= 1; stencil deduplicated below 3) */
+    int ncell_total;
+    float r_cut, skin;
+    float r_list;          /* fl32(r_cut + skin) */
+    float r_list2;         /* fl32(r_list * r_list) */
+    float half_skin2;      /* fl32((skin/2)^2): rebuild threshold on displacement^2 */
+    float cell_scale[3];   /* ncell / L */
+    size_t ws_bytes;       /* scratch needed by this plan */
+    /* caller-owned device memory, bound with md_nbr_bind: */
+    int32_t *nbr;          /* [N][cap] */
+    int32_t *cnt;          /* [N] */
+    float *rref;           /* [N][4] positions at the last build */
+    void *ws;              /* ws_bytes of scratch (cells, sorted copy, control words, reduction partials) */
+} md_nbr;
+
+/* Plan a neighbor list for N particles in space s.  Fails with
+ * MD_ERR_BOX_TOO_SMALL if any used box edge is < 2 r_list, MD_ERR_INVALID
+ * for N < 1, cap < 1, r_cut <= 0 or skin < 0.  Fills out (pointers NULL). */
+JMD_API md_status md_nbr_plan(const md_space *s, int N, float r_cut, float skin, int cap, md_nbr *out);
+
+/* Attach caller memory: d_nbr [N*cap] int32, d_cnt [N] int32, d_rref [N*4]
+ * float (16-byte aligned), d_ws [ws_bytes] (256-byte aligned).  Zeroes the
+ * control words and the cell histogram of d_ws on `stream`. */
+JMD_API md_status md_nbr_bind(md_nbr *nb, int32_t *d_nbr, int32_t *d_cnt, float *d_rref, void *d_ws,
+                              md_stream_t stream);
+
+/* Unconditional rebuild from positions d_r [N][4]. */
+JMD_API md_status md_neighbor_list_build(const md_space *s, const float *d_r, md_nbr *nb, uint32_t *d_status,
+                                         md_stream_t stream);
+
+/* Rebuild only if some particle moved more than skin/2 from its position at
+ * the last build (minimum image; the check runs on the device, the host
+ * does not wait). */
+JMD_API md_status md_neighbor_list_update(const md_space *s, const float *d_r, md_nbr *nb, uint32_t *d_status,
+                                          md_stream_t stream);
+
+/* Synchronous on `stream`: builds done since bind, largest row count seen
+ * by any build since bind. */
+JMD_API md_status md_nbr_stats(const md_nbr *nb, int64_t *builds, int32_t *max_count, md_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Energy functions (Sec. 3.3.2) summed over the neighbor list (smap.neighbors,
+ * Sec. 3.2.2): U = 1/2 sum_{i != j} u(r_ij), F = -grad U.                   */
+/* ------------------------------------------------------------------------ */
+typedef enum { MD_LJ = 0, MD_SOFT_SPHERE = 1, MD_SW = 2, MD_BP = 3 } md_potential;
+
+typedef struct {
+    md_potential kind;
+    /* MD_LJ: u = 4 eps [(sigma/r)^12 - (sigma/r)^6] - e_shift for r < r_cut
+     * (the r < r_cut test in FP32 as for the neighbor list); forces unshifted. */
+    float eps, sigma, r_cut, e_shift;
+    /* MD_SOFT_SPHERE: u = (eps/alpha) (1 - r/s_ij)^alpha for r < s_ij,
+     * s_ij = (w_i + w_j)/2 from the position w column. */
+    float alpha;
+    /* MD_SW: {eps, sigma, a, lambda, gamma, A, B, p, q, cos0}; cutoff a*sigma. */
+    float sw[10];
+    /* MD_BP: pointer to a learned-potential model descriptor. */
+    const void *model;
+} md_pot;
+
+/* Forces and per-particle energies into d_f [N][4]; if d_E != NULL the FP64
+ * total energy sum_i e_i is written to *d_E (device).  Needs a built list
+ * with r_list >= the potential's range. */
+JMD_API md_status md_energy_forces(const md_space *s, const md_pot *p, const float *d_r, const md_nbr *nb,
+                                   float *d_f, double *d_E, uint32_t *d_status, md_stream_t stream);
+
+/* Threads per particle of the pair-force kernels (4, 8, 16 or 32): the
+ * group that gathers one row.  A tuning knob; results are identical up to
+ * FP32 summation order. */
+JMD_API md_status md_set_pair_tpp(int tpp);
+
+/* ------------------------------------------------------------------------ */
+/* Dynamics (Sec. 3.3.1).                                                   */
+/* ------------------------------------------------------------------------ */
+/* nsteps of velocity-Verlet NVE.  On entry d_f must hold the forces at d_r
+ * (md_energy_forces) and nb a list built for d_r.  Each step:
+ *   v += dt/2 F/m;  r = wrap(r + dt v);  rebuild the list if needed;
+ *   F = F(r);       v += dt/2 F/m;
+ * mass is in energy*time^2/length^2.  d_PE / d_KE (nsteps doubles each, may
+ * be NULL) receive the FP64 potential and kinetic energy after each step.
+ * use_graph != 0 runs the whole loop as one CUDA graph launch with device-
+ * side loop control (captured once per argument set and cached; the first
+ * call with a new argument set must not happen during a stream capture). */
+JMD_API md_status md_integrate_nve(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f,
+                                   float mass, float dt, int nsteps, md_nbr *nb, double *d_PE, double *d_KE,
+                                   int use_graph, uint32_t *d_status, md_stream_t stream);
+
+/* Minimisation (Sec. 3.3.1): kind 0 = gradient descent r <- r + step * F in
+ * unwrapped coordinates (the list bins wrapped copies).  d_E (nsteps+1
+ * doubles, may be NULL) receives U before every step and after the last;
+ * d_f holds F at the final positions on return. */
+JMD_API md_status md_minimize(const md_space *s, const md_pot *p, int kind, float step, int nsteps, float *d_r,
+                              float *d_f, md_nbr *nb, double *d_E, uint32_t *d_status, md_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Status and accounting                                                     */
+/* ------------------------------------------------------------------------ */
+/* Synchronous: copies *d_status to *h_status after `stream` drains. */
+JMD_API md_status md_status_poll(const uint32_t *d_status, uint32_t *h_status, md_stream_t stream);
+
+/* Number of this library's kernels that have run in this process (graph
+ * launches count every kernel node they ran).  Synchronizes the device. */
+JMD_API uint64_t md_launch_count(void);
+
+/* Library version string. */
+JMD_API const char *md_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JMD_H */

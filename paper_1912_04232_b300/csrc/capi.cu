@@ -1,0 +1,52 @@
+// capi.cu -- periodic space, status and accounting entry points.
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace jmd {
+static launch_reader_t g_readers[64];
+static int g_nreaders = 0;
+void register_launch_reader(launch_reader_t f)
+{
+    if (g_nreaders < 64) g_readers[g_nreaders++] = f;
+}
+}  // namespace jmd
+
+using namespace jmd;
+
+extern "C" md_status md_space_periodic(int dim, const double *box, md_space *out)
+{
+    if (!box || !out || (dim != 2 && dim != 3)) return MD_ERR_INVALID;
+    md_space s;
+    memset(&s, 0, sizeof(s));
+    s.dim = dim;
+    for (int k = 0; k < 3; ++k) {
+        double L = k < dim ? box[k] : 1.0;
+        if (!(L > 0.0) || !std::isfinite(L)) return MD_ERR_INVALID;
+        s.L64[k] = L;
+        s.L[k] = (float)L;
+        s.Linv[k] = (float)(1.0 / L);
+    }
+    *out = s;
+    return MD_OK;
+}
+
+extern "C" md_status md_status_poll(const uint32_t *d_status, uint32_t *h_status, md_stream_t stream)
+{
+    if (!d_status || !h_status) return MD_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    JMD_CUDA_TRY(cudaMemcpyAsync(h_status, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    JMD_CUDA_TRY(cudaStreamSynchronize(st));
+    return MD_OK;
+}
+
+extern "C" uint64_t md_launch_count(void)
+{
+    if (cudaDeviceSynchronize() != cudaSuccess) return 0;
+    unsigned long long v = 0;
+    for (int k = 0; k < g_nreaders; ++k) v += g_readers[k]();
+    return (uint64_t)v;
+}
+
+extern "C" const char *md_version(void) { return "jmd-b300 0.1 (sm_103a)"; }

@@ -1,0 +1,190 @@
+// common.cuh -- device helpers shared by the libjmd kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/jmd.h"
+
+namespace jmd {
+
+// ---------------------------------------------------------------------------
+// Control words at the head of every neighbor-list workspace.
+// ---------------------------------------------------------------------------
+enum CtlWord : int {
+    CTL_REBUILD = 0,     // 1 -> the gated rebuild chain runs
+    CTL_TICKET = 1,      // last-block ticket of the energy reductions
+    CTL_MAXCNT = 2,      // largest row count seen by any build
+    CTL_STEP = 3,        // device step counter of the running loop
+    CTL_BUILDS_LO = 4,   // number of builds (64-bit, two words)
+    CTL_BUILDS_HI = 5,
+    CTL_TICKET2 = 6,     // second ticket (displacement-check hand-off)
+    CTL_NSTEPS = 7,      // loop length for device-side loop control
+    CTL_WORDS = 64
+};
+
+struct Box {
+    float L[3];
+    float Linv[3];
+};
+
+__host__ __device__ inline Box make_box(const md_space *s)
+{
+    Box b;
+    for (int k = 0; k < 3; ++k) {
+        b.L[k] = s->L[k];
+        b.Linv[k] = s->Linv[k];
+    }
+    return b;
+}
+
+// Nearest-image component, every operation rounded separately (Sec. 3.2.1):
+//   t = a - b;  d = t - L * rint(t * Linv)
+__device__ __forceinline__ float min_image_rn(float a, float b, float L, float Linv)
+{
+    float t = __fsub_rn(a, b);
+    float n = rintf(__fmul_rn(t, Linv));
+    return __fsub_rn(t, __fmul_rn(L, n));
+}
+
+// Squared nearest-image distance, r2 = (dx*dx + dy*dy) + dz*dz, no FMA.
+// This exact expression decides every pair-membership test (neighbor list
+// and cutoffs) so the decision is reproducible bit for bit.
+template <int DIM>
+__device__ __forceinline__ float dist2_rn(const float4 &a, const float4 &b, const Box &bx, float &dx, float &dy,
+                                          float &dz)
+{
+    dx = min_image_rn(a.x, b.x, bx.L[0], bx.Linv[0]);
+    dy = min_image_rn(a.y, b.y, bx.L[1], bx.Linv[1]);
+    float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    if (DIM == 3) {
+        dz = min_image_rn(a.z, b.z, bx.L[2], bx.Linv[2]);
+        r2 = __fadd_rn(r2, __fmul_rn(dz, dz));
+    } else {
+        dz = 0.0f;
+    }
+    return r2;
+}
+
+// Wrap a coordinate into [0, L): x - L floor(x Linv), folded once more if
+// rounding left it on the boundary.
+__device__ __forceinline__ float wrap_coord(float x, float L, float Linv)
+{
+    float y = x - L * floorf(x * Linv);
+    if (y >= L) y -= L;
+    if (y < 0.0f) y = 0.0f;
+    return y;
+}
+
+__device__ __forceinline__ void raise_status(uint32_t *st, uint32_t bits)
+{
+    if (st) atomicOr(st, bits);
+}
+
+// One atomic per kernel launch: block 0 / thread 0 counts the launch, so the
+// library can report exactly how many of its kernels ran (graph bodies
+// included).  Each translation unit has its own counter (no relocatable
+// device code); a static registrar adds the unit's reader to a host list
+// that md_launch_count() sums.
+static __device__ unsigned long long g_kernel_launches = 0ull;
+__device__ __forceinline__ void count_launch()
+{
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&g_kernel_launches, 1ull);
+}
+
+typedef unsigned long long (*launch_reader_t)(void);
+void register_launch_reader(launch_reader_t f);
+static unsigned long long tu_launches(void)
+{
+    unsigned long long v = 0ull;
+    if (cudaMemcpyFromSymbol(&v, g_kernel_launches, sizeof(v)) != cudaSuccess) return 0ull;
+    return v;
+}
+namespace {
+struct LaunchRegistrar {
+    LaunchRegistrar() { register_launch_reader(&tu_launches); }
+};
+static LaunchRegistrar g_launch_registrar;
+}  // namespace
+
+// Fixed-order FP64 block sum (all threads participate, result valid in
+// thread 0).  `sh` needs blockDim.x/32 doubles.
+__device__ __forceinline__ double block_sum_f64(double v, double *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        s = (l < nw) ? sh[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout of a neighbor list (all offsets 256-byte aligned).
+// ---------------------------------------------------------------------------
+struct WsLayout {
+    size_t ctl, cell_count, cell_start, cell_of, rank, atoms, rsorted, partials, total;
+    int max_blocks;
+};
+
+__host__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+__host__ inline WsLayout ws_layout(int N, int ncell_total)
+{
+    WsLayout w;
+    size_t o = 0;
+    w.ctl = o;          o = align256(o + sizeof(uint32_t) * CTL_WORDS);
+    w.cell_count = o;   o = align256(o + sizeof(int32_t) * (size_t)ncell_total);
+    w.cell_start = o;   o = align256(o + sizeof(int32_t) * ((size_t)ncell_total + 1));
+    w.cell_of = o;      o = align256(o + sizeof(int32_t) * (size_t)N);
+    w.rank = o;         o = align256(o + sizeof(int32_t) * (size_t)N);
+    w.atoms = o;        o = align256(o + sizeof(int32_t) * (size_t)N);
+    w.rsorted = o;      o = align256(o + sizeof(float4) * (size_t)N);
+    w.max_blocks = N / 4 + 64;
+    w.partials = o;     o = align256(o + sizeof(double2) * (size_t)w.max_blocks);
+    w.total = o;
+    return w;
+}
+
+struct WsPtrs {
+    uint32_t *ctl;
+    int32_t *cell_count, *cell_start, *cell_of, *rank, *atoms;
+    float4 *rsorted;
+    double2 *partials;
+    int max_blocks;
+};
+
+__host__ inline WsPtrs ws_ptrs(const md_nbr *nb)
+{
+    WsLayout w = ws_layout(nb->N, nb->ncell_total);
+    char *b = (char *)nb->ws;
+    WsPtrs p;
+    p.ctl = (uint32_t *)(b + w.ctl);
+    p.cell_count = (int32_t *)(b + w.cell_count);
+    p.cell_start = (int32_t *)(b + w.cell_start);
+    p.cell_of = (int32_t *)(b + w.cell_of);
+    p.rank = (int32_t *)(b + w.rank);
+    p.atoms = (int32_t *)(b + w.atoms);
+    p.rsorted = (float4 *)(b + w.rsorted);
+    p.partials = (double2 *)(b + w.partials);
+    p.max_blocks = w.max_blocks;
+    return p;
+}
+
+// Host-side CUDA error to status.
+#define JMD_CUDA_TRY(expr)                                                                              \
+    do {                                                                                                \
+        cudaError_t _e = (expr);                                                                        \
+        if (_e != cudaSuccess) return MD_ERR_CUDA;                                                      \
+    } while (0)
+
+}  // namespace jmd

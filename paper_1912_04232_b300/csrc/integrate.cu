@@ -1,0 +1,316 @@
+// integrate.cu -- dynamics and minimisation (Sec. 3.3.1).
+//
+// Velocity-Verlet NVE step as three stages:
+//   k_kick_drift   v += dt/2 F/m; r = wrap(r + dt v); displacement check
+//   rebuild chain  (only when some particle moved > skin/2; see nbr.cu)
+//   k_pair<KICK>   F(r), then v += dt/2 F/m, FP64 PE/KE of the step
+// Gradient-descent step:
+//   k_pair         F(r_t), U(r_t)
+//   k_gd_step      r += eta F (unwrapped), displacement check
+//   rebuild chain
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace jmd {
+
+template <int DIM, int COND>
+__global__ void __launch_bounds__(256) k_kick_drift(float4 *r, float4 *v, const float4 *f, const float4 *rref, int N,
+                                                    float hdm, float dt, Box box, float half_skin2, uint32_t *ctl,
+                                                    unsigned long long cond_if)
+{
+    count_launch();
+    __shared__ bool last;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool mv = false;
+    if (i < N) {
+        float4 fi = f[i], vi = v[i], ri = r[i];
+        vi.x += hdm * fi.x;
+        vi.y += hdm * fi.y;
+        ri.x = wrap_coord(ri.x + dt * vi.x, box.L[0], box.Linv[0]);
+        ri.y = wrap_coord(ri.y + dt * vi.y, box.L[1], box.Linv[1]);
+        if (DIM == 3) {
+            vi.z += hdm * fi.z;
+            ri.z = wrap_coord(ri.z + dt * vi.z, box.L[2], box.Linv[2]);
+        }
+        v[i] = vi;
+        r[i] = ri;
+        float dx, dy, dz;
+        mv = dist2_rn<DIM>(ri, rref[i], box, dx, dy, dz) > half_skin2;
+    }
+    if (__any_sync(0xffffffffu, mv) && (threadIdx.x & 31) == 0) {
+        ctl[CTL_REBUILD] = 1u;
+        if (COND) __threadfence();
+    }
+    if (COND) {
+        // the last block to finish hands the rebuild decision to the graph's
+        // IF node (a single caller of cudaGraphSetConditional per launch)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            unsigned t = atomicAdd(&ctl[CTL_TICKET2], 1u);
+            last = (t == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (last && threadIdx.x == 0) {
+            __threadfence();
+            unsigned flag = *(volatile uint32_t *)&ctl[CTL_REBUILD];
+            ctl[CTL_TICKET2] = 0u;
+            cudaGraphSetConditional((cudaGraphConditionalHandle)cond_if, flag ? 1u : 0u);
+        }
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_gd_step(float4 *r, const float4 *f, const float4 *rref, int N, float eta,
+                                                 Box box, float half_skin2, uint32_t *ctl)
+{
+    count_launch();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool mv = false;
+    if (i < N) {
+        float4 fi = f[i], ri = r[i];
+        ri.x += eta * fi.x;
+        ri.y += eta * fi.y;
+        if (DIM == 3) ri.z += eta * fi.z;
+        r[i] = ri;
+        float dx, dy, dz;
+        mv = dist2_rn<DIM>(ri, rref[i], box, dx, dy, dz) > half_skin2;
+    }
+    if (__any_sync(0xffffffffu, mv) && (threadIdx.x & 31) == 0) ctl[CTL_REBUILD] = 1u;
+}
+
+__global__ void k_loop_init(uint32_t *ctl, uint32_t nsteps)
+{
+    count_launch();
+    ctl[CTL_STEP] = 0u;
+    ctl[CTL_NSTEPS] = nsteps;
+}
+
+struct NveCtx {
+    Box box;
+    int dim, N;
+    float4 *r, *v, *f, *rref;
+    float hdm, dt, half_skin2;
+    uint32_t *ctl;
+    NbrArgs na;
+    int ncell_total;
+    PairArgs pa;
+    int pot;
+    unsigned long long cond_if;   // graph IF handle (0 outside graphs)
+};
+
+static void enqueue_kick_drift(const NveCtx &c, int cond, cudaStream_t st)
+{
+    int g = (c.N + 255) / 256;
+    if (c.dim == 3) {
+        if (cond)
+            k_kick_drift<3, 1><<<g, 256, 0, st>>>(c.r, c.v, c.f, c.rref, c.N, c.hdm, c.dt, c.box, c.half_skin2, c.ctl,
+                                                  c.cond_if);
+        else
+            k_kick_drift<3, 0><<<g, 256, 0, st>>>(c.r, c.v, c.f, c.rref, c.N, c.hdm, c.dt, c.box, c.half_skin2, c.ctl,
+                                                  0ull);
+    } else {
+        if (cond)
+            k_kick_drift<2, 1><<<g, 256, 0, st>>>(c.r, c.v, c.f, c.rref, c.N, c.hdm, c.dt, c.box, c.half_skin2, c.ctl,
+                                                  c.cond_if);
+        else
+            k_kick_drift<2, 0><<<g, 256, 0, st>>>(c.r, c.v, c.f, c.rref, c.N, c.hdm, c.dt, c.box, c.half_skin2, c.ctl,
+                                                  0ull);
+    }
+}
+
+static void enqueue_nve_step(const NveCtx &c, cudaStream_t st)
+{
+    enqueue_kick_drift(c, 0, st);
+    enqueue_rebuild_chain(c.na, c.ncell_total, st);
+    enqueue_pair(c.pa, c.dim, c.pot, 1, st);
+}
+
+// ---------------------------------------------------------------------------
+// The whole NVE loop as one CUDA graph: a WHILE node whose body is one step,
+// with the rebuild chain under an IF node.  The kick-drift kernel's last
+// block sets the IF condition from the device rebuild flag; the force
+// kernel's last block advances the step counter and sets the WHILE
+// condition.  No host involvement per step and no launches of an idle
+// rebuild chain.  Graphs are cached per argument set and device.
+// ---------------------------------------------------------------------------
+struct NveGraph {
+    NveCtx key;
+    int device;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+static std::vector<NveGraph> g_nve_graphs;
+static std::mutex g_nve_mu;
+
+static cudaGraphNodeParams *zeroed_params(unsigned char *raw)
+{
+    memset(raw, 0, sizeof(cudaGraphNodeParams));
+    return reinterpret_cast<cudaGraphNodeParams *>(raw);
+}
+
+static md_status build_nve_graph(const NveCtx &c0, NveGraph &out)
+{
+    NveCtx c = c0;
+    cudaGraph_t g = nullptr;
+    JMD_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle hw, hi;
+    JMD_CUDA_TRY(cudaGraphConditionalHandleCreate(&hw, g, 1u, cudaGraphCondAssignDefault));
+    JMD_CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, g, 0u, cudaGraphCondAssignDefault));
+    alignas(cudaGraphNodeParams) unsigned char wraw[sizeof(cudaGraphNodeParams)];
+    cudaGraphNodeParams *wp = zeroed_params(wraw);
+    wp->type = cudaGraphNodeTypeConditional;
+    wp->conditional.handle = hw;
+    wp->conditional.type = cudaGraphCondTypeWhile;
+    wp->conditional.size = 1;
+    cudaGraphNode_t wn;
+    JMD_CUDA_TRY(cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, wp));
+    cudaGraph_t body = wp->conditional.phGraph_out[0];
+
+    cudaStream_t cs = nullptr, cs2 = nullptr;
+    JMD_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    JMD_CUDA_TRY(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
+    JMD_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    c.cond_if = (unsigned long long)hi;
+    c.pa.cond_while = (unsigned long long)hw;
+    c.pa.use_cond = 1;
+    enqueue_kick_drift(c, 1, cs);
+
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    JMD_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd));
+    alignas(cudaGraphNodeParams) unsigned char iraw[sizeof(cudaGraphNodeParams)];
+    cudaGraphNodeParams *ip = zeroed_params(iraw);
+    ip->type = cudaGraphNodeTypeConditional;
+    ip->conditional.handle = hi;
+    ip->conditional.type = cudaGraphCondTypeIf;
+    ip->conditional.size = 1;
+    cudaGraphNode_t in;
+    JMD_CUDA_TRY(cudaGraphAddNode(&in, cg, deps, nullptr, nd, ip));
+    JMD_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &in, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t ibody = ip->conditional.phGraph_out[0];
+    JMD_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs2, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    NbrArgs na = c.na;
+    na.gated = 0;
+    enqueue_rebuild_chain(na, c.ncell_total, cs2);
+    JMD_CUDA_TRY(cudaStreamEndCapture(cs2, &ibody));
+
+    enqueue_pair(c.pa, c.dim, c.pot, 1, cs);
+    JMD_CUDA_TRY(cudaStreamEndCapture(cs, &body));
+    cudaStreamDestroy(cs2);
+    cudaStreamDestroy(cs);
+
+    cudaGraphExec_t ex = nullptr;
+    JMD_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
+    out.key = c0;
+    out.graph = g;
+    out.exec = ex;
+    return MD_OK;
+}
+
+static md_status nve_graph_run(const NveCtx &c, int nsteps, cudaStream_t st)
+{
+    int dev = 0;
+    JMD_CUDA_TRY(cudaGetDevice(&dev));
+    cudaGraphExec_t ex = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_nve_mu);
+        for (auto &e : g_nve_graphs)
+            if (e.device == dev && memcmp(&e.key, &c, sizeof(NveCtx)) == 0) ex = e.exec;
+        if (!ex) {
+            NveGraph ng;
+            memset(&ng, 0, sizeof(ng));
+            md_status s = build_nve_graph(c, ng);
+            if (s != MD_OK) return s;
+            ng.device = dev;
+            g_nve_graphs.push_back(ng);
+            ex = ng.exec;
+        }
+    }
+    k_loop_init<<<1, 1, 0, st>>>(c.ctl, (uint32_t)nsteps);
+    JMD_CUDA_TRY(cudaGraphLaunch(ex, st));
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+}  // namespace jmd
+
+using namespace jmd;
+
+extern "C" md_status md_integrate_nve(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f,
+                                      float mass, float dt, int nsteps, md_nbr *nb, double *d_PE, double *d_KE,
+                                      int use_graph, uint32_t *d_status, md_stream_t stream)
+{
+    if (!s || !p || !d_r || !d_v || !d_f || !nb || nsteps < 0 || !(mass > 0.0f)) return MD_ERR_INVALID;
+    if (s->dim != nb->dim || !nb->ws || !nb->rref) return MD_ERR_INVALID;
+    if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE) return MD_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    NveCtx c;
+    memset(&c, 0, sizeof(c));   // the graph cache compares contexts bytewise
+    c.box = make_box(s);
+    c.dim = s->dim;
+    c.N = nb->N;
+    c.r = (float4 *)d_r;
+    c.v = (float4 *)d_v;
+    c.f = (float4 *)d_f;
+    c.rref = (float4 *)nb->rref;
+    c.hdm = 0.5f * dt / mass;
+    c.dt = dt;
+    c.half_skin2 = nb->half_skin2;
+    c.ctl = ws_ptrs(nb).ctl;
+    c.na = make_nbr_args(s, d_r, nb, d_status, 1);
+    c.ncell_total = nb->ncell_total;
+    if (!make_pair_args(s, p, d_r, nb, d_f, c.pa)) return MD_ERR_INVALID;
+    c.pa.v = (float4 *)d_v;
+    c.pa.half_dt_over_m = c.hdm;
+    c.pa.mass = mass;
+    c.pa.E_out = d_PE;
+    c.pa.KE_out = d_KE;
+    c.pa.series = 1;
+    c.pa.status = d_status;
+    c.pot = p->kind;
+    if (nsteps == 0) return MD_OK;
+    if (use_graph) return nve_graph_run(c, nsteps, st);
+    k_loop_init<<<1, 1, 0, st>>>(c.ctl, (uint32_t)nsteps);
+    for (int k = 0; k < nsteps; ++k) enqueue_nve_step(c, st);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+extern "C" md_status md_minimize(const md_space *s, const md_pot *p, int kind, float step, int nsteps, float *d_r,
+                                 float *d_f, md_nbr *nb, double *d_E, uint32_t *d_status, md_stream_t stream)
+{
+    if (!s || !p || !d_r || !d_f || !nb || nsteps < 0 || kind != 0) return MD_ERR_INVALID;
+    if (s->dim != nb->dim || !nb->ws || !nb->rref) return MD_ERR_INVALID;
+    if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE) return MD_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    PairArgs pa;
+    if (!make_pair_args(s, p, d_r, nb, d_f, pa)) return MD_ERR_INVALID;
+    pa.E_out = d_E;
+    pa.series = d_E ? 1 : 0;
+    pa.status = d_status;
+    NbrArgs na = make_nbr_args(s, d_r, nb, d_status, 1);
+    uint32_t *ctl = ws_ptrs(nb).ctl;
+    Box box = make_box(s);
+    int g = (nb->N + 255) / 256;
+    k_loop_init<<<1, 1, 0, st>>>(ctl, (uint32_t)(nsteps + 1));
+    for (int t = 0; t < nsteps; ++t) {
+        enqueue_pair(pa, s->dim, p->kind, 0, st);
+        if (s->dim == 3)
+            k_gd_step<3><<<g, 256, 0, st>>>((float4 *)d_r, (const float4 *)d_f, (const float4 *)nb->rref, nb->N, step,
+                                            box, nb->half_skin2, ctl);
+        else
+            k_gd_step<2><<<g, 256, 0, st>>>((float4 *)d_r, (const float4 *)d_f, (const float4 *)nb->rref, nb->N, step,
+                                            box, nb->half_skin2, ctl);
+        enqueue_rebuild_chain(na, nb->ncell_total, st);
+    }
+    enqueue_pair(pa, s->dim, p->kind, 0, st);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}

@@ -1,0 +1,60 @@
+// kernels.cuh -- argument blocks and enqueue functions shared between the
+// libjmd translation units (host side).
+#pragma once
+
+#include "common.cuh"
+
+namespace jmd {
+
+struct NbrArgs {
+    Box box;
+    int N, cap, dim;
+    int nc[3];
+    float cell_scale[3];
+    float r_list2;
+    const float4 *r;
+    int32_t *nbr, *cnt;
+    float4 *rref;
+    WsPtrs ws;
+    uint32_t *status;
+    int gated;   // 1: run only if ctl[CTL_REBUILD] != 0
+};
+
+struct PairArgs {
+    Box box;
+    int N, cap, tpp;
+    const float4 *r;
+    const int32_t *nbr, *cnt;
+    float4 *f;
+    float4 *v;              // KICK only
+    float half_dt_over_m;   // KICK only
+    float mass;             // KICK only (kinetic energy)
+    // LJ
+    float rc2, sigma2, c24eps, c4eps, e_shift;
+    // soft sphere
+    float eps, alpha;
+    // reductions
+    double *E_out, *KE_out;
+    int series;             // 1: write E_out[ctl[CTL_STEP]] and advance the counter
+    uint32_t *ctl;
+    double2 *partials;
+    uint32_t *status;
+    // device-side loop control inside a CUDA graph WHILE node: the last
+    // block sets the loop condition to (step + 1 < ctl[CTL_NSTEPS])
+    unsigned long long cond_while;
+    int use_cond;
+};
+
+NbrArgs make_nbr_args(const md_space *s, const float *d_r, const md_nbr *nb, uint32_t *d_status, int gated);
+void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st);
+void enqueue_check_disp(const md_space *s, const float *d_r, const md_nbr *nb, cudaStream_t st);
+
+bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const md_nbr *nb, float *d_f,
+                    PairArgs &a);
+void enqueue_pair(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st);
+int pair_blocks(int N, int tpp);
+
+}  // namespace jmd
+
+md_status md_energy_forces_sw(const md_space *s, const md_pot *p, const float *d_r, const md_nbr *nb, float *d_f,
+                              double *d_E, uint32_t *d_status, md_stream_t stream);

@@ -1,0 +1,405 @@
+// nbr.cu -- cell-list binning and Verlet neighbor-list build (Sec. 3.2.3).
+//
+// Rebuild chain (every kernel can be gated by the device rebuild flag, so the
+// chain can sit in a stream and cost only an early exit when no particle has
+// moved more than skin/2; inside the NVE graph it sits under an IF node and
+// runs ungated):
+//   k_bin_count : cell of each particle; warp-aggregated atomic histogram
+//                 (one atomic per distinct cell per warp); the returned
+//                 offset is the particle's rank inside its cell
+//   k_scan      : exclusive scan of the histogram -> cell_start (1 CTA);
+//                 zeroes the histogram for the next build
+//   k_scatter   : counting-sort scatter of indices and a cell-ordered float4
+//                 copy of the positions (coalesced candidate reads)
+//   k_build     : one warp per particle scans the 27 (9 in 2-D) stencil
+//                 cells, compacts hits with ballot into shared memory,
+//                 bitonic-sorts the row and writes it as a padded int32 row
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace jmd {
+
+__device__ __forceinline__ int cell_axis(float x, float L, float Linv, float scale, int n)
+{
+    float y = wrap_coord(x, L, Linv);
+    int q = (int)(y * scale);
+    return q < 0 ? 0 : (q >= n ? n - 1 : q);
+}
+
+__device__ __forceinline__ bool chain_active(const NbrArgs &a)
+{
+    return !a.gated || *(volatile uint32_t *)&a.ws.ctl[CTL_REBUILD] != 0u;
+}
+
+__global__ void __launch_bounds__(256) k_bin_count(NbrArgs a)
+{
+    count_launch();
+    if (!chain_active(a)) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool act = i < a.N;
+    int c = -1;
+    if (act) {
+        float4 p = a.r[i];
+        int cx = cell_axis(p.x, a.box.L[0], a.box.Linv[0], a.cell_scale[0], a.nc[0]);
+        int cy = cell_axis(p.y, a.box.L[1], a.box.Linv[1], a.cell_scale[1], a.nc[1]);
+        int cz = a.dim == 3 ? cell_axis(p.z, a.box.L[2], a.box.Linv[2], a.cell_scale[2], a.nc[2]) : 0;
+        c = (cz * a.nc[1] + cy) * a.nc[0] + cx;
+    }
+    unsigned amask = __ballot_sync(0xffffffffu, act);
+    if (!act) return;
+    unsigned peers = __match_any_sync(amask, c);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(peers) - 1;
+    int below = __popc(peers & ((1u << lane) - 1u));
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&a.ws.cell_count[c], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    a.ws.cell_of[i] = c;
+    a.ws.rank[i] = base + below;
+}
+
+// Exclusive scan over ncell counts by one CTA of 1024 threads; each thread
+// owns a contiguous chunk.  Also clears the histogram for the next build.
+__global__ void __launch_bounds__(1024) k_scan(NbrArgs a, int ncell)
+{
+    count_launch();
+    if (!chain_active(a)) return;
+    __shared__ int warp_tot[32];
+    int t = threadIdx.x;
+    int per = (ncell + blockDim.x - 1) / blockDim.x;
+    int b = t * per, e = min(b + per, ncell);
+    int s = 0;
+    for (int q = b; q < e; ++q) s += a.ws.cell_count[q];
+    int lane = t & 31, w = t >> 5;
+    int x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int v = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        warp_tot[lane] = v;   // inclusive over warps
+    }
+    __syncthreads();
+    int run = x - s + (w > 0 ? warp_tot[w - 1] : 0);
+    for (int q = b; q < e; ++q) {
+        a.ws.cell_start[q] = run;
+        run += a.ws.cell_count[q];
+        a.ws.cell_count[q] = 0;
+    }
+    if (t == blockDim.x - 1) a.ws.cell_start[ncell] = warp_tot[(blockDim.x >> 5) - 1];
+}
+
+__global__ void __launch_bounds__(256) k_scatter(NbrArgs a)
+{
+    count_launch();
+    if (!chain_active(a)) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    int slot = a.ws.cell_start[a.ws.cell_of[i]] + a.ws.rank[i];
+    a.ws.atoms[slot] = i;
+    a.ws.rsorted[slot] = a.r[i];
+}
+
+// Per-axis stencil cells with duplicates (fewer than 3 cells) removed.
+__device__ __forceinline__ int axis_cells(int q, int n, int *out)
+{
+    if (n >= 3) {
+        out[0] = q == 0 ? n - 1 : q - 1;
+        out[1] = q;
+        out[2] = q == n - 1 ? 0 : q + 1;
+        return 3;
+    }
+    if (n == 2) {
+        out[0] = 0;
+        out[1] = 1;
+        return 2;
+    }
+    out[0] = 0;
+    return 1;
+}
+
+template <int DIM, int WARPS, int CAPP2>
+__global__ void __launch_bounds__(WARPS * 32) k_build(NbrArgs a)
+{
+    count_launch();
+    if (!chain_active(a)) return;
+    __shared__ int rows[WARPS][CAPP2];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int i = blockIdx.x * WARPS + w;
+    if (i >= a.N) return;   // whole warp leaves together
+    int *row = rows[w];
+    float4 ri = a.r[i];
+    int c = a.ws.cell_of[i];
+    int cx = c % a.nc[0];
+    int cy = (c / a.nc[0]) % a.nc[1];
+    int cz = c / (a.nc[0] * a.nc[1]);
+    int sx[3], sy[3], sz[3];
+    int mx = axis_cells(cx, a.nc[0], sx);
+    int my = axis_cells(cy, a.nc[1], sy);
+    int mz = DIM == 3 ? axis_cells(cz, a.nc[2], sz) : 1;
+    if (DIM != 3) sz[0] = 0;
+    int count = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int zz = 0; zz < mz; ++zz)
+        for (int yy = 0; yy < my; ++yy)
+            for (int xx = 0; xx < mx; ++xx) {
+                int q = (sz[zz] * a.nc[1] + sy[yy]) * a.nc[0] + sx[xx];
+                int b = a.ws.cell_start[q], e = a.ws.cell_start[q + 1];
+                for (int s = b; s < e; s += 32) {
+                    int slot = s + lane;
+                    bool hit = false;
+                    int j = 0;
+                    if (slot < e) {
+                        j = a.ws.atoms[slot];
+                        float4 rj = a.ws.rsorted[slot];
+                        float dx, dy, dz;
+                        float r2 = dist2_rn<DIM>(ri, rj, a.box, dx, dy, dz);
+                        hit = (j != i) && (r2 < a.r_list2);
+                    }
+                    unsigned m = __ballot_sync(0xffffffffu, hit);
+                    int pos = count + __popc(m & lt);
+                    if (hit && pos < CAPP2) row[pos] = j;
+                    count += __popc(m);
+                }
+            }
+    __syncwarp();
+    int n = count < a.cap ? count : a.cap;
+    // pad to the power of two with INT_MAX and bitonic-sort ascending
+    for (int k = n + lane; k < CAPP2; k += 32) row[k] = 0x7fffffff;
+    __syncwarp();
+    for (int size = 2; size <= CAPP2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < CAPP2 / 2; t += 32) {
+                int lo = 2 * t - (t & (stride - 1));
+                int hi = lo + stride;
+                bool up = ((lo & size) == 0);
+                int x = row[lo], y = row[hi];
+                if ((x > y) == up) {
+                    row[lo] = y;
+                    row[hi] = x;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    int32_t *out = a.nbr + (size_t)i * a.cap;
+    for (int k = lane; k < a.cap; k += 32) out[k] = (k < n) ? row[k] : a.N;
+    if (lane == 0) {
+        a.cnt[i] = count;
+        a.rref[i] = ri;
+        if (count > a.cap) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+        atomicMax(&a.ws.ctl[CTL_MAXCNT], (uint32_t)count);
+    }
+}
+
+// Sets the rebuild flag if any particle moved more than skin/2 (minimum
+// image) since the last build.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_check_disp(const float4 *r, const float4 *rref, int N, Box box,
+                                                    float half_skin2, uint32_t *ctl)
+{
+    count_launch();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool mv = false;
+    if (i < N) {
+        float dx, dy, dz;
+        mv = dist2_rn<DIM>(r[i], rref[i], box, dx, dy, dz) > half_skin2;
+    }
+    if (__any_sync(0xffffffffu, mv) && (threadIdx.x & 31) == 0) ctl[CTL_REBUILD] = 1u;
+}
+
+__global__ void k_set_flag(uint32_t *ctl, uint32_t v)
+{
+    count_launch();
+    ctl[CTL_REBUILD] = v;
+}
+
+// Counts a finished build and clears the rebuild flag (single thread).
+__global__ void k_finish_build(uint32_t *ctl)
+{
+    count_launch();
+    if (ctl[CTL_REBUILD] != 0u) {
+        unsigned long long *b = (unsigned long long *)&ctl[CTL_BUILDS_LO];
+        *b += 1ull;
+    }
+    ctl[CTL_REBUILD] = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+NbrArgs make_nbr_args(const md_space *s, const float *d_r, const md_nbr *nb, uint32_t *d_status, int gated)
+{
+    NbrArgs a;
+    memset(&a, 0, sizeof(a));
+    a.box = make_box(s);
+    a.N = nb->N;
+    a.cap = nb->cap;
+    a.dim = nb->dim;
+    for (int k = 0; k < 3; ++k) {
+        a.nc[k] = nb->ncell[k];
+        a.cell_scale[k] = nb->cell_scale[k];
+    }
+    a.r_list2 = nb->r_list2;
+    a.r = (const float4 *)d_r;
+    a.nbr = nb->nbr;
+    a.cnt = nb->cnt;
+    a.rref = (float4 *)nb->rref;
+    a.ws = ws_ptrs(nb);
+    a.status = d_status;
+    a.gated = gated;
+    return a;
+}
+
+template <int DIM, int CAPP2>
+static void launch_build(const NbrArgs &a, cudaStream_t st)
+{
+    constexpr int W = CAPP2 <= 128 ? 8 : 4;
+    k_build<DIM, W, CAPP2><<<(a.N + W - 1) / W, W * 32, 0, st>>>(a);
+}
+
+template <int DIM>
+static void launch_build_dim(const NbrArgs &a, cudaStream_t st)
+{
+    if (a.cap <= 32) launch_build<DIM, 32>(a, st);
+    else if (a.cap <= 64) launch_build<DIM, 64>(a, st);
+    else if (a.cap <= 128) launch_build<DIM, 128>(a, st);
+    else if (a.cap <= 256) launch_build<DIM, 256>(a, st);
+    else launch_build<DIM, 512>(a, st);
+}
+
+// Enqueue the (gated or ungated) rebuild chain.  The flag is consumed by
+// k_finish_build at the end.
+void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st)
+{
+    int tb = 256, nb = (a.N + tb - 1) / tb;
+    k_bin_count<<<nb, tb, 0, st>>>(a);
+    k_scan<<<1, 1024, 0, st>>>(a, ncell_total);
+    k_scatter<<<nb, tb, 0, st>>>(a);
+    if (a.dim == 3) launch_build_dim<3>(a, st);
+    else launch_build_dim<2>(a, st);
+    k_finish_build<<<1, 1, 0, st>>>(a.ws.ctl);
+}
+
+void enqueue_check_disp(const md_space *s, const float *d_r, const md_nbr *nb, cudaStream_t st)
+{
+    WsPtrs w = ws_ptrs(nb);
+    int tb = 256, g = (nb->N + tb - 1) / tb;
+    Box box = make_box(s);
+    if (nb->dim == 3)
+        k_check_disp<3><<<g, tb, 0, st>>>((const float4 *)d_r, (const float4 *)nb->rref, nb->N, box, nb->half_skin2,
+                                          w.ctl);
+    else
+        k_check_disp<2><<<g, tb, 0, st>>>((const float4 *)d_r, (const float4 *)nb->rref, nb->N, box, nb->half_skin2,
+                                          w.ctl);
+}
+
+static bool nbr_ready(const md_nbr *nb)
+{
+    return nb && nb->nbr && nb->cnt && nb->rref && nb->ws && nb->N > 0 && nb->cap > 0 && nb->cap <= 512;
+}
+
+}  // namespace jmd
+
+using namespace jmd;
+
+extern "C" md_status md_nbr_plan(const md_space *s, int N, float r_cut, float skin, int cap, md_nbr *out)
+{
+    if (!s || !out || N < 1 || cap < 1 || cap > 512 || !(r_cut > 0.0f) || !(skin >= 0.0f) ||
+        (s->dim != 2 && s->dim != 3))
+        return MD_ERR_INVALID;
+    md_nbr nb;
+    memset(&nb, 0, sizeof(nb));
+    nb.dim = s->dim;
+    nb.N = N;
+    nb.cap = cap;
+    nb.r_cut = r_cut;
+    nb.skin = skin;
+    float rl = r_cut + skin;
+    nb.r_list = rl;
+    nb.r_list2 = rl * rl;
+    float hs = 0.5f * skin;
+    nb.half_skin2 = hs * hs;
+    nb.ncell_total = 1;
+    for (int k = 0; k < 3; ++k) {
+        nb.ncell[k] = 1;
+        nb.cell_scale[k] = 0.0f;
+        if (k < s->dim) {
+            if ((double)s->L[k] < 2.0 * (double)rl) return MD_ERR_BOX_TOO_SMALL;
+            // cells of side >= r_list with a margin above FP32 rounding of
+            // coordinates and of the membership test
+            int n = (int)floor((double)s->L[k] / ((double)rl * (1.0 + 1e-4)));
+            nb.ncell[k] = n < 1 ? 1 : n;
+            nb.cell_scale[k] = (float)((double)nb.ncell[k] / (double)s->L[k]);
+        }
+        nb.ncell_total *= nb.ncell[k];
+    }
+    nb.ws_bytes = ws_layout(N, nb.ncell_total).total;
+    *out = nb;
+    return MD_OK;
+}
+
+extern "C" md_status md_nbr_bind(md_nbr *nb, int32_t *d_nbr, int32_t *d_cnt, float *d_rref, void *d_ws,
+                                 md_stream_t stream)
+{
+    if (!nb || !d_nbr || !d_cnt || !d_rref || !d_ws) return MD_ERR_INVALID;
+    if (((uintptr_t)d_ws & 255u) || ((uintptr_t)d_rref & 15u)) return MD_ERR_INVALID;
+    nb->nbr = d_nbr;
+    nb->cnt = d_cnt;
+    nb->rref = d_rref;
+    nb->ws = d_ws;
+    WsPtrs w = ws_ptrs(nb);
+    cudaStream_t st = (cudaStream_t)stream;
+    JMD_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, sizeof(uint32_t) * CTL_WORDS, st));
+    JMD_CUDA_TRY(cudaMemsetAsync(w.cell_count, 0, sizeof(int32_t) * (size_t)nb->ncell_total, st));
+    return MD_OK;
+}
+
+extern "C" md_status md_neighbor_list_build(const md_space *s, const float *d_r, md_nbr *nb, uint32_t *d_status,
+                                            md_stream_t stream)
+{
+    if (!s || !d_r || !nbr_ready(nb) || s->dim != nb->dim) return MD_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    WsPtrs w = ws_ptrs(nb);
+    k_set_flag<<<1, 1, 0, st>>>(w.ctl, 1u);
+    NbrArgs a = make_nbr_args(s, d_r, nb, d_status, 1);
+    enqueue_rebuild_chain(a, nb->ncell_total, st);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+extern "C" md_status md_neighbor_list_update(const md_space *s, const float *d_r, md_nbr *nb, uint32_t *d_status,
+                                             md_stream_t stream)
+{
+    if (!s || !d_r || !nbr_ready(nb) || s->dim != nb->dim) return MD_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    enqueue_check_disp(s, d_r, nb, st);
+    NbrArgs a = make_nbr_args(s, d_r, nb, d_status, 1);
+    enqueue_rebuild_chain(a, nb->ncell_total, st);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+extern "C" md_status md_nbr_stats(const md_nbr *nb, int64_t *builds, int32_t *max_count, md_stream_t stream)
+{
+    if (!nbr_ready(nb)) return MD_ERR_INVALID;
+    WsPtrs w = ws_ptrs(nb);
+    uint32_t h[CTL_WORDS];
+    cudaStream_t st = (cudaStream_t)stream;
+    JMD_CUDA_TRY(cudaMemcpyAsync(h, w.ctl, sizeof(h), cudaMemcpyDeviceToHost, st));
+    JMD_CUDA_TRY(cudaStreamSynchronize(st));
+    if (builds) *builds = (int64_t)(((uint64_t)h[CTL_BUILDS_HI] << 32) | h[CTL_BUILDS_LO]);
+    if (max_count) *max_count = (int32_t)h[CTL_MAXCNT];
+    return MD_OK;
+}

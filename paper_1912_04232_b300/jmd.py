@@ -1,0 +1,252 @@
+"""Thin ctypes binding over libjmd (include/jmd.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of libjmd.so.  torch tensors serve as device storage; the binding
+passes their data pointers and the current CUDA stream.  There is no CPU
+fallback: if libjmd.so is missing the import fails, and every call checks
+that its tensors live on a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libjmd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libjmd.so not found at {LIB_PATH}: build it with `python -m paper_1912_04232_b300.build` "
+        "(nvcc, sm_103a). There is no fallback implementation.")
+
+_lib = C.CDLL(LIB_PATH)
+
+# status bits (md_status)
+MD_OK = 0
+MD_ERR_INVALID = 1
+MD_ERR_BOX_TOO_SMALL = 2
+MD_ERR_NBR_OVERFLOW = 4
+MD_ERR_NONFINITE = 8
+MD_ERR_TIMEOUT = 16
+MD_ERR_BOUNDS = 32
+MD_ERR_CUDA = 64
+
+MD_LJ, MD_SOFT_SPHERE, MD_SW, MD_BP = 0, 1, 2, 3
+
+STATUS_NAMES = {MD_ERR_INVALID: "INVALID", MD_ERR_BOX_TOO_SMALL: "BOX_TOO_SMALL",
+                MD_ERR_NBR_OVERFLOW: "NBR_OVERFLOW", MD_ERR_NONFINITE: "NONFINITE",
+                MD_ERR_TIMEOUT: "TIMEOUT", MD_ERR_BOUNDS: "BOUNDS", MD_ERR_CUDA: "CUDA"}
+
+
+class MDError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        names = [n for b, n in STATUS_NAMES.items() if code & b] or [str(code)]
+        super().__init__(f"{where}: md_status {code} ({'|'.join(names)})")
+        self.code = code
+
+
+class md_space(C.Structure):
+    _fields_ = [("dim", C.c_int), ("L", C.c_float * 3), ("Linv", C.c_float * 3), ("L64", C.c_double * 3)]
+
+
+class md_nbr(C.Structure):
+    _fields_ = [("dim", C.c_int), ("N", C.c_int), ("cap", C.c_int), ("ncell", C.c_int * 3),
+                ("ncell_total", C.c_int), ("r_cut", C.c_float), ("skin", C.c_float), ("r_list", C.c_float),
+                ("r_list2", C.c_float), ("half_skin2", C.c_float), ("cell_scale", C.c_float * 3),
+                ("ws_bytes", C.c_size_t), ("nbr", C.c_void_p), ("cnt", C.c_void_p), ("rref", C.c_void_p),
+                ("ws", C.c_void_p)]
+
+
+class md_pot(C.Structure):
+    _fields_ = [("kind", C.c_int), ("eps", C.c_float), ("sigma", C.c_float), ("r_cut", C.c_float),
+                ("e_shift", C.c_float), ("alpha", C.c_float), ("sw", C.c_float * 10), ("model", C.c_void_p)]
+
+
+_P = C.POINTER
+_vp = C.c_void_p
+_SIGS = {
+    "md_space_periodic": [C.c_int, _P(C.c_double), _P(md_space)],
+    "md_nbr_plan": [_P(md_space), C.c_int, C.c_float, C.c_float, C.c_int, _P(md_nbr)],
+    "md_nbr_bind": [_P(md_nbr), _vp, _vp, _vp, _vp, _vp],
+    "md_neighbor_list_build": [_P(md_space), _vp, _P(md_nbr), _vp, _vp],
+    "md_neighbor_list_update": [_P(md_space), _vp, _P(md_nbr), _vp, _vp],
+    "md_nbr_stats": [_P(md_nbr), _P(C.c_int64), _P(C.c_int32), _vp],
+    "md_energy_forces": [_P(md_space), _P(md_pot), _vp, _P(md_nbr), _vp, _vp, _vp, _vp],
+    "md_set_pair_tpp": [C.c_int],
+    "md_integrate_nve": [_P(md_space), _P(md_pot), _vp, _vp, _vp, C.c_float, C.c_float, C.c_int, _P(md_nbr),
+                         _vp, _vp, C.c_int, _vp, _vp],
+    "md_minimize": [_P(md_space), _P(md_pot), C.c_int, C.c_float, C.c_int, _vp, _vp, _P(md_nbr), _vp, _vp, _vp],
+    "md_status_poll": [_vp, _P(C.c_uint32), _vp],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.md_launch_count.restype = C.c_uint64
+_lib.md_launch_count.argtypes = []
+_lib.md_version.restype = C.c_char_p
+_lib.md_version.argtypes = []
+
+
+def lib():
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != MD_OK:
+        raise MDError(code, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libjmd needs CUDA tensors (no CPU fallback)")
+    if not t.is_contiguous():
+        raise ValueError("libjmd needs contiguous tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ----------------------------------------------------------------------------
+# C ABI, same names (Sec. 3.2.1 - 3.3.2)
+# ----------------------------------------------------------------------------
+def md_space_periodic(dim: int, box) -> md_space:
+    vals = [float(x) for x in (box if hasattr(box, "__len__") else [box] * dim)]
+    b = (C.c_double * 3)(*(vals + [1.0, 1.0, 1.0])[:3])
+    out = md_space()
+    _check(_lib.md_space_periodic(int(dim), b, C.byref(out)), "md_space_periodic")
+    return out
+
+
+def md_nbr_plan(space: md_space, N: int, r_cut: float, skin: float, cap: int) -> md_nbr:
+    out = md_nbr()
+    _check(_lib.md_nbr_plan(C.byref(space), int(N), float(r_cut), float(skin), int(cap), C.byref(out)),
+           "md_nbr_plan")
+    return out
+
+
+def md_nbr_bind(nb: md_nbr, nbr, cnt, rref, ws, stream=None):
+    _check(_lib.md_nbr_bind(C.byref(nb), _ptr(nbr), _ptr(cnt), _ptr(rref), _ptr(ws), _stream(stream)),
+           "md_nbr_bind")
+
+
+def md_neighbor_list_build(space, r, nb, status, stream=None):
+    _check(_lib.md_neighbor_list_build(C.byref(space), _ptr(r), C.byref(nb), _ptr(status), _stream(stream)),
+           "md_neighbor_list_build")
+
+
+def md_neighbor_list_update(space, r, nb, status, stream=None):
+    _check(_lib.md_neighbor_list_update(C.byref(space), _ptr(r), C.byref(nb), _ptr(status), _stream(stream)),
+           "md_neighbor_list_update")
+
+
+def md_nbr_stats(nb, stream=None):
+    b = C.c_int64()
+    m = C.c_int32()
+    _check(_lib.md_nbr_stats(C.byref(nb), C.byref(b), C.byref(m), _stream(stream)), "md_nbr_stats")
+    return b.value, m.value
+
+
+def md_energy_forces(space, pot, r, nb, f, E=None, status=None, stream=None):
+    _check(_lib.md_energy_forces(C.byref(space), C.byref(pot), _ptr(r), C.byref(nb), _ptr(f), _ptr(E),
+                                 _ptr(status), _stream(stream)), "md_energy_forces")
+
+
+def md_set_pair_tpp(tpp: int):
+    _check(_lib.md_set_pair_tpp(int(tpp)), "md_set_pair_tpp")
+
+
+def md_integrate_nve(space, pot, r, v, f, mass, dt, nsteps, nb, PE=None, KE=None, use_graph=True, status=None,
+                     stream=None):
+    _check(_lib.md_integrate_nve(C.byref(space), C.byref(pot), _ptr(r), _ptr(v), _ptr(f), float(mass), float(dt),
+                                 int(nsteps), C.byref(nb), _ptr(PE), _ptr(KE), int(bool(use_graph)), _ptr(status),
+                                 _stream(stream)), "md_integrate_nve")
+
+
+def md_minimize(space, pot, kind, step, nsteps, r, f, nb, E=None, status=None, stream=None):
+    _check(_lib.md_minimize(C.byref(space), C.byref(pot), int(kind), float(step), int(nsteps), _ptr(r), _ptr(f),
+                            C.byref(nb), _ptr(E), _ptr(status), _stream(stream)), "md_minimize")
+
+
+def md_status_poll(status, stream=None) -> int:
+    h = C.c_uint32()
+    _check(_lib.md_status_poll(_ptr(status), C.byref(h), _stream(stream)), "md_status_poll")
+    return h.value
+
+
+def md_launch_count() -> int:
+    return int(_lib.md_launch_count())
+
+
+def md_version() -> str:
+    return _lib.md_version().decode()
+
+
+# ----------------------------------------------------------------------------
+# Potential descriptors
+# ----------------------------------------------------------------------------
+def lj_pot(eps=1.0, sigma=1.0, r_cut=2.5, shifted=True) -> md_pot:
+    """LJ (Sec. 3.3.2): e_shift = u(r_cut) evaluated in FP64 when shifted."""
+    p = md_pot()
+    p.kind = MD_LJ
+    p.eps, p.sigma, p.r_cut = eps, sigma, r_cut
+    sr6 = (sigma / r_cut) ** 6
+    p.e_shift = 4.0 * eps * (sr6 * sr6 - sr6) if shifted else 0.0
+    return p
+
+
+def soft_pot(eps=1.0, alpha=2.0) -> md_pot:
+    p = md_pot()
+    p.kind = MD_SOFT_SPHERE
+    p.eps, p.alpha = eps, alpha
+    return p
+
+
+def sw_pot(params) -> md_pot:
+    p = md_pot()
+    p.kind = MD_SW
+    for k, v in enumerate(params):
+        p.sw[k] = float(v)
+    return p
+
+
+# ----------------------------------------------------------------------------
+# Device-memory plumbing (torch tensors) for a neighbor list
+# ----------------------------------------------------------------------------
+class NeighborList:
+    """Plans a list, allocates its caller-owned tensors with torch and binds them."""
+
+    def __init__(self, space: md_space, N: int, r_cut: float, skin: float, cap: int, device="cuda", stream=None):
+        import torch
+        self.space = space
+        self.plan = md_nbr_plan(space, N, r_cut, skin, cap)
+        self.nbr = torch.empty((N, cap), dtype=torch.int32, device=device)
+        self.cnt = torch.zeros(N, dtype=torch.int32, device=device)
+        self.rref = torch.zeros((N, 4), dtype=torch.float32, device=device)
+        self.ws = torch.empty(int(self.plan.ws_bytes) + 256, dtype=torch.uint8, device=device)
+        off = (-self.ws.data_ptr()) % 256
+        self.ws_view = self.ws[off: off + int(self.plan.ws_bytes)]
+        md_nbr_bind(self.plan, self.nbr, self.cnt, self.rref, self.ws_view, stream)
+
+    @property
+    def N(self):
+        return self.plan.N
+
+    @property
+    def cap(self):
+        return self.plan.cap
+
+    def build(self, r, status, stream=None):
+        md_neighbor_list_build(self.space, r, self.plan, status, stream)
+
+    def update(self, r, status, stream=None):
+        md_neighbor_list_update(self.space, r, self.plan, status, stream)
+
+    def stats(self, stream=None):
+        return md_nbr_stats(self.plan, stream)
