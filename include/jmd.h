@@ -122,6 +122,33 @@ JMD_API md_status md_neighbor_list_build(const md_space *s, const float *d_r, md
 JMD_API md_status md_neighbor_list_update(const md_space *s, const float *d_r, md_nbr *nb, uint32_t *d_status,
                                           md_stream_t stream);
 
+/* Neighbor-list build that allocates nothing and needs no workspace.
+ * The paper has no counterpart; this serves callers that cannot give the
+ * library device memory beyond their own inputs and outputs (a host that
+ * passes only its particle buffers through a plugin interface, or a loop
+ * that must not pay for cudaMalloc).  It runs the same kernels as
+ * md_neighbor_list_build and writes the same rows to d_nbr [N][cap] and
+ * counts to d_cnt [N]; the scratch (cells, sorted copy, control words,
+ * build positions) comes from a fixed pool of md_noalloc_scratch_bytes()
+ * bytes inside the library, held by every GPU that loads it until exit.
+ *   - Returns MD_ERR_INVALID when N and the cell grid need more scratch
+ *     than the pool holds (48 bytes per particle plus 8 per cell: roughly
+ *     85,000 particles), besides the md_nbr_plan errors.  It calls no
+ *     allocating routine.
+ *   - The first call on each device looks up the pool's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first
+ *     call before any stream capture.
+ *   - All calls on a device share that device's pool, which keeps the last
+ *     call's contents (the parts that must start at zero are cleared by
+ *     every call); calls that can overlap on the same GPU, for example on
+ *     two streams, race on it. */
+JMD_API md_status md_neighbor_list_build_noalloc(const md_space *s, const float *d_r, int N, float r_cut, float skin,
+                                                 int cap, int32_t *d_nbr, int32_t *d_cnt, uint32_t *d_status,
+                                                 md_stream_t stream);
+
+/* Size in bytes of the pool used by md_neighbor_list_build_noalloc. */
+JMD_API size_t md_noalloc_scratch_bytes(void);
+
 /* Synchronous on `stream`: builds done since bind, largest row count seen
  * by any build since bind. */
 JMD_API md_status md_nbr_stats(const md_nbr *nb, int64_t *builds, int32_t *max_count, md_stream_t stream);

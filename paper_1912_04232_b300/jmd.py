@@ -77,6 +77,8 @@ _SIGS = {
                          _vp, _vp, C.c_int, _vp, _vp],
     "md_minimize": [_P(md_space), _P(md_pot), C.c_int, C.c_float, C.c_int, _vp, _vp, _P(md_nbr), _vp, _vp, _vp],
     "md_status_poll": [_vp, _P(C.c_uint32), _vp],
+    "md_neighbor_list_build_noalloc": [_P(md_space), _vp, C.c_int, C.c_float, C.c_float, C.c_int, _vp, _vp, _vp,
+                                       _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -84,6 +86,8 @@ for _name, _args in _SIGS.items():
     _f.restype = C.c_int
 _lib.md_launch_count.restype = C.c_uint64
 _lib.md_launch_count.argtypes = []
+_lib.md_noalloc_scratch_bytes.restype = C.c_size_t
+_lib.md_noalloc_scratch_bytes.argtypes = []
 _lib.md_version.restype = C.c_char_p
 _lib.md_version.argtypes = []
 
@@ -172,6 +176,18 @@ def md_integrate_nve(space, pot, r, v, f, mass, dt, nsteps, nb, PE=None, KE=None
 def md_minimize(space, pot, kind, step, nsteps, r, f, nb, E=None, status=None, stream=None):
     _check(_lib.md_minimize(C.byref(space), C.byref(pot), int(kind), float(step), int(nsteps), _ptr(r), _ptr(f),
                             C.byref(nb), _ptr(E), _ptr(status), _stream(stream)), "md_minimize")
+
+
+def md_neighbor_list_build_noalloc(space, r, N, r_cut, skin, cap, nbr, cnt, status=None, stream=None):
+    """Neighbor-list build on the library's fixed scratch pool: for callers
+    that can pass only their input and output buffers (see include/jmd.h)."""
+    _check(_lib.md_neighbor_list_build_noalloc(C.byref(space), _ptr(r), int(N), float(r_cut), float(skin), int(cap),
+                                               _ptr(nbr), _ptr(cnt), _ptr(status), _stream(stream)),
+           "md_neighbor_list_build_noalloc")
+
+
+def md_noalloc_scratch_bytes() -> int:
+    return int(_lib.md_noalloc_scratch_bytes())
 
 
 def md_status_poll(status, stream=None) -> int:
