@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tpp", type=int, default=0)
+    ap.add_argument("--no-graph", action="store_true", help="launch every kernel from the host (profiling)")
     return ap.parse_args()
 
 
@@ -201,7 +202,7 @@ def main():
     def job():
         nl.build(r, st)
         P.md_energy_forces(s, pot, r, nl.plan, f, None, st)
-        P.md_integrate_nve(s, pot, r, v, f, c.mass, c.dt, md_steps, nl.plan, PE, KE, True, st)
+        P.md_integrate_nve(s, pot, r, v, f, c.mass, c.dt, md_steps, nl.plan, PE, KE, not args.no_graph, st)
 
     def one_step():
         r.copy_(r0)
@@ -316,7 +317,8 @@ def main():
                        "md_steps_per_step": md_steps, "density": 0.84, "T": 1.0, "r_cut": c.r_cut, "skin": c.skin,
                        "dt": c.dt, "neighbor_cap": nl.cap, "rebuilds_per_step": builds / args.steps,
                        "max_energy_drift_per_particle": drift, "l2": "flushed between bench steps",
-                       "parallelism": f"replicas{world}", "pair_tpp": args.tpp or 8},
+                       "parallelism": f"replicas{world}", "pair_tpp": args.tpp or 8,
+                       "loop": "host launches" if args.no_graph else "one CUDA graph (device WHILE/IF)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": "k_pair<LJ> (md_energy_forces)",
                          "bytes_per_particle": bytes_per_particle, "kernel_ms": kt * 1e3,

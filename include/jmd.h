@@ -200,6 +200,18 @@ JMD_API md_status md_integrate_nve(const md_space *s, const md_pot *p, float *d_
                                    float mass, float dt, int nsteps, md_nbr *nb, double *d_PE, double *d_KE,
                                    int use_graph, uint32_t *d_status, md_stream_t stream);
 
+/* nsteps of BAOAB Langevin dynamics at constant temperature (Sec. 3.3.1,
+ * "Langevin ... simulations at constant temperature"), 3-D only:
+ *   v += dt/2 F/m; r += dt/2 v; v = c1 v + c2 z; r += dt/2 v; F = F(r); v += dt/2 F/m
+ * with c1 = exp(-gamma dt), c2 = sqrt((1 - c1^2) kT / m).  z are standard
+ * normals from Philox4x32-10 with key `seed` and counter (i, step0 + k, 0, 0)
+ * at step k, through Box-Muller on uniforms ((x >> 8) + 1) 2^-24.  Other
+ * arguments and the graph behaviour as md_integrate_nve. */
+JMD_API md_status md_integrate_langevin(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f,
+                                        float mass, float dt, float gamma, float kT, uint64_t seed, uint32_t step0,
+                                        int nsteps, md_nbr *nb, double *d_PE, double *d_KE, int use_graph,
+                                        uint32_t *d_status, md_stream_t stream);
+
 /* Minimisation (Sec. 3.3.1): kind 0 = gradient descent r <- r + step * F in
  * unwrapped coordinates (the list bins wrapped copies).  d_E (nsteps+1
  * doubles, may be NULL) receives U before every step and after the last;

@@ -1,6 +1,8 @@
 """Build libjmd.so (all CUDA kernels + the C ABI) for sm_103a, in-tree.
 
-    python -m paper_1912_04232_b300.build [--force] [-v]
+    python paper_1912_04232_b300/build.py [--force] [-v]
+
+(run it as a script: importing the package loads libjmd.so).
 
 Every translation unit is compiled with
     nvcc -gencode arch=compute_103a,code=sm_103a -O3 -lineinfo

@@ -21,6 +21,9 @@ enum CtlWord : int {
     CTL_BUILDS_HI = 5,
     CTL_TICKET2 = 6,     // second ticket (displacement-check hand-off)
     CTL_NSTEPS = 7,      // loop length for device-side loop control
+    CTL_SEED_LO = 8,     // Langevin noise key (64 bits)
+    CTL_SEED_HI = 9,
+    CTL_STEP0 = 10,      // noise counter of the loop's first step
     CTL_WORDS = 64
 };
 
@@ -75,6 +78,40 @@ __device__ __forceinline__ float wrap_coord(float x, float L, float Linv)
     if (y >= L) y -= L;
     if (y < 0.0f) y = 0.0f;
     return y;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) from its published
+// definition: ten rounds of
+//   (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+// with M0 = 0xD2511F53, M1 = 0xCD9E8D57 and the key advanced by
+// (0x9E3779B9, 0xBB67AE85) between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Three standard normals for particle i at noise step s: one Philox block
+// with counter (i, s, 0, 0); uniforms u = ((x >> 8) + 1) 2^-24 in (0, 1];
+// Box-Muller on (u0, u1) and (u2, u3).
+__device__ __forceinline__ float3 normal3(unsigned i, unsigned s, uint2 key)
+{
+    uint4 x = philox4x32_10(make_uint4(i, s, 0u, 0u), key);
+    const float sc = 1.0f / 16777216.0f;
+    float u0 = (float)((x.x >> 8) + 1u) * sc, u1 = (float)((x.y >> 8) + 1u) * sc;
+    float u2 = (float)((x.z >> 8) + 1u) * sc, u3 = (float)((x.w >> 8) + 1u) * sc;
+    float ra = sqrtf(-2.0f * logf(u0)), rb = sqrtf(-2.0f * logf(u2));
+    float s1, c1, s3, c3;
+    sincospif(2.0f * u1, &s1, &c1);
+    sincospif(2.0f * u3, &s3, &c3);
+    return make_float3(ra * c1, ra * s1, rb * c3);
 }
 
 __device__ __forceinline__ void raise_status(uint32_t *st, uint32_t bits)

@@ -8,6 +8,7 @@
 //   k_pair         F(r_t), U(r_t)
 //   k_gd_step      r += eta F (unwrapped), displacement check
 //   rebuild chain
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -63,6 +64,63 @@ __global__ void __launch_bounds__(256) k_kick_drift(float4 *r, float4 *v, const 
     }
 }
 
+// BAOAB Langevin (Sec. 3.3.1), first part B-A-O-A:
+//   v += dt/2 F/m;  r += dt/2 v;  v = c1 v + c2 z;  r += dt/2 v;  wrap
+// with c1 = exp(-gamma dt), c2 = sqrt((1 - c1^2) kT / m) and z from Philox
+// counter (i, step0 + step).  The closing B is the force kernel's kick.
+template <int COND>
+__global__ void __launch_bounds__(256) k_baoa(float4 *r, float4 *v, const float4 *f, const float4 *rref, int N,
+                                              float hdm, float dt, float c1, float c2, Box box, float half_skin2,
+                                              uint32_t *ctl, unsigned long long cond_if)
+{
+    count_launch();
+    __shared__ bool last;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool mv = false;
+    if (i < N) {
+        const unsigned s = ctl[CTL_STEP0] + ctl[CTL_STEP];
+        const uint2 key = make_uint2(ctl[CTL_SEED_LO], ctl[CTL_SEED_HI]);
+        float3 z = normal3((unsigned)i, s, key);
+        float4 fi = f[i], vi = v[i], ri = r[i];
+        const float h = 0.5f * dt;
+        vi.x += hdm * fi.x;
+        vi.y += hdm * fi.y;
+        vi.z += hdm * fi.z;
+        ri.x += h * vi.x;
+        ri.y += h * vi.y;
+        ri.z += h * vi.z;
+        vi.x = c1 * vi.x + c2 * z.x;
+        vi.y = c1 * vi.y + c2 * z.y;
+        vi.z = c1 * vi.z + c2 * z.z;
+        ri.x = wrap_coord(ri.x + h * vi.x, box.L[0], box.Linv[0]);
+        ri.y = wrap_coord(ri.y + h * vi.y, box.L[1], box.Linv[1]);
+        ri.z = wrap_coord(ri.z + h * vi.z, box.L[2], box.Linv[2]);
+        v[i] = vi;
+        r[i] = ri;
+        float dx, dy, dz;
+        mv = dist2_rn<3>(ri, rref[i], box, dx, dy, dz) > half_skin2;
+    }
+    if (__any_sync(0xffffffffu, mv) && (threadIdx.x & 31) == 0) {
+        ctl[CTL_REBUILD] = 1u;
+        if (COND) __threadfence();
+    }
+    if (COND) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            unsigned t = atomicAdd(&ctl[CTL_TICKET2], 1u);
+            last = (t == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (last && threadIdx.x == 0) {
+            __threadfence();
+            unsigned flag = *(volatile uint32_t *)&ctl[CTL_REBUILD];
+            ctl[CTL_TICKET2] = 0u;
+            cudaGraphSetConditional((cudaGraphConditionalHandle)cond_if, flag ? 1u : 0u);
+        }
+    }
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(256) k_gd_step(float4 *r, const float4 *f, const float4 *rref, int N, float eta,
                                                  Box box, float half_skin2, uint32_t *ctl)
@@ -82,11 +140,14 @@ __global__ void __launch_bounds__(256) k_gd_step(float4 *r, const float4 *f, con
     if (__any_sync(0xffffffffu, mv) && (threadIdx.x & 31) == 0) ctl[CTL_REBUILD] = 1u;
 }
 
-__global__ void k_loop_init(uint32_t *ctl, uint32_t nsteps)
+__global__ void k_loop_init(uint32_t *ctl, uint32_t nsteps, uint32_t step0, unsigned long long seed)
 {
     count_launch();
     ctl[CTL_STEP] = 0u;
     ctl[CTL_NSTEPS] = nsteps;
+    ctl[CTL_STEP0] = step0;
+    ctl[CTL_SEED_LO] = (uint32_t)seed;
+    ctl[CTL_SEED_HI] = (uint32_t)(seed >> 32);
 }
 
 struct NveCtx {
@@ -99,12 +160,23 @@ struct NveCtx {
     int ncell_total;
     PairArgs pa;
     int pot;
+    int langevin;                 // 0: NVE kick-drift, 1: BAOAB first part
+    float c1, c2;                 // Langevin O-step coefficients
     unsigned long long cond_if;   // graph IF handle (0 outside graphs)
 };
 
 static void enqueue_kick_drift(const NveCtx &c, int cond, cudaStream_t st)
 {
     int g = (c.N + 255) / 256;
+    if (c.langevin) {
+        if (cond)
+            k_baoa<1><<<g, 256, 0, st>>>(c.r, c.v, c.f, c.rref, c.N, c.hdm, c.dt, c.c1, c.c2, c.box, c.half_skin2,
+                                         c.ctl, c.cond_if);
+        else
+            k_baoa<0><<<g, 256, 0, st>>>(c.r, c.v, c.f, c.rref, c.N, c.hdm, c.dt, c.c1, c.c2, c.box, c.half_skin2,
+                                         c.ctl, 0ull);
+        return;
+    }
     if (c.dim == 3) {
         if (cond)
             k_kick_drift<3, 1><<<g, 256, 0, st>>>(c.r, c.v, c.f, c.rref, c.N, c.hdm, c.dt, c.box, c.half_skin2, c.ctl,
@@ -126,7 +198,7 @@ static void enqueue_nve_step(const NveCtx &c, cudaStream_t st)
 {
     enqueue_kick_drift(c, 0, st);
     enqueue_rebuild_chain(c.na, c.ncell_total, st);
-    enqueue_pair(c.pa, c.dim, c.pot, 1, st);
+    enqueue_forces(c.pa, c.dim, c.pot, 1, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -201,7 +273,7 @@ static md_status build_nve_graph(const NveCtx &c0, NveGraph &out)
     enqueue_rebuild_chain(na, c.ncell_total, cs2);
     JMD_CUDA_TRY(cudaStreamEndCapture(cs2, &ibody));
 
-    enqueue_pair(c.pa, c.dim, c.pot, 1, cs);
+    enqueue_forces(c.pa, c.dim, c.pot, 1, cs);
     JMD_CUDA_TRY(cudaStreamEndCapture(cs, &body));
     cudaStreamDestroy(cs2);
     cudaStreamDestroy(cs);
@@ -214,7 +286,8 @@ static md_status build_nve_graph(const NveCtx &c0, NveGraph &out)
     return MD_OK;
 }
 
-static md_status nve_graph_run(const NveCtx &c, int nsteps, cudaStream_t st)
+static md_status nve_graph_run(const NveCtx &c, int nsteps, uint32_t step0, unsigned long long seed,
+                               cudaStream_t st)
 {
     int dev = 0;
     JMD_CUDA_TRY(cudaGetDevice(&dev));
@@ -233,7 +306,7 @@ static md_status nve_graph_run(const NveCtx &c, int nsteps, cudaStream_t st)
             ex = ng.exec;
         }
     }
-    k_loop_init<<<1, 1, 0, st>>>(c.ctl, (uint32_t)nsteps);
+    k_loop_init<<<1, 1, 0, st>>>(c.ctl, (uint32_t)nsteps, step0, seed);
     JMD_CUDA_TRY(cudaGraphLaunch(ex, st));
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
@@ -243,14 +316,15 @@ static md_status nve_graph_run(const NveCtx &c, int nsteps, cudaStream_t st)
 
 using namespace jmd;
 
-extern "C" md_status md_integrate_nve(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f,
-                                      float mass, float dt, int nsteps, md_nbr *nb, double *d_PE, double *d_KE,
-                                      int use_graph, uint32_t *d_status, md_stream_t stream)
+static md_status run_dynamics(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f, float mass,
+                              float dt, int nsteps, md_nbr *nb, double *d_PE, double *d_KE, int use_graph,
+                              uint32_t *d_status, cudaStream_t st, int langevin, float gamma, float kT,
+                              unsigned long long seed, uint32_t step0)
 {
     if (!s || !p || !d_r || !d_v || !d_f || !nb || nsteps < 0 || !(mass > 0.0f)) return MD_ERR_INVALID;
     if (s->dim != nb->dim || !nb->ws || !nb->rref) return MD_ERR_INVALID;
-    if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE) return MD_ERR_INVALID;
-    cudaStream_t st = (cudaStream_t)stream;
+    if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE && p->kind != MD_SW) return MD_ERR_INVALID;
+    if (langevin && (s->dim != 3 || !(gamma >= 0.0f) || !(kT >= 0.0f))) return MD_ERR_INVALID;
     NveCtx c;
     memset(&c, 0, sizeof(c));   // the graph cache compares contexts bytewise
     c.box = make_box(s);
@@ -275,12 +349,35 @@ extern "C" md_status md_integrate_nve(const md_space *s, const md_pot *p, float 
     c.pa.series = 1;
     c.pa.status = d_status;
     c.pot = p->kind;
+    c.langevin = langevin;
+    if (langevin) {
+        double e = exp(-(double)gamma * (double)dt);
+        c.c1 = (float)e;
+        c.c2 = (float)sqrt((1.0 - e * e) * (double)kT / (double)mass);
+    }
     if (nsteps == 0) return MD_OK;
-    if (use_graph) return nve_graph_run(c, nsteps, st);
-    k_loop_init<<<1, 1, 0, st>>>(c.ctl, (uint32_t)nsteps);
+    if (use_graph) return nve_graph_run(c, nsteps, step0, seed, st);
+    k_loop_init<<<1, 1, 0, st>>>(c.ctl, (uint32_t)nsteps, step0, seed);
     for (int k = 0; k < nsteps; ++k) enqueue_nve_step(c, st);
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
+}
+
+extern "C" md_status md_integrate_nve(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f,
+                                      float mass, float dt, int nsteps, md_nbr *nb, double *d_PE, double *d_KE,
+                                      int use_graph, uint32_t *d_status, md_stream_t stream)
+{
+    return run_dynamics(s, p, d_r, d_v, d_f, mass, dt, nsteps, nb, d_PE, d_KE, use_graph, d_status,
+                        (cudaStream_t)stream, 0, 0.0f, 0.0f, 0ull, 0u);
+}
+
+extern "C" md_status md_integrate_langevin(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f,
+                                           float mass, float dt, float gamma, float kT, uint64_t seed,
+                                           uint32_t step0, int nsteps, md_nbr *nb, double *d_PE, double *d_KE,
+                                           int use_graph, uint32_t *d_status, md_stream_t stream)
+{
+    return run_dynamics(s, p, d_r, d_v, d_f, mass, dt, nsteps, nb, d_PE, d_KE, use_graph, d_status,
+                        (cudaStream_t)stream, 1, gamma, kT, (unsigned long long)seed, step0);
 }
 
 extern "C" md_status md_minimize(const md_space *s, const md_pot *p, int kind, float step, int nsteps, float *d_r,
@@ -299,7 +396,7 @@ extern "C" md_status md_minimize(const md_space *s, const md_pot *p, int kind, f
     uint32_t *ctl = ws_ptrs(nb).ctl;
     Box box = make_box(s);
     int g = (nb->N + 255) / 256;
-    k_loop_init<<<1, 1, 0, st>>>(ctl, (uint32_t)(nsteps + 1));
+    k_loop_init<<<1, 1, 0, st>>>(ctl, (uint32_t)(nsteps + 1), 0u, 0ull);
     for (int t = 0; t < nsteps; ++t) {
         enqueue_pair(pa, s->dim, p->kind, 0, st);
         if (s->dim == 3)

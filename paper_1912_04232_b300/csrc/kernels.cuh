@@ -33,6 +33,8 @@ struct PairArgs {
     float rc2, sigma2, c24eps, c4eps, e_shift;
     // soft sphere
     float eps, alpha;
+    // Stillinger-Weber {eps, sigma, a, lambda, gamma, A, B, p, q, cos0, rc, rc2}
+    float sw[12];
     // reductions
     double *E_out, *KE_out;
     int series;             // 1: write E_out[ctl[CTL_STEP]] and advance the counter
@@ -52,9 +54,11 @@ void enqueue_check_disp(const md_space *s, const float *d_r, const md_nbr *nb, c
 bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const md_nbr *nb, float *d_f,
                     PairArgs &a);
 void enqueue_pair(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st);
+// Force evaluation for any supported potential (pair kernels or SW).
+void enqueue_forces(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st);
+void enqueue_sw(const PairArgs &a, int kick, cudaStream_t st);
 int pair_blocks(int N, int tpp);
 
 }  // namespace jmd
 
-md_status md_energy_forces_sw(const md_space *s, const md_pot *p, const float *d_r, const md_nbr *nb, float *d_f,
-                              double *d_E, uint32_t *d_status, md_stream_t stream);
+

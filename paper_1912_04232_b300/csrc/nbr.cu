@@ -129,18 +129,15 @@ __device__ __forceinline__ int axis_cells(int q, int n, int *out)
     return 1;
 }
 
-template <int DIM, int WARPS, int CAPP2>
-__global__ void __launch_bounds__(WARPS * 32) k_build(NbrArgs a)
+// Row of particle i found by one warp scanning the stencil cells directly
+// from global memory, then bitonic-sorted in the warp's shared buffer
+// (CAPP2 >= cap, power of two).  Used for cells whose stencil holds more
+// candidates than the block-staged path can keep in shared memory.
+template <int DIM, int CAPP2>
+__device__ void build_row_warp(const NbrArgs &a, int i, int c, int *row)
 {
-    count_launch();
-    if (!chain_active(a)) return;
-    __shared__ int rows[WARPS][CAPP2];
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int i = blockIdx.x * WARPS + w;
-    if (i >= a.N) return;   // whole warp leaves together
-    int *row = rows[w];
+    const int lane = threadIdx.x & 31;
     float4 ri = a.r[i];
-    int c = a.ws.cell_of[i];
     int cx = c % a.nc[0];
     int cy = (c / a.nc[0]) % a.nc[1];
     int cz = c / (a.nc[0] * a.nc[1]);
@@ -164,8 +161,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_build(NbrArgs a)
                         j = a.ws.atoms[slot];
                         float4 rj = a.ws.rsorted[slot];
                         float dx, dy, dz;
-                        float r2 = dist2_rn<DIM>(ri, rj, a.box, dx, dy, dz);
-                        hit = (j != i) && (r2 < a.r_list2);
+                        hit = (j != i) && (dist2_rn<DIM>(ri, rj, a.box, dx, dy, dz) < a.r_list2);
                     }
                     unsigned m = __ballot_sync(0xffffffffu, hit);
                     int pos = count + __popc(m & lt);
@@ -175,7 +171,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_build(NbrArgs a)
             }
     __syncwarp();
     int n = count < a.cap ? count : a.cap;
-    // pad to the power of two with INT_MAX and bitonic-sort ascending
     for (int k = n + lane; k < CAPP2; k += 32) row[k] = 0x7fffffff;
     __syncwarp();
     for (int size = 2; size <= CAPP2; size <<= 1) {
@@ -200,6 +195,141 @@ __global__ void __launch_bounds__(WARPS * 32) k_build(NbrArgs a)
         a.rref[i] = ri;
         if (count > a.cap) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
         atomicMax(&a.ws.ctl[CTL_MAXCNT], (uint32_t)count);
+    }
+    __syncwarp();
+}
+
+// One CTA per cell.  The candidates of the cell's (deduplicated) stencil are
+// staged once in shared memory as 64-bit keys (index << 16 | slot), sorted
+// ascending with a block-wide bitonic network, and their positions gathered
+// into the sorted order.  Each warp then takes particles of the cell and
+// sweeps the sorted candidates 32 at a time; ballot compaction writes hits
+// straight into the output row, which therefore comes out sorted ascending
+// without a per-particle sort.  All particles of a cell share the staging
+// and the sort.
+constexpr int BUILD_CMAX = 1024;   // candidates a block stages in shared memory
+constexpr int BUILD_WARPS = 8;
+
+template <int DIM>
+__global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
+{
+    count_launch();
+    if (!chain_active(a)) return;
+    __shared__ unsigned long long keys[BUILD_CMAX];
+    __shared__ float4 cpos[BUILD_CMAX];
+    __shared__ float4 spos[BUILD_CMAX];
+    __shared__ int soff[28];        // prefix of the stencil cells' counts
+    __shared__ int scell[27];
+    __shared__ int sbeg[27];
+    __shared__ int nst;
+    const int q = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int own_b = a.ws.cell_start[q], own_e = a.ws.cell_start[q + 1];
+    if (own_e == own_b) return;   // uniform: empty cell
+    if (tid < 32) {
+        // stencil cells and their counts, one lane each, prefix by shuffles
+        int cx = q % a.nc[0];
+        int cy = (q / a.nc[0]) % a.nc[1];
+        int cz = q / (a.nc[0] * a.nc[1]);
+        int sx[3], sy[3], sz[3];
+        int mx = axis_cells(cx, a.nc[0], sx);
+        int my = axis_cells(cy, a.nc[1], sy);
+        int mz = DIM == 3 ? axis_cells(cz, a.nc[2], sz) : 1;
+        if (DIM != 3) sz[0] = 0;
+        int m = mx * my * mz;
+        int c = 0, cnt = 0;
+        if (tid < m) {
+            int xx = tid % mx, yy = (tid / mx) % my, zz = tid / (mx * my);
+            c = (sz[zz] * a.nc[1] + sy[yy]) * a.nc[0] + sx[xx];
+            cnt = a.ws.cell_start[c + 1] - a.ws.cell_start[c];
+            scell[tid] = c;
+            sbeg[tid] = a.ws.cell_start[c];
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += y;
+        }
+        if (tid < m) soff[tid + 1] = incl;
+        if (tid == 0) {
+            soff[0] = 0;
+            nst = m;
+        }
+    }
+    __syncthreads();
+    const int M = soff[nst];
+    if (M > BUILD_CMAX) {
+        // dense stencil: per-warp rows with the rows' own sort; the 16 KB
+        // candidate-position array is reused as 8 warp buffers of 512 ints
+        static_assert(sizeof(cpos) >= BUILD_WARPS * 512 * sizeof(int), "row buffers must fit");
+        int *rowbuf = reinterpret_cast<int *>(cpos) + (tid >> 5) * 512;
+        for (int s = own_b + (tid >> 5); s < own_e; s += BUILD_WARPS) {
+            int i = a.ws.atoms[s];
+            if (a.cap <= 128) build_row_warp<DIM, 128>(a, i, q, rowbuf);
+            else if (a.cap <= 256) build_row_warp<DIM, 256>(a, i, q, rowbuf);
+            else build_row_warp<DIM, 512>(a, i, q, rowbuf);
+        }
+        return;
+    }
+    // stage candidates (all slots in parallel): key = index << 16 | slot
+    for (int slot = tid; slot < M; slot += blockDim.x) {
+        int m = 0;
+        while (soff[m + 1] <= slot) ++m;
+        int src = sbeg[m] + (slot - soff[m]);
+        keys[slot] = ((unsigned long long)(unsigned)a.ws.atoms[src] << 16) | (unsigned)slot;
+        cpos[slot] = a.ws.rsorted[src];
+    }
+    int P2 = 32;
+    while (P2 < M) P2 <<= 1;
+    for (int k = M + tid; k < P2; k += blockDim.x) keys[k] = ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= P2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = tid; t < P2 / 2; t += blockDim.x) {
+                int lo = 2 * t - (t & (stride - 1));
+                int hi = lo + stride;
+                bool up = ((lo & size) == 0);
+                unsigned long long x = keys[lo], y = keys[hi];
+                if ((x > y) == up) {
+                    keys[lo] = y;
+                    keys[hi] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int k = tid; k < M; k += blockDim.x) spos[k] = cpos[(int)(keys[k] & 0xffffull)];
+    __syncthreads();
+    const int lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int s = own_b + (tid >> 5); s < own_e; s += BUILD_WARPS) {
+        int i = a.ws.atoms[s];
+        float4 ri = a.ws.rsorted[s];
+        int32_t *out = a.nbr + (size_t)i * a.cap;
+        int count = 0;
+        for (int k0 = 0; k0 < M; k0 += 32) {
+            int k = k0 + lane;
+            bool hit = false;
+            int j = 0;
+            if (k < M) {
+                j = (int)(keys[k] >> 16);
+                float dx, dy, dz;
+                hit = (j != i) && (dist2_rn<DIM>(ri, spos[k], a.box, dx, dy, dz) < a.r_list2);
+            }
+            unsigned mk = __ballot_sync(0xffffffffu, hit);
+            int pos = count + __popc(mk & lt);
+            if (hit && pos < a.cap) out[pos] = j;
+            count += __popc(mk);
+        }
+        int n = count < a.cap ? count : a.cap;
+        for (int k = n + lane; k < a.cap; k += 32) out[k] = a.N;
+        if (lane == 0) {
+            a.cnt[i] = count;
+            a.rref[i] = ri;
+            if (count > a.cap) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+            atomicMax(&a.ws.ctl[CTL_MAXCNT], (uint32_t)count);
+        }
     }
 }
 
@@ -262,23 +392,6 @@ NbrArgs make_nbr_args(const md_space *s, const float *d_r, const md_nbr *nb, uin
     return a;
 }
 
-template <int DIM, int CAPP2>
-static void launch_build(const NbrArgs &a, cudaStream_t st)
-{
-    constexpr int W = CAPP2 <= 128 ? 8 : 4;
-    k_build<DIM, W, CAPP2><<<(a.N + W - 1) / W, W * 32, 0, st>>>(a);
-}
-
-template <int DIM>
-static void launch_build_dim(const NbrArgs &a, cudaStream_t st)
-{
-    if (a.cap <= 32) launch_build<DIM, 32>(a, st);
-    else if (a.cap <= 64) launch_build<DIM, 64>(a, st);
-    else if (a.cap <= 128) launch_build<DIM, 128>(a, st);
-    else if (a.cap <= 256) launch_build<DIM, 256>(a, st);
-    else launch_build<DIM, 512>(a, st);
-}
-
 // Enqueue the (gated or ungated) rebuild chain.  The flag is consumed by
 // k_finish_build at the end.
 void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st)
@@ -287,8 +400,8 @@ void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st)
     k_bin_count<<<nb, tb, 0, st>>>(a);
     k_scan<<<1, 1024, 0, st>>>(a, ncell_total);
     k_scatter<<<nb, tb, 0, st>>>(a);
-    if (a.dim == 3) launch_build_dim<3>(a, st);
-    else launch_build_dim<2>(a, st);
+    if (a.dim == 3) k_build_cells<3><<<ncell_total, BUILD_WARPS * 32, 0, st>>>(a);
+    else k_build_cells<2><<<ncell_total, BUILD_WARPS * 32, 0, st>>>(a);
     k_finish_build<<<1, 1, 0, st>>>(a.ws.ctl);
 }
 
@@ -354,7 +467,7 @@ extern "C" md_status md_nbr_bind(md_nbr *nb, int32_t *d_nbr, int32_t *d_cnt, flo
                                  md_stream_t stream)
 {
     if (!nb || !d_nbr || !d_cnt || !d_rref || !d_ws) return MD_ERR_INVALID;
-    if (((uintptr_t)d_ws & 255u) || ((uintptr_t)d_rref & 15u)) return MD_ERR_INVALID;
+    if (((uintptr_t)d_ws & 255u) || ((uintptr_t)d_rref & 15u) || ((uintptr_t)d_nbr & 15u)) return MD_ERR_INVALID;
     nb->nbr = d_nbr;
     nb->cnt = d_cnt;
     nb->rref = d_rref;

@@ -12,125 +12,133 @@
 // finish (ticket) adds the partials in a fixed order.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "reduce.cuh"
 
 namespace jmd {
 
+// One neighbor pair: accumulates F_i and the pair energy into the lane's sums.
+template <int DIM, int POT>
+__device__ __forceinline__ void pair_term(const PairArgs &a, const float4 &ri, const float4 &rj, float &fx, float &fy,
+                                          float &fz, float &e)
+{
+    float dx, dy, dz;
+    float r2 = dist2_rn<DIM>(ri, rj, a.box, dx, dy, dz);
+    if (POT == MD_LJ) {
+        if (r2 < a.rc2) {
+            float ir2 = __fdividef(1.0f, r2);
+            float s2 = a.sigma2 * ir2;
+            float s6 = s2 * s2 * s2;
+            float fr = a.c24eps * ir2 * s6 * (2.0f * s6 - 1.0f);
+            fx += fr * dx;
+            fy += fr * dy;
+            fz += fr * dz;
+            e += a.c4eps * s6 * (s6 - 1.0f) - a.e_shift;
+        }
+    } else {  // soft sphere, s_ij = (w_i + w_j)/2
+        float sg = 0.5f * (ri.w + rj.w);
+        if (r2 < sg * sg) {
+            float rr = sqrtf(r2);
+            float isg = __fdividef(1.0f, sg);
+            float x = 1.0f - rr * isg;
+            float xa1, ua;
+            if (a.alpha == 2.0f) {
+                xa1 = x;
+                ua = 0.5f * x * x;
+            } else {
+                xa1 = __powf(x, a.alpha - 1.0f);
+                ua = xa1 * x / a.alpha;
+            }
+            // F_i += (eps/s) x^(alpha-1) d / r
+            float fr = a.eps * isg * xa1 * __fdividef(1.0f, rr);
+            fx += fr * dx;
+            fy += fr * dy;
+            fz += fr * dz;
+            e += a.eps * ua;
+        }
+    }
+}
+
+// Grid-stride over groups of PPB = 256/TPP particles.  Energies accumulate per thread in FP32 over the particles it
+// owns, per warp in FP32, across the block's 8 warps in FP64, and across
+// blocks in FP64 (fixed order, last block).
 template <int DIM, int TPP, int POT, int KICK>
 __global__ void __launch_bounds__(256) k_pair(PairArgs a)
 {
     count_launch();
-    __shared__ double sh[8];
-    __shared__ bool last;
-    int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = gid / TPP;
-    int lg = threadIdx.x & (TPP - 1);
-    bool valid = i < a.N;
-    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
-    float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid) {
-        ri = a.r[i];
-        int n = a.cnt[i];
-        n = n < a.cap ? n : a.cap;
-        const int32_t *row = a.nbr + (size_t)i * a.cap;
-        for (int k = lg; k < n; k += TPP) {
-            int j = __ldg(row + k);
-            float4 rj = __ldg(a.r + j);
-            float dx, dy, dz;
-            float r2 = dist2_rn<DIM>(ri, rj, a.box, dx, dy, dz);
-            if (POT == MD_LJ) {
-                if (r2 < a.rc2) {
-                    float ir2 = __fdividef(1.0f, r2);
-                    float s2 = a.sigma2 * ir2;
-                    float s6 = s2 * s2 * s2;
-                    float fr = a.c24eps * ir2 * s6 * (2.0f * s6 - 1.0f);
-                    fx += fr * dx;
-                    fy += fr * dy;
-                    fz += fr * dz;
-                    e += a.c4eps * s6 * (s6 - 1.0f) - a.e_shift;
-                }
-            } else {  // soft sphere, s_ij = (w_i + w_j)/2
-                float sg = 0.5f * (ri.w + rj.w);
-                if (r2 < sg * sg) {
-                    float rr = sqrtf(r2);
-                    float isg = __fdividef(1.0f, sg);
-                    float x = 1.0f - rr * isg;
-                    float xa1, ua;
-                    if (a.alpha == 2.0f) {
-                        xa1 = x;
-                        ua = 0.5f * x * x;
-                    } else {
-                        xa1 = __powf(x, a.alpha - 1.0f);
-                        ua = xa1 * x / a.alpha;
-                    }
-                    // F_i += (eps/s) x^(alpha-1) d / r
-                    float fr = a.eps * isg * xa1 * __fdividef(1.0f, rr);
-                    fx += fr * dx;
-                    fy += fr * dy;
-                    fz += fr * dz;
-                    e += a.eps * ua;
-                }
+    constexpr int PPB = 256 / TPP;
+    const int lg = threadIdx.x & (TPP - 1);
+    const int gl = threadIdx.x / TPP;
+    float pe_acc = 0.0f, ke_acc = 0.0f;
+    for (int base = blockIdx.x * PPB; base < a.N; base += gridDim.x * PPB) {
+        int i = base + gl;
+        bool valid = i < a.N;
+        float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+        float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) {
+            ri = __ldg(a.r + i);
+            int n = __ldg(a.cnt + i);
+            n = n < a.cap ? n : a.cap;
+            const int32_t *row = a.nbr + (size_t)i * a.cap;
+            // lanes of a group take consecutive entries of the sorted row, so
+            // one gather instruction touches few cache lines; four entries per
+            // lane per trip keep four gathers in flight
+            for (int k0 = lg; k0 < n; k0 += 4 * TPP) {
+                const int k1 = k0 + TPP, k2 = k0 + 2 * TPP, k3 = k0 + 3 * TPP;
+                int j0 = __ldg(row + k0);
+                int j1 = k1 < n ? __ldg(row + k1) : i;
+                int j2 = k2 < n ? __ldg(row + k2) : i;
+                int j3 = k3 < n ? __ldg(row + k3) : i;
+                float4 r0 = __ldg(a.r + j0);
+                float4 r1 = __ldg(a.r + j1);
+                float4 r2 = __ldg(a.r + j2);
+                float4 r3 = __ldg(a.r + j3);
+                pair_term<DIM, POT>(a, ri, r0, fx, fy, fz, e);
+                if (k1 < n) pair_term<DIM, POT>(a, ri, r1, fx, fy, fz, e);
+                if (k2 < n) pair_term<DIM, POT>(a, ri, r2, fx, fy, fz, e);
+                if (k3 < n) pair_term<DIM, POT>(a, ri, r3, fx, fy, fz, e);
             }
         }
-    }
 #pragma unroll
-    for (int o = TPP / 2; o > 0; o >>= 1) {
-        fx += __shfl_xor_sync(0xffffffffu, fx, o);
-        fy += __shfl_xor_sync(0xffffffffu, fy, o);
-        fz += __shfl_xor_sync(0xffffffffu, fz, o);
-        e += __shfl_xor_sync(0xffffffffu, e, o);
-    }
-    double pe = 0.0, ke = 0.0;
-    if (valid && lg == 0) {
-        float ei = 0.5f * e;
-        a.f[i] = make_float4(fx, fy, fz, ei);
-        pe = (double)ei;
-        if (KICK) {
-            float4 v = a.v[i];
-            v.x += a.half_dt_over_m * fx;
-            v.y += a.half_dt_over_m * fy;
-            if (DIM == 3) v.z += a.half_dt_over_m * fz;
-            a.v[i] = v;
-            float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
-            ke = 0.5 * (double)a.mass * (double)v2;
+        for (int o = TPP / 2; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+        }
+        if (valid && lg == 0) {
+            float ei = 0.5f * e;
+            a.f[i] = make_float4(fx, fy, fz, ei);
+            pe_acc += ei;
+            if (KICK) ke_acc += half_kick<DIM>(a, i, fx, fy, fz);
         }
     }
     if (!a.E_out && !KICK) return;
-    double bpe = block_sum_f64(pe, sh);
-    double bke = KICK ? block_sum_f64(ke, sh) : 0.0;
-    if (threadIdx.x == 0) {
-        a.partials[blockIdx.x] = make_double2(bpe, bke);
-        __threadfence();
-        unsigned t = atomicAdd(&a.ctl[CTL_TICKET], 1u);
-        last = (t == gridDim.x - 1);
+    energy_epilogue(pe_acc, ke_acc, a);
+}
+
+// Blocks per launch: enough resident blocks to fill every SM (grid-stride
+// loop inside), never more than there are particle groups.
+template <int DIM, int TPP, int POT, int KICK>
+static int pair_grid(int N)
+{
+    static int per_sm = 0, sms = 0;
+    if (!per_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<DIM, TPP, POT, KICK>, 256, 0);
+        if (per_sm < 1) per_sm = 1;
+        if (sms < 1) sms = 1;
     }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double spe = 0.0, ske = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        const volatile double *p = (const volatile double *)(a.partials + b);
-        spe += p[0];
-        ske += p[1];
-    }
-    spe = block_sum_f64(spe, sh);
-    ske = block_sum_f64(ske, sh);
-    if (threadIdx.x == 0) {
-        a.ctl[CTL_TICKET] = 0u;
-        if (!isfinite(spe) || !isfinite(ske)) raise_status(a.status, MD_ERR_NONFINITE);
-        unsigned step = a.series ? a.ctl[CTL_STEP] : 0u;
-        if (a.E_out) a.E_out[step] = spe;
-        if (a.KE_out) a.KE_out[step] = ske;
-        if (a.series) a.ctl[CTL_STEP] = step + 1u;
-        if (a.use_cond)
-            cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond_while,
-                                    (step + 1u < a.ctl[CTL_NSTEPS]) ? 1u : 0u);
-    }
+    int groups = (int)(((long long)N * TPP + 255) / 256);
+    int g = per_sm * sms;
+    return groups < g ? groups : g;
 }
 
 template <int DIM, int TPP, int POT, int KICK>
 static void launch_pair_t(const PairArgs &a, cudaStream_t st)
 {
-    k_pair<DIM, TPP, POT, KICK><<<pair_blocks(a.N, TPP), 256, 0, st>>>(a);
+    k_pair<DIM, TPP, POT, KICK><<<pair_grid<DIM, TPP, POT, KICK>(a.N), 256, 0, st>>>(a);
 }
 
 template <int DIM, int POT, int KICK>
@@ -157,12 +165,19 @@ void enqueue_pair(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st
 
 int pair_blocks(int N, int tpp) { return (int)(((long long)N * tpp + 255) / 256); }
 
-static int g_tpp = 8;
+void enqueue_forces(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st)
+{
+    if (pot == MD_SW) enqueue_sw(a, kick, st);
+    else enqueue_pair(a, dim, pot, kick, st);
+}
+
+static int g_tpp = 4;
 
 bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const md_nbr *nb, float *d_f, PairArgs &a)
 {
     if (!s || !p || !d_r || !nb || !d_f || !nb->nbr || !nb->cnt || !nb->ws) return false;
-    if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE) return false;
+    if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE && p->kind != MD_SW) return false;
+    if (p->kind == MD_SW && s->dim != 3) return false;
     memset(&a, 0, sizeof(a));
     a.box = make_box(s);
     a.N = nb->N;
@@ -183,9 +198,15 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
         a.c24eps = 24.0f * p->eps;
         a.c4eps = 4.0f * p->eps;
         a.e_shift = p->e_shift;
-    } else {
+    } else if (p->kind == MD_SOFT_SPHERE) {
         a.eps = p->eps;
         a.alpha = p->alpha;
+    } else {
+        for (int k = 0; k < 10; ++k) a.sw[k] = p->sw[k];
+        float rc = p->sw[2] * p->sw[1];   // a * sigma
+        if (rc > nb->r_list) return false;
+        a.sw[10] = rc;
+        a.sw[11] = rc * rc;
     }
     return pair_blocks(a.N, a.tpp) <= w.max_blocks;
 }
@@ -206,12 +227,11 @@ extern "C" md_status md_energy_forces(const md_space *s, const md_pot *p, const 
 {
     if (!p || !s || !nb) return MD_ERR_INVALID;
     if (s->dim != nb->dim) return MD_ERR_INVALID;
-    if (p->kind == MD_SW) return md_energy_forces_sw(s, p, d_r, nb, d_f, d_E, d_status, stream);
     PairArgs a;
     if (!make_pair_args(s, p, d_r, nb, d_f, a)) return MD_ERR_INVALID;
     a.E_out = d_E;
     a.status = d_status;
-    enqueue_pair(a, s->dim, p->kind, 0, (cudaStream_t)stream);
+    enqueue_forces(a, s->dim, p->kind, 0, (cudaStream_t)stream);
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
 }

@@ -1,10 +1,223 @@
-// sw.cu -- Stillinger-Weber three-body forces (Sec. 3.3.2).
+// sw.cu -- Stillinger-Weber forces (Sec. 3.3.2; form of Stillinger & Weber 1985):
+//   E = sum_{i<j} phi2(r_ij) + sum_i sum_{j<k in N(i)} phi3(r_ij, r_ik, theta_jik)
+//   phi2(r) = A eps [B (sigma/r)^p - (sigma/r)^q] exp(sigma/(r - a sigma))
+//   phi3    = lambda eps (cos theta - cos0)^2 g(r_ij) g(r_ik),
+//   g(r)    = exp(gamma sigma / (r - a sigma)),      all for r < a sigma.
+//
+// Gather form, one warp per atom i, no atomics.  F_i collects
+//   (1) the two-body terms of every neighbor j,
+//   (2) the triplets centred on i (legs j < k of i's neighbors), and
+//   (3) the triplets centred on each neighbor j in which i is a leg
+//       (the other leg k runs over j's row).
+// e_i = 1/2 sum_j phi2(r_ij) + sum_{j<k} phi3(i; j, k), so sum_i e_i = E.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "reduce.cuh"
 
-md_status md_energy_forces_sw(const md_space *s, const md_pot *p, const float *d_r, const md_nbr *nb, float *d_f,
-                              double *d_E, uint32_t *d_status, md_stream_t stream)
+namespace jmd {
+
+constexpr int SW_MAXN = 64;   // neighbors inside a*sigma kept per atom
+constexpr int SW_WARPS = 8;
+
+struct SwP {
+    float eps, sg, rc, lam, gam, A, B, p, q, c0, rc2;
+};
+
+__device__ __forceinline__ SwP sw_params(const PairArgs &a)
 {
-    (void)s; (void)p; (void)d_r; (void)nb; (void)d_f; (void)d_E; (void)d_status; (void)stream;
-    return MD_ERR_INVALID;
+    SwP P;
+    P.eps = a.sw[0];
+    P.sg = a.sw[1];
+    P.lam = a.sw[3];
+    P.gam = a.sw[4];
+    P.A = a.sw[5];
+    P.B = a.sw[6];
+    P.p = a.sw[7];
+    P.q = a.sw[8];
+    P.c0 = a.sw[9];
+    P.rc = a.sw[10];
+    P.rc2 = a.sw[11];
+    return P;
 }
+
+// phi2 and its derivative d phi2 / dr (r < rc)
+__device__ __forceinline__ float sw_phi2(const SwP &P, float r, float &dphi)
+{
+    float sr = P.sg / r;
+    float srp = __powf(sr, P.p), srq = __powf(sr, P.q);
+    float bra = P.B * srp - srq;
+    float dbra = (-P.p * P.B * srp + P.q * srq) / r;
+    float x = r - P.rc;
+    float ex = expf(P.sg / x);
+    float dex = ex * (-P.sg / (x * x));
+    dphi = P.A * P.eps * (dbra * ex + bra * dex);
+    return P.A * P.eps * bra * ex;
+}
+
+// g(r) = exp(gamma sigma / (r - rc)) and g'(r)
+__device__ __forceinline__ float sw_g(const SwP &P, float r, float &dg)
+{
+    float x = r - P.rc;
+    float v = expf(P.gam * P.sg / x);
+    dg = v * (-P.gam * P.sg / (x * x));
+    return v;
+}
+
+// Triplet with centre c, legs u = r_a - r_c and w = r_b - r_c (|u|, |w| < rc).
+// Returns h and its gradients with respect to u and w.
+__device__ __forceinline__ float sw_triplet(const SwP &P, float ux, float uy, float uz, float ru, float wx, float wy,
+                                            float wz, float rw, float gu[3], float gw[3])
+{
+    float iu = 1.0f / ru, iw = 1.0f / rw;
+    float c = (ux * wx + uy * wy + uz * wz) * iu * iw;
+    float dgu, dgw;
+    float g1 = sw_g(P, ru, dgu), g2 = sw_g(P, rw, dgw);
+    float cc = c - P.c0;
+    float le = P.lam * P.eps;
+    float h = le * cc * cc * g1 * g2;
+    float dh_dc = 2.0f * le * cc * g1 * g2;
+    float dh_dru = le * cc * cc * dgu * g2;
+    float dh_drw = le * cc * cc * g1 * dgw;
+    float uu[3] = {ux, uy, uz}, ww[3] = {wx, wy, wz};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float dc_du = ww[q] * iu * iw - c * uu[q] * iu * iu;
+        float dc_dw = uu[q] * iu * iw - c * ww[q] * iw * iw;
+        gu[q] = dh_dc * dc_du + dh_dru * uu[q] * iu;
+        gw[q] = dh_dc * dc_dw + dh_drw * ww[q] * iw;
+    }
+    return h;
+}
+
+template <int KICK>
+__global__ void __launch_bounds__(SW_WARPS * 32) k_sw(PairArgs a)
+{
+    count_launch();
+    __shared__ int nj[SW_WARPS][SW_MAXN];
+    __shared__ float4 nd[SW_WARPS][SW_MAXN];   // (ux, uy, uz, r): u = r_j - r_i
+    const SwP P = sw_params(a);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    float pe_acc = 0.0f, ke_acc = 0.0f;
+    for (int i = blockIdx.x * SW_WARPS + w; i < a.N; i += gridDim.x * SW_WARPS) {
+        const float4 ri = a.r[i];
+        int n = a.cnt[i];
+        n = n < a.cap ? n : a.cap;
+        const int32_t *row = a.nbr + (size_t)i * a.cap;
+        // (0) neighbors inside a*sigma, compacted into shared memory
+        int m = 0;
+        for (int k0 = 0; k0 < n; k0 += 32) {
+            int k = k0 + lane;
+            bool in = false;
+            int j = 0;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+            if (k < n) {
+                j = row[k];
+                float4 rj = __ldg(a.r + j);
+                r2 = dist2_rn<3>(rj, ri, a.box, dx, dy, dz);   // u = r_j - r_i
+                in = r2 < P.rc2;
+            }
+            unsigned mk = __ballot_sync(0xffffffffu, in);
+            int pos = m + __popc(mk & lt);
+            if (in && pos < SW_MAXN) {
+                nj[w][pos] = j;
+                nd[w][pos] = make_float4(dx, dy, dz, sqrtf(r2));
+            }
+            m += __popc(mk);
+        }
+        if (m > SW_MAXN) {
+            if (lane == 0) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+            m = SW_MAXN;
+        }
+        __syncwarp();
+        float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+        // (1) two-body: F_i += phi2'(r) u / r
+        for (int s = lane; s < m; s += 32) {
+            float4 u = nd[w][s];
+            float dphi;
+            float ph = sw_phi2(P, u.w, dphi);
+            float fr = dphi / u.w;
+            fx += fr * u.x;
+            fy += fr * u.y;
+            fz += fr * u.z;
+            e += 0.5f * ph;
+        }
+        // (2) triplets centred on i: F_i += dh/du + dh/dw
+        for (int t = lane; t < m * m; t += 32) {
+            int s1 = t / m, s2 = t - s1 * m;
+            if (s1 >= s2) continue;
+            float4 u = nd[w][s1], v = nd[w][s2];
+            float gu[3], gw[3];
+            float h = sw_triplet(P, u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, gu, gw);
+            fx += gu[0] + gw[0];
+            fy += gu[1] + gw[1];
+            fz += gu[2] + gw[2];
+            e += h;
+        }
+        // (3) triplets centred on neighbor j with i as a leg:
+        //     u' = r_i - r_j = -u, w' = r_k - r_j; F_i -= dh/du'
+        for (int s = 0; s < m; ++s) {
+            const int j = nj[w][s];
+            const float4 uj = nd[w][s];
+            const float4 rj = __ldg(a.r + j);
+            int nn = a.cnt[j];
+            nn = nn < a.cap ? nn : a.cap;
+            const int32_t *rowj = a.nbr + (size_t)j * a.cap;
+            for (int k0 = 0; k0 < nn; k0 += 32) {
+                int k = k0 + lane;
+                if (k >= nn) continue;
+                int kk = rowj[k];
+                if (kk == i) continue;
+                float4 rk = __ldg(a.r + kk);
+                float wx, wy, wz;
+                float w2 = dist2_rn<3>(rk, rj, a.box, wx, wy, wz);
+                if (!(w2 < P.rc2)) continue;
+                float gu[3], gw[3];
+                sw_triplet(P, -uj.x, -uj.y, -uj.z, uj.w, wx, wy, wz, sqrtf(w2), gu, gw);
+                fx -= gu[0];
+                fy -= gu[1];
+                fz -= gu[2];
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+        }
+        if (lane == 0) {
+            a.f[i] = make_float4(fx, fy, fz, e);
+            pe_acc += e;
+            if (KICK) ke_acc += half_kick<3>(a, i, fx, fy, fz);
+        }
+        __syncwarp();
+    }
+    if (!a.E_out && !KICK) return;
+    energy_epilogue(pe_acc, ke_acc, a);
+}
+
+template <int KICK>
+static int sw_grid(int N)
+{
+    static int per_sm = 0, sms = 0;
+    if (!per_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sw<KICK>, SW_WARPS * 32, 0);
+        if (per_sm < 1) per_sm = 1;
+        if (sms < 1) sms = 1;
+    }
+    int groups = (N + SW_WARPS - 1) / SW_WARPS;
+    int g = per_sm * sms;
+    return groups < g ? groups : g;
+}
+
+void enqueue_sw(const PairArgs &a, int kick, cudaStream_t st)
+{
+    if (kick) k_sw<1><<<sw_grid<1>(a.N), SW_WARPS * 32, 0, st>>>(a);
+    else k_sw<0><<<sw_grid<0>(a.N), SW_WARPS * 32, 0, st>>>(a);
+}
+
+}  // namespace jmd

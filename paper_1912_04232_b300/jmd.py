@@ -75,6 +75,8 @@ _SIGS = {
     "md_set_pair_tpp": [C.c_int],
     "md_integrate_nve": [_P(md_space), _P(md_pot), _vp, _vp, _vp, C.c_float, C.c_float, C.c_int, _P(md_nbr),
                          _vp, _vp, C.c_int, _vp, _vp],
+    "md_integrate_langevin": [_P(md_space), _P(md_pot), _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float,
+                              C.c_uint64, C.c_uint32, C.c_int, _P(md_nbr), _vp, _vp, C.c_int, _vp, _vp],
     "md_minimize": [_P(md_space), _P(md_pot), C.c_int, C.c_float, C.c_int, _vp, _vp, _P(md_nbr), _vp, _vp, _vp],
     "md_status_poll": [_vp, _P(C.c_uint32), _vp],
     "md_neighbor_list_build_noalloc": [_P(md_space), _vp, C.c_int, C.c_float, C.c_float, C.c_int, _vp, _vp, _vp,
@@ -171,6 +173,14 @@ def md_integrate_nve(space, pot, r, v, f, mass, dt, nsteps, nb, PE=None, KE=None
     _check(_lib.md_integrate_nve(C.byref(space), C.byref(pot), _ptr(r), _ptr(v), _ptr(f), float(mass), float(dt),
                                  int(nsteps), C.byref(nb), _ptr(PE), _ptr(KE), int(bool(use_graph)), _ptr(status),
                                  _stream(stream)), "md_integrate_nve")
+
+
+def md_integrate_langevin(space, pot, r, v, f, mass, dt, gamma, kT, seed, step0, nsteps, nb, PE=None, KE=None,
+                          use_graph=True, status=None, stream=None):
+    _check(_lib.md_integrate_langevin(C.byref(space), C.byref(pot), _ptr(r), _ptr(v), _ptr(f), float(mass),
+                                      float(dt), float(gamma), float(kT), int(seed), int(step0), int(nsteps),
+                                      C.byref(nb), _ptr(PE), _ptr(KE), int(bool(use_graph)), _ptr(status),
+                                      _stream(stream)), "md_integrate_langevin")
 
 
 def md_minimize(space, pot, kind, step, nsteps, r, f, nb, E=None, status=None, stream=None):

@@ -27,7 +27,10 @@ def test_header_declares_entry_points():
 
 
 def test_library_exports_every_declared_symbol():
-    from paper_1912_04232_b300 import build
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("_jmd_build", os.path.join(ROOT, "paper_1912_04232_b300", "build.py"))
+    build = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(build)
     lib = ctypes.CDLL(build.build())
     missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
     assert not missing, missing

@@ -57,6 +57,19 @@ def test_neighbor_list_bit_exact_tiny_and_ragged(P, dim, ncell):
     assert list(nl.plan.ncell)[:dim] == [ncell] * dim
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_neighbor_list_dense_stencil_fallback(P, dim):
+    # a 3x3(x3) grid whose stencil holds every particle (more candidates than
+    # a block stages in shared memory): rows come from the per-warp path
+    L = 3 * 1.3 * 1.01
+    N = 1100
+    rng = np.random.Generator(np.random.PCG64(77 + dim))
+    r = np.zeros((N, 4), np.float32)
+    r[:, :dim] = W.uniform_box_positions(N, L, dim, rng)
+    cap = 256 if dim == 3 else 512
+    _nbr_case(P, r, L, (1.0, 0.3), cap=cap, dim=dim)
+
+
 def test_neighbor_list_bit_exact_lj256k(P):
     c = W.lj_large()
     _nbr_case(P, c.r, c.L, cap=128)
