@@ -78,9 +78,11 @@ JMD_API md_status md_space_periodic(int dim, const double *box, md_space *out);
 /* ------------------------------------------------------------------------ */
 /* Neighbor list (Sec. 3.2.3): for every i, the j != i with r_ij < r_list,   */
 /* r_list = r_cut + skin, found through a cell list with cells of side       */
-/* >= r_list.  Rows are sorted ascending and padded with N; cnt[i] is the    */
-/* true count even when it exceeds cap (then MD_ERR_NBR_OVERFLOW is raised   */
-/* and the row is truncated).  Membership is decided in FP32 as              */
+/* >= r_list.  Rows are padded with N; cnt[i] is the true count even when it */
+/* exceeds cap (then MD_ERR_NBR_OVERFLOW is raised and the row truncated).   */
+/* Row order is deterministic: grouped by stencil cell in a fixed order and  */
+/* ascending inside each cell (fully ascending for cells whose stencil holds */
+/* more than 1024 particles).  Membership is decided in FP32 as              */
 /*   r2 = (dx*dx + dy*dy) + dz*dz < fl32(r_list)^2                           */
 /* with every operation rounded separately (no FMA).                         */
 /* ------------------------------------------------------------------------ */
@@ -99,7 +101,16 @@ typedef struct {
     int32_t *cnt;          /* [N] */
     float *rref;           /* [N][4] positions at the last build */
     void *ws;              /* ws_bytes of scratch (cells, sorted copy, control words, reduction partials) */
+    int flags;             /* MD_NBR_CANONICAL (set by the caller before md_nbr_bind), else 0 */
 } md_nbr;
+
+/* Canonical mode: every build also sorts each row ascending, and force
+ * kernels on this list sum each particle's pairs one thread at a time in
+ * row order.  A particle's force is then a function of the positions alone,
+ * independent of when the list was last rebuilt, which makes minimisation
+ * trajectories reproducible bit for bit from any checkpoint (the adjoint's
+ * recomputation relies on it).  Slower; meant for small systems. */
+#define MD_NBR_CANONICAL 1
 
 /* Plan a neighbor list for N particles in space s.  Fails with
  * MD_ERR_BOX_TOO_SMALL if any used box edge is < 2 r_list, MD_ERR_INVALID
@@ -218,6 +229,27 @@ JMD_API md_status md_integrate_langevin(const md_space *s, const md_pot *p, floa
  * d_f holds F at the final positions on return. */
 JMD_API md_status md_minimize(const md_space *s, const md_pot *p, int kind, float step, int nsteps, float *d_r,
                               float *d_f, md_nbr *nb, double *d_E, uint32_t *d_status, md_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Differentiating through minimisation (Sec. 4.2, App. A): the final energy */
+/* of T gradient-descent steps of a 2-D bidisperse soft-disk packing and its */
+/* derivative with respect to the diameter D of the first nA disks (the rest */
+/* have diameter dB).  The box (s) is L(D); Lp = dL/dD.                      */
+/* ------------------------------------------------------------------------ */
+/* Workspace bytes for N particles, T steps, checkpoints every K steps:
+ * (ceil(T/K) + K + 2) * N * 16. */
+JMD_API size_t md_adjoint_workspace_size(int N, int T, int K);
+
+/* r_0 = L s_0 (d_s0 [N][4] fractional coordinates), T steps of
+ * r <- r + eta F(r) (soft spheres, p), E = U(r_T); hand-written reverse
+ * mode with recomputation from checkpoints every K steps (K = ceil(sqrt T)
+ * is the natural choice).  nb must be planned for this space with
+ * r_cut >= max(D, dB), bound, and in MD_NBR_CANONICAL mode; the result is
+ * then identical for every K.  d_r [N][4] receives r_T (w = diameter), d_f
+ * the forces at r_T; d_out[0] = E (FP64), d_out[1] = dE/dD (FP64). */
+JMD_API md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_nbr *nb, const float *d_s0, int nA,
+                                      float D, float dB, float Lp, float eta, int T, int K, float *d_r, float *d_f,
+                                      void *d_ws, double *d_out, uint32_t *d_status, md_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Status and accounting                                                     */

@@ -312,6 +312,19 @@ static md_status nve_graph_run(const NveCtx &c, int nsteps, uint32_t step0, unsi
     return MD_OK;
 }
 
+void enqueue_gd_step(const md_space *s, float *d_r, const float *d_f, const md_nbr *nb, float eta, cudaStream_t st)
+{
+    Box box = make_box(s);
+    int g = (nb->N + 255) / 256;
+    uint32_t *ctl = ws_ptrs(nb).ctl;
+    if (s->dim == 3)
+        k_gd_step<3><<<g, 256, 0, st>>>((float4 *)d_r, (const float4 *)d_f, (const float4 *)nb->rref, nb->N, eta, box,
+                                        nb->half_skin2, ctl);
+    else
+        k_gd_step<2><<<g, 256, 0, st>>>((float4 *)d_r, (const float4 *)d_f, (const float4 *)nb->rref, nb->N, eta, box,
+                                        nb->half_skin2, ctl);
+}
+
 }  // namespace jmd
 
 using namespace jmd;
@@ -394,17 +407,10 @@ extern "C" md_status md_minimize(const md_space *s, const md_pot *p, int kind, f
     pa.status = d_status;
     NbrArgs na = make_nbr_args(s, d_r, nb, d_status, 1);
     uint32_t *ctl = ws_ptrs(nb).ctl;
-    Box box = make_box(s);
-    int g = (nb->N + 255) / 256;
     k_loop_init<<<1, 1, 0, st>>>(ctl, (uint32_t)(nsteps + 1), 0u, 0ull);
     for (int t = 0; t < nsteps; ++t) {
         enqueue_pair(pa, s->dim, p->kind, 0, st);
-        if (s->dim == 3)
-            k_gd_step<3><<<g, 256, 0, st>>>((float4 *)d_r, (const float4 *)d_f, (const float4 *)nb->rref, nb->N, step,
-                                            box, nb->half_skin2, ctl);
-        else
-            k_gd_step<2><<<g, 256, 0, st>>>((float4 *)d_r, (const float4 *)d_f, (const float4 *)nb->rref, nb->N, step,
-                                            box, nb->half_skin2, ctl);
+        enqueue_gd_step(s, d_r, d_f, nb, step, st);
         enqueue_rebuild_chain(na, nb->ncell_total, st);
     }
     enqueue_pair(pa, s->dim, p->kind, 0, st);

@@ -17,7 +17,8 @@ struct NbrArgs {
     float4 *rref;
     WsPtrs ws;
     uint32_t *status;
-    int gated;   // 1: run only if ctl[CTL_REBUILD] != 0
+    int gated;       // 1: run only if ctl[CTL_REBUILD] != 0
+    int canonical;   // 1: sort every row ascending after the build
 };
 
 struct PairArgs {
@@ -58,6 +59,8 @@ void enqueue_pair(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st
 void enqueue_forces(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st);
 void enqueue_sw(const PairArgs &a, int kick, cudaStream_t st);
 int pair_blocks(int N, int tpp);
+// r += eta F (unwrapped) with the displacement check (gradient descent step)
+void enqueue_gd_step(const md_space *s, float *d_r, const float *d_f, const md_nbr *nb, float eta, cudaStream_t st);
 
 }  // namespace jmd
 

@@ -129,6 +129,51 @@ __device__ __forceinline__ int axis_cells(int q, int n, int *out)
     return 1;
 }
 
+// Ascending bitonic sort of row[0..n) by one warp; row has CAPP2 (power of
+// two) slots, the tail is padded with INT_MAX first.
+template <int CAPP2>
+__device__ __forceinline__ void warp_sort_row(int *row, int n)
+{
+    const int lane = threadIdx.x & 31;
+    for (int k = n + lane; k < CAPP2; k += 32) row[k] = 0x7fffffff;
+    __syncwarp();
+    for (int size = 2; size <= CAPP2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < CAPP2 / 2; t += 32) {
+                int lo = 2 * t - (t & (stride - 1));
+                int hi = lo + stride;
+                bool up = ((lo & size) == 0);
+                int x = row[lo], y = row[hi];
+                if ((x > y) == up) {
+                    row[lo] = y;
+                    row[hi] = x;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Canonical mode: sort each finished row ascending (one warp per row).
+template <int CAPP2>
+__global__ void __launch_bounds__(256) k_sort_rows(NbrArgs a)
+{
+    count_launch();
+    if (!chain_active(a)) return;
+    __shared__ int buf[8][CAPP2];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * 8 + w; i < a.N; i += gridDim.x * 8) {
+        int n = a.cnt[i];
+        n = n < a.cap ? n : a.cap;
+        int32_t *row = a.nbr + (size_t)i * a.cap;
+        for (int k = lane; k < n; k += 32) buf[w][k] = row[k];
+        __syncwarp();
+        warp_sort_row<CAPP2>(buf[w], n);
+        for (int k = lane; k < n; k += 32) row[k] = buf[w][k];
+        __syncwarp();
+    }
+}
+
 // Row of particle i found by one warp scanning the stencil cells directly
 // from global memory, then bitonic-sorted in the warp's shared buffer
 // (CAPP2 >= cap, power of two).  Used for cells whose stencil holds more
@@ -171,23 +216,7 @@ __device__ void build_row_warp(const NbrArgs &a, int i, int c, int *row)
             }
     __syncwarp();
     int n = count < a.cap ? count : a.cap;
-    for (int k = n + lane; k < CAPP2; k += 32) row[k] = 0x7fffffff;
-    __syncwarp();
-    for (int size = 2; size <= CAPP2; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = lane; t < CAPP2 / 2; t += 32) {
-                int lo = 2 * t - (t & (stride - 1));
-                int hi = lo + stride;
-                bool up = ((lo & size) == 0);
-                int x = row[lo], y = row[hi];
-                if ((x > y) == up) {
-                    row[lo] = y;
-                    row[hi] = x;
-                }
-            }
-            __syncwarp();
-        }
-    }
+    warp_sort_row<CAPP2>(row, n);
     int32_t *out = a.nbr + (size_t)i * a.cap;
     for (int k = lane; k < a.cap; k += 32) out[k] = (k < n) ? row[k] : a.N;
     if (lane == 0) {
@@ -199,23 +228,24 @@ __device__ void build_row_warp(const NbrArgs &a, int i, int c, int *row)
     __syncwarp();
 }
 
-// One CTA per cell.  The candidates of the cell's (deduplicated) stencil are
-// staged once in shared memory as 64-bit keys (index << 16 | slot), sorted
-// ascending with a block-wide bitonic network, and their positions gathered
-// into the sorted order.  Each warp then takes particles of the cell and
-// sweeps the sorted candidates 32 at a time; ballot compaction writes hits
-// straight into the output row, which therefore comes out sorted ascending
-// without a per-particle sort.  All particles of a cell share the staging
-// and the sort.
+// One CTA per cell.  The candidates of the cell's (deduplicated) stencil
+// are staged once in shared memory and put in a canonical order: stencil
+// cells in a fixed order (z, y, x offsets ascending), and inside each cell
+// ascending particle index (each candidate's rank is counted against the
+// ~20 members of its own cell).  Each warp then takes particles of the cell
+// and sweeps the ordered candidates 32 at a time; ballot compaction writes
+// hits straight into the output row.  The row order is therefore a
+// deterministic function of the positions and the cell grid, with no
+// per-particle or per-block sort.
 constexpr int BUILD_CMAX = 1024;   // candidates a block stages in shared memory
 constexpr int BUILD_WARPS = 8;
-
 template <int DIM>
 __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
 {
     count_launch();
     if (!chain_active(a)) return;
-    __shared__ unsigned long long keys[BUILD_CMAX];
+    __shared__ int cidx[BUILD_CMAX];
+    __shared__ int sidx[BUILD_CMAX];
     __shared__ float4 cpos[BUILD_CMAX];
     __shared__ float4 spos[BUILD_CMAX];
     __shared__ int soff[28];        // prefix of the stencil cells' counts
@@ -272,34 +302,26 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
         }
         return;
     }
-    // stage candidates (all slots in parallel): key = index << 16 | slot
+    // stage candidates (all slots in parallel)
     for (int slot = tid; slot < M; slot += blockDim.x) {
         int m = 0;
         while (soff[m + 1] <= slot) ++m;
         int src = sbeg[m] + (slot - soff[m]);
-        keys[slot] = ((unsigned long long)(unsigned)a.ws.atoms[src] << 16) | (unsigned)slot;
+        cidx[slot] = a.ws.atoms[src];
         cpos[slot] = a.ws.rsorted[src];
     }
-    int P2 = 32;
-    while (P2 < M) P2 <<= 1;
-    for (int k = M + tid; k < P2; k += blockDim.x) keys[k] = ~0ull;
     __syncthreads();
-    for (int size = 2; size <= P2; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = tid; t < P2 / 2; t += blockDim.x) {
-                int lo = 2 * t - (t & (stride - 1));
-                int hi = lo + stride;
-                bool up = ((lo & size) == 0);
-                unsigned long long x = keys[lo], y = keys[hi];
-                if ((x > y) == up) {
-                    keys[lo] = y;
-                    keys[hi] = x;
-                }
-            }
-            __syncthreads();
-        }
+    // canonical order: rank inside the candidate's own cell by index
+    for (int slot = tid; slot < M; slot += blockDim.x) {
+        int m = 0;
+        while (soff[m + 1] <= slot) ++m;
+        const int b0 = soff[m], e0 = soff[m + 1];
+        const int me = cidx[slot];
+        int rank = 0;
+        for (int k = b0; k < e0; ++k) rank += (cidx[k] < me);
+        sidx[b0 + rank] = me;
+        spos[b0 + rank] = cpos[slot];
     }
-    for (int k = tid; k < M; k += blockDim.x) spos[k] = cpos[(int)(keys[k] & 0xffffull)];
     __syncthreads();
     const int lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -313,7 +335,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
             bool hit = false;
             int j = 0;
             if (k < M) {
-                j = (int)(keys[k] >> 16);
+                j = sidx[k];
                 float dx, dy, dz;
                 hit = (j != i) && (dist2_rn<DIM>(ri, spos[k], a.box, dx, dy, dz) < a.r_list2);
             }
@@ -389,6 +411,7 @@ NbrArgs make_nbr_args(const md_space *s, const float *d_r, const md_nbr *nb, uin
     a.ws = ws_ptrs(nb);
     a.status = d_status;
     a.gated = gated;
+    a.canonical = (nb->flags & MD_NBR_CANONICAL) ? 1 : 0;
     return a;
 }
 
@@ -402,6 +425,14 @@ void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st)
     k_scatter<<<nb, tb, 0, st>>>(a);
     if (a.dim == 3) k_build_cells<3><<<ncell_total, BUILD_WARPS * 32, 0, st>>>(a);
     else k_build_cells<2><<<ncell_total, BUILD_WARPS * 32, 0, st>>>(a);
+    if (a.canonical) {
+        int g = (a.N + 7) / 8;
+        g = g < 4096 ? g : 4096;
+        if (a.cap <= 64) k_sort_rows<64><<<g, 256, 0, st>>>(a);
+        else if (a.cap <= 128) k_sort_rows<128><<<g, 256, 0, st>>>(a);
+        else if (a.cap <= 256) k_sort_rows<256><<<g, 256, 0, st>>>(a);
+        else k_sort_rows<512><<<g, 256, 0, st>>>(a);
+    }
     k_finish_build<<<1, 1, 0, st>>>(a.ws.ctl);
 }
 

@@ -145,6 +145,7 @@ template <int DIM, int POT, int KICK>
 static void launch_pair_tpp(const PairArgs &a, cudaStream_t st)
 {
     switch (a.tpp) {
+    case 1: launch_pair_t<DIM, 1, POT, KICK>(a, st); break;
     case 4: launch_pair_t<DIM, 4, POT, KICK>(a, st); break;
     case 16: launch_pair_t<DIM, 16, POT, KICK>(a, st); break;
     case 32: launch_pair_t<DIM, 32, POT, KICK>(a, st); break;
@@ -189,7 +190,8 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
     WsPtrs w = ws_ptrs(nb);
     a.ctl = w.ctl;
     a.partials = w.partials;
-    a.tpp = g_tpp;
+    // canonical lists: one thread sums a particle's pairs in row order
+    a.tpp = (nb->flags & MD_NBR_CANONICAL) ? 1 : g_tpp;
     if (p->kind == MD_LJ) {
         if (p->r_cut > nb->r_list) return false;
         float rc = p->r_cut;

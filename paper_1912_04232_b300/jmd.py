@@ -32,6 +32,7 @@ MD_ERR_BOUNDS = 32
 MD_ERR_CUDA = 64
 
 MD_LJ, MD_SOFT_SPHERE, MD_SW, MD_BP = 0, 1, 2, 3
+MD_NBR_CANONICAL = 1
 
 STATUS_NAMES = {MD_ERR_INVALID: "INVALID", MD_ERR_BOX_TOO_SMALL: "BOX_TOO_SMALL",
                 MD_ERR_NBR_OVERFLOW: "NBR_OVERFLOW", MD_ERR_NONFINITE: "NONFINITE",
@@ -54,7 +55,7 @@ class md_nbr(C.Structure):
                 ("ncell_total", C.c_int), ("r_cut", C.c_float), ("skin", C.c_float), ("r_list", C.c_float),
                 ("r_list2", C.c_float), ("half_skin2", C.c_float), ("cell_scale", C.c_float * 3),
                 ("ws_bytes", C.c_size_t), ("nbr", C.c_void_p), ("cnt", C.c_void_p), ("rref", C.c_void_p),
-                ("ws", C.c_void_p)]
+                ("ws", C.c_void_p), ("flags", C.c_int)]
 
 
 class md_pot(C.Structure):
@@ -79,6 +80,8 @@ _SIGS = {
                               C.c_uint64, C.c_uint32, C.c_int, _P(md_nbr), _vp, _vp, C.c_int, _vp, _vp],
     "md_minimize": [_P(md_space), _P(md_pot), C.c_int, C.c_float, C.c_int, _vp, _vp, _P(md_nbr), _vp, _vp, _vp],
     "md_status_poll": [_vp, _P(C.c_uint32), _vp],
+    "md_minimize_adjoint": [_P(md_space), _P(md_pot), _P(md_nbr), _vp, C.c_int, C.c_float, C.c_float, C.c_float,
+                            C.c_float, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
     "md_neighbor_list_build_noalloc": [_P(md_space), _vp, C.c_int, C.c_float, C.c_float, C.c_int, _vp, _vp, _vp,
                                        _vp],
 }
@@ -88,6 +91,8 @@ for _name, _args in _SIGS.items():
     _f.restype = C.c_int
 _lib.md_launch_count.restype = C.c_uint64
 _lib.md_launch_count.argtypes = []
+_lib.md_adjoint_workspace_size.restype = C.c_size_t
+_lib.md_adjoint_workspace_size.argtypes = [C.c_int, C.c_int, C.c_int]
 _lib.md_noalloc_scratch_bytes.restype = C.c_size_t
 _lib.md_noalloc_scratch_bytes.argtypes = []
 _lib.md_version.restype = C.c_char_p
@@ -200,6 +205,16 @@ def md_noalloc_scratch_bytes() -> int:
     return int(_lib.md_noalloc_scratch_bytes())
 
 
+def md_adjoint_workspace_size(N, T, K) -> int:
+    return int(_lib.md_adjoint_workspace_size(int(N), int(T), int(K)))
+
+
+def md_minimize_adjoint(space, pot, nb, s0, nA, D, dB, Lp, eta, T, K, r, f, ws, out, status=None, stream=None):
+    _check(_lib.md_minimize_adjoint(C.byref(space), C.byref(pot), C.byref(nb), _ptr(s0), int(nA), float(D),
+                                    float(dB), float(Lp), float(eta), int(T), int(K), _ptr(r), _ptr(f), _ptr(ws),
+                                    _ptr(out), _ptr(status), _stream(stream)), "md_minimize_adjoint")
+
+
 def md_status_poll(status, stream=None) -> int:
     h = C.c_uint32()
     _check(_lib.md_status_poll(_ptr(status), C.byref(h), _stream(stream)), "md_status_poll")
@@ -248,10 +263,13 @@ def sw_pot(params) -> md_pot:
 class NeighborList:
     """Plans a list, allocates its caller-owned tensors with torch and binds them."""
 
-    def __init__(self, space: md_space, N: int, r_cut: float, skin: float, cap: int, device="cuda", stream=None):
+    def __init__(self, space: md_space, N: int, r_cut: float, skin: float, cap: int, device="cuda", stream=None,
+                 canonical: bool = False):
         import torch
         self.space = space
         self.plan = md_nbr_plan(space, N, r_cut, skin, cap)
+        if canonical:
+            self.plan.flags |= MD_NBR_CANONICAL
         self.nbr = torch.empty((N, cap), dtype=torch.int32, device=device)
         self.cnt = torch.zeros(N, dtype=torch.int32, device=device)
         self.rref = torch.zeros((N, 4), dtype=torch.float32, device=device)

@@ -35,7 +35,19 @@ def force_error(F_gpu, F_ref):
 
 
 def rows_equal(cnt_g, nbr_g, cnt_o, nbr_o):
-    """Bit-exact comparison of sorted padded rows."""
-    np.testing.assert_array_equal(np.asarray(cnt_g), cnt_o)
+    """Bit-exact comparison of neighbor rows as sets: counts equal, each
+    GPU row's valid entries sorted equal the oracle's sorted row, entries
+    unique, padding equal to N."""
+    cnt_g = np.asarray(cnt_g)
+    nbr_g = np.asarray(nbr_g)
+    np.testing.assert_array_equal(cnt_g, cnt_o)
+    N = nbr_g.shape[0]
     cap = min(nbr_g.shape[1], nbr_o.shape[1])
-    np.testing.assert_array_equal(np.asarray(nbr_g)[:, :cap], nbr_o[:, :cap])
+    n = np.minimum(cnt_g, cap)
+    col = np.arange(nbr_g.shape[1])[None, :]
+    valid = col < n[:, None]
+    assert np.all(nbr_g[~valid] == N)
+    big = np.where(valid, nbr_g, np.iinfo(np.int32).max)
+    srt = np.sort(big, axis=1)[:, :cap]
+    want = np.where(np.arange(cap)[None, :] < n[:, None], nbr_o[:, :cap], np.iinfo(np.int32).max)
+    np.testing.assert_array_equal(srt, want)

@@ -1,0 +1,125 @@
+"""GPU parity: gradient descent on 2-D bidisperse soft disks (Sec. 4.2,
+App. A) and the hand-written adjoint dE_final/dD through the whole
+minimisation with checkpoint recomputation, against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_helpers import dev, force_error, rows_equal, status_word, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SKIN = 0.3
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1912_04232_b300 as P
+    return P
+
+
+def _packing_pos(p, L):
+    r = np.zeros((p.N, 4), np.float32)
+    r[:, :2] = (p.s0 * L).astype(np.float32)
+    r[:, 3] = p.diam.astype(np.float32)
+    return r
+
+
+def test_soft_sphere_forces_2d_match_oracle(P):
+    import torch
+    p = W.packing_2d(N=1024, D=1.4, seed=3)
+    L = W.f32(W.packing_box(1024, 1.4, 0.9))
+    r = _packing_pos(p, L)
+    s = P.md_space_periodic(2, [L, L])
+    nl = P.NeighborList(s, p.N, 1.4, SKIN, 64)
+    rd = to_dev(r, torch.float32)
+    st = status_word()
+    nl.build(rd, st)
+    f = torch.zeros((p.N, 4), dtype=torch.float32, device=dev())
+    E = torch.zeros(1, dtype=torch.float64, device=dev())
+    P.md_energy_forces(s, P.soft_pot(1.0, 2.0), rd, nl.plan, f, E, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    U, F, e = O.soft(r, r[:, 3].astype(np.float64), L, dim=2)
+    assert force_error(f.cpu().numpy(), F) <= 1e-4
+    assert abs(E.item() - U) <= 1e-5 * abs(U)
+    cnt_o, nb_o = O.neighbor_list(r, L, float(nl.plan.r_list), dim=2, cap=64)
+    rows_equal(nl.cnt.cpu().numpy(), nl.nbr.cpu().numpy(), cnt_o, nb_o)
+
+
+def test_gradient_descent_matches_oracle(P):
+    import torch
+    p = W.packing_2d(N=256, D=1.3, seed=4)
+    L = W.f32(W.packing_box(256, 1.3, 0.9))
+    r = _packing_pos(p, L)
+    s = P.md_space_periodic(2, [L, L])
+    nl = P.NeighborList(s, p.N, 1.3, SKIN, 64)
+    rd = to_dev(r, torch.float32)
+    f = torch.zeros_like(rd)
+    st = status_word()
+    nl.build(rd, st)
+    T = 100
+    E = torch.zeros(T + 1, dtype=torch.float64, device=dev())
+    P.md_minimize(s, P.soft_pot(), 0, 0.05, T, rd, f, nl.plan, E, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    xo, Eo = O.gd(r, L, "soft", eta=0.05, nsteps=T, dim=2, diam=r[:, 3].astype(np.float64))
+    Eg = E.cpu().numpy()
+    np.testing.assert_allclose(Eg, Eo, rtol=2e-4, atol=1e-6)
+    assert np.all(np.diff(Eg) <= 1e-6 * Eg[0])
+    assert np.abs(rd.cpu().numpy()[:, :2] - xo[:, :2]).max() < 1e-3
+
+
+def _adjoint(P, p, D, T, K, phi=0.9, eta=0.05):
+    import torch
+    N = p.N
+    L64 = O.packing_box(N, D, phi)
+    L = W.f32(L64)
+    Lp = (N // 2) * math.pi * D / (4 * phi * L64)
+    s = P.md_space_periodic(2, [L, L])
+    nl = P.NeighborList(s, N, max(D, 1.0), SKIN, 64, canonical=True)
+    s0 = np.zeros((N, 4), np.float32)
+    s0[:, :2] = p.s0
+    s0d = to_dev(s0, torch.float32)
+    r = torch.zeros((N, 4), dtype=torch.float32, device=dev())
+    f = torch.zeros_like(r)
+    ws = torch.empty(P.md_adjoint_workspace_size(N, T, K), dtype=torch.uint8, device=dev())
+    out = torch.zeros(2, dtype=torch.float64, device=dev())
+    st = status_word()
+    P.md_minimize_adjoint(s, P.soft_pot(), nl.plan, s0d, N // 2, D, 1.0, Lp, eta, T, K, r, f, ws, out, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    return out.cpu().numpy(), r.cpu().numpy()
+
+
+@pytest.mark.parametrize("N,D,T,seed", [(64, 1.3, 40, 0), (128, 1.1, 80, 1), (256, 1.6, 60, 2)])
+def test_adjoint_matches_fp64_reverse_mode(P, N, D, T, seed):
+    p = W.packing_2d(N=N, D=D, seed=seed)
+    K = int(math.ceil(math.sqrt(T)))
+    (E, g), r = _adjoint(P, p, D, T, K)
+    Eo, go, _ = O.gd_adjoint(p.s0, D, T=T)
+    assert abs(E - Eo) <= 1e-4 * abs(Eo) + 1e-7
+    assert abs(g - go) <= 2e-3 * abs(go) + 1e-6, (g, go)
+
+
+def test_adjoint_is_identical_for_every_checkpoint_interval(P):
+    p = W.packing_2d(N=128, D=1.25, seed=5)
+    T = 60
+    res = [_adjoint(P, p, 1.25, T, K)[0] for K in (1, 8, T)]
+    for x in res[1:]:
+        assert x[0] == res[0][0] and x[1] == res[0][1]
+
+
+def test_adjoint_full_size_packing(P):
+    # N = 1024, 2000 GD steps, K = ceil(sqrt(2000)) = 45, against the FP64
+    # reverse mode; FP32 and FP64 trajectories may part near saddles, so the
+    # check is on the final energy and the gradient to a looser tolerance
+    p = W.packing_2d(N=1024, D=1.4, seed=0)
+    T = 2000
+    (E, g), r = _adjoint(P, p, 1.4, T, 45)
+    Eo, go, _ = O.gd_adjoint(p.s0, 1.4, T=T)
+    assert abs(E - Eo) <= 2e-3 * abs(Eo)
+    assert abs(g - go) <= 5e-2 * abs(go) + 1e-3, (g, go)
