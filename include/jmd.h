@@ -184,6 +184,19 @@ typedef struct {
     const void *model;
 } md_pot;
 
+/* Learned potential (MD_BP, Sec. 3.2.4 and 4.1): Behler-Parrinello
+ * symmetry functions (8 radial, 8 angular; cutoff 3.77 A) feeding a per-atom
+ * network 16 -> 64 -> 64 -> 1 with SiLU.  All pointers are device memory
+ * owned by the caller. */
+typedef struct {
+    const float *params;  /* [5313] FP32: W1 [64][16], b1 [64], W2 [64][64], b2 [64], w3 [64], b3 */
+    const float *norm;    /* [32] FP32: descriptor mean [16] then standard deviation [16] */
+    float *G;             /* [N][16] scratch: descriptors */
+    float *dEdG;          /* [N][16] scratch: network input gradient */
+    float *Ei;            /* [N] scratch: per-atom energies */
+    int sys_n;            /* 0, or atoms per system for concatenated equal-size systems */
+} md_bp_model;
+
 /* Forces and per-particle energies into d_f [N][4]; if d_E != NULL the FP64
  * total energy sum_i e_i is written to *d_E (device).  Needs a built list
  * with r_list >= the potential's range. */
@@ -229,6 +242,64 @@ JMD_API md_status md_integrate_langevin(const md_space *s, const md_pot *p, floa
  * d_f holds F at the final positions on return. */
 JMD_API md_status md_minimize(const md_space *s, const md_pot *p, int kind, float step, int nsteps, float *d_r,
                               float *d_f, md_nbr *nb, double *d_E, uint32_t *d_status, md_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Learned potential: the pieces of a forward/backward and a training step   */
+/* (Sec. 4.1: energy + force loss).  sys_n as in md_bp_model.                */
+/* ------------------------------------------------------------------------ */
+/* G [N][16] from positions (list with r_list >= 3.77 A). */
+JMD_API md_status md_bp_descriptors(const md_space *s, const float *d_r, const md_nbr *nb, int sys_n, float *d_G,
+                                    uint32_t *d_status, md_stream_t stream);
+
+/* Per-atom network: E_i [N] and dE_i/dG_i [N][16] (FP32). */
+JMD_API md_status md_bp_mlp_infer(const float *d_params, const float *d_norm, const float *d_G, int N, float *d_Ei,
+                                  float *d_dEdG, md_stream_t stream);
+
+/* The same network on the tensor cores: tcgen05 MMAs with BF16 operands and
+ * FP32 accumulation in tensor memory, 128 atoms per tile (4 MMAs: two
+ * forward layers, two backward products).  BF16 rounding of the inputs and
+ * hidden activations makes it agree with md_bp_mlp_infer to about 1e-2
+ * relative.  Device waits are bounded: MD_ERR_TIMEOUT in *d_status. */
+JMD_API md_status md_bp_mlp_infer_tc(const float *d_params, const float *d_norm, const float *d_G, int N,
+                                     float *d_Ei, float *d_dEdG, uint32_t *d_status, md_stream_t stream);
+
+/* Which network kernel MD_BP force evaluations use: 1 = tensor cores (BF16),
+ * 0 = FP32 CUDA cores (default). */
+JMD_API md_status md_bp_set_tensor_cores(int on);
+
+/* F_k = -sum_i dE_i/dG_i . dG_i/dr_k into d_f [N][4] (w = E_k when d_Ei is
+ * given); optional FP64 total of d_Ei into *d_E. */
+JMD_API md_status md_bp_forces(const md_space *s, const float *d_r, const md_nbr *nb, int sys_n,
+                               const float *d_dEdG, const float *d_Ei, float *d_f, double *d_E, uint32_t *d_status,
+                               md_stream_t stream);
+
+/* V_i = sum_k dG_i/dr_k . dF_k (descriptor Jacobian applied to d_dF [N][4]). */
+JMD_API md_status md_bp_jvp(const md_space *s, const float *d_r, const md_nbr *nb, int sys_n, const float *d_dF,
+                            float *d_V, uint32_t *d_status, md_stream_t stream);
+
+/* Scratch bytes of md_bp_mlp_train for N atoms. */
+JMD_API size_t md_bp_train_scratch_size(int N);
+
+/* Gradient of J = sum_i [c_E,i E_i - c_F dE_i/dG_i . V_i] with respect to the
+ * packed parameters into d_grad [5313].  With c_E,i = 2 (E_s - E_ref,s) /
+ * (S N^2) for atom i of snapshot s and V = the JVP of c_F-scaled force
+ * errors this is the gradient of the energy + force loss. */
+JMD_API md_status md_bp_mlp_train(const float *d_params, const float *d_norm, const float *d_G, const float *d_V,
+                                  const float *d_cE, float cF, int N, void *d_scratch, float *d_grad,
+                                  md_stream_t stream);
+
+/* Loss of the energy + force fit (Sec. 4.1) over S snapshots of n atoms:
+ *   loss = mean_s ((E_s - E_ref,s) / n)^2 + w_F mean (F - F_ref)^2
+ * Writes c_E [S n] and dF [S n][4] (the force errors scaled by
+ * 2 w_F / (3 n S), to feed md_bp_jvp and md_bp_mlp_train with c_F = 1) and
+ * the per-snapshot loss terms d_loss [2 S] (energy, force). */
+JMD_API md_status md_bp_loss_prep(const float *d_Ei, const float *d_F, const float *d_Fref, const double *d_Eref,
+                                  int S, int n, float wF, float *d_cE, float *d_dF, double *d_loss,
+                                  md_stream_t stream);
+
+/* Adam (bias-corrected) on an FP32 vector; step counts from 1. */
+JMD_API md_status md_adam_step(float *d_params, const float *d_grad, float *d_m, float *d_v, int n, float lr,
+                               float beta1, float beta2, float eps, int step, md_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Differentiating through minimisation (Sec. 4.2, App. A): the final energy */

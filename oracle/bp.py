@@ -159,4 +159,4 @@ def loss_and_grads(batch, p, mu, sd, w_F=1.0):
         nF += 3 * N
     loss = lossE / len(batch) + w_F * lossF / nF
     grads = torch.autograd.grad(loss, list(params.values()))
-    return float(loss), {k: gr.detach() for k, gr in zip(params.keys(), grads)}
+    return loss.item(), {k: gr.detach() for k, gr in zip(params.keys(), grads)}

@@ -1,0 +1,521 @@
+// bp.cu -- Behler-Parrinello symmetry-function descriptors (Sec. 3.2.4, 4.1)
+// and the two gathers that tie them to forces and to training.
+//
+//   f_c(r) = (cos(pi r / R_c) + 1) / 2,  R_c = 3.77 A
+//   radial   G_m  = sum_j exp(-eta_r (r_ij - R_m)^2) f_c(r_ij),   R_m = 2 + 0.25 (m-1), m = 1..8
+//   angular  G_zl = 2^(1-z) sum_{j<k} (1 + l cos theta_jik)^z exp(-eta_a (r_ij^2 + r_ik^2)) f_c f_c,
+//            z in {1, 2, 4, 16}, l in {+1, -1}
+//
+// k_bp_desc   : G [N][16], one warp per atom (pairs and triplets over lanes)
+// k_bp_force  : F_k = -sum_i sum_m e_im dG_im/dr_k with e = dE/dG from the
+//               network; gather form (self terms, pair terms of the
+//               neighbors, triplets centred on each neighbor with k as a
+//               leg), one warp per atom, no atomics
+// k_bp_jvp    : v_im = sum_k dG_im/dr_k . dF_k (the descriptor Jacobian
+//               applied to a per-atom vector field): the input of the
+//               force-loss gradient, gathered over the atom's own pairs and
+//               triplets
+#include "common.cuh"
+#include "kernels.cuh"
+#include "bp.cuh"
+#include "reduce.cuh"
+
+namespace jmd {
+
+constexpr int BP_MAXN = 48;   // neighbors inside R_c kept per atom
+constexpr int BP_WARPS = 8;
+
+struct BpConst {
+    float rc, rc2, eta_r, eta_a, pi_rc;
+};
+
+__device__ __forceinline__ BpConst bp_const()
+{
+    BpConst c;
+    c.rc = BP_RC;
+    c.rc2 = BP_RC * BP_RC;
+    c.eta_r = BP_ETA_R;
+    c.eta_a = BP_ETA_A;
+    c.pi_rc = 3.14159265358979f / BP_RC;
+    return c;
+}
+
+__device__ __forceinline__ void fcut(const BpConst &c, float r, float &f, float &df)
+{
+    float s, co;
+    __sincosf(c.pi_rc * r, &s, &co);
+    f = 0.5f * (co + 1.0f);
+    df = -0.5f * c.pi_rc * s;
+}
+
+// radial g_m(r) and dg_m/dr for all 8 centres
+__device__ __forceinline__ void radial8(const BpConst &c, float r, float g[8], float dg[8])
+{
+    float f, df;
+    fcut(c, r, f, df);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        float x = r - (2.0f + 0.25f * m);
+        float ex = __expf(-c.eta_r * x * x);
+        g[m] = ex * f;
+        dg[m] = ex * (df - 2.0f * c.eta_r * x * f);
+    }
+}
+
+// q^(z-1) and q^z for z in {1, 2, 4, 16} (slot order z-major, l-minor
+// handled by the caller)
+__device__ __forceinline__ void powers(float q, float pz[4], float pzm1[4])
+{
+    float q2 = q * q, q4 = q2 * q2, q8 = q4 * q4;
+    pz[0] = q;
+    pzm1[0] = 1.0f;
+    pz[1] = q2;
+    pzm1[1] = q;
+    pz[2] = q4;
+    pzm1[2] = q2 * q;
+    pz[3] = q8 * q8;
+    pzm1[3] = q8 * q4 * q2 * q;
+}
+
+// Angular terms of one triplet (centre at the origin, legs u, w; |u|, |w| < R_c):
+// t[8] in column order (z, l) = (1,+) (1,-) (2,+) (2,-) (4,+) ... ; when
+// grad != 0 also dt/du, dt/dw for each of the 8 columns.
+template <bool GRAD>
+__device__ __forceinline__ void angular8(const BpConst &c, float ux, float uy, float uz, float ru, float wx, float wy,
+                                         float wz, float rw, float t[8], float du[8][3], float dw[8][3])
+{
+    float iu = 1.0f / ru, iw = 1.0f / rw;
+    float cs = (ux * wx + uy * wy + uz * wz) * iu * iw;
+    float fu, dfu, fw, dfw;
+    fcut(c, ru, fu, dfu);
+    fcut(c, rw, fw, dfw);
+    float ex = __expf(-c.eta_a * (ru * ru + rw * rw));
+    float B = ex * fu * fw;
+    // dB/du = B (-2 eta_a u) + ex dfu fw u/|u|
+    float bu = -2.0f * c.eta_a * B + ex * dfu * fw * iu;
+    float bw = -2.0f * c.eta_a * B + ex * fu * dfw * iw;
+    float dcu[3], dcw[3];
+    if (GRAD) {
+        dcu[0] = wx * iu * iw - cs * ux * iu * iu;
+        dcu[1] = wy * iu * iw - cs * uy * iu * iu;
+        dcu[2] = wz * iu * iw - cs * uz * iu * iu;
+        dcw[0] = ux * iu * iw - cs * wx * iw * iw;
+        dcw[1] = uy * iu * iw - cs * wy * iw * iw;
+        dcw[2] = uz * iu * iw - cs * wz * iw * iw;
+    }
+    const float zs[4] = {1.0f, 2.0f, 4.0f, 16.0f};
+    const float pref[4] = {1.0f, 0.5f, 0.125f, 1.0f / 32768.0f};   // 2^(1 - z)
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        float lam = l == 0 ? 1.0f : -1.0f;
+        float q = 1.0f + lam * cs;
+        float pz[4], pzm1[4];
+        powers(q, pz, pzm1);
+#pragma unroll
+        for (int zi = 0; zi < 4; ++zi) {
+            int col = 2 * zi + l;
+            t[col] = pref[zi] * pz[zi] * B;
+            if (GRAD) {
+                float a = pref[zi] * zs[zi] * pzm1[zi] * lam * B;   // dt/dc
+                float b = pref[zi] * pz[zi];                          // dt/dB
+                du[col][0] = a * dcu[0] + b * bu * ux;
+                du[col][1] = a * dcu[1] + b * bu * uy;
+                du[col][2] = a * dcu[2] + b * bu * uz;
+                dw[col][0] = a * dcw[0] + b * bw * wx;
+                dw[col][1] = a * dcw[1] + b * bw * wy;
+                dw[col][2] = a * dcw[2] + b * bw * wz;
+            }
+        }
+    }
+}
+
+// Neighbors of atom i inside R_c into the warp's shared list
+// (j, u = r_j - r_i, |u|); returns the count (clamped, overflow flagged).
+__device__ __forceinline__ int gather_within(const BpArgs &a, const BpConst &c, int i, const float4 &ri, int *nj,
+                                             float4 *nd)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int n = a.cnt[i];
+    n = n < a.cap ? n : a.cap;
+    const int32_t *row = a.nbr + (size_t)i * a.cap;
+    const int base = a.sys_n ? (i / a.sys_n) * a.sys_n : 0;
+    int m = 0;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        int k = k0 + lane;
+        bool in = false;
+        int j = 0;
+        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+        if (k < n) {
+            j = row[k] + base;
+            float4 rj = __ldg(a.r + j);
+            r2 = dist2_rn<3>(rj, ri, a.box, dx, dy, dz);
+            in = r2 < c.rc2;
+        }
+        unsigned mk = __ballot_sync(0xffffffffu, in);
+        int pos = m + __popc(mk & lt);
+        if (in && pos < BP_MAXN) {
+            nj[pos] = j;
+            nd[pos] = make_float4(dx, dy, dz, sqrtf(r2));
+        }
+        m += __popc(mk);
+    }
+    if (m > BP_MAXN) {
+        if (lane == 0) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+        m = BP_MAXN;
+    }
+    __syncwarp();
+    return m;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(BP_WARPS * 32) k_bp_desc(BpArgs a)
+{
+    count_launch();
+    __shared__ int nj[BP_WARPS][BP_MAXN];
+    __shared__ float4 nd[BP_WARPS][BP_MAXN];
+    const BpConst c = bp_const();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * BP_WARPS + w; i < a.N; i += gridDim.x * BP_WARPS) {
+        const float4 ri = a.r[i];
+        const int m = gather_within(a, c, i, ri, nj[w], nd[w]);
+        float G[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) G[q] = 0.0f;
+        for (int s = lane; s < m; s += 32) {
+            float g[8], dg[8];
+            radial8(c, nd[w][s].w, g, dg);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) G[q] += g[q];
+        }
+        for (int t = lane; t < m * m; t += 32) {
+            int s1 = t / m, s2 = t - s1 * m;
+            if (s1 >= s2) continue;
+            float4 u = nd[w][s1], v = nd[w][s2];
+            float tt[8], du[8][3], dw[8][3];
+            angular8<false>(c, u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, tt, du, dw);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) G[8 + q] += tt[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) G[q] = warp_sum(G[q]);
+        if (lane == 0) {
+            float4 *o = reinterpret_cast<float4 *>(a.G + (size_t)i * 16);
+            o[0] = make_float4(G[0], G[1], G[2], G[3]);
+            o[1] = make_float4(G[4], G[5], G[6], G[7]);
+            o[2] = make_float4(G[8], G[9], G[10], G[11]);
+            o[3] = make_float4(G[12], G[13], G[14], G[15]);
+        }
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void load16(const float *p, float e[16])
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float4 v = __ldg(q + k);
+        e[4 * k] = v.x;
+        e[4 * k + 1] = v.y;
+        e[4 * k + 2] = v.z;
+        e[4 * k + 3] = v.w;
+    }
+}
+
+template <int KICK>
+__global__ void __launch_bounds__(BP_WARPS * 32) k_bp_force(BpArgs a)
+{
+    count_launch();
+    __shared__ int nj[BP_WARPS][BP_MAXN];
+    __shared__ float4 nd[BP_WARPS][BP_MAXN];
+    const BpConst c = bp_const();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float pe_acc = 0.0f, ke_acc = 0.0f;
+    for (int k = blockIdx.x * BP_WARPS + w; k < a.N; k += gridDim.x * BP_WARPS) {
+        const float4 rk = a.r[k];
+        const int m = gather_within(a, c, k, rk, nj[w], nd[w]);
+        float ek[16];
+        load16(a.dEdG + (size_t)k * 16, ek);
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        // self radial + the neighbor's radial term of the same pair:
+        // both give (e_km + e_jm) g'_m(r) u/r with u = r_j - r_k
+        for (int s = lane; s < m; s += 32) {
+            float4 u = nd[w][s];
+            float ej[16];
+            load16(a.dEdG + (size_t)nj[w][s] * 16, ej);
+            float g[8], dg[8];
+            radial8(c, u.w, g, dg);
+            float sc = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) sc += (ek[q] + ej[q]) * dg[q];
+            sc /= u.w;
+            fx += sc * u.x;
+            fy += sc * u.y;
+            fz += sc * u.z;
+        }
+        // triplets centred on k: F_k += sum_m e_km (dt/du + dt/dw)
+        for (int t = lane; t < m * m; t += 32) {
+            int s1 = t / m, s2 = t - s1 * m;
+            if (s1 >= s2) continue;
+            float4 u = nd[w][s1], v = nd[w][s2];
+            float tt[8], du[8][3], dw[8][3];
+            angular8<true>(c, u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, tt, du, dw);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                fx += ek[8 + q] * (du[q][0] + dw[q][0]);
+                fy += ek[8 + q] * (du[q][1] + dw[q][1]);
+                fz += ek[8 + q] * (du[q][2] + dw[q][2]);
+            }
+        }
+        // triplets centred on neighbor j with k as leg u' = r_k - r_j:
+        // F_k -= sum_m e_jm dt(u', w')/du', w' = r_l - r_j, l in N(j), l != k
+        for (int s = 0; s < m; ++s) {
+            const int j = nj[w][s];
+            const float4 uj = nd[w][s];
+            const float4 rj = __ldg(a.r + j);
+            float ej[8];
+            {
+                const float4 *q = reinterpret_cast<const float4 *>(a.dEdG + (size_t)j * 16 + 8);
+                float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+                ej[0] = v0.x; ej[1] = v0.y; ej[2] = v0.z; ej[3] = v0.w;
+                ej[4] = v1.x; ej[5] = v1.y; ej[6] = v1.z; ej[7] = v1.w;
+            }
+            int nn = a.cnt[j];
+            nn = nn < a.cap ? nn : a.cap;
+            const int32_t *rowj = a.nbr + (size_t)j * a.cap;
+            const int basej = a.sys_n ? (j / a.sys_n) * a.sys_n : 0;
+            for (int k0 = 0; k0 < nn; k0 += 32) {
+                int kk = k0 + lane;
+                if (kk >= nn) continue;
+                int l = rowj[kk] + basej;
+                if (l == k) continue;
+                float4 rl = __ldg(a.r + l);
+                float wx, wy, wz;
+                float w2 = dist2_rn<3>(rl, rj, a.box, wx, wy, wz);
+                if (!(w2 < c.rc2)) continue;
+                float tt[8], du[8][3], dw[8][3];
+                angular8<true>(c, -uj.x, -uj.y, -uj.z, uj.w, wx, wy, wz, sqrtf(w2), tt, du, dw);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    fx -= ej[q] * du[q][0];
+                    fy -= ej[q] * du[q][1];
+                    fz -= ej[q] * du[q][2];
+                }
+            }
+        }
+        fx = warp_sum(fx);
+        fy = warp_sum(fy);
+        fz = warp_sum(fz);
+        if (lane == 0) {
+            const float ei = a.Ei ? a.Ei[k] : 0.0f;
+            a.pa.f[k] = make_float4(fx, fy, fz, ei);
+            pe_acc += ei;
+            if (KICK) {
+                float4 v = a.pa.v[k];
+                v.x += a.pa.half_dt_over_m * fx;
+                v.y += a.pa.half_dt_over_m * fy;
+                v.z += a.pa.half_dt_over_m * fz;
+                a.pa.v[k] = v;
+                ke_acc += 0.5f * a.pa.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
+            }
+        }
+        __syncwarp();
+    }
+    if (!a.pa.E_out && !KICK) return;
+    energy_epilogue(pe_acc, ke_acc, a.pa);
+}
+
+// v_im = sum over atom i's pairs and triplets of dG_im/dr . dF (dF [N][4]).
+__global__ void __launch_bounds__(BP_WARPS * 32) k_bp_jvp(BpArgs a)
+{
+    count_launch();
+    __shared__ int nj[BP_WARPS][BP_MAXN];
+    __shared__ float4 nd[BP_WARPS][BP_MAXN];
+    const BpConst c = bp_const();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * BP_WARPS + w; i < a.N; i += gridDim.x * BP_WARPS) {
+        const float4 ri = a.r[i];
+        const int m = gather_within(a, c, i, ri, nj[w], nd[w]);
+        const float4 dFi = a.dF[i];
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+        for (int s = lane; s < m; s += 32) {
+            float4 u = nd[w][s];
+            float4 dFj = a.dF[nj[w][s]];
+            float g[8], dg[8];
+            radial8(c, u.w, g, dg);
+            float p = ((dFj.x - dFi.x) * u.x + (dFj.y - dFi.y) * u.y + (dFj.z - dFi.z) * u.z) / u.w;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] += dg[q] * p;
+        }
+        for (int t = lane; t < m * m; t += 32) {
+            int s1 = t / m, s2 = t - s1 * m;
+            if (s1 >= s2) continue;
+            float4 u = nd[w][s1], vv = nd[w][s2];
+            float4 dFj = a.dF[nj[w][s1]], dFl = a.dF[nj[w][s2]];
+            float ax = dFj.x - dFi.x, ay = dFj.y - dFi.y, az = dFj.z - dFi.z;
+            float bx = dFl.x - dFi.x, by = dFl.y - dFi.y, bz = dFl.z - dFi.z;
+            float tt[8], du[8][3], dw[8][3];
+            angular8<true>(c, u.x, u.y, u.z, u.w, vv.x, vv.y, vv.z, vv.w, tt, du, dw);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                v[8 + q] += du[q][0] * ax + du[q][1] * ay + du[q][2] * az + dw[q][0] * bx + dw[q][1] * by +
+                            dw[q][2] * bz;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = warp_sum(v[q]);
+        if (lane == 0) {
+            float4 *o = reinterpret_cast<float4 *>(a.V + (size_t)i * 16);
+            o[0] = make_float4(v[0], v[1], v[2], v[3]);
+            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+            o[2] = make_float4(v[8], v[9], v[10], v[11]);
+            o[3] = make_float4(v[12], v[13], v[14], v[15]);
+        }
+        __syncwarp();
+    }
+}
+
+static int bp_grid(int N)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    int groups = (N + BP_WARPS - 1) / BP_WARPS;
+    int g = sms * 8;
+    return groups < g ? groups : g;
+}
+
+void enqueue_bp_desc(const BpArgs &a, cudaStream_t st) { k_bp_desc<<<bp_grid(a.N), BP_WARPS * 32, 0, st>>>(a); }
+
+void enqueue_bp_force(const BpArgs &a, int kick, cudaStream_t st)
+{
+    if (kick) k_bp_force<1><<<bp_grid(a.N), BP_WARPS * 32, 0, st>>>(a);
+    else k_bp_force<0><<<bp_grid(a.N), BP_WARPS * 32, 0, st>>>(a);
+}
+
+void enqueue_bp_jvp(const BpArgs &a, cudaStream_t st) { k_bp_jvp<<<bp_grid(a.N), BP_WARPS * 32, 0, st>>>(a); }
+
+void enqueue_mlp_infer(const float *P, const float *norm, const float *G, int N, float *Ei, float *dEdG,
+                       cudaStream_t st);
+void enqueue_mlp_infer_tc(const float *P, const float *norm, const float *G, int N, float *Ei, float *dEdG,
+                          uint32_t *status, cudaStream_t st);
+
+static int g_bp_tc = 0;   // 1: network on the tensor cores (BF16), 0: FP32 CUDA cores
+
+static BpArgs bp_args_from(const PairArgs &pa)
+{
+    BpArgs b;
+    memset(&b, 0, sizeof(b));
+    b.box = pa.box;
+    b.N = pa.N;
+    b.cap = pa.cap;
+    b.sys_n = pa.bp_sys_n;
+    b.r = pa.r;
+    b.nbr = pa.nbr;
+    b.cnt = pa.cnt;
+    b.G = pa.bp_G;
+    b.dEdG = pa.bp_dEdG;
+    b.Ei = pa.bp_Ei;
+    b.status = pa.status;
+    b.pa = pa;
+    return b;
+}
+
+// Learned-potential forces: descriptors, network (energy and input
+// gradient), force gather (with the closing kick when asked).
+void enqueue_bp_step(const PairArgs &pa, int kick, cudaStream_t st)
+{
+    BpArgs b = bp_args_from(pa);
+    enqueue_bp_desc(b, st);
+    if (g_bp_tc)
+        enqueue_mlp_infer_tc(pa.bp_params, pa.bp_norm, pa.bp_G, pa.N, pa.bp_Ei, pa.bp_dEdG, pa.status, st);
+    else
+        enqueue_mlp_infer(pa.bp_params, pa.bp_norm, pa.bp_G, pa.N, pa.bp_Ei, pa.bp_dEdG, st);
+    enqueue_bp_force(b, kick, st);
+}
+
+static bool bp_list_ok(const md_space *s, const md_nbr *nb)
+{
+    return s && nb && s->dim == 3 && nb->dim == 3 && nb->nbr && nb->cnt && nb->r_list >= BP_RC;
+}
+
+static BpArgs bp_plain(const md_space *s, const float *d_r, const md_nbr *nb, int sys_n, uint32_t *d_status)
+{
+    BpArgs b;
+    memset(&b, 0, sizeof(b));
+    b.box = make_box(s);
+    b.N = nb->N;
+    b.cap = nb->cap;
+    b.sys_n = sys_n;
+    b.r = (const float4 *)d_r;
+    b.nbr = nb->nbr;
+    b.cnt = nb->cnt;
+    b.status = d_status;
+    return b;
+}
+
+}  // namespace jmd
+
+using namespace jmd;
+
+extern "C" md_status md_bp_set_tensor_cores(int on)
+{
+    g_bp_tc = on ? 1 : 0;
+    return MD_OK;
+}
+
+extern "C" md_status md_bp_descriptors(const md_space *s, const float *d_r, const md_nbr *nb, int sys_n, float *d_G,
+                                       uint32_t *d_status, md_stream_t stream)
+{
+    if (!bp_list_ok(s, nb) || !d_r || !d_G || sys_n < 0) return MD_ERR_INVALID;
+    BpArgs b = bp_plain(s, d_r, nb, sys_n, d_status);
+    b.G = d_G;
+    enqueue_bp_desc(b, (cudaStream_t)stream);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+extern "C" md_status md_bp_forces(const md_space *s, const float *d_r, const md_nbr *nb, int sys_n,
+                                  const float *d_dEdG, const float *d_Ei, float *d_f, double *d_E, uint32_t *d_status,
+                                  md_stream_t stream)
+{
+    if (!bp_list_ok(s, nb) || !d_r || !d_dEdG || !d_f || sys_n < 0 || !nb->ws) return MD_ERR_INVALID;
+    if (d_E && !d_Ei) return MD_ERR_INVALID;
+    BpArgs b = bp_plain(s, d_r, nb, sys_n, d_status);
+    b.dEdG = d_dEdG;
+    b.Ei = d_Ei;
+    WsPtrs w = ws_ptrs(nb);
+    b.pa.f = (float4 *)d_f;
+    b.pa.E_out = d_E;
+    b.pa.ctl = w.ctl;
+    b.pa.partials = w.partials;
+    b.pa.status = d_status;
+    if (bp_grid(nb->N) > w.max_blocks) return MD_ERR_INVALID;
+    enqueue_bp_force(b, 0, (cudaStream_t)stream);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+extern "C" md_status md_bp_jvp(const md_space *s, const float *d_r, const md_nbr *nb, int sys_n, const float *d_dF,
+                               float *d_V, uint32_t *d_status, md_stream_t stream)
+{
+    if (!bp_list_ok(s, nb) || !d_r || !d_dF || !d_V || sys_n < 0) return MD_ERR_INVALID;
+    BpArgs b = bp_plain(s, d_r, nb, sys_n, d_status);
+    b.dF = (const float4 *)d_dF;
+    b.V = d_V;
+    enqueue_bp_jvp(b, (cudaStream_t)stream);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}

@@ -36,6 +36,10 @@ struct PairArgs {
     float eps, alpha;
     // Stillinger-Weber {eps, sigma, a, lambda, gamma, A, B, p, q, cos0, rc, rc2}
     float sw[12];
+    // learned potential: network and per-atom scratch (device pointers)
+    const float *bp_params, *bp_norm;
+    float *bp_G, *bp_dEdG, *bp_Ei;
+    int bp_sys_n;
     // reductions
     double *E_out, *KE_out;
     int series;             // 1: write E_out[ctl[CTL_STEP]] and advance the counter
@@ -58,6 +62,7 @@ void enqueue_pair(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st
 // Force evaluation for any supported potential (pair kernels or SW).
 void enqueue_forces(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st);
 void enqueue_sw(const PairArgs &a, int kick, cudaStream_t st);
+void enqueue_bp_step(const PairArgs &a, int kick, cudaStream_t st);
 int pair_blocks(int N, int tpp);
 // r += eta F (unwrapped) with the displacement check (gradient descent step)
 void enqueue_gd_step(const md_space *s, float *d_r, const float *d_f, const md_nbr *nb, float eta, cudaStream_t st);

@@ -169,6 +169,7 @@ int pair_blocks(int N, int tpp) { return (int)(((long long)N * tpp + 255) / 256)
 void enqueue_forces(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st)
 {
     if (pot == MD_SW) enqueue_sw(a, kick, st);
+    else if (pot == MD_BP) enqueue_bp_step(a, kick, st);
     else enqueue_pair(a, dim, pot, kick, st);
 }
 
@@ -177,8 +178,8 @@ static int g_tpp = 4;
 bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const md_nbr *nb, float *d_f, PairArgs &a)
 {
     if (!s || !p || !d_r || !nb || !d_f || !nb->nbr || !nb->cnt || !nb->ws) return false;
-    if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE && p->kind != MD_SW) return false;
-    if (p->kind == MD_SW && s->dim != 3) return false;
+    if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE && p->kind != MD_SW && p->kind != MD_BP) return false;
+    if ((p->kind == MD_SW || p->kind == MD_BP) && s->dim != 3) return false;
     memset(&a, 0, sizeof(a));
     a.box = make_box(s);
     a.N = nb->N;
@@ -203,6 +204,16 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
     } else if (p->kind == MD_SOFT_SPHERE) {
         a.eps = p->eps;
         a.alpha = p->alpha;
+    } else if (p->kind == MD_BP) {
+        const md_bp_model *m = (const md_bp_model *)p->model;
+        if (!m || !m->params || !m->norm || !m->G || !m->dEdG || !m->Ei) return false;
+        if (nb->r_list < 3.77f) return false;
+        a.bp_params = m->params;
+        a.bp_norm = m->norm;
+        a.bp_G = m->G;
+        a.bp_dEdG = m->dEdG;
+        a.bp_Ei = m->Ei;
+        a.bp_sys_n = m->sys_n;
     } else {
         for (int k = 0; k < 10; ++k) a.sw[k] = p->sw[k];
         float rc = p->sw[2] * p->sw[1];   // a * sigma

@@ -63,6 +63,11 @@ class md_pot(C.Structure):
                 ("e_shift", C.c_float), ("alpha", C.c_float), ("sw", C.c_float * 10), ("model", C.c_void_p)]
 
 
+class md_bp_model(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("norm", C.c_void_p), ("G", C.c_void_p), ("dEdG", C.c_void_p),
+                ("Ei", C.c_void_p), ("sys_n", C.c_int)]
+
+
 _P = C.POINTER
 _vp = C.c_void_p
 _SIGS = {
@@ -80,6 +85,15 @@ _SIGS = {
                               C.c_uint64, C.c_uint32, C.c_int, _P(md_nbr), _vp, _vp, C.c_int, _vp, _vp],
     "md_minimize": [_P(md_space), _P(md_pot), C.c_int, C.c_float, C.c_int, _vp, _vp, _P(md_nbr), _vp, _vp, _vp],
     "md_status_poll": [_vp, _P(C.c_uint32), _vp],
+    "md_bp_descriptors": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp],
+    "md_bp_mlp_infer": [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp],
+    "md_bp_mlp_infer_tc": [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp],
+    "md_bp_set_tensor_cores": [C.c_int],
+    "md_bp_forces": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
+    "md_bp_jvp": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp, _vp],
+    "md_bp_mlp_train": [_vp, _vp, _vp, _vp, _vp, C.c_float, C.c_int, _vp, _vp, _vp],
+    "md_bp_loss_prep": [_vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _vp, _vp, _vp, _vp],
+    "md_adam_step": [_vp, _vp, _vp, _vp, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, _vp],
     "md_minimize_adjoint": [_P(md_space), _P(md_pot), _P(md_nbr), _vp, C.c_int, C.c_float, C.c_float, C.c_float,
                             C.c_float, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
     "md_neighbor_list_build_noalloc": [_P(md_space), _vp, C.c_int, C.c_float, C.c_float, C.c_int, _vp, _vp, _vp,
@@ -91,6 +105,8 @@ for _name, _args in _SIGS.items():
     _f.restype = C.c_int
 _lib.md_launch_count.restype = C.c_uint64
 _lib.md_launch_count.argtypes = []
+_lib.md_bp_train_scratch_size.restype = C.c_size_t
+_lib.md_bp_train_scratch_size.argtypes = [C.c_int]
 _lib.md_adjoint_workspace_size.restype = C.c_size_t
 _lib.md_adjoint_workspace_size.argtypes = [C.c_int, C.c_int, C.c_int]
 _lib.md_noalloc_scratch_bytes.restype = C.c_size_t
@@ -203,6 +219,78 @@ def md_neighbor_list_build_noalloc(space, r, N, r_cut, skin, cap, nbr, cnt, stat
 
 def md_noalloc_scratch_bytes() -> int:
     return int(_lib.md_noalloc_scratch_bytes())
+
+
+# ----------------------------------------------------------------------------
+# Learned potential (Sec. 3.2.4, 4.1)
+# ----------------------------------------------------------------------------
+BP_NPARAMS = 5313
+
+
+def md_bp_descriptors(space, r, nb, sys_n, G, status=None, stream=None):
+    _check(_lib.md_bp_descriptors(C.byref(space), _ptr(r), C.byref(nb), int(sys_n), _ptr(G), _ptr(status),
+                                  _stream(stream)), "md_bp_descriptors")
+
+
+def md_bp_mlp_infer(params, norm, G, N, Ei, dEdG, stream=None):
+    _check(_lib.md_bp_mlp_infer(_ptr(params), _ptr(norm), _ptr(G), int(N), _ptr(Ei), _ptr(dEdG), _stream(stream)),
+           "md_bp_mlp_infer")
+
+
+def md_bp_mlp_infer_tc(params, norm, G, N, Ei, dEdG, status=None, stream=None):
+    _check(_lib.md_bp_mlp_infer_tc(_ptr(params), _ptr(norm), _ptr(G), int(N), _ptr(Ei), _ptr(dEdG), _ptr(status),
+                                   _stream(stream)), "md_bp_mlp_infer_tc")
+
+
+def md_bp_set_tensor_cores(on: bool):
+    _check(_lib.md_bp_set_tensor_cores(int(bool(on))), "md_bp_set_tensor_cores")
+
+
+def md_bp_forces(space, r, nb, sys_n, dEdG, Ei, f, E=None, status=None, stream=None):
+    _check(_lib.md_bp_forces(C.byref(space), _ptr(r), C.byref(nb), int(sys_n), _ptr(dEdG), _ptr(Ei), _ptr(f), _ptr(E),
+                             _ptr(status), _stream(stream)), "md_bp_forces")
+
+
+def md_bp_jvp(space, r, nb, sys_n, dF, V, status=None, stream=None):
+    _check(_lib.md_bp_jvp(C.byref(space), _ptr(r), C.byref(nb), int(sys_n), _ptr(dF), _ptr(V), _ptr(status),
+                          _stream(stream)), "md_bp_jvp")
+
+
+def md_bp_train_scratch_size(N) -> int:
+    return int(_lib.md_bp_train_scratch_size(int(N)))
+
+
+def md_bp_mlp_train(params, norm, G, V, cE, cF, N, scratch, grad, stream=None):
+    _check(_lib.md_bp_mlp_train(_ptr(params), _ptr(norm), _ptr(G), _ptr(V), _ptr(cE), float(cF), int(N),
+                                _ptr(scratch), _ptr(grad), _stream(stream)), "md_bp_mlp_train")
+
+
+def md_bp_loss_prep(Ei, F, Fref, Eref, S, n, wF, cE, dF, loss, stream=None):
+    _check(_lib.md_bp_loss_prep(_ptr(Ei), _ptr(F), _ptr(Fref), _ptr(Eref), int(S), int(n), float(wF), _ptr(cE),
+                                _ptr(dF), _ptr(loss), _stream(stream)), "md_bp_loss_prep")
+
+
+def md_adam_step(params, grad, m, v, n, lr, beta1, beta2, eps, step, stream=None):
+    _check(_lib.md_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(n), float(lr), float(beta1),
+                             float(beta2), float(eps), int(step), _stream(stream)), "md_adam_step")
+
+
+class BPModel:
+    """Device buffers of a learned potential for N atoms and the md_pot that
+    points at them (kind MD_BP).  params [5313] and norm [32] are FP32 CUDA
+    tensors owned by the caller."""
+
+    def __init__(self, params, norm, N, sys_n=0, device="cuda"):
+        import torch
+        self.params, self.norm = params, norm
+        self.G = torch.zeros((N, 16), dtype=torch.float32, device=device)
+        self.dEdG = torch.zeros((N, 16), dtype=torch.float32, device=device)
+        self.Ei = torch.zeros(N, dtype=torch.float32, device=device)
+        self.model = md_bp_model(_ptr(params).value, _ptr(norm).value, _ptr(self.G).value, _ptr(self.dEdG).value,
+                                 _ptr(self.Ei).value, int(sys_n))
+        self.pot = md_pot()
+        self.pot.kind = MD_BP
+        self.pot.model = C.cast(C.pointer(self.model), C.c_void_p)
 
 
 def md_adjoint_workspace_size(N, T, K) -> int:

@@ -1,0 +1,241 @@
+"""GPU parity: the learned potential (Sec. 3.2.4, 4.1) -- symmetry-function
+descriptors, per-atom network, forces, descriptor JVP and the energy+force
+training gradient (double backward) -- through the C ABI, against the FP64
+autograd oracle."""
+import numpy as np
+import pytest
+
+import oracle.bp as B
+import workloads as W
+from gpu_helpers import dev, force_error, status_word, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SKIN = 0.3
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1912_04232_b300 as P
+    return P
+
+
+def pack(p):
+    return np.concatenate([p["W1"].numpy().ravel(), p["b1"].numpy(), p["W2"].numpy().ravel(), p["b2"].numpy(),
+                           p["w3"].numpy(), np.atleast_1d(p["b3"].numpy())]).astype(np.float32)
+
+
+def f32_params(p):
+    """The oracle's parameters rounded to FP32 (what the GPU sees)."""
+    import torch
+    return {k: torch.as_tensor(v.numpy().astype(np.float32).astype(np.float64)) for k, v in p.items()}
+
+
+def _col_err(a, ref):
+    """Largest error per descriptor column relative to that column's scale
+    (floored at 1e-3 of the largest column scale, for near-empty columns)."""
+    scale = np.abs(ref).max(axis=0)
+    scale = np.maximum(scale, 1e-3 * scale.max())
+    return float((np.abs(a - ref) / scale).max())
+
+
+def _norm(G):
+    mu = G.mean(0).astype(np.float32)
+    sd = (G.std(0) + 0.05).astype(np.float32)
+    return mu, sd
+
+
+def _snapshot(n_side=2, seed=0, jitter=0.25):
+    si = W.sw_silicon(n_side, T_K=0, jitter=jitter, seed=seed)
+    return si.r, si.L
+
+
+def _list(P, r, L, cap=48):
+    import torch
+    s = P.md_space_periodic(3, [L] * 3)
+    nl = P.NeighborList(s, r.shape[0], B.R_C, SKIN, cap)
+    rd = to_dev(r, torch.float32)
+    st = status_word()
+    nl.build(rd, st)
+    return s, nl, rd, st
+
+
+def _oracle_G(r, L):
+    import torch
+    x = np.asarray(r, np.float64)[:, :3]
+    return B.descriptors(torch.tensor(x), L, *B.triplets(*B.pairs_within(x, L), len(x))).numpy()
+
+
+@pytest.mark.parametrize("n_side,seed", [(2, 0), (4, 1)])
+def test_descriptors_match_oracle(P, n_side, seed):
+    import torch
+    r, L = _snapshot(n_side, seed)
+    s, nl, rd, st = _list(P, r, L)
+    G = torch.zeros((r.shape[0], 16), dtype=torch.float32, device=dev())
+    P.md_bp_descriptors(s, rd, nl.plan, 0, G, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    Go = _oracle_G(r, L)
+    assert _col_err(G.cpu().numpy(), Go) <= 2e-5
+
+
+def _model(P, r, L, seed=0):
+    import torch
+    p = B.init_params(seed)
+    G = _oracle_G(r, L)
+    mu, sd = _norm(G)
+    params = to_dev(pack(p), torch.float32)
+    norm = to_dev(np.concatenate([mu, sd]), torch.float32)
+    return p, mu, sd, params, norm
+
+
+@pytest.mark.parametrize("n_side,seed", [(2, 2), (4, 3)])
+def test_network_energy_and_forces_match_oracle(P, n_side, seed):
+    import torch
+    r, L = _snapshot(n_side, seed)
+    s, nl, rd, st = _list(P, r, L)
+    p, mu, sd, params, norm = _model(P, r, L, seed)
+    m = P.BPModel(params, norm, r.shape[0])
+    f = torch.zeros((r.shape[0], 4), dtype=torch.float32, device=dev())
+    E = torch.zeros(1, dtype=torch.float64, device=dev())
+    P.md_energy_forces(s, m.pot, rd, nl.plan, f, E, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    t64 = lambda a: __import__("torch").as_tensor(a.astype(np.float64))
+    Eo, Fo, Eio, _ = B.energy_forces(r, L, f32_params(p), t64(mu), t64(sd))
+    assert force_error(f.cpu().numpy(), Fo) <= 1e-4
+    np.testing.assert_allclose(m.Ei.cpu().numpy(), Eio, rtol=0, atol=1e-5 * np.abs(Eio).max())
+    assert abs(E.item() - Eo) <= 1e-5 * abs(Eo)
+
+
+def test_descriptor_jvp_matches_oracle(P):
+    import torch
+    r, L = _snapshot(2, 4)
+    s, nl, rd, st = _list(P, r, L)
+    rng = np.random.default_rng(0)
+    dF = np.zeros((r.shape[0], 4), np.float32)
+    dF[:, :3] = rng.normal(size=(r.shape[0], 3))
+    V = torch.zeros((r.shape[0], 16), dtype=torch.float32, device=dev())
+    P.md_bp_jvp(s, rd, nl.plan, 0, to_dev(dF), V, st)
+    torch.cuda.synchronize()
+    x = torch.tensor(np.asarray(r, np.float64)[:, :3])
+    graph = B.triplets(*B.pairs_within(x.numpy(), L), len(x))
+    _, Vo = torch.autograd.functional.jvp(lambda y: B.descriptors(y, L, *graph), x,
+                                          torch.tensor(dF[:, :3].astype(np.float64)))
+    Vo = Vo.numpy()
+    assert _col_err(V.cpu().numpy(), Vo) <= 1e-4
+
+
+def test_training_gradient_matches_oracle_double_backward(P):
+    import torch
+    S, n_side = 2, 2
+    snaps = [_snapshot(n_side, 10 + k) for k in range(S)]
+    L = snaps[0][1]
+    n = snaps[0][0].shape[0]
+    p, mu, sd, params, norm = _model(P, snaps[0][0], L, seed=5)
+    # references: the SW energies/forces of each snapshot (oracle)
+    import oracle as O
+    refs = [O.sw(r, L) for r, _ in snaps]
+    rs = np.concatenate([r for r, _ in snaps]).astype(np.float32)
+    N = S * n
+    # one neighbor list per snapshot, local indices, concatenated rows
+    s = P.md_space_periodic(3, [L] * 3)
+    plan = P.md_nbr_plan(s, n, B.R_C, SKIN, 48)
+    nbr = torch.zeros((N, 48), dtype=torch.int32, device=dev())
+    cnt = torch.zeros(N, dtype=torch.int32, device=dev())
+    rref = torch.zeros((N, 4), dtype=torch.float32, device=dev())
+    ws = torch.empty(int(plan.ws_bytes) + 256, dtype=torch.uint8, device=dev())
+    wsv = ws[(-ws.data_ptr()) % 256:][: int(plan.ws_bytes)]
+    rd = to_dev(rs, torch.float32)
+    st = status_word()
+    for k in range(S):
+        sl = slice(k * n, (k + 1) * n)
+        P.md_nbr_bind(plan, nbr[sl], cnt[sl], rref[sl], wsv)
+        P.md_neighbor_list_build(s, rd[sl], plan, st)
+    comb = P.md_nbr.from_buffer_copy(plan)
+    comb.N = N
+    comb.nbr, comb.cnt, comb.rref = nbr.data_ptr(), cnt.data_ptr(), rref.data_ptr()
+    G = torch.zeros((N, 16), dtype=torch.float32, device=dev())
+    Ei = torch.zeros(N, dtype=torch.float32, device=dev())
+    dEdG = torch.zeros((N, 16), dtype=torch.float32, device=dev())
+    F = torch.zeros((N, 4), dtype=torch.float32, device=dev())
+    Fref = np.zeros((N, 4), np.float32)
+    Fref[:, :3] = np.concatenate([rf[1] for rf in refs])
+    Eref = np.array([rf[0] for rf in refs])
+    cE = torch.zeros(N, dtype=torch.float32, device=dev())
+    dF = torch.zeros((N, 4), dtype=torch.float32, device=dev())
+    loss = torch.zeros(2 * S, dtype=torch.float64, device=dev())
+    V = torch.zeros((N, 16), dtype=torch.float32, device=dev())
+    scratch = torch.empty(P.md_bp_train_scratch_size(N), dtype=torch.uint8, device=dev())
+    grad = torch.zeros(P.BP_NPARAMS, dtype=torch.float32, device=dev())
+    wF = 0.7
+    P.md_bp_descriptors(s, rd, comb, n, G, st)
+    P.md_bp_mlp_infer(params, norm, G, N, Ei, dEdG)
+    P.md_bp_forces(s, rd, comb, n, dEdG, Ei, F, None, st)
+    P.md_bp_loss_prep(Ei, F, to_dev(Fref), to_dev(Eref), S, n, wF, cE, dF, loss)
+    P.md_bp_jvp(s, rd, comb, n, dF, V, st)
+    P.md_bp_mlp_train(params, norm, G, V, cE, 1.0, N, scratch, grad)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    t64 = lambda a: torch.as_tensor(np.asarray(a, np.float64))
+    batch = [(r, L, rf[0], rf[1]) for (r, _), rf in zip(snaps, refs)]
+    lo, go = B.loss_and_grads(batch, f32_params(p), t64(mu), t64(sd), w_F=wF)
+    assert abs(loss.sum().item() - lo) <= 1e-4 * lo
+    g_gpu = grad.cpu().numpy().astype(np.float64)
+    g_o = np.concatenate([go[k].numpy().ravel() for k in ("W1", "b1", "W2", "b2", "w3")] + [np.atleast_1d(go["b3"].numpy())])
+    rel = np.linalg.norm(g_gpu - g_o) / np.linalg.norm(g_o)
+    cos = g_gpu @ g_o / (np.linalg.norm(g_gpu) * np.linalg.norm(g_o))
+    assert rel <= 1e-3 and cos >= 0.99999, (rel, cos)
+
+
+@pytest.mark.parametrize("N", [1037, 64000])
+def test_tensor_core_network_matches_fp32_network(P, N):
+    # tcgen05 BF16 MMAs (FP32 accumulate) vs the FP32 CUDA-core network on
+    # the same inputs; BF16 rounds inputs, weights and hidden activations to
+    # 8 significant bits, so agreement is to about 1e-2 of each output's scale
+    import torch
+    rng = np.random.default_rng(N)
+    p = B.init_params(7)
+    G = rng.normal(size=(N, 16)).astype(np.float32) * 0.5 + 1.0
+    mu, sd = _norm(G)
+    params = to_dev(pack(p), torch.float32)
+    norm = to_dev(np.concatenate([mu, sd]), torch.float32)
+    Gd = to_dev(G, torch.float32)
+    E32 = torch.zeros(N, dtype=torch.float32, device=dev())
+    D32 = torch.zeros((N, 16), dtype=torch.float32, device=dev())
+    Etc = torch.zeros(N, dtype=torch.float32, device=dev())
+    Dtc = torch.zeros((N, 16), dtype=torch.float32, device=dev())
+    st = status_word()
+    P.md_bp_mlp_infer(params, norm, Gd, N, E32, D32)
+    P.md_bp_mlp_infer_tc(params, norm, Gd, N, Etc, Dtc, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    e32, etc = E32.cpu().numpy(), Etc.cpu().numpy()
+    d32, dtc = D32.cpu().numpy(), Dtc.cpu().numpy()
+    assert np.abs(etc - e32).max() <= 2e-2 * np.abs(e32).max()
+    assert _col_err(dtc, d32) <= 3e-2
+    # and it is really computing: correlation with the FP32 result
+    assert np.corrcoef(etc, e32)[0, 1] > 0.999
+
+
+def test_tensor_core_forces_match_oracle(P):
+    import torch
+    r, L = _snapshot(4, 8)
+    s, nl, rd, st = _list(P, r, L)
+    p, mu, sd, params, norm = _model(P, r, L, 8)
+    m = P.BPModel(params, norm, r.shape[0])
+    f = torch.zeros((r.shape[0], 4), dtype=torch.float32, device=dev())
+    E = torch.zeros(1, dtype=torch.float64, device=dev())
+    P.md_bp_set_tensor_cores(True)
+    try:
+        P.md_energy_forces(s, m.pot, rd, nl.plan, f, E, st)
+        torch.cuda.synchronize()
+    finally:
+        P.md_bp_set_tensor_cores(False)
+    assert P.md_status_poll(st) == 0
+    t64 = lambda a: torch.as_tensor(a.astype(np.float64))
+    Eo, Fo, Eio, _ = B.energy_forces(r, L, f32_params(p), t64(mu), t64(sd))
+    assert force_error(f.cpu().numpy(), Fo) <= 3e-2
+    # the total is a cancelling sum of per-atom terms: judge it on their scale
+    np.testing.assert_allclose(m.Ei.cpu().numpy(), Eio, rtol=0, atol=2e-2 * np.abs(Eio).max())
+    assert abs(E.item() - Eo) <= 1e-2 * np.abs(Eio).sum()
