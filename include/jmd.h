@@ -297,6 +297,10 @@ JMD_API md_status md_bp_loss_prep(const float *d_Ei, const float *d_F, const flo
                                   int S, int n, float wF, float *d_cE, float *d_dF, double *d_loss,
                                   md_stream_t stream);
 
+/* Column means then standard deviations of X [N][D] into d_out [2 D] (FP64
+ * accumulation): the descriptor normalisation of the network. */
+JMD_API md_status md_column_stats(const float *d_X, int N, int D, float *d_out, md_stream_t stream);
+
 /* Adam (bias-corrected) on an FP32 vector; step counts from 1. */
 JMD_API md_status md_adam_step(float *d_params, const float *d_grad, float *d_m, float *d_v, int n, float lr,
                                float beta1, float beta2, float eps, int step, md_stream_t stream);

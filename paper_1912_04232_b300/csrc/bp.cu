@@ -502,7 +502,7 @@ extern "C" md_status md_bp_forces(const md_space *s, const float *d_r, const md_
     b.pa.ctl = w.ctl;
     b.pa.partials = w.partials;
     b.pa.status = d_status;
-    if (bp_grid(nb->N) > w.max_blocks) return MD_ERR_INVALID;
+    if (d_E && bp_grid(nb->N) > w.max_blocks) return MD_ERR_INVALID;   // reduction partials
     enqueue_bp_force(b, 0, (cudaStream_t)stream);
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;

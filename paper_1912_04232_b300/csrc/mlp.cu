@@ -341,6 +341,31 @@ __global__ void __launch_bounds__(256) k_bp_loss_prep(const float *Ei, const flo
     }
 }
 
+// Column mean and standard deviation of X [N][D] (FP64, fixed order): one
+// block per column.
+__global__ void __launch_bounds__(256) k_column_stats(const float *X, int N, int D, float *out)
+{
+    count_launch();
+    __shared__ double sh[32];
+    const int c = blockIdx.x;
+    double s = 0.0, s2 = 0.0;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        double v = X[(size_t)k * D + c];
+        s += v;
+        s2 += v * v;
+    }
+    s = block_sum_f64(s, sh);
+    __shared__ double mean;
+    if (threadIdx.x == 0) mean = s / N;
+    __syncthreads();
+    s2 = block_sum_f64(s2, sh);
+    if (threadIdx.x == 0) {
+        double var = s2 / N - mean * mean;
+        out[c] = (float)mean;
+        out[D + c] = (float)sqrt(var > 0.0 ? var : 0.0);
+    }
+}
+
 static int mlp_grid(int N)
 {
     static int sms = 0;
@@ -407,6 +432,14 @@ extern "C" md_status md_bp_loss_prep(const float *d_Ei, const float *d_F, const 
     if (!d_Ei || !d_F || !d_Fref || !d_Eref || !d_cE || !d_dF || !d_loss || S < 1 || n < 1) return MD_ERR_INVALID;
     k_bp_loss_prep<<<S, 256, 0, (cudaStream_t)stream>>>(d_Ei, (const float4 *)d_F, (const float4 *)d_Fref, d_Eref, S,
                                                         n, wF, d_cE, (float4 *)d_dF, d_loss);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+extern "C" md_status md_column_stats(const float *d_X, int N, int D, float *d_out, md_stream_t stream)
+{
+    if (!d_X || !d_out || N < 1 || D < 1) return MD_ERR_INVALID;
+    k_column_stats<<<D, 256, 0, (cudaStream_t)stream>>>(d_X, N, D, d_out);
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
 }

@@ -93,6 +93,7 @@ _SIGS = {
     "md_bp_jvp": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp, _vp],
     "md_bp_mlp_train": [_vp, _vp, _vp, _vp, _vp, C.c_float, C.c_int, _vp, _vp, _vp],
     "md_bp_loss_prep": [_vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _vp, _vp, _vp, _vp],
+    "md_column_stats": [_vp, C.c_int, C.c_int, _vp, _vp],
     "md_adam_step": [_vp, _vp, _vp, _vp, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, _vp],
     "md_minimize_adjoint": [_P(md_space), _P(md_pot), _P(md_nbr), _vp, C.c_int, C.c_float, C.c_float, C.c_float,
                             C.c_float, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -268,6 +269,10 @@ def md_bp_mlp_train(params, norm, G, V, cE, cF, N, scratch, grad, stream=None):
 def md_bp_loss_prep(Ei, F, Fref, Eref, S, n, wF, cE, dF, loss, stream=None):
     _check(_lib.md_bp_loss_prep(_ptr(Ei), _ptr(F), _ptr(Fref), _ptr(Eref), int(S), int(n), float(wF), _ptr(cE),
                                 _ptr(dF), _ptr(loss), _stream(stream)), "md_bp_loss_prep")
+
+
+def md_column_stats(X, N, D, out, stream=None):
+    _check(_lib.md_column_stats(_ptr(X), int(N), int(D), _ptr(out), _stream(stream)), "md_column_stats")
 
 
 def md_adam_step(params, grad, m, v, n, lr, beta1, beta2, eps, step, stream=None):

@@ -1,0 +1,271 @@
+"""Learned potential workflow (Sec. 4.1): data from the plain Stillinger-
+Weber simulator, training of the Behler-Parrinello network with the energy +
+force loss, evaluation, and deployment in MD.
+
+Every arithmetic step runs in libjmd kernels (Langevin/NVE integrators, SW
+and learned forces, descriptors, network forward / double backward, loss
+bookkeeping, Adam, statistics).  This module only sequences those calls and
+owns the device buffers (torch tensors as storage).
+
+Units: eV, Angstrom, fs; masses in eV fs^2 / A^2 (amu x 103.6427).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import jmd as J
+
+SW_SI = (2.1683, 2.0951, 1.80, 21.0, 1.20, 7.049556277, 0.6022245584, 4.0, 0.0, -1.0 / 3.0)
+SW_RC = SW_SI[2] * SW_SI[1]
+MASS_SI = 28.0855 * 103.6427
+KB = 8.617333262e-5
+BP_RC = 3.77
+SKIN = 0.3
+CAP = 48
+N_PARAMS = 5313
+
+
+def _t():
+    import torch
+    return torch
+
+
+@dataclass
+class Dataset:
+    r: "object"        # [S, n, 4] float32 (device)
+    F: "object"        # [S, n, 4] float32 SW forces
+    E: "object"        # [S] float64 SW energies
+    T: np.ndarray      # temperature of each snapshot
+    L: float
+    n: int
+    nbr: "object" = None   # [S*n, CAP] int32, rows local to each snapshot
+    cnt: "object" = None   # [S*n] int32
+    plan: "object" = None  # md_nbr for one snapshot (box, cap)
+    ws: "object" = None
+
+
+def generate_sw_dataset(temps, n_snap, stride=20, equil=2000, n_side=4, a=5.431, gamma=0.01, dt=1.0, seed=0,
+                        device="cuda"):
+    """SW silicon (8 n_side^3 atoms, diamond start) under BAOAB Langevin at
+    each temperature; a snapshot (positions, SW forces and energy) every
+    `stride` steps after `equil` steps."""
+    torch = _t()
+    import workloads as W
+    S = len(temps) * n_snap
+    si0 = W.sw_silicon(n_side, a=a, T_K=0.0)
+    n, L = si0.N, si0.L
+    space = J.md_space_periodic(3, [L] * 3)
+    pot = J.sw_pot(SW_SI)
+    R = torch.zeros((S, n, 4), dtype=torch.float32, device=device)
+    F = torch.zeros((S, n, 4), dtype=torch.float32, device=device)
+    E = torch.zeros(S, dtype=torch.float64, device=device)
+    Ts = np.zeros(S)
+    st = torch.zeros(1, dtype=torch.int32, device=device)
+    k = 0
+    for ti, T in enumerate(temps):
+        si = W.sw_silicon(n_side, a=a, T_K=T, seed=seed * 1000 + ti)
+        nl = J.NeighborList(space, n, SW_RC, 0.5, 64, device=device)
+        r = torch.from_numpy(si.r).to(device)
+        v = torch.from_numpy(si.v).to(device)
+        f = torch.zeros_like(r)
+        pe = torch.zeros(max(stride, equil), dtype=torch.float64, device=device)
+        nl.build(r, st)
+        J.md_energy_forces(space, pot, r, nl.plan, f, None, st)
+        kT = KB * T
+        step = 0
+        J.md_integrate_langevin(space, pot, r, v, f, MASS_SI, dt, gamma, kT, seed * 7919 + ti, step, equil,
+                                nl.plan, pe, None, True, st)
+        step += equil
+        for s in range(n_snap):
+            J.md_integrate_langevin(space, pot, r, v, f, MASS_SI, dt, gamma, kT, seed * 7919 + ti, step, stride,
+                                    nl.plan, pe, None, True, st)
+            step += stride
+            R[k].copy_(r)
+            F[k].copy_(f)
+            E[k:k + 1].copy_(pe[stride - 1:stride])
+            Ts[k] = T
+            k += 1
+    code = J.md_status_poll(st)
+    if code:
+        raise J.MDError(code, "generate_sw_dataset")
+    # store in a seeded random order so contiguous index ranges mix temperatures
+    perm = np.random.default_rng(seed).permutation(S)
+    pt = torch.as_tensor(perm, device=device)
+    return Dataset(r=R[pt].contiguous(), F=F[pt].contiguous(), E=E[pt].contiguous(), T=Ts[perm], L=L, n=n)
+
+
+def build_lists(ds: Dataset, device="cuda"):
+    """One neighbor list (r_list = 3.77 + 0.3 A) per snapshot, rows local to
+    the snapshot, concatenated."""
+    torch = _t()
+    S, n = ds.r.shape[0], ds.n
+    space = J.md_space_periodic(3, [ds.L] * 3)
+    plan = J.md_nbr_plan(space, n, BP_RC, SKIN, CAP)
+    nbr = torch.zeros((S * n, CAP), dtype=torch.int32, device=device)
+    cnt = torch.zeros(S * n, dtype=torch.int32, device=device)
+    rref = torch.zeros((S * n, 4), dtype=torch.float32, device=device)
+    ws = torch.empty(int(plan.ws_bytes) + 256, dtype=torch.uint8, device=device)
+    wsv = ws[(-ws.data_ptr()) % 256:][: int(plan.ws_bytes)]
+    st = torch.zeros(1, dtype=torch.int32, device=device)
+    rflat = ds.r.reshape(S * n, 4)
+    for k in range(S):
+        sl = slice(k * n, (k + 1) * n)
+        J.md_nbr_bind(plan, nbr[sl], cnt[sl], rref[sl], wsv)
+        J.md_neighbor_list_build(space, rflat[sl], plan, st)
+    code = J.md_status_poll(st)
+    if code:
+        raise J.MDError(code, "build_lists")
+    ds.nbr, ds.cnt, ds.plan, ds.ws = nbr, cnt, plan, (ws, wsv)
+    return ds
+
+
+def _batch_list(ds: Dataset, s0: int, S: int):
+    """md_nbr view of snapshots [s0, s0 + S) as one concatenated system."""
+    nb = J.md_nbr.from_buffer_copy(ds.plan)
+    n = ds.n
+    nb.N = S * n
+    nb.nbr = ds.nbr[s0 * n:(s0 + S) * n].data_ptr()
+    nb.cnt = ds.cnt[s0 * n:(s0 + S) * n].data_ptr()
+    nb.ws = ds.ws[1].data_ptr()
+    return nb
+
+
+class Trainer:
+    """Adam on the FP32 packed parameters; batches of contiguous snapshots."""
+
+    def __init__(self, ds: Dataset, batch=16, lr=1e-3, wF=1.0, seed=0, device="cuda", params=None,
+                 init_bias=True):
+        torch = _t()
+        self.ds, self.B, self.lr, self.wF = ds, batch, lr, wF
+        n = ds.n
+        N = batch * n
+        g = torch.Generator().manual_seed(seed)
+        if params is None:
+            p = torch.zeros(N_PARAMS, dtype=torch.float32)
+            p[0:1024] = torch.randn(1024, generator=g) / 4.0
+            p[1088:5184] = torch.randn(4096, generator=g) / 8.0
+            p[5248:5312] = torch.randn(64, generator=g) / 8.0
+            params = p.to(device)
+        self.params = params
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.grad = torch.zeros_like(params)
+        self.space = J.md_space_periodic(3, [ds.L] * 3)
+        self.G = torch.zeros((N, 16), dtype=torch.float32, device=device)
+        self.Ei = torch.zeros(N, dtype=torch.float32, device=device)
+        self.dEdG = torch.zeros((N, 16), dtype=torch.float32, device=device)
+        self.Fp = torch.zeros((N, 4), dtype=torch.float32, device=device)
+        self.cE = torch.zeros(N, dtype=torch.float32, device=device)
+        self.dF = torch.zeros((N, 4), dtype=torch.float32, device=device)
+        self.V = torch.zeros((N, 16), dtype=torch.float32, device=device)
+        self.loss = torch.zeros(2 * batch, dtype=torch.float64, device=device)
+        self.scratch = torch.empty(J.md_bp_train_scratch_size(N), dtype=torch.uint8, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.step_count = 0
+        self.norm = self._normalisation(device)
+        if init_bias:
+            # output bias: mean energy per atom of the data (kernel statistics)
+            stats = torch.zeros(2, dtype=torch.float32, device=device)
+            e32 = (ds.E / ds.n).float().contiguous()
+            J.md_column_stats(e32, ds.E.shape[0], 1, stats)
+            self.params[5312:5313].copy_(stats[0:1])
+
+    def _normalisation(self, device):
+        """Descriptor mean / std over (up to) 64 snapshots."""
+        torch = _t()
+        ds = self.ds
+        S = min(64, ds.r.shape[0])
+        N = S * ds.n
+        G = torch.zeros((N, 16), dtype=torch.float32, device=device)
+        nb = _batch_list(ds, 0, S)
+        J.md_bp_descriptors(self.space, ds.r[:S].reshape(N, 4), nb, ds.n, G, self.status)
+        norm = torch.zeros(32, dtype=torch.float32, device=device)
+        J.md_column_stats(G, N, 16, norm)
+        norm[16:] += 1e-3   # floor the spread of nearly constant descriptors
+        return norm
+
+    def forward(self, s0, S):
+        ds, n = self.ds, self.ds.n
+        N = S * n
+        nb = _batch_list(ds, s0, S)
+        r = ds.r[s0:s0 + S].reshape(N, 4)
+        J.md_bp_descriptors(self.space, r, nb, n, self.G[:N], self.status)
+        J.md_bp_mlp_infer(self.params, self.norm, self.G[:N], N, self.Ei[:N], self.dEdG[:N])
+        J.md_bp_forces(self.space, r, nb, n, self.dEdG[:N], self.Ei[:N], self.Fp[:N], None, self.status)
+        J.md_bp_loss_prep(self.Ei[:N], self.Fp[:N], ds.F[s0:s0 + S].reshape(N, 4), ds.E[s0:s0 + S], S, n, self.wF,
+                          self.cE[:N], self.dF[:N], self.loss[:2 * S])
+        return nb, r, N
+
+    def step(self, s0):
+        n = self.ds.n
+        nb, r, N = self.forward(s0, self.B)
+        J.md_bp_jvp(self.space, r, nb, n, self.dF[:N], self.V[:N], self.status)
+        J.md_bp_mlp_train(self.params, self.norm, self.G[:N], self.V[:N], self.cE[:N], 1.0, N, self.scratch,
+                          self.grad)
+        self.step_count += 1
+        J.md_adam_step(self.params, self.grad, self.m, self.v, N_PARAMS, self.lr, 0.9, 0.999, 1e-8,
+                       self.step_count)
+
+    def train(self, idx_lo, idx_hi, epochs, seed=0, lr_end=None):
+        """Epochs over contiguous batches of snapshots [idx_lo, idx_hi),
+        batch order shuffled each epoch; cosine learning-rate decay."""
+        rng = np.random.default_rng(seed)
+        starts = np.arange(idx_lo, idx_hi - self.B + 1, self.B)
+        total = epochs * len(starts)
+        lr0 = self.lr
+        k = 0
+        for _ in range(epochs):
+            for s0 in rng.permutation(starts):
+                if lr_end is not None:
+                    self.lr = lr_end + 0.5 * (lr0 - lr_end) * (1 + math.cos(math.pi * k / max(1, total)))
+                self.step(int(s0))
+                k += 1
+        self.lr = lr0
+
+    def evaluate(self, idx_lo, idx_hi):
+        """(energy RMSE per atom [eV/atom], force RMSE [eV/A]) over snapshots
+        [idx_lo, idx_hi), from the loss kernel's per-snapshot terms."""
+        e2 = f2 = 0.0
+        cnt = 0
+        wF = self.wF
+        self.wF = 1.0
+        for s0 in range(idx_lo, idx_hi, self.B):
+            S = min(self.B, idx_hi - s0)
+            self.forward(s0, S)
+            l = self.loss[:2 * S].cpu().numpy()
+            e2 += l[0::2].sum() * S
+            f2 += l[1::2].sum() * S
+            cnt += S
+        self.wF = wF
+        code = J.md_status_poll(self.status)
+        if code:
+            raise J.MDError(code, "evaluate")
+        return math.sqrt(e2 / cnt), math.sqrt(f2 / cnt)
+
+
+def force_rmse_sw2body(ds: Dataset, idx_lo, idx_hi, device="cuda"):
+    """RMSE of the SW two-body forces alone (lambda = 0) against full SW,
+    through the loss kernel (force term only)."""
+    torch = _t()
+    p = list(SW_SI)
+    p[3] = 0.0
+    pot = J.sw_pot(p)
+    n = ds.n
+    space = J.md_space_periodic(3, [ds.L] * 3)
+    nl = J.NeighborList(space, n, SW_RC, 0.3, 64, device=device)
+    st = torch.zeros(1, dtype=torch.int32, device=device)
+    f = torch.zeros((n, 4), dtype=torch.float32, device=device)
+    zeros = torch.zeros(n, dtype=torch.float32, device=device)
+    cE = torch.zeros(n, dtype=torch.float32, device=device)
+    dF = torch.zeros((n, 4), dtype=torch.float32, device=device)
+    loss = torch.zeros(2, dtype=torch.float64, device=device)
+    f2 = 0.0
+    for k in range(idx_lo, idx_hi):
+        nl.build(ds.r[k], st)
+        J.md_energy_forces(space, pot, ds.r[k], nl.plan, f, None, st)
+        J.md_bp_loss_prep(zeros, f, ds.F[k], ds.E[k:k + 1], 1, n, 1.0, cE, dF, loss)
+        f2 += loss[1].item()
+    return math.sqrt(f2 / (idx_hi - idx_lo))
