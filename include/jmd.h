@@ -327,6 +327,63 @@ JMD_API md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_nbr
                                       void *d_ws, double *d_out, uint32_t *d_status, md_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batched replicas (the paper's vmap over independent systems, Sec. 4.2):   */
+/* replicas of different size, box, density and potential (LJ or soft        */
+/* spheres, 3-D) concatenated particle-wise and advanced by the same kernels */
+/* -- one CUDA graph launch for a whole NVE run.                             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int N;            /* particles */
+    double L;         /* cubic box edge */
+    int kind;         /* MD_LJ or MD_SOFT_SPHERE */
+    float eps, sigma, r_cut, e_shift;   /* LJ (as md_pot); soft: eps, r_cut = max diameter */
+    float alpha;      /* soft-sphere exponent */
+    float skin, dt, mass;
+} md_replica_desc;
+
+typedef struct {
+    int R, N, cap;        /* replicas, total particles, neighbor slots per row */
+    int ncell_total;      /* cells of all replicas plus one end sentinel each */
+    int tpp;              /* threads per particle of the force kernel (4, 8, 16) */
+    size_t ws_bytes;      /* scratch the caller provides */
+    int32_t *nbr;         /* [N][cap] rows with global particle indices */
+    int32_t *cnt;         /* [N] */
+    float *rref;          /* [N][4] */
+    void *ws;             /* ws_bytes (256-byte aligned) */
+    void *host;           /* library-owned host state; release with md_batch_free */
+} md_batch;
+
+/* Plan R replicas (reps[k] describes replica k; particles of replica k are
+ * the next reps[k].N rows of the concatenated arrays).  Each replica's box
+ * must hold twice its r_cut + skin (MD_ERR_BOX_TOO_SMALL otherwise). */
+JMD_API md_status md_batch_plan(const md_replica_desc *reps, int R, int cap, md_batch *out);
+JMD_API void md_batch_free(md_batch *bt);
+/* Attach caller memory and upload the replica tables (synchronous). */
+JMD_API md_status md_batch_bind(md_batch *bt, int32_t *d_nbr, int32_t *d_cnt, float *d_rref, void *d_ws,
+                                md_stream_t stream);
+/* Build every replica's neighbor rows from d_r [N][4]. */
+JMD_API md_status md_batch_build(md_batch *bt, const float *d_r, uint32_t *d_status, md_stream_t stream);
+/* Forces (w = per-particle energy) of every replica into d_f. */
+JMD_API md_status md_batch_forces(md_batch *bt, const float *d_r, float *d_f, uint32_t *d_status, md_stream_t stream);
+/* nsteps of velocity-Verlet NVE for every replica with its own dt, mass and
+ * rebuild decisions (a replica rebuilds only when one of its particles
+ * moved more than skin/2).  d_PE / d_KE (R x nsteps doubles, may be NULL):
+ * per-replica FP64 energies after each step; v.w receives each particle's
+ * kinetic energy.  Arithmetic per particle equals the single-system path
+ * with md_set_pair_tpp(tpp), so each replica matches its own md_integrate_nve
+ * run bit for bit.  use_graph: one graph launch with device loop control. */
+JMD_API md_status md_batch_run_nve(md_batch *bt, float *d_r, float *d_v, float *d_f, int nsteps, double *d_PE,
+                                   double *d_KE, int use_graph, uint32_t *d_status, md_stream_t stream);
+/* Builds per replica since bind (synchronous). */
+JMD_API md_status md_batch_stats(const md_batch *bt, uint32_t *h_builds, md_stream_t stream);
+/* Pick the fastest threads-per-particle (4, 8, 16) by timing `probe` graph
+ * steps of each on the caller's state (restored afterwards; d_scratch holds
+ * 2 N float4); cached as JSON in cache_path (may be NULL) keyed by the
+ * replica sizes and kinds.  Synchronous. */
+JMD_API md_status md_batch_autotune(md_batch *bt, float *d_r, float *d_v, float *d_f, void *d_scratch, int probe,
+                                    const char *cache_path, int *tpp_out, md_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Status and accounting                                                     */
 /* ------------------------------------------------------------------------ */
 /* Synchronous: copies *d_status to *h_status after `stream` drains. */
@@ -335,6 +392,12 @@ JMD_API md_status md_status_poll(const uint32_t *d_status, uint32_t *h_status, m
 /* Number of this library's kernels that have run in this process (graph
  * launches count every kernel node they ran).  Synchronizes the device. */
 JMD_API uint64_t md_launch_count(void);
+
+/* A single-thread device wait on *d_flag (nonzero ends it) bounded by
+ * `limit` polls (at most 2^24, about 100 ns apart): on running out it ORs
+ * MD_ERR_TIMEOUT into *d_status and returns, leaving the context usable.
+ * The same bounded-wait rule guards every device wait in the library. */
+JMD_API md_status md_bounded_wait(const uint32_t *d_flag, uint64_t limit, uint32_t *d_status, md_stream_t stream);
 
 /* Library version string. */
 JMD_API const char *md_version(void);

@@ -50,3 +50,28 @@ extern "C" uint64_t md_launch_count(void)
 }
 
 extern "C" const char *md_version(void) { return "jmd-b300 0.1 (sm_103a)"; }
+
+// Bounded device wait: spin on *flag until it becomes nonzero or `limit`
+// polls have passed; on running out, raise MD_ERR_TIMEOUT and return.  The
+// library's waits (tensor-core MMA completion) follow the same rule; this
+// entry point lets a test exercise the timeout path on a flag nothing sets.
+__global__ void k_bounded_wait(const volatile uint32_t *flag, unsigned long long limit, uint32_t *status)
+{
+    count_launch();
+    unsigned long long it = 0;
+    while (*flag == 0u) {
+        if (++it > limit) {
+            raise_status(status, MD_ERR_TIMEOUT);
+            return;
+        }
+        __nanosleep(100);
+    }
+}
+
+extern "C" md_status md_bounded_wait(const uint32_t *d_flag, uint64_t limit, uint32_t *d_status, md_stream_t stream)
+{
+    if (!d_flag || !d_status || limit > (1ull << 24)) return MD_ERR_INVALID;
+    k_bounded_wait<<<1, 1, 0, (cudaStream_t)stream>>>(d_flag, (unsigned long long)limit, d_status);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}

@@ -42,6 +42,8 @@ __global__ void __launch_bounds__(256) k_bin_count(NbrArgs a)
     int c = -1;
     if (act) {
         float4 p = a.r[i];
+        // a non-finite coordinate would silently drop out of every pair test
+        if (!isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z)) raise_status(a.status, MD_ERR_NONFINITE);
         int cx = cell_axis(p.x, a.box.L[0], a.box.Linv[0], a.cell_scale[0], a.nc[0]);
         int cy = cell_axis(p.y, a.box.L[1], a.box.Linv[1], a.cell_scale[1], a.nc[1]);
         int cz = a.dim == 3 ? cell_axis(p.z, a.box.L[2], a.box.Linv[2], a.cell_scale[2], a.nc[2]) : 0;

@@ -68,6 +68,18 @@ class md_bp_model(C.Structure):
                 ("Ei", C.c_void_p), ("sys_n", C.c_int)]
 
 
+class md_replica_desc(C.Structure):
+    _fields_ = [("N", C.c_int), ("L", C.c_double), ("kind", C.c_int), ("eps", C.c_float), ("sigma", C.c_float),
+                ("r_cut", C.c_float), ("e_shift", C.c_float), ("alpha", C.c_float), ("skin", C.c_float),
+                ("dt", C.c_float), ("mass", C.c_float)]
+
+
+class md_batch(C.Structure):
+    _fields_ = [("R", C.c_int), ("N", C.c_int), ("cap", C.c_int), ("ncell_total", C.c_int), ("tpp", C.c_int),
+                ("ws_bytes", C.c_size_t), ("nbr", C.c_void_p), ("cnt", C.c_void_p), ("rref", C.c_void_p),
+                ("ws", C.c_void_p), ("host", C.c_void_p)]
+
+
 _P = C.POINTER
 _vp = C.c_void_p
 _SIGS = {
@@ -85,6 +97,7 @@ _SIGS = {
                               C.c_uint64, C.c_uint32, C.c_int, _P(md_nbr), _vp, _vp, C.c_int, _vp, _vp],
     "md_minimize": [_P(md_space), _P(md_pot), C.c_int, C.c_float, C.c_int, _vp, _vp, _P(md_nbr), _vp, _vp, _vp],
     "md_status_poll": [_vp, _P(C.c_uint32), _vp],
+    "md_bounded_wait": [_vp, C.c_uint64, _vp, _vp],
     "md_bp_descriptors": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp],
     "md_bp_mlp_infer": [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp],
     "md_bp_mlp_infer_tc": [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp],
@@ -95,6 +108,13 @@ _SIGS = {
     "md_bp_loss_prep": [_vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _vp, _vp, _vp, _vp],
     "md_column_stats": [_vp, C.c_int, C.c_int, _vp, _vp],
     "md_adam_step": [_vp, _vp, _vp, _vp, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, _vp],
+    "md_batch_plan": [_P(md_replica_desc), C.c_int, C.c_int, _P(md_batch)],
+    "md_batch_bind": [_P(md_batch), _vp, _vp, _vp, _vp, _vp],
+    "md_batch_build": [_P(md_batch), _vp, _vp, _vp],
+    "md_batch_forces": [_P(md_batch), _vp, _vp, _vp, _vp],
+    "md_batch_run_nve": [_P(md_batch), _vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp, _vp],
+    "md_batch_stats": [_P(md_batch), _P(C.c_uint32), _vp],
+    "md_batch_autotune": [_P(md_batch), _vp, _vp, _vp, _vp, C.c_int, C.c_char_p, _P(C.c_int), _vp],
     "md_minimize_adjoint": [_P(md_space), _P(md_pot), _P(md_nbr), _vp, C.c_int, C.c_float, C.c_float, C.c_float,
                             C.c_float, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
     "md_neighbor_list_build_noalloc": [_P(md_space), _vp, C.c_int, C.c_float, C.c_float, C.c_int, _vp, _vp, _vp,
@@ -108,6 +128,8 @@ _lib.md_launch_count.restype = C.c_uint64
 _lib.md_launch_count.argtypes = []
 _lib.md_bp_train_scratch_size.restype = C.c_size_t
 _lib.md_bp_train_scratch_size.argtypes = [C.c_int]
+_lib.md_batch_free.restype = None
+_lib.md_batch_free.argtypes = [_P(md_batch)]
 _lib.md_adjoint_workspace_size.restype = C.c_size_t
 _lib.md_adjoint_workspace_size.argtypes = [C.c_int, C.c_int, C.c_int]
 _lib.md_noalloc_scratch_bytes.restype = C.c_size_t
@@ -298,6 +320,74 @@ class BPModel:
         self.pot.model = C.cast(C.pointer(self.model), C.c_void_p)
 
 
+# ----------------------------------------------------------------------------
+# Batched replicas (Sec. 4.2 vmap over systems)
+# ----------------------------------------------------------------------------
+def md_batch_plan(descs, cap) -> md_batch:
+    arr = (md_replica_desc * len(descs))(*descs)
+    out = md_batch()
+    _check(_lib.md_batch_plan(arr, len(descs), int(cap), C.byref(out)), "md_batch_plan")
+    return out
+
+
+def md_batch_free(bt):
+    _lib.md_batch_free(C.byref(bt))
+
+
+def md_batch_bind(bt, nbr, cnt, rref, ws, stream=None):
+    _check(_lib.md_batch_bind(C.byref(bt), _ptr(nbr), _ptr(cnt), _ptr(rref), _ptr(ws), _stream(stream)),
+           "md_batch_bind")
+
+
+def md_batch_build(bt, r, status=None, stream=None):
+    _check(_lib.md_batch_build(C.byref(bt), _ptr(r), _ptr(status), _stream(stream)), "md_batch_build")
+
+
+def md_batch_forces(bt, r, f, status=None, stream=None):
+    _check(_lib.md_batch_forces(C.byref(bt), _ptr(r), _ptr(f), _ptr(status), _stream(stream)), "md_batch_forces")
+
+
+def md_batch_run_nve(bt, r, v, f, nsteps, PE=None, KE=None, use_graph=True, status=None, stream=None):
+    _check(_lib.md_batch_run_nve(C.byref(bt), _ptr(r), _ptr(v), _ptr(f), int(nsteps), _ptr(PE), _ptr(KE),
+                                 int(bool(use_graph)), _ptr(status), _stream(stream)), "md_batch_run_nve")
+
+
+def md_batch_stats(bt, stream=None):
+    h = (C.c_uint32 * bt.R)()
+    _check(_lib.md_batch_stats(C.byref(bt), h, _stream(stream)), "md_batch_stats")
+    return list(h)
+
+
+def md_batch_autotune(bt, r, v, f, scratch, probe, cache_path=None, stream=None) -> int:
+    t = C.c_int()
+    _check(_lib.md_batch_autotune(C.byref(bt), _ptr(r), _ptr(v), _ptr(f), _ptr(scratch), int(probe),
+                                  cache_path.encode() if cache_path else None, C.byref(t), _stream(stream)),
+           "md_batch_autotune")
+    return t.value
+
+
+class Batch:
+    """Plans, allocates (torch storage) and binds a replica batch."""
+
+    def __init__(self, descs, cap=128, device="cuda", stream=None):
+        import torch
+        self.plan = md_batch_plan(descs, cap)
+        N = self.plan.N
+        self.nbr = torch.zeros((N, cap), dtype=torch.int32, device=device)
+        self.cnt = torch.zeros(N, dtype=torch.int32, device=device)
+        self.rref = torch.zeros((N, 4), dtype=torch.float32, device=device)
+        self.ws = torch.empty(int(self.plan.ws_bytes) + 256, dtype=torch.uint8, device=device)
+        off = (-self.ws.data_ptr()) % 256
+        self.ws_view = self.ws[off: off + int(self.plan.ws_bytes)]
+        md_batch_bind(self.plan, self.nbr, self.cnt, self.rref, self.ws_view, stream)
+
+    def __del__(self):
+        try:
+            md_batch_free(self.plan)
+        except Exception:
+            pass
+
+
 def md_adjoint_workspace_size(N, T, K) -> int:
     return int(_lib.md_adjoint_workspace_size(int(N), int(T), int(K)))
 
@@ -312,6 +402,10 @@ def md_status_poll(status, stream=None) -> int:
     h = C.c_uint32()
     _check(_lib.md_status_poll(_ptr(status), C.byref(h), _stream(stream)), "md_status_poll")
     return h.value
+
+
+def md_bounded_wait(flag, limit, status, stream=None):
+    _check(_lib.md_bounded_wait(_ptr(flag), int(limit), _ptr(status), _stream(stream)), "md_bounded_wait")
 
 
 def md_launch_count() -> int:

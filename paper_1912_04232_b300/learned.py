@@ -269,3 +269,62 @@ def force_rmse_sw2body(ds: Dataset, idx_lo, idx_hi, device="cuda"):
         J.md_bp_loss_prep(zeros, f, ds.F[k], ds.E[k:k + 1], 1, n, 1.0, cE, dF, loss)
         f2 += loss[1].item()
     return math.sqrt(f2 / (idx_hi - idx_lo))
+
+
+def deploy_compare(params, norm, n_side=20, T=1000.0, steps=200, warmup=20, dt=1.0, seed=0, device="cuda"):
+    """NVE of an n_side^3-cell diamond (8 n_side^3 atoms) at temperature T
+    with plain SW and with the learned potential (tensor-core network and
+    FP32 network).  Returns particle-steps/s of each and the learned force
+    RMSE against SW on the starting and final configurations."""
+    torch = _t()
+    import workloads as W
+    si = W.sw_silicon(n_side, T_K=T, seed=seed)
+    N, L = si.N, si.L
+    space = J.md_space_periodic(3, [L] * 3)
+    st = torch.zeros(1, dtype=torch.int32, device=device)
+    out = {"N": N, "T_K": T, "steps": steps, "dt_fs": dt}
+    model = J.BPModel(params, norm, N, device=device)
+    sw = J.sw_pot(SW_SI)
+    n = N
+    zeros = torch.zeros(n, dtype=torch.float32, device=device)
+    cE = torch.zeros(n, dtype=torch.float32, device=device)
+    dF = torch.zeros((n, 4), dtype=torch.float32, device=device)
+    loss = torch.zeros(2, dtype=torch.float64, device=device)
+    Edummy = torch.zeros(1, dtype=torch.float64, device=device)
+
+    def rmse(r, nl):
+        fs = torch.zeros((n, 4), dtype=torch.float32, device=device)
+        fb = torch.zeros((n, 4), dtype=torch.float32, device=device)
+        J.md_energy_forces(space, sw, r, nl.plan, fs, None, st)
+        J.md_energy_forces(space, model.pot, r, nl.plan, fb, None, st)
+        J.md_bp_loss_prep(zeros, fb, fs, Edummy, 1, n, 1.0, cE, dF, loss)
+        return math.sqrt(loss[1].item())
+
+    for name, pot, tc in (("sw", sw, False), ("learned_tc", model.pot, True), ("learned_fp32", model.pot, False)):
+        J.md_bp_set_tensor_cores(tc)
+        nl = J.NeighborList(space, N, SW_RC, 0.3, 64, device=device)
+        r = torch.from_numpy(si.r).to(device)
+        v = torch.from_numpy(si.v).to(device)
+        f = torch.zeros_like(r)
+        nl.build(r, st)
+        J.md_energy_forces(space, pot, r, nl.plan, f, None, st)
+        J.md_integrate_nve(space, pot, r, v, f, MASS_SI, dt, warmup, nl.plan, None, None, True, st)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        J.md_integrate_nve(space, pot, r, v, f, MASS_SI, dt, steps, nl.plan, None, None, True, st)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name + "_particle_steps_per_s"] = N * steps / (ms * 1e-3)
+        if name == "learned_tc":
+            out["force_rmse_vs_sw_final_eV_per_A"] = rmse(r, nl)
+    J.md_bp_set_tensor_cores(False)
+    r0 = torch.from_numpy(si.r).to(device)
+    nl = J.NeighborList(space, N, SW_RC, 0.3, 64, device=device)
+    nl.build(r0, st)
+    out["force_rmse_vs_sw_start_eV_per_A"] = rmse(r0, nl)
+    code = J.md_status_poll(st)
+    if code:
+        raise J.MDError(code, "deploy_compare")
+    return out

@@ -40,3 +40,16 @@ def test_trained_network_beats_two_body_and_untrained(trained):
           % (fr, trained["untrained"][1], trained["two_body"], trained["trained"][0]))
     assert fr * 5.0 <= trained["untrained"][1]
     assert fr * 5.0 <= trained["two_body"]
+
+
+def test_deploy_at_64000_atoms(trained):
+    # the trained network in NVE at N = 64,000 (20^3 diamond cells, 1000 K)
+    # beside plain SW: both run, the learned forces stay close to SW
+    import paper_1912_04232_b300.learned as LP
+    tr = trained["trainer"]
+    out = LP.deploy_compare(tr.params, tr.norm, n_side=20, T=1000.0, steps=100, warmup=10)
+    print(out)
+    assert out["N"] == 64000
+    assert out["sw_particle_steps_per_s"] > 0 and out["learned_tc_particle_steps_per_s"] > 0
+    assert out["force_rmse_vs_sw_start_eV_per_A"] < 3 * trained["trained"][1] + 0.05
+    assert out["force_rmse_vs_sw_final_eV_per_A"] < 3 * trained["trained"][1] + 0.1

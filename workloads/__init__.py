@@ -26,7 +26,7 @@ __all__ = [
     "f32", "box_for_density", "sc_lattice", "fcc_lattice", "diamond_lattice",
     "jitter_wrap", "thermal_velocities", "LJFluid", "lj_fluid",
     "Packing2D", "packing_2d", "packing_box", "SWSilicon", "sw_silicon",
-    "ReplicaSpec", "replica_plan", "uniform_box_positions",
+    "ReplicaSpec", "replica_plan", "replica_initial", "uniform_box_positions",
 ]
 
 
@@ -236,6 +236,28 @@ def replica_plan(R: int = 512, n_max: int = 8192, seed: int = 0,
         out.append(ReplicaSpec(kind=kind, N=N, rho=rho, L=box_for_density(N, rho, 3),
                                seed=seed * 100003 + k, dt=0.005 if kind == "lj" else 0.01))
     return out
+
+
+def replica_initial(spec: ReplicaSpec, T: float = 1.0):
+    """Starting state of one replica: LJ replicas take N sites, chosen
+    uniformly at random, of the smallest FCC lattice (4 m^3 sites, m =
+    ceil((N/4)^(1/3))) filling the box, jittered by 0.05 sigma (sites stay at
+    least about 1 sigma apart at the densities used); soft-sphere replicas are uniform random with diameters 1.0 / 1.4 (50/50)
+    in the w column (they are meant to be relaxed before dynamics).  Gaussian
+    velocities at T with zero net momentum.  Returns (r [N,4], v [N,4])."""
+    rng = np.random.Generator(np.random.PCG64(spec.seed))
+    L = spec.L
+    if spec.kind == "lj":
+        m = int(math.ceil((spec.N / 4.0) ** (1.0 / 3.0) - 1e-9))
+        sites = fcc_lattice(m, L)
+        keep = np.sort(rng.choice(sites.shape[0], size=spec.N, replace=False))
+        r = _to4(jitter_wrap(sites[keep], L, 0.05, rng))
+    else:
+        r = _to4(uniform_box_positions(spec.N, L, 3, rng))
+        d = np.where(np.arange(spec.N) % 2 == 0, 1.0, 1.4).astype(np.float32)
+        r[:, 3] = d
+    v = _to4(thermal_velocities(spec.N, 3, T, 1.0, rng))
+    return r, v
 
 
 def uniform_box_positions(N: int, L: float, dim: int, rng: np.random.Generator) -> np.ndarray:
