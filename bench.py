@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tpp", type=int, default=0)
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel from the host (profiling)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain-SW section")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-replica section")
     return ap.parse_args()
 
 
@@ -143,6 +145,128 @@ def run_reference(args, rank):
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def learned_section():
+    """Train the BP network on GPU-generated SW data, then run NVE at
+    N = 64,000 atoms with plain SW and with the learned potential."""
+    import paper_1912_04232_b300.learned as LP
+    temps = np.linspace(500.0, 3000.0, 8)
+    t0 = time.perf_counter()
+    ds = LP.generate_sw_dataset(temps, n_snap=30, stride=20, equil=300, seed=1)
+    LP.build_lists(ds)
+    S = ds.r.shape[0]
+    ntr = int(0.8 * S)
+    tr = LP.Trainer(ds, batch=8, lr=3e-3, wF=1.0, seed=0)
+    tr.train(0, ntr, epochs=40, seed=0, lr_end=1e-4)
+    e_rmse, f_rmse = tr.evaluate(ntr, S)
+    two = LP.force_rmse_sw2body(ds, ntr, S)
+    t_train = time.perf_counter() - t0
+    dep = LP.deploy_compare(tr.params, tr.norm, n_side=20, T=1000.0, steps=200, warmup=20)
+    return {
+        "sw_particle_steps_per_s": dep["sw_particle_steps_per_s"],
+        "learned_particle_steps_per_s": dep["learned_tc_particle_steps_per_s"],
+        "learned_fp32_particle_steps_per_s": dep["learned_fp32_particle_steps_per_s"],
+        "learned_over_sw": dep["learned_tc_particle_steps_per_s"] / dep["sw_particle_steps_per_s"],
+        "force_rmse_eV_per_A_heldout": f_rmse, "energy_rmse_eV_per_atom_heldout": e_rmse,
+        "force_rmse_sw_two_body_only": two, "force_rmse_vs_sw_at_deploy": dep["force_rmse_vs_sw_final_eV_per_A"],
+        "deploy": {"N": dep["N"], "T_K": 1000.0, "steps": 200, "dt_fs": 1.0, "network": "tcgen05 BF16"},
+        "train": {"snapshots": int(S), "heldout": int(S - ntr), "epochs": 40, "seconds_incl_data": t_train},
+    }
+
+
+def batched_section(steps=500):
+    """512 LJ / soft-sphere replicas (N log-uniform in [64, 8192]) for
+    `steps` NVE steps in one graph launch, against one launch per replica."""
+    import torch
+    import paper_1912_04232_b300 as P
+    import workloads as W
+    dev = torch.device("cuda")
+    specs = W.replica_plan(R=512, n_max=8192, seed=0)
+    states = []
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    for sp in specs:
+        r, v = W.replica_initial(sp)
+        if sp.kind == "soft":
+            s = P.md_space_periodic(3, [sp.L] * 3)
+            nl = P.NeighborList(s, sp.N, 1.4, 0.3, 128)
+            rd = torch.from_numpy(r).to(dev)
+            f = torch.zeros_like(rd)
+            nl.build(rd, st)
+            P.md_minimize(s, P.soft_pot(), 0, 0.05, 50, rd, f, nl.plan, None, st)
+            x = rd.cpu().numpy()
+            x[:, :3] = np.mod(x[:, :3], np.float32(sp.L)).astype(np.float32)
+            x[:, :3][x[:, :3] >= np.float32(sp.L)] = 0.0
+            r = x
+        states.append((r, v))
+
+    def desc(sp):
+        d = P.md_replica_desc()
+        d.N, d.L = sp.N, sp.L
+        if sp.kind == "lj":
+            pot = P.lj_pot()
+            d.kind, d.eps, d.sigma, d.r_cut, d.e_shift = P.MD_LJ, pot.eps, pot.sigma, pot.r_cut, pot.e_shift
+        else:
+            d.kind, d.eps, d.alpha, d.r_cut = P.MD_SOFT_SPHERE, 1.0, 2.0, 1.4
+        d.skin, d.dt, d.mass = 0.3, sp.dt, 1.0
+        return d
+
+    b = P.Batch([desc(sp) for sp in specs], cap=128)
+    r0 = torch.from_numpy(np.concatenate([s[0] for s in states])).to(dev)
+    v0 = torch.from_numpy(np.concatenate([s[1] for s in states])).to(dev)
+    r, v, f = r0.clone(), v0.clone(), torch.zeros_like(r0)
+    scratch = torch.empty((2 * b.plan.N, 4), dtype=torch.float32, device=dev)
+    import tempfile
+    tpp = P.md_batch_autotune(b.plan, r, v, f, scratch, 20, os.path.join(tempfile.gettempdir(), "jmd_batch_tune.json"))
+
+    def run_batch():
+        r.copy_(r0)
+        v.copy_(v0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.md_batch_build(b.plan, r, st)
+        P.md_batch_forces(b.plan, r, f, st)
+        P.md_batch_run_nve(b.plan, r, v, f, steps, None, None, True, st)
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    run_batch()
+    ms_b = min(run_batch() for _ in range(3))
+    # one launch (graph) per replica, same tuning
+    P.md_set_pair_tpp(tpp)
+    singles = []
+    for sp, (rr, vv) in zip(specs, states):
+        s = P.md_space_periodic(3, [sp.L] * 3)
+        nl = P.NeighborList(s, sp.N, 2.5 if sp.kind == "lj" else 1.4, 0.3, 128)
+        rd, vd = torch.from_numpy(rr).to(dev), torch.from_numpy(vv).to(dev)
+        singles.append((s, nl, rd, vd, torch.zeros_like(rd), rd.clone(), vd.clone(), sp))
+
+    def run_singles():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s, nl, rd, vd, f1, ri, vi, sp in singles:
+            rd.copy_(ri)
+            vd.copy_(vi)
+            pot = P.lj_pot() if sp.kind == "lj" else P.soft_pot()
+            nl.build(rd, st)
+            P.md_energy_forces(s, pot, rd, nl.plan, f1, None, st)
+            P.md_integrate_nve(s, pot, rd, vd, f1, 1.0, sp.dt, steps, nl.plan, None, None, True, st)
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    run_singles()
+    ms_s = run_singles()
+    P.md_set_pair_tpp(4)
+    code = P.md_status_poll(st)
+    Ntot = int(b.plan.N)
+    return {"replicas": len(specs), "N_total": Ntot, "steps": steps, "tpp_autotuned": tpp,
+            "one_launch_particle_steps_per_s": Ntot * steps / (ms_b * 1e-3),
+            "per_replica_launches_particle_steps_per_s": Ntot * steps / (ms_s * 1e-3),
+            "speedup": ms_s / ms_b, "status": code}
 
 
 def _source_sha():
@@ -308,6 +432,12 @@ def main():
     except (OSError, ValueError):
         pass
 
+    extra = {}
+    if rank == 0 and not args.no_learned:
+        extra["learned_vs_sw"] = learned_section()
+    if rank == 0 and not args.no_batch:
+        extra["batched"] = batched_section()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -317,7 +447,7 @@ def main():
                        "md_steps_per_step": md_steps, "density": 0.84, "T": 1.0, "r_cut": c.r_cut, "skin": c.skin,
                        "dt": c.dt, "neighbor_cap": nl.cap, "rebuilds_per_step": builds / args.steps,
                        "max_energy_drift_per_particle": drift, "l2": "flushed between bench steps",
-                       "parallelism": f"replicas{world}", "pair_tpp": args.tpp or 8,
+                       "parallelism": f"replicas{world}", "pair_tpp": args.tpp or 4,
                        "loop": "host launches" if args.no_graph else "one CUDA graph (device WHILE/IF)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": "k_pair<LJ> (md_energy_forces)",
@@ -328,6 +458,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
