@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tpp", type=int, default=0)
+    ap.add_argument("--pair-opt", type=int, default=-1, help="pair-kernel variant (md_set_pair_options)")
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel from the host (profiling)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain-SW section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-replica section")
@@ -310,6 +311,8 @@ def main():
     stream = torch.cuda.current_stream()
     if args.tpp:
         P.md_set_pair_tpp(args.tpp)
+    if args.pair_opt >= 0:
+        P.md_set_pair_options(args.pair_opt)
     s = P.md_space_periodic(3, [c.L] * 3)
     nl = P.NeighborList(s, c.N, c.r_cut, c.skin, 128)
     pot = P.lj_pot(c.eps, c.sigma, c.r_cut, True)

@@ -199,7 +199,8 @@ typedef struct {
 
 /* Forces and per-particle energies into d_f [N][4]; if d_E != NULL the FP64
  * total energy sum_i e_i is written to *d_E (device).  Needs a built list
- * with r_list >= the potential's range. */
+ * with r_list >= the potential's range and positions inside the box [0, L)
+ * (as the integrators keep them; md_minimize accepts unwrapped ones). */
 JMD_API md_status md_energy_forces(const md_space *s, const md_pot *p, const float *d_r, const md_nbr *nb,
                                    float *d_f, double *d_E, uint32_t *d_status, md_stream_t stream);
 
@@ -207,6 +208,12 @@ JMD_API md_status md_energy_forces(const md_space *s, const md_pot *p, const flo
  * group that gathers one row.  A tuning knob; results are identical up to
  * FP32 summation order. */
 JMD_API md_status md_set_pair_tpp(int tpp);
+
+/* Pair-kernel variant (a tuning knob; every variant gives the same bits):
+ * bit 0 = read neighbor rows past L1, bit 1 = skip the wrap arithmetic for
+ * particles at least r_list + skin from every face.  Default 1 (measured
+ * fastest on B300: the interior path diverges within warps). */
+JMD_API md_status md_set_pair_options(int opt);
 
 /* ------------------------------------------------------------------------ */
 /* Dynamics (Sec. 3.3.1).                                                   */

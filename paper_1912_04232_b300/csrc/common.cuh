@@ -70,6 +70,33 @@ __device__ __forceinline__ float dist2_rn(const float4 &a, const float4 &b, cons
     return r2;
 }
 
+// Squared distance for a particle whose every list partner is its unwrapped
+// image (the particle lies at least r_list + skin from each face): then
+// rint(t * Linv) = 0 and the nearest-image formula above reduces to d = t
+// exactly, so the same bits come out without the wrap arithmetic.
+template <int DIM>
+__device__ __forceinline__ float dist2_inner(const float4 &a, const float4 &b, float &dx, float &dy, float &dz)
+{
+    dx = __fsub_rn(a.x, b.x);
+    dy = __fsub_rn(a.y, b.y);
+    float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    if (DIM == 3) {
+        dz = __fsub_rn(a.z, b.z);
+        r2 = __fadd_rn(r2, __fmul_rn(dz, dz));
+    } else {
+        dz = 0.0f;
+    }
+    return r2;
+}
+
+// Row entries streamed past L1 (L1 is left to the gathered positions).
+__device__ __forceinline__ int ld_stream(const int32_t *p)
+{
+    int v;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 // Wrap a coordinate into [0, L): x - L floor(x Linv), folded once more if
 // rounding left it on the boundary.
 __device__ __forceinline__ float wrap_coord(float x, float L, float Linv)

@@ -352,6 +352,7 @@ static md_status run_dynamics(const md_space *s, const md_pot *p, float *d_r, fl
     c.half_skin2 = nb->half_skin2;
     c.ctl = ws_ptrs(nb).ctl;
     c.na = make_nbr_args(s, d_r, nb, d_status, 1);
+    c.na.wrapped = 1;   // the kick-drift kernels keep positions inside the box
     c.ncell_total = nb->ncell_total;
     if (!make_pair_args(s, p, d_r, nb, d_f, c.pa)) return MD_ERR_INVALID;
     c.pa.v = (float4 *)d_v;
@@ -402,6 +403,7 @@ extern "C" md_status md_minimize(const md_space *s, const md_pot *p, int kind, f
     cudaStream_t st = (cudaStream_t)stream;
     PairArgs pa;
     if (!make_pair_args(s, p, d_r, nb, d_f, pa)) return MD_ERR_INVALID;
+    pa.margin = 1e30f;   // unwrapped coordinates: always the full nearest-image formula
     pa.E_out = d_E;
     pa.series = d_E ? 1 : 0;
     pa.status = d_status;

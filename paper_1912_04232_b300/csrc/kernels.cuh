@@ -19,11 +19,14 @@ struct NbrArgs {
     uint32_t *status;
     int gated;       // 1: run only if ctl[CTL_REBUILD] != 0
     int canonical;   // 1: sort every row ascending after the build
+    int wrapped;     // 1: positions are inside [0, L) (integrators), enabling the wrap-free path
 };
 
 struct PairArgs {
     Box box;
     int N, cap, tpp;
+    float margin;           // r_list + skin: particles this far from every face skip the wrap
+    int opt;                // kernel variant: bit 0 stream rows past L1, bit 1 interior fast path
     const float4 *r;
     const int32_t *nbr, *cnt;
     float4 *f;

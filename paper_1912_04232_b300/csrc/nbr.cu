@@ -246,10 +246,10 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
 {
     count_launch();
     if (!chain_active(a)) return;
-    __shared__ int cidx[BUILD_CMAX];
     __shared__ int sidx[BUILD_CMAX];
     __shared__ float4 cpos[BUILD_CMAX];
     __shared__ float4 spos[BUILD_CMAX];
+    __shared__ int bmax;
     __shared__ int soff[28];        // prefix of the stencil cells' counts
     __shared__ int scell[27];
     __shared__ int sbeg[27];
@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
     const int tid = threadIdx.x;
     const int own_b = a.ws.cell_start[q], own_e = a.ws.cell_start[q + 1];
     if (own_e == own_b) return;   // uniform: empty cell
+    if (tid == 0) bmax = 0;
     if (tid < 32) {
         // stencil cells and their counts, one lane each, prefix by shuffles
         int cx = q % a.nc[0];
@@ -304,29 +305,44 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
         }
         return;
     }
-    // stage candidates (all slots in parallel)
-    for (int slot = tid; slot < M; slot += blockDim.x) {
-        int m = 0;
-        while (soff[m + 1] <= slot) ++m;
-        int src = sbeg[m] + (slot - soff[m]);
-        cidx[slot] = a.ws.atoms[src];
-        cpos[slot] = a.ws.rsorted[src];
+    // stage candidates in canonical order: warp w takes stencil cells
+    // w, w + 8, ...; its lanes load the cell's members and rank them by
+    // particle index with shuffles (cells hold at most 32 per pass)
+    {
+        const int w = tid >> 5, ln = tid & 31;
+        for (int m = w; m < nst; m += BUILD_WARPS) {
+            const int b0 = soff[m], n = soff[m + 1] - b0, src = sbeg[m];
+            for (int base = 0; base < n; base += 32) {
+                // members [base, base + 32) are ranked against the whole cell
+                int k = base + ln;
+                int me = k < n ? a.ws.atoms[src + k] : 0x7fffffff;
+                float4 pos = k < n ? a.ws.rsorted[src + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                int rank = 0;
+                for (int c0 = 0; c0 < n; c0 += 32) {
+                    int other = (c0 + ln < n) ? a.ws.atoms[src + c0 + ln] : 0x7fffffff;
+#pragma unroll 8
+                    for (int t = 0; t < 32; ++t) rank += (__shfl_sync(0xffffffffu, other, t) < me);
+                }
+                if (k < n) {
+                    sidx[b0 + rank] = me;
+                    spos[b0 + rank] = pos;
+                }
+            }
+        }
     }
     __syncthreads();
-    // canonical order: rank inside the candidate's own cell by index
-    for (int slot = tid; slot < M; slot += blockDim.x) {
-        int m = 0;
-        while (soff[m + 1] <= slot) ++m;
-        const int b0 = soff[m], e0 = soff[m + 1];
-        const int me = cidx[slot];
-        int rank = 0;
-        for (int k = b0; k < e0; ++k) rank += (cidx[k] < me);
-        sidx[b0 + rank] = me;
-        spos[b0 + rank] = cpos[slot];
+    // interior cell (no stencil cell wraps, >= 5 cells per axis): every
+    // candidate is its own nearest image and rint(t Linv) = 0
+    bool inner = a.wrapped != 0;
+    {
+        int lq = q;
+        int cxyz[3] = {lq % a.nc[0], (lq / a.nc[0]) % a.nc[1], lq / (a.nc[0] * a.nc[1])};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) inner = inner && a.nc[d] >= 5 && cxyz[d] >= 1 && cxyz[d] <= a.nc[d] - 2;
     }
-    __syncthreads();
     const int lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
+    int wmax = 0;
     for (int s = own_b + (tid >> 5); s < own_e; s += BUILD_WARPS) {
         int i = a.ws.atoms[s];
         float4 ri = a.ws.rsorted[s];
@@ -339,7 +355,9 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
             if (k < M) {
                 j = sidx[k];
                 float dx, dy, dz;
-                hit = (j != i) && (dist2_rn<DIM>(ri, spos[k], a.box, dx, dy, dz) < a.r_list2);
+                float r2 = inner ? dist2_inner<DIM>(ri, spos[k], dx, dy, dz)
+                                 : dist2_rn<DIM>(ri, spos[k], a.box, dx, dy, dz);
+                hit = (j != i) && (r2 < a.r_list2);
             }
             unsigned mk = __ballot_sync(0xffffffffu, hit);
             int pos = count + __popc(mk & lt);
@@ -352,9 +370,13 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
             a.cnt[i] = count;
             a.rref[i] = ri;
             if (count > a.cap) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
-            atomicMax(&a.ws.ctl[CTL_MAXCNT], (uint32_t)count);
+            wmax = count > wmax ? count : wmax;
         }
     }
+    // one atomic per block for the largest row count (not one per particle)
+    if (lane == 0) atomicMax(&bmax, wmax);
+    __syncthreads();
+    if (tid == 0 && bmax > 0) atomicMax(&a.ws.ctl[CTL_MAXCNT], (uint32_t)bmax);
 }
 
 // Sets the rebuild flag if any particle moved more than skin/2 (minimum

@@ -17,12 +17,13 @@
 namespace jmd {
 
 // One neighbor pair: accumulates F_i and the pair energy into the lane's sums.
-template <int DIM, int POT>
+// INNER: the particle is away from every face (see dist2_inner).
+template <int DIM, int POT, bool INNER = false>
 __device__ __forceinline__ void pair_term(const PairArgs &a, const float4 &ri, const float4 &rj, float &fx, float &fy,
                                           float &fz, float &e)
 {
     float dx, dy, dz;
-    float r2 = dist2_rn<DIM>(ri, rj, a.box, dx, dy, dz);
+    float r2 = INNER ? dist2_inner<DIM>(ri, rj, dx, dy, dz) : dist2_rn<DIM>(ri, rj, a.box, dx, dy, dz);
     if (POT == MD_LJ) {
         if (r2 < a.rc2) {
             float ir2 = __fdividef(1.0f, r2);
@@ -58,10 +59,34 @@ __device__ __forceinline__ void pair_term(const PairArgs &a, const float4 &ri, c
     }
 }
 
+// The lanes of a group take consecutive entries of the row, so one gather
+// instruction touches few cache lines; four entries per lane per trip keep
+// four gathers in flight; row entries bypass L1.
+template <int DIM, int TPP, int POT, bool INNER, bool STREAM>
+__device__ __forceinline__ void pair_loop(const PairArgs &a, int i, int n, const int32_t *row, const float4 &ri,
+                                          int lg, float &fx, float &fy, float &fz, float &e)
+{
+    for (int k0 = lg; k0 < n; k0 += 4 * TPP) {
+        const int k1 = k0 + TPP, k2 = k0 + 2 * TPP, k3 = k0 + 3 * TPP;
+        int j0 = STREAM ? ld_stream(row + k0) : __ldg(row + k0);
+        int j1 = k1 < n ? (STREAM ? ld_stream(row + k1) : __ldg(row + k1)) : i;
+        int j2 = k2 < n ? (STREAM ? ld_stream(row + k2) : __ldg(row + k2)) : i;
+        int j3 = k3 < n ? (STREAM ? ld_stream(row + k3) : __ldg(row + k3)) : i;
+        float4 r0 = __ldg(a.r + j0);
+        float4 r1 = __ldg(a.r + j1);
+        float4 r2 = __ldg(a.r + j2);
+        float4 r3 = __ldg(a.r + j3);
+        pair_term<DIM, POT, INNER>(a, ri, r0, fx, fy, fz, e);
+        if (k1 < n) pair_term<DIM, POT, INNER>(a, ri, r1, fx, fy, fz, e);
+        if (k2 < n) pair_term<DIM, POT, INNER>(a, ri, r2, fx, fy, fz, e);
+        if (k3 < n) pair_term<DIM, POT, INNER>(a, ri, r3, fx, fy, fz, e);
+    }
+}
+
 // Grid-stride over groups of PPB = 256/TPP particles.  Energies accumulate per thread in FP32 over the particles it
 // owns, per warp in FP32, across the block's 8 warps in FP64, and across
 // blocks in FP64 (fixed order, last block).
-template <int DIM, int TPP, int POT, int KICK>
+template <int DIM, int TPP, int POT, int KICK, int OPT>
 __global__ void __launch_bounds__(256) k_pair(PairArgs a)
 {
     count_launch();
@@ -79,24 +104,15 @@ __global__ void __launch_bounds__(256) k_pair(PairArgs a)
             int n = __ldg(a.cnt + i);
             n = n < a.cap ? n : a.cap;
             const int32_t *row = a.nbr + (size_t)i * a.cap;
-            // lanes of a group take consecutive entries of the sorted row, so
-            // one gather instruction touches few cache lines; four entries per
-            // lane per trip keep four gathers in flight
-            for (int k0 = lg; k0 < n; k0 += 4 * TPP) {
-                const int k1 = k0 + TPP, k2 = k0 + 2 * TPP, k3 = k0 + 3 * TPP;
-                int j0 = __ldg(row + k0);
-                int j1 = k1 < n ? __ldg(row + k1) : i;
-                int j2 = k2 < n ? __ldg(row + k2) : i;
-                int j3 = k3 < n ? __ldg(row + k3) : i;
-                float4 r0 = __ldg(a.r + j0);
-                float4 r1 = __ldg(a.r + j1);
-                float4 r2 = __ldg(a.r + j2);
-                float4 r3 = __ldg(a.r + j3);
-                pair_term<DIM, POT>(a, ri, r0, fx, fy, fz, e);
-                if (k1 < n) pair_term<DIM, POT>(a, ri, r1, fx, fy, fz, e);
-                if (k2 < n) pair_term<DIM, POT>(a, ri, r2, fx, fy, fz, e);
-                if (k3 < n) pair_term<DIM, POT>(a, ri, r3, fx, fy, fz, e);
+            // interior particles skip the wrap arithmetic (same bits)
+            bool inner = (OPT & 2) != 0;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                float x = d == 0 ? ri.x : (d == 1 ? ri.y : ri.z);
+                inner = inner && (x >= a.margin) && (x <= a.box.L[d] - a.margin);
             }
+            if (inner) pair_loop<DIM, TPP, POT, true, (OPT & 1) != 0>(a, i, n, row, ri, lg, fx, fy, fz, e);
+            else pair_loop<DIM, TPP, POT, false, (OPT & 1) != 0>(a, i, n, row, ri, lg, fx, fy, fz, e);
         }
 #pragma unroll
         for (int o = TPP / 2; o > 0; o >>= 1) {
@@ -118,7 +134,7 @@ __global__ void __launch_bounds__(256) k_pair(PairArgs a)
 
 // Blocks per launch: enough resident blocks to fill every SM (grid-stride
 // loop inside), never more than there are particle groups.
-template <int DIM, int TPP, int POT, int KICK>
+template <int DIM, int TPP, int POT, int KICK, int OPT>
 static int pair_grid(int N)
 {
     static int per_sm = 0, sms = 0;
@@ -126,7 +142,7 @@ static int pair_grid(int N)
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<DIM, TPP, POT, KICK>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair<DIM, TPP, POT, KICK, OPT>, 256, 0);
         if (per_sm < 1) per_sm = 1;
         if (sms < 1) sms = 1;
     }
@@ -135,10 +151,17 @@ static int pair_grid(int N)
     return groups < g ? groups : g;
 }
 
+static int g_pair_opt = 1;   // bit 0: stream rows past L1; bit 1: interior wrap-free path
+
 template <int DIM, int TPP, int POT, int KICK>
 static void launch_pair_t(const PairArgs &a, cudaStream_t st)
 {
-    k_pair<DIM, TPP, POT, KICK><<<pair_grid<DIM, TPP, POT, KICK>(a.N), 256, 0, st>>>(a);
+    switch (a.opt) {
+    case 0: k_pair<DIM, TPP, POT, KICK, 0><<<pair_grid<DIM, TPP, POT, KICK, 0>(a.N), 256, 0, st>>>(a); break;
+    case 1: k_pair<DIM, TPP, POT, KICK, 1><<<pair_grid<DIM, TPP, POT, KICK, 1>(a.N), 256, 0, st>>>(a); break;
+    case 3: k_pair<DIM, TPP, POT, KICK, 3><<<pair_grid<DIM, TPP, POT, KICK, 3>(a.N), 256, 0, st>>>(a); break;
+    default: k_pair<DIM, TPP, POT, KICK, 2><<<pair_grid<DIM, TPP, POT, KICK, 2>(a.N), 256, 0, st>>>(a); break;
+    }
 }
 
 template <int DIM, int POT, int KICK>
@@ -193,6 +216,9 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
     a.partials = w.partials;
     // canonical lists: one thread sums a particle's pairs in row order
     a.tpp = (nb->flags & MD_NBR_CANONICAL) ? 1 : g_tpp;
+    // beyond this distance from every face all list partners are unwrapped
+    a.margin = nb->r_list + nb->skin;
+    a.opt = g_pair_opt;
     if (p->kind == MD_LJ) {
         if (p->r_cut > nb->r_list) return false;
         float rc = p->r_cut;
@@ -227,6 +253,13 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
 }  // namespace jmd
 
 using namespace jmd;
+
+extern "C" md_status md_set_pair_options(int opt)
+{
+    if (opt < 0 || opt > 3) return MD_ERR_INVALID;
+    g_pair_opt = opt;
+    return MD_OK;
+}
 
 extern "C" md_status md_set_pair_tpp(int tpp)
 {

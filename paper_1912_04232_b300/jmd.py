@@ -91,6 +91,7 @@ _SIGS = {
     "md_nbr_stats": [_P(md_nbr), _P(C.c_int64), _P(C.c_int32), _vp],
     "md_energy_forces": [_P(md_space), _P(md_pot), _vp, _P(md_nbr), _vp, _vp, _vp, _vp],
     "md_set_pair_tpp": [C.c_int],
+    "md_set_pair_options": [C.c_int],
     "md_integrate_nve": [_P(md_space), _P(md_pot), _vp, _vp, _vp, C.c_float, C.c_float, C.c_int, _P(md_nbr),
                          _vp, _vp, C.c_int, _vp, _vp],
     "md_integrate_langevin": [_P(md_space), _P(md_pot), _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float,
@@ -206,6 +207,10 @@ def md_nbr_stats(nb, stream=None):
 def md_energy_forces(space, pot, r, nb, f, E=None, status=None, stream=None):
     _check(_lib.md_energy_forces(C.byref(space), C.byref(pot), _ptr(r), C.byref(nb), _ptr(f), _ptr(E),
                                  _ptr(status), _stream(stream)), "md_energy_forces")
+
+
+def md_set_pair_options(opt: int):
+    _check(_lib.md_set_pair_options(int(opt)), "md_set_pair_options")
 
 
 def md_set_pair_tpp(tpp: int):
