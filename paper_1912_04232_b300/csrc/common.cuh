@@ -196,7 +196,7 @@ __device__ __forceinline__ double block_sum_f64(double v, double *sh)
 // Workspace layout of a neighbor list (all offsets 256-byte aligned).
 // ---------------------------------------------------------------------------
 struct WsLayout {
-    size_t ctl, cell_count, cell_start, cell_of, rank, atoms, rsorted, partials, total;
+    size_t ctl, cell_count, cell_start, cell_of, rank, atoms_u, atoms, rsorted, partials, total;
     int max_blocks;
 };
 
@@ -211,6 +211,7 @@ __host__ inline WsLayout ws_layout(int N, int ncell_total)
     w.cell_start = o;   o = align256(o + sizeof(int32_t) * ((size_t)ncell_total + 1));
     w.cell_of = o;      o = align256(o + sizeof(int32_t) * (size_t)N);
     w.rank = o;         o = align256(o + sizeof(int32_t) * (size_t)N);
+    w.atoms_u = o;      o = align256(o + sizeof(int32_t) * (size_t)N);
     w.atoms = o;        o = align256(o + sizeof(int32_t) * (size_t)N);
     w.rsorted = o;      o = align256(o + sizeof(float4) * (size_t)N);
     w.max_blocks = N / 4 + 64;
@@ -221,7 +222,7 @@ __host__ inline WsLayout ws_layout(int N, int ncell_total)
 
 struct WsPtrs {
     uint32_t *ctl;
-    int32_t *cell_count, *cell_start, *cell_of, *rank, *atoms;
+    int32_t *cell_count, *cell_start, *cell_of, *rank, *atoms_u, *atoms;
     float4 *rsorted;
     double2 *partials;
     int max_blocks;
@@ -237,6 +238,7 @@ __host__ inline WsPtrs ws_ptrs(const md_nbr *nb)
     p.cell_start = (int32_t *)(b + w.cell_start);
     p.cell_of = (int32_t *)(b + w.cell_of);
     p.rank = (int32_t *)(b + w.rank);
+    p.atoms_u = (int32_t *)(b + w.atoms_u);
     p.atoms = (int32_t *)(b + w.atoms);
     p.rsorted = (float4 *)(b + w.rsorted);
     p.partials = (double2 *)(b + w.partials);

@@ -9,11 +9,14 @@
 //                 offset is the particle's rank inside its cell
 //   k_scan      : exclusive scan of the histogram -> cell_start (1 CTA);
 //                 zeroes the histogram for the next build
-//   k_scatter   : counting-sort scatter of indices and a cell-ordered float4
-//                 copy of the positions (coalesced candidate reads)
-//   k_build     : one warp per particle scans the 27 (9 in 2-D) stencil
-//                 cells, compacts hits with ballot into shared memory,
-//                 bitonic-sorts the row and writes it as a padded int32 row
+//   k_scatter   : counting-sort scatter of the particle indices (the order
+//                 inside a cell is the atomics' arrival order)
+//   k_sort_cells: one warp per cell puts its members in ascending particle
+//                 order and writes the cell-ordered float4 positions, so the
+//                 candidate order is fixed once per build
+//   k_build_cells: one CTA per cell stages its stencil's candidates in
+//                 shared memory and sweeps them with ballot compaction into
+//                 padded int32 rows
 #include <cmath>
 
 #include "common.cuh"
@@ -109,8 +112,37 @@ __global__ void __launch_bounds__(256) k_scatter(NbrArgs a)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.N) return;
     int slot = a.ws.cell_start[a.ws.cell_of[i]] + a.ws.rank[i];
-    a.ws.atoms[slot] = i;
-    a.ws.rsorted[slot] = a.r[i];
+    a.ws.atoms_u[slot] = i;
+}
+
+// One warp per cell: rank every member by particle index against the whole
+// cell (shuffles, 32 members per pass) and write the members and their
+// positions in that order.  Every stencil that visits the cell then reads
+// it already in canonical order.
+constexpr int SORT_WARPS = 8;
+__global__ void __launch_bounds__(SORT_WARPS * 32) k_sort_cells(NbrArgs a, int ncell)
+{
+    count_launch();
+    if (!chain_active(a)) return;
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * SORT_WARPS + (threadIdx.x >> 5);
+    if (q >= ncell) return;   // whole warp
+    const int b = a.ws.cell_start[q], n = a.ws.cell_start[q + 1] - b;
+    const int32_t *u = a.ws.atoms_u + b;
+    for (int base = 0; base < n; base += 32) {
+        const int k = base + lane;
+        const int me = k < n ? u[k] : 0x7fffffff;
+        int rk = 0;
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            int other = (c0 + lane < n) ? u[c0 + lane] : 0x7fffffff;
+#pragma unroll 8
+            for (int t = 0; t < 32; ++t) rk += (__shfl_sync(0xffffffffu, other, t) < me);
+        }
+        if (k < n) {
+            a.ws.atoms[b + rk] = me;
+            a.ws.rsorted[b + rk] = a.r[me];
+        }
+    }
 }
 
 // Per-axis stencil cells with duplicates (fewer than 3 cells) removed.
@@ -230,28 +262,66 @@ __device__ void build_row_warp(const NbrArgs &a, int i, int c, int *row)
     __syncwarp();
 }
 
-// One CTA per cell.  The candidates of the cell's (deduplicated) stencil
-// are staged once in shared memory and put in a canonical order: stencil
-// cells in a fixed order (z, y, x offsets ascending), and inside each cell
-// ascending particle index (each candidate's rank is counted against the
-// ~20 members of its own cell).  Each warp then takes particles of the cell
-// and sweeps the ordered candidates 32 at a time; ballot compaction writes
-// hits straight into the output row.  The row order is therefore a
-// deterministic function of the positions and the cell grid, with no
-// per-particle or per-block sort.
-constexpr int BUILD_CMAX = 1024;   // candidates a block stages in shared memory
+// Rows of the particles of one cell from its staged stencil candidates:
+// each warp takes particles of the cell and sweeps the M candidates 32 at a
+// time; ballot compaction writes hits straight into the output row.  INNER:
+// no stencil cell wraps, so rint(t * Linv) = 0 and the plain difference is
+// the nearest-image displacement bit for bit.
 constexpr int BUILD_WARPS = 8;
+template <int DIM, bool INNER>
+__device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *spos, int M, int own_b, int own_e)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int wmax = 0;
+    for (int s = own_b + (threadIdx.x >> 5); s < own_e; s += BUILD_WARPS) {
+        const int i = a.ws.atoms[s];
+        const float4 ri = a.ws.rsorted[s];
+        int32_t *out = a.nbr + (size_t)i * a.cap;
+        int count = 0;
+        for (int k0 = 0; k0 < M; k0 += 32) {
+            const int k = k0 + lane;
+            bool hit = false;
+            int j = 0;
+            if (k < M) {
+                const float4 c = spos[k];
+                j = __float_as_int(c.w);
+                float dx, dy, dz;
+                const float r2 = INNER ? dist2_inner<DIM>(ri, c, dx, dy, dz) : dist2_rn<DIM>(ri, c, a.box, dx, dy, dz);
+                hit = (j != i) && (r2 < a.r_list2);
+            }
+            const unsigned mk = __ballot_sync(0xffffffffu, hit);
+            const int pos = count + __popc(mk & lt);
+            if (hit && pos < a.cap) out[pos] = j;
+            count += __popc(mk);
+        }
+        const int n = count < a.cap ? count : a.cap;
+        for (int k = n + lane; k < a.cap; k += 32) out[k] = a.N;
+        if (lane == 0) {
+            a.cnt[i] = count;
+            a.rref[i] = ri;
+            if (count > a.cap) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+            wmax = count > wmax ? count : wmax;
+        }
+    }
+    return wmax;
+}
+
+// One CTA per cell.  The candidates of the cell's (deduplicated) stencil
+// are copied once into shared memory in canonical order: stencil cells in
+// a fixed order (z, y, x offsets ascending), inside each cell ascending
+// particle index (k_sort_cells has ordered the members), the particle
+// index riding in the w lane.  The row order is therefore a deterministic
+// function of the positions and the cell grid, with no per-row sort.
+constexpr int BUILD_CMAX = 1024;   // candidates a block stages in shared memory
 template <int DIM>
 __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
 {
     count_launch();
     if (!chain_active(a)) return;
-    __shared__ int sidx[BUILD_CMAX];
-    __shared__ float4 cpos[BUILD_CMAX];
     __shared__ float4 spos[BUILD_CMAX];
     __shared__ int bmax;
     __shared__ int soff[28];        // prefix of the stencil cells' counts
-    __shared__ int scell[27];
     __shared__ int sbeg[27];
     __shared__ int nst;
     const int q = blockIdx.x;
@@ -270,12 +340,11 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
         int mz = DIM == 3 ? axis_cells(cz, a.nc[2], sz) : 1;
         if (DIM != 3) sz[0] = 0;
         int m = mx * my * mz;
-        int c = 0, cnt = 0;
+        int cnt = 0;
         if (tid < m) {
             int xx = tid % mx, yy = (tid / mx) % my, zz = tid / (mx * my);
-            c = (sz[zz] * a.nc[1] + sy[yy]) * a.nc[0] + sx[xx];
+            int c = (sz[zz] * a.nc[1] + sy[yy]) * a.nc[0] + sx[xx];
             cnt = a.ws.cell_start[c + 1] - a.ws.cell_start[c];
-            scell[tid] = c;
             sbeg[tid] = a.ws.cell_start[c];
         }
         int incl = cnt;
@@ -294,9 +363,9 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
     const int M = soff[nst];
     if (M > BUILD_CMAX) {
         // dense stencil: per-warp rows with the rows' own sort; the 16 KB
-        // candidate-position array is reused as 8 warp buffers of 512 ints
-        static_assert(sizeof(cpos) >= BUILD_WARPS * 512 * sizeof(int), "row buffers must fit");
-        int *rowbuf = reinterpret_cast<int *>(cpos) + (tid >> 5) * 512;
+        // candidate array is reused as 8 warp buffers of 512 ints
+        static_assert(sizeof(spos) >= BUILD_WARPS * 512 * sizeof(int), "row buffers must fit");
+        int *rowbuf = reinterpret_cast<int *>(spos) + (tid >> 5) * 512;
         for (int s = own_b + (tid >> 5); s < own_e; s += BUILD_WARPS) {
             int i = a.ws.atoms[s];
             if (a.cap <= 128) build_row_warp<DIM, 128>(a, i, q, rowbuf);
@@ -305,76 +374,31 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
         }
         return;
     }
-    // stage candidates in canonical order: warp w takes stencil cells
-    // w, w + 8, ...; its lanes load the cell's members and rank them by
-    // particle index with shuffles (cells hold at most 32 per pass)
+    // staging: warp w copies stencil cells w, w + 8, ...
     {
         const int w = tid >> 5, ln = tid & 31;
         for (int m = w; m < nst; m += BUILD_WARPS) {
             const int b0 = soff[m], n = soff[m + 1] - b0, src = sbeg[m];
-            for (int base = 0; base < n; base += 32) {
-                // members [base, base + 32) are ranked against the whole cell
-                int k = base + ln;
-                int me = k < n ? a.ws.atoms[src + k] : 0x7fffffff;
-                float4 pos = k < n ? a.ws.rsorted[src + k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                int rank = 0;
-                for (int c0 = 0; c0 < n; c0 += 32) {
-                    int other = (c0 + ln < n) ? a.ws.atoms[src + c0 + ln] : 0x7fffffff;
-#pragma unroll 8
-                    for (int t = 0; t < 32; ++t) rank += (__shfl_sync(0xffffffffu, other, t) < me);
-                }
-                if (k < n) {
-                    sidx[b0 + rank] = me;
-                    spos[b0 + rank] = pos;
-                }
+            for (int k = ln; k < n; k += 32) {
+                float4 p = a.ws.rsorted[src + k];
+                p.w = __int_as_float(a.ws.atoms[src + k]);
+                spos[b0 + k] = p;
             }
         }
     }
     __syncthreads();
-    // interior cell (no stencil cell wraps, >= 5 cells per axis): every
-    // candidate is its own nearest image and rint(t Linv) = 0
+    // interior cell (no stencil cell wraps, >= 5 cells per axis) of
+    // positions inside [0, L): every candidate is its own nearest image
     bool inner = a.wrapped != 0;
     {
-        int lq = q;
-        int cxyz[3] = {lq % a.nc[0], (lq / a.nc[0]) % a.nc[1], lq / (a.nc[0] * a.nc[1])};
+        int cxyz[3] = {q % a.nc[0], (q / a.nc[0]) % a.nc[1], q / (a.nc[0] * a.nc[1])};
 #pragma unroll
         for (int d = 0; d < DIM; ++d) inner = inner && a.nc[d] >= 5 && cxyz[d] >= 1 && cxyz[d] <= a.nc[d] - 2;
     }
-    const int lane = tid & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    int wmax = 0;
-    for (int s = own_b + (tid >> 5); s < own_e; s += BUILD_WARPS) {
-        int i = a.ws.atoms[s];
-        float4 ri = a.ws.rsorted[s];
-        int32_t *out = a.nbr + (size_t)i * a.cap;
-        int count = 0;
-        for (int k0 = 0; k0 < M; k0 += 32) {
-            int k = k0 + lane;
-            bool hit = false;
-            int j = 0;
-            if (k < M) {
-                j = sidx[k];
-                float dx, dy, dz;
-                float r2 = inner ? dist2_inner<DIM>(ri, spos[k], dx, dy, dz)
-                                 : dist2_rn<DIM>(ri, spos[k], a.box, dx, dy, dz);
-                hit = (j != i) && (r2 < a.r_list2);
-            }
-            unsigned mk = __ballot_sync(0xffffffffu, hit);
-            int pos = count + __popc(mk & lt);
-            if (hit && pos < a.cap) out[pos] = j;
-            count += __popc(mk);
-        }
-        int n = count < a.cap ? count : a.cap;
-        for (int k = n + lane; k < a.cap; k += 32) out[k] = a.N;
-        if (lane == 0) {
-            a.cnt[i] = count;
-            a.rref[i] = ri;
-            if (count > a.cap) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
-            wmax = count > wmax ? count : wmax;
-        }
-    }
+    const int wmax = inner ? build_sweep<DIM, true>(a, spos, M, own_b, own_e)
+                           : build_sweep<DIM, false>(a, spos, M, own_b, own_e);
     // one atomic per block for the largest row count (not one per particle)
-    if (lane == 0) atomicMax(&bmax, wmax);
+    if ((tid & 31) == 0) atomicMax(&bmax, wmax);
     __syncthreads();
     if (tid == 0 && bmax > 0) atomicMax(&a.ws.ctl[CTL_MAXCNT], (uint32_t)bmax);
 }
@@ -447,6 +471,7 @@ void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st)
     k_bin_count<<<nb, tb, 0, st>>>(a);
     k_scan<<<1, 1024, 0, st>>>(a, ncell_total);
     k_scatter<<<nb, tb, 0, st>>>(a);
+    k_sort_cells<<<(ncell_total + SORT_WARPS - 1) / SORT_WARPS, SORT_WARPS * 32, 0, st>>>(a, ncell_total);
     if (a.dim == 3) k_build_cells<3><<<ncell_total, BUILD_WARPS * 32, 0, st>>>(a);
     else k_build_cells<2><<<ncell_total, BUILD_WARPS * 32, 0, st>>>(a);
     if (a.canonical) {
