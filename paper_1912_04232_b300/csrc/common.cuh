@@ -51,6 +51,20 @@ __device__ __forceinline__ float min_image_rn(float a, float b, float L, float L
     return __fsub_rn(t, __fmul_rn(L, n));
 }
 
+// The same displacement for |t * Linv| < 1.5, which holds whenever both
+// positions lie inside [0, L) (or a little outside): rint(u) can then only
+// be -1, 0 or 1 and is decided by two comparisons (rint(+-0.5) = 0, so the
+// tests are strict), and t - L*n is formed with the same single rounding
+// (L*n is exactly -L, 0 or L).  The bits equal min_image_rn's for every such
+// input; it avoids the round-to-integer conversion.
+__device__ __forceinline__ float min_image_near(float a, float b, float L, float Linv)
+{
+    const float t = __fsub_rn(a, b);
+    const float u = __fmul_rn(t, Linv);
+    const float s = u > 0.5f ? L : (u < -0.5f ? -L : 0.0f);
+    return __fsub_rn(t, s);
+}
+
 // Squared nearest-image distance, r2 = (dx*dx + dy*dy) + dz*dz, no FMA.
 // This exact expression decides every pair-membership test (neighbor list
 // and cutoffs) so the decision is reproducible bit for bit.
@@ -63,6 +77,23 @@ __device__ __forceinline__ float dist2_rn(const float4 &a, const float4 &b, cons
     float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
     if (DIM == 3) {
         dz = min_image_rn(a.z, b.z, bx.L[2], bx.Linv[2]);
+        r2 = __fadd_rn(r2, __fmul_rn(dz, dz));
+    } else {
+        dz = 0.0f;
+    }
+    return r2;
+}
+
+// dist2_rn for positions inside [0, L) (min_image_near on every axis).
+template <int DIM>
+__device__ __forceinline__ float dist2_near(const float4 &a, const float4 &b, const Box &bx, float &dx, float &dy,
+                                            float &dz)
+{
+    dx = min_image_near(a.x, b.x, bx.L[0], bx.Linv[0]);
+    dy = min_image_near(a.y, b.y, bx.L[1], bx.Linv[1]);
+    float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    if (DIM == 3) {
+        dz = min_image_near(a.z, b.z, bx.L[2], bx.Linv[2]);
         r2 = __fadd_rn(r2, __fmul_rn(dz, dz));
     } else {
         dz = 0.0f;

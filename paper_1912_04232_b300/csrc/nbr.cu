@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_scatter(NbrArgs a)
 
 // One warp per cell: rank every member by particle index against the whole
 // cell (shuffles, 32 members per pass) and write the members and their
-// positions in that order.  Every stencil that visits the cell then reads
+// positions in that order, the particle index in the w lane.  Every stencil that visits the cell then reads
 // it already in canonical order.
 constexpr int SORT_WARPS = 8;
 __global__ void __launch_bounds__(SORT_WARPS * 32) k_sort_cells(NbrArgs a, int ncell)
@@ -139,8 +139,10 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_sort_cells(NbrArgs a, int n
             for (int t = 0; t < 32; ++t) rk += (__shfl_sync(0xffffffffu, other, t) < me);
         }
         if (k < n) {
+            const float4 p = a.r[me];
             a.ws.atoms[b + rk] = me;
-            a.ws.rsorted[b + rk] = a.r[me];
+            a.ws.rsorted[b + rk] = make_float4(p.x, p.y, p.z, __int_as_float(me));   // index in w
+            a.rref[me] = p;   // positions of this build (displacement check)
         }
     }
 }
@@ -262,44 +264,197 @@ __device__ void build_row_warp(const NbrArgs &a, int i, int c, int *row)
     __syncwarp();
 }
 
-// Rows of the particles of one cell from its staged stencil candidates:
-// each warp takes particles of the cell and sweeps the M candidates 32 at a
-// time; ballot compaction writes hits straight into the output row.  INNER:
-// no stencil cell wraps, so rint(t * Linv) = 0 and the plain difference is
-// the nearest-image displacement bit for bit.
-constexpr int BUILD_WARPS = 8;
-template <int DIM, bool INNER>
-__device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *spos, int M, int own_b, int own_e)
+// ---------------------------------------------------------------------------
+// Neighbor-list build: persistent CTAs walk the cells q = blockIdx.x,
+// blockIdx.x + gridDim.x, ...  For each cell the candidates of its
+// (deduplicated) stencil are copied into shared memory in canonical order:
+// stencil cells in a fixed order (z, y, x offsets ascending), inside each
+// cell ascending particle index (k_sort_cells has ordered the members and
+// put the index in the w lane).  The copy of the next cell (cp.async) and
+// the lookup of the cell after it are in flight while the warps sweep the
+// current one, so the CTA never waits on a dependent global load.  Each warp
+// takes particles of the cell, sweeps the M candidates 32 at a time and
+// compacts hits with ballot into a shared-memory row that already holds the
+// padding, then writes the row out with 16-byte stores.  The row order is a
+// deterministic function of the positions and the cell grid.
+// ---------------------------------------------------------------------------
+constexpr int BUILD_WARPS = 4;
+constexpr int BUILD_CMAX = 1024;   // candidates a CTA stages per cell (else the per-warp dense path)
+constexpr int BUILD_NBUF = 1;      // 2: persistent CTAs with the next cell's copy in flight; 1: one CTA per cell
+constexpr int BUILD_ROWS_SMEM = 0; // rows assembled in shared memory, written with 16-byte stores
+constexpr int BUILD_ILP = 2;       // candidate chunks of 32 swept together per warp
+
+struct StencilInfo {
+    int soff[28];          // prefix of the stencil cells' counts
+    int sbeg[27];          // first slot of each stencil cell
+    int nst;               // stencil cells
+    int own_off, own_n;    // the cell's own members in the staged array
+    int own_beg;           // ... and their first slot
+    int inner;             // no stencil cell wraps (positions inside [0, L))
+};
+
+// Stencil cells of one axis (duplicates removed when the axis has < 3 cells):
+// offset o of coordinate c; the own cell's offset.
+__device__ __forceinline__ int axis_count(int n) { return n >= 3 ? 3 : n; }
+__device__ __forceinline__ int axis_cell(int c, int n, int o)
+{
+    if (n >= 3) {
+        int x = c + o - 1;
+        return x < 0 ? x + n : (x >= n ? x - n : x);
+    }
+    return o;
+}
+__device__ __forceinline__ int axis_own(int c, int n) { return n >= 3 ? 1 : (n == 2 ? c : 0); }
+
+// Warp 0, lane m: first slot and count of stencil cell m of cell q.
+template <int DIM>
+__device__ __forceinline__ void stencil_locate(const NbrArgs &a, int q, int lane, int &beg, int &cnt)
+{
+    const int cx = q % a.nc[0], cy = (q / a.nc[0]) % a.nc[1], cz = q / (a.nc[0] * a.nc[1]);
+    const int mx = axis_count(a.nc[0]), my = axis_count(a.nc[1]), mz = DIM == 3 ? axis_count(a.nc[2]) : 1;
+    beg = 0;
+    cnt = 0;
+    if (lane < mx * my * mz) {
+        const int xx = lane % mx, yy = (lane / mx) % my, zz = lane / (mx * my);
+        const int c = ((DIM == 3 ? axis_cell(cz, a.nc[2], zz) : 0) * a.nc[1] + axis_cell(cy, a.nc[1], yy)) * a.nc[0] +
+                      axis_cell(cx, a.nc[0], xx);
+        beg = a.ws.cell_start[c];
+        cnt = a.ws.cell_start[c + 1] - beg;
+    }
+}
+
+// Warp 0: prefix of the located counts and the rest of the cell's info.
+template <int DIM>
+__device__ __forceinline__ void stencil_publish(const NbrArgs &a, int q, int lane, int beg, int cnt, StencilInfo &inf)
+{
+    const int cx = q % a.nc[0], cy = (q / a.nc[0]) % a.nc[1], cz = q / (a.nc[0] * a.nc[1]);
+    const int mx = axis_count(a.nc[0]), my = axis_count(a.nc[1]), mz = DIM == 3 ? axis_count(a.nc[2]) : 1;
+    const int m = mx * my * mz;
+    const int own = ((DIM == 3 ? axis_own(cz, a.nc[2]) : 0) * my + axis_own(cy, a.nc[1])) * mx + axis_own(cx, a.nc[0]);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int own_off = __shfl_sync(0xffffffffu, incl - cnt, own);
+    const int own_n = __shfl_sync(0xffffffffu, cnt, own);
+    const int own_beg = __shfl_sync(0xffffffffu, beg, own);
+    if (lane < m) {
+        inf.soff[lane + 1] = incl;
+        inf.sbeg[lane] = beg;
+    }
+    if (lane == 0) {
+        bool inner = a.wrapped != 0;
+        const int cc[3] = {cx, cy, cz};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) inner = inner && a.nc[d] >= 5 && cc[d] >= 1 && cc[d] <= a.nc[d] - 2;
+        inf.soff[0] = 0;
+        inf.nst = m;
+        inf.own_off = own_off;
+        inf.own_n = own_n;
+        inf.own_beg = own_beg;
+        inf.inner = inner ? 1 : 0;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// All warps: copy the stencil candidates of one cell into dst (warp w takes
+// stencil cells w, w + BUILD_WARPS, ...).  Dense stencils are not staged.
+// The staged array is padded to whole sweep chunks with NaN positions, which
+// fail every distance test, so the sweep needs no bounds check.
+constexpr int BUILD_CHUNK = 32 * BUILD_ILP;
+constexpr int BUILD_BUF = BUILD_CMAX;   // float4 slots per buffer: padded_m(M <= BUILD_CMAX) fits
+static_assert(BUILD_CMAX % BUILD_CHUNK == 0, "padding must fit the buffer");
+__device__ __forceinline__ int padded_m(int M) { return (M + BUILD_CHUNK - 1) / BUILD_CHUNK * BUILD_CHUNK; }
+
+__device__ __forceinline__ void stencil_stage(const NbrArgs &a, const StencilInfo &inf, float4 *dst)
+{
+    const int M = inf.soff[inf.nst];
+    if (M > BUILD_CMAX) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int m = warp; m < inf.nst; m += BUILD_WARPS) {
+        const int b0 = inf.soff[m], n = inf.soff[m + 1] - b0;
+        const float4 *src = a.ws.rsorted + inf.sbeg[m];
+        for (int k = lane; k < n; k += 32) cp_async16(dst + b0 + k, src + k);
+    }
+    const float nan = __int_as_float(0x7fc00000);
+    for (int k = M + threadIdx.x; k < padded_m(M); k += BUILD_WARPS * 32) dst[k] = make_float4(nan, nan, nan, __int_as_float(-1));
+}
+
+// One warp: rows of the cell's particles p = warp, warp + BUILD_WARPS, ...
+// The distance form, all with the same bits: MODE 2, no stencil cell wraps,
+// so rint(t * Linv) = 0 and the plain difference is the nearest-image
+// displacement; MODE 1, positions inside [0, L) (min_image_near); MODE 0,
+// the general formula.
+template <int DIM, int MODE>
+__device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand, const StencilInfo &inf, int *row,
+                                           int vec_rows)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
+    const int M = padded_m(inf.soff[inf.nst]);
     int wmax = 0;
-    for (int s = own_b + (threadIdx.x >> 5); s < own_e; s += BUILD_WARPS) {
-        const int i = a.ws.atoms[s];
-        const float4 ri = a.ws.rsorted[s];
-        int32_t *out = a.nbr + (size_t)i * a.cap;
-        int count = 0;
-        for (int k0 = 0; k0 < M; k0 += 32) {
-            const int k = k0 + lane;
-            bool hit = false;
-            int j = 0;
-            if (k < M) {
-                const float4 c = spos[k];
-                j = __float_as_int(c.w);
-                float dx, dy, dz;
-                const float r2 = INNER ? dist2_inner<DIM>(ri, c, dx, dy, dz) : dist2_rn<DIM>(ri, c, a.box, dx, dy, dz);
-                hit = (j != i) && (r2 < a.r_list2);
+    for (int p = threadIdx.x >> 5; p < inf.own_n; p += BUILD_WARPS) {
+        const float4 ri = cand[inf.own_off + p];
+        const int i = __float_as_int(ri.w);
+        if (BUILD_ROWS_SMEM) {
+            if (vec_rows) {
+                for (int k = lane * 4; k < a.cap; k += 128)
+                    *reinterpret_cast<int4 *>(row + k) = make_int4(a.N, a.N, a.N, a.N);
+            } else {
+                for (int k = lane; k < a.cap; k += 32) row[k] = a.N;
             }
-            const unsigned mk = __ballot_sync(0xffffffffu, hit);
-            const int pos = count + __popc(mk & lt);
-            if (hit && pos < a.cap) out[pos] = j;
-            count += __popc(mk);
+            __syncwarp();
         }
-        const int n = count < a.cap ? count : a.cap;
-        for (int k = n + lane; k < a.cap; k += 32) out[k] = a.N;
+        int count = 0;
+        int32_t *out = a.nbr + (size_t)i * a.cap;
+        for (int k0 = 0; k0 < M; k0 += 32 * BUILD_ILP) {
+            bool hit[BUILD_ILP];
+            int j[BUILD_ILP];
+#pragma unroll
+            for (int u = 0; u < BUILD_ILP; ++u) {
+                const float4 c = cand[k0 + 32 * u + lane];
+                j[u] = __float_as_int(c.w);
+                float dx, dy, dz;
+                const float r2 = MODE == 2   ? dist2_inner<DIM>(ri, c, dx, dy, dz)
+                                 : MODE == 1 ? dist2_near<DIM>(ri, c, a.box, dx, dy, dz)
+                                             : dist2_rn<DIM>(ri, c, a.box, dx, dy, dz);
+                hit[u] = (j[u] != i) && (r2 < a.r_list2);
+            }
+#pragma unroll
+            for (int u = 0; u < BUILD_ILP; ++u) {
+                const unsigned mk = __ballot_sync(0xffffffffu, hit[u]);
+                const int pos = count + __popc(mk & lt);
+                if (hit[u] && pos < a.cap) {
+                    if (BUILD_ROWS_SMEM) row[pos] = j[u];
+                    else out[pos] = j[u];
+                }
+                count += __popc(mk);
+            }
+        }
+        __syncwarp();
+        if (BUILD_ROWS_SMEM) {
+            if (vec_rows) {
+                for (int k = lane * 4; k < a.cap; k += 128)
+                    *reinterpret_cast<int4 *>(out + k) = *reinterpret_cast<const int4 *>(row + k);
+            } else {
+                for (int k = lane; k < a.cap; k += 32) out[k] = row[k];
+            }
+            __syncwarp();   // the row buffer is refilled for the next particle
+        } else {
+            const int n = count < a.cap ? count : a.cap;
+            for (int k = n + lane; k < a.cap; k += 32) out[k] = a.N;
+        }
         if (lane == 0) {
             a.cnt[i] = count;
-            a.rref[i] = ri;
             if (count > a.cap) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
             wmax = count > wmax ? count : wmax;
         }
@@ -307,100 +462,89 @@ __device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *spos,
     return wmax;
 }
 
-// One CTA per cell.  The candidates of the cell's (deduplicated) stencil
-// are copied once into shared memory in canonical order: stencil cells in
-// a fixed order (z, y, x offsets ascending), inside each cell ascending
-// particle index (k_sort_cells has ordered the members), the particle
-// index riding in the w lane.  The row order is therefore a deterministic
-// function of the positions and the cell grid, with no per-row sort.
-constexpr int BUILD_CMAX = 1024;   // candidates a block stages in shared memory
+// Dynamic shared memory: two candidate buffers, then one row buffer per warp.
+__host__ __device__ inline size_t build_smem_bytes(int cap)
+{
+    return BUILD_NBUF * BUILD_BUF * sizeof(float4) +
+           (BUILD_ROWS_SMEM ? (size_t)BUILD_WARPS * ((cap + 3) & ~3) * sizeof(int) : 0);
+}
+
 template <int DIM>
-__global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
+__global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a, int ncell, int vec_rows)
 {
     count_launch();
     if (!chain_active(a)) return;
-    __shared__ float4 spos[BUILD_CMAX];
+    extern __shared__ float4 dsm[];
+    float4 *const buf[2] = {dsm, dsm + (BUILD_NBUF - 1) * BUILD_BUF};
+    int *const row = reinterpret_cast<int *>(dsm + BUILD_NBUF * BUILD_BUF) + (threadIdx.x >> 5) * ((a.cap + 3) & ~3);
+    __shared__ StencilInfo info[3];
     __shared__ int bmax;
-    __shared__ int soff[28];        // prefix of the stencil cells' counts
-    __shared__ int sbeg[27];
-    __shared__ int nst;
-    const int q = blockIdx.x;
-    const int tid = threadIdx.x;
-    const int own_b = a.ws.cell_start[q], own_e = a.ws.cell_start[q + 1];
-    if (own_e == own_b) return;   // uniform: empty cell
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x;
+    int q = blockIdx.x;
+    if (q >= ncell) return;   // whole CTA
     if (tid == 0) bmax = 0;
-    if (tid < 32) {
-        // stencil cells and their counts, one lane each, prefix by shuffles
-        int cx = q % a.nc[0];
-        int cy = (q / a.nc[0]) % a.nc[1];
-        int cz = q / (a.nc[0] * a.nc[1]);
-        int sx[3], sy[3], sz[3];
-        int mx = axis_cells(cx, a.nc[0], sx);
-        int my = axis_cells(cy, a.nc[1], sy);
-        int mz = DIM == 3 ? axis_cells(cz, a.nc[2], sz) : 1;
-        if (DIM != 3) sz[0] = 0;
-        int m = mx * my * mz;
-        int cnt = 0;
-        if (tid < m) {
-            int xx = tid % mx, yy = (tid / mx) % my, zz = tid / (mx * my);
-            int c = (sz[zz] * a.nc[1] + sy[yy]) * a.nc[0] + sx[xx];
-            cnt = a.ws.cell_start[c + 1] - a.ws.cell_start[c];
-            sbeg[tid] = a.ws.cell_start[c];
-        }
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (tid >= o) incl += y;
-        }
-        if (tid < m) soff[tid + 1] = incl;
-        if (tid == 0) {
-            soff[0] = 0;
-            nst = m;
-        }
+    int beg = 0, cnt = 0;     // warp 0: the located stencil of the next cell to publish
+    if (warp == 0) {
+        stencil_locate<DIM>(a, q, lane, beg, cnt);
+        stencil_publish<DIM>(a, q, lane, beg, cnt, info[0]);
     }
     __syncthreads();
-    const int M = soff[nst];
-    if (M > BUILD_CMAX) {
-        // dense stencil: per-warp rows with the rows' own sort; the 16 KB
-        // candidate array is reused as 8 warp buffers of 512 ints
-        static_assert(sizeof(spos) >= BUILD_WARPS * 512 * sizeof(int), "row buffers must fit");
-        int *rowbuf = reinterpret_cast<int *>(spos) + (tid >> 5) * 512;
-        for (int s = own_b + (tid >> 5); s < own_e; s += BUILD_WARPS) {
-            int i = a.ws.atoms[s];
-            if (a.cap <= 128) build_row_warp<DIM, 128>(a, i, q, rowbuf);
-            else if (a.cap <= 256) build_row_warp<DIM, 256>(a, i, q, rowbuf);
-            else build_row_warp<DIM, 512>(a, i, q, rowbuf);
-        }
-        return;
-    }
-    // staging: warp w copies stencil cells w, w + 8, ...
-    {
-        const int w = tid >> 5, ln = tid & 31;
-        for (int m = w; m < nst; m += BUILD_WARPS) {
-            const int b0 = soff[m], n = soff[m + 1] - b0, src = sbeg[m];
-            for (int k = ln; k < n; k += 32) {
-                float4 p = a.ws.rsorted[src + k];
-                p.w = __int_as_float(a.ws.atoms[src + k]);
-                spos[b0 + k] = p;
+    stencil_stage(a, info[0], buf[0]);
+    cp_async_commit();
+    if (warp == 0 && q + G < ncell) stencil_locate<DIM>(a, q + G, lane, beg, cnt);
+    int wmax = 0;
+    for (int t = 0; q < ncell; q += G, ++t) {
+        const int qn = q + G;
+        const StencilInfo &cur = info[t % 3];
+        StencilInfo &nxt = info[(t + 1) % 3];
+        if (warp == 0 && qn < ncell) stencil_publish<DIM>(a, qn, lane, beg, cnt, nxt);
+        cp_async_wait_all();
+        __syncthreads();   // current buffer landed, next info visible, previous sweep done
+        if (qn < ncell) stencil_stage(a, nxt, buf[(t + 1) & 1]);
+        cp_async_commit();
+        if (warp == 0 && qn + G < ncell) stencil_locate<DIM>(a, qn + G, lane, beg, cnt);
+        if (cur.soff[cur.nst] > BUILD_CMAX) {
+            // dense stencil: per-warp rows straight from global memory, with
+            // the rows' own sort; the idle current buffer holds 512 ints/warp
+            static_assert(BUILD_CMAX * sizeof(float4) >= BUILD_WARPS * 512 * sizeof(int), "row buffers must fit");
+            int *rowbuf = reinterpret_cast<int *>(buf[t & 1]) + warp * 512;
+            for (int p = warp; p < cur.own_n; p += BUILD_WARPS) {
+                const int i = a.ws.atoms[cur.own_beg + p];
+                if (a.cap <= 128) build_row_warp<DIM, 128>(a, i, q, rowbuf);
+                else if (a.cap <= 256) build_row_warp<DIM, 256>(a, i, q, rowbuf);
+                else build_row_warp<DIM, 512>(a, i, q, rowbuf);
             }
+        } else {
+            const int w = cur.inner    ? build_sweep<DIM, 2>(a, buf[t & 1], cur, row, vec_rows)
+                          : a.wrapped ? build_sweep<DIM, 1>(a, buf[t & 1], cur, row, vec_rows)
+                                      : build_sweep<DIM, 0>(a, buf[t & 1], cur, row, vec_rows);
+            wmax = w > wmax ? w : wmax;
         }
     }
-    __syncthreads();
-    // interior cell (no stencil cell wraps, >= 5 cells per axis) of
-    // positions inside [0, L): every candidate is its own nearest image
-    bool inner = a.wrapped != 0;
-    {
-        int cxyz[3] = {q % a.nc[0], (q / a.nc[0]) % a.nc[1], q / (a.nc[0] * a.nc[1])};
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) inner = inner && a.nc[d] >= 5 && cxyz[d] >= 1 && cxyz[d] <= a.nc[d] - 2;
-    }
-    const int wmax = inner ? build_sweep<DIM, true>(a, spos, M, own_b, own_e)
-                           : build_sweep<DIM, false>(a, spos, M, own_b, own_e);
-    // one atomic per block for the largest row count (not one per particle)
-    if ((tid & 31) == 0) atomicMax(&bmax, wmax);
+    cp_async_wait_all();
+    // one atomic per CTA for the largest row count
+    if (lane == 0) atomicMax(&bmax, wmax);
     __syncthreads();
     if (tid == 0 && bmax > 0) atomicMax(&a.ws.ctl[CTL_MAXCNT], (uint32_t)bmax);
+}
+
+template <int DIM>
+static int build_grid(int ncell, size_t smem)
+{
+    static int per_sm = 0, sms = 0;
+    static size_t smem_seen = 0;
+    if (!per_sm || smem_seen != smem) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_cells<DIM>, BUILD_WARPS * 32, smem);
+        if (per_sm < 1) per_sm = 1;
+        if (sms < 1) sms = 1;
+        smem_seen = smem;
+    }
+    const int g = per_sm * sms;
+    return (BUILD_NBUF == 1 || ncell < g) ? ncell : g;   // one buffer: one cell per CTA
 }
 
 // Sets the rebuild flag if any particle moved more than skin/2 (minimum
@@ -472,8 +616,10 @@ void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st)
     k_scan<<<1, 1024, 0, st>>>(a, ncell_total);
     k_scatter<<<nb, tb, 0, st>>>(a);
     k_sort_cells<<<(ncell_total + SORT_WARPS - 1) / SORT_WARPS, SORT_WARPS * 32, 0, st>>>(a, ncell_total);
-    if (a.dim == 3) k_build_cells<3><<<ncell_total, BUILD_WARPS * 32, 0, st>>>(a);
-    else k_build_cells<2><<<ncell_total, BUILD_WARPS * 32, 0, st>>>(a);
+    const size_t smem = build_smem_bytes(a.cap);
+    const int vec_rows = (a.cap % 4 == 0 && ((uintptr_t)a.nbr & 15) == 0) ? 1 : 0;
+    if (a.dim == 3) k_build_cells<3><<<build_grid<3>(ncell_total, smem), BUILD_WARPS * 32, smem, st>>>(a, ncell_total, vec_rows);
+    else k_build_cells<2><<<build_grid<2>(ncell_total, smem), BUILD_WARPS * 32, smem, st>>>(a, ncell_total, vec_rows);
     if (a.canonical) {
         int g = (a.N + 7) / 8;
         g = g < 4096 ? g : 4096;

@@ -104,6 +104,9 @@ def test_batch_equals_one_launch_per_replica_bitwise(P):
     states = [_initial(P, sp) for sp in specs]
     n = 120
     b, r, v, PE, KE = _batched(P, specs, states, n)
+    # same lanes per particle as the batch plan's default, whatever an
+    # earlier test left set
+    P.md_set_pair_tpp(4)
     off = 0
     for sp, stt in zip(specs, states):
         rs, vs = _single(P, sp, stt[0], stt[1], n)

@@ -108,7 +108,7 @@ def test_lj_forces_energy_lj4096(P, tpp):
         P.md_energy_forces(s, P.lj_pot(), rd, nl.plan, f, E, st)
         torch.cuda.synchronize()
     finally:
-        P.md_set_pair_tpp(8)
+        P.md_set_pair_tpp(4)   # the library default
     assert P.md_status_poll(st) == 0
     U, F, e = O.lj(c.r, c.L)
     fg = f.cpu().numpy()
@@ -191,6 +191,22 @@ def test_nve_rebuilds_keep_every_interacting_pair(P):
         have = set(nb_g[i, : cnt_g[i]].tolist())
         need = set(nb_o[i, : cnt_o[i]].tolist())
         assert need <= have, i
+
+
+@pytest.mark.parametrize("workload", ["lj4096", "lj256k"])
+def test_neighbor_list_rebuilt_in_dynamics_bit_exact(P, workload):
+    # rebuilds inside the NVE loop see positions kept inside [0, L), so they
+    # take the build's wrapped-position forms (interior cells without the
+    # wrap, comparison-based nearest image at the faces); the rows of the
+    # last rebuild must equal the oracle's FP32-decision list at the
+    # positions of that build
+    c = W.lj_small() if workload == "lj4096" else W.lj_large()
+    r, v, f, PE, KE, nl = _run_nve(P, c, 60 if workload == "lj4096" else 30, True)
+    assert nl.stats()[0] >= 3
+    assert min(list(nl.plan.ncell)) >= 5   # interior cells exist
+    rref = nl.rref.cpu().numpy()
+    cnt_o, nb_o = O.neighbor_list(rref, c.L, float(nl.plan.r_list), cap=128, fp32_decision=True)
+    rows_equal(nl.cnt.cpu().numpy(), nl.nbr.cpu().numpy(), cnt_o, nb_o)
 
 
 def test_run_to_run_bitwise_determinism(P):
