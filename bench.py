@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--tpp", type=int, default=0)
     ap.add_argument("--pair-opt", type=int, default=-1, help="pair-kernel variant (md_set_pair_options)")
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel from the host (profiling)")
+    ap.add_argument("--local-rows", type=int, default=0,
+                    help="1: cell-centred forces over 16-bit local rows (MD_NBR_LOCAL_ROWS); 0: int32 rows")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain-SW section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-replica section")
     return ap.parse_args()
@@ -314,7 +316,7 @@ def main():
     if args.pair_opt >= 0:
         P.md_set_pair_options(args.pair_opt)
     s = P.md_space_periodic(3, [c.L] * 3)
-    nl = P.NeighborList(s, c.N, c.r_cut, c.skin, 128)
+    nl = P.NeighborList(s, c.N, c.r_cut, c.skin, 128, local_rows=bool(args.local_rows))
     pot = P.lj_pot(c.eps, c.sigma, c.r_cut, True)
     r0 = torch.from_numpy(c.r).to(dev)
     v0 = torch.from_numpy(c.v).to(dev)
@@ -410,7 +412,8 @@ def main():
 
     # roofline of the dominant kernel (pair forces), launched alone with events
     mean_cnt = float(nl.cnt.float().clamp(max=nl.cap).mean().item())
-    bytes_per_particle = 4.0 * mean_cnt + 4 + 16 + 16 + 16   # row, count, own r, f write, gathered r once
+    row_bytes = 2.0 if args.local_rows else 4.0              # 16-bit local or int32 row entries
+    bytes_per_particle = row_bytes * mean_cnt + 4 + 16 + 16 + 16   # row, count, own r, f write, gathered r once
     fe = []
     for _ in range(30):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -451,9 +454,10 @@ def main():
                        "dt": c.dt, "neighbor_cap": nl.cap, "rebuilds_per_step": builds / args.steps,
                        "max_energy_drift_per_particle": drift, "l2": "flushed between bench steps",
                        "parallelism": f"replicas{world}", "pair_tpp": args.tpp or 4,
+                       "neighbor_rows": "int32 + 16-bit local" if args.local_rows else "int32",
                        "loop": "host launches" if args.no_graph else "one CUDA graph (device WHILE/IF)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_pair<LJ> (md_energy_forces)",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": ("k_pair_cell<LJ>" if args.local_rows else "k_pair<LJ>") + " (md_energy_forces)",
                          "bytes_per_particle": bytes_per_particle, "kernel_ms": kt * 1e3,
                          "peak_source": peak_src},
             "cpu_baseline": cpu_baseline,

@@ -101,7 +101,7 @@ typedef struct {
     int32_t *cnt;          /* [N] */
     float *rref;           /* [N][4] positions at the last build */
     void *ws;              /* ws_bytes of scratch (cells, sorted copy, control words, reduction partials) */
-    int flags;             /* MD_NBR_CANONICAL (set by the caller before md_nbr_bind), else 0 */
+    int flags;             /* MD_NBR_* bits (md_nbr_set_flags, before md_nbr_bind), else 0 */
 } md_nbr;
 
 /* Canonical mode: every build also sorts each row ascending, and force
@@ -112,10 +112,25 @@ typedef struct {
  * recomputation relies on it).  Slower; meant for small systems. */
 #define MD_NBR_CANONICAL 1
 
+/* Local rows: every build also writes, for each row entry, the entry's index
+ * into the candidate array of the particle's cell (the cells of its stencil
+ * concatenated in canonical order, members in ascending particle order) as
+ * a 16-bit row in the workspace.  Pair forces (Lennard-Jones, soft sphere)
+ * then run one CTA per cell that stages the stencil's positions in shared
+ * memory and gathers from there; the forces are bitwise those of the int32
+ * rows.  Cells whose stencil holds more than 1024 candidates keep using the
+ * int32 rows.  Not combinable with MD_NBR_CANONICAL. */
+#define MD_NBR_LOCAL_ROWS 2
+
 /* Plan a neighbor list for N particles in space s.  Fails with
  * MD_ERR_BOX_TOO_SMALL if any used box edge is < 2 r_list, MD_ERR_INVALID
  * for N < 1, cap < 1, r_cut <= 0 or skin < 0.  Fills out (pointers NULL). */
 JMD_API md_status md_nbr_plan(const md_space *s, int N, float r_cut, float skin, int cap, md_nbr *out);
+
+/* Set the MD_NBR_* bits of a plan and update its ws_bytes (local rows need
+ * N*cap*2 more bytes).  Call before md_nbr_bind; MD_ERR_INVALID for unknown
+ * bits or MD_NBR_CANONICAL | MD_NBR_LOCAL_ROWS. */
+JMD_API md_status md_nbr_set_flags(md_nbr *nb, int flags);
 
 /* Attach caller memory: d_nbr [N*cap] int32, d_cnt [N] int32, d_rref [N*4]
  * float (16-byte aligned), d_ws [ws_bytes] (256-byte aligned).  Zeroes the
@@ -210,9 +225,8 @@ JMD_API md_status md_energy_forces(const md_space *s, const md_pot *p, const flo
 JMD_API md_status md_set_pair_tpp(int tpp);
 
 /* Pair-kernel variant (a tuning knob; every variant gives the same bits):
- * bit 0 = read neighbor rows past L1, bit 1 = skip the wrap arithmetic for
- * particles at least r_list + skin from every face.  Default 1 (measured
- * fastest on B300: the interior path diverges within warps). */
+ * opt = 1 reads neighbor rows past L1 (default, measured faster on B300),
+ * opt = 0 through it.  Other values: MD_ERR_INVALID. */
 JMD_API md_status md_set_pair_options(int opt);
 
 /* ------------------------------------------------------------------------ */

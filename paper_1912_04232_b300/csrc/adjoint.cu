@@ -225,7 +225,6 @@ extern "C" md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_
 
     PairArgs pa;
     if (!make_pair_args(s, p, d_r, nb, d_f, pa)) return MD_ERR_INVALID;
-    pa.margin = 1e30f;   // unwrapped coordinates: always the full nearest-image formula
     pa.status = d_status;
     NbrArgs na = make_nbr_args(s, d_r, nb, d_status, 1);
     WsPtrs w = ws_ptrs(nb);

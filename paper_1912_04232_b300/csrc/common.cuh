@@ -127,6 +127,12 @@ __device__ __forceinline__ int ld_stream(const int32_t *p)
     asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
+__device__ __forceinline__ int ld_stream_u16(const uint16_t *p)
+{
+    unsigned short v;
+    asm volatile("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
 
 // Wrap a coordinate into [0, L): x - L floor(x Linv), folded once more if
 // rounding left it on the boundary.
@@ -227,13 +233,14 @@ __device__ __forceinline__ double block_sum_f64(double v, double *sh)
 // Workspace layout of a neighbor list (all offsets 256-byte aligned).
 // ---------------------------------------------------------------------------
 struct WsLayout {
-    size_t ctl, cell_count, cell_start, cell_of, rank, atoms_u, atoms, rsorted, partials, total;
+    size_t ctl, cell_count, cell_start, cell_of, rank, atoms_u, atoms, rsorted, partials, lrow, total;
     int max_blocks;
 };
 
 __host__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-__host__ inline WsLayout ws_layout(int N, int ncell_total)
+// Scratch of a neighbor list; the 16-bit local rows only with MD_NBR_LOCAL_ROWS.
+__host__ inline WsLayout ws_layout(int N, int ncell_total, int cap, int flags)
 {
     WsLayout w;
     size_t o = 0;
@@ -247,6 +254,8 @@ __host__ inline WsLayout ws_layout(int N, int ncell_total)
     w.rsorted = o;      o = align256(o + sizeof(float4) * (size_t)N);
     w.max_blocks = N / 4 + 64;
     w.partials = o;     o = align256(o + sizeof(double2) * (size_t)w.max_blocks);
+    w.lrow = o;
+    if (flags & MD_NBR_LOCAL_ROWS) o = align256(o + sizeof(uint16_t) * (size_t)N * (size_t)cap);
     w.total = o;
     return w;
 }
@@ -256,12 +265,13 @@ struct WsPtrs {
     int32_t *cell_count, *cell_start, *cell_of, *rank, *atoms_u, *atoms;
     float4 *rsorted;
     double2 *partials;
+    uint16_t *lrow;   // NULL without MD_NBR_LOCAL_ROWS
     int max_blocks;
 };
 
 __host__ inline WsPtrs ws_ptrs(const md_nbr *nb)
 {
-    WsLayout w = ws_layout(nb->N, nb->ncell_total);
+    WsLayout w = ws_layout(nb->N, nb->ncell_total, nb->cap, nb->flags);
     char *b = (char *)nb->ws;
     WsPtrs p;
     p.ctl = (uint32_t *)(b + w.ctl);
@@ -273,8 +283,18 @@ __host__ inline WsPtrs ws_ptrs(const md_nbr *nb)
     p.atoms = (int32_t *)(b + w.atoms);
     p.rsorted = (float4 *)(b + w.rsorted);
     p.partials = (double2 *)(b + w.partials);
+    p.lrow = (nb->flags & MD_NBR_LOCAL_ROWS) ? (uint16_t *)(b + w.lrow) : nullptr;
     p.max_blocks = w.max_blocks;
     return p;
+}
+
+// The plan's flags are valid and its layout fits the bound scratch (guards
+// against flags changed after md_nbr_set_flags / md_nbr_bind).
+__host__ inline bool nbr_layout_ok(const md_nbr *nb)
+{
+    if (nb->flags & ~(MD_NBR_CANONICAL | MD_NBR_LOCAL_ROWS)) return false;
+    if ((nb->flags & MD_NBR_CANONICAL) && (nb->flags & MD_NBR_LOCAL_ROWS)) return false;
+    return ws_layout(nb->N, nb->ncell_total, nb->cap, nb->flags).total <= nb->ws_bytes;
 }
 
 // Host-side CUDA error to status.

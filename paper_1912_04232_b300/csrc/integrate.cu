@@ -403,7 +403,6 @@ extern "C" md_status md_minimize(const md_space *s, const md_pot *p, int kind, f
     cudaStream_t st = (cudaStream_t)stream;
     PairArgs pa;
     if (!make_pair_args(s, p, d_r, nb, d_f, pa)) return MD_ERR_INVALID;
-    pa.margin = 1e30f;   // unwrapped coordinates: always the full nearest-image formula
     pa.E_out = d_E;
     pa.series = d_E ? 1 : 0;
     pa.status = d_status;

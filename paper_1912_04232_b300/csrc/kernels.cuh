@@ -14,6 +14,7 @@ struct NbrArgs {
     float r_list2;
     const float4 *r;
     int32_t *nbr, *cnt;
+    uint16_t *lrow;  // local rows (MD_NBR_LOCAL_ROWS) or NULL
     float4 *rref;
     WsPtrs ws;
     uint32_t *status;
@@ -25,8 +26,7 @@ struct NbrArgs {
 struct PairArgs {
     Box box;
     int N, cap, tpp;
-    float margin;           // r_list + skin: particles this far from every face skip the wrap
-    int opt;                // kernel variant: bit 0 stream rows past L1, bit 1 interior fast path
+    int opt;                // kernel variant: bit 0 stream rows past L1
     const float4 *r;
     const int32_t *nbr, *cnt;
     float4 *f;
@@ -43,6 +43,10 @@ struct PairArgs {
     const float *bp_params, *bp_norm;
     float *bp_G, *bp_dEdG, *bp_Ei;
     int bp_sys_n;
+    // cell-centred path (lists with local rows): 16-bit rows and the cell list
+    const uint16_t *lrow;
+    const int32_t *atoms, *cell_start;
+    int nc[3], ncell, max_blocks;
     // reductions
     double *E_out, *KE_out;
     int series;             // 1: write E_out[ctl[CTL_STEP]] and advance the counter

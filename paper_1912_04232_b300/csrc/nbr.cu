@@ -19,6 +19,7 @@
 //                 padded int32 rows
 #include <cmath>
 
+#include "cells.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -265,138 +266,28 @@ __device__ void build_row_warp(const NbrArgs &a, int i, int c, int *row)
 }
 
 // ---------------------------------------------------------------------------
-// Neighbor-list build: persistent CTAs walk the cells q = blockIdx.x,
-// blockIdx.x + gridDim.x, ...  For each cell the candidates of its
-// (deduplicated) stencil are copied into shared memory in canonical order:
-// stencil cells in a fixed order (z, y, x offsets ascending), inside each
-// cell ascending particle index (k_sort_cells has ordered the members and
-// put the index in the w lane).  The copy of the next cell (cp.async) and
-// the lookup of the cell after it are in flight while the warps sweep the
-// current one, so the CTA never waits on a dependent global load.  Each warp
-// takes particles of the cell, sweeps the M candidates 32 at a time and
-// compacts hits with ballot into a shared-memory row that already holds the
-// padding, then writes the row out with 16-byte stores.  The row order is a
+// Neighbor-list build: one CTA per cell.  The candidates of the cell's
+// stencil (cells.cuh) are copied into shared memory in canonical order with
+// the particle index in the w lane (k_sort_cells), and padded with NaN
+// positions to whole sweep steps (a NaN fails every distance test, so the
+// sweep needs no bounds check).  Each warp takes particles of the cell and
+// sweeps the candidates 64 at a time (two ballots), writing hits straight
+// into the padded int32 row and, when the list keeps local rows, each hit's
+// index into the staged array into the 16-bit row.  The row order is a
 // deterministic function of the positions and the cell grid.
 // ---------------------------------------------------------------------------
 constexpr int BUILD_WARPS = 4;
-constexpr int BUILD_CMAX = 1024;   // candidates a CTA stages per cell (else the per-warp dense path)
-constexpr int BUILD_NBUF = 1;      // 2: persistent CTAs with the next cell's copy in flight; 1: one CTA per cell
-constexpr int BUILD_ROWS_SMEM = 0; // rows assembled in shared memory, written with 16-byte stores
-constexpr int BUILD_ILP = 2;       // candidate chunks of 32 swept together per warp
-
-struct StencilInfo {
-    int soff[28];          // prefix of the stencil cells' counts
-    int sbeg[27];          // first slot of each stencil cell
-    int nst;               // stencil cells
-    int own_off, own_n;    // the cell's own members in the staged array
-    int own_beg;           // ... and their first slot
-    int inner;             // no stencil cell wraps (positions inside [0, L))
-};
-
-// Stencil cells of one axis (duplicates removed when the axis has < 3 cells):
-// offset o of coordinate c; the own cell's offset.
-__device__ __forceinline__ int axis_count(int n) { return n >= 3 ? 3 : n; }
-__device__ __forceinline__ int axis_cell(int c, int n, int o)
-{
-    if (n >= 3) {
-        int x = c + o - 1;
-        return x < 0 ? x + n : (x >= n ? x - n : x);
-    }
-    return o;
-}
-__device__ __forceinline__ int axis_own(int c, int n) { return n >= 3 ? 1 : (n == 2 ? c : 0); }
-
-// Warp 0, lane m: first slot and count of stencil cell m of cell q.
-template <int DIM>
-__device__ __forceinline__ void stencil_locate(const NbrArgs &a, int q, int lane, int &beg, int &cnt)
-{
-    const int cx = q % a.nc[0], cy = (q / a.nc[0]) % a.nc[1], cz = q / (a.nc[0] * a.nc[1]);
-    const int mx = axis_count(a.nc[0]), my = axis_count(a.nc[1]), mz = DIM == 3 ? axis_count(a.nc[2]) : 1;
-    beg = 0;
-    cnt = 0;
-    if (lane < mx * my * mz) {
-        const int xx = lane % mx, yy = (lane / mx) % my, zz = lane / (mx * my);
-        const int c = ((DIM == 3 ? axis_cell(cz, a.nc[2], zz) : 0) * a.nc[1] + axis_cell(cy, a.nc[1], yy)) * a.nc[0] +
-                      axis_cell(cx, a.nc[0], xx);
-        beg = a.ws.cell_start[c];
-        cnt = a.ws.cell_start[c + 1] - beg;
-    }
-}
-
-// Warp 0: prefix of the located counts and the rest of the cell's info.
-template <int DIM>
-__device__ __forceinline__ void stencil_publish(const NbrArgs &a, int q, int lane, int beg, int cnt, StencilInfo &inf)
-{
-    const int cx = q % a.nc[0], cy = (q / a.nc[0]) % a.nc[1], cz = q / (a.nc[0] * a.nc[1]);
-    const int mx = axis_count(a.nc[0]), my = axis_count(a.nc[1]), mz = DIM == 3 ? axis_count(a.nc[2]) : 1;
-    const int m = mx * my * mz;
-    const int own = ((DIM == 3 ? axis_own(cz, a.nc[2]) : 0) * my + axis_own(cy, a.nc[1])) * mx + axis_own(cx, a.nc[0]);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const int own_off = __shfl_sync(0xffffffffu, incl - cnt, own);
-    const int own_n = __shfl_sync(0xffffffffu, cnt, own);
-    const int own_beg = __shfl_sync(0xffffffffu, beg, own);
-    if (lane < m) {
-        inf.soff[lane + 1] = incl;
-        inf.sbeg[lane] = beg;
-    }
-    if (lane == 0) {
-        bool inner = a.wrapped != 0;
-        const int cc[3] = {cx, cy, cz};
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) inner = inner && a.nc[d] >= 5 && cc[d] >= 1 && cc[d] <= a.nc[d] - 2;
-        inf.soff[0] = 0;
-        inf.nst = m;
-        inf.own_off = own_off;
-        inf.own_n = own_n;
-        inf.own_beg = own_beg;
-        inf.inner = inner ? 1 : 0;
-    }
-}
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// All warps: copy the stencil candidates of one cell into dst (warp w takes
-// stencil cells w, w + BUILD_WARPS, ...).  Dense stencils are not staged.
-// The staged array is padded to whole sweep chunks with NaN positions, which
-// fail every distance test, so the sweep needs no bounds check.
-constexpr int BUILD_CHUNK = 32 * BUILD_ILP;
-constexpr int BUILD_BUF = BUILD_CMAX;   // float4 slots per buffer: padded_m(M <= BUILD_CMAX) fits
-static_assert(BUILD_CMAX % BUILD_CHUNK == 0, "padding must fit the buffer");
+constexpr int BUILD_CHUNK = 64;   // candidates per sweep step (two per lane)
+static_assert(STAGE_CMAX % BUILD_CHUNK == 0, "the padding must fit the staging buffer");
 __device__ __forceinline__ int padded_m(int M) { return (M + BUILD_CHUNK - 1) / BUILD_CHUNK * BUILD_CHUNK; }
 
-__device__ __forceinline__ void stencil_stage(const NbrArgs &a, const StencilInfo &inf, float4 *dst)
-{
-    const int M = inf.soff[inf.nst];
-    if (M > BUILD_CMAX) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int m = warp; m < inf.nst; m += BUILD_WARPS) {
-        const int b0 = inf.soff[m], n = inf.soff[m + 1] - b0;
-        const float4 *src = a.ws.rsorted + inf.sbeg[m];
-        for (int k = lane; k < n; k += 32) cp_async16(dst + b0 + k, src + k);
-    }
-    const float nan = __int_as_float(0x7fc00000);
-    for (int k = M + threadIdx.x; k < padded_m(M); k += BUILD_WARPS * 32) dst[k] = make_float4(nan, nan, nan, __int_as_float(-1));
-}
-
-// One warp: rows of the cell's particles p = warp, warp + BUILD_WARPS, ...
-// The distance form, all with the same bits: MODE 2, no stencil cell wraps,
-// so rint(t * Linv) = 0 and the plain difference is the nearest-image
+// Rows of the cell's particles p = warp, warp + BUILD_WARPS, ...  The
+// distance form, all with the same bits: MODE 2, no stencil cell wraps, so
+// rint(t * Linv) = 0 and the plain difference is the nearest-image
 // displacement; MODE 1, positions inside [0, L) (min_image_near); MODE 0,
 // the general formula.
 template <int DIM, int MODE>
-__device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand, const StencilInfo &inf, int *row,
-                                           int vec_rows)
+__device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand, const StencilInfo &inf)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -405,22 +296,14 @@ __device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand,
     for (int p = threadIdx.x >> 5; p < inf.own_n; p += BUILD_WARPS) {
         const float4 ri = cand[inf.own_off + p];
         const int i = __float_as_int(ri.w);
-        if (BUILD_ROWS_SMEM) {
-            if (vec_rows) {
-                for (int k = lane * 4; k < a.cap; k += 128)
-                    *reinterpret_cast<int4 *>(row + k) = make_int4(a.N, a.N, a.N, a.N);
-            } else {
-                for (int k = lane; k < a.cap; k += 32) row[k] = a.N;
-            }
-            __syncwarp();
-        }
         int count = 0;
         int32_t *out = a.nbr + (size_t)i * a.cap;
-        for (int k0 = 0; k0 < M; k0 += 32 * BUILD_ILP) {
-            bool hit[BUILD_ILP];
-            int j[BUILD_ILP];
+        uint16_t *lout = a.lrow ? a.lrow + (size_t)i * a.cap : nullptr;
+        for (int k0 = 0; k0 < M; k0 += BUILD_CHUNK) {
+            bool hit[2];
+            int j[2];
 #pragma unroll
-            for (int u = 0; u < BUILD_ILP; ++u) {
+            for (int u = 0; u < 2; ++u) {
                 const float4 c = cand[k0 + 32 * u + lane];
                 j[u] = __float_as_int(c.w);
                 float dx, dy, dz;
@@ -430,28 +313,20 @@ __device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand,
                 hit[u] = (j[u] != i) && (r2 < a.r_list2);
             }
 #pragma unroll
-            for (int u = 0; u < BUILD_ILP; ++u) {
+            for (int u = 0; u < 2; ++u) {
                 const unsigned mk = __ballot_sync(0xffffffffu, hit[u]);
                 const int pos = count + __popc(mk & lt);
                 if (hit[u] && pos < a.cap) {
-                    if (BUILD_ROWS_SMEM) row[pos] = j[u];
-                    else out[pos] = j[u];
+                    out[pos] = j[u];
+                    if (lout) lout[pos] = (uint16_t)(k0 + 32 * u + lane);
                 }
                 count += __popc(mk);
             }
         }
-        __syncwarp();
-        if (BUILD_ROWS_SMEM) {
-            if (vec_rows) {
-                for (int k = lane * 4; k < a.cap; k += 128)
-                    *reinterpret_cast<int4 *>(out + k) = *reinterpret_cast<const int4 *>(row + k);
-            } else {
-                for (int k = lane; k < a.cap; k += 32) out[k] = row[k];
-            }
-            __syncwarp();   // the row buffer is refilled for the next particle
-        } else {
-            const int n = count < a.cap ? count : a.cap;
-            for (int k = n + lane; k < a.cap; k += 32) out[k] = a.N;
+        const int n = count < a.cap ? count : a.cap;
+        for (int k = n + lane; k < a.cap; k += 32) {
+            out[k] = a.N;
+            if (lout) lout[k] = LROW_PAD;
         }
         if (lane == 0) {
             a.cnt[i] = count;
@@ -462,89 +337,55 @@ __device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand,
     return wmax;
 }
 
-// Dynamic shared memory: two candidate buffers, then one row buffer per warp.
-__host__ __device__ inline size_t build_smem_bytes(int cap)
-{
-    return BUILD_NBUF * BUILD_BUF * sizeof(float4) +
-           (BUILD_ROWS_SMEM ? (size_t)BUILD_WARPS * ((cap + 3) & ~3) * sizeof(int) : 0);
-}
-
 template <int DIM>
-__global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a, int ncell, int vec_rows)
+__global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
 {
     count_launch();
     if (!chain_active(a)) return;
-    extern __shared__ float4 dsm[];
-    float4 *const buf[2] = {dsm, dsm + (BUILD_NBUF - 1) * BUILD_BUF};
-    int *const row = reinterpret_cast<int *>(dsm + BUILD_NBUF * BUILD_BUF) + (threadIdx.x >> 5) * ((a.cap + 3) & ~3);
-    __shared__ StencilInfo info[3];
+    __shared__ float4 cand[STAGE_CMAX];
+    __shared__ StencilInfo inf;
     __shared__ int bmax;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int G = gridDim.x;
-    int q = blockIdx.x;
-    if (q >= ncell) return;   // whole CTA
-    if (tid == 0) bmax = 0;
-    int beg = 0, cnt = 0;     // warp 0: the located stencil of the next cell to publish
+    const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (warp == 0) {
-        stencil_locate<DIM>(a, q, lane, beg, cnt);
-        stencil_publish<DIM>(a, q, lane, beg, cnt, info[0]);
+        int beg, cnt;
+        stencil_locate<DIM>(a.nc, a.ws.cell_start, q, lane, beg, cnt);
+        stencil_publish<DIM>(a.nc, a.wrapped, q, lane, beg, cnt, inf);
     }
+    if (tid == 0) bmax = 0;
     __syncthreads();
-    stencil_stage(a, info[0], buf[0]);
-    cp_async_commit();
-    if (warp == 0 && q + G < ncell) stencil_locate<DIM>(a, q + G, lane, beg, cnt);
+    if (inf.own_n == 0) return;   // whole CTA: empty cell
+    const int M = inf.soff[inf.nst];
     int wmax = 0;
-    for (int t = 0; q < ncell; q += G, ++t) {
-        const int qn = q + G;
-        const StencilInfo &cur = info[t % 3];
-        StencilInfo &nxt = info[(t + 1) % 3];
-        if (warp == 0 && qn < ncell) stencil_publish<DIM>(a, qn, lane, beg, cnt, nxt);
-        cp_async_wait_all();
-        __syncthreads();   // current buffer landed, next info visible, previous sweep done
-        if (qn < ncell) stencil_stage(a, nxt, buf[(t + 1) & 1]);
-        cp_async_commit();
-        if (warp == 0 && qn + G < ncell) stencil_locate<DIM>(a, qn + G, lane, beg, cnt);
-        if (cur.soff[cur.nst] > BUILD_CMAX) {
-            // dense stencil: per-warp rows straight from global memory, with
-            // the rows' own sort; the idle current buffer holds 512 ints/warp
-            static_assert(BUILD_CMAX * sizeof(float4) >= BUILD_WARPS * 512 * sizeof(int), "row buffers must fit");
-            int *rowbuf = reinterpret_cast<int *>(buf[t & 1]) + warp * 512;
-            for (int p = warp; p < cur.own_n; p += BUILD_WARPS) {
-                const int i = a.ws.atoms[cur.own_beg + p];
-                if (a.cap <= 128) build_row_warp<DIM, 128>(a, i, q, rowbuf);
-                else if (a.cap <= 256) build_row_warp<DIM, 256>(a, i, q, rowbuf);
-                else build_row_warp<DIM, 512>(a, i, q, rowbuf);
-            }
-        } else {
-            const int w = cur.inner    ? build_sweep<DIM, 2>(a, buf[t & 1], cur, row, vec_rows)
-                          : a.wrapped ? build_sweep<DIM, 1>(a, buf[t & 1], cur, row, vec_rows)
-                                      : build_sweep<DIM, 0>(a, buf[t & 1], cur, row, vec_rows);
-            wmax = w > wmax ? w : wmax;
+    if (M > STAGE_CMAX) {
+        // dense stencil: per-warp rows straight from global memory with the
+        // rows' own sort (int32 rows only); the candidate buffer holds 512
+        // ints per warp
+        static_assert(sizeof(cand) >= BUILD_WARPS * 512 * sizeof(int), "row buffers must fit");
+        int *rowbuf = reinterpret_cast<int *>(cand) + warp * 512;
+        for (int p = warp; p < inf.own_n; p += BUILD_WARPS) {
+            const int i = a.ws.atoms[inf.own_beg + p];
+            if (a.cap <= 128) build_row_warp<DIM, 128>(a, i, q, rowbuf);
+            else if (a.cap <= 256) build_row_warp<DIM, 256>(a, i, q, rowbuf);
+            else build_row_warp<DIM, 512>(a, i, q, rowbuf);
         }
+    } else {
+        for (int m = warp; m < inf.nst; m += BUILD_WARPS) {
+            const int b0 = inf.soff[m], n = inf.soff[m + 1] - b0;
+            const float4 *src = a.ws.rsorted + inf.sbeg[m];
+            for (int k = lane; k < n; k += 32) cand[b0 + k] = src[k];
+        }
+        const float nan = __int_as_float(0x7fc00000);
+        for (int k = M + tid; k < padded_m(M); k += BUILD_WARPS * 32)
+            cand[k] = make_float4(nan, nan, nan, __int_as_float(-1));
+        __syncthreads();
+        wmax = inf.inner   ? build_sweep<DIM, 2>(a, cand, inf)
+               : a.wrapped ? build_sweep<DIM, 1>(a, cand, inf)
+                           : build_sweep<DIM, 0>(a, cand, inf);
     }
-    cp_async_wait_all();
     // one atomic per CTA for the largest row count
-    if (lane == 0) atomicMax(&bmax, wmax);
+    if (lane == 0 && wmax > 0) atomicMax(&bmax, wmax);
     __syncthreads();
     if (tid == 0 && bmax > 0) atomicMax(&a.ws.ctl[CTL_MAXCNT], (uint32_t)bmax);
-}
-
-template <int DIM>
-static int build_grid(int ncell, size_t smem)
-{
-    static int per_sm = 0, sms = 0;
-    static size_t smem_seen = 0;
-    if (!per_sm || smem_seen != smem) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_cells<DIM>, BUILD_WARPS * 32, smem);
-        if (per_sm < 1) per_sm = 1;
-        if (sms < 1) sms = 1;
-        smem_seen = smem;
-    }
-    const int g = per_sm * sms;
-    return (BUILD_NBUF == 1 || ncell < g) ? ncell : g;   // one buffer: one cell per CTA
 }
 
 // Sets the rebuild flag if any particle moved more than skin/2 (minimum
@@ -598,6 +439,7 @@ NbrArgs make_nbr_args(const md_space *s, const float *d_r, const md_nbr *nb, uin
     a.r_list2 = nb->r_list2;
     a.r = (const float4 *)d_r;
     a.nbr = nb->nbr;
+    a.lrow = ws_ptrs(nb).lrow;
     a.cnt = nb->cnt;
     a.rref = (float4 *)nb->rref;
     a.ws = ws_ptrs(nb);
@@ -616,10 +458,8 @@ void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st)
     k_scan<<<1, 1024, 0, st>>>(a, ncell_total);
     k_scatter<<<nb, tb, 0, st>>>(a);
     k_sort_cells<<<(ncell_total + SORT_WARPS - 1) / SORT_WARPS, SORT_WARPS * 32, 0, st>>>(a, ncell_total);
-    const size_t smem = build_smem_bytes(a.cap);
-    const int vec_rows = (a.cap % 4 == 0 && ((uintptr_t)a.nbr & 15) == 0) ? 1 : 0;
-    if (a.dim == 3) k_build_cells<3><<<build_grid<3>(ncell_total, smem), BUILD_WARPS * 32, smem, st>>>(a, ncell_total, vec_rows);
-    else k_build_cells<2><<<build_grid<2>(ncell_total, smem), BUILD_WARPS * 32, smem, st>>>(a, ncell_total, vec_rows);
+    if (a.dim == 3) k_build_cells<3><<<ncell_total, BUILD_WARPS * 32, 0, st>>>(a);
+    else k_build_cells<2><<<ncell_total, BUILD_WARPS * 32, 0, st>>>(a);
     if (a.canonical) {
         int g = (a.N + 7) / 8;
         g = g < 4096 ? g : 4096;
@@ -646,7 +486,8 @@ void enqueue_check_disp(const md_space *s, const float *d_r, const md_nbr *nb, c
 
 static bool nbr_ready(const md_nbr *nb)
 {
-    return nb && nb->nbr && nb->cnt && nb->rref && nb->ws && nb->N > 0 && nb->cap > 0 && nb->cap <= 512;
+    return nb && nb->nbr && nb->cnt && nb->rref && nb->ws && nb->N > 0 && nb->cap > 0 && nb->cap <= 512 &&
+           nbr_layout_ok(nb);
 }
 
 }  // namespace jmd
@@ -684,8 +525,18 @@ extern "C" md_status md_nbr_plan(const md_space *s, int N, float r_cut, float sk
         }
         nb.ncell_total *= nb.ncell[k];
     }
-    nb.ws_bytes = ws_layout(N, nb.ncell_total).total;
+    nb.flags = 0;
+    nb.ws_bytes = ws_layout(N, nb.ncell_total, cap, 0).total;
     *out = nb;
+    return MD_OK;
+}
+
+extern "C" md_status md_nbr_set_flags(md_nbr *nb, int flags)
+{
+    if (!nb || (flags & ~(MD_NBR_CANONICAL | MD_NBR_LOCAL_ROWS))) return MD_ERR_INVALID;
+    if ((flags & MD_NBR_CANONICAL) && (flags & MD_NBR_LOCAL_ROWS)) return MD_ERR_INVALID;
+    nb->flags = flags;
+    nb->ws_bytes = ws_layout(nb->N, nb->ncell_total, nb->cap, flags).total;
     return MD_OK;
 }
 
@@ -693,6 +544,7 @@ extern "C" md_status md_nbr_bind(md_nbr *nb, int32_t *d_nbr, int32_t *d_cnt, flo
                                  md_stream_t stream)
 {
     if (!nb || !d_nbr || !d_cnt || !d_rref || !d_ws) return MD_ERR_INVALID;
+    if (!nbr_layout_ok(nb)) return MD_ERR_INVALID;
     if (((uintptr_t)d_ws & 255u) || ((uintptr_t)d_rref & 15u) || ((uintptr_t)d_nbr & 15u)) return MD_ERR_INVALID;
     nb->nbr = d_nbr;
     nb->cnt = d_cnt;

@@ -10,6 +10,7 @@
 // closing half-kick v += dt/2 F/m of velocity Verlet and the block emits
 // FP64 partial sums of potential and kinetic energy; the last block to
 // finish (ticket) adds the partials in a fixed order.
+#include "cells.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
@@ -17,13 +18,14 @@
 namespace jmd {
 
 // One neighbor pair: accumulates F_i and the pair energy into the lane's sums.
-// INNER: the particle is away from every face (see dist2_inner).
-template <int DIM, int POT, bool INNER = false>
+// (The comparison-based nearest image, which pays off in the issue-bound
+// neighbor build, measured slower here, where the gathers bound the time.)
+template <int DIM, int POT>
 __device__ __forceinline__ void pair_term(const PairArgs &a, const float4 &ri, const float4 &rj, float &fx, float &fy,
                                           float &fz, float &e)
 {
     float dx, dy, dz;
-    float r2 = INNER ? dist2_inner<DIM>(ri, rj, dx, dy, dz) : dist2_rn<DIM>(ri, rj, a.box, dx, dy, dz);
+    float r2 = dist2_rn<DIM>(ri, rj, a.box, dx, dy, dz);
     if (POT == MD_LJ) {
         if (r2 < a.rc2) {
             float ir2 = __fdividef(1.0f, r2);
@@ -62,7 +64,7 @@ __device__ __forceinline__ void pair_term(const PairArgs &a, const float4 &ri, c
 // The lanes of a group take consecutive entries of the row, so one gather
 // instruction touches few cache lines; four entries per lane per trip keep
 // four gathers in flight; row entries bypass L1.
-template <int DIM, int TPP, int POT, bool INNER, bool STREAM>
+template <int DIM, int TPP, int POT, bool STREAM>
 __device__ __forceinline__ void pair_loop(const PairArgs &a, int i, int n, const int32_t *row, const float4 &ri,
                                           int lg, float &fx, float &fy, float &fz, float &e)
 {
@@ -76,10 +78,10 @@ __device__ __forceinline__ void pair_loop(const PairArgs &a, int i, int n, const
         float4 r1 = __ldg(a.r + j1);
         float4 r2 = __ldg(a.r + j2);
         float4 r3 = __ldg(a.r + j3);
-        pair_term<DIM, POT, INNER>(a, ri, r0, fx, fy, fz, e);
-        if (k1 < n) pair_term<DIM, POT, INNER>(a, ri, r1, fx, fy, fz, e);
-        if (k2 < n) pair_term<DIM, POT, INNER>(a, ri, r2, fx, fy, fz, e);
-        if (k3 < n) pair_term<DIM, POT, INNER>(a, ri, r3, fx, fy, fz, e);
+        pair_term<DIM, POT>(a, ri, r0, fx, fy, fz, e);
+        if (k1 < n) pair_term<DIM, POT>(a, ri, r1, fx, fy, fz, e);
+        if (k2 < n) pair_term<DIM, POT>(a, ri, r2, fx, fy, fz, e);
+        if (k3 < n) pair_term<DIM, POT>(a, ri, r3, fx, fy, fz, e);
     }
 }
 
@@ -104,15 +106,7 @@ __global__ void __launch_bounds__(256) k_pair(PairArgs a)
             int n = __ldg(a.cnt + i);
             n = n < a.cap ? n : a.cap;
             const int32_t *row = a.nbr + (size_t)i * a.cap;
-            // interior particles skip the wrap arithmetic (same bits)
-            bool inner = (OPT & 2) != 0;
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                float x = d == 0 ? ri.x : (d == 1 ? ri.y : ri.z);
-                inner = inner && (x >= a.margin) && (x <= a.box.L[d] - a.margin);
-            }
-            if (inner) pair_loop<DIM, TPP, POT, true, (OPT & 1) != 0>(a, i, n, row, ri, lg, fx, fy, fz, e);
-            else pair_loop<DIM, TPP, POT, false, (OPT & 1) != 0>(a, i, n, row, ri, lg, fx, fy, fz, e);
+            pair_loop<DIM, TPP, POT, (OPT & 1) != 0>(a, i, n, row, ri, lg, fx, fy, fz, e);
         }
 #pragma unroll
         for (int o = TPP / 2; o > 0; o >>= 1) {
@@ -130,6 +124,126 @@ __global__ void __launch_bounds__(256) k_pair(PairArgs a)
     }
     if (!a.E_out && !KICK) return;
     energy_epilogue(pe_acc, ke_acc, a);
+}
+
+// ---------------------------------------------------------------------------
+// Cell-centred pair forces (lists with local rows).  One CTA per cell, grid-
+// stride over the cells: the positions of the cell's stencil candidates are
+// gathered once into shared memory in the staged order of the last build,
+// then each particle's group of TPP lanes reads its 16-bit local row and
+// takes the partners from shared memory.  Entries, their order and the
+// arithmetic are those of k_pair, so the forces are the same bits.  Cells
+// whose stencil was too large to stage use their int32 rows.
+// ---------------------------------------------------------------------------
+constexpr int PC_WARPS = 4;
+
+template <int DIM, int TPP, int POT>
+__device__ __forceinline__ void pair_loop_local(const PairArgs &a, int n, const uint16_t *row, const float4 *cand,
+                                                const float4 &ri, int lg, float &fx, float &fy, float &fz, float &e)
+{
+    for (int k0 = lg; k0 < n; k0 += 4 * TPP) {
+        const int k1 = k0 + TPP, k2 = k0 + 2 * TPP, k3 = k0 + 3 * TPP;
+        const int j0 = ld_stream_u16(row + k0);
+        const int j1 = k1 < n ? ld_stream_u16(row + k1) : 0;
+        const int j2 = k2 < n ? ld_stream_u16(row + k2) : 0;
+        const int j3 = k3 < n ? ld_stream_u16(row + k3) : 0;
+        const float4 r0 = cand[j0], r1 = cand[j1], r2 = cand[j2], r3 = cand[j3];
+        pair_term<DIM, POT>(a, ri, r0, fx, fy, fz, e);
+        if (k1 < n) pair_term<DIM, POT>(a, ri, r1, fx, fy, fz, e);
+        if (k2 < n) pair_term<DIM, POT>(a, ri, r2, fx, fy, fz, e);
+        if (k3 < n) pair_term<DIM, POT>(a, ri, r3, fx, fy, fz, e);
+    }
+}
+
+template <int DIM, int TPP, int POT, int KICK>
+__global__ void __launch_bounds__(PC_WARPS * 32) k_pair_cell(PairArgs a)
+{
+    count_launch();
+    constexpr int GPB = PC_WARPS * 32 / TPP;   // particles per pass
+    __shared__ float4 cand[STAGE_CMAX];
+    __shared__ StencilInfo inf;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lg = tid & (TPP - 1), gl = tid / TPP;
+    float pe_acc = 0.0f, ke_acc = 0.0f;
+    for (int q = blockIdx.x; q < a.ncell; q += gridDim.x) {
+        if (warp == 0) {
+            int beg, cnt;
+            stencil_locate<DIM>(a.nc, a.cell_start, q, lane, beg, cnt);
+            stencil_publish<DIM>(a.nc, 0, q, lane, beg, cnt, inf);
+        }
+        __syncthreads();
+        const bool staged = inf.soff[inf.nst] <= STAGE_CMAX;
+        if (staged) {
+            for (int m = warp; m < inf.nst; m += PC_WARPS) {
+                const int b0 = inf.soff[m], nm = inf.soff[m + 1] - b0;
+                const int32_t *src = a.atoms + inf.sbeg[m];
+                for (int t = lane; t < nm; t += 32) cand[b0 + t] = __ldg(a.r + __ldg(src + t));
+            }
+        }
+        __syncthreads();
+        for (int p0 = 0; p0 < inf.own_n; p0 += GPB) {
+            const int p = p0 + gl;
+            const bool valid = p < inf.own_n;
+            float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+            int i = 0;
+            if (valid) {
+                i = __ldg(a.atoms + inf.own_beg + p);
+                int n = __ldg(a.cnt + i);
+                n = n < a.cap ? n : a.cap;
+                if (staged) {
+                    const float4 ri = cand[inf.own_off + p];
+                    pair_loop_local<DIM, TPP, POT>(a, n, a.lrow + (size_t)i * a.cap, cand, ri, lg, fx, fy, fz, e);
+                } else {
+                    const float4 ri = __ldg(a.r + i);
+                    pair_loop<DIM, TPP, POT, true>(a, i, n, a.nbr + (size_t)i * a.cap, ri, lg, fx, fy, fz, e);
+                }
+            }
+#pragma unroll
+            for (int o = TPP / 2; o > 0; o >>= 1) {
+                fx += __shfl_xor_sync(0xffffffffu, fx, o);
+                fy += __shfl_xor_sync(0xffffffffu, fy, o);
+                fz += __shfl_xor_sync(0xffffffffu, fz, o);
+                e += __shfl_xor_sync(0xffffffffu, e, o);
+            }
+            if (valid && lg == 0) {
+                const float ei = 0.5f * e;
+                a.f[i] = make_float4(fx, fy, fz, ei);
+                pe_acc += ei;
+                if (KICK) ke_acc += half_kick<DIM>(a, i, fx, fy, fz);
+            }
+        }
+        __syncthreads();   // the next cell reuses cand and inf
+    }
+    if (!a.E_out && !KICK) return;
+    energy_epilogue(pe_acc, ke_acc, a);
+}
+
+template <int DIM, int TPP, int POT, int KICK>
+static int pair_cell_grid(const PairArgs &a)
+{
+    static int per_sm = 0, sms = 0;
+    if (!per_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_cell<DIM, TPP, POT, KICK>, PC_WARPS * 32, 0);
+        if (per_sm < 1) per_sm = 1;
+        if (sms < 1) sms = 1;
+    }
+    int g = per_sm * sms;
+    g = a.ncell < g ? a.ncell : g;
+    return g < a.max_blocks ? g : a.max_blocks;
+}
+
+template <int DIM, int POT, int KICK>
+static void launch_pair_cell(const PairArgs &a, cudaStream_t st)
+{
+    switch (a.tpp) {
+    case 4: k_pair_cell<DIM, 4, POT, KICK><<<pair_cell_grid<DIM, 4, POT, KICK>(a), PC_WARPS * 32, 0, st>>>(a); break;
+    case 16: k_pair_cell<DIM, 16, POT, KICK><<<pair_cell_grid<DIM, 16, POT, KICK>(a), PC_WARPS * 32, 0, st>>>(a); break;
+    case 32: k_pair_cell<DIM, 32, POT, KICK><<<pair_cell_grid<DIM, 32, POT, KICK>(a), PC_WARPS * 32, 0, st>>>(a); break;
+    default: k_pair_cell<DIM, 8, POT, KICK><<<pair_cell_grid<DIM, 8, POT, KICK>(a), PC_WARPS * 32, 0, st>>>(a); break;
+    }
 }
 
 // Blocks per launch: enough resident blocks to fill every SM (grid-stride
@@ -151,17 +265,13 @@ static int pair_grid(int N)
     return groups < g ? groups : g;
 }
 
-static int g_pair_opt = 1;   // bit 0: stream rows past L1; bit 1: interior wrap-free path
+static int g_pair_opt = 1;   // bit 0: stream rows past L1
 
 template <int DIM, int TPP, int POT, int KICK>
 static void launch_pair_t(const PairArgs &a, cudaStream_t st)
 {
-    switch (a.opt) {
-    case 0: k_pair<DIM, TPP, POT, KICK, 0><<<pair_grid<DIM, TPP, POT, KICK, 0>(a.N), 256, 0, st>>>(a); break;
-    case 1: k_pair<DIM, TPP, POT, KICK, 1><<<pair_grid<DIM, TPP, POT, KICK, 1>(a.N), 256, 0, st>>>(a); break;
-    case 3: k_pair<DIM, TPP, POT, KICK, 3><<<pair_grid<DIM, TPP, POT, KICK, 3>(a.N), 256, 0, st>>>(a); break;
-    default: k_pair<DIM, TPP, POT, KICK, 2><<<pair_grid<DIM, TPP, POT, KICK, 2>(a.N), 256, 0, st>>>(a); break;
-    }
+    if (a.opt & 1) k_pair<DIM, TPP, POT, KICK, 1><<<pair_grid<DIM, TPP, POT, KICK, 1>(a.N), 256, 0, st>>>(a);
+    else k_pair<DIM, TPP, POT, KICK, 0><<<pair_grid<DIM, TPP, POT, KICK, 0>(a.N), 256, 0, st>>>(a);
 }
 
 template <int DIM, int POT, int KICK>
@@ -178,6 +288,16 @@ static void launch_pair_tpp(const PairArgs &a, cudaStream_t st)
 
 void enqueue_pair(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st)
 {
+    if (a.lrow) {
+        if (dim == 3) {
+            if (pot == MD_LJ) kick ? launch_pair_cell<3, MD_LJ, 1>(a, st) : launch_pair_cell<3, MD_LJ, 0>(a, st);
+            else kick ? launch_pair_cell<3, MD_SOFT_SPHERE, 1>(a, st) : launch_pair_cell<3, MD_SOFT_SPHERE, 0>(a, st);
+        } else {
+            if (pot == MD_LJ) kick ? launch_pair_cell<2, MD_LJ, 1>(a, st) : launch_pair_cell<2, MD_LJ, 0>(a, st);
+            else kick ? launch_pair_cell<2, MD_SOFT_SPHERE, 1>(a, st) : launch_pair_cell<2, MD_SOFT_SPHERE, 0>(a, st);
+        }
+        return;
+    }
     if (dim == 3) {
         if (pot == MD_LJ) kick ? launch_pair_tpp<3, MD_LJ, 1>(a, st) : launch_pair_tpp<3, MD_LJ, 0>(a, st);
         else kick ? launch_pair_tpp<3, MD_SOFT_SPHERE, 1>(a, st) : launch_pair_tpp<3, MD_SOFT_SPHERE, 0>(a, st);
@@ -200,7 +320,7 @@ static int g_tpp = 4;
 
 bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const md_nbr *nb, float *d_f, PairArgs &a)
 {
-    if (!s || !p || !d_r || !nb || !d_f || !nb->nbr || !nb->cnt || !nb->ws) return false;
+    if (!s || !p || !d_r || !nb || !d_f || !nb->nbr || !nb->cnt || !nb->ws || !nbr_layout_ok(nb)) return false;
     if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE && p->kind != MD_SW && p->kind != MD_BP) return false;
     if ((p->kind == MD_SW || p->kind == MD_BP) && s->dim != 3) return false;
     memset(&a, 0, sizeof(a));
@@ -216,9 +336,13 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
     a.partials = w.partials;
     // canonical lists: one thread sums a particle's pairs in row order
     a.tpp = (nb->flags & MD_NBR_CANONICAL) ? 1 : g_tpp;
-    // beyond this distance from every face all list partners are unwrapped
-    a.margin = nb->r_list + nb->skin;
     a.opt = g_pair_opt;
+    a.lrow = w.lrow;
+    a.atoms = w.atoms;
+    a.cell_start = w.cell_start;
+    for (int k = 0; k < 3; ++k) a.nc[k] = nb->ncell[k];
+    a.ncell = nb->ncell_total;
+    a.max_blocks = w.max_blocks;
     if (p->kind == MD_LJ) {
         if (p->r_cut > nb->r_list) return false;
         float rc = p->r_cut;
@@ -256,7 +380,7 @@ using namespace jmd;
 
 extern "C" md_status md_set_pair_options(int opt)
 {
-    if (opt < 0 || opt > 3) return MD_ERR_INVALID;
+    if (opt < 0 || opt > 1) return MD_ERR_INVALID;
     g_pair_opt = opt;
     return MD_OK;
 }

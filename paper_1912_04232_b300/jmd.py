@@ -33,6 +33,7 @@ MD_ERR_CUDA = 64
 
 MD_LJ, MD_SOFT_SPHERE, MD_SW, MD_BP = 0, 1, 2, 3
 MD_NBR_CANONICAL = 1
+MD_NBR_LOCAL_ROWS = 2
 
 STATUS_NAMES = {MD_ERR_INVALID: "INVALID", MD_ERR_BOX_TOO_SMALL: "BOX_TOO_SMALL",
                 MD_ERR_NBR_OVERFLOW: "NBR_OVERFLOW", MD_ERR_NONFINITE: "NONFINITE",
@@ -85,6 +86,7 @@ _vp = C.c_void_p
 _SIGS = {
     "md_space_periodic": [C.c_int, _P(C.c_double), _P(md_space)],
     "md_nbr_plan": [_P(md_space), C.c_int, C.c_float, C.c_float, C.c_int, _P(md_nbr)],
+    "md_nbr_set_flags": [_P(md_nbr), C.c_int],
     "md_nbr_bind": [_P(md_nbr), _vp, _vp, _vp, _vp, _vp],
     "md_neighbor_list_build": [_P(md_space), _vp, _P(md_nbr), _vp, _vp],
     "md_neighbor_list_update": [_P(md_space), _vp, _P(md_nbr), _vp, _vp],
@@ -180,6 +182,10 @@ def md_nbr_plan(space: md_space, N: int, r_cut: float, skin: float, cap: int) ->
     _check(_lib.md_nbr_plan(C.byref(space), int(N), float(r_cut), float(skin), int(cap), C.byref(out)),
            "md_nbr_plan")
     return out
+
+
+def md_nbr_set_flags(nb: md_nbr, flags: int):
+    _check(_lib.md_nbr_set_flags(C.byref(nb), int(flags)), "md_nbr_set_flags")
 
 
 def md_nbr_bind(nb: md_nbr, nbr, cnt, rref, ws, stream=None):
@@ -456,12 +462,13 @@ class NeighborList:
     """Plans a list, allocates its caller-owned tensors with torch and binds them."""
 
     def __init__(self, space: md_space, N: int, r_cut: float, skin: float, cap: int, device="cuda", stream=None,
-                 canonical: bool = False):
+                 canonical: bool = False, local_rows: bool = False):
         import torch
         self.space = space
         self.plan = md_nbr_plan(space, N, r_cut, skin, cap)
-        if canonical:
-            self.plan.flags |= MD_NBR_CANONICAL
+        flags = (MD_NBR_CANONICAL if canonical else 0) | (MD_NBR_LOCAL_ROWS if local_rows else 0)
+        if flags:
+            md_nbr_set_flags(self.plan, flags)
         self.nbr = torch.empty((N, cap), dtype=torch.int32, device=device)
         self.cnt = torch.zeros(N, dtype=torch.int32, device=device)
         self.rref = torch.zeros((N, 4), dtype=torch.float32, device=device)
