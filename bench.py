@@ -273,8 +273,12 @@ def batched_section(steps=500):
 
 
 def _source_sha():
+    """Hash of the sources of the pair-force kernels (a stored DRAM-traffic
+    figure is only reported while it still describes the built kernel)."""
     h = hashlib.sha256()
-    for p in ("paper_1912_04232_b300/csrc/pair.cu", "paper_1912_04232_b300/csrc/common.cuh"):
+    for p in ("paper_1912_04232_b300/csrc/pair.cu", "paper_1912_04232_b300/csrc/common.cuh",
+              "paper_1912_04232_b300/csrc/kernels.cuh", "paper_1912_04232_b300/csrc/reduce.cuh",
+              "paper_1912_04232_b300/csrc/cells.cuh"):
         with open(os.path.join(ROOT, p), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -432,7 +436,7 @@ def main():
     traffic = None
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        ent = tr.get("k_pair_lj", {})
+        ent = tr.get("k_pair_cell_lj" if args.local_rows else "k_pair_lj", {})
         if ent.get("source_sha") == _source_sha() and ent.get("N") == c.N:
             traffic = ent.get("dram_bytes_per_launch")
     except (OSError, ValueError):
