@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--tpp", type=int, default=0)
     ap.add_argument("--pair-opt", type=int, default=-1, help="pair-kernel variant (md_set_pair_options)")
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel from the host (profiling)")
+    ap.add_argument("--nve-fusion", type=int, default=1, help="1: kick-drift fused into the force kernel (md_set_nve_fusion)")
     ap.add_argument("--local-rows", type=int, default=0,
                     help="1: cell-centred forces over 16-bit local rows (MD_NBR_LOCAL_ROWS); 0: int32 rows")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain-SW section")
@@ -319,6 +320,7 @@ def main():
         P.md_set_pair_tpp(args.tpp)
     if args.pair_opt >= 0:
         P.md_set_pair_options(args.pair_opt)
+    P.md_set_nve_fusion(bool(args.nve_fusion))
     s = P.md_space_periodic(3, [c.L] * 3)
     nl = P.NeighborList(s, c.N, c.r_cut, c.skin, 128, local_rows=bool(args.local_rows))
     pot = P.lj_pot(c.eps, c.sigma, c.r_cut, True)
@@ -459,6 +461,7 @@ def main():
                        "max_energy_drift_per_particle": drift, "l2": "flushed between bench steps",
                        "parallelism": f"replicas{world}", "pair_tpp": args.tpp or 4,
                        "neighbor_rows": "int32 + 16-bit local" if args.local_rows else "int32",
+                       "kick_drift": "fused into the force kernel" if args.nve_fusion and not args.local_rows else "separate kernel",
                        "loop": "host launches" if args.no_graph else "one CUDA graph (device WHILE/IF)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": ("k_pair_cell<LJ>" if args.local_rows else "k_pair<LJ>") + " (md_energy_forces)",

@@ -229,6 +229,13 @@ JMD_API md_status md_set_pair_tpp(int tpp);
  * opt = 0 through it.  Other values: MD_ERR_INVALID. */
 JMD_API md_status md_set_pair_options(int opt);
 
+/* NVE with Lennard-Jones or soft-sphere forces on int32 rows: 1 (default)
+ * fuses each step's kick-drift into the previous step's force kernel, with
+ * the positions alternating between d_r and a workspace buffer (the final
+ * positions are copied back to d_r); 0 runs the separate kick-drift kernel.
+ * Both give the same bits.  MD_ERR_INVALID for other values. */
+JMD_API md_status md_set_nve_fusion(int on);
+
 /* ------------------------------------------------------------------------ */
 /* Dynamics (Sec. 3.3.1).                                                   */
 /* ------------------------------------------------------------------------ */

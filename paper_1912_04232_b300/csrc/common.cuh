@@ -233,7 +233,7 @@ __device__ __forceinline__ double block_sum_f64(double v, double *sh)
 // Workspace layout of a neighbor list (all offsets 256-byte aligned).
 // ---------------------------------------------------------------------------
 struct WsLayout {
-    size_t ctl, cell_count, cell_start, cell_of, rank, atoms_u, atoms, rsorted, partials, lrow, total;
+    size_t ctl, cell_count, cell_start, cell_of, rank, atoms_u, atoms, rsorted, ralt, partials, lrow, total;
     int max_blocks;
 };
 
@@ -252,6 +252,7 @@ __host__ inline WsLayout ws_layout(int N, int ncell_total, int cap, int flags)
     w.atoms_u = o;      o = align256(o + sizeof(int32_t) * (size_t)N);
     w.atoms = o;        o = align256(o + sizeof(int32_t) * (size_t)N);
     w.rsorted = o;      o = align256(o + sizeof(float4) * (size_t)N);
+    w.ralt = o;         o = align256(o + sizeof(float4) * (size_t)N);
     w.max_blocks = N / 4 + 64;
     w.partials = o;     o = align256(o + sizeof(double2) * (size_t)w.max_blocks);
     w.lrow = o;
@@ -264,6 +265,7 @@ struct WsPtrs {
     uint32_t *ctl;
     int32_t *cell_count, *cell_start, *cell_of, *rank, *atoms_u, *atoms;
     float4 *rsorted;
+    float4 *ralt;     // second position buffer of the fused NVE step
     double2 *partials;
     uint16_t *lrow;   // NULL without MD_NBR_LOCAL_ROWS
     int max_blocks;
@@ -282,6 +284,7 @@ __host__ inline WsPtrs ws_ptrs(const md_nbr *nb)
     p.atoms_u = (int32_t *)(b + w.atoms_u);
     p.atoms = (int32_t *)(b + w.atoms);
     p.rsorted = (float4 *)(b + w.rsorted);
+    p.ralt = (float4 *)(b + w.ralt);
     p.partials = (double2 *)(b + w.partials);
     p.lrow = (nb->flags & MD_NBR_LOCAL_ROWS) ? (uint16_t *)(b + w.lrow) : nullptr;
     p.max_blocks = w.max_blocks;

@@ -140,6 +140,15 @@ __global__ void __launch_bounds__(256) k_gd_step(float4 *r, const float4 *f, con
     if (__any_sync(0xffffffffu, mv) && (threadIdx.x & 31) == 0) ctl[CTL_REBUILD] = 1u;
 }
 
+// Fused NVE loop: positions alternate between r and r_alt, so after an even
+// number of steps the final positions are in r_alt.
+__global__ void __launch_bounds__(256) k_final_positions(float4 *r, const float4 *r_alt, int N, const uint32_t *ctl)
+{
+    count_launch();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N && (ctl[CTL_NSTEPS] & 1u) == 0u) r[i] = r_alt[i];
+}
+
 __global__ void k_loop_init(uint32_t *ctl, uint32_t nsteps, uint32_t step0, unsigned long long seed)
 {
     count_launch();
@@ -161,6 +170,7 @@ struct NveCtx {
     PairArgs pa;
     int pot;
     int langevin;                 // 0: NVE kick-drift, 1: BAOAB first part
+    int fused;                    // 1: kick-drift fused into the force kernel (pair potentials, NVE)
     float c1, c2;                 // Langevin O-step coefficients
     unsigned long long cond_if;   // graph IF handle (0 outside graphs)
 };
@@ -196,9 +206,14 @@ static void enqueue_kick_drift(const NveCtx &c, int cond, cudaStream_t st)
 
 static void enqueue_nve_step(const NveCtx &c, cudaStream_t st)
 {
-    enqueue_kick_drift(c, 0, st);
+    if (!c.fused) enqueue_kick_drift(c, 0, st);
     enqueue_rebuild_chain(c.na, c.ncell_total, st);
-    enqueue_forces(c.pa, c.dim, c.pot, 1, st);
+    enqueue_forces(c.pa, c.dim, c.pot, c.fused ? 2 : 1, st);
+}
+
+static void enqueue_final_positions(const NveCtx &c, cudaStream_t st)
+{
+    k_final_positions<<<(c.N + 255) / 256, 256, 0, st>>>(c.r, c.pa.r_alt, c.N, c.ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -206,8 +221,12 @@ static void enqueue_nve_step(const NveCtx &c, cudaStream_t st)
 // with the rebuild chain under an IF node.  The kick-drift kernel's last
 // block sets the IF condition from the device rebuild flag; the force
 // kernel's last block advances the step counter and sets the WHILE
-// condition.  No host involvement per step and no launches of an idle
-// rebuild chain.  Graphs are cached per argument set and device.
+// condition.  Fused loop: the first kick-drift runs before the WHILE node
+// (and sets the first IF condition), the body is IF(rebuild) + the fused
+// force kernel, whose last block also sets the next IF condition, and a copy
+// after the loop returns the final positions to the caller's buffer.  No
+// host involvement per step and no launches of an idle rebuild chain.
+// Graphs are cached per argument set and device.
 // ---------------------------------------------------------------------------
 struct NveGraph {
     NveCtx key;
@@ -239,18 +258,34 @@ static md_status build_nve_graph(const NveCtx &c0, NveGraph &out)
     wp->conditional.handle = hw;
     wp->conditional.type = cudaGraphCondTypeWhile;
     wp->conditional.size = 1;
-    cudaGraphNode_t wn;
-    JMD_CUDA_TRY(cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, wp));
-    cudaGraph_t body = wp->conditional.phGraph_out[0];
-
     cudaStream_t cs = nullptr, cs2 = nullptr;
     JMD_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     JMD_CUDA_TRY(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
-    JMD_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     c.cond_if = (unsigned long long)hi;
     c.pa.cond_while = (unsigned long long)hw;
     c.pa.use_cond = 1;
-    enqueue_kick_drift(c, 1, cs);
+    if (c.fused) c.pa.cond_if = (unsigned long long)hi;
+    cudaGraphNode_t wn;
+    if (c.fused) {
+        // top level: first kick-drift -> WHILE -> final copy
+        JMD_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        enqueue_kick_drift(c, 1, cs);
+        cudaStreamCaptureStatus tst;
+        cudaGraph_t tg = nullptr;
+        const cudaGraphNode_t *tdeps = nullptr;
+        size_t tnd = 0;
+        JMD_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &tst, nullptr, &tg, &tdeps, nullptr, &tnd));
+        JMD_CUDA_TRY(cudaGraphAddNode(&wn, tg, tdeps, nullptr, tnd, wp));
+        JMD_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+        enqueue_final_positions(c, cs);
+        JMD_CUDA_TRY(cudaStreamEndCapture(cs, &g));
+    } else {
+        JMD_CUDA_TRY(cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, wp));
+    }
+    cudaGraph_t body = wp->conditional.phGraph_out[0];
+
+    JMD_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    if (!c.fused) enqueue_kick_drift(c, 1, cs);
 
     cudaStreamCaptureStatus cst;
     cudaGraph_t cg = nullptr;
@@ -273,7 +308,7 @@ static md_status build_nve_graph(const NveCtx &c0, NveGraph &out)
     enqueue_rebuild_chain(na, c.ncell_total, cs2);
     JMD_CUDA_TRY(cudaStreamEndCapture(cs2, &ibody));
 
-    enqueue_forces(c.pa, c.dim, c.pot, 1, cs);
+    enqueue_forces(c.pa, c.dim, c.pot, c.fused ? 2 : 1, cs);
     JMD_CUDA_TRY(cudaStreamEndCapture(cs, &body));
     cudaStreamDestroy(cs2);
     cudaStreamDestroy(cs);
@@ -329,6 +364,8 @@ void enqueue_gd_step(const md_space *s, float *d_r, const float *d_f, const md_n
 
 using namespace jmd;
 
+static int g_fuse_nve = 1;   // md_set_nve_fusion
+
 static md_status run_dynamics(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f, float mass,
                               float dt, int nsteps, md_nbr *nb, double *d_PE, double *d_KE, int use_graph,
                               uint32_t *d_status, cudaStream_t st, int langevin, float gamma, float kT,
@@ -369,10 +406,23 @@ static md_status run_dynamics(const md_space *s, const md_pot *p, float *d_r, fl
         c.c1 = (float)e;
         c.c2 = (float)sqrt((1.0 - e * e) * (double)kT / (double)mass);
     }
+    // pair potentials in NVE with int32 rows: kick-drift fused into the force
+    // kernel, positions alternating with the workspace buffer
+    c.fused = (!langevin && (p->kind == MD_LJ || p->kind == MD_SOFT_SPHERE) && !c.pa.lrow && g_fuse_nve) ? 1 : 0;
+    if (c.fused) {
+        const WsPtrs w = ws_ptrs(nb);
+        c.pa.r_alt = w.ralt;
+        c.pa.rref = (const float4 *)nb->rref;
+        c.pa.dt = dt;
+        c.pa.half_skin2 = nb->half_skin2;
+        c.na.r_alt = w.ralt;
+    }
     if (nsteps == 0) return MD_OK;
     if (use_graph) return nve_graph_run(c, nsteps, step0, seed, st);
     k_loop_init<<<1, 1, 0, st>>>(c.ctl, (uint32_t)nsteps, step0, seed);
+    if (c.fused) enqueue_kick_drift(c, 0, st);
     for (int k = 0; k < nsteps; ++k) enqueue_nve_step(c, st);
+    if (c.fused) enqueue_final_positions(c, st);
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
 }
@@ -383,6 +433,13 @@ extern "C" md_status md_integrate_nve(const md_space *s, const md_pot *p, float 
 {
     return run_dynamics(s, p, d_r, d_v, d_f, mass, dt, nsteps, nb, d_PE, d_KE, use_graph, d_status,
                         (cudaStream_t)stream, 0, 0.0f, 0.0f, 0ull, 0u);
+}
+
+extern "C" md_status md_set_nve_fusion(int on)
+{
+    if (on != 0 && on != 1) return MD_ERR_INVALID;
+    g_fuse_nve = on;
+    return MD_OK;
 }
 
 extern "C" md_status md_integrate_langevin(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f,

@@ -18,6 +18,7 @@ struct NbrArgs {
     float4 *rref;
     WsPtrs ws;
     uint32_t *status;
+    const float4 *r_alt;  // fused NVE: positions alternate between r and r_alt by the parity of ctl[CTL_STEP]
     int gated;       // 1: run only if ctl[CTL_REBUILD] != 0
     int canonical;   // 1: sort every row ascending after the build
     int wrapped;     // 1: positions are inside [0, L) (integrators), enabling the wrap-free path
@@ -33,6 +34,11 @@ struct PairArgs {
     float4 *v;              // KICK only
     float half_dt_over_m;   // KICK only
     float mass;             // KICK only (kinetic energy)
+    // fused NVE step (KICK == 2): the next kick-drift into the other buffer
+    float4 *r_alt;          // positions alternate between r and r_alt by the parity of ctl[CTL_STEP]
+    const float4 *rref;     // positions at the last build (displacement check)
+    float dt, half_skin2;
+    unsigned long long cond_if;   // graph IF handle of the rebuild chain (0: none)
     // LJ
     float rc2, sigma2, c24eps, c4eps, e_shift;
     // soft sphere

@@ -32,6 +32,13 @@ __device__ __forceinline__ int cell_axis(float x, float L, float Linv, float sca
     return q < 0 ? 0 : (q >= n ? n - 1 : q);
 }
 
+// Positions the chain bins and stages: r, or in the fused NVE loop the buffer
+// of the current step (odd steps in r_alt).
+__device__ __forceinline__ const float4 *chain_positions(const NbrArgs &a)
+{
+    return (a.r_alt && (*(volatile uint32_t *)&a.ws.ctl[CTL_STEP] & 1u)) ? a.r_alt : a.r;
+}
+
 __device__ __forceinline__ bool chain_active(const NbrArgs &a)
 {
     return !a.gated || *(volatile uint32_t *)&a.ws.ctl[CTL_REBUILD] != 0u;
@@ -45,7 +52,7 @@ __global__ void __launch_bounds__(256) k_bin_count(NbrArgs a)
     bool act = i < a.N;
     int c = -1;
     if (act) {
-        float4 p = a.r[i];
+        float4 p = chain_positions(a)[i];
         // a non-finite coordinate would silently drop out of every pair test
         if (!isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z)) raise_status(a.status, MD_ERR_NONFINITE);
         int cx = cell_axis(p.x, a.box.L[0], a.box.Linv[0], a.cell_scale[0], a.nc[0]);
@@ -140,7 +147,7 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_sort_cells(NbrArgs a, int n
             for (int t = 0; t < 32; ++t) rk += (__shfl_sync(0xffffffffu, other, t) < me);
         }
         if (k < n) {
-            const float4 p = a.r[me];
+            const float4 p = chain_positions(a)[me];
             a.ws.atoms[b + rk] = me;
             a.ws.rsorted[b + rk] = make_float4(p.x, p.y, p.z, __int_as_float(me));   // index in w
             a.rref[me] = p;   // positions of this build (displacement check)
@@ -219,7 +226,7 @@ template <int DIM, int CAPP2>
 __device__ void build_row_warp(const NbrArgs &a, int i, int c, int *row)
 {
     const int lane = threadIdx.x & 31;
-    float4 ri = a.r[i];
+    float4 ri = chain_positions(a)[i];
     int cx = c % a.nc[0];
     int cy = (c / a.nc[0]) % a.nc[1];
     int cz = c / (a.nc[0] * a.nc[1]);

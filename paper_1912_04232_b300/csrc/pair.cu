@@ -65,8 +65,8 @@ __device__ __forceinline__ void pair_term(const PairArgs &a, const float4 &ri, c
 // instruction touches few cache lines; four entries per lane per trip keep
 // four gathers in flight; row entries bypass L1.
 template <int DIM, int TPP, int POT, bool STREAM>
-__device__ __forceinline__ void pair_loop(const PairArgs &a, int i, int n, const int32_t *row, const float4 &ri,
-                                          int lg, float &fx, float &fy, float &fz, float &e)
+__device__ __forceinline__ void pair_loop(const PairArgs &a, const float4 *rp, int i, int n, const int32_t *row,
+                                          const float4 &ri, int lg, float &fx, float &fy, float &fz, float &e)
 {
     for (int k0 = lg; k0 < n; k0 += 4 * TPP) {
         const int k1 = k0 + TPP, k2 = k0 + 2 * TPP, k3 = k0 + 3 * TPP;
@@ -74,10 +74,10 @@ __device__ __forceinline__ void pair_loop(const PairArgs &a, int i, int n, const
         int j1 = k1 < n ? (STREAM ? ld_stream(row + k1) : __ldg(row + k1)) : i;
         int j2 = k2 < n ? (STREAM ? ld_stream(row + k2) : __ldg(row + k2)) : i;
         int j3 = k3 < n ? (STREAM ? ld_stream(row + k3) : __ldg(row + k3)) : i;
-        float4 r0 = __ldg(a.r + j0);
-        float4 r1 = __ldg(a.r + j1);
-        float4 r2 = __ldg(a.r + j2);
-        float4 r3 = __ldg(a.r + j3);
+        float4 r0 = __ldg(rp + j0);
+        float4 r1 = __ldg(rp + j1);
+        float4 r2 = __ldg(rp + j2);
+        float4 r3 = __ldg(rp + j3);
         pair_term<DIM, POT>(a, ri, r0, fx, fy, fz, e);
         if (k1 < n) pair_term<DIM, POT>(a, ri, r1, fx, fy, fz, e);
         if (k2 < n) pair_term<DIM, POT>(a, ri, r2, fx, fy, fz, e);
@@ -85,9 +85,44 @@ __device__ __forceinline__ void pair_loop(const PairArgs &a, int i, int n, const
     }
 }
 
+// Fused NVE step (KICK == 2), lane 0 of particle i's group: the closing
+// half-kick of this step (kinetic energy at v(t)), then, unless this is the
+// loop's last step, the next step's kick-drift into the other position
+// buffer and its displacement check.  The arithmetic repeats half_kick and
+// k_kick_drift expression by expression, so the trajectory has the same bits
+// as the unfused step.  Returns the kinetic energy; *moved reports the check.
+template <int DIM>
+__device__ __forceinline__ float kick_kick_drift(const PairArgs &a, int i, float4 ri, float fx, float fy, float fz,
+                                                 bool more, float4 *rn, bool *moved)
+{
+    float4 vi = a.v[i];
+    const float4 rr = more ? a.rref[i] : ri;
+    vi.x += a.half_dt_over_m * fx;
+    vi.y += a.half_dt_over_m * fy;
+    if (DIM == 3) vi.z += a.half_dt_over_m * fz;
+    const float ke = 0.5f * a.mass * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
+    *moved = false;
+    if (more) {
+        vi.x += a.half_dt_over_m * fx;
+        vi.y += a.half_dt_over_m * fy;
+        ri.x = wrap_coord(ri.x + a.dt * vi.x, a.box.L[0], a.box.Linv[0]);
+        ri.y = wrap_coord(ri.y + a.dt * vi.y, a.box.L[1], a.box.Linv[1]);
+        if (DIM == 3) {
+            vi.z += a.half_dt_over_m * fz;
+            ri.z = wrap_coord(ri.z + a.dt * vi.z, a.box.L[2], a.box.Linv[2]);
+        }
+        rn[i] = ri;
+        float dx, dy, dz;
+        *moved = dist2_rn<DIM>(ri, rr, a.box, dx, dy, dz) > a.half_skin2;
+    }
+    a.v[i] = vi;
+    return ke;
+}
+
 // Grid-stride over groups of PPB = 256/TPP particles.  Energies accumulate per thread in FP32 over the particles it
 // owns, per warp in FP32, across the block's 8 warps in FP64, and across
-// blocks in FP64 (fixed order, last block).
+// blocks in FP64 (fixed order, last block).  KICK: 0 forces only, 1 forces
+// and the closing half-kick, 2 the fused step (kick_kick_drift).
 template <int DIM, int TPP, int POT, int KICK, int OPT>
 __global__ void __launch_bounds__(256) k_pair(PairArgs a)
 {
@@ -95,18 +130,29 @@ __global__ void __launch_bounds__(256) k_pair(PairArgs a)
     constexpr int PPB = 256 / TPP;
     const int lg = threadIdx.x & (TPP - 1);
     const int gl = threadIdx.x / TPP;
+    // fused step: this step's positions and the buffer of the next
+    const float4 *rc = a.r;
+    float4 *rn = nullptr;
+    bool more = false;
+    if (KICK == 2) {
+        const uint32_t step = *(volatile uint32_t *)&a.ctl[CTL_STEP];
+        rc = (step & 1u) ? a.r_alt : a.r;
+        rn = (step & 1u) ? const_cast<float4 *>(a.r) : a.r_alt;
+        more = step + 1u < *(volatile uint32_t *)&a.ctl[CTL_NSTEPS];
+    }
     float pe_acc = 0.0f, ke_acc = 0.0f;
+    bool moved_any = false;
     for (int base = blockIdx.x * PPB; base < a.N; base += gridDim.x * PPB) {
         int i = base + gl;
         bool valid = i < a.N;
         float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
         float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
         if (valid) {
-            ri = __ldg(a.r + i);
+            ri = __ldg(rc + i);
             int n = __ldg(a.cnt + i);
             n = n < a.cap ? n : a.cap;
             const int32_t *row = a.nbr + (size_t)i * a.cap;
-            pair_loop<DIM, TPP, POT, (OPT & 1) != 0>(a, i, n, row, ri, lg, fx, fy, fz, e);
+            pair_loop<DIM, TPP, POT, (OPT & 1) != 0>(a, rc, i, n, row, ri, lg, fx, fy, fz, e);
         }
 #pragma unroll
         for (int o = TPP / 2; o > 0; o >>= 1) {
@@ -119,8 +165,17 @@ __global__ void __launch_bounds__(256) k_pair(PairArgs a)
             float ei = 0.5f * e;
             a.f[i] = make_float4(fx, fy, fz, ei);
             pe_acc += ei;
-            if (KICK) ke_acc += half_kick<DIM>(a, i, fx, fy, fz);
+            if (KICK == 1) ke_acc += half_kick<DIM>(a, i, fx, fy, fz);
+            if (KICK == 2) {
+                bool mv;
+                ke_acc += kick_kick_drift<DIM>(a, i, ri, fx, fy, fz, more, rn, &mv);
+                moved_any = moved_any || mv;
+            }
         }
+    }
+    if (KICK == 2 && __any_sync(0xffffffffu, moved_any) && (threadIdx.x & 31) == 0) {
+        a.ctl[CTL_REBUILD] = 1u;
+        __threadfence();
     }
     if (!a.E_out && !KICK) return;
     energy_epilogue(pe_acc, ke_acc, a);
@@ -195,7 +250,7 @@ __global__ void __launch_bounds__(PC_WARPS * 32) k_pair_cell(PairArgs a)
                     pair_loop_local<DIM, TPP, POT>(a, n, a.lrow + (size_t)i * a.cap, cand, ri, lg, fx, fy, fz, e);
                 } else {
                     const float4 ri = __ldg(a.r + i);
-                    pair_loop<DIM, TPP, POT, true>(a, i, n, a.nbr + (size_t)i * a.cap, ri, lg, fx, fy, fz, e);
+                    pair_loop<DIM, TPP, POT, true>(a, a.r, i, n, a.nbr + (size_t)i * a.cap, ri, lg, fx, fy, fz, e);
                 }
             }
 #pragma unroll
@@ -286,8 +341,15 @@ static void launch_pair_tpp(const PairArgs &a, cudaStream_t st)
     }
 }
 
+// kick: 0 forces only, 1 forces + closing half-kick, 2 the fused NVE step
+// (int32 rows only; the integrator does not fuse with local rows).
 void enqueue_pair(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st)
 {
+    if (kick == 2) {
+        if (dim == 3) pot == MD_LJ ? launch_pair_tpp<3, MD_LJ, 2>(a, st) : launch_pair_tpp<3, MD_SOFT_SPHERE, 2>(a, st);
+        else pot == MD_LJ ? launch_pair_tpp<2, MD_LJ, 2>(a, st) : launch_pair_tpp<2, MD_SOFT_SPHERE, 2>(a, st);
+        return;
+    }
     if (a.lrow) {
         if (dim == 3) {
             if (pot == MD_LJ) kick ? launch_pair_cell<3, MD_LJ, 1>(a, st) : launch_pair_cell<3, MD_LJ, 0>(a, st);

@@ -60,6 +60,11 @@ __device__ __forceinline__ void energy_epilogue(float pe_acc, float ke_acc, cons
         if (a.use_cond)
             cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond_while,
                                     (step + 1u < a.ctl[CTL_NSTEPS]) ? 1u : 0u);
+        // fused NVE step: every block has raised (and fenced) the rebuild
+        // flag before its ticket, so the last block hands it to the IF node
+        if (a.cond_if)
+            cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond_if,
+                                    *(volatile uint32_t *)&a.ctl[CTL_REBUILD] ? 1u : 0u);
     }
 }
 

@@ -209,6 +209,30 @@ def test_neighbor_list_rebuilt_in_dynamics_bit_exact(P, workload):
     rows_equal(nl.cnt.cpu().numpy(), nl.nbr.cpu().numpy(), cnt_o, nb_o)
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+@pytest.mark.parametrize("nsteps", [1, 37, 80])
+def test_nve_fused_step_equals_separate_kick_drift_bitwise(P, use_graph, nsteps):
+    # the fused force + kick-drift kernel alternates two position buffers
+    # (odd and even step counts end in different ones) and must reproduce
+    # the separate kick-drift kernel bit for bit, rebuilds included
+    c = W.lj_small()
+    outs = []
+    for fuse in (0, 1):
+        P.md_set_nve_fusion(fuse)
+        try:
+            outs.append(_run_nve(P, c, nsteps, use_graph))
+        finally:
+            P.md_set_nve_fusion(1)
+    a, b = outs
+    for x, y in zip(a[:5], b[:5]):
+        np.testing.assert_array_equal(x, y)
+    assert a[5].stats()[0] == b[5].stats()[0]
+    if nsteps == 80:
+        assert b[5].stats()[0] >= 3
+    np.testing.assert_array_equal(a[5].cnt.cpu().numpy(), b[5].cnt.cpu().numpy())
+    np.testing.assert_array_equal(a[5].nbr.cpu().numpy(), b[5].nbr.cpu().numpy())
+
+
 def test_run_to_run_bitwise_determinism(P):
     c = W.lj_small()
     a = _run_nve(P, c, 50, True)
