@@ -438,7 +438,7 @@ def main():
     traffic = None
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        ent = tr.get("k_pair_cell_lj" if args.local_rows else "k_pair_lj", {})
+        ent = tr.get("k_pair_block_lj" if args.local_rows else "k_pair_lj", {})
         if ent.get("source_sha") == _source_sha() and ent.get("N") == c.N:
             traffic = ent.get("dram_bytes_per_launch")
     except (OSError, ValueError):
@@ -464,7 +464,7 @@ def main():
                        "kick_drift": "fused into the force kernel" if args.nve_fusion and not args.local_rows else "separate kernel",
                        "loop": "host launches" if args.no_graph else "one CUDA graph (device WHILE/IF)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": ("k_pair_cell<LJ>" if args.local_rows else "k_pair<LJ>") + " (md_energy_forces)",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": ("k_pair_block<LJ>" if args.local_rows else "k_pair<LJ>") + " (md_energy_forces)",
                          "bytes_per_particle": bytes_per_particle, "kernel_ms": kt * 1e3,
                          "peak_source": peak_src},
             "cpu_baseline": cpu_baseline,

@@ -113,13 +113,17 @@ typedef struct {
 #define MD_NBR_CANONICAL 1
 
 /* Local rows: every build also writes, for each row entry, the entry's index
- * into the candidate array of the particle's cell (the cells of its stencil
- * concatenated in canonical order, members in ascending particle order) as
- * a 16-bit row in the workspace.  Pair forces (Lennard-Jones, soft sphere)
- * then run one CTA per cell that stages the stencil's positions in shared
- * memory and gathers from there; the forces are bitwise those of the int32
- * rows.  Cells whose stencil holds more than 1024 candidates keep using the
- * int32 rows.  Not combinable with MD_NBR_CANONICAL. */
+ * into the region of the particle's cell block as a 16-bit row in the
+ * workspace.  Cells are grouped two per axis into blocks; a block's region is
+ * the block grown by one cell on each side (periodic), its cells taken in
+ * (z, y, x) order and their members in ascending particle order.  Pair
+ * forces (Lennard-Jones, soft sphere) then run one CTA per block that stages
+ * the region's positions in shared memory and gathers from there; the
+ * forces are bitwise those of the int32 rows.  Blocks whose region holds
+ * more than 2048 particles, or a cell whose stencil holds more than 1024,
+ * and grids with fewer than 4 cells on an axis use the int32 rows.  An
+ * opt-in: on B300 the int32-row gather kernel measured faster.  Not
+ * combinable with MD_NBR_CANONICAL. */
 #define MD_NBR_LOCAL_ROWS 2
 
 /* Plan a neighbor list for N particles in space s.  Fails with

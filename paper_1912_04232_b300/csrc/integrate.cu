@@ -406,9 +406,9 @@ static md_status run_dynamics(const md_space *s, const md_pot *p, float *d_r, fl
         c.c1 = (float)e;
         c.c2 = (float)sqrt((1.0 - e * e) * (double)kT / (double)mass);
     }
-    // pair potentials in NVE with int32 rows: kick-drift fused into the force
-    // kernel, positions alternating with the workspace buffer
-    c.fused = (!langevin && (p->kind == MD_LJ || p->kind == MD_SOFT_SPHERE) && !c.pa.lrow && g_fuse_nve) ? 1 : 0;
+    // pair potentials in NVE: kick-drift fused into the force kernel,
+    // positions alternating with the workspace buffer
+    c.fused = (!langevin && (p->kind == MD_LJ || p->kind == MD_SOFT_SPHERE) && g_fuse_nve) ? 1 : 0;
     if (c.fused) {
         const WsPtrs w = ws_ptrs(nb);
         c.pa.r_alt = w.ralt;

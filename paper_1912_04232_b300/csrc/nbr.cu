@@ -294,7 +294,8 @@ __device__ __forceinline__ int padded_m(int M) { return (M + BUILD_CHUNK - 1) / 
 // displacement; MODE 1, positions inside [0, L) (min_image_near); MODE 0,
 // the general formula.
 template <int DIM, int MODE>
-__device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand, const StencilInfo &inf)
+__device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand, const uint16_t *lidx,
+                                           const StencilInfo &inf)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -305,7 +306,7 @@ __device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand,
         const int i = __float_as_int(ri.w);
         int count = 0;
         int32_t *out = a.nbr + (size_t)i * a.cap;
-        uint16_t *lout = a.lrow ? a.lrow + (size_t)i * a.cap : nullptr;
+        uint16_t *lout = lidx ? a.lrow + (size_t)i * a.cap : nullptr;
         for (int k0 = 0; k0 < M; k0 += BUILD_CHUNK) {
             bool hit[2];
             int j[2];
@@ -325,7 +326,7 @@ __device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand,
                 const int pos = count + __popc(mk & lt);
                 if (hit[u] && pos < a.cap) {
                     out[pos] = j[u];
-                    if (lout) lout[pos] = (uint16_t)(k0 + 32 * u + lane);
+                    if (lout) lout[pos] = lidx[k0 + 32 * u + lane];
                 }
                 count += __popc(mk);
             }
@@ -350,7 +351,11 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
     count_launch();
     if (!chain_active(a)) return;
     __shared__ float4 cand[STAGE_CMAX];
+    __shared__ uint16_t lidx[STAGE_CMAX];   // each staged candidate's index in the block region
     __shared__ StencilInfo inf;
+    __shared__ RegionInfo reg;
+    __shared__ int sreg[27];                // region offset of each stencil cell
+    __shared__ int wsum[1];
     __shared__ int bmax;
     const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (warp == 0) {
@@ -362,6 +367,22 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
     __syncthreads();
     if (inf.own_n == 0) return;   // whole CTA: empty cell
     const int M = inf.soff[inf.nst];
+    // local rows: the region of the cell's block (cells.cuh); the force
+    // kernel stages the same region when it holds at most REGION_CMAX
+    bool local = a.lrow != nullptr && region_grid_ok(a.nc, DIM) && M <= STAGE_CMAX;
+    if (local) {
+        const int cx = q % a.nc[0], cy = (q / a.nc[0]) % a.nc[1], cz = q / (a.nc[0] * a.nc[1]);
+        region_locate<DIM>(a.nc, a.ws.cell_start, cx >> 1, cy >> 1, cz >> 1, reg, wsum);
+        local = reg.roff[reg.nreg] <= REGION_CMAX;
+        if (tid < inf.nst) {
+            // stencil cell (xx, yy, zz) of the cell at region position (px, py, pz)
+            const int xx = tid % 3, yy = (tid / 3) % 3, zz = tid / 9;
+            const int px = (cx & 1) + 1, py = (cy & 1) + 1, pz = DIM == 3 ? (cz & 1) + 1 : 1;
+            const int ri = ((DIM == 3 ? pz + zz - 1 : 0) * reg.ey + (py + yy - 1)) * reg.ex + (px + xx - 1);
+            sreg[tid] = reg.roff[ri];
+        }
+        __syncthreads();
+    }
     int wmax = 0;
     if (M > STAGE_CMAX) {
         // dense stencil: per-warp rows straight from global memory with the
@@ -379,15 +400,19 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
         for (int m = warp; m < inf.nst; m += BUILD_WARPS) {
             const int b0 = inf.soff[m], n = inf.soff[m + 1] - b0;
             const float4 *src = a.ws.rsorted + inf.sbeg[m];
-            for (int k = lane; k < n; k += 32) cand[b0 + k] = src[k];
+            for (int k = lane; k < n; k += 32) {
+                cand[b0 + k] = src[k];
+                if (local) lidx[b0 + k] = (uint16_t)(sreg[m] + k);
+            }
         }
         const float nan = __int_as_float(0x7fc00000);
         for (int k = M + tid; k < padded_m(M); k += BUILD_WARPS * 32)
             cand[k] = make_float4(nan, nan, nan, __int_as_float(-1));
         __syncthreads();
-        wmax = inf.inner   ? build_sweep<DIM, 2>(a, cand, inf)
-               : a.wrapped ? build_sweep<DIM, 1>(a, cand, inf)
-                           : build_sweep<DIM, 0>(a, cand, inf);
+        const uint16_t *li = local ? lidx : nullptr;
+        wmax = inf.inner   ? build_sweep<DIM, 2>(a, cand, li, inf)
+               : a.wrapped ? build_sweep<DIM, 1>(a, cand, li, inf)
+                           : build_sweep<DIM, 0>(a, cand, li, inf);
     }
     // one atomic per CTA for the largest row count
     if (lane == 0 && wmax > 0) atomicMax(&bmax, wmax);

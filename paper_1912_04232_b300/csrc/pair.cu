@@ -182,15 +182,17 @@ __global__ void __launch_bounds__(256) k_pair(PairArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Cell-centred pair forces (lists with local rows).  One CTA per cell, grid-
-// stride over the cells: the positions of the cell's stencil candidates are
-// gathered once into shared memory in the staged order of the last build,
-// then each particle's group of TPP lanes reads its 16-bit local row and
-// takes the partners from shared memory.  Entries, their order and the
-// arithmetic are those of k_pair, so the forces are the same bits.  Cells
-// whose stencil was too large to stage use their int32 rows.
+// Block-centred pair forces (lists with local rows).  One CTA per block of
+// 2 x 2 x 2 cells (cells.cuh), grid-stride over the blocks: the positions of
+// the block's region (the block grown by one cell, ~64 cells) are gathered
+// once into shared memory in the order the build indexed them; then each
+// particle's group of TPP lanes reads its 16-bit local row and takes the
+// partners from shared memory.  Entries, their order and the arithmetic are
+// those of k_pair, so the forces are the same bits.  A block whose region is
+// too large to stage, or one of whose cells had a dense stencil (the build
+// wrote no local rows there), uses the int32 rows.
 // ---------------------------------------------------------------------------
-constexpr int PC_WARPS = 4;
+constexpr int PB_THREADS = 256;
 
 template <int DIM, int TPP, int POT>
 __device__ __forceinline__ void pair_loop_local(const PairArgs &a, int n, const uint16_t *row, const float4 *cand,
@@ -211,46 +213,90 @@ __device__ __forceinline__ void pair_loop_local(const PairArgs &a, int n, const 
 }
 
 template <int DIM, int TPP, int POT, int KICK>
-__global__ void __launch_bounds__(PC_WARPS * 32) k_pair_cell(PairArgs a)
+__global__ void __launch_bounds__(PB_THREADS) k_pair_block(PairArgs a)
 {
     count_launch();
-    constexpr int GPB = PC_WARPS * 32 / TPP;   // particles per pass
-    __shared__ float4 cand[STAGE_CMAX];
-    __shared__ StencilInfo inf;
+    constexpr int PPP = PB_THREADS / TPP;   // particles per pass
+    __shared__ float4 cand[REGION_CMAX];
+    __shared__ RegionInfo reg;
+    __shared__ int wsum[1];
+    __shared__ int own_ri[8], own_off[9], n_own, local_ok;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int lg = tid & (TPP - 1), gl = tid / TPP;
+    const float4 *rc = a.r;
+    float4 *rn = nullptr;
+    bool more = false;
+    if (KICK == 2) {
+        const uint32_t step = *(volatile uint32_t *)&a.ctl[CTL_STEP];
+        rc = (step & 1u) ? a.r_alt : a.r;
+        rn = (step & 1u) ? const_cast<float4 *>(a.r) : a.r_alt;
+        more = step + 1u < *(volatile uint32_t *)&a.ctl[CTL_NSTEPS];
+    }
+    const int nbx = blocks_along(a.nc[0]), nby = blocks_along(a.nc[1]);
+    const int nbz = DIM == 3 ? blocks_along(a.nc[2]) : 1;
+    const int nblk = nbx * nby * nbz;
     float pe_acc = 0.0f, ke_acc = 0.0f;
-    for (int q = blockIdx.x; q < a.ncell; q += gridDim.x) {
-        if (warp == 0) {
-            int beg, cnt;
-            stencil_locate<DIM>(a.nc, a.cell_start, q, lane, beg, cnt);
-            stencil_publish<DIM>(a.nc, 0, q, lane, beg, cnt, inf);
+    bool moved_any = false;
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
+        region_locate<DIM>(a.nc, a.cell_start, bx, by, bz, reg, wsum);
+        if (tid == 0) {
+            // own cells are the region's interior; local rows are usable when
+            // the region fits and every own cell's stencil was staged
+            const int ox = reg.ex - 2, oy = reg.ey - 2, oz = DIM == 3 ? reg.ez - 2 : 1;
+            bool ok = reg.roff[reg.nreg] <= REGION_CMAX;
+            int k = 0, acc = 0;
+            for (int z = 0; z < oz; ++z)
+                for (int y = 0; y < oy; ++y)
+                    for (int x = 0; x < ox; ++x) {
+                        const int zr = DIM == 3 ? z + 1 : 0;
+                        const int ri = (zr * reg.ey + (y + 1)) * reg.ex + (x + 1);
+                        own_ri[k] = ri;
+                        own_off[k] = acc;
+                        acc += reg.roff[ri + 1] - reg.roff[ri];
+                        int m = 0;
+                        for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+                            for (int dy = -1; dy <= 1; ++dy) {
+                                const int rr = ((zr + dz) * reg.ey + (y + 1 + dy)) * reg.ex + x;   // x-1 .. x+1
+                                m += reg.roff[rr + 3] - reg.roff[rr];
+                            }
+                        ok = ok && m <= STAGE_CMAX;
+                        ++k;
+                    }
+            own_off[k] = acc;
+            n_own = k;
+            local_ok = ok ? 1 : 0;
         }
         __syncthreads();
-        const bool staged = inf.soff[inf.nst] <= STAGE_CMAX;
-        if (staged) {
-            for (int m = warp; m < inf.nst; m += PC_WARPS) {
-                const int b0 = inf.soff[m], nm = inf.soff[m + 1] - b0;
-                const int32_t *src = a.atoms + inf.sbeg[m];
-                for (int t = lane; t < nm; t += 32) cand[b0 + t] = __ldg(a.r + __ldg(src + t));
+        const bool loc = local_ok != 0;
+        if (loc) {
+            for (int c = warp; c < reg.nreg; c += PB_THREADS / 32) {
+                const int b0 = reg.roff[c], nm = reg.roff[c + 1] - b0;
+                const int32_t *src = a.atoms + reg.rbeg[c];
+                for (int t = lane; t < nm; t += 32) cand[b0 + t] = __ldg(rc + __ldg(src + t));
             }
         }
         __syncthreads();
-        for (int p0 = 0; p0 < inf.own_n; p0 += GPB) {
+        const int nown = own_off[n_own];
+        for (int p0 = 0; p0 < nown; p0 += PPP) {
             const int p = p0 + gl;
-            const bool valid = p < inf.own_n;
+            const bool valid = p < nown;
             float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+            float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
             int i = 0;
             if (valid) {
-                i = __ldg(a.atoms + inf.own_beg + p);
+                int c = 0;
+                while (own_off[c + 1] <= p) ++c;
+                const int t = p - own_off[c], rcix = own_ri[c];
+                i = __ldg(a.atoms + reg.rbeg[rcix] + t);
                 int n = __ldg(a.cnt + i);
                 n = n < a.cap ? n : a.cap;
-                if (staged) {
-                    const float4 ri = cand[inf.own_off + p];
+                if (loc) {
+                    ri = cand[reg.roff[rcix] + t];
                     pair_loop_local<DIM, TPP, POT>(a, n, a.lrow + (size_t)i * a.cap, cand, ri, lg, fx, fy, fz, e);
                 } else {
-                    const float4 ri = __ldg(a.r + i);
-                    pair_loop<DIM, TPP, POT, true>(a, a.r, i, n, a.nbr + (size_t)i * a.cap, ri, lg, fx, fy, fz, e);
+                    ri = __ldg(rc + i);
+                    pair_loop<DIM, TPP, POT, true>(a, rc, i, n, a.nbr + (size_t)i * a.cap, ri, lg, fx, fy, fz, e);
                 }
             }
 #pragma unroll
@@ -264,40 +310,50 @@ __global__ void __launch_bounds__(PC_WARPS * 32) k_pair_cell(PairArgs a)
                 const float ei = 0.5f * e;
                 a.f[i] = make_float4(fx, fy, fz, ei);
                 pe_acc += ei;
-                if (KICK) ke_acc += half_kick<DIM>(a, i, fx, fy, fz);
+                if (KICK == 1) ke_acc += half_kick<DIM>(a, i, fx, fy, fz);
+                if (KICK == 2) {
+                    bool mv;
+                    ke_acc += kick_kick_drift<DIM>(a, i, ri, fx, fy, fz, more, rn, &mv);
+                    moved_any = moved_any || mv;
+                }
             }
         }
-        __syncthreads();   // the next cell reuses cand and inf
+        __syncthreads();   // the next block reuses cand, reg and the own lists
+    }
+    if (KICK == 2 && __any_sync(0xffffffffu, moved_any) && lane == 0) {
+        a.ctl[CTL_REBUILD] = 1u;
+        __threadfence();
     }
     if (!a.E_out && !KICK) return;
     energy_epilogue(pe_acc, ke_acc, a);
 }
 
 template <int DIM, int TPP, int POT, int KICK>
-static int pair_cell_grid(const PairArgs &a)
+static int pair_block_grid(const PairArgs &a)
 {
     static int per_sm = 0, sms = 0;
     if (!per_sm) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_cell<DIM, TPP, POT, KICK>, PC_WARPS * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_block<DIM, TPP, POT, KICK>, PB_THREADS, 0);
         if (per_sm < 1) per_sm = 1;
         if (sms < 1) sms = 1;
     }
+    const int nblk = blocks_along(a.nc[0]) * blocks_along(a.nc[1]) * (DIM == 3 ? blocks_along(a.nc[2]) : 1);
     int g = per_sm * sms;
-    g = a.ncell < g ? a.ncell : g;
+    g = nblk < g ? nblk : g;
     return g < a.max_blocks ? g : a.max_blocks;
 }
 
 template <int DIM, int POT, int KICK>
-static void launch_pair_cell(const PairArgs &a, cudaStream_t st)
+static void launch_pair_block(const PairArgs &a, cudaStream_t st)
 {
     switch (a.tpp) {
-    case 4: k_pair_cell<DIM, 4, POT, KICK><<<pair_cell_grid<DIM, 4, POT, KICK>(a), PC_WARPS * 32, 0, st>>>(a); break;
-    case 16: k_pair_cell<DIM, 16, POT, KICK><<<pair_cell_grid<DIM, 16, POT, KICK>(a), PC_WARPS * 32, 0, st>>>(a); break;
-    case 32: k_pair_cell<DIM, 32, POT, KICK><<<pair_cell_grid<DIM, 32, POT, KICK>(a), PC_WARPS * 32, 0, st>>>(a); break;
-    default: k_pair_cell<DIM, 8, POT, KICK><<<pair_cell_grid<DIM, 8, POT, KICK>(a), PC_WARPS * 32, 0, st>>>(a); break;
+    case 4: k_pair_block<DIM, 4, POT, KICK><<<pair_block_grid<DIM, 4, POT, KICK>(a), PB_THREADS, 0, st>>>(a); break;
+    case 16: k_pair_block<DIM, 16, POT, KICK><<<pair_block_grid<DIM, 16, POT, KICK>(a), PB_THREADS, 0, st>>>(a); break;
+    case 32: k_pair_block<DIM, 32, POT, KICK><<<pair_block_grid<DIM, 32, POT, KICK>(a), PB_THREADS, 0, st>>>(a); break;
+    default: k_pair_block<DIM, 8, POT, KICK><<<pair_block_grid<DIM, 8, POT, KICK>(a), PB_THREADS, 0, st>>>(a); break;
     }
 }
 
@@ -341,31 +397,32 @@ static void launch_pair_tpp(const PairArgs &a, cudaStream_t st)
     }
 }
 
-// kick: 0 forces only, 1 forces + closing half-kick, 2 the fused NVE step
-// (int32 rows only; the integrator does not fuse with local rows).
+template <int DIM, int POT>
+static void launch_pair_kick(const PairArgs &a, int kick, bool blockk, cudaStream_t st)
+{
+    if (blockk) {
+        if (kick == 2) launch_pair_block<DIM, POT, 2>(a, st);
+        else if (kick == 1) launch_pair_block<DIM, POT, 1>(a, st);
+        else launch_pair_block<DIM, POT, 0>(a, st);
+    } else {
+        if (kick == 2) launch_pair_tpp<DIM, POT, 2>(a, st);
+        else if (kick == 1) launch_pair_tpp<DIM, POT, 1>(a, st);
+        else launch_pair_tpp<DIM, POT, 0>(a, st);
+    }
+}
+
+// kick: 0 forces only, 1 forces + closing half-kick, 2 the fused NVE step.
+// Lists with local rows on grids of >= 4 cells per axis take the
+// block-centred kernel, all others the gather kernel over int32 rows.
 void enqueue_pair(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st)
 {
-    if (kick == 2) {
-        if (dim == 3) pot == MD_LJ ? launch_pair_tpp<3, MD_LJ, 2>(a, st) : launch_pair_tpp<3, MD_SOFT_SPHERE, 2>(a, st);
-        else pot == MD_LJ ? launch_pair_tpp<2, MD_LJ, 2>(a, st) : launch_pair_tpp<2, MD_SOFT_SPHERE, 2>(a, st);
-        return;
-    }
-    if (a.lrow) {
-        if (dim == 3) {
-            if (pot == MD_LJ) kick ? launch_pair_cell<3, MD_LJ, 1>(a, st) : launch_pair_cell<3, MD_LJ, 0>(a, st);
-            else kick ? launch_pair_cell<3, MD_SOFT_SPHERE, 1>(a, st) : launch_pair_cell<3, MD_SOFT_SPHERE, 0>(a, st);
-        } else {
-            if (pot == MD_LJ) kick ? launch_pair_cell<2, MD_LJ, 1>(a, st) : launch_pair_cell<2, MD_LJ, 0>(a, st);
-            else kick ? launch_pair_cell<2, MD_SOFT_SPHERE, 1>(a, st) : launch_pair_cell<2, MD_SOFT_SPHERE, 0>(a, st);
-        }
-        return;
-    }
+    const bool blockk = a.lrow != nullptr && region_grid_ok(a.nc, dim);
     if (dim == 3) {
-        if (pot == MD_LJ) kick ? launch_pair_tpp<3, MD_LJ, 1>(a, st) : launch_pair_tpp<3, MD_LJ, 0>(a, st);
-        else kick ? launch_pair_tpp<3, MD_SOFT_SPHERE, 1>(a, st) : launch_pair_tpp<3, MD_SOFT_SPHERE, 0>(a, st);
+        if (pot == MD_LJ) launch_pair_kick<3, MD_LJ>(a, kick, blockk, st);
+        else launch_pair_kick<3, MD_SOFT_SPHERE>(a, kick, blockk, st);
     } else {
-        if (pot == MD_LJ) kick ? launch_pair_tpp<2, MD_LJ, 1>(a, st) : launch_pair_tpp<2, MD_LJ, 0>(a, st);
-        else kick ? launch_pair_tpp<2, MD_SOFT_SPHERE, 1>(a, st) : launch_pair_tpp<2, MD_SOFT_SPHERE, 0>(a, st);
+        if (pot == MD_LJ) launch_pair_kick<2, MD_LJ>(a, kick, blockk, st);
+        else launch_pair_kick<2, MD_SOFT_SPHERE>(a, kick, blockk, st);
     }
 }
 

@@ -1,7 +1,7 @@
-"""GPU parity of the cell-centred force path (lists with local rows): the
-16-bit rows index the shared-memory staging of each cell's stencil, and the
-forces, energies per particle and whole NVE trajectories must be the same
-bits as with the int32 rows (Sec. 3.2.2-3.3.1)."""
+"""GPU parity of the block-centred force path (lists with local rows): the
+16-bit rows index the shared-memory staging of the region around each block
+of 2 x 2 x 2 cells, and the forces, energies per particle and whole NVE
+trajectories must be the same bits as with the int32 rows (Sec. 3.2.2-3.3.1)."""
 import numpy as np
 import pytest
 
@@ -75,6 +75,34 @@ def test_local_rows_dense_stencils_fall_back_to_int32_rows(P):
     fb, _, nl = _forces(P, r, L, P.soft_pot(), 2.5, cap=512, skin=0.3, local=True)
     assert list(nl.plan.ncell) == [3, 3, 3]
     np.testing.assert_array_equal(fa, fb)
+
+
+def test_local_rows_mixed_blocks_fall_back_per_block(P):
+    # 8 cells per axis; x-cells 0-5 hold 35 particles each, x-cells 6-7 hold
+    # 10: block regions made only of dense cells exceed the 2,048 staged
+    # particles and use their int32 rows, the others their local rows, while
+    # every stencil stays under the 1,024 candidates the build stages
+    rng = np.random.Generator(np.random.PCG64(11))
+    nc, rl = 8, 2.8
+    L = W.f32(nc * rl * 1.01)
+    w = L / nc
+    pts = []
+    for cz in range(nc):
+        for cy in range(nc):
+            for cx in range(nc):
+                k = 35 if cx < 6 else 10
+                u = rng.uniform(0.05, 0.95, size=(k, 3))
+                pts.append((np.array([cx, cy, cz]) + u) * w)
+    x = np.concatenate(pts)
+    x = x[rng.permutation(x.shape[0])]
+    r = np.zeros((x.shape[0], 4), np.float32)
+    r[:, :3] = x.astype(np.float32)
+    r[:, 3] = 1.0
+    fa, Ea, _ = _forces(P, r, L, P.soft_pot(), 2.5, cap=256)
+    fb, Eb, nl = _forces(P, r, L, P.soft_pot(), 2.5, cap=256, local=True)
+    assert list(nl.plan.ncell) == [nc] * 3
+    np.testing.assert_array_equal(fa, fb)
+    assert abs(Ea - Eb) <= 1e-7 * max(abs(Ea), 1.0)
 
 
 @pytest.mark.parametrize("use_graph", [False, True])
