@@ -9,7 +9,8 @@
 //   k_b_kick_drift   every particle, with its replica's dt, mass and box;
 //                    sets the replica's rebuild flag (and a global "any")
 //   IF any:          k_b_bin -> k_b_scan (block per replica, segmented) ->
-//                    k_b_scatter -> k_b_build (block per cell) -> k_b_finish,
+//                    k_b_scatter -> k_b_sort_cells -> k_b_build (block per
+//                    cell) -> k_b_finish,
 //                    each skipping replicas whose flag is clear
 //   k_b_pair<KICK>   forces + closing half-kick, per-particle potential and
 //                    kinetic energy into f.w and v.w
@@ -48,8 +49,8 @@ struct BatchDev {
     const RepMeta *meta;
     const int32_t *rep_of;    // [N]
     const int32_t *cell_rep;  // [C]
-    int32_t *cell_count, *cell_start, *cell_of, *rank, *atoms;
-    float4 *rsorted;
+    int32_t *cell_count, *cell_start, *cell_of, *rank, *atoms_u, *atoms;
+    float4 *rsorted;          // cell-ordered positions, particle index in w
     uint32_t *flag;           // [R] rebuild flags
     uint32_t *builds;         // [R] builds per replica
     uint32_t *ctl;            // control words (CTL_*)
@@ -60,7 +61,8 @@ struct BatchDev {
 };
 
 struct BatchLayout {
-    size_t meta, rep_of, cell_rep, cell_count, cell_start, cell_of, rank, atoms, rsorted, flag, builds, ctl, total;
+    size_t meta, rep_of, cell_rep, cell_count, cell_start, cell_of, rank, atoms_u, atoms, rsorted, flag, builds, ctl,
+        total;
 };
 
 static BatchLayout batch_layout(int N, int R, int C)
@@ -75,6 +77,7 @@ static BatchLayout batch_layout(int N, int R, int C)
     w.cell_start = o; o = align256(o + sizeof(int32_t) * (size_t)C);
     w.cell_of = o;    o = align256(o + sizeof(int32_t) * (size_t)N);
     w.rank = o;       o = align256(o + sizeof(int32_t) * (size_t)N);
+    w.atoms_u = o;    o = align256(o + sizeof(int32_t) * (size_t)N);
     w.atoms = o;      o = align256(o + sizeof(int32_t) * (size_t)N);
     w.rsorted = o;    o = align256(o + sizeof(float4) * (size_t)N);
     w.flag = o;       o = align256(o + sizeof(uint32_t) * (size_t)R);
@@ -208,8 +211,39 @@ __global__ void __launch_bounds__(256) k_b_scatter(BatchDev b, const float4 *r)
     if (i >= b.N) return;
     if (*(volatile uint32_t *)&b.flag[b.rep_of[i]] == 0u) return;
     int slot = b.cell_start[b.cell_of[i]] + b.rank[i];
-    b.atoms[slot] = i;
-    b.rsorted[slot] = r[i];
+    b.atoms_u[slot] = i;
+}
+
+// One warp per cell (as the single-system k_sort_cells): members ranked by
+// global index, written with their positions (index in w) in that order;
+// the positions of this build go to rref.
+constexpr int BS_WARPS = 8;
+__global__ void __launch_bounds__(BS_WARPS * 32) k_b_sort_cells(BatchDev b, const float4 *r)
+{
+    count_launch();
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * BS_WARPS + (threadIdx.x >> 5);
+    if (q >= b.C) return;   // whole warp
+    const int rep = b.cell_rep[q];
+    if (rep < 0 || *(volatile uint32_t *)&b.flag[rep] == 0u) return;
+    const int s0 = b.cell_start[q], n = b.cell_start[q + 1] - s0;
+    const int32_t *u = b.atoms_u + s0;
+    for (int base = 0; base < n; base += 32) {
+        const int k = base + lane;
+        const int me = k < n ? u[k] : 0x7fffffff;
+        int rk = 0;
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            int other = (c0 + lane < n) ? u[c0 + lane] : 0x7fffffff;
+#pragma unroll 8
+            for (int t = 0; t < 32; ++t) rk += (__shfl_sync(0xffffffffu, other, t) < me);
+        }
+        if (k < n) {
+            const float4 p = r[me];
+            b.atoms[s0 + rk] = me;
+            b.rsorted[s0 + rk] = make_float4(p.x, p.y, p.z, __int_as_float(me));
+            b.rref[me] = p;
+        }
+    }
 }
 
 __device__ __forceinline__ int b_axis_cells(int q, int n, int *out)
@@ -293,22 +327,19 @@ __device__ void b_build_row_warp(const BatchDev &b, const RepMeta &m, int i, con
     for (int k = lane; k < b.cap; k += 32) out[k] = (k < n) ? row[k] : b.N;
     if (lane == 0) {
         b.cnt[i] = count;
-        b.rref[i] = pi;
         if (count > b.cap) raise_status(b.status, MD_ERR_NBR_OVERFLOW);
     }
     __syncwarp();
 }
 
 // block per (non-sentinel) cell, same candidate order as the single-system
-// build: stencil cells in fixed order, ascending global index inside a cell.
+// build: stencil cells in fixed order, ascending global index inside a cell
+// (k_b_sort_cells); candidates swept 64 at a time with two ballots.
 // Cells whose stencil exceeds the staging capacity set MD_ERR_BOUNDS
 // (replica plans keep stencils small; see md_batch_plan).
 __global__ void __launch_bounds__(BB_WARPS * 32) k_b_build(BatchDev b)
 {
     count_launch();
-    __shared__ int cidx[BB_CMAX];
-    __shared__ int sidx[BB_CMAX];
-    __shared__ float4 cpos[BB_CMAX];
     __shared__ float4 spos[BB_CMAX];
     __shared__ int soff[28], sbeg[27], nst;
     const int q = blockIdx.x;
@@ -353,7 +384,8 @@ __global__ void __launch_bounds__(BB_WARPS * 32) k_b_build(BatchDev b)
     if (M > BB_CMAX) {
         // per-warp rows; the 16 KB candidate-position array serves as 8 warp
         // buffers of 512 ints
-        int *rowbuf = reinterpret_cast<int *>(cpos) + (tid >> 5) * 512;
+        static_assert(sizeof(spos) >= BB_WARPS * 512 * sizeof(int), "row buffers must fit");
+        int *rowbuf = reinterpret_cast<int *>(spos) + (tid >> 5) * 512;
         for (int s = own_b + (tid >> 5); s < own_e; s += BB_WARPS) {
             int i = b.atoms[s];
             float4 pi = b.rsorted[s];
@@ -363,51 +395,45 @@ __global__ void __launch_bounds__(BB_WARPS * 32) k_b_build(BatchDev b)
         }
         return;
     }
-    for (int slot = tid; slot < M; slot += blockDim.x) {
-        int k = 0;
-        while (soff[k + 1] <= slot) ++k;
-        int src = sbeg[k] + (slot - soff[k]);
-        cidx[slot] = b.atoms[src];
-        cpos[slot] = b.rsorted[src];
+    // staging: the members are in canonical order already (k_b_sort_cells),
+    // padded with NaN positions (which fail every test) to whole sweep steps
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int mm = warp; mm < nst; mm += BB_WARPS) {
+        const int b0 = soff[mm], n = soff[mm + 1] - b0, src = sbeg[mm];
+        for (int k = lane; k < n; k += 32) spos[b0 + k] = b.rsorted[src + k];
     }
+    const float nan = __int_as_float(0x7fc00000);
+    const int Mp = (M + 63) / 64 * 64;
+    for (int k = M + tid; k < Mp; k += blockDim.x) spos[k] = make_float4(nan, nan, nan, __int_as_float(-1));
     __syncthreads();
-    for (int slot = tid; slot < M; slot += blockDim.x) {
-        int k = 0;
-        while (soff[k + 1] <= slot) ++k;
-        const int b0 = soff[k], e0 = soff[k + 1];
-        const int me = cidx[slot];
-        int rank = 0;
-        for (int t2 = b0; t2 < e0; ++t2) rank += (cidx[t2] < me);
-        sidx[b0 + rank] = me;
-        spos[b0 + rank] = cpos[slot];
-    }
-    __syncthreads();
-    const int lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
-    for (int s = own_b + (tid >> 5); s < own_e; s += BB_WARPS) {
-        int i = b.atoms[s];
-        float4 ri = b.rsorted[s];
+    for (int s = own_b + warp; s < own_e; s += BB_WARPS) {
+        const float4 ri = b.rsorted[s];
+        const int i = __float_as_int(ri.w);
         int32_t *out = b.nbr + (size_t)i * b.cap;
         int count = 0;
-        for (int k0 = 0; k0 < M; k0 += 32) {
-            int k = k0 + lane;
-            bool hit = false;
-            int j = 0;
-            if (k < M) {
-                j = sidx[k];
+        for (int k0 = 0; k0 < Mp; k0 += 64) {
+            bool hit[2];
+            int j[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float4 c = spos[k0 + 32 * u + lane];
+                j[u] = __float_as_int(c.w);
                 float dx, dy, dz;
-                hit = (j != i) && (dist2_rn<3>(ri, spos[k], m.box, dx, dy, dz) < m.rl2);
+                hit[u] = (j[u] != i) && (dist2_rn<3>(ri, c, m.box, dx, dy, dz) < m.rl2);
             }
-            unsigned mk = __ballot_sync(0xffffffffu, hit);
-            int pos = count + __popc(mk & lt);
-            if (hit && pos < b.cap) out[pos] = j;
-            count += __popc(mk);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const unsigned mk = __ballot_sync(0xffffffffu, hit[u]);
+                const int pos = count + __popc(mk & lt);
+                if (hit[u] && pos < b.cap) out[pos] = j[u];
+                count += __popc(mk);
+            }
         }
         int n = count < b.cap ? count : b.cap;
         for (int k = n + lane; k < b.cap; k += 32) out[k] = b.N;
         if (lane == 0) {
             b.cnt[i] = count;
-            b.rref[i] = ri;
             if (count > b.cap) raise_status(b.status, MD_ERR_NBR_OVERFLOW);
         }
     }
@@ -595,6 +621,7 @@ static BatchDev batch_dev(const md_batch *bt, uint32_t *status)
     b.cell_start = (int32_t *)(p + w.cell_start);
     b.cell_of = (int32_t *)(p + w.cell_of);
     b.rank = (int32_t *)(p + w.rank);
+    b.atoms_u = (int32_t *)(p + w.atoms_u);
     b.atoms = (int32_t *)(p + w.atoms);
     b.rsorted = (float4 *)(p + w.rsorted);
     b.flag = (uint32_t *)(p + w.flag);
@@ -618,6 +645,7 @@ static void enqueue_b_rebuild(const BatchDev &b, const float4 *r, cudaStream_t s
     k_b_bin<<<g, 256, 0, st>>>(b, r);
     k_b_scan<<<b.R, 256, 0, st>>>(b);
     k_b_scatter<<<g, 256, 0, st>>>(b, r);
+    k_b_sort_cells<<<(b.C + BS_WARPS - 1) / BS_WARPS, BS_WARPS * 32, 0, st>>>(b, r);
     k_b_build<<<b.C, BB_WARPS * 32, 0, st>>>(b);
     k_b_finish<<<1, 256, 0, st>>>(b);
 }
