@@ -50,6 +50,9 @@ def lib():
                              C.c_int, _dp, _dp]
         L.or_gd.restype = None
         L.or_gd.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, _dp, C.c_int, _dp, C.c_double, C.c_int, _dp]
+        L.or_fire.restype = None
+        L.or_fire.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, _dp, C.c_int, _dp, _dp, C.c_int, C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_philox4x32_10.restype = None
         L.or_philox4x32_10.argtypes = [_up, _up, _up]
         L.or_normal3.restype = None
@@ -217,6 +220,31 @@ def gd(r, L, pot="soft", eta=0.05, nsteps=10, dim=2, diam=None, **kw):
         dptr = diam.ctypes.data
     lib().or_gd(N, dim, x, dptr, _box(L, dim), _POT[pot], _pp(pot, **kw), eta, nsteps, E)
     return x, E
+
+
+# FIRE parameters (Bitzek et al. 2006 recommendations; dt_max = 4 dt_start)
+FIRE_DEFAULTS = dict(dt_start=0.1, dt_max=0.4, f_inc=1.1, f_dec=0.5, alpha_start=0.1, f_alpha=0.99, n_min=5)
+
+
+def fire(r, L, pot="soft", nsteps=10, dim=2, diam=None, fire_params=None, **kw):
+    """FIRE minimisation from rest.  Returns (r, v, E[nsteps+1], dt[nsteps],
+    (dt, alpha, npos) at the end)."""
+    fp = dict(FIRE_DEFAULTS, **(fire_params or {}))
+    prm = np.array([fp["dt_start"], fp["dt_max"], fp["f_inc"], fp["f_dec"], fp["alpha_start"], fp["f_alpha"],
+                    fp["n_min"]], np.float64)
+    x = _pos(r, dim)
+    N = x.shape[0]
+    E = np.zeros(nsteps + 1)
+    dts = np.zeros(max(nsteps, 1))
+    v = np.zeros((N, 3))
+    st = np.zeros(3)
+    dptr = None
+    if diam is not None:
+        diam = np.ascontiguousarray(diam, np.float64)
+        dptr = diam.ctypes.data
+    lib().or_fire(N, dim, x, dptr, _box(L, dim), _POT[pot], _pp(pot, **kw), prm, nsteps, E.ctypes.data,
+                  dts.ctypes.data, v.ctypes.data, st.ctypes.data)
+    return x, v, E, dts[:nsteps], (float(st[0]), float(st[1]), int(st[2]))
 
 
 def philox4x32_10(ctr, key):

@@ -13,7 +13,7 @@
  *   - pair energy U = 1/2 sum_{i != j} u(r_ij), F = -grad U     (Sec. 3.2.2, 3.3.2)
  *     for Lennard-Jones and soft spheres
  *   - Stillinger-Weber 2-body + 3-body energy and forces        (Sec. 3.3.2)
- *   - velocity-Verlet NVE, gradient-descent minimisation,
+ *   - velocity-Verlet NVE, gradient-descent and FIRE minimisation,
  *     BAOAB Langevin NVT                                         (Sec. 3.3.1)
  *   - reverse-mode derivative of the final energy of a gradient-descent
  *     minimisation with respect to the small-disk diameter D     (Sec. 4.2, App. A)
@@ -543,6 +543,75 @@ void or_gd(int N, int dim, double *r, const double *diam, const double *L, int p
     }
     double U = energy_forces(pot, N, dim, r, diam, L, pp, f);
     if (Eser) Eser[nsteps] = U;
+    free(f);
+}
+
+/* FIRE, the Fast Inertial Relaxation Engine (Bitzek, Koskinen, Gahler,
+ * Moseler, Gumbsch, PRL 97, 170201 (2006); Sec. 3.3.1 lists it among the
+ * minimisers), unit mass, unwrapped coordinates as in GD.  One step, in the
+ * order of the published algorithm:
+ *   MD step (velocity Verlet):  v += dt/2 F;  r += dt v;  F = F(r);  v += dt/2 F
+ *   P = F . v over all degrees of freedom
+ *   mixing:  v = (1 - alpha) v + alpha |v| F/|F|   (no F term when |F| = 0)
+ *   P > 0:   npos += 1; if npos > n_min: dt = min(dt f_inc, dt_max), alpha *= f_alpha
+ *   P <= 0:  dt *= f_dec; v = 0; alpha = alpha_start; npos = 0
+ * prm = {dt_start, dt_max, f_inc, f_dec, alpha_start, f_alpha, n_min}.
+ * Starts from rest.  Eser (nsteps+1, may be NULL): U before every step and
+ * after the last; dtser (nsteps, may be NULL): dt after each step; v (3N,
+ * may be NULL) receives the final velocities; st_out (3, may be NULL):
+ * final dt, alpha, npos. */
+void or_fire(int N, int dim, double *r, const double *diam, const double *L, int pot, const double *pp,
+             const double *prm, int nsteps, double *Eser, double *dtser, double *v_out, double *st_out)
+{
+    double *f = (double *)calloc((size_t)3 * N + 1, sizeof(double));
+    double *v = (double *)calloc((size_t)3 * N + 1, sizeof(double));
+    double dt = prm[0], alpha = prm[4];
+    const double dt_max = prm[1], f_inc = prm[2], f_dec = prm[3], alpha_start = prm[4], f_alpha = prm[5];
+    const int n_min = (int)prm[6];
+    int npos = 0;
+    double U = energy_forces(pot, N, dim, r, diam, L, pp, f);
+    for (int s = 0; s < nsteps; ++s) {
+        if (Eser) Eser[s] = U;
+        for (int i = 0; i < N; ++i)
+            for (int k = 0; k < dim; ++k) {
+                v[3 * i + k] += 0.5 * dt * f[3 * i + k];
+                r[3 * i + k] += dt * v[3 * i + k];
+            }
+        U = energy_forces(pot, N, dim, r, diam, L, pp, f);
+        double P = 0.0, vv = 0.0, ff = 0.0;
+        for (int i = 0; i < N; ++i)
+            for (int k = 0; k < dim; ++k) {
+                v[3 * i + k] += 0.5 * dt * f[3 * i + k];
+                P += f[3 * i + k] * v[3 * i + k];
+                vv += v[3 * i + k] * v[3 * i + k];
+                ff += f[3 * i + k] * f[3 * i + k];
+            }
+        const double c = ff > 0.0 ? alpha * sqrt(vv) / sqrt(ff) : 0.0;
+        for (int i = 0; i < N; ++i)
+            for (int k = 0; k < dim; ++k) v[3 * i + k] = (1.0 - alpha) * v[3 * i + k] + c * f[3 * i + k];
+        if (P > 0.0) {
+            npos += 1;
+            if (npos > n_min) {
+                dt = fmin(dt * f_inc, dt_max);
+                alpha *= f_alpha;
+            }
+        } else {
+            dt *= f_dec;
+            for (int i = 0; i < 3 * N; ++i) v[i] = 0.0;
+            alpha = alpha_start;
+            npos = 0;
+        }
+        if (dtser) dtser[s] = dt;
+    }
+    if (Eser) Eser[nsteps] = U;
+    if (v_out)
+        for (int i = 0; i < 3 * N; ++i) v_out[i] = v[i];
+    if (st_out) {
+        st_out[0] = dt;
+        st_out[1] = alpha;
+        st_out[2] = (double)npos;
+    }
+    free(v);
     free(f);
 }
 
