@@ -275,6 +275,37 @@ JMD_API md_status md_integrate_langevin(const md_space *s, const md_pot *p, floa
 JMD_API md_status md_minimize(const md_space *s, const md_pot *p, int kind, float step, int nsteps, float *d_r,
                               float *d_f, md_nbr *nb, double *d_E, uint32_t *d_status, md_stream_t stream);
 
+/* FIRE (Sec. 3.3.1 minimisers; Bitzek et al., PRL 97, 170201 (2006)), unit
+ * mass, unwrapped coordinates as in md_minimize.  Each step: velocity-Verlet
+ * MD step with the current dt; P = F.v, |v|, |F| over all degrees of
+ * freedom (FP64 sums); v = (1 - alpha) v + alpha |v| F/|F|; if P > 0 the
+ * count of consecutive P > 0 steps grows and, once above n_min, dt =
+ * min(dt f_inc, dt_max) and alpha *= f_alpha; if P <= 0, dt *= f_dec, v = 0,
+ * alpha = alpha_start and the count restarts. */
+typedef struct {
+    float dt_start, dt_max, f_inc, f_dec, alpha_start, f_alpha;
+    int n_min;
+} md_fire_params;
+
+/* Bytes of the device FIRE state (dt, alpha, count, reduction partials). */
+JMD_API size_t md_fire_state_bytes(void);
+
+/* nsteps of FIRE on d_r [N][4] (LJ or soft sphere; nb built for d_r).
+ * restart = 1 starts from rest (d_v zeroed, state reset); restart = 0
+ * continues from d_v [N][4] and d_state (md_fire_state_bytes, 256-byte
+ * aligned, from an earlier restart).  d_E (nsteps+1 doubles, may be NULL)
+ * receives U before every step and after the last; d_f holds F at the final
+ * positions.  MD_ERR_INVALID for parameters outside dt_start > 0, dt_max >=
+ * dt_start, f_inc >= 1, 0 < f_dec < 1, 0 <= alpha_start < 1,
+ * 0 < f_alpha <= 1, n_min >= 0. */
+JMD_API md_status md_minimize_fire(const md_space *s, const md_pot *p, const md_fire_params *fp, int nsteps,
+                                   float *d_r, float *d_v, float *d_f, md_nbr *nb, void *d_state, int restart,
+                                   double *d_E, uint32_t *d_status, md_stream_t stream);
+
+/* Copies (dt, alpha, count of consecutive P > 0 steps) of a FIRE state to
+ * the host (synchronises the stream). */
+JMD_API md_status md_fire_state_read(const void *d_state, double *out3, md_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Learned potential: the pieces of a forward/backward and a training step   */
 /* (Sec. 4.1: energy + force loss).  sys_n as in md_bp_model.                */

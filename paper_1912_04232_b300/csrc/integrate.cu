@@ -159,6 +159,11 @@ __global__ void k_loop_init(uint32_t *ctl, uint32_t nsteps, uint32_t step0, unsi
     ctl[CTL_SEED_HI] = (uint32_t)(seed >> 32);
 }
 
+void enqueue_loop_init(uint32_t *ctl, uint32_t nsteps, cudaStream_t st)
+{
+    k_loop_init<<<1, 1, 0, st>>>(ctl, nsteps, 0u, 0ull);
+}
+
 struct NveCtx {
     Box box;
     int dim, N;

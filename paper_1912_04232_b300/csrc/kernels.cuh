@@ -67,6 +67,8 @@ struct PairArgs {
 
 NbrArgs make_nbr_args(const md_space *s, const float *d_r, const md_nbr *nb, uint32_t *d_status, int gated);
 void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st);
+// Device loop counters: step 0 of nsteps (energy series index).
+void enqueue_loop_init(uint32_t *ctl, uint32_t nsteps, cudaStream_t st);
 void enqueue_check_disp(const md_space *s, const float *d_r, const md_nbr *nb, cudaStream_t st);
 
 bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const md_nbr *nb, float *d_f,

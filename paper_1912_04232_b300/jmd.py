@@ -69,6 +69,16 @@ class md_bp_model(C.Structure):
                 ("Ei", C.c_void_p), ("sys_n", C.c_int)]
 
 
+class md_fire_params(C.Structure):
+    _fields_ = [("dt_start", C.c_float), ("dt_max", C.c_float), ("f_inc", C.c_float), ("f_dec", C.c_float),
+                ("alpha_start", C.c_float), ("f_alpha", C.c_float), ("n_min", C.c_int)]
+
+
+def fire_params(dt_start=0.1, dt_max=0.4, f_inc=1.1, f_dec=0.5, alpha_start=0.1, f_alpha=0.99, n_min=5):
+    """FIRE parameters (Bitzek et al. 2006 recommendations, dt_max = 4 dt_start)."""
+    return md_fire_params(dt_start, dt_max, f_inc, f_dec, alpha_start, f_alpha, n_min)
+
+
 class md_replica_desc(C.Structure):
     _fields_ = [("N", C.c_int), ("L", C.c_double), ("kind", C.c_int), ("eps", C.c_float), ("sigma", C.c_float),
                 ("r_cut", C.c_float), ("e_shift", C.c_float), ("alpha", C.c_float), ("skin", C.c_float),
@@ -100,6 +110,9 @@ _SIGS = {
     "md_integrate_langevin": [_P(md_space), _P(md_pot), _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float,
                               C.c_uint64, C.c_uint32, C.c_int, _P(md_nbr), _vp, _vp, C.c_int, _vp, _vp],
     "md_minimize": [_P(md_space), _P(md_pot), C.c_int, C.c_float, C.c_int, _vp, _vp, _P(md_nbr), _vp, _vp, _vp],
+    "md_minimize_fire": [_P(md_space), _P(md_pot), _P(md_fire_params), C.c_int, _vp, _vp, _vp, _P(md_nbr), _vp, C.c_int,
+                         _vp, _vp, _vp],
+    "md_fire_state_read": [_vp, _P(C.c_double), _vp],
     "md_status_poll": [_vp, _P(C.c_uint32), _vp],
     "md_bounded_wait": [_vp, C.c_uint64, _vp, _vp],
     "md_bp_descriptors": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp],
@@ -138,6 +151,8 @@ _lib.md_adjoint_workspace_size.restype = C.c_size_t
 _lib.md_adjoint_workspace_size.argtypes = [C.c_int, C.c_int, C.c_int]
 _lib.md_noalloc_scratch_bytes.restype = C.c_size_t
 _lib.md_noalloc_scratch_bytes.argtypes = []
+_lib.md_fire_state_bytes.restype = C.c_size_t
+_lib.md_fire_state_bytes.argtypes = []
 _lib.md_version.restype = C.c_char_p
 _lib.md_version.argtypes = []
 
@@ -246,6 +261,23 @@ def md_integrate_langevin(space, pot, r, v, f, mass, dt, gamma, kT, seed, step0,
 def md_minimize(space, pot, kind, step, nsteps, r, f, nb, E=None, status=None, stream=None):
     _check(_lib.md_minimize(C.byref(space), C.byref(pot), int(kind), float(step), int(nsteps), _ptr(r), _ptr(f),
                             C.byref(nb), _ptr(E), _ptr(status), _stream(stream)), "md_minimize")
+
+
+def md_fire_state_bytes() -> int:
+    return int(_lib.md_fire_state_bytes())
+
+
+def md_minimize_fire(space, pot, params, nsteps, r, v, f, nb, state, restart=True, E=None, status=None, stream=None):
+    _check(_lib.md_minimize_fire(C.byref(space), C.byref(pot), C.byref(params), int(nsteps), _ptr(r), _ptr(v), _ptr(f),
+                                 C.byref(nb), _ptr(state), int(bool(restart)), _ptr(E), _ptr(status), _stream(stream)),
+           "md_minimize_fire")
+
+
+def md_fire_state_read(state, stream=None):
+    """(dt, alpha, count of consecutive P > 0 steps) of a FIRE state."""
+    out = (C.c_double * 3)()
+    _check(_lib.md_fire_state_read(_ptr(state), out, _stream(stream)), "md_fire_state_read")
+    return float(out[0]), float(out[1]), int(out[2])
 
 
 def md_neighbor_list_build_noalloc(space, r, N, r_cut, skin, cap, nbr, cnt, status=None, stream=None):

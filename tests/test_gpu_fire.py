@@ -1,0 +1,139 @@
+"""GPU parity of FIRE minimisation (Sec. 3.3.1; Bitzek et al. 2006) against
+the FP64 oracle: the App. A disk packing, the configuration-2 packing, a
+closed-form head-on pair, a 3-D LJ quench, and continuation across calls."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_helpers import dev, status_word, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1912_04232_b300 as P
+    return P
+
+
+def _fire_gpu(P, r, L, nsteps, dim=2, pot="soft", r_cut=None, chunks=None, params=None):
+    import torch
+    s = P.md_space_periodic(dim, [L] * dim)
+    if pot == "soft":
+        rc = float(np.max(r[:, 3])) if r_cut is None else r_cut
+        pp = P.soft_pot()
+    else:
+        rc = 2.5
+        pp = P.lj_pot()
+    nl = P.NeighborList(s, r.shape[0], rc, 0.3, 128)
+    rd = to_dev(r, torch.float32)
+    vd = torch.zeros_like(rd)
+    fd = torch.zeros_like(rd)
+    state = torch.zeros(P.md_fire_state_bytes() + 256, dtype=torch.uint8, device=dev())
+    off = (-state.data_ptr()) % 256
+    state = state[off:off + P.md_fire_state_bytes()]
+    st = status_word()
+    prm = params or P.fire_params()
+    nl.build(rd, st)
+    E = torch.zeros(nsteps + 1, dtype=torch.float64, device=dev())
+    if chunks is None:
+        P.md_minimize_fire(s, pp, prm, nsteps, rd, vd, fd, nl.plan, state, True, E, st)
+    else:
+        done, restart, parts = 0, True, []
+        for c in chunks:
+            Ec = torch.zeros(c + 1, dtype=torch.float64, device=dev())
+            P.md_minimize_fire(s, pp, prm, c, rd, vd, fd, nl.plan, state, restart, Ec, st)
+            parts.append(Ec)
+            restart = False
+            done += c
+        E = torch.cat([parts[0]] + [p[1:] for p in parts[1:]])
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    return rd.cpu().numpy(), vd.cpu().numpy(), fd.cpu().numpy(), E.cpu().numpy(), P.md_fire_state_read(state)
+
+
+def _packing(N, D, phi, seed=0):
+    pk = W.packing_2d(N=N, D=D, phi=phi, seed=seed)
+    L = W.f32(W.packing_box(pk.N, pk.D, pk.phi))
+    r = np.zeros((pk.N, 4), np.float32)
+    r[:, :2] = (pk.s0 * L).astype(np.float32)
+    r[:, :2] = np.where(r[:, :2] >= L, 0.0, r[:, :2])
+    r[:, 3] = pk.diam.astype(np.float32)
+    return r, L, pk.diam
+
+
+def test_fire_head_on_pair_closed_form(P):
+    r = np.array([[2.0, 2.0, 0, 1.0], [2.6, 2.0, 0, 1.0]], np.float32)
+    x, v, f, E, st = _fire_gpu(P, r, 10.0, 1, r_cut=1.0)
+    dt, f0 = 0.1, 0.4
+    f1 = 1.0 - (0.6 + dt * dt * f0)
+    v1 = 0.5 * dt * (f0 + f1)
+    np.testing.assert_allclose(x[:, 0], [2.0 - 0.5 * dt * dt * f0, 2.6 + 0.5 * dt * dt * f0], rtol=0, atol=2e-6)
+    np.testing.assert_allclose(v[:, 0], [-v1, v1], rtol=2e-5)
+    assert st[2] == 1
+
+
+@pytest.mark.parametrize("N, D, nsteps", [(128, 1.4, 40), (1024, 1.2, 30)])
+def test_fire_trajectory_matches_oracle(P, N, D, nsteps):
+    r, L, diam = _packing(N, D, 0.9)
+    x, v, f, E, st = _fire_gpu(P, r, L, nsteps)
+    xo, vo, Eo, dto, sto = O.fire(r, L, "soft", nsteps=nsteps, dim=2, diam=diam)
+    assert (st[2], round(st[0], 6)) == (sto[2], round(sto[0], 6))
+    assert abs(st[1] - sto[1]) <= 1e-6 * sto[1]
+    # tolerance from the trajectory's own sensitivity: the FP64 oracle from
+    # positions moved by 1e-6 (FP32 rounding of coordinates ~30) spreads by
+    # `spread`; the FP32 run may differ by at most a few times that
+    rng = np.random.Generator(np.random.PCG64(1))
+    rp = r.astype(np.float64)
+    rp[:, :2] += rng.uniform(-1e-6, 1e-6, size=(N, 2))
+    xp, vp, _, _, _ = O.fire(rp, L, "soft", nsteps=nsteps, dim=2, diam=diam)
+    spread = max(np.abs(xp[:, :2] - xo[:, :2]).max(), 1e-5)
+    vspread = max(np.abs(vp[:, :2] - vo[:, :2]).max(), 1e-5)
+    assert np.abs(x[:, :2] - xo[:, :2]).max() < 5 * spread
+    assert np.abs(v[:, :2] - vo[:, :2]).max() < 5 * vspread
+    np.testing.assert_allclose(E, Eo, rtol=2e-4, atol=1e-7 * abs(Eo[0]))
+
+
+def test_fire_app_a_packing_300_steps(P):
+    # the paper's App. A system (128 disks, 300 FIRE steps): the FP32
+    # minimisation ends at the FP64 energy and the forces vanish alike
+    r, L, diam = _packing(128, 1.4, 0.9)
+    x, v, f, E, st = _fire_gpu(P, r, L, 300)
+    xo, vo, Eo, dto, sto = O.fire(r, L, "soft", nsteps=300, dim=2, diam=diam)
+    assert E[-1] < 0.02 * E[0]
+    assert abs(E[-1] - Eo[-1]) <= 1e-3 * Eo[0]
+    assert np.abs(f[:, :2]).max() < 0.05 * np.abs(O.soft(r, diam, L, dim=2)[1]).max()
+
+
+def test_fire_continuation_is_bitwise(P):
+    r, L, diam = _packing(1024, 1.2, 0.9)
+    a = _fire_gpu(P, r, L, 50)
+    b = _fire_gpu(P, r, L, 50, chunks=[20, 17, 13])
+    for x, y in zip(a[:4], b[:4]):
+        np.testing.assert_array_equal(x, y)
+    assert a[4] == b[4]
+
+
+def test_fire_lj_quench_3d(P):
+    # LJ needs an LJ-sized step: dt_start = the NVE dt, dt_max = 4 x
+    c = W.lj_small()
+    prm = dict(dt_start=0.005, dt_max=0.02)
+    x, v, f, E, st = _fire_gpu(P, c.r, c.L, 40, dim=3, pot="lj", params=P.fire_params(**prm))
+    xo, vo, Eo, dto, sto = O.fire(c.r, c.L, "lj", nsteps=40, dim=3, fire_params=prm)
+    np.testing.assert_allclose(E, Eo, rtol=1e-4)
+    assert (st[2], round(st[0], 6)) == (sto[2], round(sto[0], 6))
+    d = x[:, :3] - xo[:, :3]
+    d -= c.L * np.round(d / c.L)
+    assert np.abs(d).max() < 1e-3
+    assert E[-1] < E[0]
+
+
+def test_fire_rejects_bad_parameters(P):
+    import torch
+    s = P.md_space_periodic(2, [10.0, 10.0])
+    nl = P.NeighborList(s, 4, 1.0, 0.3, 16)
+    z = torch.zeros((4, 4), dtype=torch.float32, device=dev())
+    state = torch.zeros(P.md_fire_state_bytes(), dtype=torch.uint8, device=dev())
+    with pytest.raises(P.MDError):
+        P.md_minimize_fire(s, P.soft_pot(), P.fire_params(f_dec=1.5), 1, z, z.clone(), z.clone(), nl.plan, state)
