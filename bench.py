@@ -54,6 +54,7 @@ def parse():
                     help="1: cell-centred forces over 16-bit local rows (MD_NBR_LOCAL_ROWS); 0: int32 rows")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain-SW section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-replica section")
+    ap.add_argument("--no-fire", action="store_true", help="skip the FIRE minimisation section")
     return ap.parse_args()
 
 
@@ -273,6 +274,62 @@ def batched_section(steps=500):
             "speedup": ms_s / ms_b, "status": code}
 
 
+def fire_section():
+    """FIRE minimisation: a quench of the N = 256,000 LJ liquid (200 steps,
+    dt_start = the NVE dt, dt_max = 4x) and the App. A packing (128 disks,
+    D = 1.4, packing fraction 0.9, 300 steps, Bitzek's parameters)."""
+    import torch
+    import paper_1912_04232_b300 as P
+    import workloads as W
+    dev = torch.device("cuda")
+    out = {}
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    sb = P.md_fire_state_bytes()
+    state = torch.zeros(sb + 256, dtype=torch.uint8, device=dev)
+    state = state[(-state.data_ptr()) % 256:][:sb]
+
+    def run(s, pot, prm, r0, rc, nsteps, reps):
+        nl = P.NeighborList(s, r0.shape[0], rc, 0.3, 128)
+        r = torch.empty_like(r0)
+        v = torch.zeros_like(r0)
+        f = torch.zeros_like(r0)
+        E = torch.zeros(nsteps + 1, dtype=torch.float64, device=dev)
+        ts = []
+        for k in range(reps + 1):
+            r.copy_(r0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            nl.build(r, st)
+            P.md_minimize_fire(s, pot, prm, nsteps, r, v, f, nl.plan, state, True, E, st)
+            e1.record()
+            e1.synchronize()
+            if k:
+                ts.append(e0.elapsed_time(e1))
+        return min(ts), E.cpu().numpy(), P.md_fire_state_read(state)
+
+    c = W.lj_large(0)
+    s = P.md_space_periodic(3, [c.L] * 3)
+    r0 = torch.from_numpy(c.r).to(dev)
+    ms, E, fs = run(s, P.lj_pot(), P.fire_params(dt_start=0.005, dt_max=0.02), r0, 2.5, 200, 2)
+    out["lj256k_quench"] = {"N": c.N, "steps": 200, "ms": ms, "particle_steps_per_s": c.N * 200 / (ms * 1e-3),
+                            "E_per_particle_start": float(E[0] / c.N), "E_per_particle_end": float(E[-1] / c.N),
+                            "final_dt_alpha_count": fs}
+    pk = W.packing_2d(N=128, D=1.4, phi=0.9, seed=0)
+    L = W.f32(W.packing_box(pk.N, pk.D, pk.phi))
+    x = np.zeros((pk.N, 4), np.float32)
+    x[:, :2] = (pk.s0 * L).astype(np.float32)
+    x[:, :2] = np.where(x[:, :2] >= L, 0.0, x[:, :2])
+    x[:, 3] = pk.diam.astype(np.float32)
+    s2 = P.md_space_periodic(2, [L, L])
+    ms2, E2, fs2 = run(s2, P.soft_pot(), P.fire_params(), torch.from_numpy(x).to(dev), 1.4, 300, 5)
+    out["app_a_packing"] = {"N": pk.N, "steps": 300, "ms": ms2, "us_per_step": 1e3 * ms2 / 300,
+                            "E_start": float(E2[0]), "E_end": float(E2[-1])}
+    code = P.md_status_poll(st)
+    out["status"] = code
+    return out
+
+
 def _source_sha():
     """Hash of the sources of the pair-force kernels (a stored DRAM-traffic
     figure is only reported while it still describes the built kernel)."""
@@ -449,6 +506,8 @@ def main():
         extra["learned_vs_sw"] = learned_section()
     if rank == 0 and not args.no_batch:
         extra["batched"] = batched_section()
+    if rank == 0 and not args.no_fire:
+        extra["fire"] = fire_section()
 
     if rank == 0:
         line = {

@@ -50,6 +50,9 @@ def lib():
                              C.c_int, _dp, _dp]
         L.or_gd.restype = None
         L.or_gd.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, _dp, C.c_int, _dp, C.c_double, C.c_int, _dp]
+        L.or_nhc.restype = None
+        L.or_nhc.argtypes = [C.c_int, C.c_int, _dp, _dp, C.c_void_p, _dp, C.c_int, _dp, C.c_double, C.c_double,
+                             C.c_double, C.c_double, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
         L.or_fire.restype = None
         L.or_fire.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, _dp, C.c_int, _dp, _dp, C.c_int, C.c_void_p,
                               C.c_void_p, C.c_void_p, C.c_void_p]
@@ -220,6 +223,27 @@ def gd(r, L, pot="soft", eta=0.05, nsteps=10, dim=2, diam=None, **kw):
         dptr = diam.ctypes.data
     lib().or_gd(N, dim, x, dptr, _box(L, dim), _POT[pot], _pp(pot, **kw), eta, nsteps, E)
     return x, E
+
+
+def nhc(r, v, L, pot="lj", mass=1.0, dt=0.005, kT=1.0, tau=None, M=3, nsteps=10, dim=3, diam=None, therm=None,
+        **kw):
+    """Nose-Hoover chain NVT (tau defaults to 100 dt).  Returns (r, v, PE,
+    KE, H' [nsteps+1 each], thermostat state (xi[M], w[M]))."""
+    x = _pos(r, dim)
+    vv = _pos(v, dim)
+    N = x.shape[0]
+    PE = np.zeros(nsteps + 1)
+    KE = np.zeros(nsteps + 1)
+    H = np.zeros(nsteps + 1)
+    th = np.zeros(2 * M) if therm is None else np.ascontiguousarray(np.concatenate(therm), np.float64).copy()
+    dptr = None
+    if diam is not None:
+        diam = np.ascontiguousarray(diam, np.float64)
+        dptr = diam.ctypes.data
+    tau = 100.0 * dt if tau is None else tau
+    lib().or_nhc(N, dim, x, vv, dptr, _box(L, dim), _POT[pot], _pp(pot, **kw), mass, dt, kT, tau, M, nsteps, th,
+                 PE, KE, H)
+    return x, vv, PE, KE, H, (th[:M].copy(), th[M:].copy())
 
 
 # FIRE parameters (Bitzek et al. 2006 recommendations; dt_max = 4 dt_start)

@@ -14,7 +14,7 @@
  *     for Lennard-Jones and soft spheres
  *   - Stillinger-Weber 2-body + 3-body energy and forces        (Sec. 3.3.2)
  *   - velocity-Verlet NVE, gradient-descent and FIRE minimisation,
- *     BAOAB Langevin NVT                                         (Sec. 3.3.1)
+ *     BAOAB Langevin NVT, Nose-Hoover chain NVT                  (Sec. 3.3.1)
  *   - reverse-mode derivative of the final energy of a gradient-descent
  *     minimisation with respect to the small-disk diameter D     (Sec. 4.2, App. A)
  *   - Philox4x32-10 counter-based generator (Salmon et al., SC'11), the
@@ -543,6 +543,96 @@ void or_gd(int N, int dim, double *r, const double *diam, const double *L, int p
     }
     double U = energy_forces(pot, N, dim, r, diam, L, pp, f);
     if (Eser) Eser[nsteps] = U;
+    free(f);
+}
+
+/* Nose-Hoover chain NVT (Sec. 3.3.1 lists Nose-Hoover constant-temperature
+ * simulation, citing Martyna, Klein, Tuckerman 1992).  One step is the
+ * symmetric Trotter splitting
+ *     chain(dt/2) . kick(dt/2) . drift(dt) . kick(dt/2) . chain(dt/2)
+ * (velocity Verlet between two thermostat half-steps).  The chain half-step
+ * is the sweep of Martyna, Tuckerman, Tobias, Klein (1996) with one
+ * sub-step, on thermostat velocities w_k = p_k/Q_k with "forces"
+ *     G_1 = (2K - g kT)/Q_1,   G_k = (Q_{k-1} w_{k-1}^2 - kT)/Q_k  (k > 1):
+ *   w_M += dt/4 G_M
+ *   k = M-1..1:  w_k *= exp(-dt/8 w_{k+1}); w_k += dt/4 G_k; w_k *= exp(-dt/8 w_{k+1})
+ *   s = exp(-dt/2 w_1);  v *= s;  K *= s^2;  xi_k += dt/2 w_k (all k)
+ *   k = 1..M-1:  w_k *= exp(-dt/8 w_{k+1}); w_k += dt/4 G_k; w_k *= exp(-dt/8 w_{k+1})
+ *   w_M += dt/4 G_M
+ * g = dim N degrees of freedom; Q_1 = g kT tau^2, Q_k = kT tau^2.  The
+ * conserved quantity is H' = K + U + sum_k Q_k w_k^2 / 2 + g kT xi_1 +
+ * kT sum_{k>1} xi_k.  therm (2M, in/out) holds (xi_1..xi_M, w_1..w_M).
+ * PE, KE, Hext: nsteps+1 entries, entry 0 the initial state. */
+static void nhc_half(int M, double *xi, double *w, const double *Q, double gkT, double kT, double dt, double *K,
+                     double *scale)
+{
+    const double h4 = 0.25 * dt, h8 = 0.125 * dt;
+    double G;
+    G = (M > 1) ? (Q[M - 2] * w[M - 2] * w[M - 2] - kT) / Q[M - 1] : (2.0 * (*K) - gkT) / Q[0];
+    w[M - 1] += h4 * G;
+    for (int k = M - 2; k >= 0; --k) {
+        const double e = exp(-h8 * w[k + 1]);
+        w[k] *= e;
+        G = (k == 0) ? (2.0 * (*K) - gkT) / Q[0] : (Q[k - 1] * w[k - 1] * w[k - 1] - kT) / Q[k];
+        w[k] += h4 * G;
+        w[k] *= e;
+    }
+    const double s = exp(-0.5 * dt * w[0]);
+    *scale = s;
+    *K *= s * s;
+    for (int k = 0; k < M; ++k) xi[k] += 0.5 * dt * w[k];
+    for (int k = 0; k < M - 1; ++k) {
+        const double e = exp(-h8 * w[k + 1]);
+        w[k] *= e;
+        G = (k == 0) ? (2.0 * (*K) - gkT) / Q[0] : (Q[k - 1] * w[k - 1] * w[k - 1] - kT) / Q[k];
+        w[k] += h4 * G;
+        w[k] *= e;
+    }
+    G = (M > 1) ? (Q[M - 2] * w[M - 2] * w[M - 2] - kT) / Q[M - 1] : (2.0 * (*K) - gkT) / Q[0];
+    w[M - 1] += h4 * G;
+}
+
+static double nhc_energy(int M, const double *xi, const double *w, const double *Q, double gkT, double kT)
+{
+    double e = 0.0;
+    for (int k = 0; k < M; ++k) e += 0.5 * Q[k] * w[k] * w[k];
+    e += gkT * xi[0];
+    for (int k = 1; k < M; ++k) e += kT * xi[k];
+    return e;
+}
+
+void or_nhc(int N, int dim, double *r, double *v, const double *diam, const double *L, int pot, const double *pp,
+            double mass, double dt, double kT, double tau, int M, int nsteps, double *therm, double *PE, double *KE,
+            double *Hext)
+{
+    double *f = (double *)calloc((size_t)3 * N + 1, sizeof(double));
+    double Q[16], *xi = therm, *w = therm + M;
+    const double g = (double)dim * N, gkT = g * kT;
+    Q[0] = gkT * tau * tau;
+    for (int k = 1; k < M; ++k) Q[k] = kT * tau * tau;
+    double U = energy_forces(pot, N, dim, r, diam, L, pp, f);
+    double K = kinetic(N, dim, v, mass);
+    if (PE) PE[0] = U;
+    if (KE) KE[0] = K;
+    if (Hext) Hext[0] = K + U + nhc_energy(M, xi, w, Q, gkT, kT);
+    for (int s = 1; s <= nsteps; ++s) {
+        double sc;
+        nhc_half(M, xi, w, Q, gkT, kT, dt, &K, &sc);
+        for (int i = 0; i < N; ++i)
+            for (int k = 0; k < dim; ++k) {
+                v[3 * i + k] = v[3 * i + k] * sc + 0.5 * dt * f[3 * i + k] / mass;
+                r[3 * i + k] = wrap64(r[3 * i + k] + dt * v[3 * i + k], L[k]);
+            }
+        U = energy_forces(pot, N, dim, r, diam, L, pp, f);
+        for (int i = 0; i < N; ++i)
+            for (int k = 0; k < dim; ++k) v[3 * i + k] += 0.5 * dt * f[3 * i + k] / mass;
+        K = kinetic(N, dim, v, mass);
+        nhc_half(M, xi, w, Q, gkT, kT, dt, &K, &sc);
+        for (int i = 0; i < 3 * N; ++i) v[i] *= sc;
+        if (PE) PE[s] = U;
+        if (KE) KE[s] = K;
+        if (Hext) Hext[s] = K + U + nhc_energy(M, xi, w, Q, gkT, kT);
+    }
     free(f);
 }
 
