@@ -243,6 +243,24 @@ JMD_API md_status md_set_nve_fusion(int on);
 /* ------------------------------------------------------------------------ */
 /* Dynamics (Sec. 3.3.1).                                                   */
 /* ------------------------------------------------------------------------ */
+/* Nose-Hoover chain NVT (Sec. 3.3.1, Nose-Hoover constant temperature;
+ * Martyna, Klein, Tuckerman 1992).  Each step is the symmetric splitting
+ * chain(dt/2) . kick(dt/2) . drift(dt) . kick(dt/2) . chain(dt/2), the chain
+ * half-step being the sweep of Martyna, Tuckerman, Tobias, Klein (1996)
+ * with one sub-step; g = dim N, Q_1 = g kT tau^2, Q_k = kT tau^2.  Any
+ * potential of md_energy_forces.  d_therm: md_nhc_state_doubles(M) device
+ * doubles, caller-owned: chain positions xi[M], velocities w[M], masses and
+ * constants; reset = 1 zeroes xi and w, reset = 0 continues.  d_PE, d_KE,
+ * d_H (nsteps doubles each, may be NULL): potential, kinetic and conserved
+ * extended energy H' = K + U + sum Q_k w_k^2/2 + g kT xi_1 + kT sum_{k>1} xi_k
+ * after each step.  1 <= M <= 8, kT > 0, tau > 0, else MD_ERR_INVALID.
+ * Positions stay inside [0, L). */
+JMD_API size_t md_nhc_state_doubles(int M);
+JMD_API md_status md_integrate_nhc(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f, float mass,
+                                   float dt, float kT, float tau, int M, int nsteps, md_nbr *nb, double *d_therm,
+                                   int reset, double *d_PE, double *d_KE, double *d_H, int use_graph,
+                                   uint32_t *d_status, md_stream_t stream);
+
 /* nsteps of velocity-Verlet NVE.  On entry d_f must hold the forces at d_r
  * (md_energy_forces) and nb a list built for d_r.  Each step:
  *   v += dt/2 F/m;  r = wrap(r + dt v);  rebuild the list if needed;

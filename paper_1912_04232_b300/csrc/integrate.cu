@@ -14,6 +14,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "nhc.cuh"
 
 namespace jmd {
 
@@ -62,6 +63,99 @@ __global__ void __launch_bounds__(256) k_kick_drift(float4 *r, float4 *v, const 
             cudaGraphSetConditional((cudaGraphConditionalHandle)cond_if, flag ? 1u : 0u);
         }
     }
+}
+
+// Nose-Hoover chain step, first part: the velocity factor left by the
+// thermostat half-steps (previous step's closing and this step's opening
+// one), then the kick and the drift, as k_kick_drift.
+template <int DIM, int COND>
+__global__ void __launch_bounds__(256) k_nhc_kick_drift(float4 *r, float4 *v, const float4 *f, const float4 *rref,
+                                                        int N, float hdm, float dt, Box box, float half_skin2,
+                                                        uint32_t *ctl, unsigned long long cond_if, const double *nhc,
+                                                        int M)
+{
+    count_launch();
+    __shared__ bool last;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool mv = false;
+    if (i < N) {
+        const float sc = (float)nhc[3 * M + NHC_SCLOSE], so = (float)nhc[3 * M + NHC_SOPEN];
+        float4 fi = f[i], vi = v[i], ri = r[i];
+        vi.x *= sc;
+        vi.y *= sc;
+        vi.z *= sc;
+        vi.x = vi.x * so + hdm * fi.x;
+        vi.y = vi.y * so + hdm * fi.y;
+        ri.x = wrap_coord(ri.x + dt * vi.x, box.L[0], box.Linv[0]);
+        ri.y = wrap_coord(ri.y + dt * vi.y, box.L[1], box.Linv[1]);
+        if (DIM == 3) {
+            vi.z = vi.z * so + hdm * fi.z;
+            ri.z = wrap_coord(ri.z + dt * vi.z, box.L[2], box.Linv[2]);
+        }
+        v[i] = vi;
+        r[i] = ri;
+        float dx, dy, dz;
+        mv = dist2_rn<DIM>(ri, rref[i], box, dx, dy, dz) > half_skin2;
+    }
+    if (__any_sync(0xffffffffu, mv) && (threadIdx.x & 31) == 0) {
+        ctl[CTL_REBUILD] = 1u;
+        if (COND) __threadfence();
+    }
+    if (COND) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            unsigned t = atomicAdd(&ctl[CTL_TICKET2], 1u);
+            last = (t == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (last && threadIdx.x == 0) {
+            __threadfence();
+            unsigned flag = *(volatile uint32_t *)&ctl[CTL_REBUILD];
+            ctl[CTL_TICKET2] = 0u;
+            cudaGraphSetConditional((cudaGraphConditionalHandle)cond_if, flag ? 1u : 0u);
+        }
+    }
+}
+
+// Before the loop (one block): the first step's opening thermostat
+// half-step, from the kinetic energy of the initial velocities (reset) or
+// the one the previous call's last step left (continuation, whose closing
+// factor the velocities already carry).
+__global__ void __launch_bounds__(1024) k_nhc_begin(const float4 *v, int N, float mass, double *nhc, int M,
+                                                    int reset)
+{
+    count_launch();
+    __shared__ double sh[32];
+    double *c = nhc + 3 * M;
+    double K = 0.0;
+    if (reset) {
+        float k = 0.0f;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const float4 vi = v[i];
+            k += 0.5f * mass * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
+        }
+        K = block_sum_f64((double)k, sh);
+    }
+    if (threadIdx.x == 0) {
+        if (!reset) K = c[NHC_K];
+        c[NHC_SCLOSE] = 1.0;
+        c[NHC_SOPEN] = nhc_half_step(nhc, M, K);
+    }
+}
+
+// After the loop: the last step's closing velocity factor.
+__global__ void __launch_bounds__(256) k_nhc_end(float4 *v, int N, const double *nhc, int M)
+{
+    count_launch();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float sc = (float)nhc[3 * M + NHC_SCLOSE];
+    float4 vi = v[i];
+    vi.x *= sc;
+    vi.y *= sc;
+    vi.z *= sc;
+    v[i] = vi;
 }
 
 // BAOAB Langevin (Sec. 3.3.1), first part B-A-O-A:
@@ -176,6 +270,8 @@ struct NveCtx {
     int pot;
     int langevin;                 // 0: NVE kick-drift, 1: BAOAB first part
     int fused;                    // 1: kick-drift fused into the force kernel (pair potentials, NVE)
+    int nhc;                      // 1: Nose-Hoover chain (thermostat state in pa.nhc)
+    int nhc_reset;                // 1: the chain starts at rest, K from the initial velocities
     float c1, c2;                 // Langevin O-step coefficients
     unsigned long long cond_if;   // graph IF handle (0 outside graphs)
 };
@@ -183,6 +279,25 @@ struct NveCtx {
 static void enqueue_kick_drift(const NveCtx &c, int cond, cudaStream_t st)
 {
     int g = (c.N + 255) / 256;
+    if (c.nhc) {
+        const unsigned long long ci = cond ? c.cond_if : 0ull;
+        if (c.dim == 3) {
+            if (cond)
+                k_nhc_kick_drift<3, 1><<<g, 256, 0, st>>>(c.r, c.v, c.f, c.rref, c.N, c.hdm, c.dt, c.box, c.half_skin2,
+                                                          c.ctl, ci, c.pa.nhc, c.pa.nhc_M);
+            else
+                k_nhc_kick_drift<3, 0><<<g, 256, 0, st>>>(c.r, c.v, c.f, c.rref, c.N, c.hdm, c.dt, c.box, c.half_skin2,
+                                                          c.ctl, ci, c.pa.nhc, c.pa.nhc_M);
+        } else {
+            if (cond)
+                k_nhc_kick_drift<2, 1><<<g, 256, 0, st>>>(c.r, c.v, c.f, c.rref, c.N, c.hdm, c.dt, c.box, c.half_skin2,
+                                                          c.ctl, ci, c.pa.nhc, c.pa.nhc_M);
+            else
+                k_nhc_kick_drift<2, 0><<<g, 256, 0, st>>>(c.r, c.v, c.f, c.rref, c.N, c.hdm, c.dt, c.box, c.half_skin2,
+                                                          c.ctl, ci, c.pa.nhc, c.pa.nhc_M);
+        }
+        return;
+    }
     if (c.langevin) {
         if (cond)
             k_baoa<1><<<g, 256, 0, st>>>(c.r, c.v, c.f, c.rref, c.N, c.hdm, c.dt, c.c1, c.c2, c.box, c.half_skin2,
@@ -219,6 +334,20 @@ static void enqueue_nve_step(const NveCtx &c, cudaStream_t st)
 static void enqueue_final_positions(const NveCtx &c, cudaStream_t st)
 {
     k_final_positions<<<(c.N + 255) / 256, 256, 0, st>>>(c.r, c.pa.r_alt, c.N, c.ctl);
+}
+
+// Work before and after the loop (fused NVE: first kick-drift / final copy;
+// Nose-Hoover chain: opening half-step / closing velocity factor).
+static void enqueue_loop_pre(const NveCtx &c, int cond, cudaStream_t st)
+{
+    if (c.fused) enqueue_kick_drift(c, cond, st);
+    if (c.nhc) k_nhc_begin<<<1, 1024, 0, st>>>(c.v, c.N, c.pa.mass, c.pa.nhc, c.pa.nhc_M, c.nhc_reset);
+}
+
+static void enqueue_loop_post(const NveCtx &c, cudaStream_t st)
+{
+    if (c.fused) enqueue_final_positions(c, st);
+    if (c.nhc) k_nhc_end<<<(c.N + 255) / 256, 256, 0, st>>>(c.v, c.N, c.pa.nhc, c.pa.nhc_M);
 }
 
 // ---------------------------------------------------------------------------
@@ -271,10 +400,10 @@ static md_status build_nve_graph(const NveCtx &c0, NveGraph &out)
     c.pa.use_cond = 1;
     if (c.fused) c.pa.cond_if = (unsigned long long)hi;
     cudaGraphNode_t wn;
-    if (c.fused) {
-        // top level: first kick-drift -> WHILE -> final copy
+    if (c.fused || c.nhc) {
+        // top level: loop prologue -> WHILE -> loop epilogue
         JMD_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-        enqueue_kick_drift(c, 1, cs);
+        enqueue_loop_pre(c, 1, cs);
         cudaStreamCaptureStatus tst;
         cudaGraph_t tg = nullptr;
         const cudaGraphNode_t *tdeps = nullptr;
@@ -282,7 +411,7 @@ static md_status build_nve_graph(const NveCtx &c0, NveGraph &out)
         JMD_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &tst, nullptr, &tg, &tdeps, nullptr, &tnd));
         JMD_CUDA_TRY(cudaGraphAddNode(&wn, tg, tdeps, nullptr, tnd, wp));
         JMD_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
-        enqueue_final_positions(c, cs);
+        enqueue_loop_post(c, cs);
         JMD_CUDA_TRY(cudaStreamEndCapture(cs, &g));
     } else {
         JMD_CUDA_TRY(cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, wp));
@@ -374,7 +503,8 @@ static int g_fuse_nve = 1;   // md_set_nve_fusion
 static md_status run_dynamics(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f, float mass,
                               float dt, int nsteps, md_nbr *nb, double *d_PE, double *d_KE, int use_graph,
                               uint32_t *d_status, cudaStream_t st, int langevin, float gamma, float kT,
-                              unsigned long long seed, uint32_t step0)
+                              unsigned long long seed, uint32_t step0, double *d_nhc = nullptr, int nhc_M = 0,
+                              double *d_H = nullptr, int nhc_reset = 1)
 {
     if (!s || !p || !d_r || !d_v || !d_f || !nb || nsteps < 0 || !(mass > 0.0f)) return MD_ERR_INVALID;
     if (s->dim != nb->dim || !nb->ws || !nb->rref) return MD_ERR_INVALID;
@@ -406,6 +536,13 @@ static md_status run_dynamics(const md_space *s, const md_pot *p, float *d_r, fl
     c.pa.status = d_status;
     c.pot = p->kind;
     c.langevin = langevin;
+    if (d_nhc) {
+        c.nhc = 1;
+        c.pa.nhc = d_nhc;
+        c.pa.nhc_M = nhc_M;
+        c.pa.H_out = d_H;
+        c.nhc_reset = nhc_reset;
+    }
     if (langevin) {
         double e = exp(-(double)gamma * (double)dt);
         c.c1 = (float)e;
@@ -413,7 +550,7 @@ static md_status run_dynamics(const md_space *s, const md_pot *p, float *d_r, fl
     }
     // pair potentials in NVE: kick-drift fused into the force kernel,
     // positions alternating with the workspace buffer
-    c.fused = (!langevin && (p->kind == MD_LJ || p->kind == MD_SOFT_SPHERE) && g_fuse_nve) ? 1 : 0;
+    c.fused = (!langevin && !c.nhc && (p->kind == MD_LJ || p->kind == MD_SOFT_SPHERE) && g_fuse_nve) ? 1 : 0;
     if (c.fused) {
         const WsPtrs w = ws_ptrs(nb);
         c.pa.r_alt = w.ralt;
@@ -425,9 +562,9 @@ static md_status run_dynamics(const md_space *s, const md_pot *p, float *d_r, fl
     if (nsteps == 0) return MD_OK;
     if (use_graph) return nve_graph_run(c, nsteps, step0, seed, st);
     k_loop_init<<<1, 1, 0, st>>>(c.ctl, (uint32_t)nsteps, step0, seed);
-    if (c.fused) enqueue_kick_drift(c, 0, st);
+    enqueue_loop_pre(c, 0, st);
     for (int k = 0; k < nsteps; ++k) enqueue_nve_step(c, st);
-    if (c.fused) enqueue_final_positions(c, st);
+    enqueue_loop_post(c, st);
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
 }
@@ -438,6 +575,36 @@ extern "C" md_status md_integrate_nve(const md_space *s, const md_pot *p, float 
 {
     return run_dynamics(s, p, d_r, d_v, d_f, mass, dt, nsteps, nb, d_PE, d_KE, use_graph, d_status,
                         (cudaStream_t)stream, 0, 0.0f, 0.0f, 0ull, 0u);
+}
+
+// Nose-Hoover chain state on the host side: masses and constants; the chain
+// positions and velocities are zeroed when reset.
+__global__ void k_nhc_setup(double *nhc, int M, double gkT, double kT, double tau, double dt, int reset)
+{
+    count_launch();
+    if (reset)
+        for (int k = 0; k < 2 * M; ++k) nhc[k] = 0.0;
+    nhc[2 * M] = gkT * tau * tau;
+    for (int k = 1; k < M; ++k) nhc[2 * M + k] = kT * tau * tau;
+    nhc[3 * M + NHC_GKT] = gkT;
+    nhc[3 * M + NHC_KT] = kT;
+    nhc[3 * M + NHC_DT] = dt;
+}
+
+extern "C" size_t md_nhc_state_doubles(int M) { return (M >= 1 && M <= NHC_MAXM) ? (size_t)nhc_words(M) : 0; }
+
+extern "C" md_status md_integrate_nhc(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f,
+                                      float mass, float dt, float kT, float tau, int M, int nsteps, md_nbr *nb,
+                                      double *d_therm, int reset, double *d_PE, double *d_KE, double *d_H,
+                                      int use_graph, uint32_t *d_status, md_stream_t stream)
+{
+    if (!d_therm || M < 1 || M > NHC_MAXM || !(kT > 0.0f) || !(tau > 0.0f) || !nb) return MD_ERR_INVALID;
+    const double gkT = (double)(s ? s->dim : 0) * (double)nb->N * (double)kT;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_nhc_setup<<<1, 1, 0, st>>>(d_therm, M, gkT, (double)kT, (double)tau, (double)dt, reset);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return run_dynamics(s, p, d_r, d_v, d_f, mass, dt, nsteps, nb, d_PE, d_KE, use_graph, d_status, st, 0, 0.0f,
+                        0.0f, 0ull, 0u, d_therm, M, d_H, reset ? 1 : 0);
 }
 
 extern "C" md_status md_set_nve_fusion(int on)

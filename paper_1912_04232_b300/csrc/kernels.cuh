@@ -53,6 +53,11 @@ struct PairArgs {
     const uint16_t *lrow;
     const int32_t *atoms, *cell_start;
     int nc[3], ncell, max_blocks;
+    // Nose-Hoover chain (nhc.cuh): thermostat state, chain length, series of
+    // the conserved extended energy
+    double *nhc;
+    int nhc_M;
+    double *H_out;
     // reductions
     double *E_out, *KE_out;
     int series;             // 1: write E_out[ctl[CTL_STEP]] and advance the counter

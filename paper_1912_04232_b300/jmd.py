@@ -113,6 +113,8 @@ _SIGS = {
     "md_minimize_fire": [_P(md_space), _P(md_pot), _P(md_fire_params), C.c_int, _vp, _vp, _vp, _P(md_nbr), _vp, C.c_int,
                          _vp, _vp, _vp],
     "md_fire_state_read": [_vp, _P(C.c_double), _vp],
+    "md_integrate_nhc": [_P(md_space), _P(md_pot), _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
+                         C.c_int, _P(md_nbr), _vp, C.c_int, _vp, _vp, _vp, C.c_int, _vp, _vp],
     "md_status_poll": [_vp, _P(C.c_uint32), _vp],
     "md_bounded_wait": [_vp, C.c_uint64, _vp, _vp],
     "md_bp_descriptors": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp],
@@ -153,6 +155,8 @@ _lib.md_noalloc_scratch_bytes.restype = C.c_size_t
 _lib.md_noalloc_scratch_bytes.argtypes = []
 _lib.md_fire_state_bytes.restype = C.c_size_t
 _lib.md_fire_state_bytes.argtypes = []
+_lib.md_nhc_state_doubles.restype = C.c_size_t
+_lib.md_nhc_state_doubles.argtypes = [C.c_int]
 _lib.md_version.restype = C.c_char_p
 _lib.md_version.argtypes = []
 
@@ -261,6 +265,18 @@ def md_integrate_langevin(space, pot, r, v, f, mass, dt, gamma, kT, seed, step0,
 def md_minimize(space, pot, kind, step, nsteps, r, f, nb, E=None, status=None, stream=None):
     _check(_lib.md_minimize(C.byref(space), C.byref(pot), int(kind), float(step), int(nsteps), _ptr(r), _ptr(f),
                             C.byref(nb), _ptr(E), _ptr(status), _stream(stream)), "md_minimize")
+
+
+def md_nhc_state_doubles(M: int) -> int:
+    return int(_lib.md_nhc_state_doubles(int(M)))
+
+
+def md_integrate_nhc(space, pot, r, v, f, mass, dt, kT, tau, M, nsteps, nb, therm, reset=True, PE=None, KE=None,
+                     H=None, use_graph=True, status=None, stream=None):
+    _check(_lib.md_integrate_nhc(C.byref(space), C.byref(pot), _ptr(r), _ptr(v), _ptr(f), float(mass), float(dt),
+                                 float(kT), float(tau), int(M), int(nsteps), C.byref(nb), _ptr(therm),
+                                 int(bool(reset)), _ptr(PE), _ptr(KE), _ptr(H), int(bool(use_graph)), _ptr(status),
+                                 _stream(stream)), "md_integrate_nhc")
 
 
 def md_fire_state_bytes() -> int:
