@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain-SW section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-replica section")
     ap.add_argument("--no-fire", action="store_true", help="skip the FIRE minimisation section")
+    ap.add_argument("--no-nhc", action="store_true", help="skip the Nose-Hoover NVT section")
     return ap.parse_args()
 
 
@@ -330,6 +331,56 @@ def fire_section():
     return out
 
 
+def nhc_section(steps=200):
+    """Nose-Hoover chain NVT (chain length 3, tau = 100 dt): the N = 256,000
+    LJ fluid at T* = 1 and Stillinger-Weber silicon, N = 64,000 atoms at
+    1000 K (dt = 1 fs), each for `steps` steps in one graph launch."""
+    import torch
+    import paper_1912_04232_b300 as P
+    import paper_1912_04232_b300.learned as LP
+    import workloads as W
+    dev = torch.device("cuda")
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = {}
+
+    def run(s, pot, r0, v0, rc, skin, cap, mass, dt, kT, reps=2):
+        nl = P.NeighborList(s, r0.shape[0], rc, skin, cap)
+        r, v, f = torch.empty_like(r0), torch.empty_like(v0), torch.zeros_like(r0)
+        th = torch.zeros(P.md_nhc_state_doubles(3), dtype=torch.float64, device=dev)
+        H = torch.zeros(steps, dtype=torch.float64, device=dev)
+        KE = torch.zeros_like(H)
+        ts = []
+        for k in range(reps + 1):
+            r.copy_(r0)
+            v.copy_(v0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            nl.build(r, st)
+            P.md_energy_forces(s, pot, r, nl.plan, f, None, st)
+            P.md_integrate_nhc(s, pot, r, v, f, mass, dt, kT, 100.0 * dt, 3, steps, nl.plan, th, True, None, KE, H,
+                               True, st)
+            e1.record()
+            e1.synchronize()
+            if k:
+                ts.append(e0.elapsed_time(e1))
+        N = r0.shape[0]
+        Hn = H.cpu().numpy()
+        return {"N": N, "steps": steps, "ms": min(ts), "particle_steps_per_s": N * steps / (min(ts) * 1e-3),
+                "max_abs_dH_per_particle": float(np.abs(Hn - Hn[0]).max() / N),
+                "T_end_over_T": float(KE[-1].item() / (1.5 * N * kT))}
+
+    c = W.lj_large(0)
+    out["lj256k"] = run(P.md_space_periodic(3, [c.L] * 3), P.lj_pot(), torch.from_numpy(c.r).to(dev),
+                        torch.from_numpy(c.v).to(dev), 2.5, 0.3, 128, 1.0, c.dt, 1.0)
+    si = W.sw_silicon(20, T_K=1000.0, seed=0)
+    out["sw_si64k_1000K"] = run(P.md_space_periodic(3, [si.L] * 3), P.sw_pot(LP.SW_SI),
+                                torch.from_numpy(si.r).to(dev), torch.from_numpy(si.v).to(dev), float(LP.SW_RC), 0.5,
+                                64, LP.MASS_SI, 1.0, W.KB_EV * 1000.0)
+    out["status"] = P.md_status_poll(st)
+    return out
+
+
 def _source_sha():
     """Hash of the sources of the pair-force kernels (a stored DRAM-traffic
     figure is only reported while it still describes the built kernel)."""
@@ -508,6 +559,8 @@ def main():
         extra["batched"] = batched_section()
     if rank == 0 and not args.no_fire:
         extra["fire"] = fire_section()
+    if rank == 0 and not args.no_nhc:
+        extra["nvt_nose_hoover"] = nhc_section()
 
     if rank == 0:
         line = {
