@@ -17,6 +17,7 @@
  *     BAOAB Langevin NVT, Nose-Hoover chain NVT                  (Sec. 3.3.1)
  *   - reverse-mode derivative of the final energy of a gradient-descent
  *     minimisation with respect to the small-disk diameter D     (Sec. 4.2, App. A)
+ *   - the flocking energy model of boids and its forward-Euler steps (Sec. 4.3)
  *   - Philox4x32-10 counter-based generator (Salmon et al., SC'11), the
  *     published definition, used for Langevin noise.
  *
@@ -544,6 +545,119 @@ void or_gd(int N, int dim, double *r, const double *diam, const double *L, int p
     double U = energy_forces(pot, N, dim, r, diam, L, pp, f);
     if (Eser) Eser[nsteps] = U;
     free(f);
+}
+
+/* Flocking energy model (Sec. 4.3 and its appendix): boids with positions
+ * R_i in a periodic square and headings theta_i, N(theta) = (cos, sin).
+ * rho(r; Rc) = (1 - r/Rc)^a / a for r < Rc (a = 2), else 0.  With R_ij the
+ * nearest-image displacement R_i - R_j and each unordered pair once:
+ *   E_align  = sum_{i<j} J_al rho(r_ij; R_al) (1 - N_i.N_j)^2
+ *              (no gradient through the displacement: it turns the boids)
+ *   E_avoid  = sum_{i<j} J_av rho(r_ij; R_av)
+ *   E_coh    = sum_i J_co/2 (1 - u_i.N_i)^2,  u_i the unit vector towards
+ *              the mean of R_j - R_i over the boids j within R_co (no term
+ *              without neighbours; no gradient through the displacements)
+ *   E_obst   = sum_i sum_o J_ob rho(|R_o - R_i|; D_o) (1 + N_i.w_io)^2,
+ *              w_io the unit vector from boid i to obstacle o (disk of
+ *              radius D_o), smallest when the boid faces away
+ * Forward Euler: R_i += dt (v N_i - dE/dR_i), theta_i -= dt dE/dtheta_i,
+ * positions wrapped.  prm = {J_al, R_al, J_av, R_av, J_co, R_co, J_ob, a, v}.
+ * obs: n_obs x 3 (x, y, D).  Brute force over all pairs. */
+static double nearest1(double t, double L) { return t - L * nearbyint(t / L); }
+static double rho_cut(double r, double Rc, double a) { return r < Rc ? pow(1.0 - r / Rc, a) / a : 0.0; }
+static double rho_cut_d(double r, double Rc, double a) { return r < Rc ? -pow(1.0 - r / Rc, a - 1.0) / Rc : 0.0; }
+
+double or_flock_grad(int N, const double *R, const double *th, const double *L, const double *prm, int n_obs,
+                     const double *obs, double *gR, double *gth, double *parts)
+{
+    const double Jal = prm[0], Ral = prm[1], Jav = prm[2], Rav = prm[3], Jco = prm[4], Rco = prm[5], Job = prm[6],
+                 a = prm[7];
+    double Eal = 0.0, Eav = 0.0, Eco = 0.0, Eob = 0.0;
+    for (int i = 0; i < 2 * N; ++i) gR[i] = 0.0;
+    for (int i = 0; i < N; ++i) gth[i] = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double cx = 0.0, cy = 0.0;
+        int nco = 0;
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            double d[2];
+            for (int k = 0; k < 2; ++k) d[k] = nearest1(R[2 * i + k] - R[2 * j + k], L[k]);
+            const double r = sqrt(d[0] * d[0] + d[1] * d[1]);
+            const double c = cos(th[i] - th[j]);
+            // alignment: d/dtheta_i of rho (1 - c)^2 = 2 rho (1 - c) sin(theta_i - theta_j)
+            const double ral = rho_cut(r, Ral, a);
+            if (j > i) Eal += Jal * ral * (1.0 - c) * (1.0 - c);
+            gth[i] += 2.0 * Jal * ral * (1.0 - c) * sin(th[i] - th[j]);
+            // avoidance
+            if (j > i) Eav += Jav * rho_cut(r, Rav, a);
+            if (r > 0.0 && r < Rav) {
+                const double g = Jav * rho_cut_d(r, Rav, a) / r;
+                gR[2 * i] += g * d[0];
+                gR[2 * i + 1] += g * d[1];
+            }
+            if (r < Rco) {
+                cx -= d[0];
+                cy -= d[1];
+                nco += 1;
+            }
+        }
+        if (nco > 0) {
+            cx /= nco;
+            cy /= nco;
+            const double m = sqrt(cx * cx + cy * cy);
+            if (m > 0.0) {
+                const double ux = cx / m, uy = cy / m;
+                const double un = ux * cos(th[i]) + uy * sin(th[i]);
+                const double up = -ux * sin(th[i]) + uy * cos(th[i]);   // u . dN/dtheta
+                Eco += 0.5 * Jco * (1.0 - un) * (1.0 - un);
+                gth[i] += -Jco * (1.0 - un) * up;
+            }
+        }
+        for (int o = 0; o < n_obs; ++o) {
+            double d[2];
+            for (int k = 0; k < 2; ++k) d[k] = nearest1(obs[3 * o + k] - R[2 * i + k], L[k]);
+            const double r = sqrt(d[0] * d[0] + d[1] * d[1]);
+            const double D = obs[3 * o + 2];
+            if (!(r > 0.0 && r < D)) continue;
+            const double wx = d[0] / r, wy = d[1] / r;
+            const double nx = cos(th[i]), ny = sin(th[i]);
+            const double q = 1.0 + nx * wx + ny * wy;
+            const double rh = rho_cut(r, D, a), rhd = rho_cut_d(r, D, a);
+            Eob += Job * rh * q * q;
+            gth[i] += 2.0 * Job * rh * q * (-sin(th[i]) * wx + cos(th[i]) * wy);
+            // d/dR_i: r depends on R_i as dr/dR_i = -w; w as dw/dR_i = -(I - w w^T)/r
+            const double nw = nx * wx + ny * wy;
+            gR[2 * i] += Job * (rhd * (-wx) * q * q + rh * 2.0 * q * (-(nx - nw * wx) / r));
+            gR[2 * i + 1] += Job * (rhd * (-wy) * q * q + rh * 2.0 * q * (-(ny - nw * wy) / r));
+        }
+    }
+    if (parts) {
+        parts[0] = Eal;
+        parts[1] = Eav;
+        parts[2] = Eco;
+        parts[3] = Eob;
+    }
+    return Eal + Eav + Eco + Eob;
+}
+
+void or_flock_run(int N, double *R, double *th, const double *L, const double *prm, int n_obs, const double *obs,
+                  double dt, int nsteps, double *Eser)
+{
+    double *gR = (double *)calloc((size_t)2 * N + 1, sizeof(double));
+    double *gth = (double *)calloc((size_t)N + 1, sizeof(double));
+    const double v = prm[8];
+    for (int s = 0; s < nsteps; ++s) {
+        const double E = or_flock_grad(N, R, th, L, prm, n_obs, obs, gR, gth, NULL);
+        if (Eser) Eser[s] = E;
+        for (int i = 0; i < N; ++i) {
+            R[2 * i] = wrap64(R[2 * i] + dt * (v * cos(th[i]) - gR[2 * i]), L[0]);
+            R[2 * i + 1] = wrap64(R[2 * i + 1] + dt * (v * sin(th[i]) - gR[2 * i + 1]), L[1]);
+            th[i] -= dt * gth[i];
+        }
+    }
+    if (Eser) Eser[nsteps] = or_flock_grad(N, R, th, L, prm, n_obs, obs, gR, gth, NULL);
+    free(gth);
+    free(gR);
 }
 
 /* Nose-Hoover chain NVT (Sec. 3.3.1 lists Nose-Hoover constant-temperature
