@@ -325,6 +325,34 @@ JMD_API md_status md_minimize_fire(const md_space *s, const md_pot *p, const md_
 JMD_API md_status md_fire_state_read(const void *d_state, double *out3, md_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Flocking energy model (Sec. 4.3 and its appendix), 2-D periodic square.   */
+/* ------------------------------------------------------------------------ */
+/* Boids: positions R_i, headings theta_i, N_i = (cos, sin) theta_i.  With
+ * rho(r; Rc) = (1 - r/Rc)^alpha / alpha below Rc and each unordered pair once:
+ *   E_align    = sum J_align rho(r_ij; R_align) (1 - N_i.N_j)^2
+ *   E_avoid    = sum J_avoid rho(r_ij; R_avoid)
+ *   E_cohesion = sum_i J_cohesion/2 (1 - u_i.N_i)^2, u_i the unit vector
+ *                towards the mean offset of the boids within R_cohesion
+ *   E_obstacle = sum_i sum_o J_obstacle rho(|R_o - R_i|; D_o) (1 + N_i.w_io)^2,
+ *                w_io the unit vector from boid i to disk obstacle o
+ * Alignment and cohesion turn the boids only (no gradient through the
+ * displacements).  Forward Euler: R_i += dt (speed N_i - dE/dR_i) (wrapped),
+ * theta_i -= dt dE/dtheta_i. */
+typedef struct {
+    float J_align, R_align, J_avoid, R_avoid, J_cohesion, R_cohesion, J_obstacle, alpha, speed;
+} md_flock_params;
+
+/* nsteps of the flocking dynamics.  d_b [N][4]: (x, y, -, -) in, (x, y,
+ * cos theta, sin theta) out; d_theta [N] headings in/out; d_b_alt [N][4]
+ * scratch; d_obs [n_obs][3] (x, y, radius) device.  nb: a 2-D list built
+ * for d_b with r_cut >= max(R_align, R_avoid, R_cohesion); rebuilt as the
+ * boids move.  d_E (nsteps doubles, may be NULL): the energy before each
+ * step. */
+JMD_API md_status md_flock_run(const md_space *s, const md_flock_params *prm, const float *d_obs, int n_obs,
+                               float *d_b, float *d_theta, float *d_b_alt, float dt, int nsteps, md_nbr *nb,
+                               double *d_E, uint32_t *d_status, md_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Learned potential: the pieces of a forward/backward and a training step   */
 /* (Sec. 4.1: energy + force loss).  sys_n as in md_bp_model.                */
 /* ------------------------------------------------------------------------ */

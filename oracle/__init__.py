@@ -253,7 +253,7 @@ def nhc(r, v, L, pot="lj", mass=1.0, dt=0.005, kT=1.0, tau=None, M=3, nsteps=10,
 # Flocking parameters: J_align, R_align, J_avoid, R_avoid, J_cohesion,
 # R_cohesion, J_obstacle, cutoff exponent, speed
 FLOCK_DEFAULTS = dict(J_align=1.0, R_align=45.0, J_avoid=25.0, R_avoid=30.0, J_cohesion=0.05, R_cohesion=40.0,
-                      J_obstacle=100.0, alpha=2.0, speed=1.0)
+                      J_obstacle=10.0, alpha=2.0, speed=1.0)
 _FLOCK_KEYS = ("J_align", "R_align", "J_avoid", "R_avoid", "J_cohesion", "R_cohesion", "J_obstacle", "alpha", "speed")
 
 

@@ -1,0 +1,243 @@
+// flock.cu -- the flocking energy model (Sec. 4.3 and its appendix) on the
+// periodic neighbor list.
+//
+// Boid i: position R_i, heading theta_i, N_i = (cos, sin) theta_i.  With
+// rho(r; Rc) = (1 - r/Rc)^a / a below Rc and each unordered pair once:
+//   E_align = sum J_al rho(r_ij; R_al) (1 - N_i.N_j)^2  (turns boids only)
+//   E_avoid = sum J_av rho(r_ij; R_av)
+//   E_coh   = sum_i J_co/2 (1 - u_i.N_i)^2, u_i towards the mean offset of
+//             the boids within R_co (turns boids only)
+//   E_obst  = sum_i sum_o J_ob rho(|R_o - R_i|; D_o) (1 + N_i.w_io)^2, w_io
+//             the unit vector from the boid to disk obstacle o
+// and forward Euler R_i += dt (v N_i - dE/dR_i), theta_i -= dt dE/dtheta_i.
+//
+// k_flock_step: a group of TPP lanes per boid gathers its row of the list
+// (float4 = x, y, cos theta, sin theta, so no pair needs a sine), reduces
+// the sums with shuffles, adds cohesion and obstacles, and writes the new
+// state to the other buffer (every boid reads its neighbours' old state);
+// the headings are updated in place by their owners.  The displacement
+// check for the list and the FP64 energy of the state before the step are
+// fused in.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace jmd {
+
+struct FlockArgs {
+    Box box;
+    int N, cap, n_obs;
+    md_flock_params p;
+    float dt;
+    const float4 *b;        // x, y, cos theta, sin theta (this step)
+    float4 *b_out;          // the next step
+    float *theta;           // headings, updated in place
+    const float *obs;       // n_obs x 3: x, y, radius
+    const int32_t *nbr, *cnt;
+    const float4 *rref;
+    float half_skin2;
+    uint32_t *ctl;
+    double2 *partials;
+    double *E_out;
+    uint32_t *status;
+};
+
+__device__ __forceinline__ float fl_rho(float r, float Rc, float a)
+{
+    if (!(r < Rc)) return 0.0f;
+    const float x = 1.0f - r / Rc;
+    return a == 2.0f ? 0.5f * x * x : __powf(x, a) / a;
+}
+__device__ __forceinline__ float fl_rho_d(float r, float Rc, float a)
+{
+    if (!(r < Rc)) return 0.0f;
+    const float x = 1.0f - r / Rc;
+    return -(a == 2.0f ? x : __powf(x, a - 1.0f)) / Rc;
+}
+
+template <int TPP>
+__global__ void __launch_bounds__(256) k_flock_step(FlockArgs a)
+{
+    count_launch();
+    __shared__ double sh[8];
+    __shared__ bool last;
+    const int lg = threadIdx.x & (TPP - 1);
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) / TPP;
+    const bool valid = i < a.N;
+    const md_flock_params &p = a.p;
+    float gth = 0.f, gx = 0.f, gy = 0.f, cx = 0.f, cy = 0.f, nco = 0.f, e = 0.f;
+    float4 bi = make_float4(0.f, 0.f, 1.f, 0.f);
+    if (valid) {
+        bi = a.b[i];
+        int n = a.cnt[i];
+        n = n < a.cap ? n : a.cap;
+        const int32_t *row = a.nbr + (size_t)i * a.cap;
+        for (int k = lg; k < n; k += TPP) {
+            const int j = __ldg(row + k);
+            const float4 bj = __ldg(a.b + j);
+            float dx, dy, dz;
+            const float r2 = dist2_rn<2>(bi, bj, a.box, dx, dy, dz);
+            const float r = sqrtf(r2);
+            const float c = bi.z * bj.z + bi.w * bj.w;       // cos(theta_i - theta_j)
+            const float s = bi.w * bj.z - bi.z * bj.w;       // sin(theta_i - theta_j)
+            if (r < p.R_align) {
+                const float rh = fl_rho(r, p.R_align, p.alpha);
+                e += 0.5f * p.J_align * rh * (1.0f - c) * (1.0f - c);
+                gth += 2.0f * p.J_align * rh * (1.0f - c) * s;
+            }
+            if (r < p.R_avoid && r > 0.0f) {
+                e += 0.5f * p.J_avoid * fl_rho(r, p.R_avoid, p.alpha);
+                const float g = p.J_avoid * fl_rho_d(r, p.R_avoid, p.alpha) / r;
+                gx += g * dx;
+                gy += g * dy;
+            }
+            if (r < p.R_cohesion) {
+                cx -= dx;
+                cy -= dy;
+                nco += 1.0f;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = TPP / 2; o > 0; o >>= 1) {
+        gth += __shfl_xor_sync(0xffffffffu, gth, o);
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        cx += __shfl_xor_sync(0xffffffffu, cx, o);
+        cy += __shfl_xor_sync(0xffffffffu, cy, o);
+        nco += __shfl_xor_sync(0xffffffffu, nco, o);
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+    }
+    bool mv = false;
+    if (valid && lg == 0) {
+        const float ci = bi.z, si = bi.w;
+        if (nco > 0.0f) {
+            const float mx = cx / nco, my = cy / nco;
+            const float m = sqrtf(mx * mx + my * my);
+            if (m > 0.0f) {
+                const float ux = mx / m, uy = my / m;
+                const float un = ux * ci + uy * si, up = -ux * si + uy * ci;
+                e += 0.5f * p.J_cohesion * (1.0f - un) * (1.0f - un);
+                gth += -p.J_cohesion * (1.0f - un) * up;
+            }
+        }
+        for (int o = 0; o < a.n_obs; ++o) {
+            const float ox = __ldg(a.obs + 3 * o), oy = __ldg(a.obs + 3 * o + 1), D = __ldg(a.obs + 3 * o + 2);
+            const float dx = min_image_rn(ox, bi.x, a.box.L[0], a.box.Linv[0]);
+            const float dy = min_image_rn(oy, bi.y, a.box.L[1], a.box.Linv[1]);
+            const float r = sqrtf(dx * dx + dy * dy);
+            if (!(r > 0.0f && r < D)) continue;
+            const float wx = dx / r, wy = dy / r;
+            const float nw = ci * wx + si * wy, q = 1.0f + nw;
+            const float rh = fl_rho(r, D, p.alpha), rhd = fl_rho_d(r, D, p.alpha);
+            e += p.J_obstacle * rh * q * q;
+            gth += 2.0f * p.J_obstacle * rh * q * (-si * wx + ci * wy);
+            gx += p.J_obstacle * (rhd * (-wx) * q * q + rh * 2.0f * q * (-(ci - nw * wx) / r));
+            gy += p.J_obstacle * (rhd * (-wy) * q * q + rh * 2.0f * q * (-(si - nw * wy) / r));
+        }
+        float th = a.theta[i];
+        const float x = wrap_coord(bi.x + a.dt * (p.speed * ci - gx), a.box.L[0], a.box.Linv[0]);
+        const float y = wrap_coord(bi.y + a.dt * (p.speed * si - gy), a.box.L[1], a.box.Linv[1]);
+        th -= a.dt * gth;
+        float sn, cs;
+        sincosf(th, &sn, &cs);
+        a.theta[i] = th;
+        const float4 bo = make_float4(x, y, cs, sn);
+        a.b_out[i] = bo;
+        float ddx, ddy, ddz;
+        mv = dist2_rn<2>(bo, a.rref[i], a.box, ddx, ddy, ddz) > a.half_skin2;
+    } else {
+        e = 0.0f;
+    }
+    if (__any_sync(0xffffffffu, mv) && (threadIdx.x & 31) == 0) a.ctl[CTL_REBUILD] = 1u;
+    if (!a.E_out) return;
+    // FP64 energy of the state before the step: warp (FP32), block and grid
+    // (FP64, fixed order by the last block)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+        a.partials[blockIdx.x] = make_double2(s, 0.0);
+        __threadfence();
+        last = atomicAdd(&a.ctl[CTL_TICKET], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double E = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) E += ((volatile double *)(a.partials + b))[0];
+    a.ctl[CTL_TICKET] = 0u;
+    if (!isfinite(E)) raise_status(a.status, MD_ERR_NONFINITE);
+    const unsigned step = a.ctl[CTL_STEP];
+    a.E_out[step] = E;
+    a.ctl[CTL_STEP] = step + 1u;
+}
+
+// (x, y) from the caller's positions, (cos, sin) of the headings.
+__global__ void __launch_bounds__(256) k_flock_init(float4 *b, const float *theta, int N)
+{
+    count_launch();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float sn, cs;
+    sincosf(theta[i], &sn, &cs);
+    float4 bi = b[i];
+    bi.z = cs;
+    bi.w = sn;
+    b[i] = bi;
+}
+
+}  // namespace jmd
+
+using namespace jmd;
+
+extern "C" md_status md_flock_run(const md_space *s, const md_flock_params *prm, const float *d_obs, int n_obs,
+                                  float *d_b, float *d_theta, float *d_b_alt, float dt, int nsteps, md_nbr *nb,
+                                  double *d_E, uint32_t *d_status, md_stream_t stream)
+{
+    if (!s || !prm || !d_b || !d_theta || !d_b_alt || !nb || nsteps < 0 || n_obs < 0) return MD_ERR_INVALID;
+    if (n_obs > 0 && !d_obs) return MD_ERR_INVALID;
+    if (s->dim != 2 || nb->dim != 2 || !nb->nbr || !nb->cnt || !nb->ws || !nb->rref || !nbr_layout_ok(nb))
+        return MD_ERR_INVALID;
+    const float rmax = fmaxf(prm->R_align, fmaxf(prm->R_avoid, prm->R_cohesion));
+    if (!(rmax > 0.0f) || rmax > nb->r_cut || !(prm->alpha >= 1.0f) || !(dt > 0.0f)) return MD_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    const WsPtrs w = ws_ptrs(nb);
+    const int N = nb->N;
+    FlockArgs a;
+    memset(&a, 0, sizeof(a));
+    a.box = make_box(s);
+    a.N = N;
+    a.cap = nb->cap;
+    a.n_obs = n_obs;
+    a.p = *prm;
+    a.dt = dt;
+    a.theta = d_theta;
+    a.obs = d_obs;
+    a.nbr = nb->nbr;
+    a.cnt = nb->cnt;
+    a.rref = (const float4 *)nb->rref;
+    a.half_skin2 = nb->half_skin2;
+    a.ctl = w.ctl;
+    a.partials = w.partials;
+    a.E_out = d_E;
+    a.status = d_status;
+    constexpr int TPP = 4;
+    const int grid = (int)(((long long)N * TPP + 255) / 256);
+    if (d_E && grid > w.max_blocks) return MD_ERR_INVALID;
+    enqueue_loop_init(w.ctl, (uint32_t)nsteps, st);
+    k_flock_init<<<(N + 255) / 256, 256, 0, st>>>((float4 *)d_b, d_theta, N);
+    NbrArgs na[2] = {make_nbr_args(s, d_b_alt, nb, d_status, 1), make_nbr_args(s, d_b, nb, d_status, 1)};
+    float4 *buf[2] = {(float4 *)d_b, (float4 *)d_b_alt};
+    for (int t = 0; t < nsteps; ++t) {
+        a.b = buf[t & 1];
+        a.b_out = buf[(t + 1) & 1];
+        k_flock_step<TPP><<<grid, 256, 0, st>>>(a);
+        enqueue_rebuild_chain(na[t & 1], nb->ncell_total, st);
+    }
+    if (nsteps & 1) JMD_CUDA_TRY(cudaMemcpyAsync(d_b, d_b_alt, sizeof(float4) * (size_t)N, cudaMemcpyDeviceToDevice, st));
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}

@@ -79,6 +79,16 @@ def fire_params(dt_start=0.1, dt_max=0.4, f_inc=1.1, f_dec=0.5, alpha_start=0.1,
     return md_fire_params(dt_start, dt_max, f_inc, f_dec, alpha_start, f_alpha, n_min)
 
 
+class md_flock_params(C.Structure):
+    _fields_ = [(n, C.c_float) for n in ("J_align", "R_align", "J_avoid", "R_avoid", "J_cohesion", "R_cohesion",
+                                         "J_obstacle", "alpha", "speed")]
+
+
+def flock_params(J_align=1.0, R_align=45.0, J_avoid=25.0, R_avoid=30.0, J_cohesion=0.05, R_cohesion=40.0,
+                 J_obstacle=10.0, alpha=2.0, speed=1.0):
+    return md_flock_params(J_align, R_align, J_avoid, R_avoid, J_cohesion, R_cohesion, J_obstacle, alpha, speed)
+
+
 class md_replica_desc(C.Structure):
     _fields_ = [("N", C.c_int), ("L", C.c_double), ("kind", C.c_int), ("eps", C.c_float), ("sigma", C.c_float),
                 ("r_cut", C.c_float), ("e_shift", C.c_float), ("alpha", C.c_float), ("skin", C.c_float),
@@ -113,6 +123,8 @@ _SIGS = {
     "md_minimize_fire": [_P(md_space), _P(md_pot), _P(md_fire_params), C.c_int, _vp, _vp, _vp, _P(md_nbr), _vp, C.c_int,
                          _vp, _vp, _vp],
     "md_fire_state_read": [_vp, _P(C.c_double), _vp],
+    "md_flock_run": [_P(md_space), _P(md_flock_params), _vp, C.c_int, _vp, _vp, _vp, C.c_float, C.c_int, _P(md_nbr),
+                     _vp, _vp, _vp],
     "md_integrate_nhc": [_P(md_space), _P(md_pot), _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
                          C.c_int, _P(md_nbr), _vp, C.c_int, _vp, _vp, _vp, C.c_int, _vp, _vp],
     "md_status_poll": [_vp, _P(C.c_uint32), _vp],
@@ -277,6 +289,12 @@ def md_integrate_nhc(space, pot, r, v, f, mass, dt, kT, tau, M, nsteps, nb, ther
                                  float(kT), float(tau), int(M), int(nsteps), C.byref(nb), _ptr(therm),
                                  int(bool(reset)), _ptr(PE), _ptr(KE), _ptr(H), int(bool(use_graph)), _ptr(status),
                                  _stream(stream)), "md_integrate_nhc")
+
+
+def md_flock_run(space, params, obs, n_obs, b, theta, b_alt, dt, nsteps, nb, E=None, status=None, stream=None):
+    _check(_lib.md_flock_run(C.byref(space), C.byref(params), _ptr(obs), int(n_obs), _ptr(b), _ptr(theta), _ptr(b_alt),
+                             float(dt), int(nsteps), C.byref(nb), _ptr(E), _ptr(status), _stream(stream)),
+           "md_flock_run")
 
 
 def md_fire_state_bytes() -> int:

@@ -25,7 +25,7 @@ import numpy as np
 __all__ = [
     "f32", "box_for_density", "sc_lattice", "fcc_lattice", "diamond_lattice",
     "jitter_wrap", "thermal_velocities", "LJFluid", "lj_fluid",
-    "Packing2D", "packing_2d", "packing_box", "SWSilicon", "sw_silicon",
+    "Packing2D", "packing_2d", "packing_box", "SWSilicon", "sw_silicon", "Flock", "flock",
     "ReplicaSpec", "replica_plan", "replica_initial", "uniform_box_positions",
 ]
 
@@ -258,6 +258,33 @@ def replica_initial(spec: ReplicaSpec, T: float = 1.0):
         r[:, 3] = d
     v = _to4(thermal_velocities(spec.N, 3, T, 1.0, rng))
     return r, v
+
+
+# --------------------------------------------------------------------------
+# Flocking (Sec. 4.3): boids in a periodic square
+# --------------------------------------------------------------------------
+@dataclass
+class Flock:
+    N: int
+    L: float
+    R: np.ndarray           # [N, 2] float32 positions
+    theta: np.ndarray       # [N] float32 headings
+    obstacles: np.ndarray   # [n_obs, 3] float32 (x, y, radius)
+
+
+def flock(N: int = 2000, neighbours: float = 20.0, R_align: float = 45.0, n_obs: int = 4,
+          obstacle_radius: float = 60.0, seed: int = 0) -> Flock:
+    """Uniform positions and headings; the box edge gives about `neighbours`
+    boids within R_align of each boid; disk obstacles at uniform centres."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = f32(math.sqrt(N * math.pi * R_align * R_align / neighbours))
+    R = rng.uniform(0.0, L, size=(N, 2)).astype(np.float32)
+    R[R >= L] = 0.0
+    theta = rng.uniform(-math.pi, math.pi, size=N).astype(np.float32)
+    obs = np.zeros((n_obs, 3), np.float32)
+    obs[:, :2] = rng.uniform(0.0, L, size=(n_obs, 2))
+    obs[:, 2] = obstacle_radius
+    return Flock(N=N, L=L, R=R, theta=theta, obstacles=obs)
 
 
 def uniform_box_positions(N: int, L: float, dim: int, rng: np.random.Generator) -> np.ndarray:
