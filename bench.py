@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-replica section")
     ap.add_argument("--no-fire", action="store_true", help="skip the FIRE minimisation section")
     ap.add_argument("--no-nhc", action="store_true", help="skip the Nose-Hoover NVT section")
+    ap.add_argument("--no-flock", action="store_true", help="skip the flocking section")
     return ap.parse_args()
 
 
@@ -381,6 +382,46 @@ def nhc_section(steps=200):
     return out
 
 
+def flock_section(N=100000, steps=200):
+    """Flocking energy model: N boids with ~20 neighbours within the
+    alignment range and 16 disk obstacles, `steps` forward-Euler steps
+    (dt = 0.1) with list rebuilds."""
+    import torch
+    import paper_1912_04232_b300 as P
+    import workloads as W
+    dev = torch.device("cuda")
+    fl = W.flock(N, n_obs=16, seed=0)
+    prm = P.flock_params()
+    s = P.md_space_periodic(2, [fl.L, fl.L])
+    nl = P.NeighborList(s, N, max(prm.R_align, prm.R_avoid, prm.R_cohesion), 4.0, 128)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    b0 = torch.zeros((N, 4), dtype=torch.float32, device=dev)
+    b0[:, :2] = torch.from_numpy(fl.R).to(dev)
+    th0 = torch.from_numpy(fl.theta).to(dev)
+    obs = torch.from_numpy(fl.obstacles).to(dev)
+    b, th, alt = torch.empty_like(b0), torch.empty_like(th0), torch.empty_like(b0)
+    E = torch.zeros(steps, dtype=torch.float64, device=dev)
+    ts = []
+    b1 = nl.stats()[0]
+    for k in range(3):
+        b.copy_(b0)
+        th.copy_(th0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        nl.build(b, st)
+        P.md_flock_run(s, prm, obs, obs.shape[0], b, th, alt, 0.1, steps, nl.plan, E, st)
+        e1.record()
+        e1.synchronize()
+        if k:
+            ts.append(e0.elapsed_time(e1))
+    ms = min(ts)
+    En = E.cpu().numpy()
+    return {"N": N, "steps": steps, "ms": ms, "boid_steps_per_s": N * steps / (ms * 1e-3),
+            "builds_per_run": (nl.stats()[0] - b1) / 3.0, "E_start": float(En[0]), "E_end": float(En[-1]),
+            "status": P.md_status_poll(st)}
+
+
 def _source_sha():
     """Hash of the sources of the pair-force kernels (a stored DRAM-traffic
     figure is only reported while it still describes the built kernel)."""
@@ -561,6 +602,8 @@ def main():
         extra["fire"] = fire_section()
     if rank == 0 and not args.no_nhc:
         extra["nvt_nose_hoover"] = nhc_section()
+    if rank == 0 and not args.no_flock:
+        extra["flocking"] = flock_section()
 
     if rank == 0:
         line = {

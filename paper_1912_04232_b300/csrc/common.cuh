@@ -24,6 +24,8 @@ enum CtlWord : int {
     CTL_SEED_LO = 8,     // Langevin noise key (64 bits)
     CTL_SEED_HI = 9,
     CTL_STEP0 = 10,      // noise counter of the loop's first step
+    CTL_ITER = 11,       // iteration counter of a graph loop (graphloop.cu)
+    CTL_NITER = 12,      // its length
     CTL_WORDS = 64
 };
 

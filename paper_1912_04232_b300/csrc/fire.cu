@@ -196,21 +196,63 @@ extern "C" md_status md_minimize_fire(const md_space *s, const md_pot *p, const 
         k_fire_init<<<1, 1, 0, st>>>(h, *fp);
     }
     enqueue_pair(pa, s->dim, p->kind, 0, st);
-    for (int t = 0; t < nsteps; ++t) {
-        if (s->dim == 3) {
-            k_fire_drift<3><<<g, 256, 0, st>>>(r, v, f, (const float4 *)nb->rref, N, h, box, nb->half_skin2, w.ctl);
+    const int dim = s->dim, kind = p->kind;
+    const float4 *rref = (const float4 *)nb->rref;
+    const float hs2 = nb->half_skin2;
+    const int ncell = nb->ncell_total;
+    const md_fire_params prm = *fp;
+    // one step: drift, rebuild (gated, or under an IF node), forces, power, mixing
+    auto step = [&](cudaStream_t cs, LoopBuilder *lb) -> md_status {
+        if (dim == 3) k_fire_drift<3><<<g, 256, 0, cs>>>(r, v, f, rref, N, h, box, hs2, w.ctl);
+        else k_fire_drift<2><<<g, 256, 0, cs>>>(r, v, f, rref, N, h, box, hs2, w.ctl);
+        if (lb) {
+            md_status e = lb->rebuild_if(na, ncell);
+            if (e != MD_OK) return e;
         } else {
-            k_fire_drift<2><<<g, 256, 0, st>>>(r, v, f, (const float4 *)nb->rref, N, h, box, nb->half_skin2, w.ctl);
+            enqueue_rebuild_chain(na, ncell, cs);
         }
-        enqueue_rebuild_chain(na, nb->ncell_total, st);
-        enqueue_pair(pa, s->dim, p->kind, 0, st);
-        if (s->dim == 3) {
-            k_fire_power<3><<<gp, 256, 0, st>>>(v, f, N, h, *fp, d_status);
-            k_fire_mix<3><<<g, 256, 0, st>>>(v, f, N, h);
+        enqueue_pair(pa, dim, kind, 0, cs);
+        if (dim == 3) {
+            k_fire_power<3><<<gp, 256, 0, cs>>>(v, f, N, h, prm, d_status);
+            k_fire_mix<3><<<g, 256, 0, cs>>>(v, f, N, h);
         } else {
-            k_fire_power<2><<<gp, 256, 0, st>>>(v, f, N, h, *fp, d_status);
-            k_fire_mix<2><<<g, 256, 0, st>>>(v, f, N, h);
+            k_fire_power<2><<<gp, 256, 0, cs>>>(v, f, N, h, prm, d_status);
+            k_fire_mix<2><<<g, 256, 0, cs>>>(v, f, N, h);
         }
+        return MD_OK;
+    };
+    if (g_loop_graphs) {
+        struct Key {
+            int tag, dim, kind, N;
+            PairArgs pa;
+            NbrArgs na;
+            const void *r, *v, *f, *h, *rref;
+            md_fire_params prm;
+            Box box;
+            float hs2;
+            uint32_t *status;
+        } key;
+        memset(&key, 0, sizeof(key));
+        key.tag = 0x46495245;   // FIRE
+        key.dim = dim;
+        key.kind = kind;
+        key.N = N;
+        key.pa = pa;
+        key.na = na;
+        key.r = r;
+        key.v = v;
+        key.f = f;
+        key.h = h;
+        key.rref = rref;
+        key.prm = prm;
+        key.box = box;
+        key.hs2 = hs2;
+        key.status = d_status;
+        md_status e = run_graph_loop(&key, sizeof(key), w.ctl, nsteps,
+                                     [&](LoopBuilder &lb) { return step(lb.cs, &lb); }, st);
+        if (e != MD_OK) return e;
+    } else {
+        for (int t = 0; t < nsteps; ++t) step(st, nullptr);
     }
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;

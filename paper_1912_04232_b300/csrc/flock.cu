@@ -231,12 +231,43 @@ extern "C" md_status md_flock_run(const md_space *s, const md_flock_params *prm,
     k_flock_init<<<(N + 255) / 256, 256, 0, st>>>((float4 *)d_b, d_theta, N);
     NbrArgs na[2] = {make_nbr_args(s, d_b_alt, nb, d_status, 1), make_nbr_args(s, d_b, nb, d_status, 1)};
     float4 *buf[2] = {(float4 *)d_b, (float4 *)d_b_alt};
-    for (int t = 0; t < nsteps; ++t) {
-        a.b = buf[t & 1];
-        a.b_out = buf[(t + 1) & 1];
-        k_flock_step<TPP><<<grid, 256, 0, st>>>(a);
-        enqueue_rebuild_chain(na[t & 1], nb->ncell_total, st);
+    const int ncell = nb->ncell_total;
+    // step t: the state in buf[t & 1] moves to the other buffer; the list is
+    // rebuilt (if needed) on the new positions
+    auto step = [&](int t, cudaStream_t cs, LoopBuilder *lb) -> md_status {
+        FlockArgs at = a;
+        at.b = buf[t & 1];
+        at.b_out = buf[(t + 1) & 1];
+        k_flock_step<TPP><<<grid, 256, 0, cs>>>(at);
+        if (lb) return lb->rebuild_if(na[t & 1], ncell);
+        enqueue_rebuild_chain(na[t & 1], ncell, cs);
+        return MD_OK;
+    };
+    int done = 0;
+    if (g_loop_graphs && nsteps >= 2) {
+        // graph loop of two steps per iteration (the buffers trade places)
+        struct Key {
+            int tag;
+            FlockArgs a;
+            NbrArgs na0, na1;
+            int ncell;
+        } key;
+        memset(&key, 0, sizeof(key));
+        key.tag = 0x464c4f43;   // FLOC
+        key.a = a;
+        key.na0 = na[0];
+        key.na1 = na[1];
+        key.ncell = ncell;
+        md_status e = run_graph_loop(&key, sizeof(key), w.ctl, nsteps / 2,
+                                     [&](LoopBuilder &lb) {
+                                         md_status e0 = step(0, lb.cs, &lb);
+                                         return e0 != MD_OK ? e0 : step(1, lb.cs, &lb);
+                                     },
+                                     st);
+        if (e != MD_OK) return e;
+        done = nsteps / 2 * 2;
     }
+    for (int t = done; t < nsteps; ++t) step(t, st, nullptr);
     if (nsteps & 1) JMD_CUDA_TRY(cudaMemcpyAsync(d_b, d_b_alt, sizeof(float4) * (size_t)N, cudaMemcpyDeviceToDevice, st));
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;

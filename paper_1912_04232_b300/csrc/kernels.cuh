@@ -2,6 +2,8 @@
 // libjmd translation units (host side).
 #pragma once
 
+#include <functional>
+
 #include "common.cuh"
 
 namespace jmd {
@@ -71,6 +73,20 @@ struct PairArgs {
 };
 
 NbrArgs make_nbr_args(const md_space *s, const float *d_r, const md_nbr *nb, uint32_t *d_status, int gated);
+
+// Graph loops (graphloop.cu): WHILE(iteration < niter) { body } as one CUDA
+// graph; inside the body, rebuild_if() adds the rebuild chain under an IF
+// node taken from the device rebuild flag.
+struct LoopBuilder {
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cs = nullptr, cs2 = nullptr;   // capture streams of the body and of IF bodies
+    uint32_t *ctl = nullptr;
+    md_status rebuild_if(const NbrArgs &na, int ncell_total);
+};
+md_status run_graph_loop(const void *key, size_t key_bytes, uint32_t *ctl, int niter,
+                         const std::function<md_status(LoopBuilder &)> &body, cudaStream_t st);
+// 1 (default): FIRE and flocking loops run as graph loops; 0: host launches.
+extern int g_loop_graphs;
 void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st);
 // Device loop counters: step 0 of nsteps (energy series index).
 void enqueue_loop_init(uint32_t *ctl, uint32_t nsteps, cudaStream_t st);

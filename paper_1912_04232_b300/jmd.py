@@ -115,6 +115,7 @@ _SIGS = {
     "md_set_pair_tpp": [C.c_int],
     "md_set_pair_options": [C.c_int],
     "md_set_nve_fusion": [C.c_int],
+    "md_set_loop_graphs": [C.c_int],
     "md_integrate_nve": [_P(md_space), _P(md_pot), _vp, _vp, _vp, C.c_float, C.c_float, C.c_int, _P(md_nbr),
                          _vp, _vp, C.c_int, _vp, _vp],
     "md_integrate_langevin": [_P(md_space), _P(md_pot), _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float,
@@ -249,6 +250,10 @@ def md_energy_forces(space, pot, r, nb, f, E=None, status=None, stream=None):
 
 def md_set_pair_options(opt: int):
     _check(_lib.md_set_pair_options(int(opt)), "md_set_pair_options")
+
+
+def md_set_loop_graphs(on: bool):
+    _check(_lib.md_set_loop_graphs(int(bool(on))), "md_set_loop_graphs")
 
 
 def md_set_nve_fusion(on: bool):

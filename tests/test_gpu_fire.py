@@ -137,3 +137,16 @@ def test_fire_rejects_bad_parameters(P):
     state = torch.zeros(P.md_fire_state_bytes(), dtype=torch.uint8, device=dev())
     with pytest.raises(P.MDError):
         P.md_minimize_fire(s, P.soft_pot(), P.fire_params(f_dec=1.5), 1, z, z.clone(), z.clone(), nl.plan, state)
+
+
+def test_fire_graph_loop_equals_host_launches_bitwise(P):
+    r, L, diam = _packing(1024, 1.2, 0.9)
+    P.md_set_loop_graphs(False)
+    try:
+        a = _fire_gpu(P, r, L, 50)
+    finally:
+        P.md_set_loop_graphs(True)
+    b = _fire_gpu(P, r, L, 50)
+    for x, y in zip(a[:4], b[:4]):
+        np.testing.assert_array_equal(x, y)
+    assert a[4] == b[4]

@@ -86,3 +86,17 @@ def test_lone_boid_crosses_the_boundary(P):
     want = np.mod(np.array([395.0, 10.0]) + 0.5 * 40 * np.array([np.cos(0.3), np.sin(0.3)]), 400.0)
     np.testing.assert_allclose(b[0, :2], want, rtol=0, atol=1e-3)
     assert th[0] == np.float32(0.3) and np.all(E == 0.0)
+
+
+def test_flock_graph_loop_equals_host_launches_bitwise(P):
+    # 41 steps: 20 graph iterations of two steps and one host-launched step
+    fl = W.flock(1500, seed=4)
+    P.md_set_loop_graphs(False)
+    try:
+        a = _run(P, fl, 0.1, 41)
+    finally:
+        P.md_set_loop_graphs(True)
+    b = _run(P, fl, 0.1, 41)
+    for x, y in zip(a[:3], b[:3]):
+        np.testing.assert_array_equal(x, y)
+    assert a[3].stats()[0] == b[3].stats()[0]
