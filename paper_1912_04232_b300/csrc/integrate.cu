@@ -144,6 +144,25 @@ __global__ void __launch_bounds__(1024) k_nhc_begin(const float4 *v, int N, floa
     }
 }
 
+// After each force kernel (one thread): the closing thermostat half-step of
+// the step from the kinetic energy the force kernel left, the extended
+// energy, and, if another step follows, the next step's opening half-step.
+// The next kick-drift applies both velocity factors (the closing one alone
+// at the end of the loop); the series get the thermostatted state.  The
+// force kernel has already advanced the step counter.
+__global__ void k_nhc_update(double *nhc, int M, const uint32_t *ctl, double *KE_out, double *H_out)
+{
+    count_launch();
+    double *c = nhc + 3 * M;
+    const unsigned step = ctl[CTL_STEP] - 1u;
+    double K = c[NHC_KRAW];
+    c[NHC_SCLOSE] = nhc_half_step(nhc, M, K);
+    c[NHC_K] = K;
+    if (KE_out) KE_out[step] = K;
+    if (H_out) H_out[step] = c[NHC_PE] + K + nhc_energy(nhc, M);
+    c[NHC_SOPEN] = (step + 1u < ctl[CTL_NSTEPS]) ? nhc_half_step(nhc, M, K) : 1.0;
+}
+
 // After the loop: the last step's closing velocity factor.
 __global__ void __launch_bounds__(256) k_nhc_end(float4 *v, int N, const double *nhc, int M)
 {
@@ -324,11 +343,17 @@ static void enqueue_kick_drift(const NveCtx &c, int cond, cudaStream_t st)
     }
 }
 
+static void enqueue_nhc_update(const NveCtx &c, cudaStream_t st)
+{
+    k_nhc_update<<<1, 1, 0, st>>>(c.pa.nhc, c.pa.nhc_M, c.ctl, c.pa.KE_out, c.pa.H_out);
+}
+
 static void enqueue_nve_step(const NveCtx &c, cudaStream_t st)
 {
     if (!c.fused) enqueue_kick_drift(c, 0, st);
     enqueue_rebuild_chain(c.na, c.ncell_total, st);
     enqueue_forces(c.pa, c.dim, c.pot, c.fused ? 2 : 1, st);
+    if (c.nhc) enqueue_nhc_update(c, st);
 }
 
 static void enqueue_final_positions(const NveCtx &c, cudaStream_t st)
@@ -443,6 +468,7 @@ static md_status build_nve_graph(const NveCtx &c0, NveGraph &out)
     JMD_CUDA_TRY(cudaStreamEndCapture(cs2, &ibody));
 
     enqueue_forces(c.pa, c.dim, c.pot, c.fused ? 2 : 1, cs);
+    if (c.nhc) enqueue_nhc_update(c, cs);
     JMD_CUDA_TRY(cudaStreamEndCapture(cs, &body));
     cudaStreamDestroy(cs2);
     cudaStreamDestroy(cs);

@@ -13,6 +13,8 @@
 //   3M + 3      closing factor of the last half-step pair, still to apply
 //   3M + 4      opening factor of the next step, still to apply
 //   3M + 5      kinetic energy after the last closing half-step
+//   3M + 6      kinetic energy of the last force kernel (before the half-step)
+//   3M + 7      its potential energy
 // The factors are applied as (v * closing) * opening, so a run continued
 // across calls repeats the arithmetic of an uninterrupted one.
 // Half-step: the sweep of Martyna, Tuckerman, Tobias, Klein (1996) with one
@@ -22,8 +24,8 @@
 namespace jmd {
 
 constexpr int NHC_MAXM = 8;
-__host__ __device__ constexpr int nhc_words(int M) { return 3 * M + 6; }
-enum { NHC_GKT = 0, NHC_KT = 1, NHC_DT = 2, NHC_SCLOSE = 3, NHC_SOPEN = 4, NHC_K = 5 };
+__host__ __device__ constexpr int nhc_words(int M) { return 3 * M + 8; }
+enum { NHC_GKT = 0, NHC_KT = 1, NHC_DT = 2, NHC_SCLOSE = 3, NHC_SOPEN = 4, NHC_K = 5, NHC_KRAW = 6, NHC_PE = 7 };
 
 __device__ __forceinline__ double nhc_force(const double *Q, const double *w, int k, double K, double gkT, double kT)
 {

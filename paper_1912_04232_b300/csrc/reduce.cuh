@@ -55,18 +55,11 @@ __device__ __forceinline__ void energy_epilogue(float pe_acc, float ke_acc, cons
         a.ctl[CTL_TICKET] = 0u;
         if (!isfinite(spe) || !isfinite(ske)) raise_status(a.status, MD_ERR_NONFINITE);
         unsigned step = a.series ? a.ctl[CTL_STEP] : 0u;
+        // Nose-Hoover chain: the totals go to the thermostat state, whose
+        // half-steps k_nhc_update takes after this kernel
         if (a.nhc) {
-            // closing thermostat half-step of this step; then, if another
-            // step follows, its opening half-step.  The next kick-drift
-            // applies both velocity factors (the closing one alone at the end
-            // of the loop); the series get the thermostatted state.
-            double *c = a.nhc + 3 * a.nhc_M;
-            double K = ske;
-            c[NHC_SCLOSE] = nhc_half_step(a.nhc, a.nhc_M, K);
-            ske = K;
-            c[NHC_K] = K;
-            if (a.H_out) a.H_out[step] = spe + ske + nhc_energy(a.nhc, a.nhc_M);
-            c[NHC_SOPEN] = (step + 1u < a.ctl[CTL_NSTEPS]) ? nhc_half_step(a.nhc, a.nhc_M, K) : 1.0;
+            a.nhc[3 * a.nhc_M + NHC_KRAW] = ske;
+            a.nhc[3 * a.nhc_M + NHC_PE] = spe;
         }
         if (a.E_out) a.E_out[step] = spe;
         if (a.KE_out) a.KE_out[step] = ske;
