@@ -51,9 +51,11 @@ def lib():
         L.or_gd.restype = None
         L.or_gd.argtypes = [C.c_int, C.c_int, _dp, C.c_void_p, _dp, C.c_int, _dp, C.c_double, C.c_int, _dp]
         L.or_flock_grad.restype = C.c_double
-        L.or_flock_grad.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.c_int, C.c_void_p, _dp, _dp, _dp]
+        L.or_flock_grad.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.c_int, C.c_void_p, C.c_int, C.c_void_p, _dp, _dp,
+                                    C.c_void_p, _dp]
         L.or_flock_run.restype = None
-        L.or_flock_run.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.c_int, C.c_void_p, C.c_double, C.c_int, _dp]
+        L.or_flock_run.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_double,
+                                   C.c_int, _dp]
         L.or_nhc.restype = None
         L.or_nhc.argtypes = [C.c_int, C.c_int, _dp, _dp, C.c_void_p, _dp, C.c_int, _dp, C.c_double, C.c_double,
                              C.c_double, C.c_double, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
@@ -251,10 +253,13 @@ def nhc(r, v, L, pot="lj", mass=1.0, dt=0.005, kT=1.0, tau=None, M=3, nsteps=10,
 
 
 # Flocking parameters: J_align, R_align, J_avoid, R_avoid, J_cohesion,
-# R_cohesion, J_obstacle, cutoff exponent, speed
+# R_cohesion, J_obstacle, cutoff exponent, speed; predators: J_flee, R_flee
+# (boids fleeing), J_chase, R_chase (predators chasing), predator speed
 FLOCK_DEFAULTS = dict(J_align=1.0, R_align=45.0, J_avoid=25.0, R_avoid=30.0, J_cohesion=0.05, R_cohesion=40.0,
-                      J_obstacle=10.0, alpha=2.0, speed=1.0)
-_FLOCK_KEYS = ("J_align", "R_align", "J_avoid", "R_avoid", "J_cohesion", "R_cohesion", "J_obstacle", "alpha", "speed")
+                      J_obstacle=10.0, alpha=2.0, speed=1.0, J_flee=10.0, R_flee=60.0, J_chase=0.2,
+                      R_chase=150.0, predator_speed=0.85)
+_FLOCK_KEYS = ("J_align", "R_align", "J_avoid", "R_avoid", "J_cohesion", "R_cohesion", "J_obstacle", "alpha", "speed",
+               "J_flee", "R_flee", "J_chase", "R_chase", "predator_speed")
 
 
 def _flock_prm(params):
@@ -262,34 +267,40 @@ def _flock_prm(params):
     return np.array([fp[k] for k in _FLOCK_KEYS], np.float64)
 
 
-def _obs(obstacles):
-    if obstacles is None or len(obstacles) == 0:
+def _rows3(x):
+    if x is None or len(x) == 0:
         return 0, None, None
-    o = np.ascontiguousarray(obstacles, np.float64).reshape(-1, 3)
+    o = np.ascontiguousarray(x, np.float64).reshape(-1, 3).copy()
     return o.shape[0], o, o.ctypes.data
 
 
-def flock_grad(R, theta, L, params=None, obstacles=None):
-    """(E, dE/dR [N,2], dE/dtheta [N], (E_align, E_avoid, E_cohesion, E_obstacle))."""
+def flock_grad(R, theta, L, params=None, obstacles=None, predators=None):
+    """(E, dE/dR [N,2], dE/dtheta [N], dE/d(predator x, y, theta) [P,3],
+    (E_align, E_avoid, E_cohesion, E_obstacle, E_flee, E_chase))."""
     R = np.ascontiguousarray(np.asarray(R, np.float64)[:, :2])
     th = np.ascontiguousarray(theta, np.float64)
     N = R.shape[0]
     gR = np.zeros((N, 2))
     gth = np.zeros(N)
-    parts = np.zeros(4)
-    n_obs, o, optr = _obs(obstacles)
-    E = lib().or_flock_grad(N, R, th, _box(L, 2), _flock_prm(params), n_obs, optr, gR, gth, parts)
-    return E, gR, gth, tuple(parts)
+    parts = np.zeros(6)
+    n_obs, o, optr = _rows3(obstacles)
+    n_p, pr, pptr = _rows3(predators)
+    gP = np.zeros((max(n_p, 1), 3))
+    E = lib().or_flock_grad(N, R, th, _box(L, 2), _flock_prm(params), n_obs, optr, n_p, pptr, gR, gth,
+                            gP.ctypes.data, parts)
+    return E, gR, gth, gP[:n_p], tuple(parts)
 
 
-def flock_run(R, theta, L, dt=0.1, nsteps=10, params=None, obstacles=None):
-    """Forward-Euler flocking.  Returns (R [N,2], theta [N], E[nsteps+1])."""
+def flock_run(R, theta, L, dt=0.1, nsteps=10, params=None, obstacles=None, predators=None):
+    """Forward-Euler flocking.  Returns (R [N,2], theta [N], predators [P,3],
+    E[nsteps+1])."""
     R = np.ascontiguousarray(np.asarray(R, np.float64)[:, :2]).copy()
     th = np.ascontiguousarray(theta, np.float64).copy()
     E = np.zeros(nsteps + 1)
-    n_obs, o, optr = _obs(obstacles)
-    lib().or_flock_run(R.shape[0], R, th, _box(L, 2), _flock_prm(params), n_obs, optr, dt, nsteps, E)
-    return R, th, E
+    n_obs, o, optr = _rows3(obstacles)
+    n_p, pr, pptr = _rows3(predators)
+    lib().or_flock_run(R.shape[0], R, th, _box(L, 2), _flock_prm(params), n_obs, optr, n_p, pptr, dt, nsteps, E)
+    return R, th, (pr if pr is not None else np.zeros((0, 3))), E
 
 
 # FIRE parameters (Bitzek et al. 2006 recommendations; dt_max = 4 dt_start)

@@ -560,21 +560,68 @@ void or_gd(int N, int dim, double *r, const double *diam, const double *L, int p
  *   E_obst   = sum_i sum_o J_ob rho(|R_o - R_i|; D_o) (1 + N_i.w_io)^2,
  *              w_io the unit vector from boid i to obstacle o (disk of
  *              radius D_o), smallest when the boid faces away
- * Forward Euler: R_i += dt (v N_i - dE/dR_i), theta_i -= dt dE/dtheta_i,
- * positions wrapped.  prm = {J_al, R_al, J_av, R_av, J_co, R_co, J_ob, a, v}.
- * obs: n_obs x 3 (x, y, D).  Brute force over all pairs. */
+ * Predators p (position, heading), a two-player game: the boids add
+ *   E_flee   = sum_i sum_p J_fl rho(|R_p - R_i|; R_fl) (1 + N_i.w_ip)^2
+ * (the obstacle form, gradient in the boid's variables), and the predators
+ * minimise
+ *   E_chase  = sum_p J_ch/2 (1 - u_p.N_p)^2, u_p towards the mean offset of
+ *              the boids within R_ch (the cohesion form), plus E_obst of
+ *              the predators (gradient in the predator's variables).
+ * Forward Euler for both: R += dt (v N - dE/dR), theta -= dt dE/dtheta,
+ * positions wrapped; speeds v (boids) and v_p (predators).
+ * prm = {J_al, R_al, J_av, R_av, J_co, R_co, J_ob, a, v, J_fl, R_fl, J_ch,
+ *        R_ch, v_p};  obs: n_obs x 3 (x, y, D);  pred: n_p x 3 (x, y, theta).
+ * Brute force over all pairs. */
 static double nearest1(double t, double L) { return t - L * nearbyint(t / L); }
 static double rho_cut(double r, double Rc, double a) { return r < Rc ? pow(1.0 - r / Rc, a) / a : 0.0; }
 static double rho_cut_d(double r, double Rc, double a) { return r < Rc ? -pow(1.0 - r / Rc, a - 1.0) / Rc : 0.0; }
 
+/* The obstacle form J rho(r; D) (1 + N.w)^2 of an agent at (x, y) with
+ * heading th against a disk at (ox, oy) of radius D; adds its energy and its
+ * gradient in the agent's variables. */
+static double disk_term(double x, double y, double th, double ox, double oy, double D, double J, double a,
+                        const double *L, double *gx, double *gy, double *gth)
+{
+    const double dx = nearest1(ox - x, L[0]), dy = nearest1(oy - y, L[1]);
+    const double r = sqrt(dx * dx + dy * dy);
+    if (!(r > 0.0 && r < D)) return 0.0;
+    const double wx = dx / r, wy = dy / r;
+    const double nx = cos(th), ny = sin(th);
+    const double nw = nx * wx + ny * wy, q = 1.0 + nw;
+    const double rh = rho_cut(r, D, a), rhd = rho_cut_d(r, D, a);
+    *gth += 2.0 * J * rh * q * (-sin(th) * wx + cos(th) * wy);
+    /* r depends on the agent as dr/dR = -w; w as dw/dR = -(I - w w^T)/r */
+    *gx += J * (rhd * (-wx) * q * q + rh * 2.0 * q * (-(nx - nw * wx) / r));
+    *gy += J * (rhd * (-wy) * q * q + rh * 2.0 * q * (-(ny - nw * wy) / r));
+    return J * rh * q * q;
+}
+
+/* The cohesion form J/2 (1 - u.N)^2 from the summed offsets (cx, cy) of n
+ * agents; adds its heading gradient. */
+static double heading_term(double cx, double cy, int n, double th, double J, double *gth)
+{
+    if (n <= 0) return 0.0;
+    cx /= n;
+    cy /= n;
+    const double m = sqrt(cx * cx + cy * cy);
+    if (!(m > 0.0)) return 0.0;
+    const double ux = cx / m, uy = cy / m;
+    const double un = ux * cos(th) + uy * sin(th);
+    const double up = -ux * sin(th) + uy * cos(th);   /* u . dN/dtheta */
+    *gth += -J * (1.0 - un) * up;
+    return 0.5 * J * (1.0 - un) * (1.0 - un);
+}
+
 double or_flock_grad(int N, const double *R, const double *th, const double *L, const double *prm, int n_obs,
-                     const double *obs, double *gR, double *gth, double *parts)
+                     const double *obs, int n_p, const double *pred, double *gR, double *gth, double *gP,
+                     double *parts)
 {
     const double Jal = prm[0], Ral = prm[1], Jav = prm[2], Rav = prm[3], Jco = prm[4], Rco = prm[5], Job = prm[6],
-                 a = prm[7];
-    double Eal = 0.0, Eav = 0.0, Eco = 0.0, Eob = 0.0;
+                 a = prm[7], Jfl = prm[9], Rfl = prm[10], Jch = prm[11], Rch = prm[12];
+    double Eal = 0.0, Eav = 0.0, Eco = 0.0, Eob = 0.0, Efl = 0.0, Ech = 0.0;
     for (int i = 0; i < 2 * N; ++i) gR[i] = 0.0;
     for (int i = 0; i < N; ++i) gth[i] = 0.0;
+    for (int i = 0; i < 3 * n_p; ++i) gP[i] = 0.0;
     for (int i = 0; i < N; ++i) {
         double cx = 0.0, cy = 0.0;
         int nco = 0;
@@ -584,11 +631,10 @@ double or_flock_grad(int N, const double *R, const double *th, const double *L, 
             for (int k = 0; k < 2; ++k) d[k] = nearest1(R[2 * i + k] - R[2 * j + k], L[k]);
             const double r = sqrt(d[0] * d[0] + d[1] * d[1]);
             const double c = cos(th[i] - th[j]);
-            // alignment: d/dtheta_i of rho (1 - c)^2 = 2 rho (1 - c) sin(theta_i - theta_j)
+            /* alignment: d/dtheta_i of rho (1 - c)^2 = 2 rho (1 - c) sin(theta_i - theta_j) */
             const double ral = rho_cut(r, Ral, a);
             if (j > i) Eal += Jal * ral * (1.0 - c) * (1.0 - c);
             gth[i] += 2.0 * Jal * ral * (1.0 - c) * sin(th[i] - th[j]);
-            // avoidance
             if (j > i) Eav += Jav * rho_cut(r, Rav, a);
             if (r > 0.0 && r < Rav) {
                 const double g = Jav * rho_cut_d(r, Rav, a) / r;
@@ -601,61 +647,65 @@ double or_flock_grad(int N, const double *R, const double *th, const double *L, 
                 nco += 1;
             }
         }
-        if (nco > 0) {
-            cx /= nco;
-            cy /= nco;
-            const double m = sqrt(cx * cx + cy * cy);
-            if (m > 0.0) {
-                const double ux = cx / m, uy = cy / m;
-                const double un = ux * cos(th[i]) + uy * sin(th[i]);
-                const double up = -ux * sin(th[i]) + uy * cos(th[i]);   // u . dN/dtheta
-                Eco += 0.5 * Jco * (1.0 - un) * (1.0 - un);
-                gth[i] += -Jco * (1.0 - un) * up;
+        Eco += heading_term(cx, cy, nco, th[i], Jco, &gth[i]);
+        for (int o = 0; o < n_obs; ++o)
+            Eob += disk_term(R[2 * i], R[2 * i + 1], th[i], obs[3 * o], obs[3 * o + 1], obs[3 * o + 2], Job, a, L,
+                             &gR[2 * i], &gR[2 * i + 1], &gth[i]);
+        for (int p = 0; p < n_p; ++p)
+            Efl += disk_term(R[2 * i], R[2 * i + 1], th[i], pred[3 * p], pred[3 * p + 1], Rfl, Jfl, a, L, &gR[2 * i],
+                             &gR[2 * i + 1], &gth[i]);
+    }
+    for (int p = 0; p < n_p; ++p) {
+        double cx = 0.0, cy = 0.0;
+        int n = 0;
+        for (int i = 0; i < N; ++i) {
+            const double dx = nearest1(R[2 * i] - pred[3 * p], L[0]), dy = nearest1(R[2 * i + 1] - pred[3 * p + 1], L[1]);
+            if (sqrt(dx * dx + dy * dy) < Rch) {
+                cx += dx;
+                cy += dy;
+                n += 1;
             }
         }
-        for (int o = 0; o < n_obs; ++o) {
-            double d[2];
-            for (int k = 0; k < 2; ++k) d[k] = nearest1(obs[3 * o + k] - R[2 * i + k], L[k]);
-            const double r = sqrt(d[0] * d[0] + d[1] * d[1]);
-            const double D = obs[3 * o + 2];
-            if (!(r > 0.0 && r < D)) continue;
-            const double wx = d[0] / r, wy = d[1] / r;
-            const double nx = cos(th[i]), ny = sin(th[i]);
-            const double q = 1.0 + nx * wx + ny * wy;
-            const double rh = rho_cut(r, D, a), rhd = rho_cut_d(r, D, a);
-            Eob += Job * rh * q * q;
-            gth[i] += 2.0 * Job * rh * q * (-sin(th[i]) * wx + cos(th[i]) * wy);
-            // d/dR_i: r depends on R_i as dr/dR_i = -w; w as dw/dR_i = -(I - w w^T)/r
-            const double nw = nx * wx + ny * wy;
-            gR[2 * i] += Job * (rhd * (-wx) * q * q + rh * 2.0 * q * (-(nx - nw * wx) / r));
-            gR[2 * i + 1] += Job * (rhd * (-wy) * q * q + rh * 2.0 * q * (-(ny - nw * wy) / r));
-        }
+        Ech += heading_term(cx, cy, n, pred[3 * p + 2], Jch, &gP[3 * p + 2]);
+        for (int o = 0; o < n_obs; ++o)
+            Eob += disk_term(pred[3 * p], pred[3 * p + 1], pred[3 * p + 2], obs[3 * o], obs[3 * o + 1], obs[3 * o + 2],
+                             Job, a, L, &gP[3 * p], &gP[3 * p + 1], &gP[3 * p + 2]);
     }
     if (parts) {
         parts[0] = Eal;
         parts[1] = Eav;
         parts[2] = Eco;
         parts[3] = Eob;
+        parts[4] = Efl;
+        parts[5] = Ech;
     }
-    return Eal + Eav + Eco + Eob;
+    return Eal + Eav + Eco + Eob + Efl + Ech;
 }
 
 void or_flock_run(int N, double *R, double *th, const double *L, const double *prm, int n_obs, const double *obs,
-                  double dt, int nsteps, double *Eser)
+                  int n_p, double *pred, double dt, int nsteps, double *Eser)
 {
     double *gR = (double *)calloc((size_t)2 * N + 1, sizeof(double));
     double *gth = (double *)calloc((size_t)N + 1, sizeof(double));
-    const double v = prm[8];
+    double *gP = (double *)calloc((size_t)3 * n_p + 1, sizeof(double));
+    const double v = prm[8], vp = prm[13];
     for (int s = 0; s < nsteps; ++s) {
-        const double E = or_flock_grad(N, R, th, L, prm, n_obs, obs, gR, gth, NULL);
+        const double E = or_flock_grad(N, R, th, L, prm, n_obs, obs, n_p, pred, gR, gth, gP, NULL);
         if (Eser) Eser[s] = E;
         for (int i = 0; i < N; ++i) {
             R[2 * i] = wrap64(R[2 * i] + dt * (v * cos(th[i]) - gR[2 * i]), L[0]);
             R[2 * i + 1] = wrap64(R[2 * i + 1] + dt * (v * sin(th[i]) - gR[2 * i + 1]), L[1]);
             th[i] -= dt * gth[i];
         }
+        for (int p = 0; p < n_p; ++p) {
+            const double tp = pred[3 * p + 2];
+            pred[3 * p] = wrap64(pred[3 * p] + dt * (vp * cos(tp) - gP[3 * p]), L[0]);
+            pred[3 * p + 1] = wrap64(pred[3 * p + 1] + dt * (vp * sin(tp) - gP[3 * p + 1]), L[1]);
+            pred[3 * p + 2] = tp - dt * gP[3 * p + 2];
+        }
     }
-    if (Eser) Eser[nsteps] = or_flock_grad(N, R, th, L, prm, n_obs, obs, gR, gth, NULL);
+    if (Eser) Eser[nsteps] = or_flock_grad(N, R, th, L, prm, n_obs, obs, n_p, pred, gR, gth, gP, NULL);
+    free(gP);
     free(gth);
     free(gR);
 }
