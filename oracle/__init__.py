@@ -257,9 +257,10 @@ def nhc(r, v, L, pot="lj", mass=1.0, dt=0.005, kT=1.0, tau=None, M=3, nsteps=10,
 # (boids fleeing), J_chase, R_chase (predators chasing), predator speed
 FLOCK_DEFAULTS = dict(J_align=1.0, R_align=45.0, J_avoid=25.0, R_avoid=30.0, J_cohesion=0.05, R_cohesion=40.0,
                       J_obstacle=10.0, alpha=2.0, speed=1.0, J_flee=10.0, R_flee=60.0, J_chase=0.2,
-                      R_chase=150.0, predator_speed=0.85)
+                      R_chase=150.0, predator_speed=0.85, sprint_period=50, sprint_steps=10, sprint_factor=2.0)
 _FLOCK_KEYS = ("J_align", "R_align", "J_avoid", "R_avoid", "J_cohesion", "R_cohesion", "J_obstacle", "alpha", "speed",
-               "J_flee", "R_flee", "J_chase", "R_chase", "predator_speed")
+               "J_flee", "R_flee", "J_chase", "R_chase", "predator_speed", "sprint_period", "sprint_steps",
+               "sprint_factor")
 
 
 def _flock_prm(params):

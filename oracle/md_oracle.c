@@ -568,9 +568,13 @@ void or_gd(int N, int dim, double *r, const double *diam, const double *L, int p
  *              the boids within R_ch (the cohesion form), plus E_obst of
  *              the predators (gradient in the predator's variables).
  * Forward Euler for both: R += dt (v N - dE/dR), theta -= dt dE/dtheta,
- * positions wrapped; speeds v (boids) and v_p (predators).
+ * positions wrapped; speeds v (boids) and v_p (predators).  Sprints (the
+ * paper lets predators sprint now and then without saying how): in step s
+ * (counted from 0 in each run) the predators swim at v_p * f_sp when
+ * P_sp > 0 and s mod P_sp < n_sp.
  * prm = {J_al, R_al, J_av, R_av, J_co, R_co, J_ob, a, v, J_fl, R_fl, J_ch,
- *        R_ch, v_p};  obs: n_obs x 3 (x, y, D);  pred: n_p x 3 (x, y, theta).
+ *        R_ch, v_p, P_sp, n_sp, f_sp};  obs: n_obs x 3 (x, y, D);
+ *        pred: n_p x 3 (x, y, theta).
  * Brute force over all pairs. */
 static double nearest1(double t, double L) { return t - L * nearbyint(t / L); }
 static double rho_cut(double r, double Rc, double a) { return r < Rc ? pow(1.0 - r / Rc, a) / a : 0.0; }
@@ -688,8 +692,10 @@ void or_flock_run(int N, double *R, double *th, const double *L, const double *p
     double *gR = (double *)calloc((size_t)2 * N + 1, sizeof(double));
     double *gth = (double *)calloc((size_t)N + 1, sizeof(double));
     double *gP = (double *)calloc((size_t)3 * n_p + 1, sizeof(double));
-    const double v = prm[8], vp = prm[13];
+    const double v = prm[8];
+    const long P_sp = (long)prm[14], n_sp = (long)prm[15];
     for (int s = 0; s < nsteps; ++s) {
+        const double vp = (P_sp > 0 && s % P_sp < n_sp) ? prm[13] * prm[16] : prm[13];
         const double E = or_flock_grad(N, R, th, L, prm, n_obs, obs, n_p, pred, gR, gth, gP, NULL);
         if (Eser) Eser[s] = E;
         for (int i = 0; i < N; ++i) {

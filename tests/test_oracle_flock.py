@@ -130,3 +130,24 @@ def test_lone_boid_swims_straight():
     np.testing.assert_allclose(R[0], R0[0] + 0.25 * 40 * FP["speed"] * np.array([np.cos(0.7), np.sin(0.7)]),
                                rtol=0, atol=1e-10)
     assert th[0] == 0.7 and np.all(E == 0.0)
+
+
+def test_lone_predator_sprints():
+    # no boids in chase range and no obstacles: the predator swims straight,
+    # at twice its speed in the first sprint_steps of every sprint_period
+    L = 2000.0
+    R0 = np.array([[10.0, 10.0]])
+    p0 = np.array([[1000.0, 1000.0, -0.4]])
+    prm = dict(sprint_period=7, sprint_steps=3, sprint_factor=2.0)
+    n, dt = 23, 0.5
+    _, _, p, _ = O.flock_run(R0, np.array([0.0]), L, dt=dt, nsteps=n, params=prm, predators=p0)
+    fast = sum(1 for s in range(n) if s % 7 < 3)
+    dist = dt * FP["predator_speed"] * (2.0 * fast + (n - fast))
+    np.testing.assert_allclose(p[0, :2], p0[0, :2] + dist * np.array([np.cos(-0.4), np.sin(-0.4)]), rtol=0,
+                               atol=1e-9)
+    assert p[0, 2] == -0.4
+    # sprints off: plain speed
+    _, _, p, _ = O.flock_run(R0, np.array([0.0]), L, dt=dt, nsteps=n, params=dict(sprint_period=0),
+                             predators=p0)
+    np.testing.assert_allclose(p[0, :2], p0[0, :2] + dt * n * FP["predator_speed"] *
+                               np.array([np.cos(-0.4), np.sin(-0.4)]), rtol=0, atol=1e-9)
