@@ -382,15 +382,15 @@ def nhc_section(steps=200):
     return out
 
 
-def flock_section(N=100000, steps=200):
+def flock_section(N=100000, steps=200, n_pred=8):
     """Flocking energy model: N boids with ~20 neighbours within the
-    alignment range and 16 disk obstacles, `steps` forward-Euler steps
-    (dt = 0.1) with list rebuilds."""
+    alignment range, 16 disk obstacles and n_pred predators, `steps`
+    forward-Euler steps (dt = 0.1) with list rebuilds."""
     import torch
     import paper_1912_04232_b300 as P
     import workloads as W
     dev = torch.device("cuda")
-    fl = W.flock(N, n_obs=16, seed=0)
+    fl = W.flock(N, n_obs=16, seed=0, n_pred=n_pred)
     prm = P.flock_params()
     s = P.md_space_periodic(2, [fl.L, fl.L])
     nl = P.NeighborList(s, N, max(prm.R_align, prm.R_avoid, prm.R_cohesion), 4.0, 128)
@@ -400,24 +400,28 @@ def flock_section(N=100000, steps=200):
     th0 = torch.from_numpy(fl.theta).to(dev)
     obs = torch.from_numpy(fl.obstacles).to(dev)
     b, th, alt = torch.empty_like(b0), torch.empty_like(th0), torch.empty_like(b0)
+    p0 = torch.zeros((n_pred, 4), dtype=torch.float32, device=dev)
+    p0[:, :3] = torch.from_numpy(fl.predators).to(dev)
+    pr, pr_alt = torch.empty_like(p0), torch.empty_like(p0)
     E = torch.zeros(steps, dtype=torch.float64, device=dev)
     ts = []
     b1 = nl.stats()[0]
     for k in range(3):
         b.copy_(b0)
         th.copy_(th0)
+        pr.copy_(p0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         nl.build(b, st)
-        P.md_flock_run(s, prm, obs, obs.shape[0], b, th, alt, 0.1, steps, nl.plan, E, st)
+        P.md_flock_run(s, prm, obs, obs.shape[0], pr, pr_alt, n_pred, b, th, alt, 0.1, steps, nl.plan, E, st)
         e1.record()
         e1.synchronize()
         if k:
             ts.append(e0.elapsed_time(e1))
     ms = min(ts)
     En = E.cpu().numpy()
-    return {"N": N, "steps": steps, "ms": ms, "boid_steps_per_s": N * steps / (ms * 1e-3),
+    return {"N": N, "predators": n_pred, "steps": steps, "ms": ms, "boid_steps_per_s": N * steps / (ms * 1e-3),
             "builds_per_run": (nl.stats()[0] - b1) / 3.0, "E_start": float(En[0]), "E_end": float(En[-1]),
             "status": P.md_status_poll(st)}
 

@@ -343,20 +343,34 @@ JMD_API md_status md_fire_state_read(const void *d_state, double *out3, md_strea
  *                w_io the unit vector from boid i to disk obstacle o
  * Alignment and cohesion turn the boids only (no gradient through the
  * displacements).  Forward Euler: R_i += dt (speed N_i - dE/dR_i) (wrapped),
- * theta_i -= dt dE/dtheta_i. */
+ * theta_i -= dt dE/dtheta_i.
+ * Predators (position, heading), a two-player game: the boids add
+ *   E_flee     = sum_i sum_p J_flee rho(|R_p - R_i|; R_flee) (1 + N_i.w_ip)^2
+ * (the obstacle form), the predators minimise their own energy, the
+ * cohesion form towards the boids within R_chase (heading only) plus the
+ * obstacle terms, with forward-Euler steps at predator_speed.  The paper
+ * lets predators sprint without defining it: here they swim at
+ * predator_speed * sprint_factor in the steps s (counted from 0 in each
+ * md_flock_run call) with s mod sprint_period < sprint_steps. */
 typedef struct {
     float J_align, R_align, J_avoid, R_avoid, J_cohesion, R_cohesion, J_obstacle, alpha, speed;
+    float J_flee, R_flee, J_chase, R_chase, predator_speed;   /* predators */
+    int sprint_period, sprint_steps;                         /* sprints; period 0: none */
+    float sprint_factor;
 } md_flock_params;
 
 /* nsteps of the flocking dynamics.  d_b [N][4]: (x, y, -, -) in, (x, y,
  * cos theta, sin theta) out; d_theta [N] headings in/out; d_b_alt [N][4]
- * scratch; d_obs [n_obs][3] (x, y, radius) device.  nb: a 2-D list built
- * for d_b with r_cut >= max(R_align, R_avoid, R_cohesion); rebuilt as the
- * boids move.  d_E (nsteps doubles, may be NULL): the energy before each
- * step. */
+ * scratch; d_obs [n_obs][3] (x, y, radius) device; d_pred [n_pred][4]
+ * predators (x, y, theta, -) in/out (w: the predator's energy of the last
+ * state), d_pred_alt [n_pred][4] scratch.  nb: a 2-D list built for d_b with
+ * r_cut >= max(R_align, R_avoid, R_cohesion); rebuilt as the boids move.
+ * d_E (nsteps doubles, may be NULL): the total energy (boids' and
+ * predators') before each step. */
 JMD_API md_status md_flock_run(const md_space *s, const md_flock_params *prm, const float *d_obs, int n_obs,
-                               float *d_b, float *d_theta, float *d_b_alt, float dt, int nsteps, md_nbr *nb,
-                               double *d_E, uint32_t *d_status, md_stream_t stream);
+                               float *d_pred, float *d_pred_alt, int n_pred, float *d_b, float *d_theta,
+                               float *d_b_alt, float dt, int nsteps, md_nbr *nb, double *d_E, uint32_t *d_status,
+                               md_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Learned potential: the pieces of a forward/backward and a training step   */

@@ -9,7 +9,13 @@
 //             the boids within R_co (turns boids only)
 //   E_obst  = sum_i sum_o J_ob rho(|R_o - R_i|; D_o) (1 + N_i.w_io)^2, w_io
 //             the unit vector from the boid to disk obstacle o
+//   E_flee  = the obstacle form against each predator (range R_fl)
 // and forward Euler R_i += dt (v N_i - dE/dR_i), theta_i -= dt dE/dtheta_i.
+// Predators minimise their own energy: the cohesion form towards the boids
+// within R_ch (heading only) plus the obstacles (k_predator_scan over slabs
+// of boids, k_predator_step per predator).  They sprint (speed x sprint_factor) in
+// the steps s with s mod sprint_period < sprint_steps, s counted from 0 in
+// each call.
 //
 // k_flock_step: a group of TPP lanes per boid gathers its row of the list
 // (float4 = x, y, cos theta, sin theta, so no pair needs a sine), reduces
@@ -18,6 +24,8 @@
 // the headings are updated in place by their owners.  The displacement
 // check for the list and the FP64 energy of the state before the step are
 // fused in.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -32,6 +40,9 @@ struct FlockArgs {
     float4 *b_out;          // the next step
     float *theta;           // headings, updated in place
     const float *obs;       // n_obs x 3: x, y, radius
+    const float4 *pred;     // n_pred predators this step: x, y, theta, energy of the previous state
+    float4 *pred_out;       // the next step (w: its energy in this state)
+    int n_pred;
     const int32_t *nbr, *cnt;
     const float4 *rref;
     float half_skin2;
@@ -52,6 +63,40 @@ __device__ __forceinline__ float fl_rho_d(float r, float Rc, float a)
     if (!(r < Rc)) return 0.0f;
     const float x = 1.0f - r / Rc;
     return -(a == 2.0f ? x : __powf(x, a - 1.0f)) / Rc;
+}
+
+// The disk form J rho(r; D) (1 + N.w)^2 of an agent at (x, y), heading
+// (ci, si), against a disk at (ox, oy): adds energy and the gradient in the
+// agent's variables.
+__device__ __forceinline__ void fl_disk(const FlockArgs &a, float x, float y, float ci, float si, float ox, float oy,
+                                        float D, float J, float &e, float &gx, float &gy, float &gth)
+{
+    const float dx = min_image_rn(ox, x, a.box.L[0], a.box.Linv[0]);
+    const float dy = min_image_rn(oy, y, a.box.L[1], a.box.Linv[1]);
+    const float r = sqrtf(dx * dx + dy * dy);
+    if (!(r > 0.0f && r < D)) return;
+    const float wx = dx / r, wy = dy / r;
+    const float nw = ci * wx + si * wy, q = 1.0f + nw;
+    const float rh = fl_rho(r, D, a.p.alpha), rhd = fl_rho_d(r, D, a.p.alpha);
+    e += J * rh * q * q;
+    gth += 2.0f * J * rh * q * (-si * wx + ci * wy);
+    gx += J * (rhd * (-wx) * q * q + rh * 2.0f * q * (-(ci - nw * wx) / r));
+    gy += J * (rhd * (-wy) * q * q + rh * 2.0f * q * (-(si - nw * wy) / r));
+}
+
+// The cohesion form J/2 (1 - u.N)^2 from summed offsets (cx, cy) of n
+// agents: adds energy and the heading gradient.
+__device__ __forceinline__ void fl_heading(float cx, float cy, float n, float ci, float si, float J, float &e,
+                                           float &gth)
+{
+    if (!(n > 0.0f)) return;
+    const float mx = cx / n, my = cy / n;
+    const float m = sqrtf(mx * mx + my * my);
+    if (!(m > 0.0f)) return;
+    const float ux = mx / m, uy = my / m;
+    const float un = ux * ci + uy * si, up = -ux * si + uy * ci;
+    e += 0.5f * J * (1.0f - un) * (1.0f - un);
+    gth += -J * (1.0f - un) * up;
 }
 
 template <int TPP>
@@ -110,29 +155,13 @@ __global__ void __launch_bounds__(256) k_flock_step(FlockArgs a)
     bool mv = false;
     if (valid && lg == 0) {
         const float ci = bi.z, si = bi.w;
-        if (nco > 0.0f) {
-            const float mx = cx / nco, my = cy / nco;
-            const float m = sqrtf(mx * mx + my * my);
-            if (m > 0.0f) {
-                const float ux = mx / m, uy = my / m;
-                const float un = ux * ci + uy * si, up = -ux * si + uy * ci;
-                e += 0.5f * p.J_cohesion * (1.0f - un) * (1.0f - un);
-                gth += -p.J_cohesion * (1.0f - un) * up;
-            }
-        }
-        for (int o = 0; o < a.n_obs; ++o) {
-            const float ox = __ldg(a.obs + 3 * o), oy = __ldg(a.obs + 3 * o + 1), D = __ldg(a.obs + 3 * o + 2);
-            const float dx = min_image_rn(ox, bi.x, a.box.L[0], a.box.Linv[0]);
-            const float dy = min_image_rn(oy, bi.y, a.box.L[1], a.box.Linv[1]);
-            const float r = sqrtf(dx * dx + dy * dy);
-            if (!(r > 0.0f && r < D)) continue;
-            const float wx = dx / r, wy = dy / r;
-            const float nw = ci * wx + si * wy, q = 1.0f + nw;
-            const float rh = fl_rho(r, D, p.alpha), rhd = fl_rho_d(r, D, p.alpha);
-            e += p.J_obstacle * rh * q * q;
-            gth += 2.0f * p.J_obstacle * rh * q * (-si * wx + ci * wy);
-            gx += p.J_obstacle * (rhd * (-wx) * q * q + rh * 2.0f * q * (-(ci - nw * wx) / r));
-            gy += p.J_obstacle * (rhd * (-wy) * q * q + rh * 2.0f * q * (-(si - nw * wy) / r));
+        fl_heading(cx, cy, nco, ci, si, p.J_cohesion, e, gth);
+        for (int o = 0; o < a.n_obs; ++o)
+            fl_disk(a, bi.x, bi.y, ci, si, __ldg(a.obs + 3 * o), __ldg(a.obs + 3 * o + 1), __ldg(a.obs + 3 * o + 2),
+                    p.J_obstacle, e, gx, gy, gth);
+        for (int q = 0; q < a.n_pred; ++q) {
+            const float4 pq = a.pred[q];
+            fl_disk(a, bi.x, bi.y, ci, si, pq.x, pq.y, p.R_flee, p.J_flee, e, gx, gy, gth);
         }
         float th = a.theta[i];
         const float x = wrap_coord(bi.x + a.dt * (p.speed * ci - gx), a.box.L[0], a.box.Linv[0]);
@@ -149,7 +178,10 @@ __global__ void __launch_bounds__(256) k_flock_step(FlockArgs a)
         e = 0.0f;
     }
     if (__any_sync(0xffffffffu, mv) && (threadIdx.x & 31) == 0) a.ctl[CTL_REBUILD] = 1u;
-    if (!a.E_out) return;
+    if (!a.E_out) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl[CTL_STEP] += 1u;   // the step count (sprints)
+        return;
+    }
     // FP64 energy of the state before the step: warp (FP32), block and grid
     // (FP64, fixed order by the last block)
 #pragma unroll
@@ -168,11 +200,100 @@ __global__ void __launch_bounds__(256) k_flock_step(FlockArgs a)
     __threadfence();
     double E = 0.0;
     for (int b = 0; b < (int)gridDim.x; ++b) E += ((volatile double *)(a.partials + b))[0];
+    for (int q = 0; q < a.n_pred; ++q) E += (double)a.pred_out[q].w;
     a.ctl[CTL_TICKET] = 0u;
     if (!isfinite(E)) raise_status(a.status, MD_ERR_NONFINITE);
     const unsigned step = a.ctl[CTL_STEP];
     a.E_out[step] = E;
     a.ctl[CTL_STEP] = step + 1u;
+}
+
+// Chase sums, in two kernels so that the scan of the boids fills the GPU and
+// the sums keep a fixed order: k_predator_scan block s takes the boids of
+// slab s and writes, per predator q, the summed offsets R_i - R_q of the
+// boids within R_ch and their count to ppart[q * S + s]; k_predator_step
+// (one warp per predator) adds the S slabs, then takes the predator's chase
+// and obstacle energy and gradient and its forward-Euler step into pred_out
+// (w = its energy in the state before the step).
+__global__ void __launch_bounds__(256) k_predator_scan(FlockArgs a, float4 *ppart, int S)
+{
+    count_launch();
+    __shared__ float sh[3][8];
+    const int s = blockIdx.x;
+    const int chunk = (a.N + S - 1) / S;
+    const int i0 = s * chunk, i1 = min(a.N, i0 + chunk);
+    const float R2 = a.p.R_chase * a.p.R_chase;
+    for (int q = 0; q < a.n_pred; ++q) {
+        const float4 pq = a.pred[q];
+        float cx = 0.f, cy = 0.f, n = 0.f;
+        for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) {
+            const float4 bi = a.b[i];
+            const float dx = min_image_rn(bi.x, pq.x, a.box.L[0], a.box.Linv[0]);
+            const float dy = min_image_rn(bi.y, pq.y, a.box.L[1], a.box.Linv[1]);
+            if (dx * dx + dy * dy < R2) {
+                cx += dx;
+                cy += dy;
+                n += 1.0f;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cx += __shfl_xor_sync(0xffffffffu, cx, o);
+            cy += __shfl_xor_sync(0xffffffffu, cy, o);
+            n += __shfl_xor_sync(0xffffffffu, n, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            sh[0][threadIdx.x >> 5] = cx;
+            sh[1][threadIdx.x >> 5] = cy;
+            sh[2][threadIdx.x >> 5] = n;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            cx = cy = n = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                cx += sh[0][w];
+                cy += sh[1][w];
+                n += sh[2][w];
+            }
+            ppart[(size_t)q * S + s] = make_float4(cx, cy, n, 0.f);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(32) k_predator_step(FlockArgs a, const float4 *ppart, int S)
+{
+    count_launch();
+    const int q = blockIdx.x;
+    const float4 pq = a.pred[q];
+    float cx = 0.f, cy = 0.f, n = 0.f;
+    for (int s = (int)threadIdx.x; s < S; s += 32) {
+        const float4 v = ppart[(size_t)q * S + s];
+        cx += v.x;
+        cy += v.y;
+        n += v.z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cx += __shfl_xor_sync(0xffffffffu, cx, o);
+        cy += __shfl_xor_sync(0xffffffffu, cy, o);
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+    }
+    if (threadIdx.x != 0) return;
+    float sn, cs;
+    sincosf(pq.z, &sn, &cs);
+    float e = 0.f, gx = 0.f, gy = 0.f, gth = 0.f;
+    fl_heading(cx, cy, n, cs, sn, a.p.J_chase, e, gth);
+    for (int o = 0; o < a.n_obs; ++o)
+        fl_disk(a, pq.x, pq.y, cs, sn, __ldg(a.obs + 3 * o), __ldg(a.obs + 3 * o + 1), __ldg(a.obs + 3 * o + 2),
+                a.p.J_obstacle, e, gx, gy, gth);
+    const uint32_t step = *(const volatile uint32_t *)&a.ctl[CTL_STEP];
+    const float vp = (a.p.sprint_period > 0 && (int)(step % (uint32_t)a.p.sprint_period) < a.p.sprint_steps)
+                         ? a.p.predator_speed * a.p.sprint_factor
+                         : a.p.predator_speed;
+    const float x = wrap_coord(pq.x + a.dt * (vp * cs - gx), a.box.L[0], a.box.Linv[0]);
+    const float y = wrap_coord(pq.y + a.dt * (vp * sn - gy), a.box.L[1], a.box.Linv[1]);
+    a.pred_out[q] = make_float4(x, y, pq.z - a.dt * gth, e);
 }
 
 // (x, y) from the caller's positions, (cos, sin) of the headings.
@@ -194,15 +315,18 @@ __global__ void __launch_bounds__(256) k_flock_init(float4 *b, const float *thet
 using namespace jmd;
 
 extern "C" md_status md_flock_run(const md_space *s, const md_flock_params *prm, const float *d_obs, int n_obs,
-                                  float *d_b, float *d_theta, float *d_b_alt, float dt, int nsteps, md_nbr *nb,
-                                  double *d_E, uint32_t *d_status, md_stream_t stream)
+                                  float *d_pred, float *d_pred_alt, int n_pred, float *d_b, float *d_theta,
+                                  float *d_b_alt, float dt, int nsteps, md_nbr *nb, double *d_E, uint32_t *d_status,
+                                  md_stream_t stream)
 {
-    if (!s || !prm || !d_b || !d_theta || !d_b_alt || !nb || nsteps < 0 || n_obs < 0) return MD_ERR_INVALID;
-    if (n_obs > 0 && !d_obs) return MD_ERR_INVALID;
+    if (!s || !prm || !d_b || !d_theta || !d_b_alt || !nb || nsteps < 0 || n_obs < 0 || n_pred < 0)
+        return MD_ERR_INVALID;
+    if ((n_obs > 0 && !d_obs) || (n_pred > 0 && (!d_pred || !d_pred_alt))) return MD_ERR_INVALID;
     if (s->dim != 2 || nb->dim != 2 || !nb->nbr || !nb->cnt || !nb->ws || !nb->rref || !nbr_layout_ok(nb))
         return MD_ERR_INVALID;
     const float rmax = fmaxf(prm->R_align, fmaxf(prm->R_avoid, prm->R_cohesion));
     if (!(rmax > 0.0f) || rmax > nb->r_cut || !(prm->alpha >= 1.0f) || !(dt > 0.0f)) return MD_ERR_INVALID;
+    if (prm->sprint_period < 0 || prm->sprint_steps < 0) return MD_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     const WsPtrs w = ws_ptrs(nb);
     const int N = nb->N;
@@ -216,6 +340,9 @@ extern "C" md_status md_flock_run(const md_space *s, const md_flock_params *prm,
     a.dt = dt;
     a.theta = d_theta;
     a.obs = d_obs;
+    a.n_pred = n_pred;
+    a.pred = (const float4 *)d_pred;   // (the graph key holds both predator buffers)
+    a.pred_out = (float4 *)d_pred_alt;
     a.nbr = nb->nbr;
     a.cnt = nb->cnt;
     a.rref = (const float4 *)nb->rref;
@@ -227,10 +354,15 @@ extern "C" md_status md_flock_run(const md_space *s, const md_flock_params *prm,
     constexpr int TPP = 4;
     const int grid = (int)(((long long)N * TPP + 255) / 256);
     if (d_E && grid > w.max_blocks) return MD_ERR_INVALID;
+    // the chase partials borrow the energy partials (free until k_flock_step)
+    if (n_pred > w.max_blocks) return MD_ERR_INVALID;
+    const int S = n_pred > 0 ? std::max(1, std::min((N + 255) / 256, w.max_blocks / n_pred)) : 1;
+    float4 *ppart = (float4 *)w.partials;
     enqueue_loop_init(w.ctl, (uint32_t)nsteps, st);
     k_flock_init<<<(N + 255) / 256, 256, 0, st>>>((float4 *)d_b, d_theta, N);
     NbrArgs na[2] = {make_nbr_args(s, d_b_alt, nb, d_status, 1), make_nbr_args(s, d_b, nb, d_status, 1)};
     float4 *buf[2] = {(float4 *)d_b, (float4 *)d_b_alt};
+    float4 *pbuf[2] = {(float4 *)d_pred, (float4 *)d_pred_alt};
     const int ncell = nb->ncell_total;
     // step t: the state in buf[t & 1] moves to the other buffer; the list is
     // rebuilt (if needed) on the new positions
@@ -238,6 +370,12 @@ extern "C" md_status md_flock_run(const md_space *s, const md_flock_params *prm,
         FlockArgs at = a;
         at.b = buf[t & 1];
         at.b_out = buf[(t + 1) & 1];
+        at.pred = pbuf[t & 1];
+        at.pred_out = pbuf[(t + 1) & 1];
+        if (n_pred > 0) {
+            k_predator_scan<<<S, 256, 0, cs>>>(at, ppart, S);
+            k_predator_step<<<n_pred, 32, 0, cs>>>(at, ppart, S);
+        }
         k_flock_step<TPP><<<grid, 256, 0, cs>>>(at);
         if (lb) return lb->rebuild_if(na[t & 1], ncell);
         enqueue_rebuild_chain(na[t & 1], ncell, cs);
@@ -268,7 +406,12 @@ extern "C" md_status md_flock_run(const md_space *s, const md_flock_params *prm,
         done = nsteps / 2 * 2;
     }
     for (int t = done; t < nsteps; ++t) step(t, st, nullptr);
-    if (nsteps & 1) JMD_CUDA_TRY(cudaMemcpyAsync(d_b, d_b_alt, sizeof(float4) * (size_t)N, cudaMemcpyDeviceToDevice, st));
+    if (nsteps & 1) {
+        JMD_CUDA_TRY(cudaMemcpyAsync(d_b, d_b_alt, sizeof(float4) * (size_t)N, cudaMemcpyDeviceToDevice, st));
+        if (n_pred > 0)
+            JMD_CUDA_TRY(cudaMemcpyAsync(d_pred, d_pred_alt, sizeof(float4) * (size_t)n_pred,
+                                         cudaMemcpyDeviceToDevice, st));
+    }
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
 }

@@ -81,12 +81,17 @@ def fire_params(dt_start=0.1, dt_max=0.4, f_inc=1.1, f_dec=0.5, alpha_start=0.1,
 
 class md_flock_params(C.Structure):
     _fields_ = [(n, C.c_float) for n in ("J_align", "R_align", "J_avoid", "R_avoid", "J_cohesion", "R_cohesion",
-                                         "J_obstacle", "alpha", "speed")]
+                                         "J_obstacle", "alpha", "speed", "J_flee", "R_flee", "J_chase", "R_chase",
+                                         "predator_speed")] + [("sprint_period", C.c_int), ("sprint_steps", C.c_int),
+                                                               ("sprint_factor", C.c_float)]
 
 
 def flock_params(J_align=1.0, R_align=45.0, J_avoid=25.0, R_avoid=30.0, J_cohesion=0.05, R_cohesion=40.0,
-                 J_obstacle=10.0, alpha=2.0, speed=1.0):
-    return md_flock_params(J_align, R_align, J_avoid, R_avoid, J_cohesion, R_cohesion, J_obstacle, alpha, speed)
+                 J_obstacle=10.0, alpha=2.0, speed=1.0, J_flee=10.0, R_flee=60.0, J_chase=0.2, R_chase=150.0,
+                 predator_speed=0.85, sprint_period=50, sprint_steps=10, sprint_factor=2.0):
+    return md_flock_params(J_align, R_align, J_avoid, R_avoid, J_cohesion, R_cohesion, J_obstacle, alpha, speed,
+                           J_flee, R_flee, J_chase, R_chase, predator_speed, int(sprint_period), int(sprint_steps),
+                           sprint_factor)
 
 
 class md_replica_desc(C.Structure):
@@ -124,8 +129,8 @@ _SIGS = {
     "md_minimize_fire": [_P(md_space), _P(md_pot), _P(md_fire_params), C.c_int, _vp, _vp, _vp, _P(md_nbr), _vp, C.c_int,
                          _vp, _vp, _vp],
     "md_fire_state_read": [_vp, _P(C.c_double), _vp],
-    "md_flock_run": [_P(md_space), _P(md_flock_params), _vp, C.c_int, _vp, _vp, _vp, C.c_float, C.c_int, _P(md_nbr),
-                     _vp, _vp, _vp],
+    "md_flock_run": [_P(md_space), _P(md_flock_params), _vp, C.c_int, _vp, _vp, C.c_int, _vp, _vp, _vp, C.c_float,
+                     C.c_int, _P(md_nbr), _vp, _vp, _vp],
     "md_integrate_nhc": [_P(md_space), _P(md_pot), _vp, _vp, _vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
                          C.c_int, _P(md_nbr), _vp, C.c_int, _vp, _vp, _vp, C.c_int, _vp, _vp],
     "md_status_poll": [_vp, _P(C.c_uint32), _vp],
@@ -296,10 +301,11 @@ def md_integrate_nhc(space, pot, r, v, f, mass, dt, kT, tau, M, nsteps, nb, ther
                                  _stream(stream)), "md_integrate_nhc")
 
 
-def md_flock_run(space, params, obs, n_obs, b, theta, b_alt, dt, nsteps, nb, E=None, status=None, stream=None):
-    _check(_lib.md_flock_run(C.byref(space), C.byref(params), _ptr(obs), int(n_obs), _ptr(b), _ptr(theta), _ptr(b_alt),
-                             float(dt), int(nsteps), C.byref(nb), _ptr(E), _ptr(status), _stream(stream)),
-           "md_flock_run")
+def md_flock_run(space, params, obs, n_obs, pred, pred_alt, n_pred, b, theta, b_alt, dt, nsteps, nb, E=None,
+                 status=None, stream=None):
+    _check(_lib.md_flock_run(C.byref(space), C.byref(params), _ptr(obs), int(n_obs), _ptr(pred), _ptr(pred_alt),
+                             int(n_pred), _ptr(b), _ptr(theta), _ptr(b_alt), float(dt), int(nsteps), C.byref(nb),
+                             _ptr(E), _ptr(status), _stream(stream)), "md_flock_run")
 
 
 def md_fire_state_bytes() -> int:

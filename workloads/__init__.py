@@ -270,10 +270,11 @@ class Flock:
     R: np.ndarray           # [N, 2] float32 positions
     theta: np.ndarray       # [N] float32 headings
     obstacles: np.ndarray   # [n_obs, 3] float32 (x, y, radius)
+    predators: np.ndarray = None   # [n_pred, 3] float32 (x, y, theta)
 
 
 def flock(N: int = 2000, neighbours: float = 20.0, R_align: float = 45.0, n_obs: int = 4,
-          obstacle_radius: float = 60.0, seed: int = 0) -> Flock:
+          obstacle_radius: float = 60.0, seed: int = 0, n_pred: int = 0) -> Flock:
     """Uniform positions and headings; the box edge gives about `neighbours`
     boids within R_align of each boid; disk obstacles at uniform centres."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -284,7 +285,10 @@ def flock(N: int = 2000, neighbours: float = 20.0, R_align: float = 45.0, n_obs:
     obs = np.zeros((n_obs, 3), np.float32)
     obs[:, :2] = rng.uniform(0.0, L, size=(n_obs, 2))
     obs[:, 2] = obstacle_radius
-    return Flock(N=N, L=L, R=R, theta=theta, obstacles=obs)
+    pred = np.zeros((n_pred, 3), np.float32)
+    pred[:, :2] = rng.uniform(0.0, L, size=(n_pred, 2))
+    pred[:, 2] = rng.uniform(-math.pi, math.pi, size=n_pred)
+    return Flock(N=N, L=L, R=R, theta=theta, obstacles=obs, predators=pred)
 
 
 def uniform_box_positions(N: int, L: float, dim: int, rng: np.random.Generator) -> np.ndarray:
