@@ -296,3 +296,28 @@ def uniform_box_positions(N: int, L: float, dim: int, rng: np.random.Generator) 
     r = np.mod(rng.uniform(0.0, L, size=(N, dim)), L).astype(np.float32)
     r[r >= np.float32(L)] = 0.0
     return r
+
+
+# --------------------------------------------------------------------------
+# Graph-network potential weights (Sec. 3.2.4 / 4.1): random, seeded
+# --------------------------------------------------------------------------
+def gnn_param_count(H: int, T: int) -> int:
+    return 5 * H + T * (5 * H * H + 2 * H) + H * H + 2 * H + 1
+
+
+def gnn_params(H: int = 64, T: int = 2, seed: int = 0, out_scale: float = 0.1,
+               bias_scale: float = 0.1) -> np.ndarray:
+    """Flat FP32 weights in the library's layout (W_enc, b_enc, u, T x {A, a,
+    B, b}, D, d, w, c): matrices N(0, 1/fan_in), biases and u
+    N(0, bias_scale^2), the read-out w N(0, out_scale^2 / H) so that
+    energies are of order out_scale per atom."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = lambda n, s: rng.normal(0.0, s, size=n)
+    parts = [g(3 * H, 1.0 / math.sqrt(3.0)), g(H, bias_scale), g(H, 1.0)]
+    for _ in range(T):
+        parts += [g(3 * H * H, 1.0 / math.sqrt(3 * H)), g(H, bias_scale), g(2 * H * H, 1.0 / math.sqrt(2 * H)),
+                  g(H, bias_scale)]
+    parts += [g(H * H, 1.0 / math.sqrt(H)), g(H, bias_scale), g(H, out_scale / math.sqrt(H)), np.zeros(1)]
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.shape[0] == gnn_param_count(H, T)
+    return p
