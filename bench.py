@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-fire", action="store_true", help="skip the FIRE minimisation section")
     ap.add_argument("--no-nhc", action="store_true", help="skip the Nose-Hoover NVT section")
     ap.add_argument("--no-flock", action="store_true", help="skip the flocking section")
+    ap.add_argument("--no-gnn", action="store_true", help="skip the graph-network potential section")
     return ap.parse_args()
 
 
@@ -382,6 +383,60 @@ def nhc_section(steps=200):
     return out
 
 
+def gnn_section(steps=100, H=64, T=2):
+    """Graph-network potential deployed in Nose-Hoover NVT: silicon, N =
+    64,000 atoms at 1000 K (dt = 1 fs, r_c = 3.77 A, hidden width H, T
+    message-passing steps, seeded random weights), `steps` steps in one graph
+    launch; and one energy + force evaluation timed alone."""
+    import torch
+    import paper_1912_04232_b300 as P
+    import paper_1912_04232_b300.learned as LP
+    import workloads as W
+    dev = torch.device("cuda")
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    si = W.sw_silicon(20, T_K=1000.0, seed=0)
+    N, cap, rc = si.N, 48, 3.77
+    s = P.md_space_periodic(3, [si.L] * 3)
+    nl = P.NeighborList(s, N, rc, 0.5, cap)
+    params = torch.from_numpy(W.gnn_params(H, T, seed=0, out_scale=0.3)).to(dev)
+    model = P.GNNModel(params, N, cap, H, T, rc)
+    r0, v0 = torch.from_numpy(si.r).to(dev), torch.from_numpy(si.v).to(dev)
+    r, v, f = torch.empty_like(r0), torch.empty_like(v0), torch.zeros_like(r0)
+    th = torch.zeros(P.md_nhc_state_doubles(3), dtype=torch.float64, device=dev)
+    Hx = torch.zeros(steps, dtype=torch.float64, device=dev)
+    KE = torch.zeros_like(Hx)
+    kT, dt = W.KB_EV * 1000.0, 1.0
+    ts, tf = [], []
+    for k in range(3):
+        r.copy_(r0)
+        v.copy_(v0)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        nl.build(r, st)
+        P.md_energy_forces(s, model.pot, r, nl.plan, f, None, st)
+        e1.record()
+        P.md_integrate_nhc(s, model.pot, r, v, f, LP.MASS_SI, dt, kT, 100.0 * dt, 3, steps, nl.plan, th, True, None,
+                           KE, Hx, True, st)
+        e2.record()
+        e2.synchronize()
+        if k:
+            ts.append(e1.elapsed_time(e2))
+    # one evaluation alone (list already built)
+    for k in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.md_energy_forces(s, model.pot, r, nl.plan, f, None, st)
+        e1.record()
+        e1.synchronize()
+        if k >= 2:
+            tf.append(e0.elapsed_time(e1))
+    Hn = Hx.cpu().numpy()
+    return {"N": N, "H": H, "T": T, "steps": steps, "ms": min(ts), "atom_steps_per_s": N * steps / (min(ts) * 1e-3),
+            "force_eval_ms": min(tf), "max_abs_dH_per_atom": float(np.abs(Hn - Hn[0]).max() / N),
+            "T_end_over_T": float(KE[-1].item() / (1.5 * N * kT)), "weights": "seeded random (out_scale 0.3)",
+            "status": P.md_status_poll(st)}
+
+
 def flock_section(N=100000, steps=200, n_pred=8):
     """Flocking energy model: N boids with ~20 neighbours within the
     alignment range, 16 disk obstacles and n_pred predators, `steps`
@@ -608,6 +663,8 @@ def main():
         extra["nvt_nose_hoover"] = nhc_section()
     if rank == 0 and not args.no_flock:
         extra["flocking"] = flock_section()
+    if rank == 0 and not args.no_gnn:
+        extra["gnn_nvt"] = gnn_section()
 
     if rank == 0:
         line = {

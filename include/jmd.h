@@ -187,7 +187,7 @@ JMD_API md_status md_nbr_stats(const md_nbr *nb, int64_t *builds, int32_t *max_c
 /* Energy functions (Sec. 3.3.2) summed over the neighbor list (smap.neighbors,
  * Sec. 3.2.2): U = 1/2 sum_{i != j} u(r_ij), F = -grad U.                   */
 /* ------------------------------------------------------------------------ */
-typedef enum { MD_LJ = 0, MD_SOFT_SPHERE = 1, MD_SW = 2, MD_BP = 3 } md_potential;
+typedef enum { MD_LJ = 0, MD_SOFT_SPHERE = 1, MD_SW = 2, MD_BP = 3, MD_GNN = 4 } md_potential;
 
 typedef struct {
     md_potential kind;
@@ -199,7 +199,7 @@ typedef struct {
     float alpha;
     /* MD_SW: {eps, sigma, a, lambda, gamma, A, B, p, q, cos0}; cutoff a*sigma. */
     float sw[10];
-    /* MD_BP: pointer to a learned-potential model descriptor. */
+    /* MD_BP: pointer to an md_bp_model; MD_GNN: pointer to an md_gnn_model. */
     const void *model;
 } md_pot;
 
@@ -215,6 +215,43 @@ typedef struct {
     float *Ei;            /* [N] scratch: per-atom energies */
     int sys_n;            /* 0, or atoms per system for concatenated equal-size systems */
 } md_bp_model;
+
+/* Graph-network potential (MD_GNN; Sec. 3.2.4: GraphNet blocks as in the
+ * glass network of Bapst et al.; Sec. 4.1: trained on energies and forces,
+ * not rotation invariant).  The paper prints no architecture; this one is
+ * encode - process - decode with hidden width H and T message-passing steps
+ * on the directed edges (i <- j), r_ij < r_cut, of a 3-D neighbor list:
+ *   e_ij = silu(W_enc x_ij + b_enc),  x_ij = (R_j - R_i) / r_cut;  v_i = u
+ *   step t = 1..T:  e_ij = silu(A_e e_ij + A_r v_i + A_s v_j + a)
+ *                   m_i  = sum_j s(r_ij) e_ij,  s(r) = (cos(pi r / r_cut) + 1) / 2
+ *                   v_i  = silu(B_v v_i + B_m m_i + b)
+ *   E_i = w . silu(D v_i + d) + c,  E = sum_i E_i,  F = -dE/dR  (FP32).
+ * params (device, md_gnn_param_count(H, T) floats, row-major blocks):
+ *   W_enc [H][3], b_enc [H], u [H],
+ *   T x { A [H][3H] (columns A_e | A_r | A_s), a [H], B [H][2H] (B_v | B_m), b [H] },
+ *   D [H][H], d [H], w [H], c.
+ * ws: device scratch of md_gnn_workspace_bytes(N, cap, H, T) bytes for the
+ * list the model is evaluated on (caller-owned; contents are scratch).
+ * Needs H in {32, 64}, 1 <= T <= 4, r_cut <= the list's r_list, cap <= 64
+ * and a symmetric list (every pair in both rows; a missing reverse entry
+ * raises MD_ERR_NBR_OVERFLOW).  md_energy_forces writes F and E_i to
+ * d_f [N][4]. */
+typedef struct {
+    const float *params;
+    int H, T;
+    float r_cut;
+    void *ws;
+    size_t ws_bytes;
+} md_gnn_model;
+
+/* Parameter count 5H + T (5H^2 + 2H) + H^2 + 2H + 1; 0 for unsupported H, T. */
+JMD_API size_t md_gnn_param_count(int H, int T);
+/* Atoms per warp of the network kernels (1, 2, 4 or 8; default 4): more
+ * atoms share each weight read, fewer warps hide latency.  The forces do
+ * not depend on it.  MD_ERR_INVALID for other values. */
+JMD_API md_status md_gnn_set_group(int G);
+/* Workspace bytes for N atoms and row capacity cap; 0 if unsupported. */
+JMD_API size_t md_gnn_workspace_bytes(int N, int cap, int H, int T);
 
 /* Forces and per-particle energies into d_f [N][4]; if d_E != NULL the FP64
  * total energy sum_i e_i is written to *d_E (device).  Needs a built list

@@ -534,7 +534,8 @@ static md_status run_dynamics(const md_space *s, const md_pot *p, float *d_r, fl
 {
     if (!s || !p || !d_r || !d_v || !d_f || !nb || nsteps < 0 || !(mass > 0.0f)) return MD_ERR_INVALID;
     if (s->dim != nb->dim || !nb->ws || !nb->rref) return MD_ERR_INVALID;
-    if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE && p->kind != MD_SW && p->kind != MD_BP) return MD_ERR_INVALID;
+    if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE && p->kind != MD_SW && p->kind != MD_BP && p->kind != MD_GNN)
+        return MD_ERR_INVALID;
     if (langevin && (s->dim != 3 || !(gamma >= 0.0f) || !(kT >= 0.0f))) return MD_ERR_INVALID;
     NveCtx c;
     memset(&c, 0, sizeof(c));   // the graph cache compares contexts bytewise

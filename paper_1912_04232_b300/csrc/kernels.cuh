@@ -51,6 +51,9 @@ struct PairArgs {
     const float *bp_params, *bp_norm;
     float *bp_G, *bp_dEdG, *bp_Ei;
     int bp_sys_n;
+    // graph-network potential: the model descriptor by value (so a cached
+    // graph's key covers its device pointers)
+    md_gnn_model gnn;
     // cell-centred path (lists with local rows): 16-bit rows and the cell list
     const uint16_t *lrow;
     const int32_t *atoms, *cell_start;
@@ -99,6 +102,8 @@ void enqueue_pair(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st
 void enqueue_forces(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st);
 void enqueue_sw(const PairArgs &a, int kick, cudaStream_t st);
 void enqueue_bp_step(const PairArgs &a, int kick, cudaStream_t st);
+void enqueue_gnn_step(const PairArgs &a, int kick, cudaStream_t st);
+bool gnn_model_ok(const md_gnn_model *m, const md_nbr *nb);
 int pair_blocks(int N, int tpp);
 // r += eta F (unwrapped) with the displacement check (gradient descent step)
 void enqueue_gd_step(const md_space *s, float *d_r, const float *d_f, const md_nbr *nb, float eta, cudaStream_t st);

@@ -432,6 +432,7 @@ void enqueue_forces(const PairArgs &a, int dim, int pot, int kick, cudaStream_t 
 {
     if (pot == MD_SW) enqueue_sw(a, kick, st);
     else if (pot == MD_BP) enqueue_bp_step(a, kick, st);
+    else if (pot == MD_GNN) enqueue_gnn_step(a, kick, st);
     else enqueue_pair(a, dim, pot, kick, st);
 }
 
@@ -440,8 +441,9 @@ static int g_tpp = 4;
 bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const md_nbr *nb, float *d_f, PairArgs &a)
 {
     if (!s || !p || !d_r || !nb || !d_f || !nb->nbr || !nb->cnt || !nb->ws || !nbr_layout_ok(nb)) return false;
-    if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE && p->kind != MD_SW && p->kind != MD_BP) return false;
-    if ((p->kind == MD_SW || p->kind == MD_BP) && s->dim != 3) return false;
+    if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE && p->kind != MD_SW && p->kind != MD_BP && p->kind != MD_GNN)
+        return false;
+    if ((p->kind == MD_SW || p->kind == MD_BP || p->kind == MD_GNN) && s->dim != 3) return false;
     memset(&a, 0, sizeof(a));
     a.box = make_box(s);
     a.N = nb->N;
@@ -473,6 +475,10 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
     } else if (p->kind == MD_SOFT_SPHERE) {
         a.eps = p->eps;
         a.alpha = p->alpha;
+    } else if (p->kind == MD_GNN) {
+        const md_gnn_model *m = (const md_gnn_model *)p->model;
+        if (!gnn_model_ok(m, nb) || (size_t)nb->N * nb->cap >= (size_t)INT32_MAX) return false;
+        a.gnn = *m;
     } else if (p->kind == MD_BP) {
         const md_bp_model *m = (const md_bp_model *)p->model;
         if (!m || !m->params || !m->norm || !m->G || !m->dEdG || !m->Ei) return false;

@@ -31,7 +31,7 @@ MD_ERR_TIMEOUT = 16
 MD_ERR_BOUNDS = 32
 MD_ERR_CUDA = 64
 
-MD_LJ, MD_SOFT_SPHERE, MD_SW, MD_BP = 0, 1, 2, 3
+MD_LJ, MD_SOFT_SPHERE, MD_SW, MD_BP, MD_GNN = 0, 1, 2, 3, 4
 MD_NBR_CANONICAL = 1
 MD_NBR_LOCAL_ROWS = 2
 
@@ -67,6 +67,11 @@ class md_pot(C.Structure):
 class md_bp_model(C.Structure):
     _fields_ = [("params", C.c_void_p), ("norm", C.c_void_p), ("G", C.c_void_p), ("dEdG", C.c_void_p),
                 ("Ei", C.c_void_p), ("sys_n", C.c_int)]
+
+
+class md_gnn_model(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("H", C.c_int), ("T", C.c_int), ("r_cut", C.c_float), ("ws", C.c_void_p),
+                ("ws_bytes", C.c_size_t)]
 
 
 class md_fire_params(C.Structure):
@@ -139,6 +144,7 @@ _SIGS = {
     "md_bp_mlp_infer": [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp],
     "md_bp_mlp_infer_tc": [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp],
     "md_bp_set_tensor_cores": [C.c_int],
+    "md_gnn_set_group": [C.c_int],
     "md_bp_forces": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
     "md_bp_jvp": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp, _vp],
     "md_bp_mlp_train": [_vp, _vp, _vp, _vp, _vp, C.c_float, C.c_int, _vp, _vp, _vp],
@@ -175,6 +181,10 @@ _lib.md_fire_state_bytes.restype = C.c_size_t
 _lib.md_fire_state_bytes.argtypes = []
 _lib.md_nhc_state_doubles.restype = C.c_size_t
 _lib.md_nhc_state_doubles.argtypes = [C.c_int]
+_lib.md_gnn_param_count.restype = C.c_size_t
+_lib.md_gnn_param_count.argtypes = [C.c_int, C.c_int]
+_lib.md_gnn_workspace_bytes.restype = C.c_size_t
+_lib.md_gnn_workspace_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
 _lib.md_version.restype = C.c_char_p
 _lib.md_version.argtypes = []
 
@@ -410,6 +420,40 @@ class BPModel:
                                  _ptr(self.Ei).value, int(sys_n))
         self.pot = md_pot()
         self.pot.kind = MD_BP
+        self.pot.model = C.cast(C.pointer(self.model), C.c_void_p)
+
+
+def md_gnn_param_count(H, T):
+    return int(_lib.md_gnn_param_count(int(H), int(T)))
+
+
+def md_gnn_set_group(G):
+    _check(_lib.md_gnn_set_group(int(G)), "md_gnn_set_group")
+
+
+def md_gnn_workspace_bytes(N, cap, H, T):
+    return int(_lib.md_gnn_workspace_bytes(int(N), int(cap), int(H), int(T)))
+
+
+class GNNModel:
+    """Workspace of the graph-network potential for a list of N atoms with
+    row capacity cap, and the md_pot that points at the model (kind
+    MD_GNN).  params: FP32 CUDA tensor of md_gnn_param_count(H, T) floats,
+    owned by the caller."""
+
+    def __init__(self, params, N, cap, H=64, T=2, r_cut=3.77, device="cuda"):
+        import torch
+        n = md_gnn_param_count(H, T)
+        if n == 0 or params.numel() != n:
+            raise MDError(MD_ERR_INVALID, "GNNModel: parameter count")
+        nbytes = md_gnn_workspace_bytes(N, cap, H, T)
+        if nbytes == 0:
+            raise MDError(MD_ERR_INVALID, "GNNModel: unsupported N, cap, H or T")
+        self.params = params
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.model = md_gnn_model(_ptr(params).value, int(H), int(T), float(r_cut), _ptr(self.ws).value, nbytes)
+        self.pot = md_pot()
+        self.pot.kind = MD_GNN
         self.pot.model = C.cast(C.pointer(self.model), C.c_void_p)
 
 
