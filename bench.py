@@ -431,8 +431,25 @@ def gnn_section(steps=100, H=64, T=2):
         if k >= 2:
             tf.append(e0.elapsed_time(e1))
     Hn = Hx.cpu().numpy()
+    # algorithmic FLOPs of one evaluation (the matrix products; element-wise
+    # work not counted): edges 2H^2 E (2T products per edge: A_e forward per
+    # step, A_e^T of the step above and of step 0 in reverse), nodes 2H^2 N
+    # (8T - 3 products: B, A_r, A_s, D forward; D^T, B^T, A_r^T, A_s^T reverse)
+    n = nl.cnt.clamp(max=cap).long()
+    rows = nl.nbr.long().clamp(max=N - 1)
+    d = r[rows, :3] - r[:, None, :3]
+    d -= float(si.L) * torch.round(d / float(si.L))
+    valid = (torch.arange(cap, device=dev)[None, :] < n[:, None]) & ((d * d).sum(-1) < rc * rc)
+    E_edges = int(valid.sum().item())
+    flops = 2.0 * H * H * (E_edges * 2 * T + N * (8 * T - 3))
+    fp32_peak = 148 * 128 * 2 * 2032e6 / 1e12   # FP32 FMA lanes x 2 x max SM clock
+    tflops = flops / (min(tf) * 1e-3) / 1e12
     return {"N": N, "H": H, "T": T, "steps": steps, "ms": min(ts), "atom_steps_per_s": N * steps / (min(ts) * 1e-3),
-            "force_eval_ms": min(tf), "max_abs_dH_per_atom": float(np.abs(Hn - Hn[0]).max() / N),
+            "force_eval_ms": min(tf), "edges_within_rc_per_atom": E_edges / N,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": tflops / fp32_peak, "flops_per_eval": flops,
+                         "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz"},
+            "group": 4, "max_abs_dH_per_atom": float(np.abs(Hn - Hn[0]).max() / N),
             "T_end_over_T": float(KE[-1].item() / (1.5 * N * kT)), "weights": "seeded random (out_scale 0.3)",
             "status": P.md_status_poll(st)}
 

@@ -492,6 +492,24 @@ JMD_API md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_nbr
                                       float D, float dB, float Lp, float eta, int T, int K, float *d_r, float *d_f,
                                       void *d_ws, double *d_out, uint32_t *d_status, md_stream_t stream);
 
+/* FIRE instead of gradient descent (Sec. 3.3.1 minimiser; Bitzek et al.,
+ * PRL 97, 170201 (2006)): r_0 = L s_0 from rest, T FIRE steps with the
+ * parameters fp, E = U(r_T) and dE/dD by hand-written reverse mode through
+ * every step (velocity Verlet, the global norms of the mixing, the forces
+ * via Hessian-vector products, the box and the diameters), with the time
+ * steps, mixing factors and P > 0 decisions of the trajectory held fixed
+ * (the map is piecewise smooth).  States (r, v and the FIRE scalars) are
+ * kept every K steps and each segment is replayed bit for bit in the
+ * reverse sweep; nb as for md_minimize_adjoint (canonical), so the result
+ * is identical for every K.  d_ws: md_fire_adjoint_workspace_size(N, T, K)
+ * bytes, 256-byte aligned.  d_r, d_v, d_f receive r_T, v_T, F(r_T);
+ * d_out[0] = E, d_out[1] = dE/dD (FP64). */
+JMD_API size_t md_fire_adjoint_workspace_size(int N, int T, int K);
+JMD_API md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p, const md_fire_params *fp,
+                                           md_nbr *nb, const float *d_s0, int nA, float D, float dB, float Lp,
+                                           int T, int K, float *d_r, float *d_v, float *d_f, void *d_ws,
+                                           double *d_out, uint32_t *d_status, md_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batched replicas (the paper's vmap over independent systems, Sec. 4.2):   */
 /* replicas of different size, box, density and potential (LJ or soft        */

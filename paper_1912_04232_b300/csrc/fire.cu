@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) k_fire_drift(float4 *r, float4 *v, const 
 
 template <int DIM>
 __global__ void __launch_bounds__(256) k_fire_power(float4 *v, const float4 *f, int N, FireHdr *h, md_fire_params fp,
-                                                    uint32_t *status)
+                                                    uint32_t *status, FireStep *rec)
 {
     count_launch();
     __shared__ double sh[3][8];
@@ -125,6 +125,12 @@ __global__ void __launch_bounds__(256) k_fire_power(float4 *v, const float4 *f, 
     h->ff = S[2];
     h->keep = (float)(1.0 - alpha);
     h->scale = S[2] > 0.0 ? (float)(alpha * sqrt(S[1]) / sqrt(S[2])) : 0.0f;
+    if (rec) {   // what this step used: its time step, mixing and decision
+        rec->dt = (float)h->dt;
+        rec->alpha = (float)alpha;
+        rec->keep = h->keep;
+        rec->freeze = S[0] > 0.0 ? 0 : 1;
+    }
     if (S[0] > 0.0) {
         h->freeze = 0;
         h->npos += 1;
@@ -165,6 +171,73 @@ using namespace jmd;
 
 extern "C" size_t md_fire_state_bytes(void) { return fire_state_bytes(); }
 
+namespace jmd {
+
+md_status fire_params_ok(const md_fire_params *fp)
+{
+    if (!(fp->dt_start > 0.f) || !(fp->dt_max >= fp->dt_start) || !(fp->f_inc >= 1.f) || !(fp->f_dec > 0.f) ||
+        !(fp->f_dec < 1.f) || !(fp->alpha_start >= 0.f) || !(fp->alpha_start < 1.f) || !(fp->f_alpha > 0.f) ||
+        !(fp->f_alpha <= 1.f) || fp->n_min < 0)
+        return MD_ERR_INVALID;
+    return MD_OK;
+}
+
+void enqueue_fire_init(void *state, const md_fire_params &fp, cudaStream_t st)
+{
+    k_fire_init<<<1, 1, 0, st>>>((FireHdr *)state, fp);
+}
+
+// One FIRE step: drift, rebuild (gated, or under an IF node), forces,
+// power and rules (recorded into rec when given), mixing.
+md_status enqueue_fire_step(const FireCtx &c, FireStep *rec, cudaStream_t cs, LoopBuilder *lb)
+{
+    FireHdr *h = (FireHdr *)c.state;
+    const int g = (c.N + 255) / 256, gp = g < FIRE_BLOCKS ? g : FIRE_BLOCKS;
+    if (c.dim == 3) k_fire_drift<3><<<g, 256, 0, cs>>>(c.r, c.v, c.f, c.rref, c.N, h, c.box, c.hs2, c.ctl);
+    else k_fire_drift<2><<<g, 256, 0, cs>>>(c.r, c.v, c.f, c.rref, c.N, h, c.box, c.hs2, c.ctl);
+    if (lb) {
+        md_status e = lb->rebuild_if(c.na, c.ncell);
+        if (e != MD_OK) return e;
+    } else {
+        enqueue_rebuild_chain(c.na, c.ncell, cs);
+    }
+    enqueue_pair(c.pa, c.dim, c.kind, 0, cs);
+    if (c.dim == 3) {
+        k_fire_power<3><<<gp, 256, 0, cs>>>(c.v, c.f, c.N, h, c.prm, c.status, rec);
+        k_fire_mix<3><<<g, 256, 0, cs>>>(c.v, c.f, c.N, h);
+    } else {
+        k_fire_power<2><<<gp, 256, 0, cs>>>(c.v, c.f, c.N, h, c.prm, c.status, rec);
+        k_fire_mix<2><<<g, 256, 0, cs>>>(c.v, c.f, c.N, h);
+    }
+    return MD_OK;
+}
+
+bool make_fire_ctx(const md_space *s, const md_pot *p, const md_fire_params *fp, float *d_r, float *d_v, float *d_f,
+                   md_nbr *nb, void *d_state, uint32_t *d_status, FireCtx &c)
+{
+    if (!make_pair_args(s, p, d_r, nb, d_f, c.pa)) return false;
+    c.pa.status = d_status;
+    c.na = make_nbr_args(s, d_r, nb, d_status, 1);
+    WsPtrs w = ws_ptrs(nb);
+    c.ctl = w.ctl;
+    c.state = d_state;
+    c.box = make_box(s);
+    c.N = nb->N;
+    c.dim = s->dim;
+    c.kind = p->kind;
+    c.r = (float4 *)d_r;
+    c.v = (float4 *)d_v;
+    c.f = (float4 *)d_f;
+    c.rref = (const float4 *)nb->rref;
+    c.hs2 = nb->half_skin2;
+    c.ncell = nb->ncell_total;
+    c.prm = *fp;
+    c.status = d_status;
+    return true;
+}
+
+}  // namespace jmd
+
 extern "C" md_status md_minimize_fire(const md_space *s, const md_pot *p, const md_fire_params *fp, int nsteps,
                                       float *d_r, float *d_v, float *d_f, md_nbr *nb, void *d_state, int restart,
                                       double *d_E, uint32_t *d_status, md_stream_t stream)
@@ -173,86 +246,32 @@ extern "C" md_status md_minimize_fire(const md_space *s, const md_pot *p, const 
     if ((uintptr_t)d_state & 255u) return MD_ERR_INVALID;
     if (s->dim != nb->dim || !nb->ws || !nb->rref) return MD_ERR_INVALID;
     if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE) return MD_ERR_INVALID;
-    if (!(fp->dt_start > 0.f) || !(fp->dt_max >= fp->dt_start) || !(fp->f_inc >= 1.f) || !(fp->f_dec > 0.f) ||
-        !(fp->f_dec < 1.f) || !(fp->alpha_start >= 0.f) || !(fp->alpha_start < 1.f) || !(fp->f_alpha > 0.f) ||
-        !(fp->f_alpha <= 1.f) || fp->n_min < 0)
-        return MD_ERR_INVALID;
+    if (fire_params_ok(fp) != MD_OK) return MD_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
-    PairArgs pa;
-    if (!make_pair_args(s, p, d_r, nb, d_f, pa)) return MD_ERR_INVALID;
-    pa.E_out = d_E;
-    pa.series = d_E ? 1 : 0;
-    pa.status = d_status;
-    NbrArgs na = make_nbr_args(s, d_r, nb, d_status, 1);
-    WsPtrs w = ws_ptrs(nb);
-    FireHdr *h = (FireHdr *)d_state;
-    const Box box = make_box(s);
-    const int N = nb->N, g = (N + 255) / 256;
-    const int gp = g < FIRE_BLOCKS ? g : FIRE_BLOCKS;
-    float4 *r = (float4 *)d_r, *v = (float4 *)d_v, *f = (float4 *)d_f;
-    enqueue_loop_init(w.ctl, (uint32_t)(nsteps + 1), st);
+    FireCtx c;
+    if (!make_fire_ctx(s, p, fp, d_r, d_v, d_f, nb, d_state, d_status, c)) return MD_ERR_INVALID;
+    c.pa.E_out = d_E;
+    c.pa.series = d_E ? 1 : 0;
+    const int N = c.N;
+    enqueue_loop_init(c.ctl, (uint32_t)(nsteps + 1), st);
     if (restart) {
         JMD_CUDA_TRY(cudaMemsetAsync(d_v, 0, sizeof(float4) * (size_t)N, st));
-        k_fire_init<<<1, 1, 0, st>>>(h, *fp);
+        enqueue_fire_init(d_state, *fp, st);
     }
-    enqueue_pair(pa, s->dim, p->kind, 0, st);
-    const int dim = s->dim, kind = p->kind;
-    const float4 *rref = (const float4 *)nb->rref;
-    const float hs2 = nb->half_skin2;
-    const int ncell = nb->ncell_total;
-    const md_fire_params prm = *fp;
-    // one step: drift, rebuild (gated, or under an IF node), forces, power, mixing
-    auto step = [&](cudaStream_t cs, LoopBuilder *lb) -> md_status {
-        if (dim == 3) k_fire_drift<3><<<g, 256, 0, cs>>>(r, v, f, rref, N, h, box, hs2, w.ctl);
-        else k_fire_drift<2><<<g, 256, 0, cs>>>(r, v, f, rref, N, h, box, hs2, w.ctl);
-        if (lb) {
-            md_status e = lb->rebuild_if(na, ncell);
-            if (e != MD_OK) return e;
-        } else {
-            enqueue_rebuild_chain(na, ncell, cs);
-        }
-        enqueue_pair(pa, dim, kind, 0, cs);
-        if (dim == 3) {
-            k_fire_power<3><<<gp, 256, 0, cs>>>(v, f, N, h, prm, d_status);
-            k_fire_mix<3><<<g, 256, 0, cs>>>(v, f, N, h);
-        } else {
-            k_fire_power<2><<<gp, 256, 0, cs>>>(v, f, N, h, prm, d_status);
-            k_fire_mix<2><<<g, 256, 0, cs>>>(v, f, N, h);
-        }
-        return MD_OK;
-    };
+    enqueue_pair(c.pa, c.dim, c.kind, 0, st);
     if (g_loop_graphs) {
         struct Key {
-            int tag, dim, kind, N;
-            PairArgs pa;
-            NbrArgs na;
-            const void *r, *v, *f, *h, *rref;
-            md_fire_params prm;
-            Box box;
-            float hs2;
-            uint32_t *status;
+            int tag;
+            FireCtx c;
         } key;
         memset(&key, 0, sizeof(key));
         key.tag = 0x46495245;   // FIRE
-        key.dim = dim;
-        key.kind = kind;
-        key.N = N;
-        key.pa = pa;
-        key.na = na;
-        key.r = r;
-        key.v = v;
-        key.f = f;
-        key.h = h;
-        key.rref = rref;
-        key.prm = prm;
-        key.box = box;
-        key.hs2 = hs2;
-        key.status = d_status;
-        md_status e = run_graph_loop(&key, sizeof(key), w.ctl, nsteps,
-                                     [&](LoopBuilder &lb) { return step(lb.cs, &lb); }, st);
+        key.c = c;
+        md_status e = run_graph_loop(&key, sizeof(key), c.ctl, nsteps,
+                                     [&](LoopBuilder &lb) { return enqueue_fire_step(c, nullptr, lb.cs, &lb); }, st);
         if (e != MD_OK) return e;
     } else {
-        for (int t = 0; t < nsteps; ++t) step(st, nullptr);
+        for (int t = 0; t < nsteps; ++t) enqueue_fire_step(c, nullptr, st, nullptr);
     }
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;

@@ -37,7 +37,6 @@
 
 namespace jmd {
 
-constexpr int GNN_GMAX = 8;  // atoms per warp: 1, 2, 4 or 8 (md_gnn_set_group)
 // warps per block for a group size (shared memory: weights + per-warp buffers)
 __host__ __device__ constexpr int gnn_warps(int G) { return G >= 8 ? 12 : 16; }
 constexpr int GNN_EB = 8;    // edges per batch

@@ -88,6 +88,30 @@ struct LoopBuilder {
 };
 md_status run_graph_loop(const void *key, size_t key_bytes, uint32_t *ctl, int niter,
                          const std::function<md_status(LoopBuilder &)> &body, cudaStream_t st);
+// FIRE (fire.cu): one step's launches, and what the rules of a step used
+// (recorded for the reverse pass of the FIRE adjoint).
+struct FireStep {
+    float dt, alpha, keep;
+    int freeze;
+};
+struct FireCtx {
+    PairArgs pa;
+    NbrArgs na;
+    uint32_t *ctl;
+    void *state;
+    Box box;
+    int N, dim, kind, ncell;
+    float4 *r, *v, *f;
+    const float4 *rref;
+    float hs2;
+    md_fire_params prm;
+    uint32_t *status;
+};
+md_status fire_params_ok(const md_fire_params *fp);
+bool make_fire_ctx(const md_space *s, const md_pot *p, const md_fire_params *fp, float *d_r, float *d_v, float *d_f,
+                   md_nbr *nb, void *d_state, uint32_t *d_status, FireCtx &c);
+void enqueue_fire_init(void *state, const md_fire_params &fp, cudaStream_t st);
+md_status enqueue_fire_step(const FireCtx &c, FireStep *rec, cudaStream_t cs, LoopBuilder *lb);
 // 1 (default): FIRE and flocking loops run as graph loops; 0: host launches.
 extern int g_loop_graphs;
 void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st);

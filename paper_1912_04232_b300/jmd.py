@@ -160,6 +160,8 @@ _SIGS = {
     "md_batch_autotune": [_P(md_batch), _vp, _vp, _vp, _vp, C.c_int, C.c_char_p, _P(C.c_int), _vp],
     "md_minimize_adjoint": [_P(md_space), _P(md_pot), _P(md_nbr), _vp, C.c_int, C.c_float, C.c_float, C.c_float,
                             C.c_float, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
+    "md_minimize_fire_adjoint": [_P(md_space), _P(md_pot), _P(md_fire_params), _P(md_nbr), _vp, C.c_int, C.c_float,
+                                 C.c_float, C.c_float, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "md_neighbor_list_build_noalloc": [_P(md_space), _vp, C.c_int, C.c_float, C.c_float, C.c_int, _vp, _vp, _vp,
                                        _vp],
 }
@@ -175,6 +177,8 @@ _lib.md_batch_free.restype = None
 _lib.md_batch_free.argtypes = [_P(md_batch)]
 _lib.md_adjoint_workspace_size.restype = C.c_size_t
 _lib.md_adjoint_workspace_size.argtypes = [C.c_int, C.c_int, C.c_int]
+_lib.md_fire_adjoint_workspace_size.restype = C.c_size_t
+_lib.md_fire_adjoint_workspace_size.argtypes = [C.c_int, C.c_int, C.c_int]
 _lib.md_noalloc_scratch_bytes.restype = C.c_size_t
 _lib.md_noalloc_scratch_bytes.argtypes = []
 _lib.md_fire_state_bytes.restype = C.c_size_t
@@ -533,6 +537,18 @@ def md_minimize_adjoint(space, pot, nb, s0, nA, D, dB, Lp, eta, T, K, r, f, ws, 
     _check(_lib.md_minimize_adjoint(C.byref(space), C.byref(pot), C.byref(nb), _ptr(s0), int(nA), float(D),
                                     float(dB), float(Lp), float(eta), int(T), int(K), _ptr(r), _ptr(f), _ptr(ws),
                                     _ptr(out), _ptr(status), _stream(stream)), "md_minimize_adjoint")
+
+
+def md_fire_adjoint_workspace_size(N, T, K) -> int:
+    return int(_lib.md_fire_adjoint_workspace_size(int(N), int(T), int(K)))
+
+
+def md_minimize_fire_adjoint(space, pot, fire, nb, s0, nA, D, dB, Lp, T, K, r, v, f, ws, out, status=None,
+                             stream=None):
+    _check(_lib.md_minimize_fire_adjoint(C.byref(space), C.byref(pot), C.byref(fire), C.byref(nb), _ptr(s0), int(nA),
+                                         float(D), float(dB), float(Lp), int(T), int(K), _ptr(r), _ptr(v), _ptr(f),
+                                         _ptr(ws), _ptr(out), _ptr(status), _stream(stream)),
+           "md_minimize_fire_adjoint")
 
 
 def md_status_poll(status, stream=None) -> int:
