@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -328,6 +329,30 @@ def fire_section():
     ms2, E2, fs2 = run(s2, P.soft_pot(), P.fire_params(), torch.from_numpy(x).to(dev), 1.4, 300, 5)
     out["app_a_packing"] = {"N": pk.N, "steps": 300, "ms": ms2, "us_per_step": 1e3 * ms2 / 300,
                             "E_start": float(E2[0]), "E_end": float(E2[-1])}
+    # dE_final/dD through the 300 FIRE steps (reverse mode, K = 18)
+    L64 = W.packing_box(pk.N, pk.D, pk.phi)
+    Lp = (pk.N // 2) * math.pi * pk.D / (4 * pk.phi * L64)
+    nlc = P.NeighborList(s2, pk.N, 1.4, 0.3, 64, canonical=True)
+    s0 = torch.zeros((pk.N, 4), dtype=torch.float32, device=dev)
+    s0[:, :2] = torch.from_numpy(pk.s0.astype(np.float32)).to(dev)
+    ra, va, fa = (torch.zeros((pk.N, 4), dtype=torch.float32, device=dev) for _ in range(3))
+    wsz = P.md_fire_adjoint_workspace_size(pk.N, 300, 18)
+    wsb = torch.empty(wsz + 256, dtype=torch.uint8, device=dev)
+    wsv = wsb[(-wsb.data_ptr()) % 256:]
+    outd = torch.zeros(2, dtype=torch.float64, device=dev)
+    ta = []
+    for k in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.md_minimize_fire_adjoint(s2, P.soft_pot(), P.fire_params(), nlc.plan, s0, pk.N // 2, pk.D, 1.0, Lp, 300,
+                                   18, ra, va, fa, wsv, outd, st)
+        e1.record()
+        e1.synchronize()
+        if k:
+            ta.append(e0.elapsed_time(e1))
+    o = outd.cpu().numpy()
+    out["app_a_fire_adjoint"] = {"N": pk.N, "steps": 300, "K": 18, "ms": min(ta), "E_final": float(o[0]),
+                                 "dE_dD": float(o[1])}
     code = P.md_status_poll(st)
     out["status"] = code
     return out
