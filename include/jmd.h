@@ -246,6 +246,11 @@ typedef struct {
 
 /* Parameter count 5H + T (5H^2 + 2H) + H^2 + 2H + 1; 0 for unsupported H, T. */
 JMD_API size_t md_gnn_param_count(int H, int T);
+/* 1: the products of md_energy_forces with MD_GNN run on the tensor cores
+ * (tcgen05, BF16 operands, FP32 accumulation; H = 64 only, other widths
+ * keep the FP32 kernels), the edges compacted in receiver order; 0
+ * (default): FP32 CUDA-core kernels.  MD_ERR_INVALID for other values. */
+JMD_API md_status md_gnn_set_tensor_cores(int on);
 /* Atoms per warp of the network kernels (1, 2, 4 or 8; default 4): more
  * atoms share each weight read, fewer warps hide latency.  The forces do
  * not depend on it.  MD_ERR_INVALID for other values. */

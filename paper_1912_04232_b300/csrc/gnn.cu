@@ -32,88 +32,11 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "gnn.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
 
 namespace jmd {
-
-// warps per block for a group size (shared memory: weights + per-warp buffers)
-__host__ __device__ constexpr int gnn_warps(int G) { return G >= 8 ? 12 : 16; }
-constexpr int GNN_EB = 8;    // edges per batch
-constexpr int GNN_MAXT = 4;
-constexpr int GNN_MAXCAP = 64;
-
-struct GnnOff {
-    int Wenc, benc, u, A[GNN_MAXT], a[GNN_MAXT], B[GNN_MAXT], b[GNN_MAXT], D, d, w, c, count;
-};
-
-static GnnOff gnn_offsets(int H, int T)
-{
-    GnnOff o;
-    memset(&o, 0, sizeof(o));
-    int p = 0;
-    o.Wenc = p; p += 3 * H;
-    o.benc = p; p += H;
-    o.u = p;    p += H;
-    for (int t = 0; t < T; ++t) {
-        o.A[t] = p; p += 3 * H * H;
-        o.a[t] = p; p += H;
-        o.B[t] = p; p += 2 * H * H;
-        o.b[t] = p; p += H;
-    }
-    o.D = p; p += H * H;
-    o.d = p; p += H;
-    o.w = p; p += H;
-    o.c = p; p += 1;
-    o.count = p;
-    return o;
-}
-
-struct GnnArgs {
-    Box box;
-    int N, cap, T;
-    float rc, rc2;
-    const float4 *r;
-    const int32_t *nbr, *cnt;
-    const float *P;
-    GnnOff off;
-    int32_t *rev;     // [N*cap] slot of the reverse edge (j*cap + p), -1: no edge
-    float4 *dr;       // [N*cap] R_j - R_i (minimum image), r
-    float2 *cut;      // [N*cap] s(r), s'(r) / r
-    float *gs;        // [N*cap] dE/ds summed over the steps
-    float4 *gpos;     // [N*cap] dE/d(R_j - R_i)
-    float *ze;        // [T][N*cap][H] edge pre-activations; reverse: their gradients
-    float *zv;        // [T][N][H] node pre-activations
-    float *rr, *ps;   // [2][N][H] receiver term A_r v + a and sender term A_s v of the next step
-    float *gvd;       // [N][H] node gradient carried to the step below
-    float *Ei;        // [N]
-    uint32_t *status;
-};
-
-__device__ __forceinline__ float gnn_sig(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
-__device__ __forceinline__ float gnn_silu(float x) { return x * gnn_sig(x); }
-__device__ __forceinline__ float gnn_dsilu(float x)
-{
-    const float s = gnn_sig(x);
-    return s * (1.0f + x * (1.0f - s));
-}
-
-__device__ __forceinline__ float gnn_wsum(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// s(r) and s'(r)/r
-__device__ __forceinline__ void gnn_cut(float r, float rc, float &s, float &dsr)
-{
-    float sn, cs;
-    sincospif(r / rc, &sn, &cs);
-    s = 0.5f * (cs + 1.0f);
-    // s'(r) / r = -pi sin(pi r / r_c) / (2 r_c r); its limit at r = 0 is -pi^2 / (2 r_c^2)
-    dsr = r > 0.0f ? -0.5f * 3.14159265358979f * sn / (rc * r) : -0.5f * 9.8696044010894f / (rc * rc);
-}
 
 // Stage an H x K block of a row-major matrix (rows h, ld columns, first
 // column c0) in shared memory as M[c][h] (forward product W v: lane h reads
@@ -720,31 +643,9 @@ static size_t gnn_smem_bwd(int t)
     return sizeof(float) * ((t == 0 ? 6 : 5) * H * H) + sizeof(GnnWarpSmem<H, G>) * gnn_warps(G);
 }
 
-struct GnnWs {
-    size_t rev, dr, cut, gs, gpos, ze, zv, rr, ps, gvd, Ei, total;
-};
-
-static GnnWs gnn_ws_layout(int N, int cap, int H, int T)
-{
-    GnnWs w;
-    const size_t NE = (size_t)N * cap;
-    size_t o = 0;
-    w.rev = o;  o = align256(o + sizeof(int32_t) * NE);
-    w.dr = o;   o = align256(o + sizeof(float4) * NE);
-    w.cut = o;  o = align256(o + sizeof(float2) * NE);
-    w.gs = o;   o = align256(o + sizeof(float) * NE);
-    w.gpos = o; o = align256(o + sizeof(float4) * NE);
-    w.ze = o;   o = align256(o + sizeof(float) * (size_t)T * NE * H);
-    w.zv = o;   o = align256(o + sizeof(float) * (size_t)T * N * H);
-    w.rr = o;   o = align256(o + sizeof(float) * 2 * (size_t)N * H);
-    w.ps = o;   o = align256(o + sizeof(float) * 2 * (size_t)N * H);
-    w.gvd = o;  o = align256(o + sizeof(float) * (size_t)N * H);
-    w.Ei = o;   o = align256(o + sizeof(float) * (size_t)N);
-    w.total = o;
-    return w;
-}
 
 static int g_gnn_group = 4;   // atoms per warp (md_gnn_set_group)
+static int g_gnn_tc = 0;      // 1: the tensor-core kernels (gnn_tc.cu; H = 64)
 
 static int gnn_sms()
 {
@@ -824,7 +725,23 @@ void enqueue_gnn_step(const PairArgs &pa, int kick, cudaStream_t st)
     g.ps = (float *)(b + L.ps);
     g.gvd = (float *)(b + L.gvd);
     g.Ei = (float *)(b + L.Ei);
+    g.H = m->H;
+    g.nv = (int *)(b + L.nv);
+    g.eoff = (int *)(b + L.off);
+    g.ctot = (int *)(b + L.ctot);
+    g.erecv = (int *)(b + L.erecv);
+    g.esend = (int *)(b + L.esend);
+    g.erev = (int *)(b + L.erev);
+    g.eslot = (int *)(b + L.eslot);
+    g.cidx = (int *)(b + L.cidx);
+    g.edr = (float4 *)(b + L.edr);
+    g.ecut = (float2 *)(b + L.ecut);
+    g.gm = (float *)(b + L.gm);
     g.status = pa.status;
+    if (g_gnn_tc && m->H == 64) {
+        enqueue_gnn_tc(g, pa, kick, st);
+        return;
+    }
     if (m->H == 64) gnn_launch_h<64>(g, st);
     else gnn_launch_h<32>(g, st);
     const int fgrid = std::max(1, std::min((pa.N + 7) / 8, pa.max_blocks));
@@ -840,6 +757,13 @@ extern "C" size_t md_gnn_param_count(int H, int T)
 {
     if ((H != 32 && H != 64) || T < 1 || T > GNN_MAXT) return 0;
     return (size_t)gnn_offsets(H, T).count;
+}
+
+extern "C" md_status md_gnn_set_tensor_cores(int on)
+{
+    if (on != 0 && on != 1) return MD_ERR_INVALID;
+    g_gnn_tc = on;
+    return MD_OK;
 }
 
 extern "C" md_status md_gnn_set_group(int G)

@@ -145,6 +145,7 @@ _SIGS = {
     "md_bp_mlp_infer_tc": [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp],
     "md_bp_set_tensor_cores": [C.c_int],
     "md_gnn_set_group": [C.c_int],
+    "md_gnn_set_tensor_cores": [C.c_int],
     "md_bp_forces": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
     "md_bp_jvp": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp, _vp],
     "md_bp_mlp_train": [_vp, _vp, _vp, _vp, _vp, C.c_float, C.c_int, _vp, _vp, _vp],
@@ -429,6 +430,10 @@ class BPModel:
 
 def md_gnn_param_count(H, T):
     return int(_lib.md_gnn_param_count(int(H), int(T)))
+
+
+def md_gnn_set_tensor_cores(on):
+    _check(_lib.md_gnn_set_tensor_cores(int(bool(on))), "md_gnn_set_tensor_cores")
 
 
 def md_gnn_set_group(G):

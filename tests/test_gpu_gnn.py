@@ -171,3 +171,68 @@ def test_group_sizes_bitwise_equal(P):
         P.md_gnn_set_group(4)
     with pytest.raises(P.MDError):
         P.md_gnn_set_group(3)
+
+
+def _readout_norm(p32, H, T):
+    """|w| of the decoder read-out (the block before the final bias c)."""
+    return float(np.linalg.norm(p32[-1 - H:-1]))
+
+
+@pytest.fixture
+def tensor_cores(P):
+    P.md_gnn_set_tensor_cores(True)
+    yield
+    P.md_gnn_set_tensor_cores(False)
+
+
+@pytest.mark.parametrize("T,n_side,vac", [(2, 4, 0), (2, 4, 7), (3, 3, 2), (1, 5, 0)])
+def test_tensor_cores_match_oracle(P, tensor_cores, T, n_side, vac):
+    # weights BF16-representable (the model the tensor cores hold exactly),
+    # activations split into two BF16 parts (about 2^-17 relative), FP32
+    # accumulation: the FP32 bar within a factor of a few
+    H = 64
+    r, L = _si(n_side, seed=30 + T, vacancies=vac)
+    p32 = W.gnn_params(H, T, seed=T + 7, out_scale=1.0, bf16=True)
+    f, E = _gpu(P, r, L, p32, H, T)
+    Eo, Eio, Fo = G.energy_forces(r[:, :3].astype(np.float64), float(L), p32.astype(np.float64), H, T, RC)
+    wn = _readout_norm(p32, H, T)
+    ee = np.abs(f[:, 3] - Eio).max() / wn
+    fe = force_error(f, Fo)
+    assert ee <= 2e-5, ee
+    assert abs(E - Eo) <= 2e-5 * wn * r.shape[0]
+    assert fe <= 5e-4, fe
+
+
+def test_tensor_cores_deployment_size(P, tensor_cores):
+    H, T = 64, 2
+    r, L = _si(20, seed=11, jitter=0.15)
+    p32 = W.gnn_params(H, T, seed=0, out_scale=0.1, bf16=True)
+    f, E = _gpu(P, r, L, p32, H, T)
+    P.md_gnn_set_tensor_cores(False)
+    f32, E32 = _gpu(P, r, L, p32, H, T)
+    assert force_error(f, f32) <= 5e-4
+    wn = _readout_norm(p32, H, T)
+    assert np.abs(f[:, 3] - f32[:, 3]).max() <= 2e-5 * wn
+    assert abs(E - E32) <= 2e-5 * wn * r.shape[0]
+    # sampled atoms against the oracle (exact by locality, as above)
+    rng = np.random.Generator(np.random.PCG64(6))
+    for k in rng.choice(r.shape[0], 3, replace=False):
+        idx, x = _cluster(r, L, k, 2 * T * RC + 0.5)
+        _, Ei, F = G.energy_forces(x, 1.0e6, p32.astype(np.float64), H, T, RC)
+        assert np.linalg.norm(f[k, :3] - F[0]) <= 5e-4 * max(np.linalg.norm(F[0]), 1e-2)
+
+
+def test_tensor_cores_unrepresentable_weights_stay_close(P, tensor_cores):
+    # weights that are not BF16-representable are rounded once when staged:
+    # the tensor-core model then differs from the FP32 one by that rounding
+    H, T = 64, 2
+    r, L = _si(4, seed=40, jitter=0.4)
+    p32 = W.gnn_params(H, T, seed=9, out_scale=1.0)
+    f, E = _gpu(P, r, L, p32, H, T)
+    _, Eio, Fo = G.energy_forces(r[:, :3].astype(np.float64), float(L), p32.astype(np.float64), H, T, RC)
+    assert np.abs(f[:, 3] - Eio).max() <= 5e-3 * _readout_norm(p32, H, T)
+    assert force_error(f, Fo) <= 5e-2
+
+
+def test_tensor_cores_nose_hoover_run(P, tensor_cores):
+    test_nose_hoover_run(P)

@@ -305,8 +305,16 @@ def gnn_param_count(H: int, T: int) -> int:
     return 5 * H + T * (5 * H * H + 2 * H) + H * H + 2 * H + 1
 
 
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Round FP32 values to the nearest BF16-representable value (ties to
+    even), returned as FP32."""
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
 def gnn_params(H: int = 64, T: int = 2, seed: int = 0, out_scale: float = 0.1,
-               bias_scale: float = 0.1) -> np.ndarray:
+               bias_scale: float = 0.1, bf16: bool = False) -> np.ndarray:
     """Flat FP32 weights in the library's layout (W_enc, b_enc, u, T x {A, a,
     B, b}, D, d, w, c): matrices N(0, 1/fan_in), biases and u
     N(0, bias_scale^2), the read-out w N(0, out_scale^2 / H) so that
@@ -320,4 +328,4 @@ def gnn_params(H: int = 64, T: int = 2, seed: int = 0, out_scale: float = 0.1,
     parts += [g(H * H, 1.0 / math.sqrt(H)), g(H, bias_scale), g(H, out_scale / math.sqrt(H)), np.zeros(1)]
     p = np.concatenate(parts).astype(np.float32)
     assert p.shape[0] == gnn_param_count(H, T)
-    return p
+    return bf16_round(p) if bf16 else p
