@@ -35,6 +35,7 @@ namespace jmd {
 
 constexpr int TH = 64;                    // hidden width of this path
 constexpr int TM = 128;                   // rows per tile
+constexpr int TT = 256;                   // threads per tile CTA: two per row
 constexpr uint32_t TCOLS = 256;           // tensor-memory columns per CTA
 constexpr uint32_t SMEM_TC = 108 * 1024;  // dynamic shared memory (also caps residency at 2 CTAs per SM)
 
@@ -148,7 +149,8 @@ __device__ __forceinline__ void tc_tile_end()
     __syncthreads();
 }
 
-__device__ __forceinline__ uint32_t tc_row(const TcBar &B) { return B.tmem + ((uint32_t)(threadIdx.x & ~31) << 16); }
+// This thread's tensor-memory lane quarter (warp w reads lanes 32 (w % 4) ..).
+__device__ __forceinline__ uint32_t tc_row(const TcBar &B) { return B.tmem + ((uint32_t)(threadIdx.x & 96) << 16); }
 
 __device__ __forceinline__ void ld4(const float *p, float *v)
 {
@@ -273,8 +275,7 @@ __global__ void __launch_bounds__(1024) k_gnnt_scan2(GnnArgs a, int nchunk)
         if (threadIdx.x == 0) base = b0 + tot;
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < a.N; i += 1024) a.eoff[i] += a.ctot[i >> 10];
-    if (threadIdx.x == 0) a.eoff[a.N] = base;
+    if (threadIdx.x == 0) a.eoff[a.N] = base;   // k_gnnt_compact adds the chunk offsets
 }
 
 __global__ void __launch_bounds__(256) k_gnnt_compact(GnnArgs a)
@@ -284,7 +285,9 @@ __global__ void __launch_bounds__(256) k_gnnt_compact(GnnArgs a)
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < a.N; i += (gridDim.x * blockDim.x) >> 5) {
         int n = a.cnt[i];
         n = n < a.cap ? n : a.cap;
-        int x = a.eoff[i];
+        int x = a.eoff[i] + a.ctot[i >> 10];
+        __syncwarp();
+        if (lane == 0) a.eoff[i] = x;
         for (int k0 = 0; k0 < n; k0 += 32) {
             const int k = k0 + lane;
             const size_t E = (size_t)i * a.cap + k;
@@ -322,7 +325,10 @@ __global__ void __launch_bounds__(256) k_gnnt_erev(GnnArgs a)
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(TM, 2) k_gnnt_fe(GnnArgs a, int t)
+// Two threads per row (TT = 256): thread x owns row x & 127 (tensor-memory
+// lane) and the column half cb = 32 (x >> 7) of every 64-wide block, so each
+// row's loads are split over two threads and more of them are in flight.
+__global__ void __launch_bounds__(TT, 2) k_gnnt_fe(GnnArgs a, int t)
 {
     count_launch();
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -356,56 +362,57 @@ __global__ void __launch_bounds__(TM, 2) k_gnnt_fe(GnnArgs a, int t)
     float *ze_t = a.ze + (size_t)t * NE * TH;
     const float *ze_p = t > 0 ? a.ze + (size_t)(t - 1) * NE * TH : nullptr;
     const float inv_rc = 1.0f / a.rc;
-    const int tid = threadIdx.x;
+    const int row = threadIdx.x & (TM - 1), cb = 32 * (threadIdx.x >> 7);
     for (int tile = blockIdx.x; tile * TM < E; tile += gridDim.x) {
-        const int e = tile * TM + tid;
+        const int e = tile * TM + row;
         const bool valid = e < E;
-        float4 d4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (valid && t == 0) d4 = a.edr[e];
-        for (int k0 = 0; k0 < TH; k0 += 8) {
-            float v[8];
-            if (!valid) {
+        float v[32];
+        if (!valid) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = 0.0f;
-            } else if (t == 0) {
+            for (int q = 0; q < 32; ++q) v[q] = 0.0f;
+        } else if (t == 0) {
+            const float4 d4 = a.edr[e];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int c = k0 + q;
-                    v[q] = gnn_silu(wenc[3 * c] * (d4.x * inv_rc) + wenc[3 * c + 1] * (d4.y * inv_rc) +
-                                    wenc[3 * c + 2] * (d4.z * inv_rc) + benc[c]);
-                }
-            } else {
-                ld4(ze_p + (size_t)e * TH + k0, v);
-                ld4(ze_p + (size_t)e * TH + k0 + 4, v + 4);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = gnn_silu(v[q]);
+            for (int q = 0; q < 32; ++q) {
+                const int c = cb + q;
+                v[q] = gnn_silu(wenc[3 * c] * (d4.x * inv_rc) + wenc[3 * c + 1] * (d4.y * inv_rc) +
+                                wenc[3 * c + 2] * (d4.z * inv_rc) + benc[c]);
             }
-            put8(sm, SX, LO, tid, k0, TH, v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 32; q += 4) ld4(ze_p + (size_t)e * TH + cb + q, v + q);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = gnn_silu(v[q]);
         }
+#pragma unroll
+        for (int q = 0; q < 32; q += 8) put8(sm, SX, LO, row, cb + q, TH, v + q);
         tc_mma(B, phase, sbase, SX, LO, SW, TH, TH, 0);
         const int recv = valid ? a.erecv[e] : 0, send = valid ? a.esend[e] : 0;
-        for (int c0 = 0; c0 < TH; c0 += 16) {
+        float x[32], y[32];
+        if (valid) {
+            if (t == 0) {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    x[q] = cv[cb + q];
+                    y[q] = cv[TH + cb + q];
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; q += 4) {
+                    ld4(a.rr + (size_t)recv * TH + cb + q, x + q);
+                    ld4(a.ps + (size_t)send * TH + cb + q, y + q);
+                }
+            }
+        }
+#pragma unroll
+        for (int c0 = 0; c0 < 32; c0 += 16) {
             float d[16];
-            tmem_ld16(tc_row(B) + c0, d);
+            tmem_ld16(tc_row(B) + cb + c0, d);
             if (valid) {
 #pragma unroll
-                for (int q = 0; q < 16; q += 4) {
-                    float x[4], y[4];
-                    if (t == 0) {
+                for (int q = 0; q < 16; ++q) d[q] += x[c0 + q] + y[c0 + q];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            x[u] = cv[c0 + q + u];
-                            y[u] = cv[TH + c0 + q + u];
-                        }
-                    } else {
-                        ld4(a.rr + (size_t)recv * TH + c0 + q, x);
-                        ld4(a.ps + (size_t)send * TH + c0 + q, y);
-                    }
-                    float z[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) z[u] = d[q + u] + x[u] + y[u];
-                    st4(ze_t + (size_t)e * TH + c0 + q, z);
-                }
+                for (int q = 0; q < 16; q += 4) st4(ze_t + (size_t)e * TH + cb + c0 + q, d + q);
             }
         }
         tc_tile_end();
@@ -413,12 +420,13 @@ __global__ void __launch_bounds__(TM, 2) k_gnnt_fe(GnnArgs a, int t)
     tc_teardown(B, a.status);
 }
 
-__global__ void __launch_bounds__(TM, 2) k_gnnt_fn(GnnArgs a, int t)
+__global__ void __launch_bounds__(TT, 2) k_gnnt_fn(GnnArgs a, int t)
 {
     count_launch();
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ TcBar B;
     __shared__ float bt[TH], an[TH], dd[TH], ww[TH], uu[TH];
+    __shared__ float red[TM];
     constexpr uint32_t SWB = 0;                       // B_t: [64][128]
     constexpr uint32_t SWN = SWB + TH * 2 * TH * 2;   // [A_r; A_s] of t + 1: [128][64]; last: D [64][64]
     constexpr uint32_t SWD = SWN + 2 * TH * TH * 2;   // last: D^T [64][64]
@@ -452,97 +460,106 @@ __global__ void __launch_bounds__(TM, 2) k_gnnt_fn(GnnArgs a, int t)
     const size_t NE = (size_t)a.N * a.cap;
     const float *ze_t = a.ze + (size_t)t * NE * TH;
     const float cdec = __ldg(P + o.c);
-    const int tid = threadIdx.x;
+    const int row = threadIdx.x & (TM - 1), hf = threadIdx.x >> 7, cb = 32 * hf;
     for (int tile = blockIdx.x; tile * TM < a.N; tile += gridDim.x) {
-        const int i = tile * TM + tid;
+        const int i = tile * TM + row;
         const bool valid = i < a.N;
         const int e0 = valid ? a.eoff[i] : 0, e1 = valid ? a.eoff[i + 1] : 0;
-        // A row: [v of step t - 1 | m]
-        for (int k0 = 0; k0 < TH; k0 += 8) {
-            float v[8], m[8];
+        // A row: [v of step t - 1 | m], columns cb .. cb + 32 of each half
+        {
+            float v[32], m[32];
             if (!valid) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = 0.0f;
+                for (int q = 0; q < 32; ++q) v[q] = 0.0f;
             } else if (t == 0) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = uu[k0 + q];
+                for (int q = 0; q < 32; ++q) v[q] = uu[cb + q];
             } else {
-                const float *zp = a.zv + ((size_t)(t - 1) * a.N + i) * TH + k0;
-                ld4(zp, v);
-                ld4(zp + 4, v + 4);
+                const float *zp = a.zv + ((size_t)(t - 1) * a.N + i) * TH + cb;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = gnn_silu(v[q]);
+                for (int q = 0; q < 32; q += 4) ld4(zp + q, v + q);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = gnn_silu(v[q]);
             }
 #pragma unroll
-            for (int q = 0; q < 8; ++q) m[q] = 0.0f;
+            for (int q = 0; q < 32; ++q) m[q] = 0.0f;
             for (int e = e0; e < e1; ++e) {
                 const float s = a.ecut[e].x;
-                float z[8];
-                ld4(ze_t + (size_t)e * TH + k0, z);
-                ld4(ze_t + (size_t)e * TH + k0 + 4, z + 4);
+                float z[32];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) m[q] += s * gnn_silu(z[q]);
+                for (int q = 0; q < 32; q += 4) ld4(ze_t + (size_t)e * TH + cb + q, z + q);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) m[q] += s * gnn_silu(z[q]);
             }
-            put8(sm, SX, LO, tid, k0, 2 * TH, v);
-            put8(sm, SX, LO, tid, TH + k0, 2 * TH, m);
+#pragma unroll
+            for (int q = 0; q < 32; q += 8) {
+                put8(sm, SX, LO, row, cb + q, 2 * TH, v + q);
+                put8(sm, SX, LO, row, TH + cb + q, 2 * TH, m + q);
+            }
         }
         tc_mma(B, phase, sbase, SX, LO, SWB, 2 * TH, TH, 0);
         // zv = D + b; v = silu(zv)
-        for (int c0 = 0; c0 < TH; c0 += 16) {
-            float d[16];
-            tmem_ld16(tc_row(B) + c0, d);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) d[q] += bt[c0 + q];
+        for (int c0 = 0; c0 < 32; c0 += 16) {
+            float d[16];
+            tmem_ld16(tc_row(B) + cb + c0, d);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) d[q] += bt[cb + c0 + q];
             if (valid) {
 #pragma unroll
-                for (int q = 0; q < 16; q += 4) st4(a.zv + ((size_t)t * a.N + i) * TH + c0 + q, d + q);
+                for (int q = 0; q < 16; q += 4) st4(a.zv + ((size_t)t * a.N + i) * TH + cb + c0 + q, d + q);
             }
 #pragma unroll
             for (int q = 0; q < 16; ++q) d[q] = valid ? gnn_silu(d[q]) : 0.0f;
-            put8(sm, SX2, LO2, tid, c0, TH, d);
-            put8(sm, SX2, LO2, tid, c0 + 8, TH, d + 8);
+            put8(sm, SX2, LO2, row, cb + c0, TH, d);
+            put8(sm, SX2, LO2, row, cb + c0 + 8, TH, d + 8);
         }
         if (!last) {
+            // receiver term (first half of the threads) and sender term (second)
             tc_mma(B, phase, sbase, SX2, LO2, SWN, TH, 2 * TH, TH);
-            for (int c0 = 0; c0 < 2 * TH; c0 += 16) {
+            float *dst = (hf ? a.ps : a.rr) + (size_t)i * TH;
+#pragma unroll
+            for (int c0 = 0; c0 < TH; c0 += 16) {
                 float d[16];
-                tmem_ld16(tc_row(B) + TH + c0, d);
+                tmem_ld16(tc_row(B) + TH + hf * TH + c0, d);
                 if (valid) {
-                    if (c0 < TH) {
+                    if (!hf) {
 #pragma unroll
                         for (int q = 0; q < 16; ++q) d[q] += an[c0 + q];
-#pragma unroll
-                        for (int q = 0; q < 16; q += 4) st4(a.rr + (size_t)i * TH + c0 + q, d + q);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 16; q += 4) st4(a.ps + (size_t)i * TH + c0 - TH + q, d + q);
                     }
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4) st4(dst + c0 + q, d + q);
                 }
             }
         } else {
             // decoder: E_i = w . silu(D v + d) + c, and g = w silu'(D v + d) for D^T g
             tc_mma(B, phase, sbase, SX2, LO2, SWN, TH, TH, TH);
-            float Ei = cdec;
-            for (int c0 = 0; c0 < TH; c0 += 16) {
+            float part = 0.0f;
+#pragma unroll
+            for (int c0 = 0; c0 < 32; c0 += 16) {
                 float d[16];
-                tmem_ld16(tc_row(B) + TH + c0, d);
+                tmem_ld16(tc_row(B) + TH + cb + c0, d);
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const float z = d[q] + dd[c0 + q], sg = gnn_sig(z);
-                    Ei += ww[c0 + q] * z * sg;
-                    d[q] = valid ? ww[c0 + q] * sg * (1.0f + z * (1.0f - sg)) : 0.0f;
+                    const int c = cb + c0 + q;
+                    const float z = d[q] + dd[c], sg = gnn_sig(z);
+                    part += ww[c] * z * sg;
+                    d[q] = valid ? ww[c] * sg * (1.0f + z * (1.0f - sg)) : 0.0f;
                 }
-                put8(sm, SX2, LO2, tid, c0, TH, d);
-                put8(sm, SX2, LO2, tid, c0 + 8, TH, d + 8);
+                put8(sm, SX2, LO2, row, cb + c0, TH, d);
+                put8(sm, SX2, LO2, row, cb + c0 + 8, TH, d + 8);
             }
-            if (valid) a.Ei[i] = Ei;
+            if (hf) red[row] = part;
+            __syncthreads();
+            if (!hf && valid) a.Ei[i] = part + red[row] + cdec;
             tc_mma(B, phase, sbase, SX2, LO2, SWD, TH, TH, 2 * TH);
-            for (int c0 = 0; c0 < TH; c0 += 16) {
+#pragma unroll
+            for (int c0 = 0; c0 < 32; c0 += 16) {
                 float d[16];
-                tmem_ld16(tc_row(B) + 2 * TH + c0, d);
+                tmem_ld16(tc_row(B) + 2 * TH + cb + c0, d);
                 if (valid) {
 #pragma unroll
-                    for (int q = 0; q < 16; q += 4) st4(a.gvd + (size_t)i * TH + c0 + q, d + q);
+                    for (int q = 0; q < 16; q += 4) st4(a.gvd + (size_t)i * TH + cb + c0 + q, d + q);
                 }
             }
         }
@@ -554,7 +571,7 @@ __global__ void __launch_bounds__(TM, 2) k_gnnt_fn(GnnArgs a, int t)
 // ---------------------------------------------------------------------------
 // reverse
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(TM, 2) k_gnnt_bn(GnnArgs a, int t)
+__global__ void __launch_bounds__(TT, 2) k_gnnt_bn(GnnArgs a, int t)
 {
     count_launch();
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -580,38 +597,41 @@ __global__ void __launch_bounds__(TM, 2) k_gnnt_bn(GnnArgs a, int t)
     uint32_t phase = 0;
     const size_t NE = (size_t)a.N * a.cap;
     const float *gz_n = last ? nullptr : a.ze + (size_t)(t + 1) * NE * TH;
-    const int tid = threadIdx.x;
+    const int row = threadIdx.x & (TM - 1), hf = threadIdx.x >> 7, cb = 32 * hf;
     for (int tile = blockIdx.x; tile * TM < a.N; tile += gridDim.x) {
-        const int i = tile * TM + tid;
+        const int i = tile * TM + row;
         const bool valid = i < a.N;
         if (!last) {
             const int e0 = valid ? a.eoff[i] : 0, e1 = valid ? a.eoff[i + 1] : 0;
-            for (int k0 = 0; k0 < TH; k0 += 8) {
-                float sr[8], ss[8];
+            float sr[32], ss[32];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) sr[q] = ss[q] = 0.0f;
-                for (int e = e0; e < e1; ++e) {
-                    const int er = a.erev[e];
-                    float x[8], y[8];
-                    ld4(gz_n + (size_t)e * TH + k0, x);
-                    ld4(gz_n + (size_t)e * TH + k0 + 4, x + 4);
-                    ld4(gz_n + (size_t)er * TH + k0, y);
-                    ld4(gz_n + (size_t)er * TH + k0 + 4, y + 4);
+            for (int q = 0; q < 32; ++q) sr[q] = ss[q] = 0.0f;
+            for (int e = e0; e < e1; ++e) {
+                const int er = a.erev[e];
+                float x[32], y[32];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        sr[q] += x[q];
-                        ss[q] += y[q];
-                    }
+                for (int q = 0; q < 32; q += 4) {
+                    ld4(gz_n + (size_t)e * TH + cb + q, x + q);
+                    ld4(gz_n + (size_t)er * TH + cb + q, y + q);
                 }
-                put8(sm, SX, LO, tid, k0, 2 * TH, sr);
-                put8(sm, SX, LO, tid, TH + k0, 2 * TH, ss);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    sr[q] += x[q];
+                    ss[q] += y[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 32; q += 8) {
+                put8(sm, SX, LO, row, cb + q, 2 * TH, sr + q);
+                put8(sm, SX, LO, row, TH + cb + q, 2 * TH, ss + q);
             }
             tc_mma(B, phase, sbase, SX, LO, SWS, 2 * TH, TH, 0);
         }
         // g_v silu'(zv) -> A operand of the node-update transpose
-        for (int c0 = 0; c0 < TH; c0 += 16) {
+#pragma unroll
+        for (int c0 = 0; c0 < 32; c0 += 16) {
             float g[16];
-            if (!last) tmem_ld16(tc_row(B) + c0, g);
+            if (!last) tmem_ld16(tc_row(B) + cb + c0, g);
             else {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) g[q] = 0.0f;
@@ -620,8 +640,8 @@ __global__ void __launch_bounds__(TM, 2) k_gnnt_bn(GnnArgs a, int t)
                 float gd[16], z[16];
 #pragma unroll
                 for (int q = 0; q < 16; q += 4) {
-                    ld4(a.gvd + (size_t)i * TH + c0 + q, gd + q);
-                    ld4(a.zv + ((size_t)t * a.N + i) * TH + c0 + q, z + q);
+                    ld4(a.gvd + (size_t)i * TH + cb + c0 + q, gd + q);
+                    ld4(a.zv + ((size_t)t * a.N + i) * TH + cb + c0 + q, z + q);
                 }
 #pragma unroll
                 for (int q = 0; q < 16; ++q) g[q] = (g[q] + gd[q]) * gnn_dsilu(z[q]);
@@ -629,22 +649,20 @@ __global__ void __launch_bounds__(TM, 2) k_gnnt_bn(GnnArgs a, int t)
 #pragma unroll
                 for (int q = 0; q < 16; ++q) g[q] = 0.0f;
             }
-            put8(sm, SX2, LO2, tid, c0, TH, g);
-            put8(sm, SX2, LO2, tid, c0 + 8, TH, g + 8);
+            put8(sm, SX2, LO2, row, cb + c0, TH, g);
+            put8(sm, SX2, LO2, row, cb + c0 + 8, TH, g + 8);
         }
         tc_mma(B, phase, sbase, SX2, LO2, SWB, TH, 2 * TH, TH);
-        for (int c0 = 0; c0 < 2 * TH; c0 += 16) {
-            float d[16];
-            tmem_ld16(tc_row(B) + TH + c0, d);
-            if (valid) {
-                if (c0 < TH) {
-                    if (t > 0) {
+        // direct gradient of step t - 1 (first half) and message gradient (second)
+        if (hf == 1 || t > 0) {
+            float *dst = (hf ? a.gm : a.gvd) + (size_t)i * TH;
 #pragma unroll
-                        for (int q = 0; q < 16; q += 4) st4(a.gvd + (size_t)i * TH + c0 + q, d + q);
-                    }
-                } else {
+            for (int c0 = 0; c0 < TH; c0 += 16) {
+                float d[16];
+                tmem_ld16(tc_row(B) + TH + hf * TH + c0, d);
+                if (valid) {
 #pragma unroll
-                    for (int q = 0; q < 16; q += 4) st4(a.gm + (size_t)i * TH + c0 - TH + q, d + q);
+                    for (int q = 0; q < 16; q += 4) st4(dst + c0 + q, d + q);
                 }
             }
         }
@@ -653,12 +671,13 @@ __global__ void __launch_bounds__(TM, 2) k_gnnt_bn(GnnArgs a, int t)
     tc_teardown(B, a.status);
 }
 
-__global__ void __launch_bounds__(TM, 2) k_gnnt_be(GnnArgs a, int t)
+__global__ void __launch_bounds__(TT, 2) k_gnnt_be(GnnArgs a, int t)
 {
     count_launch();
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ TcBar B;
     __shared__ float wenc[3 * TH], benc[TH];
+    __shared__ float4 red[TM];
     constexpr uint32_t SWA = 0;                  // A_e^T of step t + 1: [64][64]
     constexpr uint32_t SW0 = SWA + TH * TH * 2;  // A_e^T of step 0: [64][64]
     constexpr uint32_t SX = SW0 + TH * TH * 2;   // gz of step t + 1: [128][64], hi then lo
@@ -683,63 +702,68 @@ __global__ void __launch_bounds__(TM, 2) k_gnnt_be(GnnArgs a, int t)
     float *ze_t = a.ze + (size_t)t * NE * TH;
     const float *gz_n = last ? nullptr : a.ze + (size_t)(t + 1) * NE * TH;
     const float inv_rc = 1.0f / a.rc;
-    const int tid = threadIdx.x;
+    const int row = threadIdx.x & (TM - 1), hf = threadIdx.x >> 7, cb = 32 * hf;
     for (int tile = blockIdx.x; tile * TM < E; tile += gridDim.x) {
-        const int e = tile * TM + tid;
+        const int e = tile * TM + row;
         const bool valid = e < E;
         if (!last) {
-            for (int k0 = 0; k0 < TH; k0 += 8) {
-                float v[8];
-                if (valid) {
-                    ld4(gz_n + (size_t)e * TH + k0, v);
-                    ld4(gz_n + (size_t)e * TH + k0 + 4, v + 4);
-                } else {
+            float v[32];
+            if (valid) {
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) v[q] = 0.0f;
-                }
-                put8(sm, SX, LO, tid, k0, TH, v);
+                for (int q = 0; q < 32; q += 4) ld4(gz_n + (size_t)e * TH + cb + q, v + q);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = 0.0f;
             }
+#pragma unroll
+            for (int q = 0; q < 32; q += 8) put8(sm, SX, LO, row, cb + q, TH, v + q);
             tc_mma(B, phase, sbase, SX, LO, SWA, TH, TH, 0);
         }
         const int recv = valid ? a.erecv[e] : 0;
         const float s = valid ? a.ecut[e].x : 0.0f;
+        float z[32], gm[32];
+        if (valid) {
+#pragma unroll
+            for (int q = 0; q < 32; q += 4) {
+                ld4(ze_t + (size_t)e * TH + cb + q, z + q);
+                ld4(a.gm + (size_t)recv * TH + cb + q, gm + q);
+            }
+        }
         float gsv = 0.0f;
-        for (int c0 = 0; c0 < TH; c0 += 16) {
+#pragma unroll
+        for (int c0 = 0; c0 < 32; c0 += 16) {
             float d[16];
-            if (!last) tmem_ld16(tc_row(B) + c0, d);
+            if (!last) tmem_ld16(tc_row(B) + cb + c0, d);
             else {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) d[q] = 0.0f;
             }
             if (valid) {
-                float z[16], gm[16];
-#pragma unroll
-                for (int q = 0; q < 16; q += 4) {
-                    ld4(ze_t + (size_t)e * TH + c0 + q, z + q);
-                    ld4(a.gm + (size_t)recv * TH + c0 + q, gm + q);
-                }
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const float sg = gnn_sig(z[q]);
-                    gsv += gm[q] * (z[q] * sg);
-                    d[q] = (s * gm[q] + d[q]) * (sg * (1.0f + z[q] * (1.0f - sg)));
+                    const float zz = z[c0 + q], sg = gnn_sig(zz);
+                    gsv += gm[c0 + q] * (zz * sg);
+                    d[q] = (s * gm[c0 + q] + d[q]) * (sg * (1.0f + zz * (1.0f - sg)));
                 }
                 if (t > 0) {
 #pragma unroll
-                    for (int q = 0; q < 16; q += 4) st4(ze_t + (size_t)e * TH + c0 + q, d + q);
+                    for (int q = 0; q < 16; q += 4) st4(ze_t + (size_t)e * TH + cb + c0 + q, d + q);
                 }
             } else {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) d[q] = 0.0f;
             }
             if (t == 0) {
-                put8(sm, SX2, LO, tid, c0, TH, d);
-                put8(sm, SX2, LO, tid, c0 + 8, TH, d + 8);
+                put8(sm, SX2, LO, row, cb + c0, TH, d);
+                put8(sm, SX2, LO, row, cb + c0 + 8, TH, d + 8);
             }
         }
+        // dE/ds of the edge: the two halves' parts
+        if (hf) red[row].x = gsv;
+        __syncthreads();
         float gs_tot = 0.0f;
-        if (valid) {
-            gs_tot = last ? gsv : a.gs[e] + gsv;
+        if (!hf && valid) {
+            gs_tot = (last ? 0.0f : a.gs[e]) + gsv + red[row].x;
             a.gs[e] = gs_tot;
         }
         if (t == 0) {
@@ -747,12 +771,13 @@ __global__ void __launch_bounds__(TM, 2) k_gnnt_be(GnnArgs a, int t)
             tc_mma(B, phase, sbase, SX2, LO, SW0, TH, TH, TH);
             const float4 d4 = valid ? a.edr[e] : make_float4(0.f, 0.f, 0.f, 1.f);
             float gx = 0.f, gy = 0.f, gz = 0.f;
-            for (int c0 = 0; c0 < TH; c0 += 16) {
+#pragma unroll
+            for (int c0 = 0; c0 < 32; c0 += 16) {
                 float g0[16];
-                tmem_ld16(tc_row(B) + TH + c0, g0);
+                tmem_ld16(tc_row(B) + TH + cb + c0, g0);
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const int c = c0 + q;
+                    const int c = cb + c0 + q;
                     const float z0 = wenc[3 * c] * (d4.x * inv_rc) + wenc[3 * c + 1] * (d4.y * inv_rc) +
                                      wenc[3 * c + 2] * (d4.z * inv_rc) + benc[c];
                     const float g = g0[q] * gnn_dsilu(z0);
@@ -761,10 +786,13 @@ __global__ void __launch_bounds__(TM, 2) k_gnnt_be(GnnArgs a, int t)
                     gz += wenc[3 * c + 2] * g;
                 }
             }
-            if (valid) {
+            if (hf) red[row] = make_float4(gx, gy, gz, 0.0f);
+            __syncthreads();
+            if (!hf && valid) {
+                const float4 o2 = red[row];
                 const float cc = gs_tot * a.ecut[e].y;
-                a.gpos[e] = make_float4(gx * inv_rc + cc * d4.x, gy * inv_rc + cc * d4.y, gz * inv_rc + cc * d4.z,
-                                        0.0f);
+                a.gpos[e] = make_float4((gx + o2.x) * inv_rc + cc * d4.x, (gy + o2.y) * inv_rc + cc * d4.y,
+                                        (gz + o2.z) * inv_rc + cc * d4.z, 0.0f);
             }
         }
         tc_tile_end();
@@ -824,12 +852,12 @@ void enqueue_gnn_tc(const GnnArgs &g, const PairArgs &pa, int kick, cudaStream_t
     k_gnnt_erev<<<sms * 4, 256, 0, st>>>(g);
     const int tgrid = 2 * sms;
     for (int t = 0; t < g.T; ++t) {
-        k_gnnt_fe<<<tgrid, TM, SMEM_TC, st>>>(g, t);
-        k_gnnt_fn<<<tgrid, TM, SMEM_TC, st>>>(g, t);
+        k_gnnt_fe<<<tgrid, TT, SMEM_TC, st>>>(g, t);
+        k_gnnt_fn<<<tgrid, TT, SMEM_TC, st>>>(g, t);
     }
     for (int t = g.T - 1; t >= 0; --t) {
-        k_gnnt_bn<<<tgrid, TM, SMEM_TC, st>>>(g, t);
-        k_gnnt_be<<<tgrid, TM, SMEM_TC, st>>>(g, t);
+        k_gnnt_bn<<<tgrid, TT, SMEM_TC, st>>>(g, t);
+        k_gnnt_be<<<tgrid, TT, SMEM_TC, st>>>(g, t);
     }
     const int fgrid = std::max(1, std::min((g.N + 7) / 8, pa.max_blocks));
     if (kick) k_gnnt_force<1><<<fgrid, 256, 0, st>>>(g, pa);
