@@ -408,11 +408,21 @@ def nhc_section(steps=200):
     return out
 
 
+def _hbm_peak():
+    """(GB/s, source): the measured copy bandwidth, else the fallback figure."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
 def gnn_section(steps=100, H=64, T=2):
     """Graph-network potential deployed in Nose-Hoover NVT: silicon, N =
     64,000 atoms at 1000 K (dt = 1 fs, r_c = 3.77 A, hidden width H, T
-    message-passing steps, seeded random weights), `steps` steps in one graph
-    launch; and one energy + force evaluation timed alone."""
+    message-passing steps, seeded random weights that are BF16-representable,
+    so the FP32 and the tensor-core kernels hold the same model), `steps`
+    steps in one graph launch, and one energy + force evaluation timed
+    alone; for the FP32 CUDA-core kernels and for the tcgen05 kernels."""
     import torch
     import paper_1912_04232_b300 as P
     import paper_1912_04232_b300.learned as LP
@@ -423,7 +433,7 @@ def gnn_section(steps=100, H=64, T=2):
     N, cap, rc = si.N, 48, 3.77
     s = P.md_space_periodic(3, [si.L] * 3)
     nl = P.NeighborList(s, N, rc, 0.5, cap)
-    params = torch.from_numpy(W.gnn_params(H, T, seed=0, out_scale=0.3)).to(dev)
+    params = torch.from_numpy(W.gnn_params(H, T, seed=0, out_scale=0.3, bf16=True)).to(dev)
     model = P.GNNModel(params, N, cap, H, T, rc)
     r0, v0 = torch.from_numpy(si.r).to(dev), torch.from_numpy(si.v).to(dev)
     r, v, f = torch.empty_like(r0), torch.empty_like(v0), torch.zeros_like(r0)
@@ -431,52 +441,66 @@ def gnn_section(steps=100, H=64, T=2):
     Hx = torch.zeros(steps, dtype=torch.float64, device=dev)
     KE = torch.zeros_like(Hx)
     kT, dt = W.KB_EV * 1000.0, 1.0
-    ts, tf = [], []
-    for k in range(3):
-        r.copy_(r0)
-        v.copy_(v0)
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record()
-        nl.build(r, st)
-        P.md_energy_forces(s, model.pot, r, nl.plan, f, None, st)
-        e1.record()
-        P.md_integrate_nhc(s, model.pot, r, v, f, LP.MASS_SI, dt, kT, 100.0 * dt, 3, steps, nl.plan, th, True, None,
-                           KE, Hx, True, st)
-        e2.record()
-        e2.synchronize()
-        if k:
-            ts.append(e1.elapsed_time(e2))
-    # one evaluation alone (list already built)
-    for k in range(5):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        P.md_energy_forces(s, model.pot, r, nl.plan, f, None, st)
-        e1.record()
-        e1.synchronize()
-        if k >= 2:
-            tf.append(e0.elapsed_time(e1))
-    Hn = Hx.cpu().numpy()
-    # algorithmic FLOPs of one evaluation (the matrix products; element-wise
-    # work not counted): edges 2H^2 E (2T products per edge: A_e forward per
-    # step, A_e^T of the step above and of step 0 in reverse), nodes 2H^2 N
-    # (8T - 3 products: B, A_r, A_s, D forward; D^T, B^T, A_r^T, A_s^T reverse)
-    n = nl.cnt.clamp(max=cap).long()
-    rows = nl.nbr.long().clamp(max=N - 1)
-    d = r[rows, :3] - r[:, None, :3]
-    d -= float(si.L) * torch.round(d / float(si.L))
-    valid = (torch.arange(cap, device=dev)[None, :] < n[:, None]) & ((d * d).sum(-1) < rc * rc)
-    E_edges = int(valid.sum().item())
-    flops = 2.0 * H * H * (E_edges * 2 * T + N * (8 * T - 3))
     fp32_peak = 148 * 128 * 2 * 2032e6 / 1e12   # FP32 FMA lanes x 2 x max SM clock
-    tflops = flops / (min(tf) * 1e-3) / 1e12
-    return {"N": N, "H": H, "T": T, "steps": steps, "ms": min(ts), "atom_steps_per_s": N * steps / (min(ts) * 1e-3),
-            "force_eval_ms": min(tf), "edges_within_rc_per_atom": E_edges / N,
-            "roofline": {"bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": tflops / fp32_peak, "flops_per_eval": flops,
-                         "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz"},
-            "group": 4, "max_abs_dH_per_atom": float(np.abs(Hn - Hn[0]).max() / N),
-            "T_end_over_T": float(KE[-1].item() / (1.5 * N * kT)), "weights": "seeded random (out_scale 0.3)",
-            "status": P.md_status_poll(st)}
+    out = {"N": N, "H": H, "T": T, "steps": steps, "weights": "seeded random, BF16-representable (out_scale 0.3)"}
+    for name, tc in (("fp32", 0), ("tcgen05", 1)):
+        P.md_gnn_set_tensor_cores(tc)
+        ts, tf = [], []
+        for k in range(3):
+            r.copy_(r0)
+            v.copy_(v0)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            nl.build(r, st)
+            P.md_energy_forces(s, model.pot, r, nl.plan, f, None, st)
+            e1.record()
+            P.md_integrate_nhc(s, model.pot, r, v, f, LP.MASS_SI, dt, kT, 100.0 * dt, 3, steps, nl.plan, th, True,
+                               None, KE, Hx, True, st)
+            e2.record()
+            e2.synchronize()
+            if k:
+                ts.append(e1.elapsed_time(e2))
+        for k in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            P.md_energy_forces(s, model.pot, r, nl.plan, f, None, st)
+            e1.record()
+            e1.synchronize()
+            if k >= 2:
+                tf.append(e0.elapsed_time(e1))
+        # edges within r_c on the final configuration
+        n = nl.cnt.clamp(max=cap).long()
+        rows = nl.nbr.long().clamp(max=N - 1)
+        d = r[rows, :3] - r[:, None, :3]
+        d -= float(si.L) * torch.round(d / float(si.L))
+        valid = (torch.arange(cap, device=dev)[None, :] < n[:, None]) & ((d * d).sum(-1) < rc * rc)
+        E_edges = int(valid.sum().item())
+        # FP32 path: FLOP-bound by its products, 2H^2 (2T E + (8T - 3) N)
+        # (edges: A_e forward per step, A_e^T of the step above and of step
+        # 0 in reverse; nodes: B, A_r, A_s, D forward, D^T, B^T, A_r^T, A_s^T
+        # reverse).  Tensor-core path: bound by the per-step edge and node
+        # vectors in HBM, written once and read once in each direction:
+        # 16 H T (E + N) bytes.
+        Hn = Hx.cpu().numpy()
+        ent = {"ms": min(ts), "atom_steps_per_s": N * steps / (min(ts) * 1e-3), "force_eval_ms": min(tf),
+               "edges_within_rc_per_atom": E_edges / N, "max_abs_dH_per_atom": float(np.abs(Hn - Hn[0]).max() / N),
+               "T_end_over_T": float(KE[-1].item() / (1.5 * N * kT))}
+        if tc:
+            byts = 16.0 * H * T * (E_edges + N)
+            gbs = byts / (min(tf) * 1e-3) / 1e9
+            hbm, src = _hbm_peak()
+            ent["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                               "bytes_per_eval": byts, "peak_source": src}
+        else:
+            flops = 2.0 * H * H * (E_edges * 2 * T + N * (8 * T - 3))
+            tfl = flops / (min(tf) * 1e-3) / 1e12
+            ent["roofline"] = {"bound": "alu", "achieved": tfl, "peak": fp32_peak, "unit": "TFLOP/s",
+                               "frac": tfl / fp32_peak, "flops_per_eval": flops,
+                               "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz"}
+        out[name] = ent
+    P.md_gnn_set_tensor_cores(0)
+    out["status"] = P.md_status_poll(st)
+    return out
 
 
 def flock_section(N=100000, steps=200, n_pred=8):
@@ -680,10 +704,7 @@ def main():
         fe.append((e0, e1))
     torch.cuda.synchronize()
     kt = statistics.median(a.elapsed_time(b) for a, b in fe[5:]) * 1e-3
-    try:
-        peak, peak_src = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
-    except (OSError, KeyError, ValueError):
-        peak, peak_src = 6400.0, "fallback"
+    peak, peak_src = _hbm_peak()
     achieved = bytes_per_particle * c.N / kt / 1e9
     traffic = None
     try:

@@ -413,6 +413,7 @@ void enqueue_mlp_infer_tc(const float *P, const float *norm, const float *G, int
                           uint32_t *status, cudaStream_t st);
 
 static int g_bp_tc = 0;   // 1: network on the tensor cores (BF16), 0: FP32 CUDA cores
+int bp_variant() { return g_bp_tc; }
 
 static BpArgs bp_args_from(const PairArgs &pa)
 {

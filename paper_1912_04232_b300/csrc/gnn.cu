@@ -646,6 +646,7 @@ static size_t gnn_smem_bwd(int t)
 
 static int g_gnn_group = 4;   // atoms per warp (md_gnn_set_group)
 static int g_gnn_tc = 0;      // 1: the tensor-core kernels (gnn_tc.cu; H = 64)
+int gnn_variant() { return g_gnn_tc | (g_gnn_group << 1); }
 
 static int gnn_sms()
 {

@@ -54,6 +54,9 @@ struct PairArgs {
     // graph-network potential: the model descriptor by value (so a cached
     // graph's key covers its device pointers)
     md_gnn_model gnn;
+    // library switches that change which kernels are enqueued (tensor cores
+    // for the networks, atoms per warp): part of every cached graph's key
+    int variant;
     // cell-centred path (lists with local rows): 16-bit rows and the cell list
     const uint16_t *lrow;
     const int32_t *atoms, *cell_start;
@@ -128,6 +131,8 @@ void enqueue_sw(const PairArgs &a, int kick, cudaStream_t st);
 void enqueue_bp_step(const PairArgs &a, int kick, cudaStream_t st);
 void enqueue_gnn_step(const PairArgs &a, int kick, cudaStream_t st);
 bool gnn_model_ok(const md_gnn_model *m, const md_nbr *nb);
+int bp_variant();
+int gnn_variant();
 int pair_blocks(int N, int tpp);
 // r += eta F (unwrapped) with the displacement check (gradient descent step)
 void enqueue_gd_step(const md_space *s, float *d_r, const float *d_f, const md_nbr *nb, float eta, cudaStream_t st);

@@ -464,6 +464,7 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
     for (int k = 0; k < 3; ++k) a.nc[k] = nb->ncell[k];
     a.ncell = nb->ncell_total;
     a.max_blocks = w.max_blocks;
+    a.variant = bp_variant() | (gnn_variant() << 1);
     if (p->kind == MD_LJ) {
         if (p->r_cut > nb->r_list) return false;
         float rc = p->r_cut;

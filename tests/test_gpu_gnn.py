@@ -236,3 +236,40 @@ def test_tensor_cores_unrepresentable_weights_stay_close(P, tensor_cores):
 
 def test_tensor_cores_nose_hoover_run(P, tensor_cores):
     test_nose_hoover_run(P)
+
+
+def test_switching_kernels_recaptures_the_md_graph(P):
+    # the cached MD graph is keyed by the kernel switches too: the same
+    # buffers run with tensor cores after an FP32 run give the tensor-core
+    # trajectory, not a replay of the FP32 graph
+    import torch
+    H, T = 64, 2
+    r0, L = _si(4, seed=50, jitter=0.1)
+    v0 = W.sw_silicon(4, T_K=600.0, seed=50).v
+    p32 = W.gnn_params(H, T, seed=4, out_scale=0.3, bf16=True)
+    s = P.md_space_periodic(3, [L] * 3)
+    nl = P.NeighborList(s, r0.shape[0], RC, SKIN, CAP)
+    m = P.GNNModel(to_dev(p32, torch.float32), r0.shape[0], CAP, H, T, RC)
+    rd, vd = to_dev(r0, torch.float32), to_dev(v0, torch.float32)
+    f = torch.zeros_like(rd)
+    st = status_word()
+
+    def run(tc, r_buf, v_buf):
+        P.md_gnn_set_tensor_cores(tc)
+        r_buf.copy_(to_dev(r0, torch.float32))
+        v_buf.copy_(to_dev(v0, torch.float32))
+        nl.build(r_buf, st)
+        P.md_energy_forces(s, m.pot, r_buf, nl.plan, f, None, st)
+        P.md_integrate_nve(s, m.pot, r_buf, v_buf, f, 28.0855 * 103.6427, 0.5, 20, nl.plan, None, None, True, st)
+        torch.cuda.synchronize()
+        return r_buf.cpu().numpy().copy()
+
+    try:
+        a = run(False, rd, vd)
+        b = run(True, rd, vd)
+        c = run(True, torch.empty_like(rd), torch.empty_like(vd))
+    finally:
+        P.md_gnn_set_tensor_cores(False)
+    assert P.md_status_poll(st) == 0
+    np.testing.assert_array_equal(b, c)
+    assert not np.array_equal(a, b)
