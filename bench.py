@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tpp", type=int, default=0)
     ap.add_argument("--pair-opt", type=int, default=-1, help="pair-kernel variant (md_set_pair_options)")
-    ap.add_argument("--no-graph", action="store_true", help="launch every kernel from the host (profiling)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every kernel from the host, the FIRE and flocking loops too (profiling)")
     ap.add_argument("--nve-fusion", type=int, default=1, help="1: kick-drift fused into the force kernel (md_set_nve_fusion)")
     ap.add_argument("--local-rows", type=int, default=0,
                     help="1: cell-centred forces over 16-bit local rows (MD_NBR_LOCAL_ROWS); 0: int32 rows")
@@ -595,6 +596,7 @@ def main():
     if args.pair_opt >= 0:
         P.md_set_pair_options(args.pair_opt)
     P.md_set_nve_fusion(bool(args.nve_fusion))
+    P.md_set_loop_graphs(not args.no_graph)
     s = P.md_space_periodic(3, [c.L] * 3)
     nl = P.NeighborList(s, c.N, c.r_cut, c.skin, 128, local_rows=bool(args.local_rows))
     pot = P.lj_pot(c.eps, c.sigma, c.r_cut, True)
