@@ -117,3 +117,32 @@ def energy_forces(R_np, L, params, H, T, rc, edges=None):
     E, Ei = energy(R, L, p, H, T, rc, edges)
     (g,) = torch.autograd.grad(E, R)
     return float(E.detach()), Ei.detach().numpy(), -g.numpy()
+
+
+def loss(batch, params, H, T, rc, w_F=1.0, create_graph=False):
+    """Energy + force loss over snapshots [(R, L, E_ref, F_ref)] (the fit of
+    Sec. 4.1, as for the BP network):
+        mean_s ((E_s - E_ref,s) / n)^2 + w_F mean_{s,i,c} (F - F_ref)^2
+    params: a torch FP64 vector (may require grad)."""
+    lossE = 0.0
+    lossF = 0.0
+    nF = 0
+    for (R_np, L, E_ref, F_ref) in batch:
+        R = torch.tensor(np.asarray(R_np, np.float64)[:, :3], dtype=F64, requires_grad=True)
+        n = R.shape[0]
+        E, _ = energy(R, L, params, H, T, rc, edges_within(R_np, L, rc))
+        (g,) = torch.autograd.grad(E, R, create_graph=create_graph)
+        F = -g
+        lossE = lossE + ((E - float(E_ref)) / n) ** 2
+        lossF = lossF + ((F - torch.as_tensor(np.asarray(F_ref, np.float64)[:, :3])) ** 2).sum()
+        nF += 3 * n
+    return lossE / len(batch) + w_F * lossF / nF
+
+
+def loss_and_grads(batch, params, H, T, rc, w_F=1.0):
+    """(loss, d loss / d params as a flat FP64 array): the force term's
+    gradient is a double backward (autograd through autograd)."""
+    p = torch.tensor(np.asarray(params, np.float64), dtype=F64, requires_grad=True)
+    L_ = loss(batch, p, H, T, rc, w_F, create_graph=True)
+    (g,) = torch.autograd.grad(L_, p)
+    return float(L_.detach()), g.numpy()

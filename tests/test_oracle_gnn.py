@@ -222,3 +222,26 @@ def test_continuous_as_a_pair_crosses_the_cutoff():
         # s(r) ~ (pi eps / 2)^2 near the cutoff and s' ~ eps
         assert abs(Ein - Eout) < 10 * (math.pi * eps / 2) ** 2
         assert np.abs(Fin).max() < 10 * eps
+
+
+def test_loss_gradient_matches_finite_differences():
+    # the force-matching term needs second derivatives: check the double
+    # backward against central differences of the loss itself
+    H, T, L = 8, 2, 8.0
+    p = W.gnn_params(H, T, seed=12, out_scale=1.0).astype(np.float64)
+    batch = []
+    for s in range(2):
+        R = _config(20, L, 30 + s)
+        rng = np.random.Generator(np.random.PCG64(40 + s))
+        batch.append((R, L, rng.normal(0.0, 1.0), rng.normal(0.0, 0.1, size=(20, 3))))
+    loss0, g = G.loss_and_grads(batch, p, H, T, RC, w_F=0.7)
+    import torch
+    f = lambda q: float(G.loss(batch, torch.tensor(q), H, T, RC, 0.7))
+    h = 1e-6
+    idx = list(range(0, 3 * H, 5)) + list(range(5 * H, 5 * H + 3 * H * H, 97)) + [len(p) - 2 - H, len(p) - 1]
+    for k in idx:
+        qp, qm = p.copy(), p.copy()
+        qp[k] += h
+        qm[k] -= h
+        fd = (f(qp) - f(qm)) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])), (k, fd, g[k])
