@@ -242,6 +242,7 @@ typedef struct {
     float r_cut;
     void *ws;
     size_t ws_bytes;
+    int sys_n;            /* 0, or atoms per system for concatenated equal-size systems (rows local to each) */
 } md_gnn_model;
 
 /* Parameter count 5H + T (5H^2 + 2H) + H^2 + 2H + 1; 0 for unsupported H, T. */
@@ -257,6 +258,25 @@ JMD_API md_status md_gnn_set_tensor_cores(int on);
 JMD_API md_status md_gnn_set_group(int G);
 /* Workspace bytes for N atoms and row capacity cap; 0 if unsupported. */
 JMD_API size_t md_gnn_workspace_bytes(int N, int cap, int H, int T);
+
+/* Training (Sec. 4.1: the network is fitted to energies and forces).
+ * Gradient with respect to the parameters of
+ *     J = sum_i c_E,i E_i - sum_k u_k . dE/dR_k
+ * which, with c_E = dL/dE_i and u = dL/dF_k (md_bp_loss_prep: d_cE [N],
+ * d_dF [N][4]), is the gradient of the energy + force loss L.  The force
+ * term needs second derivatives: the network runs forward carrying the
+ * tangent along u, then one reverse sweep goes through values and tangents;
+ * weight gradients are summed over edges and atoms in a fixed order (FP64
+ * across row batches).  FP32 kernels; H = 64 only.  d_r, nb: the atoms
+ * (N = nb->N), all in the box s; with m->sys_n > 0 they are systems of
+ * sys_n atoms whose rows are local to each system.  m: the model (its
+ * workspace for this N and cap is used as scratch too).  d_scratch:
+ * md_gnn_train_scratch_bytes(N, cap, H, T) bytes, 256-byte aligned.
+ * d_grad: md_gnn_param_count(H, T) floats, overwritten. */
+JMD_API size_t md_gnn_train_scratch_bytes(int N, int cap, int H, int T);
+JMD_API md_status md_gnn_train_grad(const md_space *s, const float *d_r, const md_nbr *nb, const md_gnn_model *m,
+                                    const float *d_cE, const float *d_dF, void *d_scratch, size_t scratch_bytes,
+                                    float *d_grad, uint32_t *d_status, md_stream_t stream);
 
 /* Forces and per-particle energies into d_f [N][4]; if d_E != NULL the FP64
  * total energy sum_i e_i is written to *d_E (device).  Needs a built list

@@ -203,10 +203,11 @@ __global__ void __launch_bounds__(gnn_warps(G) * 32) k_gnn_fwd(GnnArgs a, int t)
                 n = n < a.cap ? n : a.cap;
                 if (k >= n) continue;
                 const size_t E = (size_t)i * a.cap + k;
-                const int j = a.nbr[E];
+                const int base = a.sys_n ? (i / a.sys_n) * a.sys_n : 0;
+                const int j = a.nbr[E] + base;
                 int rv = -1;
                 float4 d4 = make_float4(0.f, 0.f, 0.f, -1.0f);
-                if (j >= 0 && j < a.N && j != i) {
+                if (j >= base && j < (a.sys_n ? base + a.sys_n : a.N) && j < a.N && j != i) {
                     float dx, dy, dz;
                     const float r2 = dist2_rn<3>(a.r[j], a.r[i], a.box, dx, dy, dz);
                     if (r2 < a.rc2) {
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(gnn_warps(G) * 32) k_gnn_fwd(GnnArgs a, int t)
                         for (int p = 0; p < nj && rv < 0; p += 4) {
                             int q4[4];
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) q4[u] = p + u < nj ? rowj[p + u] : -1;
+                            for (int u = 0; u < 4; ++u) q4[u] = p + u < nj ? rowj[p + u] + base : -1;
 #pragma unroll
                             for (int u = 0; u < 4; ++u)
                                 if (rv < 0 && q4[u] == i) rv = j * a.cap + p + u;
@@ -694,26 +695,13 @@ bool gnn_model_ok(const md_gnn_model *m, const md_nbr *nb)
     if (m->T < 1 || m->T > GNN_MAXT) return false;
     if (!(m->r_cut > 0.0f) || m->r_cut > nb->r_list) return false;
     if (nb->cap > GNN_MAXCAP || nb->dim != 3) return false;
+    if (m->sys_n < 0 || (m->sys_n > 0 && nb->N % m->sys_n != 0)) return false;
     return m->ws_bytes >= gnn_ws_layout(nb->N, nb->cap, m->H, m->T).total;
 }
 
-void enqueue_gnn_step(const PairArgs &pa, int kick, cudaStream_t st)
+void gnn_bind_workspace(GnnArgs &g, const md_gnn_model *m)
 {
-    const md_gnn_model *m = &pa.gnn;
-    GnnArgs g;
-    memset(&g, 0, sizeof(g));
-    g.box = pa.box;
-    g.N = pa.N;
-    g.cap = pa.cap;
-    g.T = m->T;
-    g.rc = m->r_cut;
-    g.rc2 = m->r_cut * m->r_cut;
-    g.r = pa.r;
-    g.nbr = pa.nbr;
-    g.cnt = pa.cnt;
-    g.P = m->params;
-    g.off = gnn_offsets(m->H, m->T);
-    const GnnWs L = gnn_ws_layout(pa.N, pa.cap, m->H, m->T);
+    const GnnWs L = gnn_ws_layout(g.N, g.cap, m->H, m->T);
     unsigned char *b = (unsigned char *)m->ws;
     g.rev = (int32_t *)(b + L.rev);
     g.dr = (float4 *)(b + L.dr);
@@ -738,6 +726,26 @@ void enqueue_gnn_step(const PairArgs &pa, int kick, cudaStream_t st)
     g.edr = (float4 *)(b + L.edr);
     g.ecut = (float2 *)(b + L.ecut);
     g.gm = (float *)(b + L.gm);
+}
+
+void enqueue_gnn_step(const PairArgs &pa, int kick, cudaStream_t st)
+{
+    const md_gnn_model *m = &pa.gnn;
+    GnnArgs g;
+    memset(&g, 0, sizeof(g));
+    g.box = pa.box;
+    g.N = pa.N;
+    g.cap = pa.cap;
+    g.T = m->T;
+    g.rc = m->r_cut;
+    g.rc2 = m->r_cut * m->r_cut;
+    g.r = pa.r;
+    g.nbr = pa.nbr;
+    g.cnt = pa.cnt;
+    g.P = m->params;
+    g.off = gnn_offsets(m->H, m->T);
+    g.sys_n = m->sys_n;
+    gnn_bind_workspace(g, m);
     g.status = pa.status;
     if (g_gnn_tc && m->H == 64) {
         enqueue_gnn_tc(g, pa, kick, st);

@@ -42,6 +42,7 @@ inline GnnOff gnn_offsets(int H, int T)
 struct GnnArgs {
     Box box;
     int N, cap, T;
+    int sys_n;        // 0: rows hold global indices; else atoms per system, rows local to each system
     float rc, rc2;
     const float4 *r;
     const int32_t *nbr, *cnt;
@@ -133,5 +134,8 @@ inline GnnWs gnn_ws_layout(int N, int cap, int H, int T)
 
 struct PairArgs;
 void enqueue_gnn_tc(const GnnArgs &g, const PairArgs &pa, int kick, cudaStream_t st);
+void enqueue_gnn_compact(const GnnArgs &g, cudaStream_t st);
+// Points g's arrays into the model's workspace (g.N, g.cap, g.T set).
+void gnn_bind_workspace(GnnArgs &g, const md_gnn_model *m);
 
 }  // namespace jmd

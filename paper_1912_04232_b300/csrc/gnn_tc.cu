@@ -182,10 +182,11 @@ __global__ void __launch_bounds__(256) k_gnnt_prep(GnnArgs a)
             bool ok = false;
             if (k < n) {
                 const size_t E = (size_t)i * a.cap + k;
-                const int j = a.nbr[E];
+                const int base = a.sys_n ? (i / a.sys_n) * a.sys_n : 0;
+                const int j = a.nbr[E] + base;
                 int rv = -1;
                 float4 d4 = make_float4(0.f, 0.f, 0.f, -1.0f);
-                if (j >= 0 && j < a.N && j != i) {
+                if (j >= base && j < (a.sys_n ? base + a.sys_n : a.N) && j < a.N && j != i) {
                     float dx, dy, dz;
                     const float r2 = dist2_rn<3>(a.r[j], ri, a.box, dx, dy, dz);
                     if (r2 < a.rc2) {
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(256) k_gnnt_prep(GnnArgs a)
                         nj = nj < a.cap ? nj : a.cap;
                         const int32_t *rowj = a.nbr + (size_t)j * a.cap;
                         for (int p = 0; p < nj; ++p)
-                            if (rowj[p] == i) {
+                            if (rowj[p] + base == i) {
                                 rv = j * a.cap + p;
                                 break;
                             }
@@ -830,6 +831,26 @@ __global__ void __launch_bounds__(256) k_gnnt_force(GnnArgs g, PairArgs pa)
     energy_epilogue(pe_acc, ke_acc, pa);
 }
 
+// The edges with r < r_c compacted in receiver order (also used by the
+// training kernels of gnn_train.cu).
+void enqueue_gnn_compact(const GnnArgs &g, cudaStream_t st)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    const int wgrid = std::max(1, std::min((g.N * 32 + 255) / 256, sms * 8));
+    k_gnnt_prep<<<wgrid, 256, 0, st>>>(g);
+    const int nchunk = (g.N + 1023) / 1024;
+    k_gnnt_scan1<<<nchunk, 1024, 0, st>>>(g);
+    k_gnnt_scan2<<<1, 1024, 0, st>>>(g, nchunk);
+    k_gnnt_compact<<<wgrid, 256, 0, st>>>(g);
+    k_gnnt_erev<<<sms * 4, 256, 0, st>>>(g);
+}
+
 void enqueue_gnn_tc(const GnnArgs &g, const PairArgs &pa, int kick, cudaStream_t st)
 {
     static int sms = 0;
@@ -843,13 +864,7 @@ void enqueue_gnn_tc(const GnnArgs &g, const PairArgs &pa, int kick, cudaStream_t
         cudaFuncSetAttribute(k_gnnt_bn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_TC);
         cudaFuncSetAttribute(k_gnnt_be, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_TC);
     }
-    const int wgrid = std::max(1, std::min((g.N * 32 + 255) / 256, sms * 8));
-    k_gnnt_prep<<<wgrid, 256, 0, st>>>(g);
-    const int nchunk = (g.N + 1023) / 1024;
-    k_gnnt_scan1<<<nchunk, 1024, 0, st>>>(g);
-    k_gnnt_scan2<<<1, 1024, 0, st>>>(g, nchunk);
-    k_gnnt_compact<<<wgrid, 256, 0, st>>>(g);
-    k_gnnt_erev<<<sms * 4, 256, 0, st>>>(g);
+    enqueue_gnn_compact(g, st);
     const int tgrid = 2 * sms;
     for (int t = 0; t < g.T; ++t) {
         k_gnnt_fe<<<tgrid, TT, SMEM_TC, st>>>(g, t);

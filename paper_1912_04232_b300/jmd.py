@@ -71,7 +71,7 @@ class md_bp_model(C.Structure):
 
 class md_gnn_model(C.Structure):
     _fields_ = [("params", C.c_void_p), ("H", C.c_int), ("T", C.c_int), ("r_cut", C.c_float), ("ws", C.c_void_p),
-                ("ws_bytes", C.c_size_t)]
+                ("ws_bytes", C.c_size_t), ("sys_n", C.c_int)]
 
 
 class md_fire_params(C.Structure):
@@ -146,6 +146,8 @@ _SIGS = {
     "md_bp_set_tensor_cores": [C.c_int],
     "md_gnn_set_group": [C.c_int],
     "md_gnn_set_tensor_cores": [C.c_int],
+    "md_gnn_train_grad": [_P(md_space), _vp, _P(md_nbr), _P(md_gnn_model), _vp, _vp, _vp, C.c_size_t, _vp, _vp,
+                          _vp],
     "md_bp_forces": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
     "md_bp_jvp": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp, _vp],
     "md_bp_mlp_train": [_vp, _vp, _vp, _vp, _vp, C.c_float, C.c_int, _vp, _vp, _vp],
@@ -188,6 +190,8 @@ _lib.md_nhc_state_doubles.restype = C.c_size_t
 _lib.md_nhc_state_doubles.argtypes = [C.c_int]
 _lib.md_gnn_param_count.restype = C.c_size_t
 _lib.md_gnn_param_count.argtypes = [C.c_int, C.c_int]
+_lib.md_gnn_train_scratch_bytes.restype = C.c_size_t
+_lib.md_gnn_train_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
 _lib.md_gnn_workspace_bytes.restype = C.c_size_t
 _lib.md_gnn_workspace_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
 _lib.md_version.restype = C.c_char_p
@@ -444,13 +448,25 @@ def md_gnn_workspace_bytes(N, cap, H, T):
     return int(_lib.md_gnn_workspace_bytes(int(N), int(cap), int(H), int(T)))
 
 
+def md_gnn_train_scratch_bytes(N, cap, H, T):
+    return int(_lib.md_gnn_train_scratch_bytes(int(N), int(cap), int(H), int(T)))
+
+
+def md_gnn_train_grad(space, r, nb, model, cE, dF, scratch, grad, status=None, stream=None):
+    """model: a GNNModel (its md_gnn_model is passed); scratch: a 256-byte
+    aligned uint8 tensor."""
+    _check(_lib.md_gnn_train_grad(C.byref(space), _ptr(r), C.byref(nb), C.byref(model.model), _ptr(cE), _ptr(dF),
+                                  _ptr(scratch), int(scratch.numel()), _ptr(grad), _ptr(status), _stream(stream)),
+           "md_gnn_train_grad")
+
+
 class GNNModel:
     """Workspace of the graph-network potential for a list of N atoms with
     row capacity cap, and the md_pot that points at the model (kind
     MD_GNN).  params: FP32 CUDA tensor of md_gnn_param_count(H, T) floats,
     owned by the caller."""
 
-    def __init__(self, params, N, cap, H=64, T=2, r_cut=3.77, device="cuda"):
+    def __init__(self, params, N, cap, H=64, T=2, r_cut=3.77, device="cuda", sys_n=0):
         import torch
         n = md_gnn_param_count(H, T)
         if n == 0 or params.numel() != n:
@@ -460,7 +476,8 @@ class GNNModel:
             raise MDError(MD_ERR_INVALID, "GNNModel: unsupported N, cap, H or T")
         self.params = params
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
-        self.model = md_gnn_model(_ptr(params).value, int(H), int(T), float(r_cut), _ptr(self.ws).value, nbytes)
+        self.model = md_gnn_model(_ptr(params).value, int(H), int(T), float(r_cut), _ptr(self.ws).value, nbytes,
+                                  int(sys_n))
         self.pot = md_pot()
         self.pot.kind = MD_GNN
         self.pot.model = C.cast(C.pointer(self.model), C.c_void_p)

@@ -133,6 +133,31 @@ def _batch_list(ds: Dataset, s0: int, S: int):
     return nb
 
 
+def batch_list_view(ds: Dataset, s0: int, S: int):
+    """md_nbr view of snapshots [s0, s0 + S) as one concatenated system
+    (rows local to each snapshot) with a workspace planned for the S n
+    atoms, so that md_energy_forces can run on it (the force kernels'
+    reductions live there)."""
+    torch = _t()
+    n = ds.n
+    key = ("view_ws", S)
+    cache = getattr(ds, "_view_ws", None)
+    if cache is None:
+        cache = {}
+        ds._view_ws = cache
+    if key not in cache:
+        space = J.md_space_periodic(3, [ds.L] * 3)
+        big = J.md_nbr_plan(space, S * n, BP_RC, SKIN, CAP)
+        ws = torch.zeros(int(big.ws_bytes) + 256, dtype=torch.uint8, device=ds.nbr.device)   # control words start at 0
+        cache[key] = (big, ws, ws[(-ws.data_ptr()) % 256:][: int(big.ws_bytes)])
+    big, _, wsv = cache[key]
+    nb = J.md_nbr.from_buffer_copy(big)
+    nb.nbr = ds.nbr[s0 * n:(s0 + S) * n].data_ptr()
+    nb.cnt = ds.cnt[s0 * n:(s0 + S) * n].data_ptr()
+    nb.ws = wsv.data_ptr()
+    return nb
+
+
 class Trainer:
     """Adam on the FP32 packed parameters; batches of contiguous snapshots."""
 

@@ -1,0 +1,79 @@
+"""GPU parity of the graph network's training gradient (Sec. 4.1: energy +
+force fit): the loss and its full parameter gradient (forward with the
+position tangent, reverse through values and tangents, fixed-order weight
+sums) against the FP64 double backward of the oracle, on a batch of
+concatenated snapshots with rows local to each."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import dev, status_word, to_dev
+from oracle import gnn as G
+
+pytestmark = pytest.mark.gpu
+
+RC = 3.77
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1912_04232_b300 as P
+    return P
+
+
+def _batch(S, n_side, seed):
+    snaps = [W.sw_silicon(n_side, T_K=0, jitter=0.25, seed=seed + k) for k in range(S)]
+    rng = np.random.Generator(np.random.PCG64(seed + 99))
+    n = snaps[0].N
+    Eref = rng.normal(-0.2 * n, 0.5, size=S)
+    Fref = rng.normal(0.0, 0.3, size=(S, n, 3))
+    return snaps, Eref, Fref
+
+
+def _gpu_loss_grad(P, snaps, Eref, Fref, p32, H, T, wF):
+    import torch
+    import paper_1912_04232_b300.learned as LP
+    S, n, L = len(snaps), snaps[0].N, snaps[0].L
+    r = torch.stack([to_dev(s_.r, torch.float32) for s_ in snaps])
+    ds = LP.Dataset(r=r, F=None, E=None, T=np.zeros(S), L=L, n=n)
+    LP.build_lists(ds)
+    nb = LP.batch_list_view(ds, 0, S)
+    space = P.md_space_periodic(3, [L] * 3)
+    N = S * n
+    m = P.GNNModel(to_dev(p32, torch.float32), N, int(nb.cap), H, T, RC, sys_n=n)
+    rf = r.reshape(N, 4)
+    f = torch.zeros((N, 4), dtype=torch.float32, device=dev())
+    st = status_word()
+    P.md_energy_forces(space, m.pot, rf, nb, f, None, st)
+    Fr = torch.zeros((N, 4), dtype=torch.float32, device=dev())
+    Fr[:, :3] = to_dev(Fref.reshape(N, 3), torch.float32)
+    Er = to_dev(np.asarray(Eref, np.float64), torch.float64)
+    cE = torch.zeros(N, dtype=torch.float32, device=dev())
+    dF = torch.zeros((N, 4), dtype=torch.float32, device=dev())
+    loss = torch.zeros(2 * S, dtype=torch.float64, device=dev())
+    Ei = f[:, 3].contiguous()
+    P.md_bp_loss_prep(Ei, f, Fr, Er, S, n, wF, cE, dF, loss)
+    nbytes = P.md_gnn_train_scratch_bytes(N, int(nb.cap), H, T)
+    scratch = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev())
+    sv = scratch[(-scratch.data_ptr()) % 256:]
+    grad = torch.zeros(P.md_gnn_param_count(H, T), dtype=torch.float32, device=dev())
+    P.md_gnn_train_grad(space, rf, nb, m, cE, dF, sv, grad, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    return float(loss.sum().item()), grad.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("T,S,seed", [(2, 3, 0), (1, 2, 5), (3, 2, 7)])
+def test_training_gradient_matches_double_backward(P, T, S, seed):
+    H, wF = 64, 0.8
+    snaps, Eref, Fref = _batch(S, 2, seed)
+    p32 = W.gnn_params(H, T, seed=seed + 1, out_scale=1.0)
+    lg, gg = _gpu_loss_grad(P, snaps, Eref, Fref, p32, H, T, wF)
+    batch = [(s_.r[:, :3].astype(np.float64), float(s_.L), Eref[k], Fref[k]) for k, s_ in enumerate(snaps)]
+    lo, go = G.loss_and_grads(batch, p32.astype(np.float64), H, T, RC, w_F=wF)
+    assert abs(lg - lo) <= 1e-4 * abs(lo), (lg, lo)
+    rel = np.linalg.norm(gg - go) / np.linalg.norm(go)
+    cos = float(gg @ go / (np.linalg.norm(gg) * np.linalg.norm(go)))
+    assert rel <= 1e-3 and cos >= 0.99999, (rel, cos)
+    # every parameter block carries gradient (none left at zero)
+    assert np.count_nonzero(gg) >= 0.9 * gg.size
