@@ -271,6 +271,68 @@ class Trainer:
         return math.sqrt(e2 / cnt), math.sqrt(f2 / cnt)
 
 
+class GNNTrainer(Trainer):
+    """The graph-network potential (Sec. 4.1: the GNN fitted to energies and
+    forces with Adam) on the same data: forward by md_energy_forces on the
+    concatenated batch (rows local to each snapshot), loss terms by the
+    loss kernel, the parameter gradient by md_gnn_train_grad (forward with
+    the force-error tangent, reverse through values and tangents), Adam.
+    Epochs, learning-rate decay and evaluation are the BP trainer's."""
+
+    def __init__(self, ds: Dataset, batch=16, lr=1e-3, wF=1.0, seed=0, device="cuda", params=None, H=64, T=2,
+                 init_bias=True):
+        torch = _t()
+        import workloads as W
+        self.ds, self.B, self.lr, self.wF = ds, batch, lr, wF
+        self.H, self.T = H, T
+        n = ds.n
+        N = batch * n
+        if params is None:
+            params = torch.from_numpy(W.gnn_params(H, T, seed=seed, out_scale=0.1)).to(device)
+        self.params = params
+        self.n_params = J.md_gnn_param_count(H, T)
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.grad = torch.zeros_like(params)
+        self.space = J.md_space_periodic(3, [ds.L] * 3)
+        self.model = J.GNNModel(params, N, CAP, H, T, BP_RC, device=device, sys_n=n)
+        self.Ei = torch.zeros(N, dtype=torch.float32, device=device)
+        self.Fp = torch.zeros((N, 4), dtype=torch.float32, device=device)
+        self.cE = torch.zeros(N, dtype=torch.float32, device=device)
+        self.dF = torch.zeros((N, 4), dtype=torch.float32, device=device)
+        self.loss = torch.zeros(2 * batch, dtype=torch.float64, device=device)
+        nbytes = J.md_gnn_train_scratch_bytes(N, CAP, H, T)
+        self._scratch = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        self.scratch = self._scratch[(-self._scratch.data_ptr()) % 256:][:nbytes]
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.step_count = 0
+        if init_bias:
+            # read-out bias c (the last parameter): mean energy per atom of the data
+            stats = torch.zeros(2, dtype=torch.float32, device=device)
+            e32 = (ds.E / ds.n).float().contiguous()
+            J.md_column_stats(e32, ds.E.shape[0], 1, stats)
+            self.params[self.n_params - 1:self.n_params].copy_(stats[0:1])
+
+    def forward(self, s0, S):
+        ds, n = self.ds, self.ds.n
+        N = S * n
+        nb = batch_list_view(ds, s0, S)
+        r = ds.r[s0:s0 + S].reshape(N, 4)
+        J.md_energy_forces(self.space, self.model.pot, r, nb, self.Fp[:N], None, self.status)
+        self.Ei[:N].copy_(self.Fp[:N, 3])
+        J.md_bp_loss_prep(self.Ei[:N], self.Fp[:N], ds.F[s0:s0 + S].reshape(N, 4), ds.E[s0:s0 + S], S, n, self.wF,
+                          self.cE[:N], self.dF[:N], self.loss[:2 * S])
+        return nb, r, N
+
+    def step(self, s0):
+        nb, r, N = self.forward(s0, self.B)
+        J.md_gnn_train_grad(self.space, r, nb, self.model, self.cE[:N], self.dF[:N], self.scratch, self.grad,
+                            self.status)
+        self.step_count += 1
+        J.md_adam_step(self.params, self.grad, self.m, self.v, self.n_params, self.lr, 0.9, 0.999, 1e-8,
+                       self.step_count)
+
+
 def force_rmse_sw2body(ds: Dataset, idx_lo, idx_hi, device="cuda"):
     """RMSE of the SW two-body forces alone (lambda = 0) against full SW,
     through the loss kernel (force term only)."""

@@ -77,3 +77,28 @@ def test_training_gradient_matches_double_backward(P, T, S, seed):
     assert rel <= 1e-3 and cos >= 0.99999, (rel, cos)
     # every parameter block carries gradient (none left at zero)
     assert np.count_nonzero(gg) >= 0.9 * gg.size
+
+
+@pytest.fixture(scope="module")
+def trained_gnn():
+    import paper_1912_04232_b300.learned as LP
+    temps = np.linspace(500.0, 3000.0, 8)
+    ds = LP.generate_sw_dataset(temps, n_snap=40, stride=20, equil=500, seed=1)
+    LP.build_lists(ds)
+    S = ds.r.shape[0]
+    n_train = int(0.8 * S)
+    tr = LP.GNNTrainer(ds, batch=8, lr=3e-3, wF=1.0, seed=0)
+    untrained = tr.evaluate(n_train, S)
+    tr.train(0, n_train, epochs=40, seed=0, lr_end=1e-4)
+    trained = tr.evaluate(n_train, S)
+    two_body = LP.force_rmse_sw2body(ds, n_train, S)
+    return dict(untrained=untrained, trained=trained, two_body=two_body)
+
+
+def test_trained_gnn_beats_two_body_and_untrained(trained_gnn):
+    # trained on the GPU by md_gnn_train_grad + Adam on SW silicon at 500-3000 K
+    fr = trained_gnn["trained"][1]
+    print("GNN force RMSE eV/A: trained %.4f untrained %.4f two-body %.4f; energy RMSE trained %.4f eV/atom"
+          % (fr, trained_gnn["untrained"][1], trained_gnn["two_body"], trained_gnn["trained"][0]))
+    assert fr * 3.0 <= trained_gnn["untrained"][1]
+    assert fr * 3.0 <= trained_gnn["two_body"]
