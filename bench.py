@@ -158,8 +158,9 @@ def run_reference(args, rank):
 
 
 def learned_section():
-    """Train the BP network on GPU-generated SW data, then run NVE at
-    N = 64,000 atoms with plain SW and with the learned potential."""
+    """Train the BP network (and the graph network) on GPU-generated SW
+    data, then run NVE at N = 64,000 atoms with plain SW and with the
+    learned potentials."""
     import paper_1912_04232_b300.learned as LP
     temps = np.linspace(500.0, 3000.0, 8)
     t0 = time.perf_counter()
@@ -173,6 +174,14 @@ def learned_section():
     two = LP.force_rmse_sw2body(ds, ntr, S)
     t_train = time.perf_counter() - t0
     dep = LP.deploy_compare(tr.params, tr.norm, n_side=20, T=1000.0, steps=200, warmup=20)
+    # the graph network on the same data (trained by md_gnn_train_grad + Adam)
+    t1 = time.perf_counter()
+    gt = LP.GNNTrainer(ds, batch=8, lr=3e-3, wF=1.0, seed=0, H=64, T=2)
+    g_untrained = gt.evaluate(ntr, S)
+    gt.train(0, ntr, epochs=200, seed=0, lr_end=1e-4)
+    g_e, g_f = gt.evaluate(ntr, S)
+    t_gnn = time.perf_counter() - t1
+    gdep = LP.gnn_deploy_compare(gt.params, H=64, T=2, n_side=20, temp=1000.0, steps=100, warmup=10)
     return {
         "sw_particle_steps_per_s": dep["sw_particle_steps_per_s"],
         "learned_particle_steps_per_s": dep["learned_tc_particle_steps_per_s"],
@@ -182,6 +191,9 @@ def learned_section():
         "force_rmse_sw_two_body_only": two, "force_rmse_vs_sw_at_deploy": dep["force_rmse_vs_sw_final_eV_per_A"],
         "deploy": {"N": dep["N"], "T_K": 1000.0, "steps": 200, "dt_fs": 1.0, "network": "tcgen05 BF16"},
         "train": {"snapshots": int(S), "heldout": int(S - ntr), "epochs": 40, "seconds_incl_data": t_train},
+        "gnn": {"force_rmse_eV_per_A_heldout": g_f, "energy_rmse_eV_per_atom_heldout": g_e,
+                "force_rmse_untrained": g_untrained[1], "epochs": 200, "seconds": t_gnn, "H": 64, "T": 2,
+                "deploy": gdep},
     }
 
 

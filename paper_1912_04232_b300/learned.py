@@ -1,6 +1,6 @@
 """Learned potential workflow (Sec. 4.1): data from the plain Stillinger-
-Weber simulator, training of the Behler-Parrinello network with the energy +
-force loss, evaluation, and deployment in MD.
+Weber simulator, training of the Behler-Parrinello network and of the graph
+network with the energy + force loss, evaluation, and deployment in MD.
 
 Every arithmetic step runs in libjmd kernels (Langevin/NVE integrators, SW
 and learned forces, descriptors, network forward / double backward, loss
@@ -414,4 +414,52 @@ def deploy_compare(params, norm, n_side=20, T=1000.0, steps=200, warmup=20, dt=1
     code = J.md_status_poll(st)
     if code:
         raise J.MDError(code, "deploy_compare")
+    return out
+
+
+def gnn_deploy_compare(params, H=64, T=2, n_side=20, temp=1000.0, steps=200, warmup=20, dt=1.0, seed=0,
+                       device="cuda"):
+    """NVE of the n_side^3-cell diamond at temperature temp with the trained
+    graph network, FP32 kernels and tcgen05 kernels (the latter hold the
+    weights rounded to BF16).  Returns particle-steps/s of each and the
+    force RMSE against plain SW on the final configurations."""
+    torch = _t()
+    import workloads as W
+    si = W.sw_silicon(n_side, T_K=temp, seed=seed)
+    N, L = si.N, si.L
+    space = J.md_space_periodic(3, [L] * 3)
+    st = torch.zeros(1, dtype=torch.int32, device=device)
+    model = J.GNNModel(params, N, 64, H, T, BP_RC, device=device)
+    sw = J.sw_pot(SW_SI)
+    cE = torch.zeros(N, dtype=torch.float32, device=device)
+    dF = torch.zeros((N, 4), dtype=torch.float32, device=device)
+    loss = torch.zeros(2, dtype=torch.float64, device=device)
+    zeros = torch.zeros(N, dtype=torch.float32, device=device)
+    Edummy = torch.zeros(1, dtype=torch.float64, device=device)
+    out = {"N": N, "T_K": temp, "steps": steps, "dt_fs": dt, "H": H, "T": T}
+    for name, tc in (("gnn_fp32", False), ("gnn_tc", True)):
+        J.md_gnn_set_tensor_cores(tc)
+        nl = J.NeighborList(space, N, BP_RC, 0.3, 64, device=device)
+        r = torch.from_numpy(si.r).to(device)
+        v = torch.from_numpy(si.v).to(device)
+        f = torch.zeros_like(r)
+        nl.build(r, st)
+        J.md_energy_forces(space, model.pot, r, nl.plan, f, None, st)
+        J.md_integrate_nve(space, model.pot, r, v, f, MASS_SI, dt, warmup, nl.plan, None, None, True, st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        J.md_integrate_nve(space, model.pot, r, v, f, MASS_SI, dt, steps, nl.plan, None, None, True, st)
+        e1.record()
+        e1.synchronize()
+        out[name + "_particle_steps_per_s"] = N * steps / (e0.elapsed_time(e1) * 1e-3)
+        fs = torch.zeros((N, 4), dtype=torch.float32, device=device)
+        fg = torch.zeros((N, 4), dtype=torch.float32, device=device)
+        J.md_energy_forces(space, sw, r, nl.plan, fs, None, st)
+        J.md_energy_forces(space, model.pot, r, nl.plan, fg, None, st)
+        J.md_bp_loss_prep(zeros, fg, fs, Edummy, 1, N, 1.0, cE, dF, loss)
+        out[name + "_force_rmse_vs_sw_final_eV_per_A"] = math.sqrt(loss[1].item())
+    J.md_gnn_set_tensor_cores(False)
+    code = J.md_status_poll(st)
+    if code:
+        raise J.MDError(code, "gnn_deploy_compare")
     return out
