@@ -97,6 +97,41 @@ def generate_sw_dataset(temps, n_snap, stride=20, equil=2000, n_side=4, a=5.431,
     return Dataset(r=R[pt].contiguous(), F=F[pt].contiguous(), E=E[pt].contiguous(), T=Ts[perm], L=L, n=n)
 
 
+def augment_cubic(ds: Dataset, idx_lo, idx_hi, copies, seed=0, keep=None):
+    """Snapshots [idx_lo, idx_hi) under `copies` random symmetry operations
+    each of the periodic cubic box (axis permutations and reflections, the
+    periodic form of the random rotations and flips the paper trains its
+    graph network with: that network is not rotation invariant), followed
+    by the snapshots `keep` = (lo, hi) unchanged (held out).  Energies are
+    unchanged, positions mapped and wrapped into [0, L), forces mapped."""
+    torch = _t()
+    rng = np.random.default_rng(seed)
+    L = float(ds.L)
+    R, F, E, T = [], [], [], []
+    for s in range(idx_lo, idx_hi):
+        for _ in range(copies):
+            perm = torch.as_tensor(rng.permutation(3), device=ds.r.device)
+            sign = torch.as_tensor(rng.choice([-1.0, 1.0], 3), dtype=torch.float32, device=ds.r.device)
+            r = ds.r[s].clone()
+            x = ds.r[s][:, perm] * sign
+            x = torch.remainder(x, L)
+            r[:, :3] = torch.where(x >= L, x - L, x)
+            f = ds.F[s].clone()
+            f[:, :3] = ds.F[s][:, perm] * sign
+            R.append(r)
+            F.append(f)
+            E.append(ds.E[s:s + 1])
+            T.append(ds.T[s])
+    if keep is not None:
+        for s in range(*keep):
+            R.append(ds.r[s])
+            F.append(ds.F[s])
+            E.append(ds.E[s:s + 1])
+            T.append(ds.T[s])
+    return Dataset(r=torch.stack(R).contiguous(), F=torch.stack(F).contiguous(), E=torch.cat(E).contiguous(),
+                   T=np.asarray(T), L=ds.L, n=ds.n)
+
+
 def build_lists(ds: Dataset, device="cuda"):
     """One neighbor list (r_list = 3.77 + 0.3 A) per snapshot, rows local to
     the snapshot, concatenated."""
