@@ -277,15 +277,20 @@ __global__ void __launch_bounds__(256) k_fa_sums(FaArgs f)
         last = atomicAdd(&f.a.ctl[CTL_TICKET], 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
     double S0 = 0.0, S1 = 0.0, S2 = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
         const volatile double *p = (const volatile double *)(f.a.partials + 2 * b);
         S0 += p[0];
         S1 += p[1];
         S2 += p[2];
     }
+    __shared__ double shs[3][8];
+    S0 = block_sum_f64(S0, shs[0]);
+    S1 = block_sum_f64(S1, shs[1]);
+    S2 = block_sum_f64(S2, shs[2]);
+    if (threadIdx.x != 0) return;
     f.a.ctl[CTL_TICKET] = 0u;
     f.scal[0] = S0;
     f.scal[1] = S1;

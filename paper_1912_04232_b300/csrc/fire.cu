@@ -111,12 +111,15 @@ __global__ void __launch_bounds__(256) k_fire_power(float4 *v, const float4 *f, 
         last = atomicAdd(&h->ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
-    // the FIRE rules, one thread, partials summed in block order
+    // partials summed by the whole last block (fixed order), then the FIRE
+    // rules in one thread
     double S[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < (int)gridDim.x; ++b)
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
         for (int c = 0; c < 3; ++c) S[c] += ((volatile double *)part)[3 * b + c];
+    for (int c = 0; c < 3; ++c) S[c] = block_sum_f64(S[c], sh[c]);
+    if (threadIdx.x != 0) return;
     h->ticket = 0u;
     if (!isfinite(S[0]) || !isfinite(S[1]) || !isfinite(S[2])) raise_status(status, MD_ERR_NONFINITE);
     const double alpha = h->alpha;

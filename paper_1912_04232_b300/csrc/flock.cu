@@ -196,10 +196,13 @@ __global__ void __launch_bounds__(256) k_flock_step(FlockArgs a)
         last = atomicAdd(&a.ctl[CTL_TICKET], 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
+    // the block partials summed by the whole last block (fixed order)
     double E = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) E += ((volatile double *)(a.partials + b))[0];
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) E += ((volatile double *)(a.partials + b))[0];
+    E = block_sum_f64(E, sh);
+    if (threadIdx.x != 0) return;
     for (int q = 0; q < a.n_pred; ++q) E += (double)a.pred_out[q].w;
     a.ctl[CTL_TICKET] = 0u;
     if (!isfinite(E)) raise_status(a.status, MD_ERR_NONFINITE);
