@@ -35,6 +35,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s (LJ N=256k); learned vs plain SW at stated force RMSE"
 UNIT = "particle-steps/s"
+# CUDA graphs for the MD loops of the sections (off with --no-graph, for profiling)
+USE_GRAPH = True
 
 
 def parse():
@@ -50,7 +52,7 @@ def parse():
     ap.add_argument("--tpp", type=int, default=0)
     ap.add_argument("--pair-opt", type=int, default=-1, help="pair-kernel variant (md_set_pair_options)")
     ap.add_argument("--no-graph", action="store_true",
-                    help="launch every kernel from the host, the FIRE and flocking loops too (profiling)")
+                    help="launch every kernel from the host, in every section (profiling)")
     ap.add_argument("--nve-fusion", type=int, default=1, help="1: kick-drift fused into the force kernel (md_set_nve_fusion)")
     ap.add_argument("--local-rows", type=int, default=0,
                     help="1: cell-centred forces over 16-bit local rows (MD_NBR_LOCAL_ROWS); 0: int32 rows")
@@ -404,7 +406,7 @@ def nhc_section(steps=200):
             nl.build(r, st)
             P.md_energy_forces(s, pot, r, nl.plan, f, None, st)
             P.md_integrate_nhc(s, pot, r, v, f, mass, dt, kT, 100.0 * dt, 3, steps, nl.plan, th, True, None, KE, H,
-                               True, st)
+                               USE_GRAPH, st)
             e1.record()
             e1.synchronize()
             if k:
@@ -473,7 +475,7 @@ def gnn_section(steps=100, H=64, T=2):
             P.md_energy_forces(s, model.pot, r, nl.plan, f, None, st)
             e1.record()
             P.md_integrate_nhc(s, model.pot, r, v, f, LP.MASS_SI, dt, kT, 100.0 * dt, 3, steps, nl.plan, th, True,
-                               None, KE, Hx, True, st)
+                               None, KE, Hx, USE_GRAPH, st)
             e2.record()
             e2.synchronize()
             if k:
@@ -614,6 +616,8 @@ def main():
         P.md_set_pair_options(args.pair_opt)
     P.md_set_nve_fusion(bool(args.nve_fusion))
     P.md_set_loop_graphs(not args.no_graph)
+    global USE_GRAPH
+    USE_GRAPH = not args.no_graph
     s = P.md_space_periodic(3, [c.L] * 3)
     nl = P.NeighborList(s, c.N, c.r_cut, c.skin, 128, local_rows=bool(args.local_rows))
     pot = P.lj_pot(c.eps, c.sigma, c.r_cut, True)
