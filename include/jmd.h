@@ -608,6 +608,16 @@ JMD_API uint64_t md_launch_count(void);
  * The same bounded-wait rule guards every device wait in the library. */
 JMD_API md_status md_bounded_wait(const uint32_t *d_flag, uint64_t limit, uint32_t *d_status, md_stream_t stream);
 
+/* FP32 FMA throughput probe (measurement only, not a step of the path):
+ * launches `blocks` x `threads` threads, each running 8 independent chains of
+ * `iters` fused multiply-adds, and writes one float per thread to d_out
+ * (caller-owned, blocks*threads floats).  *flops (host, may be NULL)
+ * receives the FLOP count of the launch (an FMA counts 2).  Timing it with
+ * events on `stream` gives the FP32 peak that ALU-bound kernels are compared
+ * against.  MD_ERR_INVALID for a null d_out, blocks <= 0, iters <= 0 or
+ * threads not a multiple of 32 in [32, 1024]. */
+JMD_API md_status md_fma_probe(float *d_out, int blocks, int threads, int iters, uint64_t *flops, md_stream_t stream);
+
 /* Library version string. */
 JMD_API const char *md_version(void);
 

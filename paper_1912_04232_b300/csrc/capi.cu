@@ -75,3 +75,35 @@ extern "C" md_status md_bounded_wait(const uint32_t *d_flag, uint64_t limit, uin
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
 }
+
+// FP32 FMA throughput probe, the denominator of the ALU-bound rooflines:
+// every thread runs FMA_CHAINS independent recurrences x <- x*a + b, enough
+// independent work per warp to cover the FMA latency on every FP32 lane.
+// The sums are stored so that no chain can be dropped.
+#define FMA_CHAINS 8
+__global__ void __launch_bounds__(1024) k_fma_probe(float *out, int iters, float a, float b)
+{
+    float x[FMA_CHAINS];
+#pragma unroll
+    for (int k = 0; k < FMA_CHAINS; ++k) x[k] = 1e-3f * (float)(threadIdx.x + k);
+#pragma unroll 8
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < FMA_CHAINS; ++k) x[k] = fmaf(x[k], a, b);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < FMA_CHAINS; ++k) s += x[k];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+extern "C" md_status md_fma_probe(float *d_out, int blocks, int threads, int iters, uint64_t *flops,
+                                  md_stream_t stream)
+{
+    if (!d_out || blocks <= 0 || threads < 32 || threads > 1024 || threads % 32 || iters <= 0)
+        return MD_ERR_INVALID;
+    k_fma_probe<<<blocks, threads, 0, (cudaStream_t)stream>>>(d_out, iters, 0.999f, 1e-3f);
+    JMD_CUDA_TRY(cudaGetLastError());
+    if (flops) *flops = 2ull * FMA_CHAINS * (uint64_t)iters * (uint64_t)threads * (uint64_t)blocks;
+    return MD_OK;
+}

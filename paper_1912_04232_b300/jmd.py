@@ -140,6 +140,7 @@ _SIGS = {
                          C.c_int, _P(md_nbr), _vp, C.c_int, _vp, _vp, _vp, C.c_int, _vp, _vp],
     "md_status_poll": [_vp, _P(C.c_uint32), _vp],
     "md_bounded_wait": [_vp, C.c_uint64, _vp, _vp],
+    "md_fma_probe": [_vp, C.c_int, C.c_int, C.c_int, _P(C.c_uint64), _vp],
     "md_bp_descriptors": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp],
     "md_bp_mlp_infer": [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp],
     "md_bp_mlp_infer_tc": [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp],
@@ -581,6 +582,14 @@ def md_status_poll(status, stream=None) -> int:
 
 def md_bounded_wait(flag, limit, status, stream=None):
     _check(_lib.md_bounded_wait(_ptr(flag), int(limit), _ptr(status), _stream(stream)), "md_bounded_wait")
+
+
+def md_fma_probe(out, blocks, threads, iters, stream=None) -> int:
+    """Launch the FP32 FMA throughput probe; returns the launch's FLOP count."""
+    fl = C.c_uint64(0)
+    _check(_lib.md_fma_probe(_ptr(out), int(blocks), int(threads), int(iters), C.byref(fl), _stream(stream)),
+           "md_fma_probe")
+    return int(fl.value)
 
 
 def md_launch_count() -> int:
