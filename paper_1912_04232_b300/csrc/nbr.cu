@@ -278,13 +278,13 @@ __device__ void build_row_warp(const NbrArgs &a, int i, int c, int *row)
 // the particle index in the w lane (k_sort_cells), and padded with NaN
 // positions to whole sweep steps (a NaN fails every distance test, so the
 // sweep needs no bounds check).  Each warp takes particles of the cell and
-// sweeps the candidates 64 at a time (two ballots), writing hits straight
+// sweeps the candidates 128 at a time (four ballots), writing hits straight
 // into the padded int32 row and, when the list keeps local rows, each hit's
 // index into the staged array into the 16-bit row.  The row order is a
 // deterministic function of the positions and the cell grid.
 // ---------------------------------------------------------------------------
 constexpr int BUILD_WARPS = 4;
-constexpr int BUILD_CHUNK = 64;   // candidates per sweep step (two per lane)
+constexpr int BUILD_CHUNK = 128;  // candidates per sweep step (BUILD_CHUNK / 32 per lane)
 static_assert(STAGE_CMAX % BUILD_CHUNK == 0, "the padding must fit the staging buffer");
 __device__ __forceinline__ int padded_m(int M) { return (M + BUILD_CHUNK - 1) / BUILD_CHUNK * BUILD_CHUNK; }
 
@@ -293,7 +293,7 @@ __device__ __forceinline__ int padded_m(int M) { return (M + BUILD_CHUNK - 1) / 
 // rint(t * Linv) = 0 and the plain difference is the nearest-image
 // displacement; MODE 1, positions inside [0, L) (min_image_near); MODE 0,
 // the general formula.
-template <int DIM, int MODE>
+template <int DIM, int MODE, bool LOCAL>
 __device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand, const uint16_t *lidx,
                                            const StencilInfo &inf)
 {
@@ -306,12 +306,13 @@ __device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand,
         const int i = __float_as_int(ri.w);
         int count = 0;
         int32_t *out = a.nbr + (size_t)i * a.cap;
-        uint16_t *lout = lidx ? a.lrow + (size_t)i * a.cap : nullptr;
+        uint16_t *lout = LOCAL ? a.lrow + (size_t)i * a.cap : nullptr;
         for (int k0 = 0; k0 < M; k0 += BUILD_CHUNK) {
-            bool hit[2];
-            int j[2];
+            constexpr int BU = BUILD_CHUNK / 32;
+            bool hit[BU];
+            int j[BU];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < BU; ++u) {
                 const float4 c = cand[k0 + 32 * u + lane];
                 j[u] = __float_as_int(c.w);
                 float dx, dy, dz;
@@ -321,12 +322,12 @@ __device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand,
                 hit[u] = (j[u] != i) && (r2 < a.r_list2);
             }
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < BU; ++u) {
                 const unsigned mk = __ballot_sync(0xffffffffu, hit[u]);
                 const int pos = count + __popc(mk & lt);
                 if (hit[u] && pos < a.cap) {
                     out[pos] = j[u];
-                    if (lout) lout[pos] = lidx[k0 + 32 * u + lane];
+                    if (LOCAL) lout[pos] = lidx[k0 + 32 * u + lane];
                 }
                 count += __popc(mk);
             }
@@ -334,7 +335,7 @@ __device__ __forceinline__ int build_sweep(const NbrArgs &a, const float4 *cand,
         const int n = count < a.cap ? count : a.cap;
         for (int k = n + lane; k < a.cap; k += 32) {
             out[k] = a.N;
-            if (lout) lout[k] = LROW_PAD;
+            if (LOCAL) lout[k] = LROW_PAD;
         }
         if (lane == 0) {
             a.cnt[i] = count;
@@ -409,10 +410,16 @@ __global__ void __launch_bounds__(BUILD_WARPS * 32) k_build_cells(NbrArgs a)
         for (int k = M + tid; k < padded_m(M); k += BUILD_WARPS * 32)
             cand[k] = make_float4(nan, nan, nan, __int_as_float(-1));
         __syncthreads();
-        const uint16_t *li = local ? lidx : nullptr;
-        wmax = inf.inner   ? build_sweep<DIM, 2>(a, cand, li, inf)
-               : a.wrapped ? build_sweep<DIM, 1>(a, cand, li, inf)
-                           : build_sweep<DIM, 0>(a, cand, li, inf);
+        // the local-row stores are a template switch, so the plain sweep
+        // carries no branch for them
+        if (local)
+            wmax = inf.inner   ? build_sweep<DIM, 2, true>(a, cand, lidx, inf)
+                   : a.wrapped ? build_sweep<DIM, 1, true>(a, cand, lidx, inf)
+                               : build_sweep<DIM, 0, true>(a, cand, lidx, inf);
+        else
+            wmax = inf.inner   ? build_sweep<DIM, 2, false>(a, cand, nullptr, inf)
+                   : a.wrapped ? build_sweep<DIM, 1, false>(a, cand, nullptr, inf)
+                               : build_sweep<DIM, 0, false>(a, cand, nullptr, inf);
     }
     // one atomic per CTA for the largest row count
     if (lane == 0 && wmax > 0) atomicMax(&bmax, wmax);
