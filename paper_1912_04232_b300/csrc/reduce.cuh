@@ -49,8 +49,7 @@ __device__ __forceinline__ void energy_epilogue(float pe_acc, float ke_acc, cons
         spe += p[0];
         ske += p[1];
     }
-    spe = block_sum_f64(spe, &sh[0][0]);
-    ske = block_sum_f64(ske, &sh[1][0]);
+    block_sum2_f64(spe, ske, &sh[0][0]);
     if (threadIdx.x == 0) {
         a.ctl[CTL_TICKET] = 0u;
         if (!isfinite(spe) || !isfinite(ske)) raise_status(a.status, MD_ERR_NONFINITE);
