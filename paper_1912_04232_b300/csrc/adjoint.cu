@@ -279,17 +279,16 @@ __global__ void __launch_bounds__(256) k_fa_sums(FaArgs f)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+    double S[3] = {0.0, 0.0, 0.0};
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
         const volatile double *p = (const volatile double *)(f.a.partials + 2 * b);
-        S0 += p[0];
-        S1 += p[1];
-        S2 += p[2];
+        S[0] += p[0];
+        S[1] += p[1];
+        S[2] += p[2];
     }
     __shared__ double shs[3][8];
-    S0 = block_sum_f64(S0, shs[0]);
-    S1 = block_sum_f64(S1, shs[1]);
-    S2 = block_sum_f64(S2, shs[2]);
+    block_sums_f64<3>(S, &shs[0][0], 8);
+    const double S0 = S[0], S1 = S[1], S2 = S[2];
     if (threadIdx.x != 0) return;
     f.a.ctl[CTL_TICKET] = 0u;
     f.scal[0] = S0;

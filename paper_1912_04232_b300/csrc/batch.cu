@@ -560,17 +560,17 @@ __global__ void __launch_bounds__(256) k_b_energy(BatchDev b, const float4 *v, c
                                                   int series_len, unsigned long long cond_while, int use_cond)
 {
     count_launch();
-    __shared__ double sh[32];
+    __shared__ double sh[2][32];
     __shared__ bool last;
     const int rep = blockIdx.x;
     const RepMeta &m = b.meta[rep];
-    double pe = 0.0, ke = 0.0;
+    double E[2] = {0.0, 0.0};
     for (int k = threadIdx.x; k < m.n; k += blockDim.x) {
-        pe += (double)f[m.p0 + k].w;
-        ke += (double)v[m.p0 + k].w;
+        E[0] += (double)f[m.p0 + k].w;
+        E[1] += (double)v[m.p0 + k].w;
     }
-    pe = block_sum_f64(pe, sh);
-    ke = block_sum_f64(ke, sh);
+    block_sums_f64<2>(E, &sh[0][0], 32);
+    const double pe = E[0], ke = E[1];
     const unsigned step = b.ctl[CTL_STEP];
     if (threadIdx.x == 0) {
         if (!isfinite(pe) || !isfinite(ke)) raise_status(b.status, MD_ERR_NONFINITE);

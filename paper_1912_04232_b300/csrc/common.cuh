@@ -231,34 +231,30 @@ __device__ __forceinline__ double block_sum_f64(double v, double *sh)
     return s;
 }
 
-// Two block sums at once, each in the order of block_sum_f64 (same bits):
-// the two dependency chains interleave, and the block synchronises twice
-// instead of four times.  Results valid in warp 0.
-__device__ __forceinline__ void block_sum2_f64(double &u, double &v, double *sh)
+// K block sums at once, each in the order of block_sum_f64 (same bits): the
+// K dependency chains interleave (an FP64 add has a long latency on this
+// GPU), and the block synchronises twice instead of 2K times.  sh holds K
+// rows of `stride` >= blockDim.x / 32 doubles.  Results valid in warp 0.
+template <int K>
+__device__ __forceinline__ void block_sums_f64(double (&v)[K], double *sh, int stride)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        u += __shfl_xor_sync(0xffffffffu, u, o);
-        v += __shfl_xor_sync(0xffffffffu, v, o);
-    }
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) {
-        sh[w] = u;
-        sh[32 + w] = v;
-    }
-    __syncthreads();
-    u = 0.0;
-    v = 0.0;
-    if (w == 0) {
-        int nw = blockDim.x >> 5;
-        u = (l < nw) ? sh[l] : 0.0;
-        v = (l < nw) ? sh[32 + l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            u += __shfl_xor_sync(0xffffffffu, u, o);
-            v += __shfl_xor_sync(0xffffffffu, v, o);
-        }
+        for (int c = 0; c < K; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0)
+#pragma unroll
+        for (int c = 0; c < K; ++c) sh[c * stride + w] = v[c];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < K; ++c) v[c] = (w == 0 && l < nw) ? sh[c * stride + l] : 0.0;
+    if (w == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < K; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
     }
 }
 

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) k_fire_power(float4 *v, const float4 *f, 
     double S[3] = {0.0, 0.0, 0.0};
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
         for (int c = 0; c < 3; ++c) S[c] += ((volatile double *)part)[3 * b + c];
-    for (int c = 0; c < 3; ++c) S[c] = block_sum_f64(S[c], sh[c]);
+    block_sums_f64<3>(S, &sh[0][0], 8);
     if (threadIdx.x != 0) return;
     h->ticket = 0u;
     if (!isfinite(S[0]) || !isfinite(S[1]) || !isfinite(S[2])) raise_status(status, MD_ERR_NONFINITE);

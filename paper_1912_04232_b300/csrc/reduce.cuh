@@ -43,13 +43,14 @@ __device__ __forceinline__ void energy_epilogue(float pe_acc, float ke_acc, cons
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double spe = 0.0, ske = 0.0;
+    double S[2] = {0.0, 0.0};
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
         const volatile double *p = (const volatile double *)(a.partials + b);
-        spe += p[0];
-        ske += p[1];
+        S[0] += p[0];
+        S[1] += p[1];
     }
-    block_sum2_f64(spe, ske, &sh[0][0]);
+    block_sums_f64<2>(S, &sh[0][0], 32);
+    const double spe = S[0], ske = S[1];
     if (threadIdx.x == 0) {
         a.ctl[CTL_TICKET] = 0u;
         if (!isfinite(spe) || !isfinite(ske)) raise_status(a.status, MD_ERR_NONFINITE);
