@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--pair-opt", type=int, default=-1, help="pair-kernel variant (md_set_pair_options)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel from the host, in every section (profiling)")
+    ap.add_argument("--no-fp32-peak", action="store_true", help="skip the FP32 FMA probe")
     ap.add_argument("--nve-fusion", type=int, default=1, help="1: kick-drift fused into the force kernel (md_set_nve_fusion)")
     ap.add_argument("--local-rows", type=int, default=0,
                     help="1: cell-centred forces over 16-bit local rows (MD_NBR_LOCAL_ROWS); 0: int32 rows")
@@ -776,7 +777,7 @@ def main():
         pass
 
     extra = {}
-    if rank == 0:
+    if rank == 0 and not args.no_fp32_peak:
         pk, src = fp32_peak()
         extra["fp32_fma_peak"] = {"tflops": pk, "source": src}
     if rank == 0 and not args.no_learned:
