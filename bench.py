@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain-SW section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-replica section")
     ap.add_argument("--no-fire", action="store_true", help="skip the FIRE minimisation section")
+    ap.add_argument("--no-packing", action="store_true",
+                    help="skip the packing section (Fig. 3 ensemble, gradient descent and its adjoint)")
     ap.add_argument("--no-nhc", action="store_true", help="skip the Nose-Hoover NVT section")
     ap.add_argument("--no-flock", action="store_true", help="skip the flocking section")
     ap.add_argument("--no-gnn", action="store_true", help="skip the graph-network potential section")
@@ -297,6 +299,111 @@ def batched_section(steps=500):
             "one_launch_particle_steps_per_s": Ntot * steps / (ms_b * 1e-3),
             "per_replica_launches_particle_steps_per_s": Ntot * steps / (ms_s * 1e-3),
             "speedup": ms_s / ms_b, "status": code}
+
+
+def packing_section(nseed=20):
+    """Sec. 4.2, Fig. 3, and the gradient-descent rows.  (i) The App. A
+    system (128 disks, half of diameter D and half of diameter 1, packing
+    fraction 0.9, 300 FIRE steps, reverse mode with K = 18 checkpoints) for
+    D = 0.60, 0.65, ..., 1.00 and the reciprocal peak ratio 1.25, `nseed`
+    seeded random starts each: the mean minimised energy (Fig. 3(b)) and
+    dE_final/dD (Fig. 3(c)).  Per-start derivatives through a minimisation
+    are heavy-tailed (a start near a saddle gives a huge value), so the
+    median and a trimmed mean are reported beside the mean.  (ii) The
+    configuration-2 packing (N = 1,024, D = 1.4, 2,000 gradient-descent
+    steps of 0.05): the forward minimisation and the adjoint
+    (K = ceil(sqrt(2000)) = 45) timed alone."""
+    import torch
+    import paper_1912_04232_b300 as P
+    import workloads as W
+    dev = torch.device("cuda")
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = {}
+    N, T, K, phi = 128, 300, 18, 0.9
+    wsz = P.md_fire_adjoint_workspace_size(N, T, K)
+    wsb = torch.empty(wsz + 256, dtype=torch.uint8, device=dev)
+    wsv = wsb[(-wsb.data_ptr()) % 256:]
+    rows, t_all = [], 0.0
+    for D in [0.6 + 0.05 * k for k in range(9)] + [1.25]:
+        L64 = W.packing_box(N, D, phi)
+        s = P.md_space_periodic(2, [W.f32(L64)] * 2)
+        Lp = (N // 2) * math.pi * D / (4 * phi * L64)
+        nl = P.NeighborList(s, N, max(D, 1.0), 0.3, 64, canonical=True)
+        Es, gs = [], []
+        for seed in range(nseed):
+            pk = W.packing_2d(N=N, D=D, phi=phi, seed=seed)
+            s0 = torch.zeros((N, 4), dtype=torch.float32, device=dev)
+            s0[:, :2] = torch.from_numpy(pk.s0.astype(np.float32)).to(dev)
+            ra, va, fa = (torch.zeros((N, 4), dtype=torch.float32, device=dev) for _ in range(3))
+            o = torch.zeros(2, dtype=torch.float64, device=dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            P.md_minimize_fire_adjoint(s, P.soft_pot(), P.fire_params(), nl.plan, s0, N // 2, D, 1.0, Lp, T, K,
+                                       ra, va, fa, wsv, o, st)
+            e1.record()
+            e1.synchronize()
+            t_all += e0.elapsed_time(e1)
+            oc = o.cpu().numpy()
+            Es.append(float(oc[0]))
+            gs.append(float(oc[1]))
+        g = np.sort(np.asarray(gs))
+        cut = len(g) // 10
+        rows.append({"D": round(D, 3), "E_mean": float(np.mean(Es)), "E_se": float(np.std(Es) / math.sqrt(nseed)),
+                     "dE_dD_median": float(np.median(g)), "dE_dD_trimmed_mean": float(np.mean(g[cut:len(g) - cut])),
+                     "dE_dD_mean": float(np.mean(g))})
+    scan = [r for r in rows if r["D"] <= 1.0]
+    out["fig3_app_a"] = {"N": N, "fire_steps": T, "starts_per_D": nseed, "curve": rows,
+                         "argmax_E_over_D_le_1": max(scan, key=lambda r: r["E_mean"])["D"],
+                         "argmin_E_over_D_le_1": min(scan, key=lambda r: r["E_mean"])["D"],
+                         "adjoint_runs_per_s": len(rows) * nseed / (t_all * 1e-3)}
+    # configuration 2: gradient descent and its adjoint, N = 1,024
+    N2, T2, K2, D2 = 1024, 2000, 45, 1.4
+    pk = W.packing_2d(N=N2, D=D2, phi=phi, seed=0)
+    L64 = W.packing_box(N2, D2, phi)
+    L = W.f32(L64)
+    s = P.md_space_periodic(2, [L, L])
+    nl = P.NeighborList(s, N2, D2, 0.3, 64)
+    x = np.zeros((N2, 4), np.float32)
+    x[:, :2] = (pk.s0 * L).astype(np.float32)
+    x[:, :2] = np.where(x[:, :2] >= L, 0.0, x[:, :2])
+    x[:, 3] = pk.diam.astype(np.float32)
+    x0 = torch.from_numpy(x).to(dev)
+    r, f = torch.empty_like(x0), torch.zeros_like(x0)
+    E = torch.zeros(T2 + 1, dtype=torch.float64, device=dev)
+    tg = []
+    for k in range(3):
+        r.copy_(x0)
+        nl.build(r, st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.md_minimize(s, P.soft_pot(), 0, 0.05, T2, r, f, nl.plan, E, st)
+        e1.record()
+        e1.synchronize()
+        if k:
+            tg.append(e0.elapsed_time(e1))
+    Lp = (N2 // 2) * math.pi * D2 / (4 * phi * L64)
+    nlc = P.NeighborList(s, N2, D2, 0.3, 64, canonical=True)
+    s0 = torch.zeros((N2, 4), dtype=torch.float32, device=dev)
+    s0[:, :2] = torch.from_numpy(pk.s0.astype(np.float32)).to(dev)
+    ws = torch.empty(P.md_adjoint_workspace_size(N2, T2, K2), dtype=torch.uint8, device=dev)
+    o = torch.zeros(2, dtype=torch.float64, device=dev)
+    ta = []
+    for k in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.md_minimize_adjoint(s, P.soft_pot(), nlc.plan, s0, N2 // 2, D2, 1.0, Lp, 0.05, T2, K2, r, f, ws, o, st)
+        e1.record()
+        e1.synchronize()
+        if k:
+            ta.append(e0.elapsed_time(e1))
+    oc = o.cpu().numpy()
+    out["cfg2_gd"] = {"N": N2, "D": D2, "gd_steps": T2, "gd_ms": min(tg),
+                      "gd_particle_steps_per_s": N2 * T2 / (min(tg) * 1e-3),
+                      "E_start": float(E[0].item()), "E_end": float(E[-1].item()),
+                      "adjoint_ms": min(ta), "adjoint_over_forward": min(ta) / min(tg), "checkpoints": K2,
+                      "E_final": float(oc[0]), "dE_dD": float(oc[1])}
+    out["status"] = P.md_status_poll(st)
+    return out
 
 
 def fire_section():
@@ -784,6 +891,8 @@ def main():
         extra["learned_vs_sw"] = learned_section()
     if rank == 0 and not args.no_batch:
         extra["batched"] = batched_section()
+    if rank == 0 and not args.no_packing:
+        extra["packing"] = packing_section()
     if rank == 0 and not args.no_fire:
         extra["fire"] = fire_section()
     if rank == 0 and not args.no_nhc:

@@ -302,7 +302,8 @@ JMD_API md_status md_set_pair_options(int opt);
  * Both give the same bits.  MD_ERR_INVALID for other values. */
 JMD_API md_status md_set_nve_fusion(int on);
 
-/* FIRE (md_minimize_fire) and flocking (md_flock_run) loops: 1 (default)
+/* Gradient descent (md_minimize), FIRE (md_minimize_fire) and flocking
+ * (md_flock_run) loops: 1 (default)
  * run each call as one CUDA graph with a device-controlled loop and the
  * rebuild chain under a conditional node; 0 launches every kernel from the
  * host.  Both give the same bits.  MD_ERR_INVALID for other values. */

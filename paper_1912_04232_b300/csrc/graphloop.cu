@@ -1,5 +1,5 @@
 // graphloop.cu -- device-controlled loops as CUDA graphs for the host-side
-// step loops (FIRE, flocking): WHILE(iteration < n) { body }, the body
+// step loops (gradient descent, FIRE, flocking): WHILE(iteration < n) { body }, the body
 // captured from the caller's kernels, with the neighbor-list rebuild chain
 // under an IF node whose condition a one-thread kernel takes from the
 // device rebuild flag.  An idle rebuild chain then costs nothing, and the

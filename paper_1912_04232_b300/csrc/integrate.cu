@@ -665,10 +665,45 @@ extern "C" md_status md_minimize(const md_space *s, const md_pot *p, int kind, f
     NbrArgs na = make_nbr_args(s, d_r, nb, d_status, 1);
     uint32_t *ctl = ws_ptrs(nb).ctl;
     k_loop_init<<<1, 1, 0, st>>>(ctl, (uint32_t)(nsteps + 1), 0u, 0ull);
-    for (int t = 0; t < nsteps; ++t) {
-        enqueue_pair(pa, s->dim, p->kind, 0, st);
-        enqueue_gd_step(s, d_r, d_f, nb, step, st);
-        enqueue_rebuild_chain(na, nb->ncell_total, st);
+    if (g_loop_graphs) {
+        // the same kernels in the same order as the host loop below, as one
+        // graph: WHILE { forces, step (with the displacement check),
+        // IF(rebuild) { rebuild chain } }
+        struct Key {
+            int tag, dim, kind;
+            float step;
+            md_space space;
+            md_nbr nb;
+            PairArgs pa;
+            NbrArgs na;
+            float *r;
+            const float *f;
+        } key;
+        memset(&key, 0, sizeof(key));
+        key.tag = 0x47442d31;   // GD-1
+        key.dim = s->dim;
+        key.kind = p->kind;
+        key.step = step;
+        key.space = *s;
+        key.nb = *nb;
+        key.pa = pa;
+        key.na = na;
+        key.r = d_r;
+        key.f = d_f;
+        md_status e = run_graph_loop(&key, sizeof(key), ctl, nsteps,
+                                     [&](LoopBuilder &lb) {
+                                         enqueue_pair(pa, s->dim, p->kind, 0, lb.cs);
+                                         enqueue_gd_step(s, d_r, d_f, nb, step, lb.cs);
+                                         return lb.rebuild_if(na, nb->ncell_total);
+                                     },
+                                     st);
+        if (e != MD_OK) return e;
+    } else {
+        for (int t = 0; t < nsteps; ++t) {
+            enqueue_pair(pa, s->dim, p->kind, 0, st);
+            enqueue_gd_step(s, d_r, d_f, nb, step, st);
+            enqueue_rebuild_chain(na, nb->ncell_total, st);
+        }
     }
     enqueue_pair(pa, s->dim, p->kind, 0, st);
     JMD_CUDA_TRY(cudaGetLastError());

@@ -73,6 +73,35 @@ def test_gradient_descent_matches_oracle(P):
     assert np.abs(rd.cpu().numpy()[:, :2] - xo[:, :2]).max() < 1e-3
 
 
+def test_gd_graph_loop_equals_host_launches_bitwise(P):
+    # md_minimize runs its steps as one graph with the rebuild chain under a
+    # conditional node; host launches of the same kernels give the same bits
+    import torch
+    p = W.packing_2d(N=1024, D=1.4, seed=3)
+    L = W.f32(W.packing_box(1024, 1.4, 0.9))
+    r = _packing_pos(p, L)
+    s = P.md_space_periodic(2, [L, L])
+    out = []
+    try:
+        for graphs in (True, False):
+            P.md_set_loop_graphs(graphs)
+            nl = P.NeighborList(s, p.N, 1.4, SKIN, 64)
+            rd = to_dev(r, torch.float32)
+            f = torch.zeros_like(rd)
+            st = status_word()
+            nl.build(rd, st)
+            E = torch.zeros(301, dtype=torch.float64, device=dev())
+            P.md_minimize(s, P.soft_pot(), 0, 0.05, 300, rd, f, nl.plan, E, st)
+            torch.cuda.synchronize()
+            assert P.md_status_poll(st) == 0
+            out.append((rd.cpu().numpy(), f.cpu().numpy(), E.cpu().numpy(), nl.stats()[0]))
+    finally:
+        P.md_set_loop_graphs(True)
+    for x, y in zip(out[0][:3], out[1][:3]):
+        np.testing.assert_array_equal(x, y)
+    assert out[0][3] == out[1][3] and out[0][3] > 1
+
+
 def _adjoint(P, p, D, T, K, phi=0.9, eta=0.05):
     import torch
     N = p.N

@@ -150,3 +150,33 @@ def test_fire_graph_loop_equals_host_launches_bitwise(P):
     for x, y in zip(a[:4], b[:4]):
         np.testing.assert_array_equal(x, y)
     assert a[4] == b[4]
+
+
+def test_packing_ensemble_reproduces_fig3_energy_curve(P):
+    # Sec. 4.2, Fig. 3(b), on the App. A system (128 disks, packing fraction
+    # 0.9, 300 FIRE steps): single trajectories of FP32 and FP64 part near
+    # saddles, so the GPU is compared with the FP64 oracle ensemble by
+    # ensemble: the mean minimised energy over 24 seeded starts agrees at each
+    # size ratio D within 4 standard errors, and the GPU means have the
+    # paper's shape (lowest at D = 1, peak near 0.8 above 0.65 and 0.9, and
+    # the same height at the reciprocal ratio 1.25).
+    Ds, nseed = [0.65, 0.8, 0.9, 1.0, 1.25], 24
+    g, o = {}, {}
+    for D in Ds:
+        eg, eo = [], []
+        for seed in range(nseed):
+            r, L, diam = _packing(128, D, 0.9, seed)
+            eg.append(_fire_gpu(P, r, L, 300)[3][-1])
+            pk = W.packing_2d(N=128, D=D, phi=0.9, seed=seed)
+            L64 = W.packing_box(pk.N, pk.D, pk.phi)
+            x = np.zeros((pk.N, 3))
+            x[:, :2] = pk.s0 * L64
+            eo.append(O.fire(x, L64, "soft", nsteps=300, dim=2, diam=pk.diam)[2][-1])
+        g[D] = (np.mean(eg), np.std(eg) / np.sqrt(nseed))
+        o[D] = (np.mean(eo), np.std(eo) / np.sqrt(nseed))
+        assert abs(g[D][0] - o[D][0]) <= 4.0 * np.hypot(g[D][1], o[D][1]), (D, g[D], o[D])
+    E = {D: v[0] for D, v in g.items()}
+    assert E[1.0] < 0.6 * min(E[0.65], E[0.8], E[0.9], E[1.25])
+    assert E[0.8] > E[0.65] + 3 * (g[0.8][1] + g[0.65][1])
+    assert E[0.8] > E[0.9] + 3 * (g[0.8][1] + g[0.9][1])
+    assert abs(E[1.25] - E[0.8]) < 0.1 * E[0.8]

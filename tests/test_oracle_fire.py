@@ -3,8 +3,9 @@
 Each test checks the oracle against something other than its own code: the
 velocity-Verlet NVE oracle (FIRE's MD step is one velocity-Verlet step), a
 closed-form first step of a head-on disk pair, the published time-step
-schedule, the freeze rule once the power vanishes, rotation invariance and
-convergence of a disk packing."""
+schedule, the freeze rule once the power vanishes, rotation invariance,
+convergence of a disk packing, and the shape of the paper's averaged
+packing-energy curve (Sec. 4.2, Fig. 3(b))."""
 import numpy as np
 import pytest
 
@@ -108,3 +109,36 @@ def test_fire_relaxes_a_packing():
     assert E[-1] < 0.02 * E[0]
     _, F, _ = O.soft(x, pk.diam, L, dim=2)
     assert np.abs(F).max() < 0.05 * np.abs(O.soft(r, pk.diam, L, dim=2)[1]).max()
+
+
+def _packing_energy_means(Ds, nseed):
+    # ensemble mean of the minimised energy of the App. A system (128 disks,
+    # half of diameter D and half of diameter 1, box at packing fraction
+    # 0.9, 300 FIRE steps from uniform random positions)
+    out = {}
+    for D in Ds:
+        Es = []
+        for seed in range(nseed):
+            pk = W.packing_2d(N=128, D=D, phi=0.9, seed=seed)
+            L = W.packing_box(pk.N, pk.D, pk.phi)
+            r = np.zeros((pk.N, 3))
+            r[:, :2] = pk.s0 * L
+            Es.append(O.fire(r, L, "soft", nsteps=300, dim=2, diam=pk.diam)[2][-1])
+        out[D] = (float(np.mean(Es)), float(np.std(Es) / np.sqrt(nseed)))
+    return out
+
+
+def test_packing_energy_curve_has_the_papers_shape():
+    # Sec. 4.2, Fig. 3(b): averaged over random starts, the minimised energy
+    # is lowest for equal disks (D = 1), rises as the small disks shrink and
+    # peaks at the maximally frustrated ratio D ~ 0.8, then falls again.  At
+    # fixed packing fraction the energy is scale invariant, so a ratio D and
+    # its reciprocal describe the same mixture: the peak shows again at
+    # 1/0.8 = 1.25 with the same height.  Seeds are fixed; every margin below
+    # is several standard errors of the ensemble means.
+    m = _packing_energy_means([0.65, 0.8, 0.9, 1.0, 1.25], 24)
+    E = {D: v[0] for D, v in m.items()}
+    assert E[1.0] < 0.6 * min(E[0.65], E[0.8], E[0.9], E[1.25])
+    assert E[0.8] > E[0.65] + 3 * (m[0.8][1] + m[0.65][1])
+    assert E[0.8] > E[0.9] + 3 * (m[0.8][1] + m[0.9][1])
+    assert abs(E[1.25] - E[0.8]) < 0.1 * E[0.8]
