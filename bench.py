@@ -54,12 +54,15 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel from the host, in every section (profiling)")
     ap.add_argument("--no-fp32-peak", action="store_true", help="skip the FP32 FMA probe")
+    ap.add_argument("--sort", type=int, default=1,
+                    help="1: Z-order sort of the particles at the start of each job (md_sort_particles)")
     ap.add_argument("--nve-fusion", type=int, default=1, help="1: kick-drift fused into the force kernel (md_set_nve_fusion)")
     ap.add_argument("--local-rows", type=int, default=0,
                     help="1: cell-centred forces over 16-bit local rows (MD_NBR_LOCAL_ROWS); 0: int32 rows")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain-SW section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-replica section")
     ap.add_argument("--no-fire", action="store_true", help="skip the FIRE minimisation section")
+    ap.add_argument("--no-order", action="store_true", help="skip the particle-order sensitivity section")
     ap.add_argument("--no-packing", action="store_true",
                     help="skip the packing section (Fig. 3 ensemble, gradient descent and its adjoint)")
     ap.add_argument("--no-nhc", action="store_true", help="skip the Nose-Hoover NVT section")
@@ -299,6 +302,43 @@ def batched_section(steps=500):
             "one_launch_particle_steps_per_s": Ntot * steps / (ms_b * 1e-3),
             "per_replica_launches_particle_steps_per_s": Ntot * steps / (ms_s * 1e-3),
             "speedup": ms_s / ms_b, "status": code}
+
+
+def order_section():
+    """Sensitivity of the LJ force kernel (N = 256,000) to the particle order:
+    one md_energy_forces in the generated FCC lattice order, in a random
+    order, and in that random order after md_sort_particles (median of 10
+    launches after 2, list rebuilt for each order)."""
+    import torch
+    import paper_1912_04232_b300 as P
+    dev = torch.device("cuda")
+    c = workload("lj256k", 0)
+    s = P.md_space_periodic(3, [c.L] * 3)
+    pot = P.lj_pot(c.eps, c.sigma, c.r_cut, True)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    nl = P.NeighborList(s, c.N, c.r_cut, c.skin, 128)
+    out = {}
+    p = np.random.default_rng(0).permutation(c.N)
+    for name, r0, sort in (("lattice_order", c.r, False), ("random_order", c.r[p], False),
+                           ("random_order_sorted", c.r[p], True)):
+        r = torch.from_numpy(np.ascontiguousarray(r0)).to(dev)
+        f = torch.zeros_like(r)
+        if sort:
+            nl.sort(r, None, st)
+        else:
+            nl.build(r, st)
+        ts = []
+        for k in range(12):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            P.md_energy_forces(s, pot, r, nl.plan, f, None, st)
+            e1.record()
+            e1.synchronize()
+            if k >= 2:
+                ts.append(e0.elapsed_time(e1))
+        out[name + "_force_us"] = 1e3 * statistics.median(ts)
+    out["status"] = P.md_status_poll(st)
+    return out
 
 
 def packing_section(nseed=20):
@@ -776,8 +816,17 @@ def main():
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
 
+    # Z-order sort of the particles at the start of each job (md_sort_particles
+    # also builds the list); scratch and permutation allocated once, here
+    sort_perm = torch.empty(c.N, dtype=torch.int32, device=dev)
+    sort_raw = torch.empty(P.md_sort_scratch_bytes(nl.plan) + 256, dtype=torch.uint8, device=dev)
+    sort_ws = sort_raw[(-sort_raw.data_ptr()) % 256:]
+
     def job():
-        nl.build(r, st)
+        if args.sort:
+            P.md_sort_particles(s, nl.plan, r, v, sort_perm, sort_ws, st)
+        else:
+            nl.build(r, st)
         P.md_energy_forces(s, pot, r, nl.plan, f, None, st)
         P.md_integrate_nve(s, pot, r, v, f, c.mass, c.dt, md_steps, nl.plan, PE, KE, not args.no_graph, st)
 
@@ -891,6 +940,8 @@ def main():
         extra["learned_vs_sw"] = learned_section()
     if rank == 0 and not args.no_batch:
         extra["batched"] = batched_section()
+    if rank == 0 and not args.no_order:
+        extra["particle_order"] = order_section()
     if rank == 0 and not args.no_packing:
         extra["packing"] = packing_section()
     if rank == 0 and not args.no_fire:
@@ -914,6 +965,8 @@ def main():
                        "parallelism": f"replicas{world}", "pair_tpp": args.tpp or 4,
                        "neighbor_rows": "int32 + 16-bit local" if args.local_rows else "int32",
                        "kick_drift": "fused into the force kernel" if args.nve_fusion and not args.local_rows else "separate kernel",
+                       "particle_order": ("Z-order sort at the start of each job, inside the timed region"
+                                          if args.sort else "as generated (FCC lattice order)"),
                        "loop": "host launches" if args.no_graph else "one CUDA graph (device WHILE/IF)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": ("k_pair_block<LJ>" if args.local_rows else "k_pair<LJ>") + " (md_energy_forces)",

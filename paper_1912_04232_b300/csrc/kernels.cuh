@@ -118,6 +118,7 @@ md_status enqueue_fire_step(const FireCtx &c, FireStep *rec, cudaStream_t cs, Lo
 // 1 (default): FIRE and flocking loops run as graph loops; 0: host launches.
 extern int g_loop_graphs;
 void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st);
+void enqueue_cell_binning(const NbrArgs &a, int ncell_total, cudaStream_t st);
 // Device loop counters: step 0 of nsteps (energy series index).
 void enqueue_loop_init(uint32_t *ctl, uint32_t nsteps, cudaStream_t st);
 void enqueue_check_disp(const md_space *s, const float *d_r, const md_nbr *nb, cudaStream_t st);

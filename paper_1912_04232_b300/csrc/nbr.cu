@@ -488,6 +488,17 @@ NbrArgs make_nbr_args(const md_space *s, const float *d_r, const md_nbr *nb, uin
     return a;
 }
 
+// Only the cell list of the rebuild chain (binning, counting sort, members
+// in ascending order per cell): atoms / cell_start for the spatial sort.
+void enqueue_cell_binning(const NbrArgs &a, int ncell_total, cudaStream_t st)
+{
+    int tb = 256, nb = (a.N + tb - 1) / tb;
+    k_bin_count<<<nb, tb, 0, st>>>(a);
+    k_scan<<<1, 1024, 0, st>>>(a, ncell_total);
+    k_scatter<<<nb, tb, 0, st>>>(a);
+    k_sort_cells<<<(ncell_total + SORT_WARPS - 1) / SORT_WARPS, SORT_WARPS * 32, 0, st>>>(a, ncell_total);
+}
+
 // Enqueue the (gated or ungated) rebuild chain.  The flag is consumed by
 // k_finish_build at the end.
 void enqueue_rebuild_chain(const NbrArgs &a, int ncell_total, cudaStream_t st)

@@ -140,6 +140,7 @@ _SIGS = {
                          C.c_int, _P(md_nbr), _vp, C.c_int, _vp, _vp, _vp, C.c_int, _vp, _vp],
     "md_status_poll": [_vp, _P(C.c_uint32), _vp],
     "md_bounded_wait": [_vp, C.c_uint64, _vp, _vp],
+    "md_sort_particles": [_P(md_space), _P(md_nbr), _vp, _vp, _vp, _vp, C.c_size_t, _vp, _vp],
     "md_fma_probe": [_vp, C.c_int, C.c_int, C.c_int, _P(C.c_uint64), _vp],
     "md_bp_descriptors": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp],
     "md_bp_mlp_infer": [_vp, _vp, _vp, C.c_int, _vp, _vp, _vp],
@@ -183,6 +184,8 @@ _lib.md_adjoint_workspace_size.restype = C.c_size_t
 _lib.md_adjoint_workspace_size.argtypes = [C.c_int, C.c_int, C.c_int]
 _lib.md_fire_adjoint_workspace_size.restype = C.c_size_t
 _lib.md_fire_adjoint_workspace_size.argtypes = [C.c_int, C.c_int, C.c_int]
+_lib.md_sort_scratch_bytes.restype = C.c_size_t
+_lib.md_sort_scratch_bytes.argtypes = [_P(md_nbr)]
 _lib.md_noalloc_scratch_bytes.restype = C.c_size_t
 _lib.md_noalloc_scratch_bytes.argtypes = []
 _lib.md_fire_state_bytes.restype = C.c_size_t
@@ -351,6 +354,19 @@ def md_neighbor_list_build_noalloc(space, r, N, r_cut, skin, cap, nbr, cnt, stat
     _check(_lib.md_neighbor_list_build_noalloc(C.byref(space), _ptr(r), int(N), float(r_cut), float(skin), int(cap),
                                                _ptr(nbr), _ptr(cnt), _ptr(status), _stream(stream)),
            "md_neighbor_list_build_noalloc")
+
+
+def md_sort_scratch_bytes(nb) -> int:
+    return int(_lib.md_sort_scratch_bytes(C.byref(nb)))
+
+
+def md_sort_particles(space, nb, r, v, perm, scratch, status=None, stream=None):
+    """Renumber the particles along the Z-order curve of the list's cells;
+    perm[new] = old.  scratch: a 256-byte aligned uint8 tensor of at least
+    md_sort_scratch_bytes(nb) bytes."""
+    _check(_lib.md_sort_particles(C.byref(space), C.byref(nb), _ptr(r), _ptr(v), _ptr(perm), _ptr(scratch),
+                                  int(scratch.numel() * scratch.element_size()), _ptr(status), _stream(stream)),
+           "md_sort_particles")
 
 
 def md_noalloc_scratch_bytes() -> int:
@@ -666,3 +682,17 @@ class NeighborList:
 
     def stats(self, stream=None):
         return md_nbr_stats(self.plan, stream)
+
+    def sort(self, r, v, status, stream=None):
+        """Spatially sort r and v in place (md_sort_particles) and rebuild
+        the list; returns perm (int32, perm[new] = old).  The scratch is a
+        torch tensor kept with the list."""
+        import torch
+        nbytes = md_sort_scratch_bytes(self.plan)
+        if getattr(self, "_sort_ws", None) is None or self._sort_ws_bytes < nbytes:
+            raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=r.device)
+            off = (-raw.data_ptr()) % 256
+            self._sort_raw, self._sort_ws, self._sort_ws_bytes = raw, raw[off:off + nbytes], nbytes
+        perm = torch.empty(self.N, dtype=torch.int32, device=r.device)
+        md_sort_particles(self.space, self.plan, r, v, perm, self._sort_ws, status, stream)
+        return perm
