@@ -363,6 +363,11 @@ def packing_section(nseed=20):
     wsz = P.md_fire_adjoint_workspace_size(N, T, K)
     wsb = torch.empty(wsz + 256, dtype=torch.uint8, device=dev)
     wsv = wsb[(-wsb.data_ptr()) % 256:]
+    # one set of buffers for every run, so that each size ratio's runs share
+    # one captured graph (the adjoint caches a graph per argument set)
+    s0 = torch.zeros((N, 4), dtype=torch.float32, device=dev)
+    ra, va, fa = (torch.zeros((N, 4), dtype=torch.float32, device=dev) for _ in range(3))
+    o = torch.zeros(2, dtype=torch.float64, device=dev)
     rows, t_all = [], 0.0
     for D in [0.6 + 0.05 * k for k in range(9)] + [1.25]:
         L64 = W.packing_box(N, D, phi)
@@ -372,10 +377,7 @@ def packing_section(nseed=20):
         Es, gs = [], []
         for seed in range(nseed):
             pk = W.packing_2d(N=N, D=D, phi=phi, seed=seed)
-            s0 = torch.zeros((N, 4), dtype=torch.float32, device=dev)
             s0[:, :2] = torch.from_numpy(pk.s0.astype(np.float32)).to(dev)
-            ra, va, fa = (torch.zeros((N, 4), dtype=torch.float32, device=dev) for _ in range(3))
-            o = torch.zeros(2, dtype=torch.float64, device=dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             P.md_minimize_fire_adjoint(s, P.soft_pot(), P.fire_params(), nl.plan, s0, N // 2, D, 1.0, Lp, T, K,

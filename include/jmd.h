@@ -332,10 +332,13 @@ JMD_API md_status md_set_pair_options(int opt);
 JMD_API md_status md_set_nve_fusion(int on);
 
 /* Gradient descent (md_minimize), FIRE (md_minimize_fire) and flocking
- * (md_flock_run) loops: 1 (default)
- * run each call as one CUDA graph with a device-controlled loop and the
- * rebuild chain under a conditional node; 0 launches every kernel from the
- * host.  Both give the same bits.  MD_ERR_INVALID for other values. */
+ * (md_flock_run) loops: 1 (default) run each call as one CUDA graph with a
+ * device-controlled loop and the rebuild chain under a conditional node.
+ * The adjoints (md_minimize_adjoint, md_minimize_fire_adjoint): 1 captures
+ * each call's fixed launch sequence once per argument set and replays it as
+ * one graph (at most 32 kept; evicting the oldest waits for the device to
+ * be idle).  0 launches every kernel from the host.  Both give the same
+ * bits.  MD_ERR_INVALID for other values. */
 JMD_API md_status md_set_loop_graphs(int on);
 
 /* ------------------------------------------------------------------------ */

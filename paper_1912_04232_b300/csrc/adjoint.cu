@@ -358,16 +358,15 @@ extern "C" size_t md_adjoint_workspace_size(int N, int T, int K)
     return (nseg + (size_t)K + 2) * (size_t)N * sizeof(float4);
 }
 
-extern "C" md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_nbr *nb, const float *d_s0, int nA,
-                                         float D, float dB, float Lp, float eta, int T, int K, float *d_r, float *d_f,
-                                         void *d_ws, double *d_out, uint32_t *d_status, md_stream_t stream)
+static md_status gd_adjoint_body(const md_space *s, const md_pot *p, md_nbr *nb, const float *d_s0, int nA, float D,
+                                 float dB, float Lp, float eta, int T, int K, float *d_r, float *d_f, void *d_ws,
+                                 double *d_out, uint32_t *d_status, cudaStream_t st)
 {
     if (!s || !p || !nb || !d_s0 || !d_r || !d_f || !d_ws || !d_out) return MD_ERR_INVALID;
     if (s->dim != 2 || nb->dim != 2 || p->kind != MD_SOFT_SPHERE || T < 1 || K < 1 || K > T) return MD_ERR_INVALID;
     if (!(nb->flags & MD_NBR_CANONICAL) || !nb->ws || !nb->rref || nA < 0 || nA > nb->N) return MD_ERR_INVALID;
     const float smax = D > dB ? D : dB;
     if (nb->r_cut < smax) return MD_ERR_INVALID;
-    cudaStream_t st = (cudaStream_t)stream;
     const int N = nb->N;
     const size_t sN = (size_t)N;
     float4 *ws = (float4 *)d_ws;
@@ -407,7 +406,7 @@ extern "C" md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_
 
     // forward: r_0 = L s_0, T gradient-descent steps, checkpoints every K
     k_adjoint_init_pos<<<g, 256, 0, st>>>(r, (const float4 *)d_s0, N, nA, s->L[0], D, dB, d_out);
-    md_status stt = md_neighbor_list_build(s, d_r, nb, d_status, stream);
+    md_status stt = md_neighbor_list_build(s, d_r, nb, d_status, (md_stream_t)st);
     if (stt != MD_OK) return stt;
     for (int t = 0; t < T; ++t) {
         if (t % K == 0)
@@ -431,7 +430,7 @@ extern "C" md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_
     for (int k = nseg - 1; k >= 0; --k) {
         const int t0 = k * K, t1 = (t0 + K < T) ? t0 + K : T;
         JMD_CUDA_TRY(cudaMemcpyAsync(r, ckpt + (size_t)k * sN, sN * sizeof(float4), cudaMemcpyDeviceToDevice, st));
-        stt = md_neighbor_list_build(s, d_r, nb, d_status, stream);
+        stt = md_neighbor_list_build(s, d_r, nb, d_status, (md_stream_t)st);
         if (stt != MD_OK) return stt;
         for (int t = t0; t < t1; ++t) {
             JMD_CUDA_TRY(cudaMemcpyAsync(seg + (size_t)(t - t0) * sN, r, sN * sizeof(float4),
@@ -444,7 +443,7 @@ extern "C" md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_
         }
         for (int t = t1 - 1; t >= t0; --t) {
             float *rt = (float *)(seg + (size_t)(t - t0) * sN);
-            stt = md_neighbor_list_build(s, rt, nb, d_status, stream);
+            stt = md_neighbor_list_build(s, rt, nb, d_status, (md_stream_t)st);
             if (stt != MD_OK) return stt;
             aa.r = (const float4 *)rt;
             aa.lam_in = lin;
@@ -490,10 +489,10 @@ extern "C" size_t md_fire_adjoint_workspace_size(int N, int T, int K)
     return fa_ws(N, T, K).total;
 }
 
-extern "C" md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p, const md_fire_params *fp,
-                                              md_nbr *nb, const float *d_s0, int nA, float D, float dB, float Lp,
-                                              int T, int K, float *d_r, float *d_v, float *d_f, void *d_ws,
-                                              double *d_out, uint32_t *d_status, md_stream_t stream)
+static md_status fire_adjoint_body(const md_space *s, const md_pot *p, const md_fire_params *fp, md_nbr *nb,
+                                   const float *d_s0, int nA, float D, float dB, float Lp, int T, int K, float *d_r,
+                                   float *d_v, float *d_f, void *d_ws, double *d_out, uint32_t *d_status,
+                                   cudaStream_t st)
 {
     if (!s || !p || !fp || !nb || !d_s0 || !d_r || !d_v || !d_f || !d_ws || !d_out) return MD_ERR_INVALID;
     if (s->dim != 2 || nb->dim != 2 || p->kind != MD_SOFT_SPHERE || T < 1 || K < 1 || K > T) return MD_ERR_INVALID;
@@ -502,7 +501,6 @@ extern "C" md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p
     if (fire_params_ok(fp) != MD_OK) return MD_ERR_INVALID;
     const float smax = D > dB ? D : dB;
     if (nb->r_cut < smax) return MD_ERR_INVALID;
-    cudaStream_t st = (cudaStream_t)stream;
     const int N = nb->N;
     const size_t sN = (size_t)N, f4 = sizeof(float4);
     const FaWs L = fa_ws(N, T, K);
@@ -546,7 +544,7 @@ extern "C" md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p
     k_adjoint_init_pos<<<g, 256, 0, st>>>(r, (const float4 *)d_s0, N, nA, s->L[0], D, dB, d_out);
     JMD_CUDA_TRY(cudaMemsetAsync(d_v, 0, sN * f4, st));
     enqueue_fire_init(state, *fp, st);
-    md_status stt = md_neighbor_list_build(s, d_r, nb, d_status, stream);
+    md_status stt = md_neighbor_list_build(s, d_r, nb, d_status, (md_stream_t)st);
     if (stt != MD_OK) return stt;
     enqueue_pair(c.pa, 2, MD_SOFT_SPHERE, 0, st);
     for (int t = 0; t < T; ++t) {
@@ -592,7 +590,7 @@ extern "C" md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p
         JMD_CUDA_TRY(cudaMemcpyAsync(r, ckrv + 2 * (size_t)k * sN, sN * f4, cudaMemcpyDeviceToDevice, st));
         JMD_CUDA_TRY(cudaMemcpyAsync(v, ckrv + (2 * (size_t)k + 1) * sN, sN * f4, cudaMemcpyDeviceToDevice, st));
         JMD_CUDA_TRY(cudaMemcpyAsync(state, ckh + 256 * (size_t)k, 256, cudaMemcpyDeviceToDevice, st));
-        stt = md_neighbor_list_build(s, d_r, nb, d_status, stream);
+        stt = md_neighbor_list_build(s, d_r, nb, d_status, (md_stream_t)st);
         if (stt != MD_OK) return stt;
         enqueue_pair(c.pa, 2, MD_SOFT_SPHERE, 0, st);
         for (int t = t0; t <= t1; ++t) {
@@ -606,7 +604,7 @@ extern "C" md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p
         }
         for (int q = t1 - 1; q >= t0; --q) {
             float *rn = (float *)seg_at(q + 1 - t0, 0);
-            stt = md_neighbor_list_build(s, rn, nb, d_status, stream);
+            stt = md_neighbor_list_build(s, rn, nb, d_status, (md_stream_t)st);
             if (stt != MD_OK) return stt;
             fa.a.r = (const float4 *)rn;
             fa.vq = seg_at(q - t0, 1);
@@ -621,7 +619,7 @@ extern "C" md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p
         if (k == 0) {
             // state 0: its pending Hessian product, then r_0 = L(D) s_0
             float *r0 = (float *)seg_at(0, 0);
-            stt = md_neighbor_list_build(s, r0, nb, d_status, stream);
+            stt = md_neighbor_list_build(s, r0, nb, d_status, (md_stream_t)st);
             if (stt != MD_OK) return stt;
             fa.a.r = (const float4 *)r0;
             fa.final_state = 1;
@@ -636,4 +634,87 @@ extern "C" md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p
     JMD_CUDA_TRY(cudaMemcpyAsync(fr, fin + 2 * sN, sN * f4, cudaMemcpyDeviceToDevice, st));
     JMD_CUDA_TRY(cudaGetLastError());
     return MD_OK;
+}
+
+// The adjoints' launch sequences are fixed by their arguments (step count,
+// checkpoint schedule), so each call runs as one captured graph, cached per
+// argument set (md_set_loop_graphs(0): host launches).  Same kernels, same
+// order, same bits.
+extern "C" md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_nbr *nb, const float *d_s0, int nA,
+                                         float D, float dB, float Lp, float eta, int T, int K, float *d_r, float *d_f,
+                                         void *d_ws, double *d_out, uint32_t *d_status, md_stream_t stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!s || !p || !nb || !g_loop_graphs)
+        return gd_adjoint_body(s, p, nb, d_s0, nA, D, dB, Lp, eta, T, K, d_r, d_f, d_ws, d_out, d_status, st);
+    struct Key {
+        int tag, nA, T, K;
+        float D, dB, Lp, eta;
+        md_space s;
+        md_pot p;
+        md_nbr nb;
+        const void *s0, *r, *f, *ws, *out, *status;
+    } key;
+    memset(&key, 0, sizeof(key));
+    key.tag = 0x4144474a;
+    key.nA = nA;
+    key.T = T;
+    key.K = K;
+    key.D = D;
+    key.dB = dB;
+    key.Lp = Lp;
+    key.eta = eta;
+    key.s = *s;
+    key.p = *p;
+    key.nb = *nb;
+    key.s0 = d_s0;
+    key.r = d_r;
+    key.f = d_f;
+    key.ws = d_ws;
+    key.out = d_out;
+    key.status = d_status;
+    return run_captured_call(&key, sizeof(key), [&](cudaStream_t cs) {
+        return gd_adjoint_body(s, p, nb, d_s0, nA, D, dB, Lp, eta, T, K, d_r, d_f, d_ws, d_out, d_status, cs);
+    }, st);
+}
+
+extern "C" md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p, const md_fire_params *fp,
+                                              md_nbr *nb, const float *d_s0, int nA, float D, float dB, float Lp,
+                                              int T, int K, float *d_r, float *d_v, float *d_f, void *d_ws,
+                                              double *d_out, uint32_t *d_status, md_stream_t stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!s || !p || !fp || !nb || !g_loop_graphs)
+        return fire_adjoint_body(s, p, fp, nb, d_s0, nA, D, dB, Lp, T, K, d_r, d_v, d_f, d_ws, d_out, d_status, st);
+    struct Key {
+        int tag, nA, T, K;
+        float D, dB, Lp;
+        md_space s;
+        md_pot p;
+        md_fire_params fp;
+        md_nbr nb;
+        const void *s0, *r, *v, *f, *ws, *out, *status;
+    } key;
+    memset(&key, 0, sizeof(key));
+    key.tag = 0x46414457;
+    key.nA = nA;
+    key.T = T;
+    key.K = K;
+    key.D = D;
+    key.dB = dB;
+    key.Lp = Lp;
+    key.s = *s;
+    key.p = *p;
+    key.fp = *fp;
+    key.nb = *nb;
+    key.s0 = d_s0;
+    key.r = d_r;
+    key.v = d_v;
+    key.f = d_f;
+    key.ws = d_ws;
+    key.out = d_out;
+    key.status = d_status;
+    return run_captured_call(&key, sizeof(key), [&](cudaStream_t cs) {
+        return fire_adjoint_body(s, p, fp, nb, d_s0, nA, D, dB, Lp, T, K, d_r, d_v, d_f, d_ws, d_out, d_status, cs);
+    }, st);
 }

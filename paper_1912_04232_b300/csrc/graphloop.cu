@@ -129,6 +129,63 @@ md_status run_graph_loop(const void *key, size_t key_bytes, uint32_t *ctl, int n
     return MD_OK;
 }
 
+// A whole host-driven call as one graph: the launches of `body` (kernels,
+// device-to-device copies and sets on the stream it is given) captured once
+// on a private stream per argument key and device, then replayed with one
+// graph launch on the caller's stream.  For calls whose launch sequence is
+// fixed by their arguments (the adjoints: fixed step counts and checkpoint
+// schedule); each replay runs the same kernels in the same order.
+struct CachedCall {
+    std::vector<unsigned char> key;
+    int device;
+    cudaGraphExec_t exec;
+};
+static std::vector<CachedCall> g_calls;
+static const size_t CALLS_CACHED = 32;
+static std::mutex g_calls_mu;
+
+md_status run_captured_call(const void *key, size_t key_bytes, const std::function<md_status(cudaStream_t)> &body,
+                            cudaStream_t st)
+{
+    int dev = 0;
+    JMD_CUDA_TRY(cudaGetDevice(&dev));
+    cudaGraphExec_t ex = nullptr;
+    std::lock_guard<std::mutex> lk(g_calls_mu);
+    for (auto &e : g_calls)
+        if (e.device == dev && e.key.size() == key_bytes && memcmp(e.key.data(), key, key_bytes) == 0) ex = e.exec;
+    if (!ex) {
+        cudaStream_t cs = nullptr;
+        JMD_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+        md_status s = ce == cudaSuccess ? body(cs) : MD_ERR_CUDA;
+        cudaError_t ee = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (s == MD_OK && (ce != cudaSuccess || ee != cudaSuccess)) s = MD_ERR_CUDA;
+        if (s == MD_OK && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) s = MD_ERR_CUDA;
+        if (g) cudaGraphDestroy(g);
+        if (s != MD_OK) {
+            cudaGetLastError();
+            return s;
+        }
+        // at most CALLS_CACHED graphs (a parameter sweep makes one per
+        // value): the oldest is destroyed once the device is idle, so no
+        // launch of it can still be pending on any stream
+        if (g_calls.size() >= CALLS_CACHED) {
+            JMD_CUDA_TRY(cudaDeviceSynchronize());
+            cudaGraphExecDestroy(g_calls.front().exec);
+            g_calls.erase(g_calls.begin());
+        }
+        CachedCall c;
+        c.key.assign((const unsigned char *)key, (const unsigned char *)key + key_bytes);
+        c.device = dev;
+        c.exec = ex;
+        g_calls.push_back(c);
+    }
+    JMD_CUDA_TRY(cudaGraphLaunch(ex, st));
+    return MD_OK;
+}
+
 }  // namespace jmd
 
 extern "C" md_status md_set_loop_graphs(int on)

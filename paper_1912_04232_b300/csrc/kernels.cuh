@@ -89,6 +89,8 @@ struct LoopBuilder {
     uint32_t *ctl = nullptr;
     md_status rebuild_if(const NbrArgs &na, int ncell_total);
 };
+md_status run_captured_call(const void *key, size_t key_bytes, const std::function<md_status(cudaStream_t)> &body,
+                            cudaStream_t st);
 md_status run_graph_loop(const void *key, size_t key_bytes, uint32_t *ctl, int niter,
                          const std::function<md_status(LoopBuilder &)> &body, cudaStream_t st);
 // FIRE (fire.cu): one step's launches, and what the rules of a step used

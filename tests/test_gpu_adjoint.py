@@ -152,3 +152,37 @@ def test_adjoint_full_size_packing(P):
     Eo, go, _ = O.gd_adjoint(p.s0, 1.4, T=T)
     assert abs(E - Eo) <= 2e-3 * abs(Eo)
     assert abs(g - go) <= 5e-2 * abs(go) + 1e-3, (g, go)
+
+
+def test_adjoint_graph_replay_and_host_launches_agree_bitwise(P):
+    # captured once per argument set and replayed; capture, replay and host
+    # launches give the same bits
+    import torch
+    N, D, T, K, phi = 256, 1.3, 200, 15, 0.9
+    p = W.packing_2d(N=N, D=D, seed=9)
+    L64 = O.packing_box(N, D, phi)
+    L = W.f32(L64)
+    Lp = (N // 2) * math.pi * D / (4 * phi * L64)
+    s = P.md_space_periodic(2, [L, L])
+    nl = P.NeighborList(s, N, D, SKIN, 64, canonical=True)
+    s0 = np.zeros((N, 4), np.float32)
+    s0[:, :2] = p.s0
+    s0d = to_dev(s0, torch.float32)
+    r = torch.zeros((N, 4), dtype=torch.float32, device=dev())
+    f = torch.zeros_like(r)
+    ws = torch.empty(P.md_adjoint_workspace_size(N, T, K), dtype=torch.uint8, device=dev())
+    out = torch.zeros(2, dtype=torch.float64, device=dev())
+    st = status_word()
+    res = []
+    try:
+        for graphs in (True, True, False):
+            P.md_set_loop_graphs(graphs)
+            P.md_minimize_adjoint(s, P.soft_pot(), nl.plan, s0d, N // 2, D, 1.0, Lp, 0.05, T, K, r, f, ws, out, st)
+            torch.cuda.synchronize()
+            assert P.md_status_poll(st) == 0
+            res.append([x.cpu().numpy().copy() for x in (out, r, f)])
+    finally:
+        P.md_set_loop_graphs(True)
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            np.testing.assert_array_equal(a, b)

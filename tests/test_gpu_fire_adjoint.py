@@ -108,3 +108,39 @@ def test_fire_adjoint_forward_equals_minimize_fire(P):
     assert P.md_status_poll(st) == 0
     np.testing.assert_array_equal(r.cpu().numpy(), rT)
     assert Es.cpu().numpy()[T] == E
+
+
+def test_fire_adjoint_graph_replay_and_host_launches_agree_bitwise(P):
+    # with loop graphs on, a call is captured once per argument set and
+    # replayed; the capture, its replay and plain host launches give the
+    # same bits
+    import torch
+    N, D, T, K = 128, 1.4, 300, 18
+    p = W.packing_2d(N=N, D=D, phi=0.9, seed=3)
+    L64 = O.packing_box(N, D, 0.9)
+    L = W.f32(L64)
+    Lp = (N // 2) * math.pi * D / (4 * 0.9 * L64)
+    s = P.md_space_periodic(2, [L, L])
+    nl = P.NeighborList(s, N, D, SKIN, 64, canonical=True)
+    s0 = np.zeros((N, 4), np.float32)
+    s0[:, :2] = p.s0
+    s0d = to_dev(s0, torch.float32)
+    r, v, f = (torch.zeros((N, 4), dtype=torch.float32, device=dev()) for _ in range(3))
+    ws = torch.empty(P.md_fire_adjoint_workspace_size(N, T, K) + 256, dtype=torch.uint8, device=dev())
+    wsv = ws[(-ws.data_ptr()) % 256:]
+    out = torch.zeros(2, dtype=torch.float64, device=dev())
+    st = status_word()
+    res = []
+    try:
+        for graphs in (True, True, False):
+            P.md_set_loop_graphs(graphs)
+            P.md_minimize_fire_adjoint(s, P.soft_pot(), P.fire_params(), nl.plan, s0d, N // 2, D, 1.0, Lp, T, K,
+                                       r, v, f, wsv, out, st)
+            torch.cuda.synchronize()
+            assert P.md_status_poll(st) == 0
+            res.append([x.cpu().numpy().copy() for x in (out, r, v, f)])
+    finally:
+        P.md_set_loop_graphs(True)
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            np.testing.assert_array_equal(a, b)
