@@ -56,3 +56,7 @@ def test_binding_loads_and_host_validation():
         P.md_space_periodic(4, [1.0] * 4)
     with pytest.raises(P.MDError):
         P.md_nbr_plan(s, 100, 2.5, 0.3, 1024)     # cap above the supported 512
+    for n in (0, -5):                             # empty and negative systems
+        with pytest.raises(P.MDError) as e:
+            P.md_nbr_plan(s, n, 2.5, 0.3, 64)
+        assert e.value.code == P.MD_ERR_INVALID
