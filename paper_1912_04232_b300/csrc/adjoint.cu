@@ -358,9 +358,21 @@ extern "C" size_t md_adjoint_workspace_size(int N, int T, int K)
     return (nseg + (size_t)K + 2) * (size_t)N * sizeof(float4);
 }
 
+// The list for positions x at a point of the reverse sweep.  Host launches
+// rebuild it; inside a captured graph the displacement check decides, under a
+// conditional node.  The list is canonical, so a particle's force and Hessian
+// products are functions of the positions alone and both give the same bits.
+static md_status list_for(const md_space *s, const float *x, md_nbr *nb, uint32_t *d_status, cudaStream_t st,
+                          LoopBuilder *lb)
+{
+    if (!lb) return md_neighbor_list_build(s, x, nb, d_status, (md_stream_t)st);
+    enqueue_check_disp(s, x, nb, st);
+    return lb->rebuild_if(make_nbr_args(s, x, nb, d_status, 1), nb->ncell_total);
+}
+
 static md_status gd_adjoint_body(const md_space *s, const md_pot *p, md_nbr *nb, const float *d_s0, int nA, float D,
                                  float dB, float Lp, float eta, int T, int K, float *d_r, float *d_f, void *d_ws,
-                                 double *d_out, uint32_t *d_status, cudaStream_t st)
+                                 double *d_out, uint32_t *d_status, cudaStream_t st, LoopBuilder *lb)
 {
     if (!s || !p || !nb || !d_s0 || !d_r || !d_f || !d_ws || !d_out) return MD_ERR_INVALID;
     if (s->dim != 2 || nb->dim != 2 || p->kind != MD_SOFT_SPHERE || T < 1 || K < 1 || K > T) return MD_ERR_INVALID;
@@ -414,7 +426,12 @@ static md_status gd_adjoint_body(const md_space *s, const md_pot *p, md_nbr *nb,
                                          cudaMemcpyDeviceToDevice, st));
         enqueue_pair(pa, 2, MD_SOFT_SPHERE, 0, st);
         enqueue_gd_step(s, d_r, d_f, nb, eta, st);
-        enqueue_rebuild_chain(na, nb->ncell_total, st);
+        if (lb) {
+            stt = lb->rebuild_if(na, nb->ncell_total);
+            if (stt != MD_OK) return stt;
+        } else {
+            enqueue_rebuild_chain(na, nb->ncell_total, st);
+        }
     }
     // E_final and F(r_T), then lambda_T and dU/dD at r_T
     PairArgs pe = pa;
@@ -438,12 +455,17 @@ static md_status gd_adjoint_body(const md_space *s, const md_pot *p, md_nbr *nb,
             if (t + 1 < t1) {   // the last state of the segment needs no step
                 enqueue_pair(pa, 2, MD_SOFT_SPHERE, 0, st);
                 enqueue_gd_step(s, d_r, d_f, nb, eta, st);
-                enqueue_rebuild_chain(na, nb->ncell_total, st);
+                if (lb) {
+                    stt = lb->rebuild_if(na, nb->ncell_total);
+                    if (stt != MD_OK) return stt;
+                } else {
+                    enqueue_rebuild_chain(na, nb->ncell_total, st);
+                }
             }
         }
         for (int t = t1 - 1; t >= t0; --t) {
             float *rt = (float *)(seg + (size_t)(t - t0) * sN);
-            stt = md_neighbor_list_build(s, rt, nb, d_status, (md_stream_t)st);
+            stt = list_for(s, rt, nb, d_status, st, lb);
             if (stt != MD_OK) return stt;
             aa.r = (const float4 *)rt;
             aa.lam_in = lin;
@@ -492,7 +514,7 @@ extern "C" size_t md_fire_adjoint_workspace_size(int N, int T, int K)
 static md_status fire_adjoint_body(const md_space *s, const md_pot *p, const md_fire_params *fp, md_nbr *nb,
                                    const float *d_s0, int nA, float D, float dB, float Lp, int T, int K, float *d_r,
                                    float *d_v, float *d_f, void *d_ws, double *d_out, uint32_t *d_status,
-                                   cudaStream_t st)
+                                   cudaStream_t st, LoopBuilder *lb)
 {
     if (!s || !p || !fp || !nb || !d_s0 || !d_r || !d_v || !d_f || !d_ws || !d_out) return MD_ERR_INVALID;
     if (s->dim != 2 || nb->dim != 2 || p->kind != MD_SOFT_SPHERE || T < 1 || K < 1 || K > T) return MD_ERR_INVALID;
@@ -554,7 +576,7 @@ static md_status fire_adjoint_body(const md_space *s, const md_pot *p, const md_
             JMD_CUDA_TRY(cudaMemcpyAsync(ckrv + (2 * k + 1) * sN, v, sN * f4, cudaMemcpyDeviceToDevice, st));
             JMD_CUDA_TRY(cudaMemcpyAsync(ckh + 256 * k, state, 256, cudaMemcpyDeviceToDevice, st));
         }
-        stt = enqueue_fire_step(c, hist + t, st, nullptr);
+        stt = enqueue_fire_step(c, hist + t, st, lb);
         if (stt != MD_OK) return stt;
     }
     // E = U(r_T); lambda_r(T) = -F(r_T), dU/dD at r_T; lambda_v(T) = 0
@@ -595,7 +617,7 @@ static md_status fire_adjoint_body(const md_space *s, const md_pot *p, const md_
         enqueue_pair(c.pa, 2, MD_SOFT_SPHERE, 0, st);
         for (int t = t0; t <= t1; ++t) {
             if (t > t0) {
-                stt = enqueue_fire_step(c, nullptr, st, nullptr);
+                stt = enqueue_fire_step(c, nullptr, st, lb);
                 if (stt != MD_OK) return stt;
             }
             JMD_CUDA_TRY(cudaMemcpyAsync(seg_at(t - t0, 0), r, sN * f4, cudaMemcpyDeviceToDevice, st));
@@ -604,7 +626,7 @@ static md_status fire_adjoint_body(const md_space *s, const md_pot *p, const md_
         }
         for (int q = t1 - 1; q >= t0; --q) {
             float *rn = (float *)seg_at(q + 1 - t0, 0);
-            stt = md_neighbor_list_build(s, rn, nb, d_status, (md_stream_t)st);
+            stt = list_for(s, rn, nb, d_status, st, lb);
             if (stt != MD_OK) return stt;
             fa.a.r = (const float4 *)rn;
             fa.vq = seg_at(q - t0, 1);
@@ -619,7 +641,7 @@ static md_status fire_adjoint_body(const md_space *s, const md_pot *p, const md_
         if (k == 0) {
             // state 0: its pending Hessian product, then r_0 = L(D) s_0
             float *r0 = (float *)seg_at(0, 0);
-            stt = md_neighbor_list_build(s, r0, nb, d_status, (md_stream_t)st);
+            stt = list_for(s, r0, nb, d_status, st, lb);
             if (stt != MD_OK) return stt;
             fa.a.r = (const float4 *)r0;
             fa.final_state = 1;
@@ -636,6 +658,23 @@ static md_status fire_adjoint_body(const md_space *s, const md_pot *p, const md_
     return MD_OK;
 }
 
+// A loop builder on a stream that is being captured: conditional rebuild
+// nodes go into the graph under capture (their bodies captured on a second
+// stream).
+static md_status with_loop_builder(md_nbr *nb, cudaStream_t cs, const std::function<md_status(LoopBuilder *)> &f)
+{
+    LoopBuilder lb;
+    cudaStreamCaptureStatus cst;
+    JMD_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &lb.graph, nullptr, nullptr, nullptr));
+    if (cst != cudaStreamCaptureStatusActive || !lb.graph) return MD_ERR_CUDA;
+    lb.cs = cs;
+    lb.ctl = ws_ptrs(nb).ctl;
+    JMD_CUDA_TRY(cudaStreamCreateWithFlags(&lb.cs2, cudaStreamNonBlocking));
+    const md_status r = f(&lb);
+    cudaStreamDestroy(lb.cs2);
+    return r;
+}
+
 // The adjoints' launch sequences are fixed by their arguments (step count,
 // checkpoint schedule), so each call runs as one captured graph, cached per
 // argument set (md_set_loop_graphs(0): host launches).  Same kernels, same
@@ -646,7 +685,8 @@ extern "C" md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_
 {
     cudaStream_t st = (cudaStream_t)stream;
     if (!s || !p || !nb || !g_loop_graphs)
-        return gd_adjoint_body(s, p, nb, d_s0, nA, D, dB, Lp, eta, T, K, d_r, d_f, d_ws, d_out, d_status, st);
+        return gd_adjoint_body(s, p, nb, d_s0, nA, D, dB, Lp, eta, T, K, d_r, d_f, d_ws, d_out, d_status, st,
+                               nullptr);
     struct Key {
         int tag, nA, T, K;
         float D, dB, Lp, eta;
@@ -674,7 +714,9 @@ extern "C" md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_
     key.out = d_out;
     key.status = d_status;
     return run_captured_call(&key, sizeof(key), [&](cudaStream_t cs) {
-        return gd_adjoint_body(s, p, nb, d_s0, nA, D, dB, Lp, eta, T, K, d_r, d_f, d_ws, d_out, d_status, cs);
+        return with_loop_builder(nb, cs, [&](LoopBuilder *lb) {
+            return gd_adjoint_body(s, p, nb, d_s0, nA, D, dB, Lp, eta, T, K, d_r, d_f, d_ws, d_out, d_status, cs, lb);
+        });
     }, st);
 }
 
@@ -685,7 +727,8 @@ extern "C" md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p
 {
     cudaStream_t st = (cudaStream_t)stream;
     if (!s || !p || !fp || !nb || !g_loop_graphs)
-        return fire_adjoint_body(s, p, fp, nb, d_s0, nA, D, dB, Lp, T, K, d_r, d_v, d_f, d_ws, d_out, d_status, st);
+        return fire_adjoint_body(s, p, fp, nb, d_s0, nA, D, dB, Lp, T, K, d_r, d_v, d_f, d_ws, d_out, d_status, st,
+                                 nullptr);
     struct Key {
         int tag, nA, T, K;
         float D, dB, Lp;
@@ -715,6 +758,9 @@ extern "C" md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p
     key.out = d_out;
     key.status = d_status;
     return run_captured_call(&key, sizeof(key), [&](cudaStream_t cs) {
-        return fire_adjoint_body(s, p, fp, nb, d_s0, nA, D, dB, Lp, T, K, d_r, d_v, d_f, d_ws, d_out, d_status, cs);
+        return with_loop_builder(nb, cs, [&](LoopBuilder *lb) {
+            return fire_adjoint_body(s, p, fp, nb, d_s0, nA, D, dB, Lp, T, K, d_r, d_v, d_f, d_ws, d_out, d_status, cs,
+                                     lb);
+        });
     }, st);
 }
