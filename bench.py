@@ -809,6 +809,23 @@ def _source_sha():
     return h.hexdigest()[:16]
 
 
+def max_over_ranks(x, dist=None, device=None):
+    """The largest value of x over all ranks (x itself without a process
+    group): the whole job takes as long as its slowest rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(n_particles, md_steps, steps, world, ms_max):
+    """Particle-steps per second of the whole job: every rank advances its
+    own system of n_particles (weak scaling), timed by the slowest rank."""
+    return n_particles * md_steps * steps * world / (ms_max * 1e-3)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -921,13 +938,9 @@ def main():
     E = (PE + KE).cpu().numpy()
     drift = float(np.abs(E - E[0]).max() / c.N)
 
-    t_max = ms
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, dist, dev)
     total_ps = c.N * md_steps * args.steps * world
-    value = total_ps / (t_max * 1e-3)
+    value = whole_job_rate(c.N, md_steps, args.steps, world, t_max)
 
     # end to end: host buffers in, energies out, every step
     e2e = None
@@ -951,11 +964,7 @@ def main():
             e1.synchronize()
             if k >= args.warmup:
                 tt.append(e0.elapsed_time(e1))
-        e2e_ms = sum(tt)
-        if dist:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(sum(tt), dist, dev)
         e2e = {"value": total_ps / (e2e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(hr.numel() * 4 + hv.numel() * 4),
                "d2h_bytes_per_step": int(hpe.numel() * 8 + hke.numel() * 8)}
