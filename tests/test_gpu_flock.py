@@ -171,3 +171,46 @@ def test_predator_sprints_without_energy_series(P):
         got = prd.cpu().numpy()[0]
         np.testing.assert_allclose(got[:2], po[0, :2], rtol=0, atol=2e-3)
         assert got[2] == np.float32(-0.4)
+
+
+def _order_and_spacing(R, th, L, r_align):
+    d = R[:, None, :2].astype(np.float64) - R[None, :, :2].astype(np.float64)
+    d -= L * np.round(d / L)
+    r = np.sqrt((d ** 2).sum(-1))
+    np.fill_diagonal(r, np.inf)
+    c = np.cos(th[:, None].astype(np.float64) - th[None, :].astype(np.float64))
+    return float(c[r < r_align].mean()), float(r.min())
+
+
+@pytest.mark.parametrize("terms", ["align", "all"])
+def test_rules_emerge_as_in_the_oracle(P, terms):
+    # 300 steps from uniform random headings: alignment alone orders the
+    # headings locally with nothing keeping boids apart; with avoidance and
+    # cohesion the order still grows and boids keep their distance.  The
+    # trajectories themselves part from the FP64 oracle's (chaos), so the
+    # GPU's order parameter is compared with the oracle's within 0.1.
+    import torch
+    fl = W.flock(N=400, n_obs=0, seed=3)
+    kw = dict(J_avoid=0.0, J_cohesion=0.0) if terms == "align" else {}
+    prm = P.flock_params(**kw)
+    s = P.md_space_periodic(2, [fl.L, fl.L])
+    nl = P.NeighborList(s, fl.N, max(prm.R_align, prm.R_avoid, prm.R_cohesion), 4.0, 128)
+    b = np.zeros((fl.N, 4), np.float32)
+    b[:, :2] = fl.R
+    bd = to_dev(b, torch.float32)
+    th = to_dev(fl.theta, torch.float32)
+    alt = torch.zeros_like(bd)
+    st = status_word()
+    E = torch.zeros(300, dtype=torch.float64, device=dev())
+    nl.build(bd, st)
+    P.md_flock_run(s, prm, None, 0, None, None, 0, bd, th, alt, 0.1, 300, nl.plan, E, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    og, mg = _order_and_spacing(bd.cpu().numpy(), th.cpu().numpy(), fl.L, 45.0)
+    Ro, tho, _, _ = O.flock_run(fl.R, fl.theta, fl.L, dt=0.1, nsteps=300, params=kw)
+    oo, mo = _order_and_spacing(Ro, tho, fl.L, 45.0)
+    assert og > 0.6 and abs(og - oo) < 0.1, (og, oo)
+    if terms == "align":
+        assert mg < 2.0
+    else:
+        assert mg > 5.0, (mg, mo)
