@@ -121,3 +121,20 @@ def test_nhc_rejects_bad_arguments(P):
         P.md_integrate_nhc(s, P.lj_pot(), z, z.clone(), z.clone(), 1.0, 0.005, 1.0, 0.5, 9, 1, nl.plan, th)
     with pytest.raises(P.MDError):
         P.md_integrate_nhc(s, P.lj_pot(), z, z.clone(), z.clone(), 1.0, 0.005, -1.0, 0.5, 3, 1, nl.plan, th)
+
+
+def test_nhc_samples_the_canonical_kinetic_energy(P):
+    # a long NVT run of the N = 4,096 LJ fluid at kT = 1.5 from its T = 1
+    # start (tau = 50 dt): over the second half the mean temperature is the
+    # target, and the kinetic energy fluctuates as in the canonical ensemble,
+    # Var(K) / <K>^2 = 2 / g with g = 3N (a rescaling thermostat would give
+    # no fluctuation, a weakly coupled one too little); H' stays conserved
+    c = _lj(2)
+    n, kT, tau, M = 6000, 1.5, 0.25, 3
+    x, v, PE, KE, H, th, nl = _nhc_gpu(P, c.r, c.v, c.L, P.lj_pot(), 2.5, 0.3, 1.0, c.dt, kT, tau, M, n)
+    g = 3 * c.N
+    K = KE[n // 2:]
+    assert abs(2.0 * K.mean() / (g * kT) - 1.0) < 0.02
+    rel = K.std() / K.mean()
+    assert 0.7 * np.sqrt(2.0 / g) < rel < 1.4 * np.sqrt(2.0 / g), (rel, np.sqrt(2.0 / g))
+    assert np.abs(H - H[0]).max() / c.N < 5e-3
