@@ -154,3 +154,36 @@ def test_sort_rejects_small_or_misaligned_scratch(P):
         P.md_sort_particles(s, nl.plan, r, None, perm, raw[off:off + need - 256])
     with pytest.raises(P.MDError):
         P.md_sort_particles(s, nl.plan, r, None, perm, raw[off + 16:off + 16 + need])
+
+
+@pytest.mark.parametrize("dim,ncell,N", [(3, 1, 37), (3, 2, 61), (2, 2, 45), (2, 5, 301)])
+def test_sort_on_tiny_and_ragged_grids(P, dim, ncell, N):
+    # grids of 1, 2 and 5 cells per axis (deduplicated stencils), particle
+    # counts that fill no block: the permutation is the reference one and
+    # the forces right after the sort are the relabelled ones, bit for bit
+    import torch
+    r_list = 1.3
+    L = {1: 2.0 * r_list * 1.00003, 2: 2.0 * r_list * 1.001}.get(ncell, ncell * r_list * 1.01)
+    rng = np.random.Generator(np.random.PCG64(100 + 10 * dim + ncell))
+    r0 = np.zeros((N, 4), np.float32)
+    r0[:, :dim] = W.uniform_box_positions(N, L, dim, rng)
+    s = P.md_space_periodic(dim, [L] * dim)
+    nl = P.NeighborList(s, N, 1.0, 0.3, N)
+    assert list(nl.plan.ncell)[:dim] == [ncell] * dim
+    st = status_word()
+    r = to_dev(r0)
+    f0 = torch.zeros_like(r)
+    pot = P.soft_pot()
+    r[:, 3] = 1.0                                  # unit disks / spheres
+    r0[:, 3] = 1.0
+    nl.build(r, st)
+    P.md_energy_forces(s, pot, r, nl.plan, f0, None, st)
+    perm = nl.sort(r, None, st)
+    f1 = torch.zeros_like(r)
+    P.md_energy_forces(s, pot, r, nl.plan, f1, None, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    p = perm.cpu().numpy()
+    np.testing.assert_array_equal(p, _zorder_reference(r0, s, nl.plan, dim))
+    np.testing.assert_array_equal(r.cpu().numpy(), r0[p])
+    np.testing.assert_array_equal(f1.cpu().numpy(), f0.cpu().numpy()[p])
