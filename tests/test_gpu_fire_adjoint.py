@@ -144,3 +144,42 @@ def test_fire_adjoint_graph_replay_and_host_launches_agree_bitwise(P):
     for other in res[1:]:
         for a, b in zip(res[0], other):
             np.testing.assert_array_equal(a, b)
+
+
+def test_graph_cache_eviction_keeps_results(P):
+    # a sweep over more argument sets than the adjoint keeps graphs for (32):
+    # the oldest captured graphs are evicted on the way, and every call still
+    # returns what plain host launches return for the same arguments
+    import torch
+    N, T, K = 32, 12, 4
+    p = W.packing_2d(N=N, D=1.2, phi=0.9, seed=4)
+    s0 = np.zeros((N, 4), np.float32)
+    s0[:, :2] = p.s0
+    s0d = to_dev(s0, torch.float32)
+    r, v, f = (torch.zeros((N, 4), dtype=torch.float32, device=dev()) for _ in range(3))
+    ws = torch.empty(P.md_fire_adjoint_workspace_size(N, T, K) + 256, dtype=torch.uint8, device=dev())
+    wsv = ws[(-ws.data_ptr()) % 256:]
+    out = torch.zeros(2, dtype=torch.float64, device=dev())
+    st = status_word()
+    Ds = [1.05 + 0.01 * k for k in range(36)]
+
+    def call(D):
+        L64 = O.packing_box(N, D, 0.9)
+        L = W.f32(L64)
+        Lp = (N // 2) * math.pi * D / (4 * 0.9 * L64)
+        s = P.md_space_periodic(2, [L, L])
+        nl = P.NeighborList(s, N, D, SKIN, 32, canonical=True)
+        P.md_minimize_fire_adjoint(s, P.soft_pot(), P.fire_params(), nl.plan, s0d, N // 2, D, 1.0, Lp, T, K,
+                                   r, v, f, wsv, out, st)
+        torch.cuda.synchronize()
+        assert P.md_status_poll(st) == 0
+        return out.cpu().numpy().copy()
+
+    graphs = [call(D) for D in Ds]
+    try:
+        P.md_set_loop_graphs(False)
+        host = [call(D) for D in (Ds[0], Ds[17], Ds[-1])]
+    finally:
+        P.md_set_loop_graphs(True)
+    for g, h in zip((graphs[0], graphs[17], graphs[-1]), host):
+        np.testing.assert_array_equal(g, h)
