@@ -319,9 +319,13 @@ JMD_API md_status md_energy_forces(const md_space *s, const md_pot *p, const flo
  * FP32 summation order. */
 JMD_API md_status md_set_pair_tpp(int tpp);
 
-/* Pair-kernel variant (a tuning knob; every variant gives the same bits):
- * opt = 1 reads neighbor rows past L1 (default, measured faster on B300),
- * opt = 0 through it.  Other values: MD_ERR_INVALID. */
+/* Pair-kernel variant (LJ and soft-sphere gather kernels).  Bit 0: read the
+ * neighbor rows past L1 (default 1, measured faster on B300) or through it.
+ * Bit 1: check every row entry against [0, N) before its position is
+ * gathered; an entry outside is skipped and ORs MD_ERR_BOUNDS into the status
+ * word (diagnosing a corrupted list; without it such an entry reads outside
+ * the positions).  On valid lists every variant gives the same bits.  Other
+ * values: MD_ERR_INVALID. */
 JMD_API md_status md_set_pair_options(int opt);
 
 /* NVE with Lennard-Jones or soft-sphere forces on int32 rows: 1 (default)

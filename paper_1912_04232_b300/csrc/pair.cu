@@ -61,10 +61,22 @@ __device__ __forceinline__ void pair_term(const PairArgs &a, const float4 &ri, c
     }
 }
 
+// Bounds-checked entry (CHECK): an index outside [0, N) is reported and
+// replaced by i, and its pair is skipped, so a corrupted row never reads
+// outside the positions.
+__device__ __forceinline__ void check_entry(const PairArgs &a, int i, int &j, bool &ok)
+{
+    if (ok && (unsigned)j >= (unsigned)a.N) {
+        raise_status(a.status, MD_ERR_BOUNDS);
+        j = i;
+        ok = false;
+    }
+}
+
 // The lanes of a group take consecutive entries of the row, so one gather
 // instruction touches few cache lines; four entries per lane per trip keep
 // four gathers in flight; row entries bypass L1.
-template <int DIM, int TPP, int POT, bool STREAM>
+template <int DIM, int TPP, int POT, bool STREAM, bool CHECK>
 __device__ __forceinline__ void pair_loop(const PairArgs &a, const float4 *rp, int i, int n, const int32_t *row,
                                           const float4 &ri, int lg, float &fx, float &fy, float &fz, float &e)
 {
@@ -74,14 +86,21 @@ __device__ __forceinline__ void pair_loop(const PairArgs &a, const float4 *rp, i
         int j1 = k1 < n ? (STREAM ? ld_stream(row + k1) : __ldg(row + k1)) : i;
         int j2 = k2 < n ? (STREAM ? ld_stream(row + k2) : __ldg(row + k2)) : i;
         int j3 = k3 < n ? (STREAM ? ld_stream(row + k3) : __ldg(row + k3)) : i;
+        bool ok0 = true, ok1 = k1 < n, ok2 = k2 < n, ok3 = k3 < n;
+        if (CHECK) {
+            check_entry(a, i, j0, ok0);
+            check_entry(a, i, j1, ok1);
+            check_entry(a, i, j2, ok2);
+            check_entry(a, i, j3, ok3);
+        }
         float4 r0 = __ldg(rp + j0);
         float4 r1 = __ldg(rp + j1);
         float4 r2 = __ldg(rp + j2);
         float4 r3 = __ldg(rp + j3);
-        pair_term<DIM, POT>(a, ri, r0, fx, fy, fz, e);
-        if (k1 < n) pair_term<DIM, POT>(a, ri, r1, fx, fy, fz, e);
-        if (k2 < n) pair_term<DIM, POT>(a, ri, r2, fx, fy, fz, e);
-        if (k3 < n) pair_term<DIM, POT>(a, ri, r3, fx, fy, fz, e);
+        if (ok0) pair_term<DIM, POT>(a, ri, r0, fx, fy, fz, e);
+        if (ok1) pair_term<DIM, POT>(a, ri, r1, fx, fy, fz, e);
+        if (ok2) pair_term<DIM, POT>(a, ri, r2, fx, fy, fz, e);
+        if (ok3) pair_term<DIM, POT>(a, ri, r3, fx, fy, fz, e);
     }
 }
 
@@ -152,7 +171,7 @@ __global__ void __launch_bounds__(256) k_pair(PairArgs a)
             int n = __ldg(a.cnt + i);
             n = n < a.cap ? n : a.cap;
             const int32_t *row = a.nbr + (size_t)i * a.cap;
-            pair_loop<DIM, TPP, POT, (OPT & 1) != 0>(a, rc, i, n, row, ri, lg, fx, fy, fz, e);
+            pair_loop<DIM, TPP, POT, (OPT & 1) != 0, (OPT & 2) != 0>(a, rc, i, n, row, ri, lg, fx, fy, fz, e);
         }
 #pragma unroll
         for (int o = TPP / 2; o > 0; o >>= 1) {
@@ -296,7 +315,8 @@ __global__ void __launch_bounds__(PB_THREADS) k_pair_block(PairArgs a)
                     pair_loop_local<DIM, TPP, POT>(a, n, a.lrow + (size_t)i * a.cap, cand, ri, lg, fx, fy, fz, e);
                 } else {
                     ri = __ldg(rc + i);
-                    pair_loop<DIM, TPP, POT, true>(a, rc, i, n, a.nbr + (size_t)i * a.cap, ri, lg, fx, fy, fz, e);
+                    pair_loop<DIM, TPP, POT, true, false>(a, rc, i, n, a.nbr + (size_t)i * a.cap, ri, lg, fx, fy, fz,
+                                                          e);
                 }
             }
 #pragma unroll
@@ -376,13 +396,17 @@ static int pair_grid(int N)
     return groups < g ? groups : g;
 }
 
-static int g_pair_opt = 1;   // bit 0: stream rows past L1
+static int g_pair_opt = 1;   // bit 0: stream rows past L1; bit 1: bounds-check row entries
 
 template <int DIM, int TPP, int POT, int KICK>
 static void launch_pair_t(const PairArgs &a, cudaStream_t st)
 {
-    if (a.opt & 1) k_pair<DIM, TPP, POT, KICK, 1><<<pair_grid<DIM, TPP, POT, KICK, 1>(a.N), 256, 0, st>>>(a);
-    else k_pair<DIM, TPP, POT, KICK, 0><<<pair_grid<DIM, TPP, POT, KICK, 0>(a.N), 256, 0, st>>>(a);
+    switch (a.opt & 3) {
+    case 1: k_pair<DIM, TPP, POT, KICK, 1><<<pair_grid<DIM, TPP, POT, KICK, 1>(a.N), 256, 0, st>>>(a); break;
+    case 2: k_pair<DIM, TPP, POT, KICK, 2><<<pair_grid<DIM, TPP, POT, KICK, 2>(a.N), 256, 0, st>>>(a); break;
+    case 3: k_pair<DIM, TPP, POT, KICK, 3><<<pair_grid<DIM, TPP, POT, KICK, 3>(a.N), 256, 0, st>>>(a); break;
+    default: k_pair<DIM, TPP, POT, KICK, 0><<<pair_grid<DIM, TPP, POT, KICK, 0>(a.N), 256, 0, st>>>(a); break;
+    }
 }
 
 template <int DIM, int POT, int KICK>
@@ -506,7 +530,7 @@ using namespace jmd;
 
 extern "C" md_status md_set_pair_options(int opt)
 {
-    if (opt < 0 || opt > 1) return MD_ERR_INVALID;
+    if (opt < 0 || opt > 3) return MD_ERR_INVALID;
     g_pair_opt = opt;
     return MD_OK;
 }

@@ -91,3 +91,43 @@ def test_overflowed_list_is_flagged_and_regrown(P):
     nl.build(rd, st)
     torch.cuda.synchronize()
     assert P.md_status_poll(st) == 0 and nl.stats()[1] == need
+
+
+def test_corrupted_row_entry_is_reported_with_bounds_checks(P):
+    # with the bounds-checked pair kernels (md_set_pair_options bit 1) a row
+    # entry outside [0, N) is skipped and reported as MD_ERR_BOUNDS; nothing
+    # reads outside the positions, the context stays usable, and every other
+    # particle's force keeps its bits
+    import torch
+    c = W.lj_small()
+    s = P.md_space_periodic(3, [c.L] * 3)
+    nl = P.NeighborList(s, c.N, 2.5, 0.3, 128)
+    r = to_dev(c.r)
+    st = status_word()
+    nl.build(r, st)
+    f0 = torch.zeros_like(r)
+    P.md_energy_forces(s, P.lj_pot(), r, nl.plan, f0, None, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    nl.nbr[5, 2] = c.N + 1000
+    nl.nbr[9, 0] = -3
+    f1 = torch.zeros_like(r)
+    try:
+        P.md_set_pair_options(3)
+        P.md_energy_forces(s, P.lj_pot(), r, nl.plan, f1, None, st)
+        torch.cuda.synchronize()
+    finally:
+        P.md_set_pair_options(1)
+    assert P.md_status_poll(st) == P.MD_ERR_BOUNDS
+    a, b = f1.cpu().numpy(), f0.cpu().numpy()
+    keep = np.ones(c.N, bool)
+    keep[[5, 9]] = False
+    np.testing.assert_array_equal(a[keep], b[keep])
+    assert np.all(np.isfinite(a[[5, 9]]))
+    # the context still works: a fresh list and the default kernels
+    st2 = status_word()
+    nl.build(r, st2)
+    P.md_energy_forces(s, P.lj_pot(), r, nl.plan, f1, None, st2)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st2) == 0
+    np.testing.assert_array_equal(f1.cpu().numpy(), b)
