@@ -36,6 +36,8 @@ constexpr uint32_t SM_H1 = SM_X + TC_M * 16 * 2;  // [128 x 64]
 constexpr uint32_t SM_G2 = SM_H1 + TC_M * 64 * 2; // [128 x 64]
 constexpr uint32_t SM_G1 = SM_G2 + TC_M * 64 * 2; // [128 x 64]
 constexpr uint32_t SM_TOTAL = SM_G1 + TC_M * 64 * 2;
+constexpr uint32_t SM_LAUNCH = 100 * 1024;          // >= SM_TOTAL; at most 2 CTAs per SM
+static_assert(SM_LAUNCH >= SM_TOTAL, "the launch must cover the layout");
 constexpr uint32_t TMEM_COLS = 256;               // D1 [0,64) D2 [64,128) D3 [128,192) D4 [192,208)
 
 struct TcSmallSmem {
@@ -253,11 +255,14 @@ void enqueue_mlp_infer_tc(const float *P, const float *norm, const float *G, int
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms < 1) sms = 1;
-        cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_TOTAL);
+        cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_LAUNCH);
     }
+    // two CTAs per SM: each holds 256 of the SM's 512 tensor-memory columns,
+    // and the shared memory requested per CTA (SM_LAUNCH) keeps a third off
+    // the SM, where its allocation would wait for one of the two to finish
     int tiles = (N + TC_M - 1) / TC_M;
-    int g = tiles < sms ? tiles : sms;   // one CTA per SM (TMEM: 256 of 512 columns)
-    k_mlp_infer_tc<<<g, 128, SM_TOTAL, st>>>(P, norm, G, N, Ei, dEdG, status);
+    int g = tiles < 2 * sms ? tiles : 2 * sms;
+    k_mlp_infer_tc<<<g, 128, SM_LAUNCH, st>>>(P, norm, G, N, Ei, dEdG, status);
 }
 
 }  // namespace jmd
