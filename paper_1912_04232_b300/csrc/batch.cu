@@ -57,6 +57,7 @@ struct BatchDev {
     int32_t *nbr, *cnt;
     float4 *rref;
     int N, R, C, cap, tpp;
+    int wrapped;              // 1: positions inside [0, L) (the NVE loop wraps them), near-image form in the build
     uint32_t *status;
 };
 
@@ -337,6 +338,7 @@ __device__ void b_build_row_warp(const BatchDev &b, const RepMeta &m, int i, con
 // (k_b_sort_cells); candidates swept 64 at a time with two ballots.
 // Cells whose stencil exceeds the staging capacity set MD_ERR_BOUNDS
 // (replica plans keep stencils small; see md_batch_plan).
+template <bool NEAR>
 __global__ void __launch_bounds__(BB_WARPS * 32) k_b_build(BatchDev b)
 {
     count_launch();
@@ -420,7 +422,10 @@ __global__ void __launch_bounds__(BB_WARPS * 32) k_b_build(BatchDev b)
                 const float4 c = spos[k0 + 32 * u + lane];
                 j[u] = __float_as_int(c.w);
                 float dx, dy, dz;
-                hit[u] = (j[u] != i) && (dist2_rn<3>(ri, c, m.box, dx, dy, dz) < m.rl2);
+                // NEAR: positions inside the box, where the comparison form
+                // gives the bits of the rint form
+                const float r2 = NEAR ? dist2_near<3>(ri, c, m.box, dx, dy, dz) : dist2_rn<3>(ri, c, m.box, dx, dy, dz);
+                hit[u] = (j[u] != i) && (r2 < m.rl2);
             }
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
@@ -614,6 +619,7 @@ static BatchDev batch_dev(const md_batch *bt, uint32_t *status)
     BatchLayout w = batch_layout(bt->N, bt->R, bt->ncell_total);
     char *p = (char *)bt->ws;
     BatchDev b;
+    memset(&b, 0, sizeof(b));
     b.meta = (const RepMeta *)(p + w.meta);
     b.rep_of = (const int32_t *)(p + w.rep_of);
     b.cell_rep = (const int32_t *)(p + w.cell_rep);
@@ -646,7 +652,8 @@ static void enqueue_b_rebuild(const BatchDev &b, const float4 *r, cudaStream_t s
     k_b_scan<<<b.R, 256, 0, st>>>(b);
     k_b_scatter<<<g, 256, 0, st>>>(b, r);
     k_b_sort_cells<<<(b.C + BS_WARPS - 1) / BS_WARPS, BS_WARPS * 32, 0, st>>>(b, r);
-    k_b_build<<<b.C, BB_WARPS * 32, 0, st>>>(b);
+    if (b.wrapped) k_b_build<true><<<b.C, BB_WARPS * 32, 0, st>>>(b);
+    else k_b_build<false><<<b.C, BB_WARPS * 32, 0, st>>>(b);
     k_b_finish<<<1, 256, 0, st>>>(b);
 }
 
@@ -868,6 +875,7 @@ extern "C" md_status md_batch_run_nve(md_batch *bt, float *d_r, float *d_v, floa
     BatchHost *H = (BatchHost *)bt->host;
     cudaStream_t st = (cudaStream_t)stream;
     BatchDev b = batch_dev(bt, d_status);
+    b.wrapped = 1;   // every rebuild in the loop follows a kick-drift, which wraps the positions
     float4 *r = (float4 *)d_r, *v = (float4 *)d_v, *f = (float4 *)d_f;
     if (use_graph) {
         if (!H->exec || H->g_r != d_r || H->g_v != d_v || H->g_f != d_f || H->g_pe != d_PE || H->g_ke != d_KE ||
