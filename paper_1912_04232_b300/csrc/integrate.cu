@@ -150,9 +150,15 @@ __global__ void __launch_bounds__(1024) k_nhc_begin(const float4 *v, int N, floa
 // The next kick-drift applies both velocity factors (the closing one alone
 // at the end of the loop); the series get the thermostatted state.  The
 // force kernel has already advanced the step counter.
-__global__ void k_nhc_update(double *nhc, int M, const uint32_t *ctl, double *KE_out, double *H_out)
+// The chain works on a shared-memory copy of its state: its dependent FP64
+// updates then read and write shared memory instead of making a round trip
+// to the L2 for every value (the same operations, the same bits).
+__global__ void k_nhc_update(double *nhc_g, int M, const uint32_t *ctl, double *KE_out, double *H_out)
 {
     count_launch();
+    __shared__ double nhc[nhc_words(NHC_MAXM)];
+    const int nw = nhc_words(M);
+    for (int k = 0; k < nw; ++k) nhc[k] = nhc_g[k];
     double *c = nhc + 3 * M;
     const unsigned step = ctl[CTL_STEP] - 1u;
     double K = c[NHC_KRAW];
@@ -161,6 +167,7 @@ __global__ void k_nhc_update(double *nhc, int M, const uint32_t *ctl, double *KE
     if (KE_out) KE_out[step] = K;
     if (H_out) H_out[step] = c[NHC_PE] + K + nhc_energy(nhc, M);
     c[NHC_SOPEN] = (step + 1u < ctl[CTL_NSTEPS]) ? nhc_half_step(nhc, M, K) : 1.0;
+    for (int k = 0; k < nw; ++k) nhc_g[k] = nhc[k];
 }
 
 // After the loop: the last step's closing velocity factor.
