@@ -27,9 +27,12 @@ constexpr int NHC_MAXM = 8;
 __host__ __device__ constexpr int nhc_words(int M) { return 3 * M + 8; }
 enum { NHC_GKT = 0, NHC_KT = 1, NHC_DT = 2, NHC_SCLOSE = 3, NHC_SOPEN = 4, NHC_K = 5, NHC_KRAW = 6, NHC_PE = 7 };
 
-__device__ __forceinline__ double nhc_force(const double *Q, const double *w, int k, double K, double gkT, double kT)
+// iQ: the reciprocal masses (an FP64 division is a long dependent sequence;
+// the chain needs six per half-step but only M distinct divisors)
+__device__ __forceinline__ double nhc_force(const double *Q, const double *iQ, const double *w, int k, double K,
+                                            double gkT, double kT)
 {
-    return k == 0 ? (2.0 * K - gkT) / Q[0] : (Q[k - 1] * w[k - 1] * w[k - 1] - kT) / Q[k];
+    return k == 0 ? (2.0 * K - gkT) * iQ[0] : (Q[k - 1] * w[k - 1] * w[k - 1] - kT) * iQ[k];
 }
 
 // One thermostat half-step; K (kinetic energy) is rescaled in place and the
@@ -40,19 +43,21 @@ __device__ __forceinline__ double nhc_half_step(double *st, int M, double &K)
     const double *Q = st + 2 * M, *c = st + 3 * M;
     const double gkT = c[NHC_GKT], kT = c[NHC_KT], dt = c[NHC_DT];
     const double q4 = 0.25 * dt, q8 = 0.125 * dt;
-    w[M - 1] += q4 * nhc_force(Q, w, M - 1, K, gkT, kT);
+    double iQ[NHC_MAXM];
+    for (int k = 0; k < M; ++k) iQ[k] = 1.0 / Q[k];
+    w[M - 1] += q4 * nhc_force(Q, iQ, w, M - 1, K, gkT, kT);
     for (int k = M - 2; k >= 0; --k) {
         const double e = exp(-q8 * w[k + 1]);
-        w[k] = (w[k] * e + q4 * nhc_force(Q, w, k, K, gkT, kT)) * e;
+        w[k] = (w[k] * e + q4 * nhc_force(Q, iQ, w, k, K, gkT, kT)) * e;
     }
     const double s = exp(-0.5 * dt * w[0]);
     K *= s * s;
     for (int k = 0; k < M; ++k) xi[k] += 0.5 * dt * w[k];
     for (int k = 0; k < M - 1; ++k) {
         const double e = exp(-q8 * w[k + 1]);
-        w[k] = (w[k] * e + q4 * nhc_force(Q, w, k, K, gkT, kT)) * e;
+        w[k] = (w[k] * e + q4 * nhc_force(Q, iQ, w, k, K, gkT, kT)) * e;
     }
-    w[M - 1] += q4 * nhc_force(Q, w, M - 1, K, gkT, kT);
+    w[M - 1] += q4 * nhc_force(Q, iQ, w, M - 1, K, gkT, kT);
     return s;
 }
 
