@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--sort", type=int, default=1,
                     help="1: Z-order sort of the particles at the start of each job (md_sort_particles)")
     ap.add_argument("--nve-fusion", type=int, default=1, help="1: kick-drift fused into the force kernel (md_set_nve_fusion)")
+    ap.add_argument("--tiles", type=int, default=0,
+                    help="1: the tile engine (MD_NBR_TILES) runs the NVE loop; 0: the int32-row engine")
+    ap.add_argument("--tile-tpp", type=int, default=0, help="lanes per particle of the tile step kernel (4 or 8)")
     ap.add_argument("--local-rows", type=int, default=0,
                     help="1: cell-centred forces over 16-bit local rows (MD_NBR_LOCAL_ROWS); 0: int32 rows")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain-SW section")
@@ -867,6 +870,9 @@ def main():
     stream = torch.cuda.current_stream()
     if args.tpp:
         P.md_set_pair_tpp(args.tpp)
+    if args.tile_tpp:
+        P.md_set_tile_tpp(args.tile_tpp)
+    tiles = bool(args.tiles) and not args.local_rows
     if args.pair_opt >= 0:
         P.md_set_pair_options(args.pair_opt)
     P.md_set_nve_fusion(bool(args.nve_fusion))
@@ -874,7 +880,7 @@ def main():
     global USE_GRAPH
     USE_GRAPH = not args.no_graph
     s = P.md_space_periodic(3, [c.L] * 3)
-    nl = P.NeighborList(s, c.N, c.r_cut, c.skin, 128, local_rows=bool(args.local_rows))
+    nl = P.NeighborList(s, c.N, c.r_cut, c.skin, 128, local_rows=bool(args.local_rows), tiles=tiles)
     pot = P.lj_pot(c.eps, c.sigma, c.r_cut, True)
     r0 = torch.from_numpy(c.r).to(dev)
     v0 = torch.from_numpy(c.v).to(dev)
@@ -893,7 +899,7 @@ def main():
     sort_ws = sort_raw[(-sort_raw.data_ptr()) % 256:]
 
     def job():
-        if args.sort:
+        if args.sort and not tiles:
             P.md_sort_particles(s, nl.plan, r, v, sort_perm, sort_ws, st)
         else:
             nl.build(r, st)
@@ -969,30 +975,67 @@ def main():
                "h2d_bytes_per_step": int(hr.numel() * 4 + hv.numel() * 4),
                "d2h_bytes_per_step": int(hpe.numel() * 8 + hke.numel() * 8)}
 
-    # roofline of the dominant kernel (pair forces), launched alone with events
-    mean_cnt = float(nl.cnt.float().clamp(max=nl.cap).mean().item())
-    row_bytes = 2.0 if args.local_rows else 4.0              # 16-bit local or int32 row entries
-    bytes_per_particle = row_bytes * mean_cnt + 4 + 16 + 16 + 16   # row, count, own r, f write, gathered r once
-    fe = []
-    for _ in range(30):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        P.md_energy_forces(s, pot, r, nl.plan, f, None, st)
-        e1.record(stream)
-        fe.append((e0, e1))
-    torch.cuda.synchronize()
-    kt = statistics.median(a.elapsed_time(b) for a, b in fe[5:]) * 1e-3
+    # roofline of the dominant kernel, launched alone with events on this stream
     peak, peak_src = _hbm_peak()
-    achieved = bytes_per_particle * c.N / kt / 1e9
     traffic = None
+    tr = {}
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        ent = tr.get("k_pair_block_lj" if args.local_rows else "k_pair_lj", {})
-        if ent.get("source_sha") == _source_sha() and ent.get("N") == c.N:
-            traffic = ent.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
+    if tiles:
+        # the fused step kernel (k_t_step<LJ, 8, 2>): forces from the staged
+        # region, closing half-kick, next kick-drift, displacement check.
+        # K steps on the tiled copy with its rows fixed (md_tiles_steps: one
+        # opening kick-drift launch, then K step launches); rows sized from
+        # a fresh import of the start
+        K = 20
+        r.copy_(r0)
+        v.copy_(v0)
+        nl.build(r, st)
+        P.md_energy_forces(s, pot, r, nl.plan, f, None, st)
+        P.md_tiles_import(s, r, v, f, nl.plan, st)
+        P.md_tiles_export(s, nl.plan, None, None, None, rows=True)
+        torch.cuda.synchronize()
+        mean_cnt = float(nl.cnt.float().clamp(max=nl.cap).mean().item())
+        # row entries (16-bit), count, own position (each staged position
+        # counted once), v read + write, r_ref read, next position write
+        bytes_per_particle = 2.0 * mean_cnt + 4 + 16 + 32 + 16 + 16
+        fe = []
+        for _ in range(6):
+            P.md_tiles_import(s, r, v, f, nl.plan, st)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.md_tiles_steps(s, pot, nl.plan, c.mass, c.dt, K, None, None, st)
+            e1.record(stream)
+            fe.append((e0, e1))
+        torch.cuda.synchronize()
+        kt = statistics.median(a.elapsed_time(b) for a, b in fe[1:]) * 1e-3 / K
+        kname = f"k_t_step<LJ,{args.tile_tpp or 8},2> (fused step, md_tiles_steps)"
+        ent = tr.get("k_t_step_lj", {})
+    else:
+        mean_cnt = float(nl.cnt.float().clamp(max=nl.cap).mean().item())
+        row_bytes = 2.0 if args.local_rows else 4.0              # 16-bit local or int32 row entries
+        bytes_per_particle = row_bytes * mean_cnt + 4 + 16 + 16 + 16   # row, count, own r, f write, gathered r once
+        fe = []
+        for _ in range(30):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.md_energy_forces(s, pot, r, nl.plan, f, None, st)
+            e1.record(stream)
+            fe.append((e0, e1))
+        torch.cuda.synchronize()
+        kt = statistics.median(a.elapsed_time(b) for a, b in fe[5:]) * 1e-3
+        kname = ("k_pair_block<LJ>" if args.local_rows else "k_pair<LJ>") + " (md_energy_forces)"
+        ent = tr.get("k_pair_block_lj" if args.local_rows else "k_pair_lj", {})
+    achieved = bytes_per_particle * c.N / kt / 1e9
+    if ent.get("source_sha") == _source_sha() and ent.get("N") == c.N:
+        traffic = ent.get("dram_bytes_per_launch")
+    code = P.md_status_poll(st)
+    if code & ~P.MD_ERR_NBR_OVERFLOW:
+        raise SystemExit(f"device status {code} in the roofline launches")
 
     extra = {}
     if rank == 0 and not args.no_fp32_peak:
@@ -1027,13 +1070,17 @@ def main():
                        "dt": c.dt, "neighbor_cap": nl.cap, "rebuilds_per_step": builds / args.steps,
                        "max_energy_drift_per_particle": drift, "l2": "flushed between bench steps",
                        "parallelism": f"replicas{world}", "pair_tpp": args.tpp or 4,
-                       "neighbor_rows": "int32 + 16-bit local" if args.local_rows else "int32",
-                       "kick_drift": "fused into the force kernel" if args.nve_fusion and not args.local_rows else "separate kernel",
-                       "particle_order": ("Z-order sort at the start of each job, inside the timed region"
+                       "neighbor_rows": ("16-bit tile-local" if tiles else
+                                         "int32 + 16-bit local" if args.local_rows else "int32"),
+                       "engine": "tiles (MD_NBR_TILES)" if tiles else "int32 rows",
+                       "kick_drift": ("fused into the force kernel" if (tiles or (args.nve_fusion and not args.local_rows))
+                                      else "separate kernel"),
+                       "particle_order": ("re-sorted into half-cell order at every rebuild (tile engine)" if tiles else
+                                          "Z-order sort at the start of each job, inside the timed region"
                                           if args.sort else "as generated (FCC lattice order)"),
                        "loop": "host launches" if args.no_graph else "one CUDA graph (device WHILE/IF)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": ("k_pair_block<LJ>" if args.local_rows else "k_pair<LJ>") + " (md_energy_forces)",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                          "bytes_per_particle": bytes_per_particle, "kernel_ms": kt * 1e3,
                          "peak_source": peak_src},
             "cpu_baseline": cpu_baseline,

@@ -126,14 +126,40 @@ typedef struct {
  * combinable with MD_NBR_CANONICAL. */
 #define MD_NBR_LOCAL_ROWS 2
 
+/* Tiles: the workspace also holds a second, tiled copy of the system for
+ * the velocity-Verlet loop of Lennard-Jones and soft-sphere particles in 3-D
+ * (md_integrate_nve), which then runs on it.  Every rebuild (Sec. 3.2.3)
+ * puts the particles in memory in the order of a grid of half-size cells
+ * (side >= r_list / 2, twice the list's cells per axis, members of a
+ * half-cell by ascending caller index), and writes each particle's row as
+ * 16-bit indices into the positions of its tile's region.  A tile is a
+ * 1 x t x t column of half-cells (t <= 8); its region is the tile grown by
+ * two half-cells on each side (periodic), its half-cells in (z, y, x)
+ * order.  One CTA per tile stages the region's positions in shared memory
+ * with bulk (TMA) copies and evaluates forces, the closing half-kick, the
+ * next kick-drift and the displacement check from there.  A row holds the
+ * partners whose nearest image is the plain difference first, then (stored
+ * from the end of the row backwards) those across the box boundary;
+ * between rebuilds positions are not wrapped, so that split stays valid,
+ * and they are wrapped at every rebuild and on return.  Membership and the
+ * cutoff are decided by the FP32 formula above, so the pair sets are the
+ * same as the int32 rows'.  On return md_integrate_nve writes r, v, f, the
+ * int32 rows, counts and build positions back in the caller's order.
+ * Needs dim = 3, at least 3 cells on every axis and r_cut > skin; a region
+ * holds at most about 1.25x its mean count plus 128 particles (denser
+ * regions raise MD_ERR_NBR_OVERFLOW).  Not combinable with
+ * MD_NBR_CANONICAL or MD_NBR_LOCAL_ROWS. */
+#define MD_NBR_TILES 4
+
 /* Plan a neighbor list for N particles in space s.  Fails with
  * MD_ERR_BOX_TOO_SMALL if any used box edge is < 2 r_list, MD_ERR_INVALID
  * for N < 1, cap < 1, r_cut <= 0 or skin < 0.  Fills out (pointers NULL). */
 JMD_API md_status md_nbr_plan(const md_space *s, int N, float r_cut, float skin, int cap, md_nbr *out);
 
 /* Set the MD_NBR_* bits of a plan and update its ws_bytes (local rows need
- * N*cap*2 more bytes).  Call before md_nbr_bind; MD_ERR_INVALID for unknown
- * bits or MD_NBR_CANONICAL | MD_NBR_LOCAL_ROWS. */
+ * N*cap*2 more bytes, tiles about 120 + 2*cap bytes per particle).  Call
+ * before md_nbr_bind; MD_ERR_INVALID for unknown bits, for combinations
+ * the flags exclude, and for MD_NBR_TILES on a plan that cannot use it. */
 JMD_API md_status md_nbr_set_flags(md_nbr *nb, int flags);
 
 /* Attach caller memory: d_nbr [N*cap] int32, d_cnt [N] int32, d_rref [N*4]
@@ -367,7 +393,8 @@ JMD_API md_status md_integrate_nhc(const md_space *s, const md_pot *p, float *d_
                                    uint32_t *d_status, md_stream_t stream);
 
 /* nsteps of velocity-Verlet NVE.  On entry d_f must hold the forces at d_r
- * (md_energy_forces) and nb a list built for d_r.  Each step:
+ * (md_energy_forces) and nb a list built for d_r (with MD_NBR_TILES the run
+ * imports d_r and builds its own rows; see that flag).  Each step:
  *   v += dt/2 F/m;  r = wrap(r + dt v);  rebuild the list if needed;
  *   F = F(r);       v += dt/2 F/m;
  * mass is in energy*time^2/length^2.  d_PE / d_KE (nsteps doubles each, may
@@ -378,6 +405,48 @@ JMD_API md_status md_integrate_nhc(const md_space *s, const md_pot *p, float *d_
 JMD_API md_status md_integrate_nve(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f,
                                    float mass, float dt, int nsteps, md_nbr *nb, double *d_PE, double *d_KE,
                                    int use_graph, uint32_t *d_status, md_stream_t stream);
+
+/* The tile engine (MD_NBR_TILES) as separate calls, for callers that
+ * evaluate forces on it without integrating (and for timing its force
+ * kernel alone).  The tiled copy lives in nb's workspace.
+ *   md_tiles_import: copies d_r, d_v (may be NULL: zero) and d_f (may be
+ *     NULL) into the tiled order and builds its rows from d_r (wrapped).
+ *   md_tiles_forces: Lennard-Jones or soft-sphere forces and per-particle
+ *     energies at the tiled positions into the tiled force array; d_E (one
+ *     double, may be NULL) receives the FP64 potential energy.  One launch
+ *     of the tile force kernel.
+ *   md_tiles_export: writes positions (wrapped), velocities and forces back
+ *     to d_r, d_v, d_f in the caller's order (any may be NULL) and, with
+ *     rows != 0, the tiled rows as the caller's int32 rows, counts and build
+ *     positions (nb->nbr, cnt, rref), so that nb is a valid list for the
+ *     exported positions.
+ * MD_ERR_INVALID if nb lacks MD_NBR_TILES or is not bound, or for other
+ * potentials. */
+JMD_API md_status md_tiles_import(const md_space *s, const float *d_r, const float *d_v, const float *d_f, md_nbr *nb,
+                                  uint32_t *d_status, md_stream_t stream);
+JMD_API md_status md_tiles_forces(const md_space *s, const md_pot *p, md_nbr *nb, double *d_E, uint32_t *d_status,
+                                  md_stream_t stream);
+JMD_API md_status md_tiles_export(const md_space *s, md_nbr *nb, float *d_r, float *d_v, float *d_f, int rows,
+                                  md_stream_t stream);
+
+/* nsteps velocity-Verlet steps on the tiled copy with its rows held fixed
+ * (no rebuild): the opening half-kick and drift, then one launch of the
+ * fused step kernel per step (forces, closing half-kick, next kick-drift,
+ * displacement check).  Valid while no particle moves more than skin/2 from
+ * its position at the last build (the rebuild flag is raised, not acted
+ * on); md_integrate_nve is the call that rebuilds.  On return the tiled
+ * copy holds r, v and F of the last step (md_tiles_export).  d_PE, d_KE as
+ * in md_integrate_nve. */
+JMD_API md_status md_tiles_steps(const md_space *s, const md_pot *p, md_nbr *nb, float mass, float dt, int nsteps,
+                                 double *d_PE, double *d_KE, uint32_t *d_status, md_stream_t stream);
+
+/* Geometry the tile engine chose for a plan: half-cells per axis (3), the
+ * tile's extent along y and z (2), number of tiles, region capacity in
+ * particles.  out: 7 ints.  MD_ERR_INVALID if the plan cannot use tiles. */
+JMD_API md_status md_tiles_info(const md_space *s, const md_nbr *nb, int32_t *out);
+
+/* Lanes per particle of the tile force kernel: 4 (default) or 8. */
+JMD_API md_status md_set_tile_tpp(int tpp);
 
 /* nsteps of BAOAB Langevin dynamics at constant temperature (Sec. 3.3.1,
  * "Langevin ... simulations at constant temperature"), 3-D only:

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
+#include <math.h>
 
 #include "../../include/jmd.h"
 
@@ -26,6 +27,7 @@ enum CtlWord : int {
     CTL_STEP0 = 10,      // noise counter of the loop's first step
     CTL_ITER = 11,       // iteration counter of a graph loop (graphloop.cu)
     CTL_NITER = 12,      // its length
+    CTL_TSEL = 13,       // tile engine: bit 0 current position buffer, bit 1 current velocity / id buffer
     CTL_WORDS = 64
 };
 
@@ -262,14 +264,102 @@ __device__ __forceinline__ void block_sums_f64(double (&v)[K], double *sh, int s
 // Workspace layout of a neighbor list (all offsets 256-byte aligned).
 // ---------------------------------------------------------------------------
 struct WsLayout {
-    size_t ctl, cell_count, cell_start, cell_of, rank, atoms_u, atoms, rsorted, ralt, partials, lrow, total;
+    size_t ctl, cell_count, cell_start, cell_of, rank, atoms_u, atoms, rsorted, ralt, partials, lrow, tiles, total;
     int max_blocks;
 };
 
 __host__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Scratch of the tile engine (MD_NBR_TILES), offsets from its own start.
+// nhc = half-cells (2 x 2 x 2 per cell of the list's grid).
+constexpr int TSCAN_ITEMS = 4096;       // half-cells per block of the histogram scan
+constexpr int TILE_TMAX = 8;            // largest tile extent (half-cells) along y and z
+constexpr int TILE_PIECES_MAX = 2 * (TILE_TMAX + 4) * (TILE_TMAX + 4);   // two copies per region row
+constexpr int TILE_OWN_MAX = TILE_TMAX * TILE_TMAX;                      // own half-cells
+// Per-tile table written by each build and read by every step: region
+// total, copies, own half-cells, own particles; the copies (source slot,
+// destination offset << 16 | count); the own half-cells (first slot,
+// first local index << 16 | first own particle).
+constexpr int TILE_TAB_WORDS = 4 + 2 * TILE_PIECES_MAX + 2 * TILE_OWN_MAX;
+constexpr int TILE_REG_CAP_MAX = 12800;  // region capacity limit (particles, 200 KB of shared memory)
+constexpr int TILE_TARGET = 300;         // tiles wanted for load balance (about 2 per SM)
+
+struct TilePlan {
+    int H[3];
+    int t, nty, ntz, ntiles, reg_cap;
+};
+
+// Tile geometry of N particles on a list grid of ncell cells per axis:
+// half-cells H = 2 ncell; tiles of 1 x t x t half-cells with t the largest
+// of 8, 6, 4, 2 that fits (t + 4 <= H) and still gives TILE_TARGET tiles;
+// region capacity 1.25x the mean region count plus 128.
+__host__ inline bool tile_geometry(int N, const int *ncell, TilePlan &tp)
+{
+    for (int k = 0; k < 3; ++k) {
+        if (ncell[k] < 3) return false;
+        tp.H[k] = 2 * ncell[k];
+    }
+    int best = -1, last = -1;
+    const int cand_t[4] = {8, 6, 4, 2};
+    for (int c = 0; c < 4; ++c) {
+        const int t = cand_t[c];
+        if (t + 4 > tp.H[1] || t + 4 > tp.H[2]) continue;
+        const long long nt = (long long)tp.H[0] * ((tp.H[1] + t - 1) / t) * ((tp.H[2] + t - 1) / t);
+        last = t;
+        if (nt >= TILE_TARGET) {
+            best = t;
+            break;
+        }
+    }
+    if (best < 0) best = last;
+    if (best < 0) return false;
+    tp.t = best;
+    tp.nty = (tp.H[1] + best - 1) / best;
+    tp.ntz = (tp.H[2] + best - 1) / best;
+    const long long nt = (long long)tp.H[0] * tp.nty * tp.ntz;
+    if (nt > (long long)(N / 4 + 64)) return false;   // FP64 partials of the energy reduction
+    tp.ntiles = (int)nt;
+    const double hc = (double)tp.H[0] * tp.H[1] * tp.H[2];
+    if (hc > (double)TSCAN_ITEMS * 4096.0) return false;
+    const double mean = (double)N / hc * 5.0 * (best + 4) * (best + 4);
+    int cap = (int)ceil(1.25 * mean) + 128;
+    cap = (cap + 31) & ~31;
+    if (cap > TILE_REG_CAP_MAX) return false;
+    tp.reg_cap = cap;
+    return true;
+}
+
+struct TileLayout {
+    size_t hcount, hstart, bsum, key, rank, tmp, r0, r1, v0, v1, p0, p1, rref, fs, cnt, tab, rows, total;
+};
+__host__ inline TileLayout tile_layout(int N, int nhc, int cap, int ntiles)
+{
+    TileLayout t;
+    size_t o = 0;
+    const size_t n = (size_t)N;
+    t.hcount = o;  o = align256(o + sizeof(int32_t) * (size_t)nhc);
+    t.hstart = o;  o = align256(o + sizeof(int32_t) * ((size_t)nhc + 1));
+    t.tab = o;     o = align256(o + sizeof(int32_t) * (size_t)TILE_TAB_WORDS * (size_t)ntiles);
+    t.bsum = o;    o = align256(o + sizeof(int32_t) * ((size_t)nhc / TSCAN_ITEMS + 2));
+    t.key = o;     o = align256(o + sizeof(int32_t) * n);
+    t.rank = o;    o = align256(o + sizeof(int32_t) * n);
+    t.tmp = o;     o = align256(o + sizeof(int32_t) * n);
+    t.r0 = o;      o = align256(o + sizeof(float4) * n);
+    t.r1 = o;      o = align256(o + sizeof(float4) * n);
+    t.v0 = o;      o = align256(o + sizeof(float4) * n);
+    t.v1 = o;      o = align256(o + sizeof(float4) * n);
+    t.p0 = o;      o = align256(o + sizeof(int32_t) * n);
+    t.p1 = o;      o = align256(o + sizeof(int32_t) * n);
+    t.rref = o;    o = align256(o + sizeof(float4) * n);
+    t.fs = o;      o = align256(o + sizeof(float4) * n);
+    t.cnt = o;     o = align256(o + sizeof(uint32_t) * n);
+    t.rows = o;    o = align256(o + sizeof(uint16_t) * n * (size_t)cap);
+    t.total = o;
+    return t;
+}
+
 // Scratch of a neighbor list; the 16-bit local rows only with MD_NBR_LOCAL_ROWS.
-__host__ inline WsLayout ws_layout(int N, int ncell_total, int cap, int flags)
+__host__ inline WsLayout ws_layout(int N, int ncell_total, int cap, int flags, const int *ncell = nullptr)
 {
     WsLayout w;
     size_t o = 0;
@@ -286,6 +376,12 @@ __host__ inline WsLayout ws_layout(int N, int ncell_total, int cap, int flags)
     w.partials = o;     o = align256(o + sizeof(double2) * (size_t)w.max_blocks);
     w.lrow = o;
     if (flags & MD_NBR_LOCAL_ROWS) o = align256(o + sizeof(uint16_t) * (size_t)N * (size_t)cap);
+    w.tiles = o;
+    if (flags & MD_NBR_TILES) {
+        TilePlan tp;
+        const int nt = (ncell && tile_geometry(N, ncell, tp)) ? tp.ntiles : 0;
+        o = align256(o + tile_layout(N, 8 * ncell_total, cap, nt).total);
+    }
     w.total = o;
     return w;
 }
@@ -302,7 +398,7 @@ struct WsPtrs {
 
 __host__ inline WsPtrs ws_ptrs(const md_nbr *nb)
 {
-    WsLayout w = ws_layout(nb->N, nb->ncell_total, nb->cap, nb->flags);
+    WsLayout w = ws_layout(nb->N, nb->ncell_total, nb->cap, nb->flags, nb->ncell);
     char *b = (char *)nb->ws;
     WsPtrs p;
     p.ctl = (uint32_t *)(b + w.ctl);
@@ -324,9 +420,10 @@ __host__ inline WsPtrs ws_ptrs(const md_nbr *nb)
 // against flags changed after md_nbr_set_flags / md_nbr_bind).
 __host__ inline bool nbr_layout_ok(const md_nbr *nb)
 {
-    if (nb->flags & ~(MD_NBR_CANONICAL | MD_NBR_LOCAL_ROWS)) return false;
-    if ((nb->flags & MD_NBR_CANONICAL) && (nb->flags & MD_NBR_LOCAL_ROWS)) return false;
-    return ws_layout(nb->N, nb->ncell_total, nb->cap, nb->flags).total <= nb->ws_bytes;
+    if (nb->flags & ~(MD_NBR_CANONICAL | MD_NBR_LOCAL_ROWS | MD_NBR_TILES)) return false;
+    if ((nb->flags & MD_NBR_CANONICAL) && (nb->flags & (MD_NBR_LOCAL_ROWS | MD_NBR_TILES))) return false;
+    if ((nb->flags & MD_NBR_LOCAL_ROWS) && (nb->flags & MD_NBR_TILES)) return false;
+    return ws_layout(nb->N, nb->ncell_total, nb->cap, nb->flags, nb->ncell).total <= nb->ws_bytes;
 }
 
 // Host-side CUDA error to status.

@@ -544,6 +544,9 @@ static md_status run_dynamics(const md_space *s, const md_pot *p, float *d_r, fl
     if (p->kind != MD_LJ && p->kind != MD_SOFT_SPHERE && p->kind != MD_SW && p->kind != MD_BP && p->kind != MD_GNN)
         return MD_ERR_INVALID;
     if (langevin && (s->dim != 3 || !(gamma >= 0.0f) || !(kT >= 0.0f))) return MD_ERR_INVALID;
+    // plans with tiles: NVE of pair potentials runs on the tile engine
+    if (!langevin && !d_nhc && (nb->flags & MD_NBR_TILES) && tiles_enabled(s, nb, p))
+        return run_tiled_nve(s, p, d_r, d_v, d_f, mass, dt, nsteps, nb, d_PE, d_KE, use_graph, d_status, st);
     NveCtx c;
     memset(&c, 0, sizeof(c));   // the graph cache compares contexts bytewise
     c.box = make_box(s);

@@ -137,6 +137,13 @@ bool gnn_model_ok(const md_gnn_model *m, const md_nbr *nb);
 int bp_variant();
 int gnn_variant();
 int pair_blocks(int N, int tpp);
+// Tile engine (tiles.cu): md_integrate_nve for LJ / soft spheres in 3-D on
+// plans with MD_NBR_TILES.
+bool tiles_enabled(const md_space *s, const md_nbr *nb, const md_pot *p);
+bool tiles_plan_ok(const md_space *s, const md_nbr *nb);
+md_status run_tiled_nve(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f, float mass, float dt,
+                        int nsteps, md_nbr *nb, double *d_PE, double *d_KE, int use_graph, uint32_t *d_status,
+                        cudaStream_t st);
 // r += eta F (unwrapped) with the displacement check (gradient descent step)
 void enqueue_gd_step(const md_space *s, float *d_r, const float *d_f, const md_nbr *nb, float eta, cudaStream_t st);
 

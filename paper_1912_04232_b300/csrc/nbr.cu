@@ -583,10 +583,12 @@ extern "C" md_status md_nbr_plan(const md_space *s, int N, float r_cut, float sk
 
 extern "C" md_status md_nbr_set_flags(md_nbr *nb, int flags)
 {
-    if (!nb || (flags & ~(MD_NBR_CANONICAL | MD_NBR_LOCAL_ROWS))) return MD_ERR_INVALID;
-    if ((flags & MD_NBR_CANONICAL) && (flags & MD_NBR_LOCAL_ROWS)) return MD_ERR_INVALID;
+    if (!nb || (flags & ~(MD_NBR_CANONICAL | MD_NBR_LOCAL_ROWS | MD_NBR_TILES))) return MD_ERR_INVALID;
+    if ((flags & MD_NBR_CANONICAL) && (flags & (MD_NBR_LOCAL_ROWS | MD_NBR_TILES))) return MD_ERR_INVALID;
+    if ((flags & MD_NBR_LOCAL_ROWS) && (flags & MD_NBR_TILES)) return MD_ERR_INVALID;
+    if ((flags & MD_NBR_TILES) && !tiles_plan_ok(nullptr, nb)) return MD_ERR_INVALID;
     nb->flags = flags;
-    nb->ws_bytes = ws_layout(nb->N, nb->ncell_total, nb->cap, flags).total;
+    nb->ws_bytes = ws_layout(nb->N, nb->ncell_total, nb->cap, flags, nb->ncell).total;
     return MD_OK;
 }
 
@@ -604,6 +606,17 @@ extern "C" md_status md_nbr_bind(md_nbr *nb, int32_t *d_nbr, int32_t *d_cnt, flo
     cudaStream_t st = (cudaStream_t)stream;
     JMD_CUDA_TRY(cudaMemsetAsync(w.ctl, 0, sizeof(uint32_t) * CTL_WORDS, st));
     JMD_CUDA_TRY(cudaMemsetAsync(w.cell_count, 0, sizeof(int32_t) * (size_t)nb->ncell_total, st));
+    if (nb->flags & MD_NBR_TILES) {
+        // the tile engine's histogram must start at zero; its cell starts at
+        // zero describe an empty system until the first import
+        const WsLayout wl = ws_layout(nb->N, nb->ncell_total, nb->cap, nb->flags, nb->ncell);
+        TilePlan tp;
+        const int nt = tile_geometry(nb->N, nb->ncell, tp) ? tp.ntiles : 0;
+        const TileLayout tl = tile_layout(nb->N, 8 * nb->ncell_total, nb->cap, nt);
+        char *tb = (char *)d_ws + wl.tiles;
+        // histogram, cell starts and tile tables (zero tables stage nothing)
+        JMD_CUDA_TRY(cudaMemsetAsync(tb + tl.hcount, 0, tl.bsum - tl.hcount, st));
+    }
     return MD_OK;
 }
 

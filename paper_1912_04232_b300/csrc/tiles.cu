@@ -1,0 +1,1464 @@
+// tiles.cu -- the tile engine: velocity-Verlet NVE for Lennard-Jones and
+// soft-sphere particles in 3-D (Sec. 3.3.1) on neighbor lists (Sec. 3.2.3)
+// laid out for shared memory.
+//
+// Data layout (MD_NBR_TILES scratch, see common.cuh tile_layout):
+//   * half-cells: 2 x 2 x 2 per cell of the list's grid (side >= r_list/2),
+//     index h = (hz * Hy + hy) * Hx + hx;
+//   * particles live in memory in half-cell order (slots), members of a
+//     half-cell by ascending caller index; every rebuild re-sorts them, and
+//     ids[slot] is the caller's index;
+//   * a tile is a column of 1 x t x t half-cells; its region is the tile
+//     grown by two half-cells on each side (periodic), 5 x (t+4) x (t+4)
+//     half-cells in (z, y, x) order.  A row (fixed y, z) of the region is a
+//     run of 5 consecutive half-cells along x, i.e. one or two contiguous
+//     slot ranges;
+//   * a particle's row holds 16-bit indices into its tile's region: first
+//     the n0 partners whose nearest image is the plain difference, then,
+//     from the end of the row backwards, the ns partners across the box
+//     boundary; cnt[slot] = n0 | ns << 16.
+//
+// Rebuild chain (under the loop's IF node, or gated by the rebuild flag):
+//   k_t_bin     wrap-free half-cell of every particle, warp-aggregated
+//               atomic histogram, rank inside the half-cell
+//   k_t_scan1/2/3  exclusive scan of the histogram (blocks, block totals,
+//               add), clearing the histogram
+//   k_t_scatter counting-sort scatter of the source slots
+//   k_t_place   members of each half-cell by ascending caller index;
+//               positions (wrapped), velocities, ids and build positions
+//               written to the other buffer set
+//   k_t_build   one CTA per tile: stage the region with bulk copies, then one
+//               warp per own half-cell sweeps, for each of the five z-layers
+//               of the half-cell's 5 x 5 x 5 window, the contiguous run of
+//               25 half-cells, 32 candidates at a time, testing each against
+//               every member of the half-cell (ballot compaction into rows)
+//   k_t_finish  switches the buffer sets, counts the build
+// Step:
+//   k_t_step    one CTA per tile: stage the region (bulk copies), forces
+//               from shared memory, closing half-kick, next kick-drift
+//               (positions not wrapped between rebuilds), displacement
+//               check, FP64 energies (fixed order, last block)
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace jmd {
+
+constexpr int TT = 256;                                          // threads per CTA of every tile kernel
+constexpr int NQ_MAX = 5 * (TILE_TMAX + 4) * (TILE_TMAX + 4);   // region half-cells
+constexpr int OWN_MAX = TILE_OWN_MAX;                            // own half-cells of a tile
+
+struct TileArgs {
+    Box box;
+    int N, cap;
+    int H[3], t, nty, ntz, ntiles, reg_cap, nhc;
+    float hscale[3];
+    float r_list2, half_skin2;
+    int32_t *hcount, *hstart, *bsum, *key, *rank, *tmp;
+    float4 *rb0, *rb1, *vb0, *vb1;
+    int32_t *pb0, *pb1;
+    float4 *rref, *fs;
+    uint32_t *cnt;
+    uint16_t *rows;
+    int32_t *tab;         // per-tile tables (TILE_TAB_WORDS each)
+    uint32_t *ctl;
+    double2 *partials;
+    uint32_t *status;
+    // caller arrays (import / export)
+    const float4 *r_in, *v_in, *f_in;
+    float4 *r_out, *v_out, *f_out, *rref_out;
+    int32_t *nbr_out, *cnt_out;
+    int export_rows;
+    // potential
+    int pot;
+    float rc2, sigma2, c24eps, c4eps, e_shift, eps, alpha;
+    // integration and reductions
+    float hdm, dt, mass;
+    double *E_out, *KE_out;
+    int series;
+    unsigned long long cond_while, cond_if;
+    int use_cond;
+    int gated;    // 1: the chain runs only if ctl[CTL_REBUILD] != 0
+    int import;   // 1: the chain reads the caller's arrays
+    int variant;  // lanes per particle of the step kernel (part of a cached graph's key)
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool t_active(const TileArgs &a)
+{
+    return !a.gated || *(volatile uint32_t *)&a.ctl[CTL_REBUILD] != 0u;
+}
+__device__ __forceinline__ uint32_t t_sel(const TileArgs &a) { return *(volatile uint32_t *)&a.ctl[CTL_TSEL]; }
+__device__ __forceinline__ float4 *t_r(const TileArgs &a, uint32_t b) { return b ? a.rb1 : a.rb0; }
+__device__ __forceinline__ float4 *t_v(const TileArgs &a, uint32_t b) { return b ? a.vb1 : a.vb0; }
+__device__ __forceinline__ int32_t *t_p(const TileArgs &a, uint32_t b) { return b ? a.pb1 : a.pb0; }
+__device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+__device__ __forceinline__ int h_axis(float x, float L, float Linv, float scale, int n)
+{
+    const float y = wrap_coord(x, L, Linv);
+    const int q = (int)(y * scale);
+    return q < 0 ? 0 : (q >= n ? n - 1 : q);
+}
+
+__device__ __forceinline__ uint32_t ld_nc_u32(const uint16_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Tile geometry: column x0, own half-cells y0..y0+ny-1, z0..z0+nz-1.
+struct TGeo {
+    int x0, y0, z0, ny, nz, RY, RZ, nq, nown;
+};
+__device__ __forceinline__ TGeo t_geo(const TileArgs &a, int b)
+{
+    TGeo g;
+    g.x0 = b % a.H[0];
+    const int r = b / a.H[0];
+    const int iy = r % a.nty, iz = r / a.nty;
+    g.y0 = iy * a.t;
+    g.z0 = iz * a.t;
+    g.ny = min(a.t, a.H[1] - g.y0);
+    g.nz = min(a.t, a.H[2] - g.z0);
+    g.RY = g.ny + 4;
+    g.RZ = g.nz + 4;
+    g.nq = 5 * g.RY * g.RZ;
+    g.nown = g.ny * g.nz;
+    return g;
+}
+// Global half-cell of region half-cell q.
+__device__ __forceinline__ int t_hglob(const TileArgs &a, const TGeo &g, int q)
+{
+    const int xl = q % 5, yl = (q / 5) % g.RY, zl = q / (5 * g.RY);
+    const int gx = wrapi(g.x0 - 2 + xl, a.H[0]);
+    const int gy = wrapi(g.y0 - 2 + yl, a.H[1]);
+    const int gz = wrapi(g.z0 - 2 + zl, a.H[2]);
+    return (gz * a.H[1] + gy) * a.H[0] + gx;
+}
+
+struct TileSm {
+    int hoff[NQ_MAX + 1];          // region half-cell -> first local index (exclusive prefix)
+    int own_off[OWN_MAX + 1];      // own half-cell -> first own particle (prefix)
+    int own_slot[OWN_MAX];         // own half-cell -> first slot
+    int own_loc[OWN_MAX];          // own half-cell -> first local index
+    int wtot[TT / 32];
+    int total;
+    int nown;
+    int ok;
+    unsigned char *kmap;   // own particle -> own half-cell (dynamic shared memory after the positions)
+    unsigned long long bar;        // mbarrier of the bulk copies
+};
+
+__device__ __forceinline__ uint32_t sm_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(sm_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// Bulk (TMA) copy of `bytes` (multiple of 16, both addresses 16-byte
+// aligned) from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     sm_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(sm_addr(bar))
+                 : "memory");
+}
+
+// Block-wide exclusive scan of one int per thread (TT threads); returns the
+// thread's exclusive prefix, the total in *tot (all threads).
+__device__ __forceinline__ int block_excl_scan(int v, int *wtot, int *tot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wtot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int u = lane < TT / 32 ? wtot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, u, o);
+            if (lane >= o) u += y;
+        }
+        if (lane < TT / 32) wtot[lane] = u;   // inclusive over warps
+    }
+    __syncthreads();
+    const int ex = x - v + (w > 0 ? wtot[w - 1] : 0);
+    *tot = wtot[TT / 32 - 1];
+    __syncthreads();
+    return ex;
+}
+
+// Region of tile g from the cell starts: local offset of every region
+// half-cell (sm.hoff, exclusive prefix, total in sm.total) and the own
+// half-cells' first slots, local indices and particle prefix.
+__device__ void tile_scan(const TileArgs &a, const TGeo &g, TileSm &sm)
+{
+    const int tid = threadIdx.x;
+    constexpr int PER = (NQ_MAX + TT - 1) / TT;
+    const int qb = tid * PER;
+    int c[PER];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = qb + k;
+        c[k] = 0;
+        if (q < g.nq) {
+            const int h = t_hglob(a, g, q);
+            c[k] = __ldg(a.hstart + h + 1) - __ldg(a.hstart + h);
+        }
+        s += c[k];
+    }
+    int tot;
+    int run = block_excl_scan(s, sm.wtot, &tot);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = qb + k;
+        if (q < g.nq) sm.hoff[q] = run;
+        run += c[k];
+    }
+    if (tid == 0) {
+        sm.hoff[g.nq] = tot;
+        sm.total = tot;
+    }
+    __syncthreads();
+    // own half-cells: region (2, 2 + k % ny, 2 + k / ny)
+    int oc = 0;
+    if (tid < g.nown) {
+        const int yl = 2 + tid % g.ny, zl = 2 + tid / g.ny;
+        const int q = 2 + 5 * (yl + g.RY * zl);
+        sm.own_loc[tid] = sm.hoff[q];
+        oc = sm.hoff[q + 1] - sm.hoff[q];
+        sm.own_slot[tid] = __ldg(a.hstart + t_hglob(a, g, q));
+    }
+    int otot;
+    const int oex = block_excl_scan(oc, sm.wtot, &otot);
+    if (tid < g.nown) sm.own_off[tid] = oex;
+    if (tid == 0) {
+        sm.own_off[g.nown] = otot;
+        sm.nown = g.nown;
+    }
+    __syncthreads();
+}
+
+// Own particle p -> its own half-cell (sm.kmap), from the own tables.
+__device__ __forceinline__ void tile_own_map(TileSm &sm)
+{
+    for (int k = threadIdx.x; k < sm.nown; k += TT)
+        for (int p = sm.own_off[k]; p < sm.own_off[k + 1]; ++p) sm.kmap[p] = (unsigned char)k;
+    __syncthreads();
+}
+
+// Thread 0 waits (bounded, about a second of SM clocks) for the region's
+// bulk copies; on a timeout it raises MD_ERR_TIMEOUT and waits once more for
+// the copies still in flight, which target this CTA's shared memory.  The
+// other threads wait at the block barrier.  Returns sm.ok (uniform).
+__device__ bool tile_wait(const TileArgs &a, TileSm &sm)
+{
+    if (threadIdx.x == 0) {
+        bool done = mbar_test(&sm.bar, 0u);
+        const long long t0 = clock64();
+        while (!done && clock64() - t0 < (2ll << 30)) done = mbar_test(&sm.bar, 0u);
+        if (!done) {
+            raise_status(a.status, MD_ERR_TIMEOUT);
+            const long long t1 = clock64();
+            while (!mbar_test(&sm.bar, 0u) && clock64() - t1 < (2ll << 30)) {
+            }
+        }
+        sm.ok = done ? 1 : 0;
+    }
+    __syncthreads();
+    return sm.ok != 0;
+}
+
+// Build: after tile_scan, stage the region's positions (one thread per
+// region row: the run of five half-cells along x is one slot range, or two
+// where it wraps) and write the tile's table for the steps that follow.
+// Returns false (uniformly) if the region exceeds the capacity.
+__device__ bool tile_stage_build(const TileArgs &a, const TGeo &g, TileSm &sm, const float4 *rsrc, float4 *cand,
+                                 int32_t *tab)
+{
+    const int tid = threadIdx.x;
+    const int tot = sm.total;
+    if (tid == 0) {
+        tab[0] = tot;
+        tab[1] = 2 * g.RY * g.RZ;
+        tab[2] = g.nown;
+        tab[3] = sm.own_off[g.nown];
+    }
+    if (tid < g.nown) {
+        tab[4 + 2 * TILE_PIECES_MAX + tid] = sm.own_slot[tid];
+        tab[4 + 2 * TILE_PIECES_MAX + TILE_OWN_MAX + tid] =
+            (int)(((unsigned)sm.own_loc[tid] << 16) | (unsigned)sm.own_off[tid]);
+    }
+    const bool fits = tot <= a.reg_cap;
+    if (!fits) {
+        if (tid == 0) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+    } else if (tid == 0) {
+        mbar_init(&sm.bar, 1u);
+        mbar_expect_tx(&sm.bar, (unsigned)tot * 16u);
+    }
+    __syncthreads();
+    for (int r = tid; r < g.RY * g.RZ; r += TT) {
+        const int q0 = 5 * r;
+        int qs = q0;
+        int2 pa = make_int2(0, 0), pb = make_int2(0, 0);
+        for (int xl = 1; xl <= 5; ++xl) {
+            const bool brk = xl == 5 || wrapi(g.x0 - 2 + xl, a.H[0]) == 0;
+            if (brk) {
+                const int n = sm.hoff[q0 + xl] - sm.hoff[qs];
+                const int src = __ldg(a.hstart + t_hglob(a, g, qs));
+                if (n > 0) {
+                    if (fits) bulk_g2s(cand + sm.hoff[qs], rsrc + src, (unsigned)n * 16u, &sm.bar);
+                    const int2 pc = make_int2(src, (int)(((unsigned)sm.hoff[qs] << 16) | (unsigned)n));
+                    if (pa.y == 0) pa = pc;
+                    else pb = pc;
+                }
+                qs = q0 + xl;
+            }
+        }
+        reinterpret_cast<int2 *>(tab + 4)[2 * r] = pa;
+        reinterpret_cast<int2 *>(tab + 4)[2 * r + 1] = pb;
+    }
+    if (!fits) return false;
+    return tile_wait(a, sm);
+}
+
+// Step: stage the region from the tile's table (copies and own half-cells
+// as the last build left them).  Returns false (uniformly) if the region
+// exceeds the capacity (the build raised the overflow) or the copies timed
+// out.
+__device__ bool tile_stage_tab(const TileArgs &a, TileSm &sm, const float4 *rsrc, float4 *cand, const int32_t *tab)
+{
+    const int tid = threadIdx.x;
+    const int tot = __ldg(tab + 0), npc = __ldg(tab + 1), nown = __ldg(tab + 2);
+    if (tot > a.reg_cap) return false;
+    if (tid == 0) {
+        sm.total = tot;
+        sm.nown = nown;
+        sm.own_off[nown] = __ldg(tab + 3);
+        mbar_init(&sm.bar, 1u);
+        mbar_expect_tx(&sm.bar, (unsigned)tot * 16u);
+    }
+    if (tid < nown) {
+        sm.own_slot[tid] = __ldg(tab + 4 + 2 * TILE_PIECES_MAX + tid);
+        const unsigned w = (unsigned)__ldg(tab + 4 + 2 * TILE_PIECES_MAX + TILE_OWN_MAX + tid);
+        sm.own_loc[tid] = (int)(w >> 16);
+        sm.own_off[tid] = (int)(w & 0xffffu);
+    }
+    __syncthreads();
+    const int2 *pc = reinterpret_cast<const int2 *>(tab + 4);
+    for (int k = tid; k < npc; k += TT) {
+        const int2 c = __ldg(pc + k);
+        const unsigned n = (unsigned)c.y & 0xffffu;
+        if (n > 0u) bulk_g2s(cand + ((unsigned)c.y >> 16), rsrc + c.x, n * 16u, &sm.bar);
+    }
+    return tile_wait(a, sm);
+}
+
+// ---------------------------------------------------------------------------
+// rebuild chain
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(TT) k_t_bin(TileArgs a)
+{
+    count_launch();
+    if (!t_active(a)) return;
+    const int i = blockIdx.x * TT + threadIdx.x;
+    const bool act = i < a.N;
+    int h = 0;
+    if (act) {
+        const float4 p = a.import ? a.r_in[i] : t_r(a, t_sel(a) & 1u)[i];
+        if (!isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z)) raise_status(a.status, MD_ERR_NONFINITE);
+        const int hx = h_axis(p.x, a.box.L[0], a.box.Linv[0], a.hscale[0], a.H[0]);
+        const int hy = h_axis(p.y, a.box.L[1], a.box.Linv[1], a.hscale[1], a.H[1]);
+        const int hz = h_axis(p.z, a.box.L[2], a.box.Linv[2], a.hscale[2], a.H[2]);
+        h = (hz * a.H[1] + hy) * a.H[0] + hx;
+    }
+    const unsigned amask = __ballot_sync(0xffffffffu, act);
+    if (!act) return;
+    const unsigned peers = __match_any_sync(amask, h);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    const int below = __popc(peers & ((1u << lane) - 1u));
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&a.hcount[h], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    a.key[i] = h;
+    a.rank[i] = base + below;
+}
+
+// Block-local exclusive scan of TSCAN_ITEMS counts (1024 threads x 4); the
+// block's total to bsum; the histogram is cleared for the next build.
+__global__ void __launch_bounds__(1024) k_t_scan1(TileArgs a)
+{
+    count_launch();
+    if (!t_active(a)) return;
+    __shared__ int wt[32];
+    const int base = blockIdx.x * TSCAN_ITEMS + threadIdx.x * 4;
+    int c[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        c[k] = base + k < a.nhc ? a.hcount[base + k] : 0;
+        s += c[k];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int u = wt[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, u, o);
+            if (lane >= o) u += y;
+        }
+        wt[lane] = u;
+    }
+    __syncthreads();
+    int run = x - s + (w > 0 ? wt[w - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < a.nhc) {
+            a.hstart[base + k] = run;
+            a.hcount[base + k] = 0;
+        }
+        run += c[k];
+    }
+    if (threadIdx.x == 1023) a.bsum[blockIdx.x] = wt[31];
+}
+
+// Exclusive scan of the nb block totals (one CTA, nb <= 4096); the grand
+// total to hstart[nhc].
+__global__ void __launch_bounds__(1024) k_t_scan2(TileArgs a, int nb)
+{
+    count_launch();
+    if (!t_active(a)) return;
+    __shared__ int wt[32];
+    const int base = threadIdx.x * 4;
+    int c[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        c[k] = base + k < nb ? a.bsum[base + k] : 0;
+        s += c[k];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int u = wt[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, u, o);
+            if (lane >= o) u += y;
+        }
+        wt[lane] = u;
+    }
+    __syncthreads();
+    int run = x - s + (w > 0 ? wt[w - 1] : 0);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < nb) a.bsum[base + k] = run;
+        run += c[k];
+    }
+    if (threadIdx.x == 1023) a.hstart[a.nhc] = wt[31];
+}
+
+__global__ void __launch_bounds__(TT) k_t_scan3(TileArgs a)
+{
+    count_launch();
+    if (!t_active(a)) return;
+    const int i = blockIdx.x * TT + threadIdx.x;
+    if (i < a.nhc) a.hstart[i] += a.bsum[i / TSCAN_ITEMS];
+}
+
+__global__ void __launch_bounds__(TT) k_t_scatter(TileArgs a)
+{
+    count_launch();
+    if (!t_active(a)) return;
+    const int i = blockIdx.x * TT + threadIdx.x;
+    if (i < a.N) a.tmp[a.hstart[a.key[i]] + a.rank[i]] = i;
+}
+
+// Members of each half-cell by ascending caller index: the rank of a member
+// is the number of members of its half-cell with a smaller index.  Writes
+// the other buffer set (positions wrapped into [0, L), build positions).
+__global__ void __launch_bounds__(TT) k_t_place(TileArgs a)
+{
+    count_launch();
+    if (!t_active(a)) return;
+    const int q = blockIdx.x * TT + threadIdx.x;
+    if (q >= a.N) return;
+    const uint32_t sel = t_sel(a);
+    const uint32_t rc = sel & 1u, vc = (sel >> 1) & 1u;
+    const int32_t *pc = t_p(a, vc);
+    const int s = a.tmp[q];
+    const int h = a.key[s];
+    const int b = a.hstart[h], e = a.hstart[h + 1];
+    const int id = a.import ? s : pc[s];
+    int rk = 0;
+    for (int m = b; m < e; ++m) {
+        const int s2 = a.tmp[m];
+        const int id2 = a.import ? s2 : pc[s2];
+        rk += id2 < id ? 1 : 0;
+    }
+    const int d = b + rk;
+    float4 p = a.import ? a.r_in[s] : t_r(a, rc)[s];
+    p.x = wrap_coord(p.x, a.box.L[0], a.box.Linv[0]);
+    p.y = wrap_coord(p.y, a.box.L[1], a.box.Linv[1]);
+    p.z = wrap_coord(p.z, a.box.L[2], a.box.Linv[2]);
+    t_r(a, rc ^ 1u)[d] = p;
+    a.rref[d] = p;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a.import) {
+        if (a.v_in) v = a.v_in[s];
+        a.fs[d] = a.f_in ? a.f_in[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        v = t_v(a, vc)[s];
+    }
+    t_v(a, vc ^ 1u)[d] = v;
+    t_p(a, vc ^ 1u)[d] = id;
+}
+
+// Row of one own particle (one warp).  Its candidates are the region's
+// half-cells (x 0..4, y yl-2..yl+2, z zl-2..zl+2); for each z-layer the
+// rows of y that can hold a partner form one contiguous local range (a
+// layer or a row farther than r_list from the particle, with a margin above
+// FP32 rounding, is skipped).  The warp sweeps the concatenated ranges 32
+// candidates at a time and compacts the partners with ballots into the row.
+// BND: the window reaches across the box boundary, so the nearest image takes
+// the comparison form (positions are inside [0, L) at a build) and partners
+// across the boundary go to the row's tail.
+template <bool BND>
+__device__ __forceinline__ int build_particle(const TileArgs &a, const TGeo &g, const TileSm &sm,
+                                              const float4 *cand, int k, int loc, int slot)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int yl = 2 + k % g.ny, zl = 2 + k / g.ny;
+    const float4 ri = cand[loc];
+    const float L0 = a.box.L[0], L1 = a.box.L[1], L2 = a.box.L[2];
+    const float I0 = a.box.Linv[0], I1 = a.box.Linv[1], I2 = a.box.Linv[2];
+    // pruning geometry: half-cell edges in unwrapped coordinates
+    const float wy = L1 / (float)a.H[1], wz = L2 / (float)a.H[2];
+    const float lim2 = a.r_list2 * 1.0002f + 1e-4f;
+    // the five z-layers' ranges: first local index and prefix of lengths
+    int b0, b1, b2, b3, b4, p1, p2, p3, p4, p5;
+    {
+        int beg[5], len[5];
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+            const int zr = zl - 2 + d;
+            const float zlo = (float)(g.z0 - 2 + zr) * wz, zhi = zlo + wz;
+            const float gz = fmaxf(0.f, fmaxf(zlo - ri.z, ri.z - zhi));
+            const float rz2 = gz * gz;
+            // rows below and above the particle's own, dropped from the far
+            // end while they lie beyond r_list (two rows at most per side)
+            const float g0 = fmaxf(0.f, ri.y - (float)(g.y0 - 3 + yl) * wy);   // top edge of row yl-2
+            const float g1 = fmaxf(0.f, ri.y - (float)(g.y0 - 2 + yl) * wy);   // top edge of row yl-1
+            const float h0 = fmaxf(0.f, (float)(g.y0 + yl) * wy - ri.y);       // bottom edge of row yl+2
+            const float h1 = fmaxf(0.f, (float)(g.y0 - 1 + yl) * wy - ri.y);   // bottom edge of row yl+1
+            const int ya = g0 * g0 + rz2 <= lim2 ? yl - 2 : (g1 * g1 + rz2 <= lim2 ? yl - 1 : yl);
+            const int yb = h0 * h0 + rz2 <= lim2 ? yl + 2 : (h1 * h1 + rz2 <= lim2 ? yl + 1 : yl);
+            beg[d] = sm.hoff[5 * (ya + g.RY * zr)];
+            len[d] = rz2 <= lim2 ? sm.hoff[5 * (yb + 1 + g.RY * zr)] - beg[d] : 0;
+        }
+        b0 = beg[0]; b1 = beg[1]; b2 = beg[2]; b3 = beg[3]; b4 = beg[4];
+        p1 = len[0]; p2 = p1 + len[1]; p3 = p2 + len[2]; p4 = p3 + len[3]; p5 = p4 + len[4];
+    }
+    int n0 = 0, ns = 0;
+    uint16_t *row = a.rows + (size_t)slot * a.cap;
+    for (int v0 = 0; v0 < p5; v0 += 32) {
+        const int v = v0 + lane;
+        const bool valid = v < p5;
+        const int j = v < p1 ? b0 + v
+                      : v < p2 ? b1 + (v - p1)
+                      : v < p3 ? b2 + (v - p2)
+                      : v < p4 ? b3 + (v - p3)
+                               : b4 + (v - p4);
+        const float4 cj = valid ? cand[j] : make_float4(-3e38f, -3e38f, -3e38f, 0.f);
+        float dx = __fsub_rn(ri.x, cj.x), dy = __fsub_rn(ri.y, cj.y), dz = __fsub_rn(ri.z, cj.z);
+        bool sh = false;
+        if (BND) {
+            const float ux = __fmul_rn(dx, I0), uy = __fmul_rn(dy, I1), uz = __fmul_rn(dz, I2);
+            const bool sx = ux > 0.5f || ux < -0.5f, sy = uy > 0.5f || uy < -0.5f, sz = uz > 0.5f || uz < -0.5f;
+            if (sx) dx = __fsub_rn(dx, ux > 0.5f ? L0 : -L0);
+            if (sy) dy = __fsub_rn(dy, uy > 0.5f ? L1 : -L1);
+            if (sz) dz = __fsub_rn(dz, uz > 0.5f ? L2 : -L2);
+            sh = sx || sy || sz;
+        }
+        const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        const bool pass = valid && r2 < a.r_list2 && j != loc;
+        const bool pu = pass && !sh;
+        const unsigned mu = __ballot_sync(0xffffffffu, pu);
+        if (pu) {
+            const int pos = n0 + __popc(mu & lt);
+            if (pos < a.cap) row[pos] = (uint16_t)j;
+        }
+        n0 += __popc(mu);
+        if (BND) {
+            const bool ps = pass && sh;
+            const unsigned ms = __ballot_sync(0xffffffffu, ps);
+            if (ps) {
+                const int kk = ns + __popc(ms & lt);
+                if (kk < a.cap) row[a.cap - 1 - kk] = (uint16_t)j;
+            }
+            ns += __popc(ms);
+        }
+    }
+    const int n = n0 + ns;
+    if (lane == 0) {
+        a.cnt[slot] = (uint32_t)min(n0, 0xffff) | ((uint32_t)min(ns, 0xffff) << 16);
+        if (n > a.cap) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+    }
+    return n;
+}
+
+__global__ void __launch_bounds__(TT) k_t_build(TileArgs a)
+{
+    count_launch();
+    if (!t_active(a)) return;
+    extern __shared__ __align__(16) float4 cand[];
+    __shared__ TileSm sm;
+    __shared__ int bmax;
+    const TGeo g = t_geo(a, blockIdx.x);
+    const uint32_t sel = t_sel(a);
+    // the positions k_t_place just wrote (the buffer k_t_finish switches to)
+    const float4 *rs = t_r(a, (sel & 1u) ^ 1u);
+    if (threadIdx.x == 0) {
+        bmax = 0;
+        sm.kmap = reinterpret_cast<unsigned char *>(cand + a.reg_cap);
+    }
+    tile_scan(a, g, sm);
+    if (!tile_stage_build(a, g, sm, rs, cand, a.tab + (size_t)blockIdx.x * TILE_TAB_WORDS)) return;
+    tile_own_map(sm);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nown = sm.own_off[g.nown];
+    int wmax = 0;
+    for (int p = warp; p < nown; p += TT / 32) {
+        const int k = sm.kmap[p];
+        const int t = p - sm.own_off[k];
+        const int gy = g.y0 + k % g.ny, gz = g.z0 + k / g.ny;
+        const bool bnd = g.x0 < 2 || g.x0 >= a.H[0] - 2 || gy < 2 || gy >= a.H[1] - 2 || gz < 2 || gz >= a.H[2] - 2;
+        const int loc = sm.own_loc[k] + t, slot = sm.own_slot[k] + t;
+        const int n = bnd ? build_particle<true>(a, g, sm, cand, k, loc, slot)
+                          : build_particle<false>(a, g, sm, cand, k, loc, slot);
+        wmax = max(wmax, n);
+    }
+    if (lane == 0 && wmax > 0) atomicMax(&bmax, wmax);
+    __syncthreads();
+    if (threadIdx.x == 0 && bmax > 0) atomicMax(&a.ctl[CTL_MAXCNT], (uint32_t)bmax);
+}
+
+// Switches to the buffer set the chain wrote and counts the build.
+__global__ void k_t_finish(TileArgs a)
+{
+    count_launch();
+    if (!t_active(a)) return;
+    a.ctl[CTL_TSEL] ^= 3u;
+    unsigned long long *b = (unsigned long long *)&a.ctl[CTL_BUILDS_LO];
+    *b += 1ull;
+    a.ctl[CTL_REBUILD] = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// forces and the fused step
+// ---------------------------------------------------------------------------
+template <int POT>
+__device__ __forceinline__ void t_term(const TileArgs &a, float dx, float dy, float dz, float r2, float wi, float wj,
+                                       float &fx, float &fy, float &fz, float &e)
+{
+    if (POT == MD_LJ) {
+        if (r2 < a.rc2) {
+            const float ir2 = __fdividef(1.0f, r2);
+            const float s2 = a.sigma2 * ir2;
+            const float s6 = s2 * s2 * s2;
+            const float fr = a.c24eps * ir2 * s6 * (2.0f * s6 - 1.0f);
+            fx += fr * dx;
+            fy += fr * dy;
+            fz += fr * dz;
+            e += a.c4eps * s6 * (s6 - 1.0f) - a.e_shift;
+        }
+    } else {
+        const float sg = 0.5f * (wi + wj);
+        if (r2 < sg * sg) {
+            const float rr = sqrtf(r2);
+            const float isg = __fdividef(1.0f, sg);
+            const float x = 1.0f - rr * isg;
+            float xa1, ua;
+            if (a.alpha == 2.0f) {
+                xa1 = x;
+                ua = 0.5f * x * x;
+            } else {
+                xa1 = __powf(x, a.alpha - 1.0f);
+                ua = xa1 * x / a.alpha;
+            }
+            const float fr = a.eps * isg * xa1 * __fdividef(1.0f, rr);
+            fx += fr * dx;
+            fy += fr * dy;
+            fz += fr * dz;
+            e += a.eps * ua;
+        }
+    }
+}
+
+// Partner with the plain difference as nearest image.
+template <int POT>
+__device__ __forceinline__ void t_pair_plain(const TileArgs &a, const float4 &ri, const float4 &rj, float &fx,
+                                             float &fy, float &fz, float &e)
+{
+    const float dx = __fsub_rn(ri.x, rj.x), dy = __fsub_rn(ri.y, rj.y), dz = __fsub_rn(ri.z, rj.z);
+    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    t_term<POT>(a, dx, dy, dz, r2, ri.w, rj.w, fx, fy, fz, e);
+}
+// Partner across the boundary: the full nearest-image formula.
+template <int POT>
+__device__ __forceinline__ void t_pair_image(const TileArgs &a, const float4 &ri, const float4 &rj, float &fx,
+                                             float &fy, float &fz, float &e)
+{
+    float dx, dy, dz;
+    const float r2 = dist2_rn<3>(ri, rj, a.box, dx, dy, dz);
+    t_term<POT>(a, dx, dy, dz, r2, ri.w, rj.w, fx, fy, fz, e);
+}
+
+// FP64 totals: FP32 per warp, FP64 across warps and (last block, fixed
+// order) across blocks; the last block writes the series, advances the step,
+// sets the graph conditions and, after a step that moved the particles,
+// switches the position buffer.
+__device__ __forceinline__ void t_epilogue(float pe_acc, float ke_acc, const TileArgs &a, bool flip)
+{
+    __shared__ double sh[2][32];
+    __shared__ bool last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pe_acc += __shfl_xor_sync(0xffffffffu, pe_acc, o);
+        ke_acc += __shfl_xor_sync(0xffffffffu, ke_acc, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][w] = (double)pe_acc;
+        sh[1][w] = (double)ke_acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bpe = 0.0, bke = 0.0;
+        for (int k = 0; k < TT / 32; ++k) {
+            bpe += sh[0][k];
+            bke += sh[1][k];
+        }
+        a.partials[blockIdx.x] = make_double2(bpe, bke);
+        __threadfence();
+        const unsigned t = atomicAdd(&a.ctl[CTL_TICKET], 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double S[2] = {0.0, 0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += TT) {
+        const volatile double *p = (const volatile double *)(a.partials + b);
+        S[0] += p[0];
+        S[1] += p[1];
+    }
+    block_sums_f64<2>(S, &sh[0][0], 32);
+    if (threadIdx.x == 0) {
+        const double spe = S[0], ske = S[1];
+        a.ctl[CTL_TICKET] = 0u;
+        if (!isfinite(spe) || !isfinite(ske)) raise_status(a.status, MD_ERR_NONFINITE);
+        const unsigned step = a.series ? a.ctl[CTL_STEP] : 0u;
+        if (a.E_out) a.E_out[step] = spe;
+        if (a.KE_out) a.KE_out[step] = ske;
+        if (a.series) a.ctl[CTL_STEP] = step + 1u;
+        if (flip) a.ctl[CTL_TSEL] ^= 1u;
+        if (a.use_cond) {
+            cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond_while,
+                                    (step + 1u < a.ctl[CTL_NSTEPS]) ? 1u : 0u);
+            cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond_if,
+                                    *(volatile uint32_t *)&a.ctl[CTL_REBUILD] ? 1u : 0u);
+        }
+    }
+}
+
+// One CTA per tile.  KICK 0: forces and per-particle energies into fs;
+// KICK 2: the fused velocity-Verlet step (closing half-kick at the new
+// forces, then, unless this is the loop's last step, the next kick and
+// drift into the other position buffer with the displacement check; the
+// last step writes the forces instead).
+template <int POT, int TPP, int KICK>
+__global__ void __launch_bounds__(TT, 4) k_t_step(TileArgs a)
+{
+    count_launch();
+    extern __shared__ __align__(16) float4 cand[];
+    __shared__ TileSm sm;
+    constexpr int RW = 40 / TPP;      // row words (two entries each) per lane fetched ahead: 80 entries per group
+    constexpr int RS = 16 / TPP;      // tail entries per lane fetched ahead: 16 per group
+    const uint32_t sel = t_sel(a);
+    const uint32_t rcb = sel & 1u;
+    const float4 *rc = t_r(a, rcb);
+    float4 *rn = t_r(a, rcb ^ 1u);
+    float4 *vv = t_v(a, (sel >> 1) & 1u);
+    bool more = false;
+    if (KICK == 2) {
+        const uint32_t step = *(volatile uint32_t *)&a.ctl[CTL_STEP];
+        more = step + 1u < *(volatile uint32_t *)&a.ctl[CTL_NSTEPS];
+    }
+    if (threadIdx.x == 0) sm.kmap = reinterpret_cast<unsigned char *>(cand + a.reg_cap);
+    float pe_acc = 0.f, ke_acc = 0.f;
+    bool moved = false;
+    if (tile_stage_tab(a, sm, rc, cand, a.tab + (size_t)blockIdx.x * TILE_TAB_WORDS)) {
+        tile_own_map(sm);
+        const int lg = threadIdx.x & (TPP - 1), gi = threadIdx.x / TPP;
+        const int nown = sm.own_off[sm.nown];
+        // every lane of a warp runs every trip (the group reductions below
+        // are full-warp shuffles); lanes past the tile's last particle
+        // carry zeros
+        for (int p0 = 0; p0 < nown; p0 += TT / TPP) {
+            const int p = p0 + gi;
+            const bool valid = p < nown;
+            float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+            int s = 0;
+            float4 ri = make_float4(0.f, 0.f, 0.f, 0.f), vi = ri, rr = ri;
+            if (valid) {
+                const int k = sm.kmap[p];
+                const int t = p - sm.own_off[k];
+                s = sm.own_slot[k] + t;
+                const uint32_t c = __ldg(a.cnt + s);
+                ri = cand[sm.own_loc[k] + t];
+                // the kick's operands are fetched now, used after the sums
+                if (KICK == 2 && lg == 0) {
+                    vi = vv[s];
+                    if (more) rr = __ldg(a.rref + s);
+                }
+                const int n0 = min((int)(c & 0xffffu), a.cap);
+                const int ns = min((int)(c >> 16), a.cap - n0);
+                const uint16_t *row = a.rows + (size_t)s * a.cap;
+                // the lane's row words and tail entries fetched ahead
+                uint32_t w[RW];
+                int js[RS];
+#pragma unroll
+                for (int k2 = 0; k2 < RW; ++k2) {
+                    const int wi = lg + k2 * TPP;
+                    w[k2] = 2 * wi < n0 ? ld_nc_u32(row + 2 * wi) : 0u;
+                }
+#pragma unroll
+                for (int k2 = 0; k2 < RS; ++k2) {
+                    const int ki = lg + k2 * TPP;
+                    js[k2] = ki < ns ? ld_stream_u16(row + a.cap - ns + ki) : 0;
+                }
+                // partners whose nearest image is the plain difference
+#pragma unroll
+                for (int k2 = 0; k2 < RW; ++k2) {
+                    const int wi = lg + k2 * TPP;
+                    if (2 * wi < n0) {
+                        t_pair_plain<POT>(a, ri, cand[w[k2] & 0xffffu], fx, fy, fz, e);
+                        if (2 * wi + 1 < n0) t_pair_plain<POT>(a, ri, cand[w[k2] >> 16], fx, fy, fz, e);
+                    }
+                }
+                for (int wi = lg + RW * TPP; 2 * wi < n0; wi += TPP) {   // rows longer than 80
+                    const uint32_t x = ld_nc_u32(row + 2 * wi);
+                    t_pair_plain<POT>(a, ri, cand[x & 0xffffu], fx, fy, fz, e);
+                    if (2 * wi + 1 < n0) t_pair_plain<POT>(a, ri, cand[x >> 16], fx, fy, fz, e);
+                }
+                // partners across the box boundary (row tail)
+#pragma unroll
+                for (int k2 = 0; k2 < RS; ++k2)
+                    if (lg + k2 * TPP < ns) t_pair_image<POT>(a, ri, cand[js[k2]], fx, fy, fz, e);
+                for (int ki = lg + RS * TPP; ki < ns; ki += TPP)
+                    t_pair_image<POT>(a, ri, cand[ld_stream_u16(row + a.cap - ns + ki)], fx, fy, fz, e);
+            }
+#pragma unroll
+            for (int o = TPP / 2; o > 0; o >>= 1) {
+                fx += __shfl_xor_sync(0xffffffffu, fx, o);
+                fy += __shfl_xor_sync(0xffffffffu, fy, o);
+                fz += __shfl_xor_sync(0xffffffffu, fz, o);
+                e += __shfl_xor_sync(0xffffffffu, e, o);
+            }
+            if (valid && lg == 0) {
+                const float ei = 0.5f * e;
+                pe_acc += ei;
+                if (KICK == 0) {
+                    a.fs[s] = make_float4(fx, fy, fz, ei);
+                } else {
+                    vi.x += a.hdm * fx;
+                    vi.y += a.hdm * fy;
+                    vi.z += a.hdm * fz;
+                    ke_acc += 0.5f * a.mass * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
+                    if (more) {
+                        vi.x += a.hdm * fx;
+                        vi.y += a.hdm * fy;
+                        vi.z += a.hdm * fz;
+                        float4 r2 = ri;
+                        r2.x = ri.x + a.dt * vi.x;
+                        r2.y = ri.y + a.dt * vi.y;
+                        r2.z = ri.z + a.dt * vi.z;
+                        rn[s] = r2;
+                        float dx, dy, dz;
+                        moved = moved || dist2_rn<3>(r2, rr, a.box, dx, dy, dz) > a.half_skin2;
+                    } else {
+                        a.fs[s] = make_float4(fx, fy, fz, ei);
+                    }
+                    vv[s] = vi;
+                }
+            }
+        }
+    }
+    if (KICK == 2 && __any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) {
+        a.ctl[CTL_REBUILD] = 1u;
+        __threadfence();
+    }
+    t_epilogue(pe_acc, ke_acc, a, KICK == 2 && more);
+}
+
+// First half of the loop's first step: v += dt/2 F/m; r += dt v (not
+// wrapped), in place; displacement check; the last block hands the rebuild
+// decision to the graph's IF node.
+__global__ void __launch_bounds__(TT) k_t_kick(TileArgs a)
+{
+    count_launch();
+    __shared__ bool last;
+    const uint32_t sel = t_sel(a);
+    float4 *r = t_r(a, sel & 1u);
+    float4 *v = t_v(a, (sel >> 1) & 1u);
+    const int i = blockIdx.x * TT + threadIdx.x;
+    bool mv = false;
+    if (i < a.N) {
+        const float4 f = a.fs[i];
+        float4 vi = v[i], ri = r[i];
+        vi.x += a.hdm * f.x;
+        vi.y += a.hdm * f.y;
+        vi.z += a.hdm * f.z;
+        ri.x = ri.x + a.dt * vi.x;
+        ri.y = ri.y + a.dt * vi.y;
+        ri.z = ri.z + a.dt * vi.z;
+        v[i] = vi;
+        r[i] = ri;
+        float dx, dy, dz;
+        mv = dist2_rn<3>(ri, a.rref[i], a.box, dx, dy, dz) > a.half_skin2;
+    }
+    if (__any_sync(0xffffffffu, mv) && (threadIdx.x & 31) == 0) {
+        a.ctl[CTL_REBUILD] = 1u;
+        __threadfence();
+    }
+    if (!a.use_cond) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(&a.ctl[CTL_TICKET2], 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const unsigned flag = *(volatile uint32_t *)&a.ctl[CTL_REBUILD];
+        a.ctl[CTL_TICKET2] = 0u;
+        cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond_if, flag ? 1u : 0u);
+    }
+}
+
+// Positions (wrapped), velocities, forces and build positions back to the
+// caller's order.
+__global__ void __launch_bounds__(TT) k_t_export(TileArgs a)
+{
+    count_launch();
+    const int s = blockIdx.x * TT + threadIdx.x;
+    if (s >= a.N) return;
+    const uint32_t sel = t_sel(a);
+    const int id = t_p(a, (sel >> 1) & 1u)[s];
+    if (a.r_out) {
+        float4 p = t_r(a, sel & 1u)[s];
+        p.x = wrap_coord(p.x, a.box.L[0], a.box.Linv[0]);
+        p.y = wrap_coord(p.y, a.box.L[1], a.box.Linv[1]);
+        p.z = wrap_coord(p.z, a.box.L[2], a.box.Linv[2]);
+        a.r_out[id] = p;
+    }
+    if (a.v_out) a.v_out[id] = t_v(a, (sel >> 1) & 1u)[s];
+    if (a.f_out) a.f_out[id] = a.fs[s];
+    if (a.export_rows) a.rref_out[id] = a.rref[s];
+}
+
+// The tiled rows as the caller's int32 rows (one warp per own particle):
+// local index -> region half-cell (binary search) -> slot -> caller index;
+// padded with N; counts are the true totals.
+__global__ void __launch_bounds__(TT) k_t_rows(TileArgs a)
+{
+    count_launch();
+    __shared__ TileSm sm;
+    const TGeo g = t_geo(a, blockIdx.x);
+    tile_scan(a, g, sm);
+    const uint32_t sel = t_sel(a);
+    const int32_t *ids = t_p(a, (sel >> 1) & 1u);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nown = sm.own_off[g.nown];
+    for (int p = warp; p < nown; p += TT / 32) {
+        int lo = 0, hi = g.nown - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sm.own_off[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        const int s = sm.own_slot[lo] + (p - sm.own_off[lo]);
+        const int id = ids[s];
+        const uint32_t c = a.cnt[s];
+        const int n0r = (int)(c & 0xffffu), nsr = (int)(c >> 16);
+        const int n0 = min(n0r, a.cap), ns = min(nsr, a.cap - n0);
+        const uint16_t *row = a.rows + (size_t)s * a.cap;
+        int32_t *out = a.nbr_out + (size_t)id * a.cap;
+        for (int k = lane; k < a.cap; k += 32) {
+            int v = a.N;
+            const int li = k < n0 + ns ? (int)row[k < n0 ? k : a.cap - ns + (k - n0)] : sm.total;
+            if (li < sm.total) {   // rows of a tile whose region overflowed were never written
+                int ql = 0, qh = g.nq - 1;
+                while (ql < qh) {
+                    const int mid = (ql + qh + 1) >> 1;
+                    if (sm.hoff[mid] <= li) ql = mid;
+                    else qh = mid - 1;
+                }
+                v = ids[__ldg(a.hstart + t_hglob(a, g, ql)) + (li - sm.hoff[ql])];
+            }
+            out[k] = v;
+        }
+        if (lane == 0) a.cnt_out[id] = n0r + nsr;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int g_tile_tpp = 4;
+
+static bool tile_plan(const md_space *s, const md_nbr *nb, TilePlan &tp)
+{
+    if (!nb || (s && s->dim != 3) || nb->dim != 3 || nb->N < 1 || (nb->cap & 1) || nb->cap > 0xffff) return false;
+    if (!(nb->r_cut > nb->skin)) return false;
+    return tile_geometry(nb->N, nb->ncell, tp);
+}
+
+static bool tiles_ready(const md_space *s, const md_nbr *nb, TilePlan &tp)
+{
+    return nb && nb->ws && nb->nbr && nb->cnt && nb->rref && (nb->flags & MD_NBR_TILES) && nbr_layout_ok(nb) &&
+           tile_plan(s, nb, tp);
+}
+
+static void make_tile_args(const md_space *s, const md_nbr *nb, const TilePlan &tp, uint32_t *d_status, TileArgs &a)
+{
+    memset(&a, 0, sizeof(a));
+    a.box = make_box(s);
+    a.N = nb->N;
+    a.cap = nb->cap;
+    for (int k = 0; k < 3; ++k) {
+        a.H[k] = tp.H[k];
+        a.hscale[k] = (float)((double)tp.H[k] / (double)s->L[k]);
+    }
+    a.t = tp.t;
+    a.nty = tp.nty;
+    a.ntz = tp.ntz;
+    a.ntiles = tp.ntiles;
+    a.reg_cap = tp.reg_cap;
+    a.nhc = tp.H[0] * tp.H[1] * tp.H[2];
+    a.r_list2 = nb->r_list2;
+    a.half_skin2 = nb->half_skin2;
+    const WsLayout wl = ws_layout(nb->N, nb->ncell_total, nb->cap, nb->flags, nb->ncell);
+    const TileLayout tl = tile_layout(nb->N, a.nhc, nb->cap, tp.ntiles);
+    char *b = (char *)nb->ws + wl.tiles;
+    a.hcount = (int32_t *)(b + tl.hcount);
+    a.hstart = (int32_t *)(b + tl.hstart);
+    a.bsum = (int32_t *)(b + tl.bsum);
+    a.key = (int32_t *)(b + tl.key);
+    a.rank = (int32_t *)(b + tl.rank);
+    a.tmp = (int32_t *)(b + tl.tmp);
+    a.rb0 = (float4 *)(b + tl.r0);
+    a.rb1 = (float4 *)(b + tl.r1);
+    a.vb0 = (float4 *)(b + tl.v0);
+    a.vb1 = (float4 *)(b + tl.v1);
+    a.pb0 = (int32_t *)(b + tl.p0);
+    a.pb1 = (int32_t *)(b + tl.p1);
+    a.rref = (float4 *)(b + tl.rref);
+    a.fs = (float4 *)(b + tl.fs);
+    a.cnt = (uint32_t *)(b + tl.cnt);
+    a.rows = (uint16_t *)(b + tl.rows);
+    a.tab = (int32_t *)(b + tl.tab);
+    const WsPtrs w = ws_ptrs(nb);
+    a.ctl = w.ctl;
+    a.partials = w.partials;
+    a.status = d_status;
+}
+
+static bool set_tile_pot(const md_pot *p, const md_nbr *nb, TileArgs &a)
+{
+    if (!p) return false;
+    a.pot = p->kind;
+    if (p->kind == MD_LJ) {
+        if (!(p->r_cut > 0.0f) || p->r_cut > nb->r_list) return false;
+        a.rc2 = p->r_cut * p->r_cut;
+        a.sigma2 = p->sigma * p->sigma;
+        a.c24eps = 24.0f * p->eps;
+        a.c4eps = 4.0f * p->eps;
+        a.e_shift = p->e_shift;
+        return true;
+    }
+    if (p->kind == MD_SOFT_SPHERE) {
+        a.eps = p->eps;
+        a.alpha = p->alpha;
+        return true;
+    }
+    return false;
+}
+
+// positions of the region, then one byte per own particle (kmap)
+static size_t tile_smem(const TileArgs &a) { return (size_t)a.reg_cap * (sizeof(float4) + 1) + 16; }
+
+template <typename K>
+static void tile_smem_attr(K kern)
+{
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_REG_CAP_MAX * (int)(sizeof(float4) + 1) + 16);
+}
+
+// Dynamic shared memory above 48 KB for the staging kernels, once per
+// device, before any launch or capture of them.
+static void ensure_tile_attrs()
+{
+    static std::mutex mu;
+    static unsigned long long done = 0ull;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done & (1ull << dev)) return;
+    tile_smem_attr(k_t_build);
+    tile_smem_attr(k_t_step<MD_LJ, 4, 0>);
+    tile_smem_attr(k_t_step<MD_LJ, 8, 0>);
+    tile_smem_attr(k_t_step<MD_LJ, 4, 2>);
+    tile_smem_attr(k_t_step<MD_LJ, 8, 2>);
+    tile_smem_attr(k_t_step<MD_SOFT_SPHERE, 4, 0>);
+    tile_smem_attr(k_t_step<MD_SOFT_SPHERE, 8, 0>);
+    tile_smem_attr(k_t_step<MD_SOFT_SPHERE, 4, 2>);
+    tile_smem_attr(k_t_step<MD_SOFT_SPHERE, 8, 2>);
+    done |= 1ull << dev;
+}
+
+// The rebuild chain (import: from the caller's arrays).
+static void enqueue_tile_chain(TileArgs a, int import, int gated, cudaStream_t st)
+{
+    a.import = import;
+    a.gated = gated;
+    const int gN = (a.N + TT - 1) / TT;
+    const int nb = (a.nhc + TSCAN_ITEMS - 1) / TSCAN_ITEMS;
+    k_t_bin<<<gN, TT, 0, st>>>(a);
+    k_t_scan1<<<nb, 1024, 0, st>>>(a);
+    k_t_scan2<<<1, 1024, 0, st>>>(a, nb);
+    k_t_scan3<<<(a.nhc + TT - 1) / TT, TT, 0, st>>>(a);
+    k_t_scatter<<<gN, TT, 0, st>>>(a);
+    k_t_place<<<gN, TT, 0, st>>>(a);
+    k_t_build<<<a.ntiles, TT, tile_smem(a), st>>>(a);
+    k_t_finish<<<1, 1, 0, st>>>(a);
+}
+
+template <int POT, int TPP, int KICK>
+static void launch_step_t(const TileArgs &a, cudaStream_t st)
+{
+    k_t_step<POT, TPP, KICK><<<a.ntiles, TT, tile_smem(a), st>>>(a);
+}
+
+template <int KICK>
+static void launch_step(const TileArgs &a, cudaStream_t st)
+{
+    if (a.pot == MD_LJ) {
+        if (g_tile_tpp == 4) launch_step_t<MD_LJ, 4, KICK>(a, st);
+        else launch_step_t<MD_LJ, 8, KICK>(a, st);
+    } else {
+        if (g_tile_tpp == 4) launch_step_t<MD_SOFT_SPHERE, 4, KICK>(a, st);
+        else launch_step_t<MD_SOFT_SPHERE, 8, KICK>(a, st);
+    }
+}
+
+static void enqueue_tile_export(TileArgs a, float *d_r, float *d_v, float *d_f, const md_nbr *nb, int rows,
+                                cudaStream_t st)
+{
+    a.r_out = (float4 *)d_r;
+    a.v_out = (float4 *)d_v;
+    a.f_out = (float4 *)d_f;
+    a.export_rows = rows;
+    a.rref_out = (float4 *)nb->rref;
+    a.nbr_out = nb->nbr;
+    a.cnt_out = nb->cnt;
+    k_t_export<<<(a.N + TT - 1) / TT, TT, 0, st>>>(a);
+    if (rows) k_t_rows<<<a.ntiles, TT, 0, st>>>(a);
+}
+
+// Cached graphs of the tiled NVE loop: import chain -> first kick ->
+// WHILE { IF(rebuild) { chain } -> fused step } -> export.
+struct TileGraph {
+    TileArgs key;
+    int device;
+    cudaGraphExec_t exec;
+};
+static std::vector<TileGraph> g_tile_graphs;
+static std::mutex g_tile_mu;
+
+static cudaGraphNodeParams *zparams(unsigned char *raw)
+{
+    memset(raw, 0, sizeof(cudaGraphNodeParams));
+    return reinterpret_cast<cudaGraphNodeParams *>(raw);
+}
+
+static md_status build_tile_graph(const TileArgs &a0, const md_nbr *nb, float *d_r, float *d_v, float *d_f,
+                                  cudaGraphExec_t *out)
+{
+    TileArgs a = a0;
+    cudaGraph_t g = nullptr;
+    JMD_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle hw, hi;
+    JMD_CUDA_TRY(cudaGraphConditionalHandleCreate(&hw, g, 1u, cudaGraphCondAssignDefault));
+    JMD_CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, g, 0u, cudaGraphCondAssignDefault));
+    a.cond_while = (unsigned long long)hw;
+    a.cond_if = (unsigned long long)hi;
+    a.use_cond = 1;
+    cudaStream_t cs = nullptr, cs2 = nullptr;
+    JMD_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    JMD_CUDA_TRY(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
+    JMD_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    enqueue_tile_chain(a, 1, 0, cs);
+    k_t_kick<<<(a.N + TT - 1) / TT, TT, 0, cs>>>(a);
+    alignas(cudaGraphNodeParams) unsigned char wraw[sizeof(cudaGraphNodeParams)];
+    cudaGraphNodeParams *wp = zparams(wraw);
+    wp->type = cudaGraphNodeTypeConditional;
+    wp->conditional.handle = hw;
+    wp->conditional.type = cudaGraphCondTypeWhile;
+    wp->conditional.size = 1;
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    JMD_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNode_t wn;
+    JMD_CUDA_TRY(cudaGraphAddNode(&wn, cg, deps, nullptr, nd, wp));
+    JMD_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+    enqueue_tile_export(a, d_r, d_v, d_f, nb, 1, cs);
+    JMD_CUDA_TRY(cudaStreamEndCapture(cs, &g));
+    cudaGraph_t body = wp->conditional.phGraph_out[0];
+
+    JMD_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    alignas(cudaGraphNodeParams) unsigned char iraw[sizeof(cudaGraphNodeParams)];
+    cudaGraphNodeParams *ip = zparams(iraw);
+    ip->type = cudaGraphNodeTypeConditional;
+    ip->conditional.handle = hi;
+    ip->conditional.type = cudaGraphCondTypeIf;
+    ip->conditional.size = 1;
+    JMD_CUDA_TRY(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNode_t in;
+    JMD_CUDA_TRY(cudaGraphAddNode(&in, cg, deps, nullptr, nd, ip));
+    JMD_CUDA_TRY(cudaStreamUpdateCaptureDependencies(cs, &in, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t ibody = ip->conditional.phGraph_out[0];
+    JMD_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs2, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    enqueue_tile_chain(a, 0, 0, cs2);
+    JMD_CUDA_TRY(cudaStreamEndCapture(cs2, &ibody));
+    launch_step<2>(a, cs);
+    JMD_CUDA_TRY(cudaStreamEndCapture(cs, &body));
+    cudaStreamDestroy(cs2);
+    cudaStreamDestroy(cs);
+    cudaGraphExec_t ex = nullptr;
+    JMD_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
+    cudaGraphDestroy(g);
+    *out = ex;
+    return MD_OK;
+}
+
+// md_integrate_nve on the tile engine (LJ / soft sphere, 3-D).
+md_status run_tiled_nve(const md_space *s, const md_pot *p, float *d_r, float *d_v, float *d_f, float mass, float dt,
+                        int nsteps, md_nbr *nb, double *d_PE, double *d_KE, int use_graph, uint32_t *d_status,
+                        cudaStream_t st)
+{
+    TilePlan tp;
+    if (!tiles_ready(s, nb, tp)) return MD_ERR_INVALID;
+    TileArgs a;
+    ensure_tile_attrs();
+    make_tile_args(s, nb, tp, d_status, a);
+    if (!set_tile_pot(p, nb, a)) return MD_ERR_INVALID;
+    a.r_in = (const float4 *)d_r;
+    a.v_in = (const float4 *)d_v;
+    a.f_in = (const float4 *)d_f;
+    a.hdm = 0.5f * dt / mass;
+    a.dt = dt;
+    a.mass = mass;
+    a.E_out = d_PE;
+    a.KE_out = d_KE;
+    a.series = 1;
+    a.variant = g_tile_tpp;
+    if (nsteps == 0) return MD_OK;
+    const uint32_t *ctl = a.ctl;
+    if (use_graph) {
+        int dev = 0;
+        JMD_CUDA_TRY(cudaGetDevice(&dev));
+        cudaGraphExec_t ex = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(g_tile_mu);
+            for (auto &e : g_tile_graphs)
+                if (e.device == dev && memcmp(&e.key, &a, sizeof(TileArgs)) == 0) ex = e.exec;
+            if (!ex) {
+                md_status e = build_tile_graph(a, nb, d_r, d_v, d_f, &ex);
+                if (e != MD_OK) return e;
+                TileGraph tg;
+                memset(&tg, 0, sizeof(tg));
+                tg.key = a;
+                tg.device = dev;
+                tg.exec = ex;
+                g_tile_graphs.push_back(tg);
+            }
+        }
+        enqueue_loop_init(const_cast<uint32_t *>(ctl), (uint32_t)nsteps, st);
+        JMD_CUDA_TRY(cudaGraphLaunch(ex, st));
+        JMD_CUDA_TRY(cudaGetLastError());
+        return MD_OK;
+    }
+    enqueue_loop_init(const_cast<uint32_t *>(ctl), (uint32_t)nsteps, st);
+    enqueue_tile_chain(a, 1, 0, st);
+    k_t_kick<<<(a.N + TT - 1) / TT, TT, 0, st>>>(a);
+    for (int k = 0; k < nsteps; ++k) {
+        enqueue_tile_chain(a, 0, 1, st);
+        launch_step<2>(a, st);
+    }
+    enqueue_tile_export(a, d_r, d_v, d_f, nb, 1, st);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+bool tiles_enabled(const md_space *s, const md_nbr *nb, const md_pot *p)
+{
+    TilePlan tp;
+    return p && (p->kind == MD_LJ || p->kind == MD_SOFT_SPHERE) && tiles_ready(s, nb, tp);
+}
+
+bool tiles_plan_ok(const md_space *s, const md_nbr *nb)
+{
+    TilePlan tp;
+    return tile_plan(s, nb, tp);
+}
+
+}  // namespace jmd
+
+using namespace jmd;
+
+extern "C" md_status md_set_tile_tpp(int tpp)
+{
+    if (tpp != 4 && tpp != 8) return MD_ERR_INVALID;
+    g_tile_tpp = tpp;
+    return MD_OK;
+}
+
+extern "C" md_status md_tiles_info(const md_space *s, const md_nbr *nb, int32_t *out)
+{
+    TilePlan tp;
+    if (!out || !tile_plan(s, nb, tp)) return MD_ERR_INVALID;
+    out[0] = tp.H[0];
+    out[1] = tp.H[1];
+    out[2] = tp.H[2];
+    out[3] = tp.t;
+    out[4] = tp.t;
+    out[5] = tp.ntiles;
+    out[6] = tp.reg_cap;
+    return MD_OK;
+}
+
+extern "C" md_status md_tiles_import(const md_space *s, const float *d_r, const float *d_v, const float *d_f,
+                                     md_nbr *nb, uint32_t *d_status, md_stream_t stream)
+{
+    TilePlan tp;
+    if (!d_r || !tiles_ready(s, nb, tp)) return MD_ERR_INVALID;
+    TileArgs a;
+    ensure_tile_attrs();
+    make_tile_args(s, nb, tp, d_status, a);
+    a.r_in = (const float4 *)d_r;
+    a.v_in = (const float4 *)d_v;
+    a.f_in = (const float4 *)d_f;
+    enqueue_tile_chain(a, 1, 0, (cudaStream_t)stream);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+extern "C" md_status md_tiles_forces(const md_space *s, const md_pot *p, md_nbr *nb, double *d_E, uint32_t *d_status,
+                                     md_stream_t stream)
+{
+    TilePlan tp;
+    if (!tiles_ready(s, nb, tp)) return MD_ERR_INVALID;
+    TileArgs a;
+    ensure_tile_attrs();
+    make_tile_args(s, nb, tp, d_status, a);
+    if (!set_tile_pot(p, nb, a)) return MD_ERR_INVALID;
+    a.E_out = d_E;
+    launch_step<0>(a, (cudaStream_t)stream);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+extern "C" md_status md_tiles_export(const md_space *s, md_nbr *nb, float *d_r, float *d_v, float *d_f, int rows,
+                                     md_stream_t stream)
+{
+    TilePlan tp;
+    if (!tiles_ready(s, nb, tp)) return MD_ERR_INVALID;
+    TileArgs a;
+    make_tile_args(s, nb, tp, nullptr, a);
+    enqueue_tile_export(a, d_r, d_v, d_f, nb, rows ? 1 : 0, (cudaStream_t)stream);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+extern "C" md_status md_tiles_steps(const md_space *s, const md_pot *p, md_nbr *nb, float mass, float dt, int nsteps,
+                                    double *d_PE, double *d_KE, uint32_t *d_status, md_stream_t stream)
+{
+    TilePlan tp;
+    if (!tiles_ready(s, nb, tp) || nsteps < 0 || !(mass > 0.0f)) return MD_ERR_INVALID;
+    TileArgs a;
+    ensure_tile_attrs();
+    make_tile_args(s, nb, tp, d_status, a);
+    if (!set_tile_pot(p, nb, a)) return MD_ERR_INVALID;
+    if (nsteps == 0) return MD_OK;
+    a.hdm = 0.5f * dt / mass;
+    a.dt = dt;
+    a.mass = mass;
+    a.E_out = d_PE;
+    a.KE_out = d_KE;
+    a.series = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    enqueue_loop_init(a.ctl, (uint32_t)nsteps, st);
+    k_t_kick<<<(a.N + TT - 1) / TT, TT, 0, st>>>(a);
+    for (int k = 0; k < nsteps; ++k) launch_step<2>(a, st);
+    JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}

@@ -34,6 +34,7 @@ MD_ERR_CUDA = 64
 MD_LJ, MD_SOFT_SPHERE, MD_SW, MD_BP, MD_GNN = 0, 1, 2, 3, 4
 MD_NBR_CANONICAL = 1
 MD_NBR_LOCAL_ROWS = 2
+MD_NBR_TILES = 4
 
 STATUS_NAMES = {MD_ERR_INVALID: "INVALID", MD_ERR_BOX_TOO_SMALL: "BOX_TOO_SMALL",
                 MD_ERR_NBR_OVERFLOW: "NBR_OVERFLOW", MD_ERR_NONFINITE: "NONFINITE",
@@ -167,6 +168,12 @@ _SIGS = {
                             C.c_float, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
     "md_minimize_fire_adjoint": [_P(md_space), _P(md_pot), _P(md_fire_params), _P(md_nbr), _vp, C.c_int, C.c_float,
                                  C.c_float, C.c_float, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "md_tiles_import": [_P(md_space), _vp, _vp, _vp, _P(md_nbr), _vp, _vp],
+    "md_tiles_forces": [_P(md_space), _P(md_pot), _P(md_nbr), _vp, _vp, _vp],
+    "md_tiles_export": [_P(md_space), _P(md_nbr), _vp, _vp, _vp, C.c_int, _vp],
+    "md_tiles_info": [_P(md_space), _P(md_nbr), _P(C.c_int32)],
+    "md_tiles_steps": [_P(md_space), _P(md_pot), _P(md_nbr), C.c_float, C.c_float, C.c_int, _vp, _vp, _vp, _vp],
+    "md_set_tile_tpp": [C.c_int],
     "md_neighbor_list_build_noalloc": [_P(md_space), _vp, C.c_int, C.c_float, C.c_float, C.c_int, _vp, _vp, _vp,
                                        _vp],
 }
@@ -297,6 +304,37 @@ def md_integrate_nve(space, pot, r, v, f, mass, dt, nsteps, nb, PE=None, KE=None
     _check(_lib.md_integrate_nve(C.byref(space), C.byref(pot), _ptr(r), _ptr(v), _ptr(f), float(mass), float(dt),
                                  int(nsteps), C.byref(nb), _ptr(PE), _ptr(KE), int(bool(use_graph)), _ptr(status),
                                  _stream(stream)), "md_integrate_nve")
+
+
+def md_tiles_import(space, r, v, f, nb, status=None, stream=None):
+    _check(_lib.md_tiles_import(C.byref(space), _ptr(r), _ptr(v), _ptr(f), C.byref(nb), _ptr(status),
+                                _stream(stream)), "md_tiles_import")
+
+
+def md_tiles_forces(space, pot, nb, E=None, status=None, stream=None):
+    _check(_lib.md_tiles_forces(C.byref(space), C.byref(pot), C.byref(nb), _ptr(E), _ptr(status), _stream(stream)),
+           "md_tiles_forces")
+
+
+def md_tiles_export(space, nb, r=None, v=None, f=None, rows=False, stream=None):
+    _check(_lib.md_tiles_export(C.byref(space), C.byref(nb), _ptr(r), _ptr(v), _ptr(f), int(bool(rows)),
+                                _stream(stream)), "md_tiles_export")
+
+
+def md_tiles_steps(space, pot, nb, mass, dt, nsteps, PE=None, KE=None, status=None, stream=None):
+    _check(_lib.md_tiles_steps(C.byref(space), C.byref(pot), C.byref(nb), float(mass), float(dt), int(nsteps),
+                               _ptr(PE), _ptr(KE), _ptr(status), _stream(stream)), "md_tiles_steps")
+
+
+def md_tiles_info(space, nb):
+    """(H (3 half-cells per axis), tile extent y, z, number of tiles, region capacity)."""
+    out = (C.c_int32 * 7)()
+    _check(_lib.md_tiles_info(C.byref(space), C.byref(nb), out), "md_tiles_info")
+    return {"H": tuple(out[0:3]), "tile": (1, out[3], out[4]), "ntiles": out[5], "region_cap": out[6]}
+
+
+def md_set_tile_tpp(tpp: int):
+    _check(_lib.md_set_tile_tpp(int(tpp)), "md_set_tile_tpp")
 
 
 def md_integrate_langevin(space, pot, r, v, f, mass, dt, gamma, kT, seed, step0, nsteps, nb, PE=None, KE=None,
@@ -651,11 +689,12 @@ class NeighborList:
     """Plans a list, allocates its caller-owned tensors with torch and binds them."""
 
     def __init__(self, space: md_space, N: int, r_cut: float, skin: float, cap: int, device="cuda", stream=None,
-                 canonical: bool = False, local_rows: bool = False):
+                 canonical: bool = False, local_rows: bool = False, tiles: bool = False):
         import torch
         self.space = space
         self.plan = md_nbr_plan(space, N, r_cut, skin, cap)
-        flags = (MD_NBR_CANONICAL if canonical else 0) | (MD_NBR_LOCAL_ROWS if local_rows else 0)
+        flags = ((MD_NBR_CANONICAL if canonical else 0) | (MD_NBR_LOCAL_ROWS if local_rows else 0)
+                 | (MD_NBR_TILES if tiles else 0))
         if flags:
             md_nbr_set_flags(self.plan, flags)
         self.nbr = torch.empty((N, cap), dtype=torch.int32, device=device)
