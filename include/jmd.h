@@ -133,9 +133,9 @@ typedef struct {
  * (side >= r_list / 2, twice the list's cells per axis, members of a
  * half-cell by ascending caller index), and writes each particle's row as
  * 16-bit indices into the positions of its tile's region.  A tile is a
- * 1 x t x t column of half-cells (t <= 8); its region is the tile grown by
- * two half-cells on each side (periodic), its half-cells in (z, y, x)
- * order.  One CTA per tile stages the region's positions in shared memory
+ * block of tx x ty x tz half-cells (tx <= 2, ty, tz <= 8, chosen per plan,
+ * md_tiles_info); its region is the tile grown by two half-cells on each
+ * side (periodic), its half-cells in (z, y, x) order.  One CTA per tile stages the region's positions in shared memory
  * with bulk (TMA) copies and evaluates forces, the closing half-kick, the
  * next kick-drift and the displacement check from there.  A row holds the
  * partners whose nearest image is the plain difference first, then (stored
@@ -441,8 +441,8 @@ JMD_API md_status md_tiles_steps(const md_space *s, const md_pot *p, md_nbr *nb,
                                  double *d_PE, double *d_KE, uint32_t *d_status, md_stream_t stream);
 
 /* Geometry the tile engine chose for a plan: half-cells per axis (3), the
- * tile's extent along y and z (2), number of tiles, region capacity in
- * particles.  out: 7 ints.  MD_ERR_INVALID if the plan cannot use tiles. */
+ * tile's extent along x, y and z (3), number of tiles, region capacity in
+ * particles.  out: 8 ints.  MD_ERR_INVALID if the plan cannot use tiles. */
 JMD_API md_status md_tiles_info(const md_space *s, const md_nbr *nb, int32_t *out);
 
 /* Lanes per particle of the tile force kernel: 4 (default) or 8. */

@@ -274,59 +274,67 @@ __host__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // nhc = half-cells (2 x 2 x 2 per cell of the list's grid).
 constexpr int TSCAN_ITEMS = 4096;       // half-cells per block of the histogram scan
 constexpr int TILE_TMAX = 8;            // largest tile extent (half-cells) along y and z
+constexpr int TILE_XMAX = 2;            // ... and along x
 constexpr int TILE_PIECES_MAX = 2 * (TILE_TMAX + 4) * (TILE_TMAX + 4);   // two copies per region row
-constexpr int TILE_OWN_MAX = TILE_TMAX * TILE_TMAX;                      // own half-cells
+constexpr int TILE_OWN_MAX = TILE_XMAX * TILE_TMAX * TILE_TMAX;          // own half-cells
 // Per-tile table written by each build and read by every step: region
 // total, copies, own half-cells, own particles; the copies (source slot,
 // destination offset << 16 | count); the own half-cells (first slot,
 // first local index << 16 | first own particle).
 constexpr int TILE_TAB_WORDS = 4 + 2 * TILE_PIECES_MAX + 2 * TILE_OWN_MAX;
 constexpr int TILE_REG_CAP_MAX = 12800;  // region capacity limit (particles, 200 KB of shared memory)
-constexpr int TILE_TARGET = 300;         // tiles wanted for load balance (about 2 per SM)
+constexpr int TILE_SLOTS = 4 * 148;      // resident tile CTAs of a B300 (148 SMs, 4 per SM) for the shape choice
 
 struct TilePlan {
     int H[3];
-    int t, nty, ntz, ntiles, reg_cap;
+    int tx, ty, tz, ntx, nty, ntz, ntiles, reg_cap;
 };
 
 // Tile geometry of N particles on a list grid of ncell cells per axis:
-// half-cells H = 2 ncell; tiles of 1 x t x t half-cells with t the largest
-// of 8, 6, 4, 2 that fits (t + 4 <= H) and still gives TILE_TARGET tiles;
-// region capacity 1.25x the mean region count plus 128.
+// half-cells H = 2 ncell; tiles of tx x ty x tz half-cells (tx in {1, 2},
+// ty, tz in {2, 4, 6, 8}, region = tile grown by 2 on each side, which must
+// not wrap onto itself).  The shape minimises a cost model of the step
+// kernel in particle units: waves of TILE_SLOTS CTAs times the per-tile
+// work (own particles + 0.08 x staged region particles + 40 fixed).
+// Region capacity 1.25x the mean region count plus 128.
 __host__ inline bool tile_geometry(int N, const int *ncell, TilePlan &tp)
 {
     for (int k = 0; k < 3; ++k) {
         if (ncell[k] < 3) return false;
         tp.H[k] = 2 * ncell[k];
     }
-    int best = -1, last = -1;
-    const int cand_t[4] = {8, 6, 4, 2};
-    for (int c = 0; c < 4; ++c) {
-        const int t = cand_t[c];
-        if (t + 4 > tp.H[1] || t + 4 > tp.H[2]) continue;
-        const long long nt = (long long)tp.H[0] * ((tp.H[1] + t - 1) / t) * ((tp.H[2] + t - 1) / t);
-        last = t;
-        if (nt >= TILE_TARGET) {
-            best = t;
-            break;
-        }
-    }
-    if (best < 0) best = last;
-    if (best < 0) return false;
-    tp.t = best;
-    tp.nty = (tp.H[1] + best - 1) / best;
-    tp.ntz = (tp.H[2] + best - 1) / best;
-    const long long nt = (long long)tp.H[0] * tp.nty * tp.ntz;
-    if (nt > (long long)(N / 4 + 64)) return false;   // FP64 partials of the energy reduction
-    tp.ntiles = (int)nt;
     const double hc = (double)tp.H[0] * tp.H[1] * tp.H[2];
     if (hc > (double)TSCAN_ITEMS * 4096.0) return false;
-    const double mean = (double)N / hc * 5.0 * (best + 4) * (best + 4);
-    int cap = (int)ceil(1.25 * mean) + 128;
-    cap = (cap + 31) & ~31;
-    if (cap > TILE_REG_CAP_MAX) return false;
-    tp.reg_cap = cap;
-    return true;
+    const int cx[2] = {2, 1}, cyz[4] = {8, 6, 4, 2};
+    double best = -1.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 4; ++b)
+            for (int c = 0; c < 4; ++c) {
+                const int tx = cx[a], ty = cyz[b], tz = cyz[c];
+                if (tx + 4 > tp.H[0] || ty + 4 > tp.H[1] || tz + 4 > tp.H[2]) continue;
+                const int ntx = (tp.H[0] + tx - 1) / tx, nty = (tp.H[1] + ty - 1) / ty, ntz = (tp.H[2] + tz - 1) / tz;
+                const long long nt = (long long)ntx * nty * ntz;
+                if (nt > (long long)(N / 4 + 64)) continue;   // FP64 partials of the energy reduction
+                const double own = (double)N * tx * ty * tz / hc;
+                const double reg = (double)N * (tx + 4) * (ty + 4) * (tz + 4) / hc;
+                const double waves = (double)((nt + TILE_SLOTS - 1) / TILE_SLOTS);
+                const double cost = waves * (own + 0.08 * reg + 40.0);
+                int cap = (int)ceil(1.25 * reg) + 128;
+                cap = (cap + 31) & ~31;
+                if (cap > TILE_REG_CAP_MAX) continue;
+                if (best < 0.0 || cost < best) {
+                    best = cost;
+                    tp.tx = tx;
+                    tp.ty = ty;
+                    tp.tz = tz;
+                    tp.ntx = ntx;
+                    tp.nty = nty;
+                    tp.ntz = ntz;
+                    tp.ntiles = (int)nt;
+                    tp.reg_cap = cap;
+                }
+            }
+    return best >= 0.0;
 }
 
 struct TileLayout {

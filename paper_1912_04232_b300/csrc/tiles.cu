@@ -47,14 +47,23 @@
 
 namespace jmd {
 
+// Self-checks of the staging and row indices (built with -DJMD_TILE_CHECKS):
+// a failed check counts itself in ctl[32 + id], raises MD_ERR_BOUNDS and
+// skips the access.
+#ifdef JMD_TILE_CHECKS
+#define TCHECK(a, cond, id) ((cond) ? true : (atomicAdd(&(a).ctl[32 + (id)], 1u), raise_status((a).status, MD_ERR_BOUNDS), false))
+#else
+#define TCHECK(a, cond, id) true
+#endif
+
 constexpr int TT = 256;                                          // threads per CTA of every tile kernel
-constexpr int NQ_MAX = 5 * (TILE_TMAX + 4) * (TILE_TMAX + 4);   // region half-cells
+constexpr int NQ_MAX = (TILE_XMAX + 4) * (TILE_TMAX + 4) * (TILE_TMAX + 4);   // region half-cells
 constexpr int OWN_MAX = TILE_OWN_MAX;                            // own half-cells of a tile
 
 struct TileArgs {
     Box box;
     int N, cap;
-    int H[3], t, nty, ntz, ntiles, reg_cap, nhc;
+    int H[3], tx, ty, tz, ntx, nty, ntz, ntiles, reg_cap, nhc;
     float hscale[3];
     float r_list2, half_skin2;
     int32_t *hcount, *hstart, *bsum, *key, *rank, *tmp;
@@ -113,34 +122,43 @@ __device__ __forceinline__ uint32_t ld_nc_u32(const uint16_t *p)
     return v;
 }
 
-// Tile geometry: column x0, own half-cells y0..y0+ny-1, z0..z0+nz-1.
+// Tile geometry: own half-cells x0..x0+nx-1, y0..y0+ny-1, z0..z0+nz-1; the
+// region is RX x RY x RZ half-cells from (x0-2, y0-2, z0-2), periodic.
 struct TGeo {
-    int x0, y0, z0, ny, nz, RY, RZ, nq, nown;
+    int x0, y0, z0, nx, ny, nz, RX, RY, RZ, nq, nown;
 };
 __device__ __forceinline__ TGeo t_geo(const TileArgs &a, int b)
 {
     TGeo g;
-    g.x0 = b % a.H[0];
-    const int r = b / a.H[0];
+    const int ix = b % a.ntx, r = b / a.ntx;
     const int iy = r % a.nty, iz = r / a.nty;
-    g.y0 = iy * a.t;
-    g.z0 = iz * a.t;
-    g.ny = min(a.t, a.H[1] - g.y0);
-    g.nz = min(a.t, a.H[2] - g.z0);
+    g.x0 = ix * a.tx;
+    g.y0 = iy * a.ty;
+    g.z0 = iz * a.tz;
+    g.nx = min(a.tx, a.H[0] - g.x0);
+    g.ny = min(a.ty, a.H[1] - g.y0);
+    g.nz = min(a.tz, a.H[2] - g.z0);
+    g.RX = g.nx + 4;
     g.RY = g.ny + 4;
     g.RZ = g.nz + 4;
-    g.nq = 5 * g.RY * g.RZ;
-    g.nown = g.ny * g.nz;
+    g.nq = g.RX * g.RY * g.RZ;
+    g.nown = g.nx * g.ny * g.nz;
     return g;
 }
 // Global half-cell of region half-cell q.
 __device__ __forceinline__ int t_hglob(const TileArgs &a, const TGeo &g, int q)
 {
-    const int xl = q % 5, yl = (q / 5) % g.RY, zl = q / (5 * g.RY);
+    const int xl = q % g.RX, yl = (q / g.RX) % g.RY, zl = q / (g.RX * g.RY);
     const int gx = wrapi(g.x0 - 2 + xl, a.H[0]);
     const int gy = wrapi(g.y0 - 2 + yl, a.H[1]);
     const int gz = wrapi(g.z0 - 2 + zl, a.H[2]);
     return (gz * a.H[1] + gy) * a.H[0] + gx;
+}
+// Region half-cell of own half-cell k.
+__device__ __forceinline__ int t_ownq(const TGeo &g, int k)
+{
+    const int xo = k % g.nx, yo = (k / g.nx) % g.ny, zo = k / (g.nx * g.ny);
+    return (2 + xo) + g.RX * ((2 + yo) + g.RY * (2 + zo));
 }
 
 struct TileSm {
@@ -249,11 +267,10 @@ __device__ void tile_scan(const TileArgs &a, const TGeo &g, TileSm &sm)
         sm.total = tot;
     }
     __syncthreads();
-    // own half-cells: region (2, 2 + k % ny, 2 + k / ny)
+    // own half-cells: region (2 + xo, 2 + yo, 2 + zo)
     int oc = 0;
     if (tid < g.nown) {
-        const int yl = 2 + tid % g.ny, zl = 2 + tid / g.ny;
-        const int q = 2 + 5 * (yl + g.RY * zl);
+        const int q = t_ownq(g, tid);
         sm.own_loc[tid] = sm.hoff[q];
         oc = sm.hoff[q + 1] - sm.hoff[q];
         sm.own_slot[tid] = __ldg(a.hstart + t_hglob(a, g, q));
@@ -327,16 +344,18 @@ __device__ bool tile_stage_build(const TileArgs &a, const TGeo &g, TileSm &sm, c
     }
     __syncthreads();
     for (int r = tid; r < g.RY * g.RZ; r += TT) {
-        const int q0 = 5 * r;
+        const int q0 = g.RX * r;
         int qs = q0;
         int2 pa = make_int2(0, 0), pb = make_int2(0, 0);
-        for (int xl = 1; xl <= 5; ++xl) {
-            const bool brk = xl == 5 || wrapi(g.x0 - 2 + xl, a.H[0]) == 0;
+        for (int xl = 1; xl <= g.RX; ++xl) {
+            const bool brk = xl == g.RX || wrapi(g.x0 - 2 + xl, a.H[0]) == 0;
             if (brk) {
                 const int n = sm.hoff[q0 + xl] - sm.hoff[qs];
                 const int src = __ldg(a.hstart + t_hglob(a, g, qs));
                 if (n > 0) {
-                    if (fits) bulk_g2s(cand + sm.hoff[qs], rsrc + src, (unsigned)n * 16u, &sm.bar);
+                    if (fits && TCHECK(a, sm.hoff[qs] + n <= tot && src >= 0 && src + n <= a.N &&
+                                              (sm_addr(cand) & 15u) == 0u, 2))
+                        bulk_g2s(cand + sm.hoff[qs], rsrc + src, (unsigned)n * 16u, &sm.bar);
                     const int2 pc = make_int2(src, (int)(((unsigned)sm.hoff[qs] << 16) | (unsigned)n));
                     if (pa.y == 0) pa = pc;
                     else pb = pc;
@@ -351,15 +370,18 @@ __device__ bool tile_stage_build(const TileArgs &a, const TGeo &g, TileSm &sm, c
     return tile_wait(a, sm);
 }
 
-// Step: stage the region from the tile's table (copies and own half-cells
-// as the last build left them).  Returns false (uniformly) if the region
-// exceeds the capacity (the build raised the overflow) or the copies timed
-// out.
-__device__ bool tile_stage_tab(const TileArgs &a, TileSm &sm, const float4 *rsrc, float4 *cand, const int32_t *tab)
+// Step: issue the copies of the region from the tile's table (copies and own
+// half-cells as the last build left them); tile_wait completes them.
+// Returns false (uniformly, nothing issued) if the region exceeds the
+// capacity (the build raised the overflow).
+__device__ bool tile_issue_tab(const TileArgs &a, TileSm &sm, const float4 *rsrc, float4 *cand, const int32_t *tab)
 {
     const int tid = threadIdx.x;
     const int tot = __ldg(tab + 0), npc = __ldg(tab + 1), nown = __ldg(tab + 2);
     if (tot > a.reg_cap) return false;
+    if (!TCHECK(a, tot >= 0 && npc >= 0 && npc <= TILE_PIECES_MAX && nown >= 0 && nown <= TILE_OWN_MAX &&
+                       (sm_addr(cand) & 15u) == 0u && (sm_addr(&sm.bar) & 7u) == 0u, 0))
+        return false;
     if (tid == 0) {
         sm.total = tot;
         sm.nown = nown;
@@ -378,9 +400,10 @@ __device__ bool tile_stage_tab(const TileArgs &a, TileSm &sm, const float4 *rsrc
     for (int k = tid; k < npc; k += TT) {
         const int2 c = __ldg(pc + k);
         const unsigned n = (unsigned)c.y & 0xffffu;
-        if (n > 0u) bulk_g2s(cand + ((unsigned)c.y >> 16), rsrc + c.x, n * 16u, &sm.bar);
+        if (n > 0u && TCHECK(a, ((unsigned)c.y >> 16) + n <= (unsigned)tot && c.x >= 0 && c.x + (int)n <= a.N, 1))
+            bulk_g2s(cand + ((unsigned)c.y >> 16), rsrc + c.x, n * 16u, &sm.bar);
     }
-    return tile_wait(a, sm);
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -573,7 +596,7 @@ __device__ __forceinline__ int build_particle(const TileArgs &a, const TGeo &g, 
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int yl = 2 + k % g.ny, zl = 2 + k / g.ny;
+    const int yl = 2 + (k / g.nx) % g.ny, zl = 2 + k / (g.nx * g.ny);
     const float4 ri = cand[loc];
     const float L0 = a.box.L[0], L1 = a.box.L[1], L2 = a.box.L[2];
     const float I0 = a.box.Linv[0], I1 = a.box.Linv[1], I2 = a.box.Linv[2];
@@ -598,8 +621,8 @@ __device__ __forceinline__ int build_particle(const TileArgs &a, const TGeo &g, 
             const float h1 = fmaxf(0.f, (float)(g.y0 - 1 + yl) * wy - ri.y);   // bottom edge of row yl+1
             const int ya = g0 * g0 + rz2 <= lim2 ? yl - 2 : (g1 * g1 + rz2 <= lim2 ? yl - 1 : yl);
             const int yb = h0 * h0 + rz2 <= lim2 ? yl + 2 : (h1 * h1 + rz2 <= lim2 ? yl + 1 : yl);
-            beg[d] = sm.hoff[5 * (ya + g.RY * zr)];
-            len[d] = rz2 <= lim2 ? sm.hoff[5 * (yb + 1 + g.RY * zr)] - beg[d] : 0;
+            beg[d] = sm.hoff[g.RX * (ya + g.RY * zr)];
+            len[d] = rz2 <= lim2 ? sm.hoff[g.RX * (yb + 1 + g.RY * zr)] - beg[d] : 0;
         }
         b0 = beg[0]; b1 = beg[1]; b2 = beg[2]; b3 = beg[3]; b4 = beg[4];
         p1 = len[0]; p2 = p1 + len[1]; p3 = p2 + len[2]; p4 = p3 + len[3]; p5 = p4 + len[4];
@@ -676,8 +699,8 @@ __global__ void __launch_bounds__(TT) k_t_build(TileArgs a)
     for (int p = warp; p < nown; p += TT / 32) {
         const int k = sm.kmap[p];
         const int t = p - sm.own_off[k];
-        const int gy = g.y0 + k % g.ny, gz = g.z0 + k / g.ny;
-        const bool bnd = g.x0 < 2 || g.x0 >= a.H[0] - 2 || gy < 2 || gy >= a.H[1] - 2 || gz < 2 || gz >= a.H[2] - 2;
+        const int gx = g.x0 + k % g.nx, gy = g.y0 + (k / g.nx) % g.ny, gz = g.z0 + k / (g.nx * g.ny);
+        const bool bnd = gx < 2 || gx >= a.H[0] - 2 || gy < 2 || gy >= a.H[1] - 2 || gz < 2 || gz >= a.H[2] - 2;
         const int loc = sm.own_loc[k] + t, slot = sm.own_slot[k] + t;
         const int n = bnd ? build_particle<true>(a, g, sm, cand, k, loc, slot)
                           : build_particle<false>(a, g, sm, cand, k, loc, slot);
@@ -763,7 +786,8 @@ __device__ __forceinline__ void t_pair_image(const TileArgs &a, const float4 &ri
 // order) across blocks; the last block writes the series, advances the step,
 // sets the graph conditions and, after a step that moved the particles,
 // switches the position buffer.
-__device__ __forceinline__ void t_epilogue(float pe_acc, float ke_acc, const TileArgs &a, bool flip)
+__device__ __forceinline__ void t_epilogue(float pe_acc, float ke_acc, const TileArgs &a, bool flip,
+                                           const int *moved_flag)
 {
     __shared__ double sh[2][32];
     __shared__ bool last;
@@ -784,6 +808,9 @@ __device__ __forceinline__ void t_epilogue(float pe_acc, float ke_acc, const Til
             bpe += sh[0][k];
             bke += sh[1][k];
         }
+        // one rebuild-flag store per block, ordered before the ticket by the
+        // fence below (a fence per warp costs much when most particles moved)
+        if (moved_flag && *moved_flag) a.ctl[CTL_REBUILD] = 1u;
         a.partials[blockIdx.x] = make_double2(bpe, bke);
         __threadfence();
         const unsigned t = atomicAdd(&a.ctl[CTL_TICKET], 1u);
@@ -822,14 +849,80 @@ __device__ __forceinline__ void t_epilogue(float pe_acc, float ke_acc, const Til
 // forces, then, unless this is the loop's last step, the next kick and
 // drift into the other position buffer with the displacement check; the
 // last step writes the forces instead).
+// Per-particle operands of one pass: the count, the first 2 RW TPP row
+// entries and the last RS TPP (fixed positions, so the loads need not wait
+// for the count), velocity and build position (group leader).  Entries
+// beyond the count are uninitialised memory: t_mask zeroes them before any
+// use, so every index that reaches shared memory is inside the region.
+// Local index j of the staged region, checked under JMD_TILE_CHECKS.
+__device__ __forceinline__ int tj(const TileArgs &a, unsigned j, int tot)
+{
+    return TCHECK(a, j < (unsigned)tot, 4) ? (int)j : 0;
+}
+
+template <int TPP, int KICK>
+struct TPre {
+    static constexpr int RW = 40 / TPP;   // row words (two entries each) per lane: 80 entries per group
+    static constexpr int RS = 16 / TPP;   // tail entries per lane: 16 per group
+    uint32_t c;
+    uint32_t w[RW];
+    int js[RS];
+    float4 v, rr;
+    int s, li;
+};
+
+template <int TPP, int KICK>
+__device__ __forceinline__ void t_prefetch(const TileArgs &a, const TileSm &sm, const float4 *vv, bool more, int p,
+                                           int lg, TPre<TPP, KICK> &q)
+{
+    const int k = sm.kmap[p];
+    const int t = p - sm.own_off[k];
+    q.s = sm.own_slot[k] + t;
+    q.li = sm.own_loc[k] + t;
+    q.c = __ldg(a.cnt + q.s);
+    const uint16_t *row = a.rows + (size_t)q.s * a.cap;
+#pragma unroll
+    for (int k2 = 0; k2 < TPre<TPP, KICK>::RW; ++k2) {
+        const int wi = lg + k2 * TPP;
+        q.w[k2] = 2 * wi + 1 < a.cap ? ld_nc_u32(row + 2 * wi) : 0u;
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < TPre<TPP, KICK>::RS; ++k2) {
+        const int kk = lg + k2 * TPP;
+        q.js[k2] = kk < a.cap ? ld_stream_u16(row + a.cap - 1 - kk) : 0;
+    }
+    if (KICK == 2 && lg == 0) {
+        q.v = vv[q.s];
+        if (more) q.rr = __ldg(a.rref + q.s);
+    }
+}
+
+// Zero the prefetched entries at and beyond the counts n0 (head) and ns
+// (tail from the end).
+template <int TPP, int KICK>
+__device__ __forceinline__ void t_mask(TPre<TPP, KICK> &q, int lg, int n0, int ns)
+{
+#pragma unroll
+    for (int k2 = 0; k2 < TPre<TPP, KICK>::RW; ++k2) {
+        const int e = 2 * (lg + k2 * TPP);
+        q.w[k2] = e + 1 < n0 ? q.w[k2] : (e < n0 ? (q.w[k2] & 0xffffu) : 0u);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < TPre<TPP, KICK>::RS; ++k2) q.js[k2] = lg + k2 * TPP < ns ? q.js[k2] : 0;
+}
+
+// One CTA per tile.  KICK 0: forces and per-particle energies into fs;
+// KICK 2: the fused velocity-Verlet step (closing half-kick at the new
+// forces, then, unless this is the loop's last step, the next kick and
+// drift into the other position buffer with the displacement check; the
+// last step writes the forces instead).
 template <int POT, int TPP, int KICK>
 __global__ void __launch_bounds__(TT, 4) k_t_step(TileArgs a)
 {
     count_launch();
     extern __shared__ __align__(16) float4 cand[];
     __shared__ TileSm sm;
-    constexpr int RW = 40 / TPP;      // row words (two entries each) per lane fetched ahead: 80 entries per group
-    constexpr int RS = 16 / TPP;      // tail entries per lane fetched ahead: 16 per group
+    using Pre = TPre<TPP, KICK>;
     const uint32_t sel = t_sel(a);
     const uint32_t rcb = sel & 1u;
     const float4 *rc = t_r(a, rcb);
@@ -840,13 +933,17 @@ __global__ void __launch_bounds__(TT, 4) k_t_step(TileArgs a)
         const uint32_t step = *(volatile uint32_t *)&a.ctl[CTL_STEP];
         more = step + 1u < *(volatile uint32_t *)&a.ctl[CTL_NSTEPS];
     }
-    if (threadIdx.x == 0) sm.kmap = reinterpret_cast<unsigned char *>(cand + a.reg_cap);
+    __shared__ int moved_any;
+    if (threadIdx.x == 0) {
+        sm.kmap = reinterpret_cast<unsigned char *>(cand + a.reg_cap);
+        moved_any = 0;
+    }
     float pe_acc = 0.f, ke_acc = 0.f;
-    bool moved = false;
-    if (tile_stage_tab(a, sm, rc, cand, a.tab + (size_t)blockIdx.x * TILE_TAB_WORDS)) {
+    if (tile_issue_tab(a, sm, rc, cand, a.tab + (size_t)blockIdx.x * TILE_TAB_WORDS) && tile_wait(a, sm)) {
         tile_own_map(sm);
         const int lg = threadIdx.x & (TPP - 1), gi = threadIdx.x / TPP;
         const int nown = sm.own_off[sm.nown];
+        const int tot = sm.total;
         // every lane of a warp runs every trip (the group reductions below
         // are full-warp shuffles); lanes past the tile's last particle
         // carry zeros
@@ -854,55 +951,35 @@ __global__ void __launch_bounds__(TT, 4) k_t_step(TileArgs a)
             const int p = p0 + gi;
             const bool valid = p < nown;
             float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
-            int s = 0;
-            float4 ri = make_float4(0.f, 0.f, 0.f, 0.f), vi = ri, rr = ri;
+            float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
+            Pre q;
             if (valid) {
-                const int k = sm.kmap[p];
-                const int t = p - sm.own_off[k];
-                s = sm.own_slot[k] + t;
-                const uint32_t c = __ldg(a.cnt + s);
-                ri = cand[sm.own_loc[k] + t];
-                // the kick's operands are fetched now, used after the sums
-                if (KICK == 2 && lg == 0) {
-                    vi = vv[s];
-                    if (more) rr = __ldg(a.rref + s);
-                }
-                const int n0 = min((int)(c & 0xffffu), a.cap);
-                const int ns = min((int)(c >> 16), a.cap - n0);
-                const uint16_t *row = a.rows + (size_t)s * a.cap;
-                // the lane's row words and tail entries fetched ahead
-                uint32_t w[RW];
-                int js[RS];
-#pragma unroll
-                for (int k2 = 0; k2 < RW; ++k2) {
-                    const int wi = lg + k2 * TPP;
-                    w[k2] = 2 * wi < n0 ? ld_nc_u32(row + 2 * wi) : 0u;
-                }
-#pragma unroll
-                for (int k2 = 0; k2 < RS; ++k2) {
-                    const int ki = lg + k2 * TPP;
-                    js[k2] = ki < ns ? ld_stream_u16(row + a.cap - ns + ki) : 0;
-                }
+                t_prefetch<TPP, KICK>(a, sm, vv, more, p, lg, q);
+                ri = cand[q.li];
+                const int n0 = min((int)(q.c & 0xffffu), a.cap);
+                const int ns = min((int)(q.c >> 16), a.cap - n0);
+                t_mask<TPP, KICK>(q, lg, n0, ns);
                 // partners whose nearest image is the plain difference
 #pragma unroll
-                for (int k2 = 0; k2 < RW; ++k2) {
+                for (int k2 = 0; k2 < Pre::RW; ++k2) {
                     const int wi = lg + k2 * TPP;
                     if (2 * wi < n0) {
-                        t_pair_plain<POT>(a, ri, cand[w[k2] & 0xffffu], fx, fy, fz, e);
-                        if (2 * wi + 1 < n0) t_pair_plain<POT>(a, ri, cand[w[k2] >> 16], fx, fy, fz, e);
+                        t_pair_plain<POT>(a, ri, cand[tj(a, q.w[k2] & 0xffffu, tot)], fx, fy, fz, e);
+                        if (2 * wi + 1 < n0) t_pair_plain<POT>(a, ri, cand[tj(a, q.w[k2] >> 16, tot)], fx, fy, fz, e);
                     }
                 }
-                for (int wi = lg + RW * TPP; 2 * wi < n0; wi += TPP) {   // rows longer than 80
+                const uint16_t *row = a.rows + (size_t)q.s * a.cap;
+                for (int wi = lg + Pre::RW * TPP; 2 * wi < n0; wi += TPP) {   // rows longer than 80
                     const uint32_t x = ld_nc_u32(row + 2 * wi);
-                    t_pair_plain<POT>(a, ri, cand[x & 0xffffu], fx, fy, fz, e);
-                    if (2 * wi + 1 < n0) t_pair_plain<POT>(a, ri, cand[x >> 16], fx, fy, fz, e);
+                    t_pair_plain<POT>(a, ri, cand[tj(a, x & 0xffffu, tot)], fx, fy, fz, e);
+                    if (2 * wi + 1 < n0) t_pair_plain<POT>(a, ri, cand[tj(a, x >> 16, tot)], fx, fy, fz, e);
                 }
-                // partners across the box boundary (row tail)
+                // partners across the box boundary (row tail, from the end)
 #pragma unroll
-                for (int k2 = 0; k2 < RS; ++k2)
-                    if (lg + k2 * TPP < ns) t_pair_image<POT>(a, ri, cand[js[k2]], fx, fy, fz, e);
-                for (int ki = lg + RS * TPP; ki < ns; ki += TPP)
-                    t_pair_image<POT>(a, ri, cand[ld_stream_u16(row + a.cap - ns + ki)], fx, fy, fz, e);
+                for (int k2 = 0; k2 < Pre::RS; ++k2)
+                    if (lg + k2 * TPP < ns) t_pair_image<POT>(a, ri, cand[tj(a, q.js[k2], tot)], fx, fy, fz, e);
+                for (int kk = lg + Pre::RS * TPP; kk < ns; kk += TPP)
+                    t_pair_image<POT>(a, ri, cand[tj(a, ld_stream_u16(row + a.cap - 1 - kk), tot)], fx, fy, fz, e);
             }
 #pragma unroll
             for (int o = TPP / 2; o > 0; o >>= 1) {
@@ -915,8 +992,9 @@ __global__ void __launch_bounds__(TT, 4) k_t_step(TileArgs a)
                 const float ei = 0.5f * e;
                 pe_acc += ei;
                 if (KICK == 0) {
-                    a.fs[s] = make_float4(fx, fy, fz, ei);
+                    a.fs[q.s] = make_float4(fx, fy, fz, ei);
                 } else {
+                    float4 vi = q.v;
                     vi.x += a.hdm * fx;
                     vi.y += a.hdm * fy;
                     vi.z += a.hdm * fz;
@@ -929,22 +1007,18 @@ __global__ void __launch_bounds__(TT, 4) k_t_step(TileArgs a)
                         r2.x = ri.x + a.dt * vi.x;
                         r2.y = ri.y + a.dt * vi.y;
                         r2.z = ri.z + a.dt * vi.z;
-                        rn[s] = r2;
+                        rn[q.s] = r2;
                         float dx, dy, dz;
-                        moved = moved || dist2_rn<3>(r2, rr, a.box, dx, dy, dz) > a.half_skin2;
+                        if (dist2_rn<3>(r2, q.rr, a.box, dx, dy, dz) > a.half_skin2) moved_any = 1;
                     } else {
-                        a.fs[s] = make_float4(fx, fy, fz, ei);
+                        a.fs[q.s] = make_float4(fx, fy, fz, ei);
                     }
-                    vv[s] = vi;
+                    vv[q.s] = vi;
                 }
             }
         }
     }
-    if (KICK == 2 && __any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) {
-        a.ctl[CTL_REBUILD] = 1u;
-        __threadfence();
-    }
-    t_epilogue(pe_acc, ke_acc, a, KICK == 2 && more);
+    t_epilogue(pe_acc, ke_acc, a, KICK == 2 && more, &moved_any);
 }
 
 // First half of the loop's first step: v += dt/2 F/m; r += dt v (not
@@ -1087,7 +1161,10 @@ static void make_tile_args(const md_space *s, const md_nbr *nb, const TilePlan &
         a.H[k] = tp.H[k];
         a.hscale[k] = (float)((double)tp.H[k] / (double)s->L[k]);
     }
-    a.t = tp.t;
+    a.tx = tp.tx;
+    a.ty = tp.ty;
+    a.tz = tp.tz;
+    a.ntx = tp.ntx;
     a.nty = tp.nty;
     a.ntz = tp.ntz;
     a.ntiles = tp.ntiles;
@@ -1389,10 +1466,11 @@ extern "C" md_status md_tiles_info(const md_space *s, const md_nbr *nb, int32_t 
     out[0] = tp.H[0];
     out[1] = tp.H[1];
     out[2] = tp.H[2];
-    out[3] = tp.t;
-    out[4] = tp.t;
-    out[5] = tp.ntiles;
-    out[6] = tp.reg_cap;
+    out[3] = tp.tx;
+    out[4] = tp.ty;
+    out[5] = tp.tz;
+    out[6] = tp.ntiles;
+    out[7] = tp.reg_cap;
     return MD_OK;
 }
 

@@ -327,10 +327,10 @@ def md_tiles_steps(space, pot, nb, mass, dt, nsteps, PE=None, KE=None, status=No
 
 
 def md_tiles_info(space, nb):
-    """(H (3 half-cells per axis), tile extent y, z, number of tiles, region capacity)."""
-    out = (C.c_int32 * 7)()
+    """Half-cells per axis, tile extent (x, y, z), number of tiles, region capacity."""
+    out = (C.c_int32 * 8)()
     _check(_lib.md_tiles_info(C.byref(space), C.byref(nb), out), "md_tiles_info")
-    return {"H": tuple(out[0:3]), "tile": (1, out[3], out[4]), "ntiles": out[5], "region_cap": out[6]}
+    return {"H": tuple(out[0:3]), "tile": tuple(out[3:6]), "ntiles": out[6], "region_cap": out[7]}
 
 
 def md_set_tile_tpp(tpp: int):

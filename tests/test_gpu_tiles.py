@@ -105,7 +105,7 @@ def test_tiles_rows_forces_lj256k(P):
     c = W.lj_large()
     s, nl, rd, st = _setup(P, c.r, c.L)
     info = P.md_tiles_info(s, nl.plan)
-    assert info["H"] == (48, 48, 48) and info["tile"] == (1, 8, 8) and info["ntiles"] == 1728
+    assert info["H"] == (48, 48, 48) and info["tile"] == (2, 8, 6) and info["ntiles"] == 1152
     f, E = _tile_forces(P, s, nl, rd, P.lj_pot(), st)
     assert P.md_status_poll(st) == 0
     cnt_o, nb_o = O.neighbor_list(c.r, c.L, float(nl.plan.r_list), cap=128, fp32_decision=True)
