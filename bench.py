@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--nve-fusion", type=int, default=1, help="1: kick-drift fused into the force kernel (md_set_nve_fusion)")
     ap.add_argument("--tiles", type=int, default=0,
                     help="1: the tile engine (MD_NBR_TILES) runs the NVE loop; 0: the int32-row engine")
-    ap.add_argument("--tile-tpp", type=int, default=0, help="lanes per particle of the tile step kernel (4 or 8)")
+    ap.add_argument("--tile-tpp", type=int, default=0, help="lanes per particle of the tile step kernel (1, 4 or 8; 0 = by tile size)")
     ap.add_argument("--local-rows", type=int, default=0,
                     help="1: cell-centred forces over 16-bit local rows (MD_NBR_LOCAL_ROWS); 0: int32 rows")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain-SW section")
@@ -1012,7 +1012,7 @@ def main():
             fe.append((e0, e1))
         torch.cuda.synchronize()
         kt = statistics.median(a.elapsed_time(b) for a, b in fe[1:]) * 1e-3 / K
-        kname = f"k_t_step<LJ,{args.tile_tpp or 8},2> (fused step, md_tiles_steps)"
+        kname = ("k_t_step1<LJ,2>" if (args.tile_tpp or 1) == 1 else f"k_t_step<LJ,{args.tile_tpp},2>") + " (fused step, md_tiles_steps)"
         ent = tr.get("k_t_step_lj", {})
     else:
         mean_cnt = float(nl.cnt.float().clamp(max=nl.cap).mean().item())

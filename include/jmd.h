@@ -145,7 +145,8 @@ typedef struct {
  * cutoff are decided by the FP32 formula above, so the pair sets are the
  * same as the int32 rows'.  On return md_integrate_nve writes r, v, f, the
  * int32 rows, counts and build positions back in the caller's order.
- * Needs dim = 3, at least 3 cells on every axis and r_cut > skin; a region
+ * Needs dim = 3, at least 3 cells on every axis, r_cut > skin and cap a
+ * multiple of 8; a region
  * holds at most about 1.25x its mean count plus 128 particles (denser
  * regions raise MD_ERR_NBR_OVERFLOW).  Not combinable with
  * MD_NBR_CANONICAL or MD_NBR_LOCAL_ROWS. */
@@ -445,7 +446,8 @@ JMD_API md_status md_tiles_steps(const md_space *s, const md_pot *p, md_nbr *nb,
  * particles.  out: 8 ints.  MD_ERR_INVALID if the plan cannot use tiles. */
 JMD_API md_status md_tiles_info(const md_space *s, const md_nbr *nb, int32_t *out);
 
-/* Lanes per particle of the tile force kernel: 4 (default) or 8. */
+/* Lanes per particle of the tile force kernel: 1, 4 or 8, or 0 (default)
+ * to choose by tile size (1 for tiles of at least 128 particles, else 4). */
 JMD_API md_status md_set_tile_tpp(int tpp);
 
 /* nsteps of BAOAB Langevin dynamics at constant temperature (Sec. 3.3.1,

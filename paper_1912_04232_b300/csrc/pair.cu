@@ -26,38 +26,39 @@ __device__ __forceinline__ void pair_term(const PairArgs &a, const float4 &ri, c
 {
     float dx, dy, dz;
     float r2 = dist2_rn<DIM>(ri, rj, a.box, dx, dy, dz);
+    // branch-free: the cutoff decision selects the force factor and the
+    // energy (a pair outside adds exactly zero), so divergent warps run no
+    // extra branch per pair
     if (POT == MD_LJ) {
-        if (r2 < a.rc2) {
-            float ir2 = __fdividef(1.0f, r2);
-            float s2 = a.sigma2 * ir2;
-            float s6 = s2 * s2 * s2;
-            float fr = a.c24eps * ir2 * s6 * (2.0f * s6 - 1.0f);
-            fx += fr * dx;
-            fy += fr * dy;
-            fz += fr * dz;
-            e += a.c4eps * s6 * (s6 - 1.0f) - a.e_shift;
-        }
+        const bool in = r2 < a.rc2;
+        const float ir2 = __fdividef(1.0f, in ? r2 : 1.0f);
+        const float s2 = a.sigma2 * ir2;
+        const float s6 = s2 * s2 * s2;
+        const float fr = in ? a.c24eps * ir2 * s6 * (2.0f * s6 - 1.0f) : 0.0f;
+        fx += fr * dx;
+        fy += fr * dy;
+        fz += fr * dz;
+        e += in ? a.c4eps * s6 * (s6 - 1.0f) - a.e_shift : 0.0f;
     } else {  // soft sphere, s_ij = (w_i + w_j)/2
-        float sg = 0.5f * (ri.w + rj.w);
-        if (r2 < sg * sg) {
-            float rr = sqrtf(r2);
-            float isg = __fdividef(1.0f, sg);
-            float x = 1.0f - rr * isg;
-            float xa1, ua;
-            if (a.alpha == 2.0f) {
-                xa1 = x;
-                ua = 0.5f * x * x;
-            } else {
-                xa1 = __powf(x, a.alpha - 1.0f);
-                ua = xa1 * x / a.alpha;
-            }
-            // F_i += (eps/s) x^(alpha-1) d / r
-            float fr = a.eps * isg * xa1 * __fdividef(1.0f, rr);
-            fx += fr * dx;
-            fy += fr * dy;
-            fz += fr * dz;
-            e += a.eps * ua;
+        const float sg = 0.5f * (ri.w + rj.w);
+        const bool in = r2 < sg * sg;
+        const float rr = sqrtf(in ? r2 : 1.0f);
+        const float isg = __fdividef(1.0f, sg);
+        const float x = 1.0f - rr * isg;
+        float xa1, ua;
+        if (a.alpha == 2.0f) {
+            xa1 = x;
+            ua = 0.5f * x * x;
+        } else {
+            xa1 = __powf(in ? x : 1.0f, a.alpha - 1.0f);
+            ua = xa1 * x / a.alpha;
         }
+        // F_i += (eps/s) x^(alpha-1) d / r
+        const float fr = in ? a.eps * isg * xa1 * __fdividef(1.0f, rr) : 0.0f;
+        fx += fr * dx;
+        fy += fr * dy;
+        fz += fr * dz;
+        e += in ? a.eps * ua : 0.0f;
     }
 }
 

@@ -581,98 +581,98 @@ __global__ void __launch_bounds__(TT) k_t_place(TileArgs a)
     t_p(a, vc ^ 1u)[d] = id;
 }
 
-// Row of one own particle (one warp).  Its candidates are the region's
-// half-cells (x 0..4, y yl-2..yl+2, z zl-2..zl+2); for each z-layer the
-// rows of y that can hold a partner form one contiguous local range (a
-// layer or a row farther than r_list from the particle, with a margin above
-// FP32 rounding, is skipped).  The warp sweeps the concatenated ranges 32
-// candidates at a time and compacts the partners with ballots into the row.
-// BND: the window reaches across the box boundary, so the nearest image takes
-// the comparison form (positions are inside [0, L) at a build) and partners
-// across the boundary go to the row's tail.
+// Row of one own particle, one thread per particle.  Its candidates are the
+// region's half-cells of its 5 x 5 x 5 window; for each (y, z) row of the
+// window the run of x that can hold a partner is one contiguous local range
+// (half-cells farther than r_list from the particle, with a margin above
+// FP32 rounding, are skipped: rows entirely, and up to two on each end of a
+// run).  Partners whose nearest image is
+// the plain difference collect eight at a time in registers (a 16-bit shift
+// register of four words) and go out as one 16-byte store; partners across
+// the box boundary go to the row's tail one by one.  BND: some particle of
+// the warp has a window across the boundary, so the nearest image takes the
+// comparison form (positions are inside [0, L) at a build).  Needs
+// cap % 8 == 0.
 template <bool BND>
-__device__ __forceinline__ int build_particle(const TileArgs &a, const TGeo &g, const TileSm &sm,
-                                              const float4 *cand, int k, int loc, int slot)
+__device__ __forceinline__ int build_thread(const TileArgs &a, const TGeo &g, const TileSm &sm, const float4 *cand,
+                                            int k, int loc, int slot, bool valid)
 {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const int yl = 2 + (k / g.nx) % g.ny, zl = 2 + k / (g.nx * g.ny);
-    const float4 ri = cand[loc];
     const float L0 = a.box.L[0], L1 = a.box.L[1], L2 = a.box.L[2];
     const float I0 = a.box.Linv[0], I1 = a.box.Linv[1], I2 = a.box.Linv[2];
-    // pruning geometry: half-cell edges in unwrapped coordinates
-    const float wy = L1 / (float)a.H[1], wz = L2 / (float)a.H[2];
+    const float wx = L0 / (float)a.H[0], wy = L1 / (float)a.H[1], wz = L2 / (float)a.H[2];
     const float lim2 = a.r_list2 * 1.0002f + 1e-4f;
-    // the five z-layers' ranges: first local index and prefix of lengths
-    int b0, b1, b2, b3, b4, p1, p2, p3, p4, p5;
-    {
-        int beg[5], len[5];
-#pragma unroll
-        for (int d = 0; d < 5; ++d) {
-            const int zr = zl - 2 + d;
-            const float zlo = (float)(g.z0 - 2 + zr) * wz, zhi = zlo + wz;
-            const float gz = fmaxf(0.f, fmaxf(zlo - ri.z, ri.z - zhi));
-            const float rz2 = gz * gz;
-            // rows below and above the particle's own, dropped from the far
-            // end while they lie beyond r_list (two rows at most per side)
-            const float g0 = fmaxf(0.f, ri.y - (float)(g.y0 - 3 + yl) * wy);   // top edge of row yl-2
-            const float g1 = fmaxf(0.f, ri.y - (float)(g.y0 - 2 + yl) * wy);   // top edge of row yl-1
-            const float h0 = fmaxf(0.f, (float)(g.y0 + yl) * wy - ri.y);       // bottom edge of row yl+2
-            const float h1 = fmaxf(0.f, (float)(g.y0 - 1 + yl) * wy - ri.y);   // bottom edge of row yl+1
-            const int ya = g0 * g0 + rz2 <= lim2 ? yl - 2 : (g1 * g1 + rz2 <= lim2 ? yl - 1 : yl);
-            const int yb = h0 * h0 + rz2 <= lim2 ? yl + 2 : (h1 * h1 + rz2 <= lim2 ? yl + 1 : yl);
-            beg[d] = sm.hoff[g.RX * (ya + g.RY * zr)];
-            len[d] = rz2 <= lim2 ? sm.hoff[g.RX * (yb + 1 + g.RY * zr)] - beg[d] : 0;
-        }
-        b0 = beg[0]; b1 = beg[1]; b2 = beg[2]; b3 = beg[3]; b4 = beg[4];
-        p1 = len[0]; p2 = p1 + len[1]; p3 = p2 + len[2]; p4 = p3 + len[3]; p5 = p4 + len[4];
-    }
-    int n0 = 0, ns = 0;
+    const float4 ri = valid ? cand[loc] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int xl = 2 + k % g.nx, yl = 2 + (k / g.nx) % g.ny, zl = 2 + k / (g.nx * g.ny);
     uint16_t *row = a.rows + (size_t)slot * a.cap;
-    for (int v0 = 0; v0 < p5; v0 += 32) {
-        const int v = v0 + lane;
-        const bool valid = v < p5;
-        const int j = v < p1 ? b0 + v
-                      : v < p2 ? b1 + (v - p1)
-                      : v < p3 ? b2 + (v - p2)
-                      : v < p4 ? b3 + (v - p3)
-                               : b4 + (v - p4);
-        const float4 cj = valid ? cand[j] : make_float4(-3e38f, -3e38f, -3e38f, 0.f);
-        float dx = __fsub_rn(ri.x, cj.x), dy = __fsub_rn(ri.y, cj.y), dz = __fsub_rn(ri.z, cj.z);
-        bool sh = false;
-        if (BND) {
-            const float ux = __fmul_rn(dx, I0), uy = __fmul_rn(dy, I1), uz = __fmul_rn(dz, I2);
-            const bool sx = ux > 0.5f || ux < -0.5f, sy = uy > 0.5f || uy < -0.5f, sz = uz > 0.5f || uz < -0.5f;
-            if (sx) dx = __fsub_rn(dx, ux > 0.5f ? L0 : -L0);
-            if (sy) dy = __fsub_rn(dy, uy > 0.5f ? L1 : -L1);
-            if (sz) dz = __fsub_rn(dz, uz > 0.5f ? L2 : -L2);
-            sh = sx || sy || sz;
-        }
-        const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-        const bool pass = valid && r2 < a.r_list2 && j != loc;
-        const bool pu = pass && !sh;
-        const unsigned mu = __ballot_sync(0xffffffffu, pu);
-        if (pu) {
-            const int pos = n0 + __popc(mu & lt);
-            if (pos < a.cap) row[pos] = (uint16_t)j;
-        }
-        n0 += __popc(mu);
-        if (BND) {
-            const bool ps = pass && sh;
-            const unsigned ms = __ballot_sync(0xffffffffu, ps);
-            if (ps) {
-                const int kk = ns + __popc(ms & lt);
-                if (kk < a.cap) row[a.cap - 1 - kk] = (uint16_t)j;
+    uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;   // shift register of the last eight entries
+    int nb = 0, n0 = 0, ns = 0;
+    // distance from the particle to region half-cell c along an axis (origin
+    // o, width w): zero inside, else to the nearer face
+    auto gap = [&](float x, int o, int c, float w) {
+        const float lo = (float)(o - 2 + c) * w;
+        return fmaxf(0.f, fmaxf(lo - x, x - (lo + w)));
+    };
+    const float gx0 = gap(ri.x, g.x0, xl - 2, wx), gx1 = gap(ri.x, g.x0, xl - 1, wx);
+    const float gx3 = gap(ri.x, g.x0, xl + 1, wx), gx4 = gap(ri.x, g.x0, xl + 2, wx);
+    for (int zr = zl - 2; zr <= zl + 2; ++zr) {
+        const float gz = gap(ri.z, g.z0, zr, wz);
+        for (int yr = yl - 2; yr <= yl + 2; ++yr) {
+            const float gy = gap(ri.y, g.y0, yr, wy);
+            const float rem = lim2 - gy * gy - gz * gz;
+            // x-run of this row that can hold a partner (the particle's own
+            // column always; one or two more on each side)
+            const int xa = gx0 * gx0 <= rem ? xl - 2 : (gx1 * gx1 <= rem ? xl - 1 : xl);
+            const int xb = gx4 * gx4 <= rem ? xl + 2 : (gx3 * gx3 <= rem ? xl + 1 : xl);
+            const int base = g.RX * (yr + g.RY * zr);
+            const int beg = sm.hoff[base + xa];
+            const int end = (valid && rem >= 0.f) ? sm.hoff[base + xb + 1] : beg;
+            for (int j = beg; j < end; ++j) {
+                const float4 cj = cand[j];
+                float dx = __fsub_rn(ri.x, cj.x), dy = __fsub_rn(ri.y, cj.y), dz = __fsub_rn(ri.z, cj.z);
+                bool sh = false;
+                if (BND) {
+                    const float ux = __fmul_rn(dx, I0), uy = __fmul_rn(dy, I1), uz = __fmul_rn(dz, I2);
+                    const bool sx = ux > 0.5f || ux < -0.5f, sy = uy > 0.5f || uy < -0.5f,
+                               sz = uz > 0.5f || uz < -0.5f;
+                    dx = sx ? __fsub_rn(dx, ux > 0.5f ? L0 : -L0) : dx;
+                    dy = sy ? __fsub_rn(dy, uy > 0.5f ? L1 : -L1) : dy;
+                    dz = sz ? __fsub_rn(dz, uz > 0.5f ? L2 : -L2) : dz;
+                    sh = sx || sy || sz;
+                }
+                const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                const bool pass = r2 < a.r_list2 && j != loc;
+                if (pass && !sh) {
+                    w0 = __funnelshift_r(w0, w1, 16);
+                    w1 = __funnelshift_r(w1, w2, 16);
+                    w2 = __funnelshift_r(w2, w3, 16);
+                    w3 = (w3 >> 16) | ((uint32_t)j << 16);
+                    if (++nb == 8) {
+                        if (n0 + 8 <= a.cap) *reinterpret_cast<uint4 *>(row + n0) = make_uint4(w0, w1, w2, w3);
+                        n0 += 8;
+                        nb = 0;
+                    }
+                }
+                if (BND && pass && sh) {
+                    if (ns < a.cap) row[a.cap - 1 - ns] = (uint16_t)j;
+                    ++ns;
+                }
             }
-            ns += __popc(ms);
         }
     }
-    const int n = n0 + ns;
-    if (lane == 0) {
-        a.cnt[slot] = (uint32_t)min(n0, 0xffff) | ((uint32_t)min(ns, 0xffff) << 16);
-        if (n > a.cap) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+    // the last nb entries sit at the top of the shift register, in order
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int pos = 8 - nb + m;   // register position of the m-th pending entry
+        const int q = pos >> 1;
+        const uint32_t wv = q == 0 ? w0 : (q == 1 ? w1 : (q == 2 ? w2 : w3));
+        if (m < nb && n0 + m < a.cap) row[n0 + m] = (uint16_t)(wv >> ((pos & 1) * 16));
     }
-    return n;
+    n0 += nb;
+    if (valid) {
+        a.cnt[slot] = (uint32_t)min(n0, 0xffff) | ((uint32_t)min(ns, 0xffff) << 16);
+        if (n0 + ns > a.cap) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+    }
+    return valid ? n0 + ns : 0;
 }
 
 __global__ void __launch_bounds__(TT) k_t_build(TileArgs a)
@@ -693,20 +693,27 @@ __global__ void __launch_bounds__(TT) k_t_build(TileArgs a)
     tile_scan(a, g, sm);
     if (!tile_stage_build(a, g, sm, rs, cand, a.tab + (size_t)blockIdx.x * TILE_TAB_WORDS)) return;
     tile_own_map(sm);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nown = sm.own_off[g.nown];
     int wmax = 0;
-    for (int p = warp; p < nown; p += TT / 32) {
-        const int k = sm.kmap[p];
-        const int t = p - sm.own_off[k];
-        const int gx = g.x0 + k % g.nx, gy = g.y0 + (k / g.nx) % g.ny, gz = g.z0 + k / (g.nx * g.ny);
-        const bool bnd = gx < 2 || gx >= a.H[0] - 2 || gy < 2 || gy >= a.H[1] - 2 || gz < 2 || gz >= a.H[2] - 2;
-        const int loc = sm.own_loc[k] + t, slot = sm.own_slot[k] + t;
-        const int n = bnd ? build_particle<true>(a, g, sm, cand, k, loc, slot)
-                          : build_particle<false>(a, g, sm, cand, k, loc, slot);
+    for (int p0 = 0; p0 < nown; p0 += TT) {
+        const int p = p0 + threadIdx.x;
+        const bool valid = p < nown;
+        int k = 0, loc = 0, slot = 0;
+        bool bnd = false;
+        if (valid) {
+            k = sm.kmap[p];
+            const int t = p - sm.own_off[k];
+            loc = sm.own_loc[k] + t;
+            slot = sm.own_slot[k] + t;
+            const int gx = g.x0 + k % g.nx, gy = g.y0 + (k / g.nx) % g.ny, gz = g.z0 + k / (g.nx * g.ny);
+            bnd = gx < 2 || gx >= a.H[0] - 2 || gy < 2 || gy >= a.H[1] - 2 || gz < 2 || gz >= a.H[2] - 2;
+        }
+        const int n = __any_sync(0xffffffffu, bnd) ? build_thread<true>(a, g, sm, cand, k, loc, slot, valid)
+                                                    : build_thread<false>(a, g, sm, cand, k, loc, slot, valid);
         wmax = max(wmax, n);
     }
-    if (lane == 0 && wmax > 0) atomicMax(&bmax, wmax);
+    wmax = __reduce_max_sync(0xffffffffu, wmax);
+    if ((threadIdx.x & 31) == 0 && wmax > 0) atomicMax(&bmax, wmax);
     __syncthreads();
     if (threadIdx.x == 0 && bmax > 0) atomicMax(&a.ctl[CTL_MAXCNT], (uint32_t)bmax);
 }
@@ -725,41 +732,43 @@ __global__ void k_t_finish(TileArgs a)
 // ---------------------------------------------------------------------------
 // forces and the fused step
 // ---------------------------------------------------------------------------
+// One pair's contribution, branch-free: the cutoff decision (r2 < r_c^2, or
+// r2 < sigma_ij^2 for soft spheres) selects the force factor and the
+// energy, so divergent warps run no extra branches.  A masked slot passes
+// r2 = 3e38 and adds exactly zero.
 template <int POT>
 __device__ __forceinline__ void t_term(const TileArgs &a, float dx, float dy, float dz, float r2, float wi, float wj,
                                        float &fx, float &fy, float &fz, float &e)
 {
     if (POT == MD_LJ) {
-        if (r2 < a.rc2) {
-            const float ir2 = __fdividef(1.0f, r2);
-            const float s2 = a.sigma2 * ir2;
-            const float s6 = s2 * s2 * s2;
-            const float fr = a.c24eps * ir2 * s6 * (2.0f * s6 - 1.0f);
-            fx += fr * dx;
-            fy += fr * dy;
-            fz += fr * dz;
-            e += a.c4eps * s6 * (s6 - 1.0f) - a.e_shift;
-        }
+        const bool in = r2 < a.rc2;
+        const float ir2 = __fdividef(1.0f, in ? r2 : 1.0f);
+        const float s2 = a.sigma2 * ir2;
+        const float s6 = s2 * s2 * s2;
+        const float fr = in ? a.c24eps * ir2 * s6 * (2.0f * s6 - 1.0f) : 0.0f;
+        fx += fr * dx;
+        fy += fr * dy;
+        fz += fr * dz;
+        e += in ? a.c4eps * s6 * (s6 - 1.0f) - a.e_shift : 0.0f;
     } else {
         const float sg = 0.5f * (wi + wj);
-        if (r2 < sg * sg) {
-            const float rr = sqrtf(r2);
-            const float isg = __fdividef(1.0f, sg);
-            const float x = 1.0f - rr * isg;
-            float xa1, ua;
-            if (a.alpha == 2.0f) {
-                xa1 = x;
-                ua = 0.5f * x * x;
-            } else {
-                xa1 = __powf(x, a.alpha - 1.0f);
-                ua = xa1 * x / a.alpha;
-            }
-            const float fr = a.eps * isg * xa1 * __fdividef(1.0f, rr);
-            fx += fr * dx;
-            fy += fr * dy;
-            fz += fr * dz;
-            e += a.eps * ua;
+        const bool in = r2 < sg * sg;
+        const float rr = sqrtf(in ? r2 : 1.0f);
+        const float isg = __fdividef(1.0f, sg);
+        const float x = 1.0f - rr * isg;
+        float xa1, ua;
+        if (a.alpha == 2.0f) {
+            xa1 = x;
+            ua = 0.5f * x * x;
+        } else {
+            xa1 = __powf(in ? x : 1.0f, a.alpha - 1.0f);
+            ua = xa1 * x / a.alpha;
         }
+        const float fr = in ? a.eps * isg * xa1 * __fdividef(1.0f, rr) : 0.0f;
+        fx += fr * dx;
+        fy += fr * dy;
+        fz += fr * dz;
+        e += in ? a.eps * ua : 0.0f;
     }
 }
 
@@ -1021,6 +1030,152 @@ __global__ void __launch_bounds__(TT, 4) k_t_step(TileArgs a)
     t_epilogue(pe_acc, ke_acc, a, KICK == 2 && more, &moved_any);
 }
 
+// The same step with one thread per own particle (tiles of a few hundred
+// particles fill a CTA in one pass): each thread streams its row in 16-byte
+// chunks (eight entries, the next chunk fetched while the current one is
+// evaluated) up to the warp's longest row, entries beyond its own count
+// masked to index 0 before they reach shared memory.  Needs cap % 8 == 0.
+__device__ __forceinline__ uint4 ld_nc_v4(const uint16_t *p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+template <int POT>
+__device__ __forceinline__ void t_pair_masked(const TileArgs &a, const float4 &ri, const float4 &rj, bool ok, float &fx,
+                                              float &fy, float &fz, float &e)
+{
+    const float dx = __fsub_rn(ri.x, rj.x), dy = __fsub_rn(ri.y, rj.y), dz = __fsub_rn(ri.z, rj.z);
+    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    t_term<POT>(a, dx, dy, dz, ok ? r2 : 3e38f, ri.w, rj.w, fx, fy, fz, e);
+}
+
+template <int POT>
+__device__ __forceinline__ void t_pair_image_masked(const TileArgs &a, const float4 &ri, const float4 &rj, bool ok,
+                                                    float &fx, float &fy, float &fz, float &e)
+{
+    float dx, dy, dz;
+    const float r2 = dist2_rn<3>(ri, rj, a.box, dx, dy, dz);
+    t_term<POT>(a, dx, dy, dz, ok ? r2 : 3e38f, ri.w, rj.w, fx, fy, fz, e);
+}
+
+template <int POT>
+__device__ __forceinline__ void t_pair_word(const TileArgs &a, const float4 *cand, const float4 &ri, uint32_t w,
+                                            int e, int n0, float &fx, float &fy, float &fz, float &e_acc)
+{
+    // entries e and e + 1 of the row, packed in w; slots beyond the count
+    // read the region's first position and add zero
+    const bool ok0 = e < n0, ok1 = e + 1 < n0;
+    const int j0 = ok0 ? (int)(w & 0xffffu) : 0, j1 = ok1 ? (int)(w >> 16) : 0;
+    t_pair_masked<POT>(a, ri, cand[j0], ok0, fx, fy, fz, e_acc);
+    t_pair_masked<POT>(a, ri, cand[j1], ok1, fx, fy, fz, e_acc);
+}
+
+template <int POT, int KICK>
+__global__ void __launch_bounds__(TT, 4) k_t_step1(TileArgs a)
+{
+    count_launch();
+    extern __shared__ __align__(16) float4 cand[];
+    __shared__ TileSm sm;
+    __shared__ int moved_any;
+    const uint32_t sel = t_sel(a);
+    const uint32_t rcb = sel & 1u;
+    const float4 *rc = t_r(a, rcb);
+    float4 *rn = t_r(a, rcb ^ 1u);
+    float4 *vv = t_v(a, (sel >> 1) & 1u);
+    bool more = false;
+    if (KICK == 2) {
+        const uint32_t step = *(volatile uint32_t *)&a.ctl[CTL_STEP];
+        more = step + 1u < *(volatile uint32_t *)&a.ctl[CTL_NSTEPS];
+    }
+    if (threadIdx.x == 0) {
+        sm.kmap = reinterpret_cast<unsigned char *>(cand + a.reg_cap);
+        moved_any = 0;
+    }
+    float pe_acc = 0.f, ke_acc = 0.f;
+    if (tile_issue_tab(a, sm, rc, cand, a.tab + (size_t)blockIdx.x * TILE_TAB_WORDS)) {
+        // the first pass's global operands are fetched while the region's
+        // bulk copies are in flight; positions are read after the wait
+        tile_own_map(sm);
+        const int nown = sm.own_off[sm.nown];
+        bool staged = false;
+        for (int p0 = 0; p0 < nown; p0 += TT) {
+            const int p = p0 + threadIdx.x;
+            const bool valid = p < nown;
+            int s = 0, n0 = 0, ns = 0, li = 0;
+            float4 ri = make_float4(0.f, 0.f, 0.f, 0.f), vi = ri, rr = ri;
+            if (valid) {
+                const int k = sm.kmap[p];
+                const int t = p - sm.own_off[k];
+                s = sm.own_slot[k] + t;
+                li = sm.own_loc[k] + t;
+                const uint32_t c = __ldg(a.cnt + s);
+                if (KICK == 2) {
+                    vi = vv[s];
+                    if (more) rr = __ldg(a.rref + s);
+                }
+                n0 = min((int)(c & 0xffffu), a.cap);
+                ns = min((int)(c >> 16), a.cap - n0);
+            }
+            const uint16_t *row = a.rows + (size_t)s * a.cap;
+            float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+            const int nmax = __reduce_max_sync(0xffffffffu, n0);
+            uint4 nxt = n0 > 0 ? ld_nc_v4(row) : make_uint4(0u, 0u, 0u, 0u);
+            if (p0 == 0) staged = tile_wait(a, sm);   // uniform
+            if (!staged) break;
+            if (valid) ri = cand[li];
+            // partners whose nearest image is the plain difference
+            for (int k0 = 0; k0 < nmax; k0 += 8) {
+                const uint4 cur = nxt;
+                nxt = k0 + 8 < n0 ? ld_nc_v4(row + k0 + 8) : make_uint4(0u, 0u, 0u, 0u);
+                t_pair_word<POT>(a, cand, ri, cur.x, k0, n0, fx, fy, fz, e);
+                t_pair_word<POT>(a, cand, ri, cur.y, k0 + 2, n0, fx, fy, fz, e);
+                t_pair_word<POT>(a, cand, ri, cur.z, k0 + 4, n0, fx, fy, fz, e);
+                t_pair_word<POT>(a, cand, ri, cur.w, k0 + 6, n0, fx, fy, fz, e);
+            }
+            // partners across the box boundary (row tail, from the end)
+            const int nsmax = __reduce_max_sync(0xffffffffu, ns);
+            for (int kk = 0; kk < nsmax; ++kk) {
+                const bool ok = kk < ns;
+                const int j = ok ? ld_stream_u16(row + a.cap - 1 - kk) : 0;
+                t_pair_image_masked<POT>(a, ri, cand[j], ok, fx, fy, fz, e);
+            }
+            if (valid) {
+                const float ei = 0.5f * e;
+                pe_acc += ei;
+                if (KICK == 0) {
+                    a.fs[s] = make_float4(fx, fy, fz, ei);
+                } else {
+                    vi.x += a.hdm * fx;
+                    vi.y += a.hdm * fy;
+                    vi.z += a.hdm * fz;
+                    ke_acc += 0.5f * a.mass * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
+                    if (more) {
+                        vi.x += a.hdm * fx;
+                        vi.y += a.hdm * fy;
+                        vi.z += a.hdm * fz;
+                        float4 r2 = ri;
+                        r2.x = ri.x + a.dt * vi.x;
+                        r2.y = ri.y + a.dt * vi.y;
+                        r2.z = ri.z + a.dt * vi.z;
+                        rn[s] = r2;
+                        float dx, dy, dz;
+                        if (dist2_rn<3>(r2, rr, a.box, dx, dy, dz) > a.half_skin2) moved_any = 1;
+                    } else {
+                        a.fs[s] = make_float4(fx, fy, fz, ei);
+                    }
+                    vv[s] = vi;
+                }
+            }
+        }
+        if (nown == 0) tile_wait(a, sm);   // no pass waited for the copies
+    }
+    t_epilogue(pe_acc, ke_acc, a, KICK == 2 && more, &moved_any);
+}
+
 // First half of the loop's first step: v += dt/2 F/m; r += dt v (not
 // wrapped), in place; displacement check; the last block hands the rebuild
 // decision to the graph's IF node.
@@ -1136,11 +1291,11 @@ __global__ void __launch_bounds__(TT) k_t_rows(TileArgs a)
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-static int g_tile_tpp = 4;
+static int g_tile_tpp = 0;   // 0: by tile size (1 for tiles of >= 128 particles, else 4)
 
 static bool tile_plan(const md_space *s, const md_nbr *nb, TilePlan &tp)
 {
-    if (!nb || (s && s->dim != 3) || nb->dim != 3 || nb->N < 1 || (nb->cap & 1) || nb->cap > 0xffff) return false;
+    if (!nb || (s && s->dim != 3) || nb->dim != 3 || nb->N < 1 || (nb->cap & 7) || nb->cap > 0xffff) return false;
     if (!(nb->r_cut > nb->skin)) return false;
     return tile_geometry(nb->N, nb->ncell, tp);
 }
@@ -1247,6 +1402,10 @@ static void ensure_tile_attrs()
     tile_smem_attr(k_t_step<MD_SOFT_SPHERE, 8, 0>);
     tile_smem_attr(k_t_step<MD_SOFT_SPHERE, 4, 2>);
     tile_smem_attr(k_t_step<MD_SOFT_SPHERE, 8, 2>);
+    tile_smem_attr(k_t_step1<MD_LJ, 0>);
+    tile_smem_attr(k_t_step1<MD_LJ, 2>);
+    tile_smem_attr(k_t_step1<MD_SOFT_SPHERE, 0>);
+    tile_smem_attr(k_t_step1<MD_SOFT_SPHERE, 2>);
     done |= 1ull << dev;
 }
 
@@ -1273,14 +1432,31 @@ static void launch_step_t(const TileArgs &a, cudaStream_t st)
     k_t_step<POT, TPP, KICK><<<a.ntiles, TT, tile_smem(a), st>>>(a);
 }
 
+// Lanes per particle of the step kernel for this plan.
+static int tile_tpp(const TileArgs &a)
+{
+    if (g_tile_tpp) return g_tile_tpp;
+    const double own = (double)a.N * a.tx * a.ty * a.tz / ((double)a.H[0] * a.H[1] * a.H[2]);
+    return own >= 128.0 ? 1 : 4;
+}
+
+template <int POT, int KICK>
+static void launch_step1(const TileArgs &a, cudaStream_t st)
+{
+    k_t_step1<POT, KICK><<<a.ntiles, TT, tile_smem(a), st>>>(a);
+}
+
 template <int KICK>
 static void launch_step(const TileArgs &a, cudaStream_t st)
 {
+    const int tpp = tile_tpp(a);
     if (a.pot == MD_LJ) {
-        if (g_tile_tpp == 4) launch_step_t<MD_LJ, 4, KICK>(a, st);
+        if (tpp == 1) launch_step1<MD_LJ, KICK>(a, st);
+        else if (tpp == 4) launch_step_t<MD_LJ, 4, KICK>(a, st);
         else launch_step_t<MD_LJ, 8, KICK>(a, st);
     } else {
-        if (g_tile_tpp == 4) launch_step_t<MD_SOFT_SPHERE, 4, KICK>(a, st);
+        if (tpp == 1) launch_step1<MD_SOFT_SPHERE, KICK>(a, st);
+        else if (tpp == 4) launch_step_t<MD_SOFT_SPHERE, 4, KICK>(a, st);
         else launch_step_t<MD_SOFT_SPHERE, 8, KICK>(a, st);
     }
 }
@@ -1397,7 +1573,7 @@ md_status run_tiled_nve(const md_space *s, const md_pot *p, float *d_r, float *d
     a.E_out = d_PE;
     a.KE_out = d_KE;
     a.series = 1;
-    a.variant = g_tile_tpp;
+    a.variant = tile_tpp(a);
     if (nsteps == 0) return MD_OK;
     const uint32_t *ctl = a.ctl;
     if (use_graph) {
@@ -1454,7 +1630,7 @@ using namespace jmd;
 
 extern "C" md_status md_set_tile_tpp(int tpp)
 {
-    if (tpp != 4 && tpp != 8) return MD_ERR_INVALID;
+    if (tpp != 0 && tpp != 1 && tpp != 4 && tpp != 8) return MD_ERR_INVALID;
     g_tile_tpp = tpp;
     return MD_OK;
 }

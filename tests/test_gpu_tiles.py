@@ -24,7 +24,7 @@ def _setup(P, r, L, r_cut=2.5, skin=0.3, cap=128):
     return s, nl, to_dev(r, torch.float32), status_word()
 
 
-def _tile_forces(P, s, nl, rd, pot, st, tpp=4):
+def _tile_forces(P, s, nl, rd, pot, st, tpp=0):
     """Import, one force evaluation on the tiles, export forces and rows."""
     import torch
     N = rd.shape[0]
@@ -37,7 +37,7 @@ def _tile_forces(P, s, nl, rd, pot, st, tpp=4):
         P.md_tiles_export(s, nl.plan, None, None, f, rows=True)
         torch.cuda.synchronize()
     finally:
-        P.md_set_tile_tpp(4)   # the library default
+        P.md_set_tile_tpp(0)   # the library default: chosen by tile size
     return f.cpu().numpy(), E.item()
 
 
@@ -47,7 +47,7 @@ def _liquid(n_side=10, jitter=0.3, seed=3):
     return W.lj_fluid("fcc", n_side, jitter=jitter, seed=seed)
 
 
-@pytest.mark.parametrize("tpp", [4, 8])
+@pytest.mark.parametrize("tpp", [1, 4, 8])
 @pytest.mark.parametrize("case", ["lj4096", "liquid4000"])
 def test_tiles_rows_forces_energies(P, case, tpp):
     c = W.lj_small() if case == "lj4096" else _liquid()
@@ -101,12 +101,13 @@ def test_tiles_soft_spheres_3d(P):
     assert abs(E - U) <= 1e-5 * abs(U)
 
 
-def test_tiles_rows_forces_lj256k(P):
+@pytest.mark.parametrize("tpp", [0, 4])
+def test_tiles_rows_forces_lj256k(P, tpp):
     c = W.lj_large()
     s, nl, rd, st = _setup(P, c.r, c.L)
     info = P.md_tiles_info(s, nl.plan)
     assert info["H"] == (48, 48, 48) and info["tile"] == (2, 8, 6) and info["ntiles"] == 1152
-    f, E = _tile_forces(P, s, nl, rd, P.lj_pot(), st)
+    f, E = _tile_forces(P, s, nl, rd, P.lj_pot(), st, tpp)
     assert P.md_status_poll(st) == 0
     cnt_o, nb_o = O.neighbor_list(c.r, c.L, float(nl.plan.r_list), cap=128, fp32_decision=True)
     rows_equal(nl.cnt.cpu().numpy(), nl.nbr.cpu().numpy(), cnt_o, nb_o)
