@@ -132,14 +132,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+ORACLE_SERIES = {}
+
+
 def oracle_sample(name, md_steps, seed=0):
     """Time the FP64 oracle on `md_steps` NVE steps of the workload (all host
-    threads).  Returns (particle-steps/s, threads, seconds)."""
+    threads).  Returns (particle-steps/s, threads, seconds); the energy
+    series is kept for the drift comparison."""
     import oracle as O
     c = workload(name, seed)
     t0 = time.perf_counter()
-    O.nve(c.r, c.v, c.L, "lj", dt=c.dt, nsteps=md_steps)
+    _, _, PEo, KEo = O.nve(c.r, c.v, c.L, "lj", dt=c.dt, nsteps=md_steps)
     dt = time.perf_counter() - t0
+    ORACLE_SERIES[(name, seed, md_steps)] = PEo + KEo
     return c.N * md_steps / dt, O.num_threads(), dt
 
 
@@ -426,7 +431,6 @@ def packing_section(nseed=20):
     for D in [0.6 + 0.05 * k for k in range(9)] + [1.25]:
         L64 = W.packing_box(N, D, phi)
         s = P.md_space_periodic(2, [W.f32(L64)] * 2)
-        Lp = (N // 2) * math.pi * D / (4 * phi * L64)
         nl = P.NeighborList(s, N, max(D, 1.0), 0.3, 64, canonical=True)
         Es, gs = [], []
         for seed in range(nseed):
@@ -434,7 +438,7 @@ def packing_section(nseed=20):
             s0[:, :2] = torch.from_numpy(pk.s0.astype(np.float32)).to(dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            P.md_minimize_fire_adjoint(s, P.soft_pot(), P.fire_params(), nl.plan, s0, N // 2, D, 1.0, Lp, T, K,
+            P.md_minimize_fire_adjoint(s, P.soft_pot(), P.fire_params(), nl.plan, s0, N // 2, D, 1.0, phi, T, K,
                                        ra, va, fa, wsv, o, st)
             e1.record()
             e1.synchronize()
@@ -477,7 +481,6 @@ def packing_section(nseed=20):
         e1.synchronize()
         if k:
             tg.append(e0.elapsed_time(e1))
-    Lp = (N2 // 2) * math.pi * D2 / (4 * phi * L64)
     nlc = P.NeighborList(s, N2, D2, 0.3, 64, canonical=True)
     s0 = torch.zeros((N2, 4), dtype=torch.float32, device=dev)
     s0[:, :2] = torch.from_numpy(pk.s0.astype(np.float32)).to(dev)
@@ -487,7 +490,7 @@ def packing_section(nseed=20):
     for k in range(3):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        P.md_minimize_adjoint(s, P.soft_pot(), nlc.plan, s0, N2 // 2, D2, 1.0, Lp, 0.05, T2, K2, r, f, ws, o, st)
+        P.md_minimize_adjoint(s, P.soft_pot(), nlc.plan, s0, N2 // 2, D2, 1.0, phi, 0.05, T2, K2, r, f, ws, o, st)
         e1.record()
         e1.synchronize()
         if k:
@@ -555,7 +558,6 @@ def fire_section():
                             "E_start": float(E2[0]), "E_end": float(E2[-1])}
     # dE_final/dD through the 300 FIRE steps (reverse mode, K = 18)
     L64 = W.packing_box(pk.N, pk.D, pk.phi)
-    Lp = (pk.N // 2) * math.pi * pk.D / (4 * pk.phi * L64)
     nlc = P.NeighborList(s2, pk.N, 1.4, 0.3, 64, canonical=True)
     s0 = torch.zeros((pk.N, 4), dtype=torch.float32, device=dev)
     s0[:, :2] = torch.from_numpy(pk.s0.astype(np.float32)).to(dev)
@@ -568,7 +570,7 @@ def fire_section():
     for k in range(3):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        P.md_minimize_fire_adjoint(s2, P.soft_pot(), P.fire_params(), nlc.plan, s0, pk.N // 2, pk.D, 1.0, Lp, 300,
+        P.md_minimize_fire_adjoint(s2, P.soft_pot(), P.fire_params(), nlc.plan, s0, pk.N // 2, pk.D, 1.0, pk.phi, 300,
                                    18, ra, va, fa, wsv, outd, st)
         e1.record()
         e1.synchronize()
@@ -943,6 +945,15 @@ def main():
         raise SystemExit(f"device status {code} in the timed region")
     E = (PE + KE).cpu().numpy()
     drift = float(np.abs(E - E[0]).max() / c.N)
+    # the GPU run's energies against the FP64 oracle over the oracle's sample
+    # (the CPU-baseline steps, same start), per particle
+    drift_vs_oracle = None
+    Eo = ORACLE_SERIES.get((args.workload, 0, 20 if args.workload == "lj256k" else 200))
+    if Eo is not None and rank == 0:
+        m = min(len(Eo) - 1, len(E))
+        drift_vs_oracle = {"steps": m, "max_abs_dE_per_particle": float(np.abs(E[:m] - Eo[1:m + 1]).max() / c.N),
+                           "drift_gpu": float(np.abs(E[:m] - E[0]).max() / c.N),
+                           "drift_oracle": float(np.abs(Eo[1:m + 1] - Eo[1]).max() / c.N)}
 
     t_max = max_over_ranks(ms, dist, dev)
     total_ps = c.N * md_steps * args.steps * world
@@ -1068,7 +1079,8 @@ def main():
             "config": {"workload": f"lj_fcc40_N{c.N}" if c.N == 256000 else f"lj_sc16_N{c.N}", "N": c.N,
                        "md_steps_per_step": md_steps, "density": 0.84, "T": 1.0, "r_cut": c.r_cut, "skin": c.skin,
                        "dt": c.dt, "neighbor_cap": nl.cap, "rebuilds_per_step": builds / args.steps,
-                       "max_energy_drift_per_particle": drift, "l2": "flushed between bench steps",
+                       "max_energy_drift_per_particle": drift, "energy_vs_oracle": drift_vs_oracle,
+                       "l2": "flushed between bench steps",
                        "parallelism": f"replicas{world}", "pair_tpp": args.tpp or 4,
                        "neighbor_rows": ("16-bit tile-local" if tiles else
                                          "int32 + 16-bit local" if args.local_rows else "int32"),

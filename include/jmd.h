@@ -608,8 +608,15 @@ JMD_API md_status md_adam_step(float *d_params, const float *d_grad, float *d_m,
 /* Differentiating through minimisation (Sec. 4.2, App. A): the final energy */
 /* of T gradient-descent steps of a 2-D bidisperse soft-disk packing and its */
 /* derivative with respect to the diameter D of the first nA disks (the rest */
-/* have diameter dB).  The box (s) is L(D); Lp = dL/dD.                      */
+/* have diameter dB).  The box is L(D) at packing fraction phi.              */
 /* ------------------------------------------------------------------------ */
+/* The packing's space: a square of edge
+ *   L(D) = sqrt((nA pi D^2 / 4 + (N - nA) pi dB^2 / 4) / phi)
+ * (FP64; out->L holds it rounded to FP32) and, if dLdD is not NULL,
+ * dL/dD = pi nA D / (4 phi L).  MD_ERR_INVALID for N < 1, nA outside
+ * [0, N] or non-positive D, dB, phi. */
+JMD_API md_status md_packing_space(int N, int nA, double D, double dB, double phi, md_space *out, double *dLdD);
+
 /* Workspace bytes for N particles, T steps, checkpoints every K steps:
  * (ceil(T/K) + K + 2) * N * 16. */
 JMD_API size_t md_adjoint_workspace_size(int N, int T, int K);
@@ -619,10 +626,13 @@ JMD_API size_t md_adjoint_workspace_size(int N, int T, int K);
  * mode with recomputation from checkpoints every K steps (K = ceil(sqrt T)
  * is the natural choice).  nb must be planned for this space with
  * r_cut >= max(D, dB), bound, and in MD_NBR_CANONICAL mode; the result is
- * then identical for every K.  d_r [N][4] receives r_T (w = diameter), d_f
- * the forces at r_T; d_out[0] = E (FP64), d_out[1] = dE/dD (FP64). */
+ * then identical for every K.  s must be the packing's space
+ * (md_packing_space(N, nA, D, dB, phi)); the library forms L(D) and dL/dD
+ * itself, MD_ERR_INVALID if s is another box.  d_r [N][4] receives r_T
+ * (w = diameter), d_f the forces at r_T; d_out[0] = E (FP64),
+ * d_out[1] = dE/dD (FP64). */
 JMD_API md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_nbr *nb, const float *d_s0, int nA,
-                                      float D, float dB, float Lp, float eta, int T, int K, float *d_r, float *d_f,
+                                      float D, float dB, double phi, float eta, int T, int K, float *d_r, float *d_f,
                                       void *d_ws, double *d_out, uint32_t *d_status, md_stream_t stream);
 
 /* FIRE instead of gradient descent (Sec. 3.3.1 minimiser; Bitzek et al.,
@@ -633,13 +643,13 @@ JMD_API md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_nbr
  * steps, mixing factors and P > 0 decisions of the trajectory held fixed
  * (the map is piecewise smooth).  States (r, v and the FIRE scalars) are
  * kept every K steps and each segment is replayed bit for bit in the
- * reverse sweep; nb as for md_minimize_adjoint (canonical), so the result
- * is identical for every K.  d_ws: md_fire_adjoint_workspace_size(N, T, K)
+ * reverse sweep; nb and s as for md_minimize_adjoint (canonical list, the
+ * packing's space at phi), so the result is identical for every K.  d_ws: md_fire_adjoint_workspace_size(N, T, K)
  * bytes, 256-byte aligned.  d_r, d_v, d_f receive r_T, v_T, F(r_T);
  * d_out[0] = E, d_out[1] = dE/dD (FP64). */
 JMD_API size_t md_fire_adjoint_workspace_size(int N, int T, int K);
 JMD_API md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p, const md_fire_params *fp,
-                                           md_nbr *nb, const float *d_s0, int nA, float D, float dB, float Lp,
+                                           md_nbr *nb, const float *d_s0, int nA, float D, float dB, double phi,
                                            int T, int K, float *d_r, float *d_v, float *d_f, void *d_ws,
                                            double *d_out, uint32_t *d_status, md_stream_t stream);
 

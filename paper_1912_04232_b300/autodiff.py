@@ -18,17 +18,6 @@ import math
 from . import jmd as J
 
 
-def packing_box(N: int, D: float, phi: float) -> float:
-    """Square box edge (FP64) holding N/2 disks of diameter D and N/2 of
-    diameter 1 at packing fraction phi."""
-    return math.sqrt((N // 2) * math.pi * (D * D + 1.0) / 4.0 / phi)
-
-
-def _f32(x: float) -> float:
-    import numpy as np
-    return float(np.float32(x))
-
-
 class _Plans:
     """Lists, workspaces and buffers per (N, D, T, K, minimiser, device),
     kept so that repeated calls reuse the adjoint's captured graph."""
@@ -41,9 +30,8 @@ class _Plans:
         key = (N, float(D), float(phi), T, K, fire, str(device))
         if key in self.cache:
             return self.cache[key]
-        L64 = packing_box(N, D, phi)
-        L = _f32(L64)
-        space = J.md_space_periodic(2, [L, L])
+        # the box L(D) at packing fraction phi comes from the library
+        space, _ = J.md_packing_space(N, N // 2, D, 1.0, phi)
         nl = J.NeighborList(space, N, max(D, 1.0), 0.3, 64, device=device, canonical=True)
         nbytes = (J.md_fire_adjoint_workspace_size if fire else J.md_adjoint_workspace_size)(N, T, K)
         raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
@@ -52,8 +40,7 @@ class _Plans:
         s0 = torch.zeros((N, 4), dtype=torch.float32, device=device)
         out = torch.zeros(2, dtype=torch.float64, device=device)
         st = torch.zeros(1, dtype=torch.int32, device=device)
-        Lp = (N // 2) * math.pi * D / (4.0 * phi * L64)    # dL/dD
-        entry = dict(space=space, nl=nl, raw=raw, ws=ws, bufs=bufs, s0=s0, out=out, st=st, Lp=Lp, L=L)
+        entry = dict(space=space, nl=nl, raw=raw, ws=ws, bufs=bufs, s0=s0, out=out, st=st, phi=phi)
         if len(self.cache) >= 64:
             self.cache.pop(next(iter(self.cache)))
         self.cache[key] = entry
@@ -82,9 +69,9 @@ class MinimizedPackingEnergy(_import_torch().autograd.Function):
         r, v, f = P["bufs"]
         if fire:
             J.md_minimize_fire_adjoint(P["space"], J.soft_pot(), J.fire_params(), P["nl"].plan, P["s0"], N // 2, d,
-                                       1.0, P["Lp"], T, K, r, v, f, P["ws"], P["out"], P["st"])
+                                       1.0, P["phi"], T, K, r, v, f, P["ws"], P["out"], P["st"])
         else:
-            J.md_minimize_adjoint(P["space"], J.soft_pot(), P["nl"].plan, P["s0"], N // 2, d, 1.0, P["Lp"], eta, T, K,
+            J.md_minimize_adjoint(P["space"], J.soft_pot(), P["nl"].plan, P["s0"], N // 2, d, 1.0, P["phi"], eta, T, K,
                                   r, f, P["ws"], P["out"], P["st"])
         code = J.md_status_poll(P["st"])
         if code != 0:

@@ -675,15 +675,43 @@ static md_status with_loop_builder(md_nbr *nb, cudaStream_t cs, const std::funct
     return r;
 }
 
+// Box of the bidisperse packing (App. A): nA disks of diameter D and N - nA
+// of diameter dB in a square of packing fraction phi,
+//   L(D) = sqrt((nA pi D^2 / 4 + (N - nA) pi dB^2 / 4) / phi),
+//   dL/dD = pi nA D / (4 phi L).
+static bool packing_box(int N, int nA, double D, double dB, double phi, double *L, double *Lp)
+{
+    if (N < 1 || nA < 0 || nA > N || !(D > 0.0) || !(dB > 0.0) || !(phi > 0.0)) return false;
+    const double pi = 3.14159265358979323846;
+    const double area = (nA * pi * D * D + (N - nA) * pi * dB * dB) / 4.0;
+    *L = sqrt(area / phi);
+    *Lp = pi * nA * D / (4.0 * phi * *L);
+    return true;
+}
+
+// The packing's box must be the space the caller planned its list in: its
+// edges equal L(D) (to the FP32 rounding of the box and of D).
+static bool packing_space_ok(const md_space *s, int N, int nA, float D, float dB, double phi, float *Lp)
+{
+    double L = 0.0, lp = 0.0;
+    if (!s || s->dim != 2 || !packing_box(N, nA, (double)D, (double)dB, phi, &L, &lp)) return false;
+    if (fabs(s->L64[0] - L) > 1e-6 * L || fabs(s->L64[1] - L) > 1e-6 * L) return false;
+    *Lp = (float)lp;
+    return true;
+}
+
 // The adjoints' launch sequences are fixed by their arguments (step count,
 // checkpoint schedule), so each call runs as one captured graph, cached per
 // argument set (md_set_loop_graphs(0): host launches).  Same kernels, same
 // order, same bits.
 extern "C" md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_nbr *nb, const float *d_s0, int nA,
-                                         float D, float dB, float Lp, float eta, int T, int K, float *d_r, float *d_f,
-                                         void *d_ws, double *d_out, uint32_t *d_status, md_stream_t stream)
+                                         float D, float dB, double phi, float eta, int T, int K, float *d_r,
+                                         float *d_f, void *d_ws, double *d_out, uint32_t *d_status,
+                                         md_stream_t stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
+    float Lp = 0.0f;
+    if (!nb || !packing_space_ok(s, nb->N, nA, D, dB, phi, &Lp)) return MD_ERR_INVALID;
     if (!s || !p || !nb || !g_loop_graphs)
         return gd_adjoint_body(s, p, nb, d_s0, nA, D, dB, Lp, eta, T, K, d_r, d_f, d_ws, d_out, d_status, st,
                                nullptr);
@@ -721,11 +749,13 @@ extern "C" md_status md_minimize_adjoint(const md_space *s, const md_pot *p, md_
 }
 
 extern "C" md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p, const md_fire_params *fp,
-                                              md_nbr *nb, const float *d_s0, int nA, float D, float dB, float Lp,
+                                              md_nbr *nb, const float *d_s0, int nA, float D, float dB, double phi,
                                               int T, int K, float *d_r, float *d_v, float *d_f, void *d_ws,
                                               double *d_out, uint32_t *d_status, md_stream_t stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
+    float Lp = 0.0f;
+    if (!nb || !packing_space_ok(s, nb->N, nA, D, dB, phi, &Lp)) return MD_ERR_INVALID;
     if (!s || !p || !fp || !nb || !g_loop_graphs)
         return fire_adjoint_body(s, p, fp, nb, d_s0, nA, D, dB, Lp, T, K, d_r, d_v, d_f, d_ws, d_out, d_status, st,
                                  nullptr);
@@ -763,4 +793,15 @@ extern "C" md_status md_minimize_fire_adjoint(const md_space *s, const md_pot *p
                                      lb);
         });
     }, st);
+}
+
+extern "C" md_status md_packing_space(int N, int nA, double D, double dB, double phi, md_space *out, double *dLdD)
+{
+    double L = 0.0, lp = 0.0;
+    if (!out || !packing_box(N, nA, D, dB, phi, &L, &lp)) return MD_ERR_INVALID;
+    const double box[2] = {L, L};
+    const md_status e = md_space_periodic(2, box, out);
+    if (e != MD_OK) return e;
+    if (dLdD) *dLdD = lp;
+    return MD_OK;
 }

@@ -164,10 +164,11 @@ _SIGS = {
     "md_batch_run_nve": [_P(md_batch), _vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp, _vp],
     "md_batch_stats": [_P(md_batch), _P(C.c_uint32), _vp],
     "md_batch_autotune": [_P(md_batch), _vp, _vp, _vp, _vp, C.c_int, C.c_char_p, _P(C.c_int), _vp],
-    "md_minimize_adjoint": [_P(md_space), _P(md_pot), _P(md_nbr), _vp, C.c_int, C.c_float, C.c_float, C.c_float,
+    "md_packing_space": [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _P(md_space), _P(C.c_double)],
+    "md_minimize_adjoint": [_P(md_space), _P(md_pot), _P(md_nbr), _vp, C.c_int, C.c_float, C.c_float, C.c_double,
                             C.c_float, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
     "md_minimize_fire_adjoint": [_P(md_space), _P(md_pot), _P(md_fire_params), _P(md_nbr), _vp, C.c_int, C.c_float,
-                                 C.c_float, C.c_float, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+                                 C.c_float, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "md_tiles_import": [_P(md_space), _vp, _vp, _vp, _P(md_nbr), _vp, _vp],
     "md_tiles_forces": [_P(md_space), _P(md_pot), _P(md_nbr), _vp, _vp, _vp],
     "md_tiles_export": [_P(md_space), _P(md_nbr), _vp, _vp, _vp, C.c_int, _vp],
@@ -610,9 +611,18 @@ def md_adjoint_workspace_size(N, T, K) -> int:
     return int(_lib.md_adjoint_workspace_size(int(N), int(T), int(K)))
 
 
-def md_minimize_adjoint(space, pot, nb, s0, nA, D, dB, Lp, eta, T, K, r, f, ws, out, status=None, stream=None):
+def md_packing_space(N, nA, D, dB, phi):
+    """(space, dL/dD) of the bidisperse disk packing at packing fraction phi."""
+    out = md_space()
+    lp = C.c_double()
+    _check(_lib.md_packing_space(int(N), int(nA), float(D), float(dB), float(phi), C.byref(out), C.byref(lp)),
+           "md_packing_space")
+    return out, lp.value
+
+
+def md_minimize_adjoint(space, pot, nb, s0, nA, D, dB, phi, eta, T, K, r, f, ws, out, status=None, stream=None):
     _check(_lib.md_minimize_adjoint(C.byref(space), C.byref(pot), C.byref(nb), _ptr(s0), int(nA), float(D),
-                                    float(dB), float(Lp), float(eta), int(T), int(K), _ptr(r), _ptr(f), _ptr(ws),
+                                    float(dB), float(phi), float(eta), int(T), int(K), _ptr(r), _ptr(f), _ptr(ws),
                                     _ptr(out), _ptr(status), _stream(stream)), "md_minimize_adjoint")
 
 
@@ -620,10 +630,10 @@ def md_fire_adjoint_workspace_size(N, T, K) -> int:
     return int(_lib.md_fire_adjoint_workspace_size(int(N), int(T), int(K)))
 
 
-def md_minimize_fire_adjoint(space, pot, fire, nb, s0, nA, D, dB, Lp, T, K, r, v, f, ws, out, status=None,
+def md_minimize_fire_adjoint(space, pot, fire, nb, s0, nA, D, dB, phi, T, K, r, v, f, ws, out, status=None,
                              stream=None):
     _check(_lib.md_minimize_fire_adjoint(C.byref(space), C.byref(pot), C.byref(fire), C.byref(nb), _ptr(s0), int(nA),
-                                         float(D), float(dB), float(Lp), int(T), int(K), _ptr(r), _ptr(v), _ptr(f),
+                                         float(D), float(dB), float(phi), int(T), int(K), _ptr(r), _ptr(v), _ptr(f),
                                          _ptr(ws), _ptr(out), _ptr(status), _stream(stream)),
            "md_minimize_fire_adjoint")
 

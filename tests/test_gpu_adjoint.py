@@ -107,7 +107,6 @@ def _adjoint(P, p, D, T, K, phi=0.9, eta=0.05):
     N = p.N
     L64 = O.packing_box(N, D, phi)
     L = W.f32(L64)
-    Lp = (N // 2) * math.pi * D / (4 * phi * L64)
     s = P.md_space_periodic(2, [L, L])
     nl = P.NeighborList(s, N, max(D, 1.0), SKIN, 64, canonical=True)
     s0 = np.zeros((N, 4), np.float32)
@@ -118,7 +117,7 @@ def _adjoint(P, p, D, T, K, phi=0.9, eta=0.05):
     ws = torch.empty(P.md_adjoint_workspace_size(N, T, K), dtype=torch.uint8, device=dev())
     out = torch.zeros(2, dtype=torch.float64, device=dev())
     st = status_word()
-    P.md_minimize_adjoint(s, P.soft_pot(), nl.plan, s0d, N // 2, D, 1.0, Lp, eta, T, K, r, f, ws, out, st)
+    P.md_minimize_adjoint(s, P.soft_pot(), nl.plan, s0d, N // 2, D, 1.0, phi, eta, T, K, r, f, ws, out, st)
     torch.cuda.synchronize()
     assert P.md_status_poll(st) == 0
     return out.cpu().numpy(), r.cpu().numpy()
@@ -162,7 +161,6 @@ def test_adjoint_graph_replay_and_host_launches_agree_bitwise(P):
     p = W.packing_2d(N=N, D=D, seed=9)
     L64 = O.packing_box(N, D, phi)
     L = W.f32(L64)
-    Lp = (N // 2) * math.pi * D / (4 * phi * L64)
     s = P.md_space_periodic(2, [L, L])
     nl = P.NeighborList(s, N, D, SKIN, 64, canonical=True)
     s0 = np.zeros((N, 4), np.float32)
@@ -177,7 +175,7 @@ def test_adjoint_graph_replay_and_host_launches_agree_bitwise(P):
     try:
         for graphs in (True, True, False):
             P.md_set_loop_graphs(graphs)
-            P.md_minimize_adjoint(s, P.soft_pot(), nl.plan, s0d, N // 2, D, 1.0, Lp, 0.05, T, K, r, f, ws, out, st)
+            P.md_minimize_adjoint(s, P.soft_pot(), nl.plan, s0d, N // 2, D, 1.0, phi, 0.05, T, K, r, f, ws, out, st)
             torch.cuda.synchronize()
             assert P.md_status_poll(st) == 0
             res.append([x.cpu().numpy().copy() for x in (out, r, f)])

@@ -28,7 +28,6 @@ def _run(P, p, D, T, K, phi=0.9):
     N = p.N
     L64 = O.packing_box(N, D, phi)
     L = W.f32(L64)
-    Lp = (N // 2) * math.pi * D / (4 * phi * L64)
     s = P.md_space_periodic(2, [L, L])
     nl = P.NeighborList(s, N, max(D, 1.0), SKIN, 64, canonical=True)
     s0 = np.zeros((N, 4), np.float32)
@@ -42,7 +41,7 @@ def _run(P, p, D, T, K, phi=0.9):
     wsv = ws[off:]
     out = torch.zeros(2, dtype=torch.float64, device=dev())
     st = status_word()
-    P.md_minimize_fire_adjoint(s, P.soft_pot(), P.fire_params(), nl.plan, s0d, N // 2, D, 1.0, Lp, T, K, r, v, f,
+    P.md_minimize_fire_adjoint(s, P.soft_pot(), P.fire_params(), nl.plan, s0d, N // 2, D, 1.0, phi, T, K, r, v, f,
                                wsv, out, st)
     torch.cuda.synchronize()
     assert P.md_status_poll(st) == 0
@@ -119,7 +118,6 @@ def test_fire_adjoint_graph_replay_and_host_launches_agree_bitwise(P):
     p = W.packing_2d(N=N, D=D, phi=0.9, seed=3)
     L64 = O.packing_box(N, D, 0.9)
     L = W.f32(L64)
-    Lp = (N // 2) * math.pi * D / (4 * 0.9 * L64)
     s = P.md_space_periodic(2, [L, L])
     nl = P.NeighborList(s, N, D, SKIN, 64, canonical=True)
     s0 = np.zeros((N, 4), np.float32)
@@ -134,7 +132,7 @@ def test_fire_adjoint_graph_replay_and_host_launches_agree_bitwise(P):
     try:
         for graphs in (True, True, False):
             P.md_set_loop_graphs(graphs)
-            P.md_minimize_fire_adjoint(s, P.soft_pot(), P.fire_params(), nl.plan, s0d, N // 2, D, 1.0, Lp, T, K,
+            P.md_minimize_fire_adjoint(s, P.soft_pot(), P.fire_params(), nl.plan, s0d, N // 2, D, 1.0, 0.9, T, K,
                                        r, v, f, wsv, out, st)
             torch.cuda.synchronize()
             assert P.md_status_poll(st) == 0
@@ -166,10 +164,9 @@ def test_graph_cache_eviction_keeps_results(P):
     def call(D):
         L64 = O.packing_box(N, D, 0.9)
         L = W.f32(L64)
-        Lp = (N // 2) * math.pi * D / (4 * 0.9 * L64)
         s = P.md_space_periodic(2, [L, L])
         nl = P.NeighborList(s, N, D, SKIN, 32, canonical=True)
-        P.md_minimize_fire_adjoint(s, P.soft_pot(), P.fire_params(), nl.plan, s0d, N // 2, D, 1.0, Lp, T, K,
+        P.md_minimize_fire_adjoint(s, P.soft_pot(), P.fire_params(), nl.plan, s0d, N // 2, D, 1.0, 0.9, T, K,
                                    r, v, f, wsv, out, st)
         torch.cuda.synchronize()
         assert P.md_status_poll(st) == 0
