@@ -189,12 +189,17 @@ JMD_API md_status md_neighbor_list_update(const md_space *s, const float *d_r, m
  * build positions) comes from a fixed pool of md_noalloc_scratch_bytes()
  * bytes inside the library, held by every GPU that loads it until exit.
  *   - Returns MD_ERR_INVALID when N and the cell grid need more scratch
- *     than the pool holds (48 bytes per particle plus 8 per cell: roughly
- *     85,000 particles), besides the md_nbr_plan errors.  It calls no
+ *     than the pool holds, besides the md_nbr_plan errors.  The need is
+ *     about 68 bytes per particle plus 8 per cell (the md_nbr_plan
+ *     workspace rounded up to 256 bytes, plus 16 bytes per particle of
+ *     build positions): 61,248 particles fit for LJ at density 0.84 with
+ *     r_list 2.8 (box 42.06, 15^3 cells), 61,249 do not.  It calls no
  *     allocating routine.
- *   - The first call on each device looks up the pool's device address
- *     (cudaGetSymbolAddress) with that device current; make that first
- *     call before any stream capture.
+ *   - Outside stream capture every call looks up the pool's device address
+ *     (cudaGetSymbolAddress) with the current device; a captured call reuses
+ *     the address of the last uncaptured one on that device.  Make one
+ *     uncaptured call per device before the first capture, and again after
+ *     a cudaDeviceReset.
  *   - All calls on a device share that device's pool, which keeps the last
  *     call's contents (the parts that must start at zero are cleared by
  *     every call); calls that can overlap on the same GPU, for example on

@@ -15,21 +15,33 @@ namespace jmd {
 
 // The static scratch pool.  Every GPU that loads libjmd holds these bytes
 // until the process exits.  In host code `g_nbr_scratch` names a host-side
-// stand-in, not device memory, so its device address is looked up with
-// cudaGetSymbolAddress (once per device) and passed to the kernels.
+// stand-in, not device memory, so its device address comes from
+// cudaGetSymbolAddress and is passed to the kernels.
 constexpr size_t kNoallocScratchBytes = 4u << 20;   // 4 MiB
 static __device__ __align__(256) unsigned char g_nbr_scratch[kNoallocScratchBytes];
 
 constexpr int kMaxDevices = 64;
-static void *g_scratch_ptr[kMaxDevices];   // device address per device, NULL = not set up
+static void *g_scratch_ptr[kMaxDevices];   // last address seen per device, NULL = never looked up
 
-// Per-device set-up on the first call made with that device current.
-static md_status scratch_for_current_device(void **out)
+// The pool's device address for the current device.  Outside stream
+// capture it is looked up on every call, so a module reloaded after
+// cudaDeviceReset (or a re-created primary context) is never written
+// through a stale pointer.  While `stream` is being captured the address
+// seen by the last uncaptured call is reused (the lookup may load the
+// module, which a capture does not allow); a library used across a device
+// reset must therefore make one uncaptured call before capturing again.
+static md_status scratch_for_current_device(cudaStream_t stream, void **out)
 {
     int dev = 0;
     JMD_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return MD_ERR_INVALID;
-    if (!g_scratch_ptr[dev]) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+        // the legacy stream while another stream captures: treat as captured
+        (void)cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;
+    }
+    if (cs == cudaStreamCaptureStatusNone || !g_scratch_ptr[dev]) {
         void *p = nullptr;
         JMD_CUDA_TRY(cudaGetSymbolAddress(&p, g_nbr_scratch));
         if (!p) return MD_ERR_CUDA;
@@ -58,7 +70,7 @@ extern "C" md_status md_neighbor_list_build_noalloc(const md_space *s, const flo
     size_t need = ws + sizeof(float4) * (size_t)N;
     if (need > kNoallocScratchBytes) return MD_ERR_INVALID;   // N or the cell grid too large for the pool
     void *base = nullptr;
-    st = scratch_for_current_device(&base);
+    st = scratch_for_current_device((cudaStream_t)stream, &base);
     if (st != MD_OK) return st;
     float *rref = (float *)((char *)base + ws);
     // md_nbr_bind clears the control words and the cell histogram, which

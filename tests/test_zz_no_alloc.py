@@ -60,3 +60,33 @@ def test_noalloc_build_rejects_sizes_beyond_the_pool():
     with pytest.raises(P.MDError) as e:
         P.md_neighbor_list_build_noalloc(s, r, N, 2.5, 0.3, 8, nbr, cnt, None)
     assert e.value.code == P.MD_ERR_INVALID
+
+
+def test_noalloc_build_at_the_pool_boundary():
+    # LJ at density 0.84 in a fixed box: the largest N whose scratch fits the
+    # pool gives the workspace build's rows bit for bit; one particle more is
+    # refused before anything runs
+    import torch
+    import paper_1912_04232_b300 as P
+    from test_host_noalloc import noalloc_limit
+    c = W.lj_fluid("fcc", 25, seed=3)          # N = 62,500, L = 42.06
+    s = P.md_space_periodic(3, [c.L] * 3)
+    n = noalloc_limit(P, s, c.N)
+    cap = 128
+    for N, ok in ((n, True), (n + 1, False)):
+        r = to_dev(c.r[:N], torch.float32)
+        nbr = torch.full((N, cap), -7, dtype=torch.int32, device=dev())
+        cnt = torch.full((N,), -7, dtype=torch.int32, device=dev())
+        st = status_word()
+        if not ok:
+            with pytest.raises(P.MDError) as e:
+                P.md_neighbor_list_build_noalloc(s, r, N, 2.5, 0.3, cap, nbr, cnt, st)
+            assert e.value.code == P.MD_ERR_INVALID
+            assert (cnt == -7).all().item()
+            continue
+        P.md_neighbor_list_build_noalloc(s, r, N, 2.5, 0.3, cap, nbr, cnt, st)
+        torch.cuda.synchronize()
+        assert P.md_status_poll(st) == 0
+        cnt_ref, nbr_ref = _reference_rows(P, s, r, N, cap)
+        np.testing.assert_array_equal(cnt.cpu().numpy(), cnt_ref)
+        np.testing.assert_array_equal(nbr.cpu().numpy(), nbr_ref)
