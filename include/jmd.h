@@ -137,11 +137,11 @@ typedef struct {
  * md_tiles_info); its region is the tile grown by two half-cells on each
  * side (periodic), its half-cells in (z, y, x) order.  One CTA per tile stages the region's positions in shared memory
  * with bulk (TMA) copies and evaluates forces, the closing half-kick, the
- * next kick-drift and the displacement check from there.  A row holds the
- * partners whose nearest image is the plain difference first, then (stored
- * from the end of the row backwards) those across the box boundary;
- * between rebuilds positions are not wrapped, so that split stays valid,
- * and they are wrapped at every rebuild and on return.  Membership and the
+ * next kick-drift and the displacement check from there.  The region's
+ * copies from across the box are staged at their periodic image, so a
+ * partner's nearest-image vector is the plain difference; between rebuilds
+ * positions are not wrapped, so those images stay valid, and they are
+ * wrapped at every rebuild and on return.  Membership and the
  * cutoff are decided by the FP32 formula above, so the pair sets are the
  * same as the int32 rows'.  On return md_integrate_nve writes r, v, f, the
  * int32 rows, counts and build positions back in the caller's order.

@@ -281,7 +281,12 @@ constexpr int TILE_OWN_MAX = TILE_XMAX * TILE_TMAX * TILE_TMAX;          // own 
 // total, copies, own half-cells, own particles; the copies (source slot,
 // destination offset << 16 | count); the own half-cells (first slot,
 // first local index << 16 | first own particle).
+// The copy's source slot carries its periodic image in the top bits: two
+// bits per axis (1: +L, 2: -L), so slots need N < 2^26.  The header's
+// copy count carries a flag (bit 16) when any copy has an image.
 constexpr int TILE_TAB_WORDS = 4 + 2 * TILE_PIECES_MAX + 2 * TILE_OWN_MAX;
+constexpr int TILE_SRC_BITS = 26;
+constexpr unsigned TILE_SRC_MASK = (1u << TILE_SRC_BITS) - 1u;
 constexpr int TILE_REG_CAP_MAX = 12800;  // region capacity limit (particles, 200 KB of shared memory)
 constexpr int TILE_SLOTS = 4 * 148;      // resident tile CTAs of a B300 (148 SMs, 4 per SM) for the shape choice
 
@@ -338,7 +343,7 @@ __host__ inline bool tile_geometry(int N, const int *ncell, TilePlan &tp)
 }
 
 struct TileLayout {
-    size_t hcount, hstart, bsum, key, rank, tmp, r0, r1, v0, v1, p0, p1, rref, fs, cnt, tab, rows, total;
+    size_t hcount, hstart, bsum, key, rank, tmp, r0, r1, v0, v1, p0, p1, rref, fs, cnt, tab, rows, sent, total;
 };
 __host__ inline TileLayout tile_layout(int N, int nhc, int cap, int ntiles)
 {
@@ -362,6 +367,7 @@ __host__ inline TileLayout tile_layout(int N, int nhc, int cap, int ntiles)
     t.fs = o;      o = align256(o + sizeof(float4) * n);
     t.cnt = o;     o = align256(o + sizeof(uint32_t) * n);
     t.rows = o;    o = align256(o + sizeof(uint16_t) * n * (size_t)cap);
+    t.sent = o;    o = align256(o + 16);   // one 16-byte row chunk of sentinel entries
     t.total = o;
     return t;
 }

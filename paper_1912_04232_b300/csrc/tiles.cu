@@ -13,10 +13,12 @@
 //     half-cells in (z, y, x) order.  A row (fixed y, z) of the region is a
 //     run of 5 consecutive half-cells along x, i.e. one or two contiguous
 //     slot ranges;
-//   * a particle's row holds 16-bit indices into its tile's region: first
-//     the n0 partners whose nearest image is the plain difference, then,
-//     from the end of the row backwards, the ns partners across the box
-//     boundary; cnt[slot] = n0 | ns << 16.
+//   * a particle's row holds 16-bit indices into its tile's region (the
+//     partners, then the sentinel index reg_cap up to the longest row of its
+//     warp rounded up to 8); cnt[slot] = the number of partners.  The step
+//     kernels stage each region copy at its periodic image (shift codes in
+//     the tile's table), so every partner's nearest-image vector is the
+//     plain difference of staged positions.
 //
 // Rebuild chain (under the loop's IF node, or gated by the rebuild flag):
 //   k_t_bin     wrap-free half-cell of every particle, warp-aggregated
@@ -27,11 +29,9 @@
 //   k_t_place   members of each half-cell by ascending caller index;
 //               positions (wrapped), velocities, ids and build positions
 //               written to the other buffer set
-//   k_t_build   one CTA per tile: stage the region with bulk copies, then one
-//               warp per own half-cell sweeps, for each of the five z-layers
-//               of the half-cell's 5 x 5 x 5 window, the contiguous run of
-//               25 half-cells, 32 candidates at a time, testing each against
-//               every member of the half-cell (ballot compaction into rows)
+//   k_t_build   one CTA per tile: stage the region (bulk copies), then one
+//               thread per own particle tests the x-pruned runs of its
+//               5 x 5 x 5 half-cell window and writes its row
 //   k_t_finish  switches the buffer sets, counts the build
 // Step:
 //   k_t_step    one CTA per tile: stage the region (bulk copies), forces
@@ -72,6 +72,7 @@ struct TileArgs {
     float4 *rref, *fs;
     uint32_t *cnt;
     uint16_t *rows;
+    uint4 *sent;          // a row chunk of eight sentinel entries (written by every build)
     int32_t *tab;         // per-tile tables (TILE_TAB_WORDS each)
     uint32_t *ctl;
     double2 *partials;
@@ -83,7 +84,8 @@ struct TileArgs {
     int export_rows;
     // potential
     int pot;
-    float rc2, sigma2, c24eps, c4eps, e_shift, eps, alpha;
+    float rc2, e_shift, eps, alpha;
+    float lj_f12, lj_f6, lj_e12, lj_e6;   // 48 eps sigma^12, 24 eps sigma^6, 4 eps sigma^12, 4 eps sigma^6
     // integration and reductions
     float hdm, dt, mass;
     double *E_out, *KE_out;
@@ -161,6 +163,19 @@ __device__ __forceinline__ int t_ownq(const TGeo &g, int k)
     return (2 + xo) + g.RX * ((2 + yo) + g.RY * (2 + zo));
 }
 
+// Shared tables of the step kernels (the build adds the region's
+// half-cell offsets, TileSm).
+struct TileStepSm {
+    int own_off[OWN_MAX + 1];      // own half-cell -> first own particle (prefix)
+    int own_slot[OWN_MAX];         // own half-cell -> first slot
+    int own_loc[OWN_MAX];          // own half-cell -> first local index
+    int total;
+    int nown;
+    int ok;
+    unsigned char *kmap;   // own particle -> own half-cell (dynamic shared memory after the positions)
+    unsigned long long bar;        // mbarrier of the bulk copies
+};
+
 struct TileSm {
     int hoff[NQ_MAX + 1];          // region half-cell -> first local index (exclusive prefix)
     int own_off[OWN_MAX + 1];      // own half-cell -> first own particle (prefix)
@@ -185,18 +200,20 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_addr(bar)), "r"(bytes) : "memory");
 }
+// try_wait may suspend the thread until the phase completes, for at most
+// the hint (20 us), so the bounded wait below spins little.
 __device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned phase)
 {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(sm_addr(bar)), "r"(phase)
+        : "r"(sm_addr(bar)), "r"(phase), "r"(20000u)
         : "memory");
     return ok != 0;
 }
-// Bulk (TMA) copy of `bytes` (multiple of 16, both addresses 16-byte
-// aligned) from global to shared memory, completing on `bar`.
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+// from global to shared memory, completing on `bar`.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
 {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -286,7 +303,8 @@ __device__ void tile_scan(const TileArgs &a, const TGeo &g, TileSm &sm)
 }
 
 // Own particle p -> its own half-cell (sm.kmap), from the own tables.
-__device__ __forceinline__ void tile_own_map(TileSm &sm)
+template <class SM>
+__device__ __forceinline__ void tile_own_map(SM &sm)
 {
     for (int k = threadIdx.x; k < sm.nown; k += TT)
         for (int p = sm.own_off[k]; p < sm.own_off[k + 1]; ++p) sm.kmap[p] = (unsigned char)k;
@@ -297,7 +315,8 @@ __device__ __forceinline__ void tile_own_map(TileSm &sm)
 // bulk copies; on a timeout it raises MD_ERR_TIMEOUT and waits once more for
 // the copies still in flight, which target this CTA's shared memory.  The
 // other threads wait at the block barrier.  Returns sm.ok (uniform).
-__device__ bool tile_wait(const TileArgs &a, TileSm &sm)
+template <class SM>
+__device__ bool tile_wait(const TileArgs &a, SM &sm)
 {
     if (threadIdx.x == 0) {
         bool done = mbar_test(&sm.bar, 0u);
@@ -316,8 +335,9 @@ __device__ bool tile_wait(const TileArgs &a, TileSm &sm)
 }
 
 // Build: after tile_scan, stage the region's positions (one thread per
-// region row: the run of five half-cells along x is one slot range, or two
-// where it wraps) and write the tile's table for the steps that follow.
+// region row: the run of half-cells along x is one slot range, or two
+// where it wraps, one bulk copy each) and write the tile's table for the
+// steps that follow.
 // Returns false (uniformly) if the region exceeds the capacity.
 __device__ bool tile_stage_build(const TileArgs &a, const TGeo &g, TileSm &sm, const float4 *rsrc, float4 *cand,
                                  int32_t *tab)
@@ -325,8 +345,11 @@ __device__ bool tile_stage_build(const TileArgs &a, const TGeo &g, TileSm &sm, c
     const int tid = threadIdx.x;
     const int tot = sm.total;
     if (tid == 0) {
+        // the region crosses the box on some axis: some copies need a shift
+        const bool wraps = g.x0 < 2 || g.x0 + g.nx + 2 > a.H[0] || g.y0 < 2 || g.y0 + g.ny + 2 > a.H[1] ||
+                           g.z0 < 2 || g.z0 + g.nz + 2 > a.H[2];
         tab[0] = tot;
-        tab[1] = 2 * g.RY * g.RZ;
+        tab[1] = (2 * g.RY * g.RZ) | (wraps ? 1 << 16 : 0);
         tab[2] = g.nown;
         tab[3] = sm.own_off[g.nown];
     }
@@ -345,6 +368,10 @@ __device__ bool tile_stage_build(const TileArgs &a, const TGeo &g, TileSm &sm, c
     __syncthreads();
     for (int r = tid; r < g.RY * g.RZ; r += TT) {
         const int q0 = g.RX * r;
+        // periodic image of the row: code 1 adds L, code 2 subtracts L
+        const int uy = g.y0 - 2 + r % g.RY, uz = g.z0 - 2 + r / g.RY;
+        const unsigned cyz = (uy < 0 ? 2u : (uy >= a.H[1] ? 1u : 0u)) << 2 |
+                             (uz < 0 ? 2u : (uz >= a.H[2] ? 1u : 0u)) << 4;
         int qs = q0;
         int2 pa = make_int2(0, 0), pb = make_int2(0, 0);
         for (int xl = 1; xl <= g.RX; ++xl) {
@@ -356,7 +383,11 @@ __device__ bool tile_stage_build(const TileArgs &a, const TGeo &g, TileSm &sm, c
                     if (fits && TCHECK(a, sm.hoff[qs] + n <= tot && src >= 0 && src + n <= a.N &&
                                               (sm_addr(cand) & 15u) == 0u, 2))
                         bulk_g2s(cand + sm.hoff[qs], rsrc + src, (unsigned)n * 16u, &sm.bar);
-                    const int2 pc = make_int2(src, (int)(((unsigned)sm.hoff[qs] << 16) | (unsigned)n));
+                    // a copy never crosses the x wrap, so one image per copy
+                    const int ux = g.x0 - 2 + (qs - q0);
+                    const unsigned code = cyz | (ux < 0 ? 2u : (ux >= a.H[0] ? 1u : 0u));
+                    const int2 pc = make_int2((int)((unsigned)src | code << TILE_SRC_BITS),
+                                              (int)(((unsigned)sm.hoff[qs] << 16) | (unsigned)n));
                     if (pa.y == 0) pa = pc;
                     else pb = pc;
                 }
@@ -370,14 +401,14 @@ __device__ bool tile_stage_build(const TileArgs &a, const TGeo &g, TileSm &sm, c
     return tile_wait(a, sm);
 }
 
-// Step: issue the copies of the region from the tile's table (copies and own
-// half-cells as the last build left them); tile_wait completes them.
-// Returns false (uniformly, nothing issued) if the region exceeds the
-// capacity (the build raised the overflow).
-__device__ bool tile_issue_tab(const TileArgs &a, TileSm &sm, const float4 *rsrc, float4 *cand, const int32_t *tab)
+// Step: issue the bulk copies of the region from the tile's table (copies
+// and own half-cells as the last build left them); tile_wait completes
+// them.  Returns false (uniformly, nothing issued) if the region exceeds
+// the capacity (the build raised the overflow).
+__device__ bool tile_issue_tab(const TileArgs &a, TileStepSm &sm, const float4 *rsrc, float4 *cand, const int32_t *tab)
 {
     const int tid = threadIdx.x;
-    const int tot = __ldg(tab + 0), npc = __ldg(tab + 1), nown = __ldg(tab + 2);
+    const int tot = __ldg(tab + 0), npc = __ldg(tab + 1) & 0xffff, nown = __ldg(tab + 2);
     if (tot > a.reg_cap) return false;
     if (!TCHECK(a, tot >= 0 && npc >= 0 && npc <= TILE_PIECES_MAX && nown >= 0 && nown <= TILE_OWN_MAX &&
                        (sm_addr(cand) & 15u) == 0u && (sm_addr(&sm.bar) & 7u) == 0u, 0))
@@ -400,10 +431,43 @@ __device__ bool tile_issue_tab(const TileArgs &a, TileSm &sm, const float4 *rsrc
     for (int k = tid; k < npc; k += TT) {
         const int2 c = __ldg(pc + k);
         const unsigned n = (unsigned)c.y & 0xffffu;
-        if (n > 0u && TCHECK(a, ((unsigned)c.y >> 16) + n <= (unsigned)tot && c.x >= 0 && c.x + (int)n <= a.N, 1))
-            bulk_g2s(cand + ((unsigned)c.y >> 16), rsrc + c.x, n * 16u, &sm.bar);
+        const int src = (int)((unsigned)c.x & TILE_SRC_MASK);
+        if (n > 0u && TCHECK(a, ((unsigned)c.y >> 16) + n <= (unsigned)tot && src + (int)n <= a.N, 1))
+            bulk_g2s(cand + ((unsigned)c.y >> 16), rsrc + src, n * 16u, &sm.bar);
     }
     return true;
+}
+
+// After the staging: the copies taken from across the box get their image
+// (+-L per axis, from the copy's code), so that every staged partner's
+// nearest-image vector is the plain difference.  Tiles whose region does
+// not cross the box skip this (uniform, from the table header).
+// Subtracting L from a coordinate near L is exact; adding L to one near 0
+// rounds once at the precision of L, as the difference of the
+// nearest-image form does.
+__device__ __forceinline__ void tile_shift(const TileArgs &a, float4 *cand, const int32_t *tab)
+{
+    const int hdr = __ldg(tab + 1);
+    if (!(hdr >> 16)) return;
+    const int npc = hdr & 0xffff;
+    const int2 *pc = reinterpret_cast<const int2 *>(tab + 4);
+    for (int k = threadIdx.x; k < npc; k += TT) {
+        const int2 c = __ldg(pc + k);
+        const unsigned code = (unsigned)c.x >> TILE_SRC_BITS;
+        if (!code) continue;
+        const float sx = (code & 1u) ? a.box.L[0] : ((code & 2u) ? -a.box.L[0] : 0.0f);
+        const float sy = (code & 4u) ? a.box.L[1] : ((code & 8u) ? -a.box.L[1] : 0.0f);
+        const float sz = (code & 16u) ? a.box.L[2] : ((code & 32u) ? -a.box.L[2] : 0.0f);
+        const unsigned o = (unsigned)c.y >> 16, n = (unsigned)c.y & 0xffffu;
+        for (unsigned e = 0; e < n; ++e) {
+            float4 p = cand[o + e];
+            p.x += sx;
+            p.y += sy;
+            p.z += sz;
+            cand[o + e] = p;
+        }
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -586,13 +650,14 @@ __global__ void __launch_bounds__(TT) k_t_place(TileArgs a)
 // window the run of x that can hold a partner is one contiguous local range
 // (half-cells farther than r_list from the particle, with a margin above
 // FP32 rounding, are skipped: rows entirely, and up to two on each end of a
-// run).  Partners whose nearest image is
-// the plain difference collect eight at a time in registers (a 16-bit shift
-// register of four words) and go out as one 16-byte store; partners across
-// the box boundary go to the row's tail one by one.  BND: some particle of
-// the warp has a window across the boundary, so the nearest image takes the
-// comparison form (positions are inside [0, L) at a build).  Needs
-// cap % 8 == 0.
+// run).  Partners collect eight at a time in registers (a 16-bit shift
+// register of four words) and go out as one 16-byte store.  The row is then
+// padded with the sentinel index (reg_cap, a far-away position the step
+// kernels place after the region) up to the warp's longest row rounded up
+// to 8, so that the step's thread-per-particle loop, whose warps are these
+// warps, runs without masks.  BND: some particle of the warp has a window
+// across the boundary, so the nearest image takes the comparison form
+// (positions are inside [0, L) at a build).  Needs cap % 8 == 0.
 template <bool BND>
 __device__ __forceinline__ int build_thread(const TileArgs &a, const TGeo &g, const TileSm &sm, const float4 *cand,
                                             int k, int loc, int slot, bool valid)
@@ -605,12 +670,18 @@ __device__ __forceinline__ int build_thread(const TileArgs &a, const TGeo &g, co
     const int xl = 2 + k % g.nx, yl = 2 + (k / g.nx) % g.ny, zl = 2 + k / (g.nx * g.ny);
     uint16_t *row = a.rows + (size_t)slot * a.cap;
     uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;   // shift register of the last eight entries
-    int nb = 0, n0 = 0, ns = 0;
+    int nb = 0, n0 = 0;
     // distance from the particle to region half-cell c along an axis (origin
     // o, width w): zero inside, else to the nearer face
     auto gap = [&](float x, int o, int c, float w) {
         const float lo = (float)(o - 2 + c) * w;
         return fmaxf(0.f, fmaxf(lo - x, x - (lo + w)));
+    };
+    auto push = [&](uint32_t j) {
+        w0 = __funnelshift_r(w0, w1, 16);
+        w1 = __funnelshift_r(w1, w2, 16);
+        w2 = __funnelshift_r(w2, w3, 16);
+        w3 = (w3 >> 16) | (j << 16);
     };
     const float gx0 = gap(ri.x, g.x0, xl - 2, wx), gx1 = gap(ri.x, g.x0, xl - 1, wx);
     const float gx3 = gap(ri.x, g.x0, xl + 1, wx), gx4 = gap(ri.x, g.x0, xl + 2, wx);
@@ -629,50 +700,41 @@ __device__ __forceinline__ int build_thread(const TileArgs &a, const TGeo &g, co
             for (int j = beg; j < end; ++j) {
                 const float4 cj = cand[j];
                 float dx = __fsub_rn(ri.x, cj.x), dy = __fsub_rn(ri.y, cj.y), dz = __fsub_rn(ri.z, cj.z);
-                bool sh = false;
                 if (BND) {
                     const float ux = __fmul_rn(dx, I0), uy = __fmul_rn(dy, I1), uz = __fmul_rn(dz, I2);
-                    const bool sx = ux > 0.5f || ux < -0.5f, sy = uy > 0.5f || uy < -0.5f,
-                               sz = uz > 0.5f || uz < -0.5f;
-                    dx = sx ? __fsub_rn(dx, ux > 0.5f ? L0 : -L0) : dx;
-                    dy = sy ? __fsub_rn(dy, uy > 0.5f ? L1 : -L1) : dy;
-                    dz = sz ? __fsub_rn(dz, uz > 0.5f ? L2 : -L2) : dz;
-                    sh = sx || sy || sz;
+                    dx = (ux > 0.5f || ux < -0.5f) ? __fsub_rn(dx, ux > 0.5f ? L0 : -L0) : dx;
+                    dy = (uy > 0.5f || uy < -0.5f) ? __fsub_rn(dy, uy > 0.5f ? L1 : -L1) : dy;
+                    dz = (uz > 0.5f || uz < -0.5f) ? __fsub_rn(dz, uz > 0.5f ? L2 : -L2) : dz;
                 }
                 const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                const bool pass = r2 < a.r_list2 && j != loc;
-                if (pass && !sh) {
-                    w0 = __funnelshift_r(w0, w1, 16);
-                    w1 = __funnelshift_r(w1, w2, 16);
-                    w2 = __funnelshift_r(w2, w3, 16);
-                    w3 = (w3 >> 16) | ((uint32_t)j << 16);
+                if (r2 < a.r_list2 && j != loc) {
+                    push((uint32_t)j);
                     if (++nb == 8) {
                         if (n0 + 8 <= a.cap) *reinterpret_cast<uint4 *>(row + n0) = make_uint4(w0, w1, w2, w3);
                         n0 += 8;
                         nb = 0;
                     }
                 }
-                if (BND && pass && sh) {
-                    if (ns < a.cap) row[a.cap - 1 - ns] = (uint16_t)j;
-                    ++ns;
-                }
             }
         }
     }
-    // the last nb entries sit at the top of the shift register, in order
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const int pos = 8 - nb + m;   // register position of the m-th pending entry
-        const int q = pos >> 1;
-        const uint32_t wv = q == 0 ? w0 : (q == 1 ? w1 : (q == 2 ? w2 : w3));
-        if (m < nb && n0 + m < a.cap) row[n0 + m] = (uint16_t)(wv >> ((pos & 1) * 16));
-    }
-    n0 += nb;
+    const int n = n0 + nb;
+    const int wmax = __reduce_max_sync(0xffffffffu, valid ? n : 0);
+    const int kend = min((wmax + 7) & ~7, a.cap);
     if (valid) {
-        a.cnt[slot] = (uint32_t)min(n0, 0xffff) | ((uint32_t)min(ns, 0xffff) << 16);
-        if (n0 + ns > a.cap) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+        const uint32_t sent = (uint32_t)a.reg_cap;
+        if (nb > 0) {
+            // the pending entries, then sentinels, as one chunk
+            for (int m = nb; m < 8; ++m) push(sent);
+            if (n0 + 8 <= a.cap) *reinterpret_cast<uint4 *>(row + n0) = make_uint4(w0, w1, w2, w3);
+            n0 += 8;
+        }
+        const uint32_t sw = sent | sent << 16;
+        for (int q = n0; q < kend; q += 8) *reinterpret_cast<uint4 *>(row + q) = make_uint4(sw, sw, sw, sw);
+        a.cnt[slot] = (uint32_t)min(n, 0xffff);
+        if (n > a.cap) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
     }
-    return valid ? n0 + ns : 0;
+    return valid ? n : 0;
 }
 
 __global__ void __launch_bounds__(TT) k_t_build(TileArgs a)
@@ -688,7 +750,7 @@ __global__ void __launch_bounds__(TT) k_t_build(TileArgs a)
     const float4 *rs = t_r(a, (sel & 1u) ^ 1u);
     if (threadIdx.x == 0) {
         bmax = 0;
-        sm.kmap = reinterpret_cast<unsigned char *>(cand + a.reg_cap);
+        sm.kmap = reinterpret_cast<unsigned char *>(cand + a.reg_cap + 1);
     }
     tile_scan(a, g, sm);
     if (!tile_stage_build(a, g, sm, rs, cand, a.tab + (size_t)blockIdx.x * TILE_TAB_WORDS)) return;
@@ -724,6 +786,8 @@ __global__ void k_t_finish(TileArgs a)
     count_launch();
     if (!t_active(a)) return;
     a.ctl[CTL_TSEL] ^= 3u;
+    const uint32_t sw = (uint32_t)a.reg_cap * 0x10001u;
+    *a.sent = make_uint4(sw, sw, sw, sw);
     unsigned long long *b = (unsigned long long *)&a.ctl[CTL_BUILDS_LO];
     *b += 1ull;
     a.ctl[CTL_REBUILD] = 0u;
@@ -732,28 +796,42 @@ __global__ void k_t_finish(TileArgs a)
 // ---------------------------------------------------------------------------
 // forces and the fused step
 // ---------------------------------------------------------------------------
+// 1/x by the PTX approximate reciprocal (at most 1 ulp from the rounded
+// quotient; subnormal results flush to zero, which only the sentinel's
+// r^-6 reaches).
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // One pair's contribution, branch-free: the cutoff decision (r2 < r_c^2, or
 // r2 < sigma_ij^2 for soft spheres) selects the force factor and the
-// energy, so divergent warps run no extra branches.  A masked slot passes
-// r2 = 3e38 and adds exactly zero.
+// energy, so divergent warps run no extra branches.  LJ in the form
+//   F/r = r^-8 (48 eps sigma^12 r^-6 - 24 eps sigma^6),
+//   U   = r^-6 (4 eps sigma^12 r^-6 - 4 eps sigma^6) - U(r_c).
+// Any r2 > 0 is safe: the sentinel partner (r2 ~ 3e36) and a masked slot
+// (r2 = 3e38) fall outside every cutoff and add exactly zero.
 template <int POT>
 __device__ __forceinline__ void t_term(const TileArgs &a, float dx, float dy, float dz, float r2, float wi, float wj,
                                        float &fx, float &fy, float &fz, float &e)
 {
     if (POT == MD_LJ) {
         const bool in = r2 < a.rc2;
-        const float ir2 = __fdividef(1.0f, in ? r2 : 1.0f);
-        const float s2 = a.sigma2 * ir2;
-        const float s6 = s2 * s2 * s2;
-        const float fr = in ? a.c24eps * ir2 * s6 * (2.0f * s6 - 1.0f) : 0.0f;
-        fx += fr * dx;
-        fy += fr * dy;
-        fz += fr * dz;
-        e += in ? a.c4eps * s6 * (s6 - 1.0f) - a.e_shift : 0.0f;
+        const float ir2 = rcp_approx(r2);
+        const float ir6 = ir2 * ir2 * ir2;
+        const float fr = (ir2 * ir6) * fmaf(a.lj_f12, ir6, -a.lj_f6);
+        const float ep = fmaf(ir6, fmaf(a.lj_e12, ir6, -a.lj_e6), -a.e_shift);
+        const float frs = in ? fr : 0.0f;
+        fx = fmaf(frs, dx, fx);
+        fy = fmaf(frs, dy, fy);
+        fz = fmaf(frs, dz, fz);
+        e += in ? ep : 0.0f;
     } else {
         const float sg = 0.5f * (wi + wj);
         const bool in = r2 < sg * sg;
-        const float rr = sqrtf(in ? r2 : 1.0f);
+        const float rr = sqrtf(r2);
         const float isg = __fdividef(1.0f, sg);
         const float x = 1.0f - rr * isg;
         float xa1, ua;
@@ -765,29 +843,21 @@ __device__ __forceinline__ void t_term(const TileArgs &a, float dx, float dy, fl
             ua = xa1 * x / a.alpha;
         }
         const float fr = in ? a.eps * isg * xa1 * __fdividef(1.0f, rr) : 0.0f;
-        fx += fr * dx;
-        fy += fr * dy;
-        fz += fr * dz;
+        fx = fmaf(fr, dx, fx);
+        fy = fmaf(fr, dy, fy);
+        fz = fmaf(fr, dz, fz);
         e += in ? a.eps * ua : 0.0f;
     }
 }
 
-// Partner with the plain difference as nearest image.
+// Partner at the staged position rj (the region's copies carry their
+// periodic image, so the plain difference is the nearest-image vector).
 template <int POT>
-__device__ __forceinline__ void t_pair_plain(const TileArgs &a, const float4 &ri, const float4 &rj, float &fx,
-                                             float &fy, float &fz, float &e)
+__device__ __forceinline__ void t_pair(const TileArgs &a, const float4 &ri, const float4 &rj, float &fx, float &fy,
+                                       float &fz, float &e)
 {
-    const float dx = __fsub_rn(ri.x, rj.x), dy = __fsub_rn(ri.y, rj.y), dz = __fsub_rn(ri.z, rj.z);
-    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    t_term<POT>(a, dx, dy, dz, r2, ri.w, rj.w, fx, fy, fz, e);
-}
-// Partner across the boundary: the full nearest-image formula.
-template <int POT>
-__device__ __forceinline__ void t_pair_image(const TileArgs &a, const float4 &ri, const float4 &rj, float &fx,
-                                             float &fy, float &fz, float &e)
-{
-    float dx, dy, dz;
-    const float r2 = dist2_rn<3>(ri, rj, a.box, dx, dy, dz);
+    const float dx = ri.x - rj.x, dy = ri.y - rj.y, dz = ri.z - rj.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
     t_term<POT>(a, dx, dy, dz, r2, ri.w, rj.w, fx, fy, fz, e);
 }
 
@@ -853,84 +923,76 @@ __device__ __forceinline__ void t_epilogue(float pe_acc, float ke_acc, const Til
     }
 }
 
-// One CTA per tile.  KICK 0: forces and per-particle energies into fs;
-// KICK 2: the fused velocity-Verlet step (closing half-kick at the new
-// forces, then, unless this is the loop's last step, the next kick and
-// drift into the other position buffer with the displacement check; the
-// last step writes the forces instead).
-// Per-particle operands of one pass: the count, the first 2 RW TPP row
-// entries and the last RS TPP (fixed positions, so the loads need not wait
-// for the count), velocity and build position (group leader).  Entries
-// beyond the count are uninitialised memory: t_mask zeroes them before any
-// use, so every index that reaches shared memory is inside the region.
-// Local index j of the staged region, checked under JMD_TILE_CHECKS.
-__device__ __forceinline__ int tj(const TileArgs &a, unsigned j, int tot)
+// The sentinel partner: rows are padded with index reg_cap, where the step
+// kernels put this position; every pair with it lies outside any cutoff.
+constexpr float T_FAR = 1e18f;
+
+// End of an own particle's step.  KICK 0: force and per-particle energy into
+// fs.  KICK 2, the fused velocity-Verlet step: closing half-kick at the new
+// forces, then, unless this is the loop's last step, the next kick and drift
+// into the other position buffer (not wrapped) with the displacement check;
+// the last step writes the forces instead.
+template <int KICK>
+__device__ __forceinline__ void t_finish(const TileArgs &a, int s, const float4 &ri, float4 vi, const float4 &rr,
+                                         bool more, float fx, float fy, float fz, float ei, float4 *rn, float4 *vv,
+                                         float &pe_acc, float &ke_acc, int *moved_any)
 {
-    return TCHECK(a, j < (unsigned)tot, 4) ? (int)j : 0;
+    pe_acc += ei;
+    if (KICK == 0) {
+        a.fs[s] = make_float4(fx, fy, fz, ei);
+        return;
+    }
+    vi.x += a.hdm * fx;
+    vi.y += a.hdm * fy;
+    vi.z += a.hdm * fz;
+    ke_acc += 0.5f * a.mass * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
+    if (more) {
+        vi.x += a.hdm * fx;
+        vi.y += a.hdm * fy;
+        vi.z += a.hdm * fz;
+        float4 r2 = ri;
+        r2.x = ri.x + a.dt * vi.x;
+        r2.y = ri.y + a.dt * vi.y;
+        r2.z = ri.z + a.dt * vi.z;
+        rn[s] = r2;
+        float dx, dy, dz;
+        if (dist2_rn<3>(r2, rr, a.box, dx, dy, dz) > a.half_skin2) *moved_any = 1;
+    } else {
+        a.fs[s] = make_float4(fx, fy, fz, ei);
+    }
+    vv[s] = vi;
 }
 
+// Own particle p of the tile -> its slot and local index.
+__device__ __forceinline__ void t_own(const TileStepSm &sm, int p, int &s, int &li)
+{
+    const int k = sm.kmap[p];
+    const int t = p - sm.own_off[k];
+    s = sm.own_slot[k] + t;
+    li = sm.own_loc[k] + t;
+}
+
+// Step with TPP lanes per particle (tiles of fewer than about 128
+// particles).  Each lane prefetches RW row words at fixed positions (so the
+// loads need not wait for the count); words at and beyond the count are
+// replaced by the sentinel before any use, so every index that reaches
+// shared memory is inside the region or the sentinel.
 template <int TPP, int KICK>
 struct TPre {
     static constexpr int RW = 40 / TPP;   // row words (two entries each) per lane: 80 entries per group
-    static constexpr int RS = 16 / TPP;   // tail entries per lane: 16 per group
     uint32_t c;
     uint32_t w[RW];
-    int js[RS];
     float4 v, rr;
     int s, li;
 };
 
-template <int TPP, int KICK>
-__device__ __forceinline__ void t_prefetch(const TileArgs &a, const TileSm &sm, const float4 *vv, bool more, int p,
-                                           int lg, TPre<TPP, KICK> &q)
-{
-    const int k = sm.kmap[p];
-    const int t = p - sm.own_off[k];
-    q.s = sm.own_slot[k] + t;
-    q.li = sm.own_loc[k] + t;
-    q.c = __ldg(a.cnt + q.s);
-    const uint16_t *row = a.rows + (size_t)q.s * a.cap;
-#pragma unroll
-    for (int k2 = 0; k2 < TPre<TPP, KICK>::RW; ++k2) {
-        const int wi = lg + k2 * TPP;
-        q.w[k2] = 2 * wi + 1 < a.cap ? ld_nc_u32(row + 2 * wi) : 0u;
-    }
-#pragma unroll
-    for (int k2 = 0; k2 < TPre<TPP, KICK>::RS; ++k2) {
-        const int kk = lg + k2 * TPP;
-        q.js[k2] = kk < a.cap ? ld_stream_u16(row + a.cap - 1 - kk) : 0;
-    }
-    if (KICK == 2 && lg == 0) {
-        q.v = vv[q.s];
-        if (more) q.rr = __ldg(a.rref + q.s);
-    }
-}
-
-// Zero the prefetched entries at and beyond the counts n0 (head) and ns
-// (tail from the end).
-template <int TPP, int KICK>
-__device__ __forceinline__ void t_mask(TPre<TPP, KICK> &q, int lg, int n0, int ns)
-{
-#pragma unroll
-    for (int k2 = 0; k2 < TPre<TPP, KICK>::RW; ++k2) {
-        const int e = 2 * (lg + k2 * TPP);
-        q.w[k2] = e + 1 < n0 ? q.w[k2] : (e < n0 ? (q.w[k2] & 0xffffu) : 0u);
-    }
-#pragma unroll
-    for (int k2 = 0; k2 < TPre<TPP, KICK>::RS; ++k2) q.js[k2] = lg + k2 * TPP < ns ? q.js[k2] : 0;
-}
-
-// One CTA per tile.  KICK 0: forces and per-particle energies into fs;
-// KICK 2: the fused velocity-Verlet step (closing half-kick at the new
-// forces, then, unless this is the loop's last step, the next kick and
-// drift into the other position buffer with the displacement check; the
-// last step writes the forces instead).
 template <int POT, int TPP, int KICK>
 __global__ void __launch_bounds__(TT, 4) k_t_step(TileArgs a)
 {
     count_launch();
     extern __shared__ __align__(16) float4 cand[];
-    __shared__ TileSm sm;
+    __shared__ TileStepSm sm;
+    __shared__ int moved_any;
     using Pre = TPre<TPP, KICK>;
     const uint32_t sel = t_sel(a);
     const uint32_t rcb = sel & 1u;
@@ -942,17 +1004,19 @@ __global__ void __launch_bounds__(TT, 4) k_t_step(TileArgs a)
         const uint32_t step = *(volatile uint32_t *)&a.ctl[CTL_STEP];
         more = step + 1u < *(volatile uint32_t *)&a.ctl[CTL_NSTEPS];
     }
-    __shared__ int moved_any;
     if (threadIdx.x == 0) {
-        sm.kmap = reinterpret_cast<unsigned char *>(cand + a.reg_cap);
+        sm.kmap = reinterpret_cast<unsigned char *>(cand + a.reg_cap + 1);
         moved_any = 0;
+        cand[a.reg_cap] = make_float4(T_FAR, T_FAR, T_FAR, 0.f);
     }
     float pe_acc = 0.f, ke_acc = 0.f;
-    if (tile_issue_tab(a, sm, rc, cand, a.tab + (size_t)blockIdx.x * TILE_TAB_WORDS) && tile_wait(a, sm)) {
+    const int32_t *tab = a.tab + (size_t)blockIdx.x * TILE_TAB_WORDS;
+    if (tile_issue_tab(a, sm, rc, cand, tab) && tile_wait(a, sm)) {
+        tile_shift(a, cand, tab);
         tile_own_map(sm);
         const int lg = threadIdx.x & (TPP - 1), gi = threadIdx.x / TPP;
         const int nown = sm.own_off[sm.nown];
-        const int tot = sm.total;
+        const uint32_t sent = (uint32_t)a.reg_cap, sw = sent * 0x10001u;
         // every lane of a warp runs every trip (the group reductions below
         // are full-warp shuffles); lanes past the tile's last particle
         // carry zeros
@@ -963,32 +1027,38 @@ __global__ void __launch_bounds__(TT, 4) k_t_step(TileArgs a)
             float4 ri = make_float4(0.f, 0.f, 0.f, 0.f);
             Pre q;
             if (valid) {
-                t_prefetch<TPP, KICK>(a, sm, vv, more, p, lg, q);
-                ri = cand[q.li];
-                const int n0 = min((int)(q.c & 0xffffu), a.cap);
-                const int ns = min((int)(q.c >> 16), a.cap - n0);
-                t_mask<TPP, KICK>(q, lg, n0, ns);
-                // partners whose nearest image is the plain difference
+                t_own(sm, p, q.s, q.li);
+                q.c = __ldg(a.cnt + q.s);
+                const uint16_t *row = a.rows + (size_t)q.s * a.cap;
 #pragma unroll
                 for (int k2 = 0; k2 < Pre::RW; ++k2) {
                     const int wi = lg + k2 * TPP;
-                    if (2 * wi < n0) {
-                        t_pair_plain<POT>(a, ri, cand[tj(a, q.w[k2] & 0xffffu, tot)], fx, fy, fz, e);
-                        if (2 * wi + 1 < n0) t_pair_plain<POT>(a, ri, cand[tj(a, q.w[k2] >> 16, tot)], fx, fy, fz, e);
+                    q.w[k2] = 2 * wi + 1 < a.cap ? ld_nc_u32(row + 2 * wi) : sw;
+                }
+                if (KICK == 2 && lg == 0) {
+                    q.v = vv[q.s];
+                    if (more) q.rr = __ldg(a.rref + q.s);
+                }
+                ri = cand[q.li];
+                const int n = min((int)(q.c & 0xffffu), a.cap);
+#pragma unroll
+                for (int k2 = 0; k2 < Pre::RW; ++k2) {
+                    const int e2 = 2 * (lg + k2 * TPP);
+                    q.w[k2] = e2 + 1 < n ? q.w[k2] : (e2 < n ? ((q.w[k2] & 0xffffu) | sent << 16) : sw);
+                }
+#pragma unroll
+                for (int k2 = 0; k2 < Pre::RW; ++k2) {
+                    if (2 * (lg + k2 * TPP) < n) {
+                        t_pair<POT>(a, ri, cand[q.w[k2] & 0xffffu], fx, fy, fz, e);
+                        t_pair<POT>(a, ri, cand[q.w[k2] >> 16], fx, fy, fz, e);
                     }
                 }
-                const uint16_t *row = a.rows + (size_t)q.s * a.cap;
-                for (int wi = lg + Pre::RW * TPP; 2 * wi < n0; wi += TPP) {   // rows longer than 80
-                    const uint32_t x = ld_nc_u32(row + 2 * wi);
-                    t_pair_plain<POT>(a, ri, cand[tj(a, x & 0xffffu, tot)], fx, fy, fz, e);
-                    if (2 * wi + 1 < n0) t_pair_plain<POT>(a, ri, cand[tj(a, x >> 16, tot)], fx, fy, fz, e);
+                for (int wi = lg + Pre::RW * TPP; 2 * wi < n; wi += TPP) {   // rows longer than 80
+                    uint32_t x = ld_nc_u32(row + 2 * wi);
+                    x = 2 * wi + 1 < n ? x : ((x & 0xffffu) | sent << 16);
+                    t_pair<POT>(a, ri, cand[x & 0xffffu], fx, fy, fz, e);
+                    t_pair<POT>(a, ri, cand[x >> 16], fx, fy, fz, e);
                 }
-                // partners across the box boundary (row tail, from the end)
-#pragma unroll
-                for (int k2 = 0; k2 < Pre::RS; ++k2)
-                    if (lg + k2 * TPP < ns) t_pair_image<POT>(a, ri, cand[tj(a, q.js[k2], tot)], fx, fy, fz, e);
-                for (int kk = lg + Pre::RS * TPP; kk < ns; kk += TPP)
-                    t_pair_image<POT>(a, ri, cand[tj(a, ld_stream_u16(row + a.cap - 1 - kk), tot)], fx, fy, fz, e);
             }
 #pragma unroll
             for (int o = TPP / 2; o > 0; o >>= 1) {
@@ -997,81 +1067,38 @@ __global__ void __launch_bounds__(TT, 4) k_t_step(TileArgs a)
                 fz += __shfl_xor_sync(0xffffffffu, fz, o);
                 e += __shfl_xor_sync(0xffffffffu, e, o);
             }
-            if (valid && lg == 0) {
-                const float ei = 0.5f * e;
-                pe_acc += ei;
-                if (KICK == 0) {
-                    a.fs[q.s] = make_float4(fx, fy, fz, ei);
-                } else {
-                    float4 vi = q.v;
-                    vi.x += a.hdm * fx;
-                    vi.y += a.hdm * fy;
-                    vi.z += a.hdm * fz;
-                    ke_acc += 0.5f * a.mass * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
-                    if (more) {
-                        vi.x += a.hdm * fx;
-                        vi.y += a.hdm * fy;
-                        vi.z += a.hdm * fz;
-                        float4 r2 = ri;
-                        r2.x = ri.x + a.dt * vi.x;
-                        r2.y = ri.y + a.dt * vi.y;
-                        r2.z = ri.z + a.dt * vi.z;
-                        rn[q.s] = r2;
-                        float dx, dy, dz;
-                        if (dist2_rn<3>(r2, q.rr, a.box, dx, dy, dz) > a.half_skin2) moved_any = 1;
-                    } else {
-                        a.fs[q.s] = make_float4(fx, fy, fz, ei);
-                    }
-                    vv[q.s] = vi;
-                }
-            }
+            if (valid && lg == 0)
+                t_finish<KICK>(a, q.s, ri, q.v, q.rr, more, fx, fy, fz, 0.5f * e, rn, vv, pe_acc, ke_acc,
+                               &moved_any);
         }
     }
     t_epilogue(pe_acc, ke_acc, a, KICK == 2 && more, &moved_any);
 }
 
 // The same step with one thread per own particle (tiles of a few hundred
-// particles fill a CTA in one pass): each thread streams its row in 16-byte
+// particles fill a CTA in one pass).  Each thread streams its row in 16-byte
 // chunks (eight entries, the next chunk fetched while the current one is
-// evaluated) up to the warp's longest row, entries beyond its own count
-// masked to index 0 before they reach shared memory.  Needs cap % 8 == 0.
-__device__ __forceinline__ uint4 ld_nc_v4(const uint16_t *p)
+// evaluated) up to the warp's longest row rounded up to 8: the build padded
+// every row of the warp that far with the sentinel, so no entry is masked.
+// Lanes past the tile's last particle read sentinels only.  Needs cap % 8
+// == 0.
+// (not volatile: the rows are read-only while the step runs, so the
+// compiler may schedule the load early)
+__device__ __forceinline__ uint4 ld_nc_v4(const void *p)
 {
     uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
     return v;
 }
 
 template <int POT>
-__device__ __forceinline__ void t_pair_masked(const TileArgs &a, const float4 &ri, const float4 &rj, bool ok, float &fx,
-                                              float &fy, float &fz, float &e)
-{
-    const float dx = __fsub_rn(ri.x, rj.x), dy = __fsub_rn(ri.y, rj.y), dz = __fsub_rn(ri.z, rj.z);
-    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    t_term<POT>(a, dx, dy, dz, ok ? r2 : 3e38f, ri.w, rj.w, fx, fy, fz, e);
-}
-
-template <int POT>
-__device__ __forceinline__ void t_pair_image_masked(const TileArgs &a, const float4 &ri, const float4 &rj, bool ok,
-                                                    float &fx, float &fy, float &fz, float &e)
-{
-    float dx, dy, dz;
-    const float r2 = dist2_rn<3>(ri, rj, a.box, dx, dy, dz);
-    t_term<POT>(a, dx, dy, dz, ok ? r2 : 3e38f, ri.w, rj.w, fx, fy, fz, e);
-}
-
-template <int POT>
 __device__ __forceinline__ void t_pair_word(const TileArgs &a, const float4 *cand, const float4 &ri, uint32_t w,
-                                            int e, int n0, float &fx, float &fy, float &fz, float &e_acc)
+                                            float &fx, float &fy, float &fz, float &e)
 {
-    // entries e and e + 1 of the row, packed in w; slots beyond the count
-    // read the region's first position and add zero
-    const bool ok0 = e < n0, ok1 = e + 1 < n0;
-    const int j0 = ok0 ? (int)(w & 0xffffu) : 0, j1 = ok1 ? (int)(w >> 16) : 0;
-    t_pair_masked<POT>(a, ri, cand[j0], ok0, fx, fy, fz, e_acc);
-    t_pair_masked<POT>(a, ri, cand[j1], ok1, fx, fy, fz, e_acc);
+    t_pair<POT>(a, ri, cand[w & 0xffffu], fx, fy, fz, e);
+    t_pair<POT>(a, ri, cand[w >> 16], fx, fy, fz, e);
 }
 
 template <int POT, int KICK>
@@ -1079,7 +1106,7 @@ __global__ void __launch_bounds__(TT, 4) k_t_step1(TileArgs a)
 {
     count_launch();
     extern __shared__ __align__(16) float4 cand[];
-    __shared__ TileSm sm;
+    __shared__ TileStepSm sm;
     __shared__ int moved_any;
     const uint32_t sel = t_sel(a);
     const uint32_t rcb = sel & 1u;
@@ -1092,83 +1119,53 @@ __global__ void __launch_bounds__(TT, 4) k_t_step1(TileArgs a)
         more = step + 1u < *(volatile uint32_t *)&a.ctl[CTL_NSTEPS];
     }
     if (threadIdx.x == 0) {
-        sm.kmap = reinterpret_cast<unsigned char *>(cand + a.reg_cap);
+        sm.kmap = reinterpret_cast<unsigned char *>(cand + a.reg_cap + 1);
         moved_any = 0;
+        cand[a.reg_cap] = make_float4(T_FAR, T_FAR, T_FAR, 0.f);
     }
     float pe_acc = 0.f, ke_acc = 0.f;
-    if (tile_issue_tab(a, sm, rc, cand, a.tab + (size_t)blockIdx.x * TILE_TAB_WORDS)) {
-        // the first pass's global operands are fetched while the region's
-        // bulk copies are in flight; positions are read after the wait
+    const int32_t *tab = a.tab + (size_t)blockIdx.x * TILE_TAB_WORDS;
+    if (tile_issue_tab(a, sm, rc, cand, tab)) {
+        // the first pass's counts and first row chunks are fetched while
+        // the region's copies are in flight; positions are read after them
         tile_own_map(sm);
         const int nown = sm.own_off[sm.nown];
         bool staged = false;
         for (int p0 = 0; p0 < nown; p0 += TT) {
             const int p = p0 + threadIdx.x;
             const bool valid = p < nown;
-            int s = 0, n0 = 0, ns = 0, li = 0;
-            float4 ri = make_float4(0.f, 0.f, 0.f, 0.f), vi = ri, rr = ri;
+            int s = 0, n = 0, li = 0;
             if (valid) {
-                const int k = sm.kmap[p];
-                const int t = p - sm.own_off[k];
-                s = sm.own_slot[k] + t;
-                li = sm.own_loc[k] + t;
-                const uint32_t c = __ldg(a.cnt + s);
+                t_own(sm, p, s, li);
+                n = min((int)(__ldg(a.cnt + s) & 0xffffu), a.cap);
+            }
+            const uint16_t *row = a.rows + (size_t)s * a.cap;
+            const int kend = (__reduce_max_sync(0xffffffffu, n) + 7) & ~7;
+            // every load is unconditional: lanes past the tile's last
+            // particle, and the chunk after the last, read the sentinel chunk
+            uint4 nxt = ld_nc_v4(valid ? (const void *)row : (const void *)a.sent);
+            if (p0 == 0) {   // uniform
+                staged = tile_wait(a, sm);
+                if (staged) tile_shift(a, cand, tab);
+            }
+            if (!staged) break;
+            const float4 ri = valid ? cand[li] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+            for (int k0 = 0; k0 < kend; k0 += 8) {
+                const uint4 cur = nxt;
+                nxt = ld_nc_v4((valid && k0 + 8 < kend) ? (const void *)(row + k0 + 8) : (const void *)a.sent);
+                t_pair_word<POT>(a, cand, ri, cur.x, fx, fy, fz, e);
+                t_pair_word<POT>(a, cand, ri, cur.y, fx, fy, fz, e);
+                t_pair_word<POT>(a, cand, ri, cur.z, fx, fy, fz, e);
+                t_pair_word<POT>(a, cand, ri, cur.w, fx, fy, fz, e);
+            }
+            if (valid) {
+                float4 vi = make_float4(0.f, 0.f, 0.f, 0.f), rr = vi;
                 if (KICK == 2) {
                     vi = vv[s];
                     if (more) rr = __ldg(a.rref + s);
                 }
-                n0 = min((int)(c & 0xffffu), a.cap);
-                ns = min((int)(c >> 16), a.cap - n0);
-            }
-            const uint16_t *row = a.rows + (size_t)s * a.cap;
-            float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
-            const int nmax = __reduce_max_sync(0xffffffffu, n0);
-            uint4 nxt = n0 > 0 ? ld_nc_v4(row) : make_uint4(0u, 0u, 0u, 0u);
-            if (p0 == 0) staged = tile_wait(a, sm);   // uniform
-            if (!staged) break;
-            if (valid) ri = cand[li];
-            // partners whose nearest image is the plain difference
-            for (int k0 = 0; k0 < nmax; k0 += 8) {
-                const uint4 cur = nxt;
-                nxt = k0 + 8 < n0 ? ld_nc_v4(row + k0 + 8) : make_uint4(0u, 0u, 0u, 0u);
-                t_pair_word<POT>(a, cand, ri, cur.x, k0, n0, fx, fy, fz, e);
-                t_pair_word<POT>(a, cand, ri, cur.y, k0 + 2, n0, fx, fy, fz, e);
-                t_pair_word<POT>(a, cand, ri, cur.z, k0 + 4, n0, fx, fy, fz, e);
-                t_pair_word<POT>(a, cand, ri, cur.w, k0 + 6, n0, fx, fy, fz, e);
-            }
-            // partners across the box boundary (row tail, from the end)
-            const int nsmax = __reduce_max_sync(0xffffffffu, ns);
-            for (int kk = 0; kk < nsmax; ++kk) {
-                const bool ok = kk < ns;
-                const int j = ok ? ld_stream_u16(row + a.cap - 1 - kk) : 0;
-                t_pair_image_masked<POT>(a, ri, cand[j], ok, fx, fy, fz, e);
-            }
-            if (valid) {
-                const float ei = 0.5f * e;
-                pe_acc += ei;
-                if (KICK == 0) {
-                    a.fs[s] = make_float4(fx, fy, fz, ei);
-                } else {
-                    vi.x += a.hdm * fx;
-                    vi.y += a.hdm * fy;
-                    vi.z += a.hdm * fz;
-                    ke_acc += 0.5f * a.mass * (vi.x * vi.x + vi.y * vi.y + vi.z * vi.z);
-                    if (more) {
-                        vi.x += a.hdm * fx;
-                        vi.y += a.hdm * fy;
-                        vi.z += a.hdm * fz;
-                        float4 r2 = ri;
-                        r2.x = ri.x + a.dt * vi.x;
-                        r2.y = ri.y + a.dt * vi.y;
-                        r2.z = ri.z + a.dt * vi.z;
-                        rn[s] = r2;
-                        float dx, dy, dz;
-                        if (dist2_rn<3>(r2, rr, a.box, dx, dy, dz) > a.half_skin2) moved_any = 1;
-                    } else {
-                        a.fs[s] = make_float4(fx, fy, fz, ei);
-                    }
-                    vv[s] = vi;
-                }
+                t_finish<KICK>(a, s, ri, vi, rr, more, fx, fy, fz, 0.5f * e, rn, vv, pe_acc, ke_acc, &moved_any);
             }
         }
         if (nown == 0) tile_wait(a, sm);   // no pass waited for the copies
@@ -1295,7 +1292,9 @@ static int g_tile_tpp = 0;   // 0: by tile size (1 for tiles of >= 128 particles
 
 static bool tile_plan(const md_space *s, const md_nbr *nb, TilePlan &tp)
 {
-    if (!nb || (s && s->dim != 3) || nb->dim != 3 || nb->N < 1 || (nb->cap & 7) || nb->cap > 0xffff) return false;
+    if (!nb || (s && s->dim != 3) || nb->dim != 3 || nb->N < 1 || nb->N > (int)TILE_SRC_MASK || (nb->cap & 7) ||
+        nb->cap > 0xffff)
+        return false;
     if (!(nb->r_cut > nb->skin)) return false;
     return tile_geometry(nb->N, nb->ncell, tp);
 }
@@ -1346,6 +1345,7 @@ static void make_tile_args(const md_space *s, const md_nbr *nb, const TilePlan &
     a.fs = (float4 *)(b + tl.fs);
     a.cnt = (uint32_t *)(b + tl.cnt);
     a.rows = (uint16_t *)(b + tl.rows);
+    a.sent = (uint4 *)(b + tl.sent);
     a.tab = (int32_t *)(b + tl.tab);
     const WsPtrs w = ws_ptrs(nb);
     a.ctl = w.ctl;
@@ -1360,9 +1360,11 @@ static bool set_tile_pot(const md_pot *p, const md_nbr *nb, TileArgs &a)
     if (p->kind == MD_LJ) {
         if (!(p->r_cut > 0.0f) || p->r_cut > nb->r_list) return false;
         a.rc2 = p->r_cut * p->r_cut;
-        a.sigma2 = p->sigma * p->sigma;
-        a.c24eps = 24.0f * p->eps;
-        a.c4eps = 4.0f * p->eps;
+        const double s6 = pow((double)p->sigma, 6.0), e = (double)p->eps;
+        a.lj_f12 = (float)(48.0 * e * s6 * s6);
+        a.lj_f6 = (float)(24.0 * e * s6);
+        a.lj_e12 = (float)(4.0 * e * s6 * s6);
+        a.lj_e6 = (float)(4.0 * e * s6);
         a.e_shift = p->e_shift;
         return true;
     }
@@ -1374,13 +1376,14 @@ static bool set_tile_pot(const md_pot *p, const md_nbr *nb, TileArgs &a)
     return false;
 }
 
-// positions of the region, then one byte per own particle (kmap)
-static size_t tile_smem(const TileArgs &a) { return (size_t)a.reg_cap * (sizeof(float4) + 1) + 16; }
+// positions of the region and the sentinel, then one byte per own particle (kmap)
+static size_t tile_smem(const TileArgs &a) { return ((size_t)a.reg_cap + 1) * sizeof(float4) + (size_t)a.reg_cap + 16; }
 
 template <typename K>
 static void tile_smem_attr(K kern)
 {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TILE_REG_CAP_MAX * (int)(sizeof(float4) + 1) + 16);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (TILE_REG_CAP_MAX + 1) * (int)sizeof(float4) + TILE_REG_CAP_MAX + 16);
 }
 
 // Dynamic shared memory above 48 KB for the staging kernels, once per
