@@ -178,6 +178,7 @@ def learned_section():
     """Train the BP network (and the graph network) on GPU-generated SW
     data, then run NVE at N = 64,000 atoms with plain SW and with the
     learned potentials."""
+    import torch
     import paper_1912_04232_b300.learned as LP
     temps = np.linspace(500.0, 3000.0, 8)
     t0 = time.perf_counter()
@@ -185,11 +186,30 @@ def learned_section():
     LP.build_lists(ds)
     S = ds.r.shape[0]
     ntr = int(0.8 * S)
+    t_data = time.perf_counter() - t0
     tr = LP.Trainer(ds, batch=8, lr=3e-3, wF=1.0, seed=0)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     tr.train(0, ntr, epochs=40, seed=0, lr_end=1e-4)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t1
     e_rmse, f_rmse = tr.evaluate(ntr, S)
     two = LP.force_rmse_sw2body(ds, ntr, S)
     t_train = time.perf_counter() - t0
+    # one training step (forward, loss, descriptor JVP, network gradient,
+    # Adam) on each network path, from the same start, CUDA events
+    step_ms = {}
+    for name, tc in (("tcgen05_bf16", True), ("fp32", False)):
+        tt = LP.Trainer(ds, batch=8, lr=3e-3, wF=1.0, seed=0, tensor_cores=tc)
+        for _ in range(3):
+            tt.step(0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(20):
+            tt.step(8 * (k % max(1, ntr // 8)))
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms[name] = e0.elapsed_time(e1) / 20
     dep = LP.deploy_compare(tr.params, tr.norm, n_side=20, T=1000.0, steps=200, warmup=20)
     # the graph network on the same data (trained by md_gnn_train_grad + Adam),
     # the training snapshots under 8 symmetry operations of the cubic box each
@@ -211,7 +231,10 @@ def learned_section():
         "force_rmse_eV_per_A_heldout": f_rmse, "energy_rmse_eV_per_atom_heldout": e_rmse,
         "force_rmse_sw_two_body_only": two, "force_rmse_vs_sw_at_deploy": dep["force_rmse_vs_sw_final_eV_per_A"],
         "deploy": {"N": dep["N"], "T_K": 1000.0, "steps": 200, "dt_fs": 1.0, "network": "tcgen05 BF16"},
-        "train": {"snapshots": int(S), "heldout": int(S - ntr), "epochs": 40, "seconds_incl_data": t_train},
+        "train": {"snapshots": int(S), "heldout": int(S - ntr), "epochs": 40, "seconds_incl_data": t_train,
+                  "seconds_data": t_data, "seconds_fit": t_fit, "network": "tcgen05 BF16 (md_bp_mlp_train_tc)",
+                  "step_ms": step_ms, "step_speedup_tc_over_fp32": step_ms["fp32"] / step_ms["tcgen05_bf16"],
+                  "atoms_per_step": 8 * int(ds.n)},
         "gnn": {"force_rmse_eV_per_A_heldout": g_f, "energy_rmse_eV_per_atom_heldout": g_e,
                 "force_rmse_untrained": g_untrained[1], "epochs": 50, "augmentation": "8 cubic symmetry copies",
                 "seconds": t_gnn, "H": 64, "T": 2,

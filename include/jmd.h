@@ -592,6 +592,19 @@ JMD_API md_status md_bp_mlp_train(const float *d_params, const float *d_norm, co
                                   const float *d_cE, float cF, int N, void *d_scratch, float *d_grad,
                                   md_stream_t stream);
 
+/* The same gradient on the tensor cores (tcgen05, BF16 operands, FP32
+ * accumulation in tensor memory): per 128-atom tile the forward pass, its
+ * tangent and the reverse pass as MMAs, and the sums over atoms as MMAs
+ * with the atoms as K, accumulated across tiles; each CTA's partial
+ * gradient is then added in CTA order in FP64 (deterministic).  BF16
+ * rounding of the weights, inputs and per-atom factors keeps it within
+ * about 1e-2 of md_bp_mlp_train (relative to the gradient's norm).
+ * d_G, d_V and d_scratch (md_bp_train_scratch_size(N) bytes) 16-byte
+ * aligned.  Device waits are bounded: MD_ERR_TIMEOUT in *d_status. */
+JMD_API md_status md_bp_mlp_train_tc(const float *d_params, const float *d_norm, const float *d_G, const float *d_V,
+                                     const float *d_cE, float cF, int N, void *d_scratch, float *d_grad,
+                                     uint32_t *d_status, md_stream_t stream);
+
 /* Loss of the energy + force fit (Sec. 4.1) over S snapshots of n atoms:
  *   loss = mean_s ((E_s - E_ref,s) / n)^2 + w_F mean (F - F_ref)^2
  * Writes c_E [S n] and dF [S n][4] (the force errors scaled by

@@ -34,5 +34,6 @@ struct BpArgs {
 void enqueue_bp_desc(const BpArgs &a, cudaStream_t st);
 void enqueue_bp_force(const BpArgs &a, int kick, cudaStream_t st);
 void enqueue_bp_jvp(const BpArgs &a, cudaStream_t st);
+size_t mlp_train_tc_scratch(int N);   // partial gradients of md_bp_mlp_train_tc
 
 }  // namespace jmd

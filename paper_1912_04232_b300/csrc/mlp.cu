@@ -393,7 +393,13 @@ void enqueue_mlp_infer(const float *P, const float *norm, const float *G, int N,
 
 using namespace jmd;
 
-extern "C" size_t md_bp_train_scratch_size(int N) { return (size_t)N * (128 * 3 + 32 + 64) * sizeof(float); }
+extern "C" size_t md_bp_train_scratch_size(int N)
+{
+    if (N < 1) return 0;
+    const size_t fp32 = (size_t)N * (128 * 3 + 32 + 64) * sizeof(float);   // per-atom factors
+    const size_t tc = mlp_train_tc_scratch(N);                               // per-CTA partial gradients
+    return fp32 > tc ? fp32 : tc;
+}
 
 extern "C" md_status md_bp_mlp_infer(const float *d_params, const float *d_norm, const float *d_G, int N,
                                      float *d_Ei, float *d_dEdG, md_stream_t stream)

@@ -154,6 +154,7 @@ _SIGS = {
     "md_bp_forces": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
     "md_bp_jvp": [_P(md_space), _vp, _P(md_nbr), C.c_int, _vp, _vp, _vp, _vp],
     "md_bp_mlp_train": [_vp, _vp, _vp, _vp, _vp, C.c_float, C.c_int, _vp, _vp, _vp],
+    "md_bp_mlp_train_tc": [_vp, _vp, _vp, _vp, _vp, C.c_float, C.c_int, _vp, _vp, _vp, _vp],
     "md_bp_loss_prep": [_vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _vp, _vp, _vp, _vp],
     "md_column_stats": [_vp, C.c_int, C.c_int, _vp, _vp],
     "md_adam_step": [_vp, _vp, _vp, _vp, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, _vp],
@@ -454,6 +455,12 @@ def md_bp_train_scratch_size(N) -> int:
 def md_bp_mlp_train(params, norm, G, V, cE, cF, N, scratch, grad, stream=None):
     _check(_lib.md_bp_mlp_train(_ptr(params), _ptr(norm), _ptr(G), _ptr(V), _ptr(cE), float(cF), int(N),
                                 _ptr(scratch), _ptr(grad), _stream(stream)), "md_bp_mlp_train")
+
+
+def md_bp_mlp_train_tc(params, norm, G, V, cE, cF, N, scratch, grad, status=None, stream=None):
+    """md_bp_mlp_train on the tensor cores (tcgen05, BF16 operands)."""
+    _check(_lib.md_bp_mlp_train_tc(_ptr(params), _ptr(norm), _ptr(G), _ptr(V), _ptr(cE), float(cF), int(N),
+                                   _ptr(scratch), _ptr(grad), _ptr(status), _stream(stream)), "md_bp_mlp_train_tc")
 
 
 def md_bp_loss_prep(Ei, F, Fref, Eref, S, n, wF, cE, dF, loss, stream=None):

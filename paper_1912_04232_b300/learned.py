@@ -194,12 +194,16 @@ def batch_list_view(ds: Dataset, s0: int, S: int):
 
 
 class Trainer:
-    """Adam on the FP32 packed parameters; batches of contiguous snapshots."""
+    """Adam on the FP32 packed parameters; batches of contiguous snapshots.
+    tensor_cores: the network's forward pass and training gradient on the
+    tcgen05 kernels (BF16 operands, FP32 accumulation; the default), else
+    the FP32 CUDA-core kernels."""
 
     def __init__(self, ds: Dataset, batch=16, lr=1e-3, wF=1.0, seed=0, device="cuda", params=None,
-                 init_bias=True):
+                 init_bias=True, tensor_cores=True):
         torch = _t()
         self.ds, self.B, self.lr, self.wF = ds, batch, lr, wF
+        self.tc = bool(tensor_cores)
         n = ds.n
         N = batch * n
         g = torch.Generator().manual_seed(seed)
@@ -253,7 +257,10 @@ class Trainer:
         nb = _batch_list(ds, s0, S)
         r = ds.r[s0:s0 + S].reshape(N, 4)
         J.md_bp_descriptors(self.space, r, nb, n, self.G[:N], self.status)
-        J.md_bp_mlp_infer(self.params, self.norm, self.G[:N], N, self.Ei[:N], self.dEdG[:N])
+        if self.tc:
+            J.md_bp_mlp_infer_tc(self.params, self.norm, self.G[:N], N, self.Ei[:N], self.dEdG[:N], self.status)
+        else:
+            J.md_bp_mlp_infer(self.params, self.norm, self.G[:N], N, self.Ei[:N], self.dEdG[:N])
         J.md_bp_forces(self.space, r, nb, n, self.dEdG[:N], self.Ei[:N], self.Fp[:N], None, self.status)
         J.md_bp_loss_prep(self.Ei[:N], self.Fp[:N], ds.F[s0:s0 + S].reshape(N, 4), ds.E[s0:s0 + S], S, n, self.wF,
                           self.cE[:N], self.dF[:N], self.loss[:2 * S])
@@ -263,8 +270,12 @@ class Trainer:
         n = self.ds.n
         nb, r, N = self.forward(s0, self.B)
         J.md_bp_jvp(self.space, r, nb, n, self.dF[:N], self.V[:N], self.status)
-        J.md_bp_mlp_train(self.params, self.norm, self.G[:N], self.V[:N], self.cE[:N], 1.0, N, self.scratch,
-                          self.grad)
+        if self.tc:
+            J.md_bp_mlp_train_tc(self.params, self.norm, self.G[:N], self.V[:N], self.cE[:N], 1.0, N, self.scratch,
+                                 self.grad, self.status)
+        else:
+            J.md_bp_mlp_train(self.params, self.norm, self.G[:N], self.V[:N], self.cE[:N], 1.0, N, self.scratch,
+                              self.grad)
         self.step_count += 1
         J.md_adam_step(self.params, self.grad, self.m, self.v, N_PARAMS, self.lr, 0.9, 0.999, 1e-8,
                        self.step_count)

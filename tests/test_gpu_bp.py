@@ -126,7 +126,10 @@ def test_descriptor_jvp_matches_oracle(P):
     assert _col_err(V.cpu().numpy(), Vo) <= 1e-4
 
 
-def test_training_gradient_matches_oracle_double_backward(P):
+def _training_case(P, wF=0.7):
+    """Two 64-atom silicon snapshots through the GPU forward pass, loss and
+    descriptor JVP; returns the training kernels' inputs and the FP64
+    oracle's loss and gradient (double backward)."""
     import torch
     S, n_side = 2, 2
     snaps = [_snapshot(n_side, 10 + k) for k in range(S)]
@@ -166,26 +169,91 @@ def test_training_gradient_matches_oracle_double_backward(P):
     dF = torch.zeros((N, 4), dtype=torch.float32, device=dev())
     loss = torch.zeros(2 * S, dtype=torch.float64, device=dev())
     V = torch.zeros((N, 16), dtype=torch.float32, device=dev())
-    scratch = torch.empty(P.md_bp_train_scratch_size(N), dtype=torch.uint8, device=dev())
-    grad = torch.zeros(P.BP_NPARAMS, dtype=torch.float32, device=dev())
-    wF = 0.7
     P.md_bp_descriptors(s, rd, comb, n, G, st)
     P.md_bp_mlp_infer(params, norm, G, N, Ei, dEdG)
     P.md_bp_forces(s, rd, comb, n, dEdG, Ei, F, None, st)
     P.md_bp_loss_prep(Ei, F, to_dev(Fref), to_dev(Eref), S, n, wF, cE, dF, loss)
     P.md_bp_jvp(s, rd, comb, n, dF, V, st)
-    P.md_bp_mlp_train(params, norm, G, V, cE, 1.0, N, scratch, grad)
     torch.cuda.synchronize()
     assert P.md_status_poll(st) == 0
     t64 = lambda a: torch.as_tensor(np.asarray(a, np.float64))
     batch = [(r, L, rf[0], rf[1]) for (r, _), rf in zip(snaps, refs)]
     lo, go = B.loss_and_grads(batch, f32_params(p), t64(mu), t64(sd), w_F=wF)
-    assert abs(loss.sum().item() - lo) <= 1e-4 * lo
-    g_gpu = grad.cpu().numpy().astype(np.float64)
-    g_o = np.concatenate([go[k].numpy().ravel() for k in ("W1", "b1", "W2", "b2", "w3")] + [np.atleast_1d(go["b3"].numpy())])
-    rel = np.linalg.norm(g_gpu - g_o) / np.linalg.norm(g_o)
-    cos = g_gpu @ g_o / (np.linalg.norm(g_gpu) * np.linalg.norm(g_o))
+    g_o = np.concatenate([go[k].numpy().ravel() for k in ("W1", "b1", "W2", "b2", "w3")] +
+                         [np.atleast_1d(go["b3"].numpy())])
+    return dict(params=params, norm=norm, G=G, V=V, cE=cE, N=N, loss=loss, lo=lo, g_o=g_o)
+
+
+# parameter blocks of the packed vector: W1, b1, W2, b2, w3, b3
+BLOCKS = [(0, 1024), (1024, 1088), (1088, 5184), (5184, 5248), (5248, 5312), (5312, 5313)]
+
+
+def _grad_errors(g, ref):
+    """Relative error of the whole gradient and of each parameter block
+    (each against its own norm), and the cosine with the reference."""
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    blocks = [np.linalg.norm(g[a:b] - ref[a:b]) / np.linalg.norm(ref[a:b]) for a, b in BLOCKS]
+    cos = g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref))
+    return rel, max(blocks), cos
+
+
+def test_training_gradient_matches_oracle_double_backward(P):
+    import torch
+    c = _training_case(P)
+    scratch = torch.empty(P.md_bp_train_scratch_size(c["N"]), dtype=torch.uint8, device=dev())
+    grad = torch.zeros(P.BP_NPARAMS, dtype=torch.float32, device=dev())
+    P.md_bp_mlp_train(c["params"], c["norm"], c["G"], c["V"], c["cE"], 1.0, c["N"], scratch, grad)
+    torch.cuda.synchronize()
+    assert abs(c["loss"].sum().item() - c["lo"]) <= 1e-4 * c["lo"]
+    rel, _, cos = _grad_errors(grad.cpu().numpy().astype(np.float64), c["g_o"])
     assert rel <= 1e-3 and cos >= 0.99999, (rel, cos)
+
+
+def test_tensor_core_training_gradient_matches_oracle(P):
+    # tcgen05 BF16 MMAs with FP32 accumulation: the weights, inputs and
+    # per-atom factors rounded to 8 significant bits; every parameter block
+    # within 2e-2 of its norm, cosine >= 0.999
+    import torch
+    c = _training_case(P)
+    scratch = torch.empty(P.md_bp_train_scratch_size(c["N"]), dtype=torch.uint8, device=dev())
+    grad = torch.zeros(P.BP_NPARAMS, dtype=torch.float32, device=dev())
+    st = status_word()
+    P.md_bp_mlp_train_tc(c["params"], c["norm"], c["G"], c["V"], c["cE"], 1.0, c["N"], scratch, grad, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    rel, worst_block, cos = _grad_errors(grad.cpu().numpy().astype(np.float64), c["g_o"])
+    assert rel <= 2e-2 and worst_block <= 2e-2 and cos >= 0.999, (rel, worst_block, cos)
+
+
+@pytest.mark.parametrize("N", [1037, 40000])
+def test_tensor_core_training_gradient_matches_fp32_kernel(P, N):
+    # many tiles (40,000 atoms: up to three per CTA, accumulated in tensor
+    # memory) and a ragged last tile, against the FP32 kernel on the same
+    # inputs; two calls give the same bits (fixed-order sum over CTAs)
+    import torch
+    rng = np.random.default_rng(N)
+    p = B.init_params(3)
+    G = rng.normal(size=(N, 16)).astype(np.float32) * 0.5 + 1.0
+    mu, sd = _norm(G)
+    V = (rng.normal(size=(N, 16)) * 0.05).astype(np.float32)
+    cE = (rng.normal(size=N) * 1e-3).astype(np.float32)
+    params = to_dev(pack(p), torch.float32)
+    norm = to_dev(np.concatenate([mu, sd]), torch.float32)
+    Gd, Vd, cEd = to_dev(G, torch.float32), to_dev(V, torch.float32), to_dev(cE, torch.float32)
+    scratch = torch.empty(P.md_bp_train_scratch_size(N), dtype=torch.uint8, device=dev())
+    g32 = torch.zeros(P.BP_NPARAMS, dtype=torch.float32, device=dev())
+    gtc = torch.zeros_like(g32)
+    gtc2 = torch.zeros_like(g32)
+    st = status_word()
+    P.md_bp_mlp_train(params, norm, Gd, Vd, cEd, 0.8, N, scratch, g32)
+    P.md_bp_mlp_train_tc(params, norm, Gd, Vd, cEd, 0.8, N, scratch, gtc, st)
+    P.md_bp_mlp_train_tc(params, norm, Gd, Vd, cEd, 0.8, N, scratch, gtc2, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    ref = g32.cpu().numpy().astype(np.float64)
+    rel, worst_block, cos = _grad_errors(gtc.cpu().numpy().astype(np.float64), ref)
+    assert rel <= 2e-2 and worst_block <= 2e-2 and cos >= 0.999, (rel, worst_block, cos)
+    assert torch.equal(gtc, gtc2)
 
 
 @pytest.mark.parametrize("N", [1037, 64000])
