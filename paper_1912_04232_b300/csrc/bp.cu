@@ -229,12 +229,43 @@ __device__ __forceinline__ void load16(const float *p, float e[16])
     }
 }
 
+// The queued triplets centred on neighbors: leg s of the atom's list
+// (u = r_j - r_k, so the leg from j to the atom is -u) and the other leg w'
+// from j; F -= sum_m e_jm dt(-u, w')/d(-u).
+__device__ __forceinline__ void bp_leg_terms(const BpArgs &a, const BpConst &c, const int *nj, const float4 *nd,
+                                             const unsigned char *qs, const float4 *qw, int qn, float &fx, float &fy,
+                                             float &fz)
+{
+    const int lane = threadIdx.x & 31;
+    for (int q = lane; q < qn; q += 32) {
+        const int s = qs[q];
+        const float4 u = nd[s], wv = qw[q];
+        const float4 *ep = reinterpret_cast<const float4 *>(a.dEdG + (size_t)nj[s] * 16 + 8);
+        const float4 e0 = __ldg(ep), e1 = __ldg(ep + 1);
+        const float ej[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+        float tt[8], du[8][3], dw[8][3];
+        angular8<true>(c, -u.x, -u.y, -u.z, u.w, wv.x, wv.y, wv.z, wv.w, tt, du, dw);
+#pragma unroll
+        for (int qq = 0; qq < 8; ++qq) {
+            fx -= ej[qq] * du[qq][0];
+            fy -= ej[qq] * du[qq][1];
+            fz -= ej[qq] * du[qq][2];
+        }
+    }
+    __syncwarp();
+}
+
+constexpr int BP_QMAX = 96;   // queued neighbor-centred triplets per warp
+
 template <int KICK>
 __global__ void __launch_bounds__(BP_WARPS * 32) k_bp_force(BpArgs a)
 {
     count_launch();
     __shared__ int nj[BP_WARPS][BP_MAXN];
     __shared__ float4 nd[BP_WARPS][BP_MAXN];
+    __shared__ int qpre[BP_WARPS][BP_MAXN + 1];       // neighbors' row offsets in the candidate sweep
+    __shared__ unsigned char qs[BP_WARPS][BP_QMAX];   // queued triplets: leg
+    __shared__ float4 qw[BP_WARPS][BP_QMAX];          // ... and the other leg (w', |w'|)
     const BpConst c = bp_const();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float pe_acc = 0.0f, ke_acc = 0.0f;
@@ -275,40 +306,67 @@ __global__ void __launch_bounds__(BP_WARPS * 32) k_bp_force(BpArgs a)
             }
         }
         // triplets centred on neighbor j with k as leg u' = r_k - r_j:
-        // F_k -= sum_m e_jm dt(u', w')/du', w' = r_l - r_j, l in N(j), l != k
-        for (int s = 0; s < m; ++s) {
-            const int j = nj[w][s];
-            const float4 uj = nd[w][s];
-            const float4 rj = __ldg(a.r + j);
-            float ej[8];
-            {
-                const float4 *q = reinterpret_cast<const float4 *>(a.dEdG + (size_t)j * 16 + 8);
-                float4 v0 = __ldg(q), v1 = __ldg(q + 1);
-                ej[0] = v0.x; ej[1] = v0.y; ej[2] = v0.z; ej[3] = v0.w;
-                ej[4] = v1.x; ej[5] = v1.y; ej[6] = v1.z; ej[7] = v1.w;
-            }
-            int nn = a.cnt[j];
-            nn = nn < a.cap ? nn : a.cap;
-            const int32_t *rowj = a.nbr + (size_t)j * a.cap;
-            const int basej = a.sys_n ? (j / a.sys_n) * a.sys_n : 0;
-            for (int k0 = 0; k0 < nn; k0 += 32) {
-                int kk = k0 + lane;
-                if (kk >= nn) continue;
-                int l = rowj[kk] + basej;
-                if (l == k) continue;
-                float4 rl = __ldg(a.r + l);
-                float wx, wy, wz;
-                float w2 = dist2_rn<3>(rl, rj, a.box, wx, wy, wz);
-                if (!(w2 < c.rc2)) continue;
-                float tt[8], du[8][3], dw[8][3];
-                angular8<true>(c, -uj.x, -uj.y, -uj.z, uj.w, wx, wy, wz, sqrtf(w2), tt, du, dw);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    fx -= ej[q] * du[q][0];
-                    fy -= ej[q] * du[q][1];
-                    fz -= ej[q] * du[q][2];
+        // F_k -= sum_m e_jm dt(u', w')/du', w' = r_l - r_j, l in N(j), l != k.
+        // The candidates (s, l) of all neighbors' rows are swept 32 per
+        // step, those inside R_c queued (leg s, w'), and the queue is
+        // evaluated with every lane busy.
+        {
+            int tot = 0;
+            for (int s0 = 0; s0 < m; s0 += 32) {   // exclusive prefix of the neighbors' row lengths
+                const int s = s0 + lane;
+                int nn = 0;
+                if (s < m) {
+                    nn = a.cnt[nj[w][s]];
+                    nn = nn < a.cap ? nn : a.cap;
                 }
+                int incl = nn;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (s < m) qpre[w][s] = tot + incl - nn;
+                tot += __shfl_sync(0xffffffffu, incl, 31);
             }
+            if (lane == 0) qpre[w][m] = tot;
+            __syncwarp();
+            int qn = 0;
+            for (int b0 = 0; b0 < tot; b0 += 32) {
+                const int it = b0 + lane;
+                bool in = false;
+                int s = 0;
+                float wx = 0.f, wy = 0.f, wz = 0.f, w2 = 0.f;
+                if (it < tot) {
+                    int lo = 0, hi = m - 1;   // last s with qpre[s] <= it
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (qpre[w][mid] <= it) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    s = lo;
+                    const int j = nj[w][s];
+                    const int basej = a.sys_n ? (j / a.sys_n) * a.sys_n : 0;
+                    const int l = a.nbr[(size_t)j * a.cap + (it - qpre[w][s])] + basej;
+                    if (l != k) {
+                        const float4 rj = __ldg(a.r + j), rl = __ldg(a.r + l);
+                        w2 = dist2_rn<3>(rl, rj, a.box, wx, wy, wz);
+                        in = w2 < c.rc2;
+                    }
+                }
+                const unsigned mk = __ballot_sync(0xffffffffu, in);
+                if (qn + __popc(mk) > BP_QMAX) {   // full: evaluate what is queued
+                    bp_leg_terms(a, c, nj[w], nd[w], qs[w], qw[w], qn, fx, fy, fz);
+                    qn = 0;
+                }
+                const int pos = qn + __popc(mk & ((1u << lane) - 1u));
+                if (in) {
+                    qs[w][pos] = (unsigned char)s;
+                    qw[w][pos] = make_float4(wx, wy, wz, sqrtf(w2));
+                }
+                qn += __popc(mk);
+                __syncwarp();
+            }
+            bp_leg_terms(a, c, nj[w], nd[w], qs[w], qw[w], qn, fx, fy, fz);
         }
         fx = warp_sum(fx);
         fy = warp_sum(fy);

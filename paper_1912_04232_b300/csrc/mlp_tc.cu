@@ -23,22 +23,48 @@
 
 namespace jmd {
 
-__device__ __forceinline__ float sgm(float x) { return 1.0f / (1.0f + __expf(-x)); }
+// Logistic sigmoid as 1/2 + tanh(x/2)/2 with the PTX approximate tanh (one
+// special-function instruction; its error, about 2^-11 relative, is below
+// the BF16 rounding the network's operands get anyway).
+__device__ __forceinline__ float sgm(float x)
+{
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * x));
+    return fmaf(0.5f, t, 0.5f);
+}
 
-// shared-memory plan (bytes): weights then the four A operands
+// shared-memory plan (bytes): weights, then the A operands.  One buffer
+// holds H1, then G2, then G1: each is written only after the MMA that read
+// the previous one has completed.
 constexpr int TC_M = 128;
 constexpr uint32_t SM_W1 = 0;                     // [64 x 16]  B of MMA1 (W1, rows = out units)
 constexpr uint32_t SM_W2 = SM_W1 + 64 * 16 * 2;   // [64 x 64]  B of MMA2 (W2)
 constexpr uint32_t SM_W2T = SM_W2 + 64 * 64 * 2;  // [64 x 64]  B of MMA3 (W2^T)
 constexpr uint32_t SM_W1T = SM_W2T + 64 * 64 * 2; // [16 x 64]  B of MMA4 (W1^T)
 constexpr uint32_t SM_X = SM_W1T + 16 * 64 * 2;   // [128 x 16]
-constexpr uint32_t SM_H1 = SM_X + TC_M * 16 * 2;  // [128 x 64]
-constexpr uint32_t SM_G2 = SM_H1 + TC_M * 64 * 2; // [128 x 64]
-constexpr uint32_t SM_G1 = SM_G2 + TC_M * 64 * 2; // [128 x 64]
-constexpr uint32_t SM_TOTAL = SM_G1 + TC_M * 64 * 2;
-constexpr uint32_t SM_LAUNCH = 100 * 1024;          // >= SM_TOTAL; at most 2 CTAs per SM
+constexpr uint32_t SM_A = SM_X + TC_M * 16 * 2;   // [128 x 64] H1, G2, G1 in turn
+constexpr uint32_t SM_TOTAL = SM_A + TC_M * 64 * 2;
+// requested per CTA: at least the layout, and enough that a fifth CTA
+// never fits on an SM (its tensor-memory allocation would have to wait)
+constexpr uint32_t SM_LAUNCH = 52 * 1024;
 static_assert(SM_LAUNCH >= SM_TOTAL, "the launch must cover the layout");
-constexpr uint32_t TMEM_COLS = 256;               // D1 [0,64) D2 [64,128) D3 [128,192) D4 [192,208)
+// tensor-memory columns: D1 [0,64) (kept for silu'(a1) of the backward
+// pass); D2, then D3, then D4 in [64,128), each written after the previous
+// one has been read.  128 columns: four CTAs per SM.
+constexpr uint32_t TMEM_COLS = 128;
+constexpr uint32_t TC_D1 = 0, TC_D2 = 64, TC_D3 = 64, TC_D4 = 64;
+
+__device__ __forceinline__ uint32_t tc_pack(float a, float b)
+{
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+// 8 consecutive K elements (k0 a multiple of 8) of row `row`, one 16-byte store
+__device__ __forceinline__ void tc_row8(unsigned char *sm, uint32_t buf, int row, int k0, int K, const float *v)
+{
+    *reinterpret_cast<uint4 *>(sm + buf + kmajor_off(row, k0, K)) =
+        make_uint4(tc_pack(v[0], v[1]), tc_pack(v[2], v[3]), tc_pack(v[4], v[5]), tc_pack(v[6], v[7]));
+}
 
 struct TcSmallSmem {
     uint64_t bar;
@@ -48,7 +74,7 @@ struct TcSmallSmem {
     float b3;
 };
 
-__global__ void __launch_bounds__(128, 1) k_mlp_infer_tc(const float *P, const float *norm, const float *G, int N,
+__global__ void __launch_bounds__(128, 4) k_mlp_infer_tc(const float *P, const float *norm, const float *G, int N,
                                                          float *Ei, float *dEdG, uint32_t *status)
 {
     count_launch();
@@ -58,18 +84,34 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer_tc(const float *P, const f
     unsigned char *sm = tc_smem;
     const uint32_t sbase = smem_u32(sm);
 
-    // stage weights (BF16, canonical layouts) and small vectors
-    for (int e = tid; e < 64 * 16; e += blockDim.x) {
-        int h = e / 16, q = e % 16;
-        __nv_bfloat16 v = __float2bfloat16_rn(P[P_W1 + e]);
-        *reinterpret_cast<__nv_bfloat16 *>(sm + SM_W1 + kmajor_off(h, q, 16)) = v;   // W1 [h][q]
-        *reinterpret_cast<__nv_bfloat16 *>(sm + SM_W1T + kmajor_off(q, h, 64)) = v;  // W1^T [q][h]
-    }
-    for (int e = tid; e < 64 * 64; e += blockDim.x) {
-        int h = e / 64, c = e % 64;
-        __nv_bfloat16 v = __float2bfloat16_rn(P[P_W2 + e]);
-        *reinterpret_cast<__nv_bfloat16 *>(sm + SM_W2 + kmajor_off(h, c, 64)) = v;   // W2 [h][c]
-        *reinterpret_cast<__nv_bfloat16 *>(sm + SM_W2T + kmajor_off(c, h, 64)) = v;  // W2^T [c][h]
+    // stage weights (BF16, canonical layouts): each thread packs blocks of 8
+    // consecutive K elements of a row into one 16-byte store; W1 [h][q] and
+    // W2 [h][c] rows are contiguous in P, the transposes read a column
+    for (int b = tid; b < 64 * 2 + 16 * 8 + 64 * 8 * 2; b += blockDim.x) {
+        float v[8];
+        uint32_t buf;
+        int row, k0, K;
+        if (b < 128) {                       // W1 [64 x 16]
+            row = b >> 1, k0 = (b & 1) * 8, K = 16, buf = SM_W1;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __ldg(P + P_W1 + row * 16 + k0 + k);
+        } else if (b < 256) {                // W1^T [16 x 64]
+            const int e = b - 128;
+            row = e >> 3, k0 = (e & 7) * 8, K = 64, buf = SM_W1T;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __ldg(P + P_W1 + (k0 + k) * 16 + row);
+        } else if (b < 768) {                // W2 [64 x 64]
+            const int e = b - 256;
+            row = e >> 3, k0 = (e & 7) * 8, K = 64, buf = SM_W2;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __ldg(P + P_W2 + row * 64 + k0 + k);
+        } else {                             // W2^T [64 x 64]
+            const int e = b - 768;
+            row = e >> 3, k0 = (e & 7) * 8, K = 64, buf = SM_W2T;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __ldg(P + P_W2 + (k0 + k) * 64 + row);
+        }
+        tc_row8(sm, buf, row, k0, K, v);
     }
     if (tid < 64) {
         S.b1[tid] = P[P_B1 + tid];
@@ -120,11 +162,11 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer_tc(const float *P, const f
         if (tid == 0) {
             tc_after_sync();
             if (which == 1) {
-                mma_bf16(tmem + 0, dX, dW1, id64, 0u);
+                mma_bf16(tmem + TC_D1, dX, dW1, id64, 0u);
             } else {
-                uint32_t a = which == 2 ? SM_H1 : (which == 3 ? SM_G2 : SM_G1);
+                const uint32_t a = SM_A;
                 uint32_t b = which == 2 ? SM_W2 : (which == 3 ? SM_W2T : SM_W1T);
-                uint32_t d = which == 2 ? 64u : (which == 3 ? 128u : 192u);
+                uint32_t d = which == 2 ? TC_D2 : (which == 3 ? TC_D3 : TC_D4);
                 uint32_t id = which == 4 ? id16 : id64;
                 for (int kk = 0; kk < 4; ++kk) {   // K = 64 in four K = 16 steps (2 core matrices each)
                     uint64_t da = sdesc(sbase + a + kk * 2 * 128, 128, 8 * 128);
@@ -154,11 +196,11 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer_tc(const float *P, const f
                     g[4 * k + 3] = v.w;
                 }
             }
+            float x[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                float x = valid ? (g[q] - S.mu[q]) * S.isd[q] : 0.0f;
-                *reinterpret_cast<__nv_bfloat16 *>(sm + SM_X + kmajor_off(tid, q, 16)) = __float2bfloat16_rn(x);
-            }
+            for (int q = 0; q < 16; ++q) x[q] = valid ? (g[q] - S.mu[q]) * S.isd[q] : 0.0f;
+            tc_row8(sm, SM_X, tid, 0, 16, x);
+            tc_row8(sm, SM_X, tid, 8, 16, x + 8);
         }
         fence_async_smem();
         tc_before_sync();
@@ -168,14 +210,15 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer_tc(const float *P, const f
         // h1 = silu(D1 + b1) -> H1
 #pragma unroll
         for (int c0 = 0; c0 < 64; c0 += 16) {
-            float d[16];
-            tmem_ld16(row_addr + c0, d);
+            float d[16], h[16];
+            tmem_ld16(row_addr + TC_D1 + c0, d);
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 float a = d[k] + S.b1[c0 + k];
-                float h = a * sgm(a);
-                *reinterpret_cast<__nv_bfloat16 *>(sm + SM_H1 + kmajor_off(tid, c0 + k, 64)) = __float2bfloat16_rn(h);
+                h[k] = a * sgm(a);
             }
+            tc_row8(sm, SM_A, tid, c0, 64, h);
+            tc_row8(sm, SM_A, tid, c0 + 8, 64, h + 8);
         }
         fence_async_smem();
         tc_before_sync();
@@ -186,17 +229,17 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer_tc(const float *P, const f
         float E = S.b3;
 #pragma unroll
         for (int c0 = 0; c0 < 64; c0 += 16) {
-            float d[16];
-            tmem_ld16(row_addr + 64 + c0, d);
+            float d[16], g2[16];
+            tmem_ld16(row_addr + TC_D2 + c0, d);
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 float a = d[k] + S.b2[c0 + k];
                 float s = sgm(a);
                 E += S.w3[c0 + k] * a * s;
-                float g2 = S.w3[c0 + k] * s * (1.0f + a * (1.0f - s));
-                *reinterpret_cast<__nv_bfloat16 *>(sm + SM_G2 + kmajor_off(tid, c0 + k, 64)) =
-                    __float2bfloat16_rn(g2);
+                g2[k] = S.w3[c0 + k] * s * (1.0f + a * (1.0f - s));
             }
+            tc_row8(sm, SM_A, tid, c0, 64, g2);
+            tc_row8(sm, SM_A, tid, c0 + 8, 64, g2 + 8);
         }
         if (valid) Ei[i] = E;
         fence_async_smem();
@@ -207,17 +250,17 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer_tc(const float *P, const f
         // G1 = D3 * silu'(D1 + b1)
 #pragma unroll
         for (int c0 = 0; c0 < 64; c0 += 16) {
-            float d3[16], d1[16];
-            tmem_ld16(row_addr + 128 + c0, d3);
-            tmem_ld16(row_addr + c0, d1);
+            float d3[16], d1[16], g1[16];
+            tmem_ld16(row_addr + TC_D3 + c0, d3);
+            tmem_ld16(row_addr + TC_D1 + c0, d1);
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 float a = d1[k] + S.b1[c0 + k];
                 float s = sgm(a);
-                float g1 = d3[k] * s * (1.0f + a * (1.0f - s));
-                *reinterpret_cast<__nv_bfloat16 *>(sm + SM_G1 + kmajor_off(tid, c0 + k, 64)) =
-                    __float2bfloat16_rn(g1);
+                g1[k] = d3[k] * s * (1.0f + a * (1.0f - s));
             }
+            tc_row8(sm, SM_A, tid, c0, 64, g1);
+            tc_row8(sm, SM_A, tid, c0 + 8, 64, g1 + 8);
         }
         fence_async_smem();
         tc_before_sync();
@@ -227,7 +270,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_infer_tc(const float *P, const f
         // dE/dG = D4 / sd
         {
             float d[16];
-            tmem_ld16(row_addr + 192, d);
+            tmem_ld16(row_addr + TC_D4, d);
             if (valid) {
                 float4 *o = reinterpret_cast<float4 *>(dEdG + (size_t)i * 16);
 #pragma unroll
@@ -257,11 +300,10 @@ void enqueue_mlp_infer_tc(const float *P, const float *norm, const float *G, int
         if (sms < 1) sms = 1;
         cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_LAUNCH);
     }
-    // two CTAs per SM: each holds 256 of the SM's 512 tensor-memory columns,
-    // and the shared memory requested per CTA (SM_LAUNCH) keeps a third off
-    // the SM, where its allocation would wait for one of the two to finish
+    // four CTAs per SM: each holds 128 of the SM's 512 tensor-memory
+    // columns; the grid never exceeds four per SM, so no allocation waits
     int tiles = (N + TC_M - 1) / TC_M;
-    int g = tiles < 2 * sms ? tiles : 2 * sms;
+    int g = tiles < 4 * sms ? tiles : 4 * sms;
     k_mlp_infer_tc<<<g, 128, SM_LAUNCH, st>>>(P, norm, G, N, Ei, dEdG, status);
 }
 

@@ -70,7 +70,14 @@ struct TrSmall {
     float b1[64], b2[64], w3[64], mu[16], isd[16];
 };
 
-__device__ __forceinline__ float tr_sigm(float x) { return 1.0f / (1.0f + __expf(-x)); }
+// Logistic sigmoid as 1/2 + tanh(x/2)/2 with the PTX approximate tanh (its
+// error, about 2^-11 relative, is below the BF16 rounding of the operands).
+__device__ __forceinline__ float tr_sigm(float x)
+{
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * x));
+    return fmaf(0.5f, t, 0.5f);
+}
 
 __device__ __forceinline__ uint32_t bf16_bits(float v) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ uint32_t bf16_pack(float a, float b) { return bf16_bits(a) | (bf16_bits(b) << 16); }
