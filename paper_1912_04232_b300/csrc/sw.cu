@@ -8,7 +8,8 @@
 //   (1) the two-body terms of every neighbor j,
 //   (2) the triplets centred on i (legs j < k of i's neighbors), and
 //   (3) the triplets centred on each neighbor j in which i is a leg
-//       (the other leg k runs over j's row).
+//       (the other leg k runs over j's row; the candidates inside a*sigma
+//       are queued first and then evaluated with every lane busy).
 // e_i = 1/2 sum_j phi2(r_ij) + sum_{j<k} phi3(i; j, k), so sum_i e_i = E.
 #include "common.cuh"
 #include "kernels.cuh"
@@ -89,12 +90,35 @@ __device__ __forceinline__ float sw_triplet(const SwP &P, float ux, float uy, fl
     return h;
 }
 
+// The queued triplets centred on neighbors: leg s of the atom's list
+// (u = r_j - r_i, so the leg from j to the atom is -u) and the other leg w'
+// from j; F -= dh(-u, w')/d(-u).
+__device__ __forceinline__ void sw_leg_terms(const SwP &P, const float4 *nd, const unsigned char *qs, const float4 *qw,
+                                             int qn, float &fx, float &fy, float &fz)
+{
+    const int lane = threadIdx.x & 31;
+    for (int q = lane; q < qn; q += 32) {
+        const float4 u = nd[qs[q]], wv = qw[q];
+        float gu[3], gw[3];
+        sw_triplet(P, -u.x, -u.y, -u.z, u.w, wv.x, wv.y, wv.z, wv.w, gu, gw);
+        fx -= gu[0];
+        fy -= gu[1];
+        fz -= gu[2];
+    }
+    __syncwarp();
+}
+
+constexpr int SW_QMAX = 96;   // queued neighbor-centred triplets per warp
+
 template <int KICK>
 __global__ void __launch_bounds__(SW_WARPS * 32) k_sw(PairArgs a)
 {
     count_launch();
     __shared__ int nj[SW_WARPS][SW_MAXN];
     __shared__ float4 nd[SW_WARPS][SW_MAXN];   // (ux, uy, uz, r): u = r_j - r_i
+    __shared__ int qpre[SW_WARPS][SW_MAXN + 1];       // neighbors' row offsets in the candidate sweep
+    __shared__ unsigned char qs[SW_WARPS][SW_QMAX];   // queued triplets: leg
+    __shared__ float4 qw[SW_WARPS][SW_QMAX];          // ... and the other leg (w', |w'|)
     const SwP P = sw_params(a);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -155,29 +179,66 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_sw(PairArgs a)
             e += h;
         }
         // (3) triplets centred on neighbor j with i as a leg:
-        //     u' = r_i - r_j = -u, w' = r_k - r_j; F_i -= dh/du'
-        for (int s = 0; s < m; ++s) {
-            const int j = nj[w][s];
-            const float4 uj = nd[w][s];
-            const float4 rj = __ldg(a.r + j);
-            int nn = a.cnt[j];
-            nn = nn < a.cap ? nn : a.cap;
-            const int32_t *rowj = a.nbr + (size_t)j * a.cap;
-            for (int k0 = 0; k0 < nn; k0 += 32) {
-                int k = k0 + lane;
-                if (k >= nn) continue;
-                int kk = rowj[k];
-                if (kk == i) continue;
-                float4 rk = __ldg(a.r + kk);
-                float wx, wy, wz;
-                float w2 = dist2_rn<3>(rk, rj, a.box, wx, wy, wz);
-                if (!(w2 < P.rc2)) continue;
-                float gu[3], gw[3];
-                sw_triplet(P, -uj.x, -uj.y, -uj.z, uj.w, wx, wy, wz, sqrtf(w2), gu, gw);
-                fx -= gu[0];
-                fy -= gu[1];
-                fz -= gu[2];
+        //     u' = r_i - r_j = -u, w' = r_k - r_j; F_i -= dh/du'.
+        //     The candidates (s, k) of all neighbors' rows are swept 32 per
+        //     step, those inside a*sigma queued (leg s, w'), and the queue
+        //     is evaluated with every lane busy.
+        {
+            int tot = 0;
+            for (int s0 = 0; s0 < m; s0 += 32) {   // exclusive prefix of the neighbors' row lengths
+                const int s = s0 + lane;
+                int nn = 0;
+                if (s < m) {
+                    nn = a.cnt[nj[w][s]];
+                    nn = nn < a.cap ? nn : a.cap;
+                }
+                int incl = nn;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (s < m) qpre[w][s] = tot + incl - nn;
+                tot += __shfl_sync(0xffffffffu, incl, 31);
             }
+            if (lane == 0) qpre[w][m] = tot;
+            __syncwarp();
+            int qn = 0;
+            for (int b0 = 0; b0 < tot; b0 += 32) {
+                const int it = b0 + lane;
+                bool in = false;
+                int s = 0;
+                float wx = 0.f, wy = 0.f, wz = 0.f, w2 = 0.f;
+                if (it < tot) {
+                    int lo = 0, hi = m - 1;   // last s with qpre[s] <= it
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (qpre[w][mid] <= it) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    s = lo;
+                    const int j = nj[w][s];
+                    const int kk = a.nbr[(size_t)j * a.cap + (it - qpre[w][s])];
+                    if (kk != i) {
+                        const float4 rj = __ldg(a.r + j), rk = __ldg(a.r + kk);
+                        w2 = dist2_rn<3>(rk, rj, a.box, wx, wy, wz);
+                        in = w2 < P.rc2;
+                    }
+                }
+                const unsigned mk = __ballot_sync(0xffffffffu, in);
+                if (qn + __popc(mk) > SW_QMAX) {   // full: evaluate what is queued
+                    sw_leg_terms(P, nd[w], qs[w], qw[w], qn, fx, fy, fz);
+                    qn = 0;
+                }
+                const int pos = qn + __popc(mk & lt);
+                if (in) {
+                    qs[w][pos] = (unsigned char)s;
+                    qw[w][pos] = make_float4(wx, wy, wz, sqrtf(w2));
+                }
+                qn += __popc(mk);
+                __syncwarp();
+            }
+            sw_leg_terms(P, nd[w], qs[w], qw[w], qn, fx, fy, fz);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
