@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--no-nhc", action="store_true", help="skip the Nose-Hoover NVT section")
     ap.add_argument("--no-flock", action="store_true", help="skip the flocking section")
     ap.add_argument("--no-gnn", action="store_true", help="skip the graph-network potential section")
+    ap.add_argument("--no-alu", action="store_true", help="skip the ALU rooflines of k_sw and the rebuild chain")
     return ap.parse_args()
 
 
@@ -278,15 +279,14 @@ def batched_section(steps=500):
         d.skin, d.dt, d.mass = 0.3, sp.dt, 1.0
         return d
 
-    b = P.Batch([desc(sp) for sp in specs], cap=128)
+    import tempfile
+    import paper_1912_04232_b300.batch_tune as BT
+    descs = [desc(sp) for sp in specs]
     r0 = torch.from_numpy(np.concatenate([s[0] for s in states])).to(dev)
     v0 = torch.from_numpy(np.concatenate([s[1] for s in states])).to(dev)
     r, v, f = r0.clone(), v0.clone(), torch.zeros_like(r0)
-    scratch = torch.empty((2 * b.plan.N, 4), dtype=torch.float32, device=dev)
-    import tempfile
-    tpp = P.md_batch_autotune(b.plan, r, v, f, scratch, 20, os.path.join(tempfile.gettempdir(), "jmd_batch_tune.json"))
 
-    def run_batch():
+    def run_batch(b):
         r.copy_(r0)
         v.copy_(v0)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -299,8 +299,23 @@ def batched_section(steps=500):
         e1.synchronize()
         return e0.elapsed_time(e1)
 
-    run_batch()
-    ms_b = min(run_batch() for _ in range(3))
+    def measure(b):
+        run_batch(b)
+        return min(run_batch(b) for _ in range(3))
+
+    # default plan (smallest cells, 4 threads per particle), then one
+    # threads-per-particle value for all (md_batch_autotune), then the
+    # per-size-class cell multipliers and threads per particle (batch_tune)
+    b = P.Batch(descs, cap=128)
+    ms_default = measure(b)
+    scratch = torch.empty((2 * b.plan.N, 4), dtype=torch.float32, device=dev)
+    tpp = P.md_batch_autotune(b.plan, r, v, f, scratch, 20, os.path.join(tempfile.gettempdir(), "jmd_batch_tune.json"))
+    ms_global = measure(b)
+    del b
+    tuned = BT.tune(descs, r0, v0, probe=20, cache_path=os.path.join(tempfile.gettempdir(), "jmd_batch_classes.json"))
+    b = P.Batch(BT.with_mults(descs, tuned["cell_mult"]), cap=128)
+    P.md_batch_set_class_tpp(b.plan, BT.tpp_per_replica(descs, tuned["tpp"]))
+    ms_b = measure(b)
     # one launch (graph) per replica, same tuning
     P.md_set_pair_tpp(tpp)
     singles = []
@@ -330,10 +345,111 @@ def batched_section(steps=500):
     P.md_set_pair_tpp(4)
     code = P.md_status_poll(st)
     Ntot = int(b.plan.N)
+    # ALU roofline of the one-launch step: every row entry is evaluated with
+    # the cutoff as a select (LJ/soft sphere with the nearest-image formula:
+    # 35 FLOP, FMA = 2), plus 24 FLOP of integration per particle-step;
+    # rebuild work is not counted, so the fraction is a lower bound
+    mean_cnt = float(b.cnt.float().clamp(max=128).mean().item())
+    flop_ps = 35.0 * mean_cnt + 24.0
+    pk, src = fp32_peak()
+    ach = flop_ps * Ntot * steps / (ms_b * 1e-3) / 1e12
     return {"replicas": len(specs), "N_total": Ntot, "steps": steps, "tpp_autotuned": tpp,
             "one_launch_particle_steps_per_s": Ntot * steps / (ms_b * 1e-3),
             "per_replica_launches_particle_steps_per_s": Ntot * steps / (ms_s * 1e-3),
-            "speedup": ms_s / ms_b, "status": code}
+            "speedup": ms_s / ms_b, "status": code,
+            "tuning": {"default_particle_steps_per_s": Ntot * steps / (ms_default * 1e-3),
+                       "global_tpp_particle_steps_per_s": Ntot * steps / (ms_global * 1e-3),
+                       "class_tuned_particle_steps_per_s": Ntot * steps / (ms_b * 1e-3),
+                       "classes_N": ["N < 512", "512 <= N < 2048", "N >= 2048"],
+                       "replicas_per_class": tuned["classes"], "cell_mult": tuned["cell_mult"],
+                       "tpp": tuned["tpp"], "tuner_cached": tuned["cached"],
+                       "tuned_over_default": ms_default / ms_b},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                         "flop_per_particle_step": flop_ps, "mean_row_entries": mean_cnt,
+                         "peak_source": src}}
+
+
+def alu_rooflines_section():
+    """The ALU-bound kernels against the measured FP32 FMA peak: algorithmic
+    FLOPs (the formulas' operations, FMA = 2, divide / sqrt / exp / pow = 1)
+    counted from the configuration, over the CUDA-event time of the launch.
+      k_sw (SW silicon, 64,000 atoms at 1000 K): 42 FLOP per ordered pair
+        inside a*sigma (distance 9, phi2 and phi2' 24, accumulation 9), 102
+        per triplet centred on the atom (the triplet 95, accumulation 7) and
+        107 per triplet in which the atom is a leg (second leg's distance 9,
+        the triplet 95, accumulation 3); with m_i partners of atom i inside
+        a*sigma: sum m_i pairs, sum m_i (m_i - 1) / 2 centred and
+        sum m_i (m_i - 1) leg triplets.
+      rebuild chain (LJ, 256,000 particles, the lattice start): 9 FLOP per
+        candidate test (difference 3, square and sum 5, compare 1), candidates
+        = sum over cells of (own particles x particles of the 27 stencil
+        cells); the time is the whole chain (binning, scan, scatter, cell
+        sort, build), of which k_build_cells is about 86%."""
+    import torch
+    import paper_1912_04232_b300 as P
+    import paper_1912_04232_b300.learned as LP
+    import workloads as W
+    dev = torch.device("cuda")
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    pk, src = fp32_peak()
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return statistics.median(ts)
+
+    out = {"peak_tflops": pk, "peak_source": src}
+    # k_sw
+    si = W.sw_silicon(20, T_K=1000.0, seed=0)
+    cap = 64
+    s = P.md_space_periodic(3, [si.L] * 3)
+    nl = P.NeighborList(s, si.N, LP.SW_RC, 0.3, cap)
+    r = torch.from_numpy(si.r).to(dev)
+    f = torch.zeros_like(r)
+    nl.build(r, st)
+    pot = P.sw_pot(LP.SW_SI)
+    t = timed(lambda: P.md_energy_forces(s, pot, r, nl.plan, f, None, st))
+    n = nl.cnt.clamp(max=cap).long()
+    rows = nl.nbr.long().clamp(max=si.N - 1)
+    d = r[rows, :3] - r[:, None, :3]
+    d -= float(si.L) * torch.round(d / float(si.L))
+    inside = (torch.arange(cap, device=dev)[None, :] < n[:, None]) & ((d * d).sum(-1) < LP.SW_RC ** 2)
+    m = inside.sum(1).double()
+    pairs, cent, legs = float(m.sum()), float((m * (m - 1) / 2).sum()), float((m * (m - 1)).sum())
+    fl = 42.0 * pairs + 102.0 * cent + 107.0 * legs
+    out["k_sw"] = {"N": si.N, "us": t * 1e6, "flops": fl, "pairs_per_atom": pairs / si.N,
+                   "triplets_per_atom": (cent + legs) / si.N,
+                   "roofline": {"bound": "alu", "achieved": fl / t / 1e12, "peak": pk, "unit": "TFLOP/s",
+                                "frac": fl / t / 1e12 / pk}}
+    # rebuild chain of the LJ list
+    c = W.lj_large(seed=0)
+    s = P.md_space_periodic(3, [c.L] * 3)
+    nl = P.NeighborList(s, c.N, c.r_cut, c.skin, 128)
+    r = torch.from_numpy(c.r).to(dev)
+    t = timed(lambda: nl.build(r, st))
+    nc = int(nl.plan.ncell[0])
+    idx = np.clip(np.floor(np.mod(c.r[:, :3].astype(np.float64), c.L) / (c.L / nc)).astype(np.int64), 0, nc - 1)
+    cnt = np.bincount((idx[:, 2] * nc + idx[:, 1]) * nc + idx[:, 0], minlength=nc ** 3).reshape(nc, nc, nc)
+    sten = np.zeros_like(cnt)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                sten += np.roll(cnt, (dz, dy, dx), axis=(0, 1, 2))
+    cand = float((cnt * sten).sum())
+    fl = 9.0 * cand
+    out["rebuild_chain_lj256k"] = {"N": c.N, "us": t * 1e6, "cells_per_axis": nc, "candidates_per_particle": cand / c.N,
+                                   "roofline": {"bound": "alu", "achieved": fl / t / 1e12, "peak": pk,
+                                                "unit": "TFLOP/s", "frac": fl / t / 1e12 / pk}}
+    out["status"] = P.md_status_poll(st)
+    return out
 
 
 def table1_section(steps=10000):
@@ -1093,6 +1209,8 @@ def main():
         extra["flocking"] = flock_section()
     if rank == 0 and not args.no_gnn:
         extra["gnn_nvt"] = gnn_section()
+    if rank == 0 and not args.no_alu:
+        extra["alu_rooflines"] = alu_rooflines_section()
 
     if rank == 0:
         line = {

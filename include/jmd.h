@@ -684,6 +684,10 @@ typedef struct {
     float eps, sigma, r_cut, e_shift;   /* LJ (as md_pot); soft: eps, r_cut = max diameter */
     float alpha;      /* soft-sphere exponent */
     float skin, dt, mass;
+    float cell_mult;  /* cell side >= cell_mult (r_cut + skin); values <= 1 mean 1 (the
+                         smallest cells).  Larger cells mean fewer, fuller cells per
+                         replica (a tuning knob, see md_batch_set_class_tpp); the rows
+                         hold the same partners, in another order. */
 } md_replica_desc;
 
 typedef struct {
@@ -727,6 +731,15 @@ JMD_API md_status md_batch_stats(const md_batch *bt, uint32_t *h_builds, md_stre
  * replica sizes and kinds.  Synchronous. */
 JMD_API md_status md_batch_autotune(md_batch *bt, float *d_r, float *d_v, float *d_f, void *d_scratch, int probe,
                                     const char *cache_path, int *tpp_out, md_stream_t stream);
+
+/* Threads per particle of the force kernel per replica: tpp_of_rep [R],
+ * each 4, 8 or 16 (host array).  The force step then runs one launch per
+ * distinct value over the particles of those replicas, listed in the
+ * workspace (synchronous upload on `stream`).  NULL returns to one launch
+ * with bt->tpp for all.  Each replica's arithmetic is that of the single-
+ * system path with its own threads per particle.  Needs a bound batch;
+ * MD_ERR_INVALID for other values. */
+JMD_API md_status md_batch_set_class_tpp(md_batch *bt, const int *tpp_of_rep, md_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Status and accounting                                                     */

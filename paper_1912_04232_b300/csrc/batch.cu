@@ -59,11 +59,19 @@ struct BatchDev {
     int N, R, C, cap, tpp;
     int wrapped;              // 1: positions inside [0, L) (the NVE loop wraps them), near-image form in the build
     uint32_t *status;
+    // per-replica threads per particle (md_batch_set_class_tpp): the
+    // particles grouped by their replica's value (4, 8, 16), counts per
+    // group; plist == NULL: one launch over all particles with tpp
+    const int32_t *plist;
+    int pgroup[3];
+    // the particle list of the launch in flight (NULL: particles 0..N-1)
+    const int32_t *pl;
+    int pn;
 };
 
 struct BatchLayout {
     size_t meta, rep_of, cell_rep, cell_count, cell_start, cell_of, rank, atoms_u, atoms, rsorted, flag, builds, ctl,
-        total;
+        plist, total;
 };
 
 static BatchLayout batch_layout(int N, int R, int C)
@@ -83,6 +91,7 @@ static BatchLayout batch_layout(int N, int R, int C)
     w.rsorted = o;    o = align256(o + sizeof(float4) * (size_t)N);
     w.flag = o;       o = align256(o + sizeof(uint32_t) * (size_t)R);
     w.builds = o;     o = align256(o + sizeof(uint32_t) * (size_t)R);
+    w.plist = o;      o = align256(o + sizeof(int32_t) * (size_t)N);
     w.total = o;
     return w;
 }
@@ -508,9 +517,11 @@ __global__ void __launch_bounds__(256) k_b_pair(BatchDev b, const float4 *r, flo
     constexpr int PPB = 256 / TPP;
     const int lg = threadIdx.x & (TPP - 1);
     const int gl = threadIdx.x / TPP;
-    for (int base = blockIdx.x * PPB; base < b.N; base += gridDim.x * PPB) {
-        int i = base + gl;
-        bool valid = i < b.N;
+    const int lim = b.pl ? b.pn : b.N;
+    for (int base = blockIdx.x * PPB; base < lim; base += gridDim.x * PPB) {
+        const int k = base + gl;
+        bool valid = k < lim;
+        int i = valid ? (b.pl ? __ldg(b.pl + k) : k) : b.N;
         float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
         const RepMeta *mp = nullptr;
         if (valid) {
@@ -612,6 +623,10 @@ struct BatchHost {
     const void *g_r = nullptr, *g_v = nullptr, *g_f = nullptr, *g_pe = nullptr, *g_ke = nullptr;
     int g_len = -1, g_tpp = 0;
     uint32_t *g_status = nullptr;
+    // per-replica threads per particle (md_batch_set_class_tpp)
+    bool classes = false;
+    int pgroup[3] = {0, 0, 0};   // particles with 4, 8, 16 threads each
+    unsigned class_version = 0, g_class_version = 0;
 };
 
 static BatchDev batch_dev(const md_batch *bt, uint32_t *status)
@@ -642,6 +657,11 @@ static BatchDev batch_dev(const md_batch *bt, uint32_t *status)
     b.cap = bt->cap;
     b.tpp = bt->tpp;
     b.status = status;
+    const BatchHost *H = (const BatchHost *)bt->host;
+    if (H && H->classes) {
+        b.plist = (const int32_t *)(p + w.plist);
+        for (int k = 0; k < 3; ++k) b.pgroup[k] = H->pgroup[k];
+    }
     return b;
 }
 
@@ -668,17 +688,39 @@ static void launch_b_pair(const BatchDev &b, const float4 *r, float4 *v, float4 
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_pair<TPP, KICK>, 256, 0);
         if (per_sm < 1) per_sm = 1;
     }
-    int groups = (int)(((long long)b.N * TPP + 255) / 256);
+    int groups = (int)(((long long)(b.pl ? b.pn : b.N) * TPP + 255) / 256);
     int g = per_sm * sms;
     k_b_pair<TPP, KICK><<<groups < g ? groups : g, 256, 0, st>>>(b, r, v, f);
 }
 
-static void enqueue_b_pair(const BatchDev &b, const float4 *r, float4 *v, float4 *f, int kick, cudaStream_t st)
+static void enqueue_b_pair_tpp(const BatchDev &b, int tpp, const float4 *r, float4 *v, float4 *f, int kick,
+                               cudaStream_t st)
 {
-    switch (b.tpp) {
+    switch (tpp) {
     case 8: kick ? launch_b_pair<8, 1>(b, r, v, f, st) : launch_b_pair<8, 0>(b, r, v, f, st); break;
     case 16: kick ? launch_b_pair<16, 1>(b, r, v, f, st) : launch_b_pair<16, 0>(b, r, v, f, st); break;
     default: kick ? launch_b_pair<4, 1>(b, r, v, f, st) : launch_b_pair<4, 0>(b, r, v, f, st); break;
+    }
+}
+
+// One launch with bt->tpp over all particles, or (per-replica threads per
+// particle) one launch per nonempty group of the particle list.
+static void enqueue_b_pair(const BatchDev &b0, const float4 *r, float4 *v, float4 *f, int kick, cudaStream_t st)
+{
+    if (!b0.plist) {
+        enqueue_b_pair_tpp(b0, b0.tpp, r, v, f, kick, st);
+        return;
+    }
+    const int tpps[3] = {4, 8, 16};
+    int off = 0;
+    for (int g = 0; g < 3; ++g) {
+        if (b0.pgroup[g] > 0) {
+            BatchDev b = b0;
+            b.pl = b0.plist + off;
+            b.pn = b0.pgroup[g];
+            enqueue_b_pair_tpp(b, tpps[g], r, v, f, kick, st);
+        }
+        off += b0.pgroup[g];
     }
 }
 
@@ -769,6 +811,16 @@ extern "C" md_status md_batch_plan(const md_replica_desc *reps, int R, int cap, 
         m.p0 = p;
         m.n = d.N;
         m.c0 = c;
+        if (d.cell_mult > 1.0f) {
+            // larger cells: side >= cell_mult r_list (the plan's margin kept)
+            nb.ncell_total = 1;
+            for (int a = 0; a < 3; ++a) {
+                int n = (int)floor(d.L / ((double)nb.r_list * (double)d.cell_mult * (1.0 + 1e-4)));
+                nb.ncell[a] = n < 1 ? 1 : n;
+                nb.cell_scale[a] = (float)((double)nb.ncell[a] / d.L);
+                nb.ncell_total *= nb.ncell[a];
+            }
+        }
         m.nct = nb.ncell_total;
         for (int a = 0; a < 3; ++a) {
             m.nc[a] = nb.ncell[a];
@@ -879,7 +931,8 @@ extern "C" md_status md_batch_run_nve(md_batch *bt, float *d_r, float *d_v, floa
     float4 *r = (float4 *)d_r, *v = (float4 *)d_v, *f = (float4 *)d_f;
     if (use_graph) {
         if (!H->exec || H->g_r != d_r || H->g_v != d_v || H->g_f != d_f || H->g_pe != d_PE || H->g_ke != d_KE ||
-            H->g_len != nsteps || H->g_tpp != bt->tpp || H->g_status != d_status) {
+            H->g_len != nsteps || H->g_tpp != bt->tpp || H->g_status != d_status ||
+            H->g_class_version != H->class_version) {
             md_status s = b_graph(*H, b, r, v, f, d_PE, d_KE, nsteps);
             if (s != MD_OK) return s;
             H->g_r = d_r;
@@ -890,6 +943,7 @@ extern "C" md_status md_batch_run_nve(md_batch *bt, float *d_r, float *d_v, floa
             H->g_len = nsteps;
             H->g_tpp = bt->tpp;
             H->g_status = d_status;
+            H->g_class_version = H->class_version;
         }
         k_b_loop_init<<<1, 1, 0, st>>>(b.ctl, (uint32_t)nsteps);
         JMD_CUDA_TRY(cudaGraphLaunch(H->exec, st));
@@ -904,6 +958,36 @@ extern "C" md_status md_batch_run_nve(md_batch *bt, float *d_r, float *d_v, floa
         }
     }
     JMD_CUDA_TRY(cudaGetLastError());
+    return MD_OK;
+}
+
+extern "C" md_status md_batch_set_class_tpp(md_batch *bt, const int *tpp_of_rep, md_stream_t stream)
+{
+    if (!bt || !bt->host || !bt->ws) return MD_ERR_INVALID;
+    BatchHost *H = (BatchHost *)bt->host;
+    ++H->class_version;
+    if (!tpp_of_rep) {
+        H->classes = false;
+        return MD_OK;
+    }
+    std::vector<int32_t> list;
+    list.reserve((size_t)bt->N);
+    const int tpps[3] = {4, 8, 16};
+    for (int k = 0; k < bt->R; ++k)
+        if (tpp_of_rep[k] != 4 && tpp_of_rep[k] != 8 && tpp_of_rep[k] != 16) return MD_ERR_INVALID;
+    for (int g = 0; g < 3; ++g) {
+        const size_t before = list.size();
+        for (int k = 0; k < bt->R; ++k)
+            if (tpp_of_rep[k] == tpps[g])
+                for (int i = 0; i < H->meta[k].n; ++i) list.push_back(H->meta[k].p0 + i);
+        H->pgroup[g] = (int)(list.size() - before);
+    }
+    BatchLayout w = batch_layout(bt->N, bt->R, bt->ncell_total);
+    cudaStream_t st = (cudaStream_t)stream;
+    JMD_CUDA_TRY(cudaMemcpyAsync((char *)bt->ws + w.plist, list.data(), sizeof(int32_t) * list.size(),
+                                 cudaMemcpyHostToDevice, st));
+    JMD_CUDA_TRY(cudaStreamSynchronize(st));
+    H->classes = true;
     return MD_OK;
 }
 

@@ -103,7 +103,7 @@ def flock_params(J_align=1.0, R_align=45.0, J_avoid=25.0, R_avoid=30.0, J_cohesi
 class md_replica_desc(C.Structure):
     _fields_ = [("N", C.c_int), ("L", C.c_double), ("kind", C.c_int), ("eps", C.c_float), ("sigma", C.c_float),
                 ("r_cut", C.c_float), ("e_shift", C.c_float), ("alpha", C.c_float), ("skin", C.c_float),
-                ("dt", C.c_float), ("mass", C.c_float)]
+                ("dt", C.c_float), ("mass", C.c_float), ("cell_mult", C.c_float)]
 
 
 class md_batch(C.Structure):
@@ -165,6 +165,7 @@ _SIGS = {
     "md_batch_run_nve": [_P(md_batch), _vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp, _vp],
     "md_batch_stats": [_P(md_batch), _P(C.c_uint32), _vp],
     "md_batch_autotune": [_P(md_batch), _vp, _vp, _vp, _vp, C.c_int, C.c_char_p, _P(C.c_int), _vp],
+    "md_batch_set_class_tpp": [_P(md_batch), _vp, _vp],
     "md_packing_space": [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _P(md_space), _P(C.c_double)],
     "md_minimize_adjoint": [_P(md_space), _P(md_pot), _P(md_nbr), _vp, C.c_int, C.c_float, C.c_float, C.c_double,
                             C.c_float, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -590,6 +591,16 @@ def md_batch_autotune(bt, r, v, f, scratch, probe, cache_path=None, stream=None)
                                   cache_path.encode() if cache_path else None, C.byref(t), _stream(stream)),
            "md_batch_autotune")
     return t.value
+
+
+def md_batch_set_class_tpp(bt, tpp_of_rep, stream=None):
+    """Threads per particle of the force kernel per replica (4, 8 or 16);
+    None returns to one launch with bt.tpp."""
+    if tpp_of_rep is None:
+        _check(_lib.md_batch_set_class_tpp(C.byref(bt), None, _stream(stream)), "md_batch_set_class_tpp")
+        return
+    arr = (C.c_int * len(tpp_of_rep))(*[int(t) for t in tpp_of_rep])
+    _check(_lib.md_batch_set_class_tpp(C.byref(bt), arr, _stream(stream)), "md_batch_set_class_tpp")
 
 
 class Batch:
