@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--no-flock", action="store_true", help="skip the flocking section")
     ap.add_argument("--no-gnn", action="store_true", help="skip the graph-network potential section")
     ap.add_argument("--no-alu", action="store_true", help="skip the ALU rooflines of k_sw and the rebuild chain")
+    ap.add_argument("--probe", default=None, choices=["learned-kernels", "train-step"],
+                    help="print the per-kernel timings of the learned potential's deployment (64,000 Si atoms) "
+                         "or of one BP training step (8 snapshots of 512 atoms) and exit")
     return ap.parse_args()
 
 
@@ -970,8 +973,100 @@ def whole_job_rate(n_particles, md_steps, steps, world, ms_max):
     return n_particles * md_steps * steps * world / (ms_max * 1e-3)
 
 
+def probe_learned_kernels():
+    """CUDA-event timings of the learned potential's kernels at 64,000 SW
+    silicon atoms (1000 K start): descriptors, the network (tcgen05 and
+    FP32), the force gather, a whole BP force evaluation, and SW forces."""
+    import torch
+    import paper_1912_04232_b300 as J
+    import paper_1912_04232_b300.learned as LP
+    import workloads as W
+    si = W.sw_silicon(20, T_K=1000.0, seed=0)
+    N, L = si.N, si.L
+    space = J.md_space_periodic(3, [L] * 3)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rng = np.random.default_rng(0)
+    params = torch.from_numpy((rng.normal(size=J.BP_NPARAMS) * 0.1).astype(np.float32)).cuda()
+    norm = torch.cat([torch.zeros(16), torch.ones(16)]).float().cuda()
+    model = J.BPModel(params, norm, N)
+    nl = J.NeighborList(space, N, LP.SW_RC, 0.3, 64)
+    r = torch.from_numpy(si.r).cuda()
+    nl.build(r, st)
+    G = torch.zeros((N, 16), device="cuda")
+    Ei = torch.zeros(N, device="cuda")
+    dEdG = torch.zeros((N, 16), device="cuda")
+    f = torch.zeros((N, 4), device="cuda")
+    sw = J.sw_pot(LP.SW_SI)
+
+    def t(fn, K=50):
+        for _ in range(5):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K * 1000
+
+    out = {"N": N, "us": {
+        "k_bp_desc": t(lambda: J.md_bp_descriptors(space, r, nl.plan, 0, G, st)),
+        "k_mlp_infer_tc": t(lambda: J.md_bp_mlp_infer_tc(params, norm, G, N, Ei, dEdG, st)),
+        "k_mlp_infer_fp32": t(lambda: J.md_bp_mlp_infer(params, norm, G, N, Ei, dEdG)),
+        "k_bp_force": t(lambda: J.md_bp_forces(space, r, nl.plan, 0, dEdG, Ei, f, None, st))}}
+    J.md_bp_set_tensor_cores(True)
+    out["us"]["bp_energy_forces_tc"] = t(lambda: J.md_energy_forces(space, model.pot, r, nl.plan, f, None, st))
+    J.md_bp_set_tensor_cores(False)
+    out["us"]["k_sw"] = t(lambda: J.md_energy_forces(space, sw, r, nl.plan, f, None, st))
+    out["status"] = J.md_status_poll(st)
+    print(json.dumps(out), flush=True)
+
+
+def probe_train_step():
+    """CUDA-event timings of one BP training step (8 snapshots of 512 SW
+    silicon atoms): forward, descriptor JVP, network gradient on the tensor
+    cores and in FP32, Adam."""
+    import torch
+    import paper_1912_04232_b300 as J
+    import paper_1912_04232_b300.learned as LP
+    ds = LP.generate_sw_dataset(np.linspace(500.0, 3000.0, 8), n_snap=4, stride=20, equil=100, seed=1)
+    LP.build_lists(ds)
+    tr = LP.Trainer(ds, batch=8, lr=3e-3, wF=1.0, seed=0)
+    for _ in range(5):
+        tr.step(0)
+    torch.cuda.synchronize()
+    n = ds.n
+    acc = {}
+    K = 50
+    for _ in range(K):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev[0].record()
+        nb, r, N = tr.forward(0, tr.B)
+        ev[1].record()
+        J.md_bp_jvp(tr.space, r, nb, n, tr.dF[:N], tr.V[:N], tr.status)
+        ev[2].record()
+        J.md_bp_mlp_train_tc(tr.params, tr.norm, tr.G[:N], tr.V[:N], tr.cE[:N], 1.0, N, tr.scratch, tr.grad,
+                             tr.status)
+        ev[3].record()
+        J.md_bp_mlp_train(tr.params, tr.norm, tr.G[:N], tr.V[:N], tr.cE[:N], 1.0, N, tr.scratch, tr.grad)
+        ev[4].record()
+        tr.step_count += 1
+        J.md_adam_step(tr.params, tr.grad, tr.m, tr.v, LP.N_PARAMS, tr.lr, 0.9, 0.999, 1e-8, tr.step_count)
+        ev[5].record()
+        torch.cuda.synchronize()
+        for k, name in enumerate(["forward", "jvp", "network_gradient_tc", "network_gradient_fp32", "adam"]):
+            acc[name] = acc.get(name, 0.0) + ev[k].elapsed_time(ev[k + 1]) * 1000 / K
+    print(json.dumps({"atoms": int(N), "us": acc, "status": J.md_status_poll(tr.status)}), flush=True)
+
+
 def main():
     args = parse()
+    if args.probe == "learned-kernels":
+        probe_learned_kernels()
+        return
+    if args.probe == "train-step":
+        probe_train_step()
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
