@@ -229,27 +229,35 @@ __device__ __forceinline__ void load16(const float *p, float e[16])
     }
 }
 
-// The queued triplets centred on neighbors: leg s of the atom's list
-// (u = r_j - r_k, so the leg from j to the atom is -u) and the other leg w'
-// from j; F -= sum_m e_jm dt(-u, w')/d(-u).
-__device__ __forceinline__ void bp_leg_terms(const BpArgs &a, const BpConst &c, const int *nj, const float4 *nd,
-                                             const unsigned char *qs, const float4 *qw, int qn, float &fx, float &fy,
-                                             float &fz)
+// The queued triplets: centred on atom k (legs s and t of its list;
+// F += sum_m e_km (dt/du + dt/dw)), or centred on neighbor j = s with k as a
+// leg (t == BP_LEG; the leg from j to k is -u, the other leg w' from j;
+// F -= sum_m e_jm dt(-u, w')/d(-u)).  One code path with selected
+// coefficients, so a warp's mixed queue runs without divergence.
+constexpr unsigned char BP_LEG = 0xff;
+__device__ __forceinline__ void bp_queue_terms(const BpArgs &a, const BpConst &c, int k, const int *nj,
+                                               const float4 *nd, const unsigned char *qs, const unsigned char *qk,
+                                               const float4 *qw, int qn, float &fx, float &fy, float &fz)
 {
     const int lane = threadIdx.x & 31;
     for (int q = lane; q < qn; q += 32) {
-        const int s = qs[q];
-        const float4 u = nd[s], wv = qw[q];
-        const float4 *ep = reinterpret_cast<const float4 *>(a.dEdG + (size_t)nj[s] * 16 + 8);
+        const int t = qk[q];
+        const bool leg = t == BP_LEG;
+        const float4 u = nd[qs[q]];
+        const float4 wv = leg ? qw[q] : nd[t];
+        const float sg = leg ? -1.0f : 1.0f;   // sign of the first leg and of its term
+        const float cw = leg ? 0.0f : 1.0f;    // the second leg's gradient counts for centred triplets only
+        const int src = leg ? nj[qs[q]] : k;   // whose dE/dG weights the term
+        const float4 *ep = reinterpret_cast<const float4 *>(a.dEdG + (size_t)src * 16 + 8);
         const float4 e0 = __ldg(ep), e1 = __ldg(ep + 1);
         const float ej[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
         float tt[8], du[8][3], dw[8][3];
-        angular8<true>(c, -u.x, -u.y, -u.z, u.w, wv.x, wv.y, wv.z, wv.w, tt, du, dw);
+        angular8<true>(c, sg * u.x, sg * u.y, sg * u.z, u.w, wv.x, wv.y, wv.z, wv.w, tt, du, dw);
 #pragma unroll
         for (int qq = 0; qq < 8; ++qq) {
-            fx -= ej[qq] * du[qq][0];
-            fy -= ej[qq] * du[qq][1];
-            fz -= ej[qq] * du[qq][2];
+            fx += ej[qq] * (sg * du[qq][0] + cw * dw[qq][0]);
+            fy += ej[qq] * (sg * du[qq][1] + cw * dw[qq][1]);
+            fz += ej[qq] * (sg * du[qq][2] + cw * dw[qq][2]);
         }
     }
     __syncwarp();
@@ -264,8 +272,9 @@ __global__ void __launch_bounds__(BP_WARPS * 32) k_bp_force(BpArgs a)
     __shared__ int nj[BP_WARPS][BP_MAXN];
     __shared__ float4 nd[BP_WARPS][BP_MAXN];
     __shared__ int qpre[BP_WARPS][BP_MAXN + 1];       // neighbors' row offsets in the candidate sweep
-    __shared__ unsigned char qs[BP_WARPS][BP_QMAX];   // queued triplets: leg
-    __shared__ float4 qw[BP_WARPS][BP_QMAX];          // ... and the other leg (w', |w'|)
+    __shared__ unsigned char qs[BP_WARPS][BP_QMAX];   // queued triplets: first leg
+    __shared__ unsigned char qk[BP_WARPS][BP_QMAX];   // ... second leg of a centred triplet, or BP_LEG
+    __shared__ float4 qw[BP_WARPS][BP_QMAX];          // ... and the other leg (w', |w'|) of a leg triplet
     const BpConst c = bp_const();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float pe_acc = 0.0f, ke_acc = 0.0f;
@@ -291,26 +300,32 @@ __global__ void __launch_bounds__(BP_WARPS * 32) k_bp_force(BpArgs a)
             fy += sc * u.y;
             fz += sc * u.z;
         }
-        // triplets centred on k: F_k += sum_m e_km (dt/du + dt/dw)
-        for (int t = lane; t < m * m; t += 32) {
-            int s1 = t / m, s2 = t - s1 * m;
-            if (s1 >= s2) continue;
-            float4 u = nd[w][s1], v = nd[w][s2];
-            float tt[8], du[8][3], dw[8][3];
-            angular8<true>(c, u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, tt, du, dw);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                fx += ek[8 + q] * (du[q][0] + dw[q][0]);
-                fy += ek[8 + q] * (du[q][1] + dw[q][1]);
-                fz += ek[8 + q] * (du[q][2] + dw[q][2]);
-            }
-        }
+        // triplets centred on k: F_k += sum_m e_km (dt/du + dt/dw), and
         // triplets centred on neighbor j with k as leg u' = r_k - r_j:
         // F_k -= sum_m e_jm dt(u', w')/du', w' = r_l - r_j, l in N(j), l != k.
-        // The candidates (s, l) of all neighbors' rows are swept 32 per
-        // step, those inside R_c queued (leg s, w'), and the queue is
-        // evaluated with every lane busy.
+        // Both kinds go into one shared-memory queue that is evaluated with
+        // every lane busy: the centred pairs (s1 < s2) first, then the leg
+        // candidates (s, l) of all neighbors' rows, swept 32 per step, those
+        // inside R_c queued with w'.
         {
+            int qn = 0;
+            for (int t0 = 0; t0 < m * m; t0 += 32) {
+                const int t = t0 + lane;
+                const int s1 = t / m, s2 = t - s1 * m;
+                const bool in = t < m * m && s1 < s2;
+                const unsigned mk = __ballot_sync(0xffffffffu, in);
+                if (qn + __popc(mk) > BP_QMAX) {
+                    bp_queue_terms(a, c, k, nj[w], nd[w], qs[w], qk[w], qw[w], qn, fx, fy, fz);
+                    qn = 0;
+                }
+                const int pos = qn + __popc(mk & ((1u << lane) - 1u));
+                if (in) {
+                    qs[w][pos] = (unsigned char)s1;
+                    qk[w][pos] = (unsigned char)s2;
+                }
+                qn += __popc(mk);
+                __syncwarp();
+            }
             int tot = 0;
             for (int s0 = 0; s0 < m; s0 += 32) {   // exclusive prefix of the neighbors' row lengths
                 const int s = s0 + lane;
@@ -330,7 +345,6 @@ __global__ void __launch_bounds__(BP_WARPS * 32) k_bp_force(BpArgs a)
             }
             if (lane == 0) qpre[w][m] = tot;
             __syncwarp();
-            int qn = 0;
             for (int b0 = 0; b0 < tot; b0 += 32) {
                 const int it = b0 + lane;
                 bool in = false;
@@ -355,18 +369,19 @@ __global__ void __launch_bounds__(BP_WARPS * 32) k_bp_force(BpArgs a)
                 }
                 const unsigned mk = __ballot_sync(0xffffffffu, in);
                 if (qn + __popc(mk) > BP_QMAX) {   // full: evaluate what is queued
-                    bp_leg_terms(a, c, nj[w], nd[w], qs[w], qw[w], qn, fx, fy, fz);
+                    bp_queue_terms(a, c, k, nj[w], nd[w], qs[w], qk[w], qw[w], qn, fx, fy, fz);
                     qn = 0;
                 }
                 const int pos = qn + __popc(mk & ((1u << lane) - 1u));
                 if (in) {
                     qs[w][pos] = (unsigned char)s;
+                    qk[w][pos] = BP_LEG;
                     qw[w][pos] = make_float4(wx, wy, wz, sqrtf(w2));
                 }
                 qn += __popc(mk);
                 __syncwarp();
             }
-            bp_leg_terms(a, c, nj[w], nd[w], qs[w], qw[w], qn, fx, fy, fz);
+            bp_queue_terms(a, c, k, nj[w], nd[w], qs[w], qk[w], qw[w], qn, fx, fy, fz);
         }
         fx = warp_sum(fx);
         fy = warp_sum(fy);

@@ -8,8 +8,9 @@
 //   (1) the two-body terms of every neighbor j,
 //   (2) the triplets centred on i (legs j < k of i's neighbors), and
 //   (3) the triplets centred on each neighbor j in which i is a leg
-//       (the other leg k runs over j's row; the candidates inside a*sigma
-//       are queued first and then evaluated with every lane busy).
+//       (the other leg k runs over j's row); the triplets of (2) and the
+//       candidates of (3) inside a*sigma are queued in shared memory first
+//       and then evaluated together with every lane busy.
 // e_i = 1/2 sum_j phi2(r_ij) + sum_{j<k} phi3(i; j, k), so sum_i e_i = E.
 #include "common.cuh"
 #include "kernels.cuh"
@@ -90,20 +91,30 @@ __device__ __forceinline__ float sw_triplet(const SwP &P, float ux, float uy, fl
     return h;
 }
 
-// The queued triplets centred on neighbors: leg s of the atom's list
-// (u = r_j - r_i, so the leg from j to the atom is -u) and the other leg w'
-// from j; F -= dh(-u, w')/d(-u).
-__device__ __forceinline__ void sw_leg_terms(const SwP &P, const float4 *nd, const unsigned char *qs, const float4 *qw,
-                                             int qn, float &fx, float &fy, float &fz)
+// The queued triplets: centred on the atom (legs s and k of its list:
+// F += dh/du + dh/dw, e += h), or centred on neighbor s with the atom as a
+// leg (k == SW_LEG; the leg from s to the atom is -u, the other leg w' from
+// s: F -= dh(-u, w')/d(-u)).  One code path with selected coefficients, so
+// a warp's mixed queue runs without divergence.
+constexpr unsigned char SW_LEG = 0xff;
+__device__ __forceinline__ void sw_queue_terms(const SwP &P, const float4 *nd, const unsigned char *qs,
+                                               const unsigned char *qk, const float4 *qw, int qn, float &fx,
+                                               float &fy, float &fz, float &e)
 {
     const int lane = threadIdx.x & 31;
     for (int q = lane; q < qn; q += 32) {
-        const float4 u = nd[qs[q]], wv = qw[q];
+        const int k = qk[q];
+        const bool leg = k == SW_LEG;
+        const float4 a = nd[qs[q]];
+        const float4 b = leg ? qw[q] : nd[k];
+        const float sg = leg ? -1.0f : 1.0f;
         float gu[3], gw[3];
-        sw_triplet(P, -u.x, -u.y, -u.z, u.w, wv.x, wv.y, wv.z, wv.w, gu, gw);
-        fx -= gu[0];
-        fy -= gu[1];
-        fz -= gu[2];
+        const float h = sw_triplet(P, sg * a.x, sg * a.y, sg * a.z, a.w, b.x, b.y, b.z, b.w, gu, gw);
+        const float cw = leg ? 0.0f : 1.0f;
+        fx += sg * gu[0] + cw * gw[0];
+        fy += sg * gu[1] + cw * gw[1];
+        fz += sg * gu[2] + cw * gw[2];
+        e += cw * h;
     }
     __syncwarp();
 }
@@ -117,8 +128,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_sw(PairArgs a)
     __shared__ int nj[SW_WARPS][SW_MAXN];
     __shared__ float4 nd[SW_WARPS][SW_MAXN];   // (ux, uy, uz, r): u = r_j - r_i
     __shared__ int qpre[SW_WARPS][SW_MAXN + 1];       // neighbors' row offsets in the candidate sweep
-    __shared__ unsigned char qs[SW_WARPS][SW_QMAX];   // queued triplets: leg
-    __shared__ float4 qw[SW_WARPS][SW_QMAX];          // ... and the other leg (w', |w'|)
+    __shared__ unsigned char qs[SW_WARPS][SW_QMAX];   // queued triplets: first leg
+    __shared__ unsigned char qk[SW_WARPS][SW_QMAX];   // ... second leg of a centred triplet, or SW_LEG
+    __shared__ float4 qw[SW_WARPS][SW_QMAX];          // ... and the other leg (w', |w'|) of a leg triplet
     const SwP P = sw_params(a);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -166,24 +178,32 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_sw(PairArgs a)
             fz += fr * u.z;
             e += 0.5f * ph;
         }
-        // (2) triplets centred on i: F_i += dh/du + dh/dw
-        for (int t = lane; t < m * m; t += 32) {
-            int s1 = t / m, s2 = t - s1 * m;
-            if (s1 >= s2) continue;
-            float4 u = nd[w][s1], v = nd[w][s2];
-            float gu[3], gw[3];
-            float h = sw_triplet(P, u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, gu, gw);
-            fx += gu[0] + gw[0];
-            fy += gu[1] + gw[1];
-            fz += gu[2] + gw[2];
-            e += h;
-        }
+        // (2) triplets centred on i: F_i += dh/du + dh/dw, e += h, and
         // (3) triplets centred on neighbor j with i as a leg:
         //     u' = r_i - r_j = -u, w' = r_k - r_j; F_i -= dh/du'.
-        //     The candidates (s, k) of all neighbors' rows are swept 32 per
-        //     step, those inside a*sigma queued (leg s, w'), and the queue
-        //     is evaluated with every lane busy.
+        // Both kinds go into one shared-memory queue that is evaluated with
+        // every lane busy: the centred pairs (s1 < s2) first, then the leg
+        // candidates (s, k) of all neighbors' rows, swept 32 per step, those
+        // inside a*sigma queued with w'.
         {
+            int qn = 0;
+            for (int t0 = 0; t0 < m * m; t0 += 32) {
+                const int t = t0 + lane;
+                const int s1 = t / m, s2 = t - s1 * m;
+                const bool in = t < m * m && s1 < s2;
+                const unsigned mk = __ballot_sync(0xffffffffu, in);
+                if (qn + __popc(mk) > SW_QMAX) {
+                    sw_queue_terms(P, nd[w], qs[w], qk[w], qw[w], qn, fx, fy, fz, e);
+                    qn = 0;
+                }
+                const int pos = qn + __popc(mk & lt);
+                if (in) {
+                    qs[w][pos] = (unsigned char)s1;
+                    qk[w][pos] = (unsigned char)s2;
+                }
+                qn += __popc(mk);
+                __syncwarp();
+            }
             int tot = 0;
             for (int s0 = 0; s0 < m; s0 += 32) {   // exclusive prefix of the neighbors' row lengths
                 const int s = s0 + lane;
@@ -203,7 +223,6 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_sw(PairArgs a)
             }
             if (lane == 0) qpre[w][m] = tot;
             __syncwarp();
-            int qn = 0;
             for (int b0 = 0; b0 < tot; b0 += 32) {
                 const int it = b0 + lane;
                 bool in = false;
@@ -227,18 +246,19 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_sw(PairArgs a)
                 }
                 const unsigned mk = __ballot_sync(0xffffffffu, in);
                 if (qn + __popc(mk) > SW_QMAX) {   // full: evaluate what is queued
-                    sw_leg_terms(P, nd[w], qs[w], qw[w], qn, fx, fy, fz);
+                    sw_queue_terms(P, nd[w], qs[w], qk[w], qw[w], qn, fx, fy, fz, e);
                     qn = 0;
                 }
                 const int pos = qn + __popc(mk & lt);
                 if (in) {
                     qs[w][pos] = (unsigned char)s;
+                    qk[w][pos] = SW_LEG;
                     qw[w][pos] = make_float4(wx, wy, wz, sqrtf(w2));
                 }
                 qn += __popc(mk);
                 __syncwarp();
             }
-            sw_leg_terms(P, nd[w], qs[w], qw[w], qn, fx, fy, fz);
+            sw_queue_terms(P, nd[w], qs[w], qk[w], qw[w], qn, fx, fy, fz, e);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
