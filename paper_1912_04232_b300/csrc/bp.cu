@@ -129,6 +129,49 @@ __device__ __forceinline__ void angular8(const BpConst &c, float ux, float uy, f
     }
 }
 
+// The angular terms' gradients contracted with a weight per column:
+// g_u = sum_col e_col dt_col/du and g_w = sum_col e_col dt_col/dw for the
+// triplet with legs u, w (|u|, |w| < R_c).  Each column is
+// t = 2^(1-z) (1 + l cos)^z B with B = exp(-eta_a (|u|^2 + |w|^2)) f_c f_c, so
+// dt/du = (dt/dcos) dcos/du + (dt/dB) dB/du and the sums over columns fold
+// into two scalars, sum e dt/dcos and sum e dt/dB, before the vectors.
+__device__ __forceinline__ void angular_grad(const BpConst &c, float ux, float uy, float uz, float ru, float wx,
+                                             float wy, float wz, float rw, const float e[8], float gu[3], float gw[3])
+{
+    const float iu = 1.0f / ru, iw = 1.0f / rw;
+    const float cs = (ux * wx + uy * wy + uz * wz) * iu * iw;
+    float fu, dfu, fw, dfw;
+    fcut(c, ru, fu, dfu);
+    fcut(c, rw, fw, dfw);
+    const float ex = __expf(-c.eta_a * (ru * ru + rw * rw));
+    const float B = ex * fu * fw;
+    const float bu = -2.0f * c.eta_a * B + ex * dfu * fw * iu;   // dB/du = bu u
+    const float bw = -2.0f * c.eta_a * B + ex * fu * dfw * iw;   // dB/dw = bw w
+    const float zs[4] = {1.0f, 2.0f, 4.0f, 16.0f};
+    const float pref[4] = {1.0f, 0.5f, 0.125f, 1.0f / 32768.0f};   // 2^(1 - z)
+    float A = 0.0f, Bs = 0.0f;   // sum e dt/dcos, sum e dt/dB
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const float lam = l == 0 ? 1.0f : -1.0f;
+        float pz[4], pzm1[4];
+        powers(1.0f + lam * cs, pz, pzm1);
+#pragma unroll
+        for (int zi = 0; zi < 4; ++zi) {
+            const float ec = e[2 * zi + l];
+            A += ec * pref[zi] * zs[zi] * pzm1[zi] * lam;
+            Bs += ec * pref[zi] * pz[zi];
+        }
+    }
+    A *= B;
+    const float iuw = iu * iw;
+    gu[0] = A * (wx * iuw - cs * ux * iu * iu) + Bs * bu * ux;
+    gu[1] = A * (wy * iuw - cs * uy * iu * iu) + Bs * bu * uy;
+    gu[2] = A * (wz * iuw - cs * uz * iu * iu) + Bs * bu * uz;
+    gw[0] = A * (ux * iuw - cs * wx * iw * iw) + Bs * bw * wx;
+    gw[1] = A * (uy * iuw - cs * wy * iw * iw) + Bs * bw * wy;
+    gw[2] = A * (uz * iuw - cs * wz * iw * iw) + Bs * bw * wz;
+}
+
 // Neighbors of atom i inside R_c into the warp's shared list
 // (j, u = r_j - r_i, |u|); returns the count (clamped, overflow flagged).
 __device__ __forceinline__ int gather_within(const BpArgs &a, const BpConst &c, int i, const float4 &ri, int *nj,
@@ -251,14 +294,11 @@ __device__ __forceinline__ void bp_queue_terms(const BpArgs &a, const BpConst &c
         const float4 *ep = reinterpret_cast<const float4 *>(a.dEdG + (size_t)src * 16 + 8);
         const float4 e0 = __ldg(ep), e1 = __ldg(ep + 1);
         const float ej[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
-        float tt[8], du[8][3], dw[8][3];
-        angular8<true>(c, sg * u.x, sg * u.y, sg * u.z, u.w, wv.x, wv.y, wv.z, wv.w, tt, du, dw);
-#pragma unroll
-        for (int qq = 0; qq < 8; ++qq) {
-            fx += ej[qq] * (sg * du[qq][0] + cw * dw[qq][0]);
-            fy += ej[qq] * (sg * du[qq][1] + cw * dw[qq][1]);
-            fz += ej[qq] * (sg * du[qq][2] + cw * dw[qq][2]);
-        }
+        float gu[3], gw[3];
+        angular_grad(c, sg * u.x, sg * u.y, sg * u.z, u.w, wv.x, wv.y, wv.z, wv.w, ej, gu, gw);
+        fx += sg * gu[0] + cw * gw[0];
+        fy += sg * gu[1] + cw * gw[1];
+        fz += sg * gu[2] + cw * gw[2];
     }
     __syncwarp();
 }
