@@ -172,6 +172,42 @@ __device__ __forceinline__ void angular_grad(const BpConst &c, float ux, float u
     gw[2] = A * (uz * iuw - cs * wz * iw * iw) + Bs * bw * wz;
 }
 
+// The angular terms' directional derivatives: out[col] += dt_col/du . a +
+// dt_col/dw . b for the triplet with legs u, w.  With dt/du = (dt/dcos)
+// dcos/du + (dt/dB) dB/du, the vector parts are the same for all columns, so
+// they reduce to two scalars first: X = dcos/du . a + dcos/dw . b and
+// Y = dB/du . a + dB/dw . b.
+__device__ __forceinline__ void angular_dir(const BpConst &c, float ux, float uy, float uz, float ru, float wx,
+                                            float wy, float wz, float rw, float ax, float ay, float az, float bx,
+                                            float by, float bz, float *out)
+{
+    const float iu = 1.0f / ru, iw = 1.0f / rw;
+    const float cs = (ux * wx + uy * wy + uz * wz) * iu * iw;
+    float fu, dfu, fw, dfw;
+    fcut(c, ru, fu, dfu);
+    fcut(c, rw, fw, dfw);
+    const float ex = __expf(-c.eta_a * (ru * ru + rw * rw));
+    const float B = ex * fu * fw;
+    const float bu = -2.0f * c.eta_a * B + ex * dfu * fw * iu;
+    const float bw = -2.0f * c.eta_a * B + ex * fu * dfw * iw;
+    const float iuw = iu * iw;
+    const float ua = ux * ax + uy * ay + uz * az, ub = ux * bx + uy * by + uz * bz;
+    const float wa = wx * ax + wy * ay + wz * az, wb = wx * bx + wy * by + wz * bz;
+    const float X = (wa * iuw - cs * ua * iu * iu) + (ub * iuw - cs * wb * iw * iw);
+    const float Y = bu * ua + bw * wb;
+    const float zs[4] = {1.0f, 2.0f, 4.0f, 16.0f};
+    const float pref[4] = {1.0f, 0.5f, 0.125f, 1.0f / 32768.0f};   // 2^(1 - z)
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const float lam = l == 0 ? 1.0f : -1.0f;
+        float pz[4], pzm1[4];
+        powers(1.0f + lam * cs, pz, pzm1);
+#pragma unroll
+        for (int zi = 0; zi < 4; ++zi)
+            out[2 * zi + l] += pref[zi] * zs[zi] * pzm1[zi] * lam * B * X + pref[zi] * pz[zi] * Y;
+    }
+}
+
 // Neighbors of atom i inside R_c into the warp's shared list
 // (j, u = r_j - r_i, |u|); returns the count (clamped, overflow flagged).
 __device__ __forceinline__ int gather_within(const BpArgs &a, const BpConst &c, int i, const float4 &ri, int *nj,
@@ -476,12 +512,7 @@ __global__ void __launch_bounds__(BP_WARPS * 32) k_bp_jvp(BpArgs a)
             float4 dFj = a.dF[nj[w][s1]], dFl = a.dF[nj[w][s2]];
             float ax = dFj.x - dFi.x, ay = dFj.y - dFi.y, az = dFj.z - dFi.z;
             float bx = dFl.x - dFi.x, by = dFl.y - dFi.y, bz = dFl.z - dFi.z;
-            float tt[8], du[8][3], dw[8][3];
-            angular8<true>(c, u.x, u.y, u.z, u.w, vv.x, vv.y, vv.z, vv.w, tt, du, dw);
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                v[8 + q] += du[q][0] * ax + du[q][1] * ay + du[q][2] * az + dw[q][0] * bx + dw[q][1] * by +
-                            dw[q][2] * bz;
+            angular_dir(c, u.x, u.y, u.z, u.w, vv.x, vv.y, vv.z, vv.w, ax, ay, az, bx, by, bz, v + 8);
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) v[q] = warp_sum(v[q]);
