@@ -202,7 +202,7 @@ def learned_section():
     t_train = time.perf_counter() - t0
     # one training step (forward, loss, descriptor JVP, network gradient,
     # Adam) on each network path, from the same start, CUDA events
-    step_ms = {}
+    step_ms, epoch_ms = {}, {}
     for name, tc in (("tcgen05_bf16", True), ("fp32", False)):
         tt = LP.Trainer(ds, batch=8, lr=3e-3, wF=1.0, seed=0, tensor_cores=tc)
         for _ in range(3):
@@ -214,7 +214,13 @@ def learned_section():
         e1.record()
         torch.cuda.synchronize()
         step_ms[name] = e0.elapsed_time(e1) / 20
+        e0.record()
+        tt.train(0, ntr, epochs=1, seed=1)
+        e1.record()
+        torch.cuda.synchronize()
+        epoch_ms[name] = e0.elapsed_time(e1)
     dep = LP.deploy_compare(tr.params, tr.norm, n_side=20, T=1000.0, steps=200, warmup=20)
+    kernels = learned_kernels(tr.params, tr.norm)
     # the graph network on the same data (trained by md_gnn_train_grad + Adam),
     # the training snapshots under 8 symmetry operations of the cubic box each
     t1 = time.perf_counter()
@@ -235,9 +241,13 @@ def learned_section():
         "force_rmse_eV_per_A_heldout": f_rmse, "energy_rmse_eV_per_atom_heldout": e_rmse,
         "force_rmse_sw_two_body_only": two, "force_rmse_vs_sw_at_deploy": dep["force_rmse_vs_sw_final_eV_per_A"],
         "deploy": {"N": dep["N"], "T_K": 1000.0, "steps": 200, "dt_fs": 1.0, "network": "tcgen05 BF16"},
+        "kernels_64000": {"us": kernels["us"], "roofline": kernels["roofline"],
+                          "pairs_per_atom": kernels["pairs_per_atom"],
+                          "triplets_per_atom": kernels["triplets_per_atom"]},
         "train": {"snapshots": int(S), "heldout": int(S - ntr), "epochs": 40, "seconds_incl_data": t_train,
                   "seconds_data": t_data, "seconds_fit": t_fit, "network": "tcgen05 BF16 (md_bp_mlp_train_tc)",
                   "step_ms": step_ms, "step_speedup_tc_over_fp32": step_ms["fp32"] / step_ms["tcgen05_bf16"],
+                  "epoch_ms": epoch_ms, "steps_per_epoch": ntr // 8,
                   "atoms_per_step": 8 * int(ds.n)},
         "gnn": {"force_rmse_eV_per_A_heldout": g_f, "energy_rmse_eV_per_atom_heldout": g_e,
                 "force_rmse_untrained": g_untrained[1], "epochs": 50, "augmentation": "8 cubic symmetry copies",
@@ -973,10 +983,19 @@ def whole_job_rate(n_particles, md_steps, steps, world, ms_max):
     return n_particles * md_steps * steps * world / (ms_max * 1e-3)
 
 
-def probe_learned_kernels():
+def learned_kernels(params=None, norm=None):
     """CUDA-event timings of the learned potential's kernels at 64,000 SW
     silicon atoms (1000 K start): descriptors, the network (tcgen05 and
-    FP32), the force gather, a whole BP force evaluation, and SW forces."""
+    FP32), the force gather, a whole BP force evaluation, and SW forces; and
+    each kernel's fraction of its roofline.  FLOPs (FMA = 2; exp, sin/cos,
+    divide = 1): the network 2 (16x64 + 64x64 + 64x64 + 64x16) = 20,480 per
+    atom on the tensor cores (BF16 peak of MEASURED_PEAKS.json); the
+    descriptors 44 per pair inside R_c (cutoff 4, eight Gaussians 40) and 50
+    per centred triplet (legs and cosine 9, cutoffs and exponential 10, the
+    powers 12, eight columns 16, sums 3); the force gather 90 per pair (both
+    atoms' weights, radial derivative) and 110 per triplet, centred or as a
+    leg (the triplet's scalars 50, the weight sums 32, the two leg gradients
+    28), against the measured FP32 peak."""
     import torch
     import paper_1912_04232_b300 as J
     import paper_1912_04232_b300.learned as LP
@@ -985,9 +1004,10 @@ def probe_learned_kernels():
     N, L = si.N, si.L
     space = J.md_space_periodic(3, [L] * 3)
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    rng = np.random.default_rng(0)
-    params = torch.from_numpy((rng.normal(size=J.BP_NPARAMS) * 0.1).astype(np.float32)).cuda()
-    norm = torch.cat([torch.zeros(16), torch.ones(16)]).float().cuda()
+    if params is None:
+        rng = np.random.default_rng(0)
+        params = torch.from_numpy((rng.normal(size=J.BP_NPARAMS) * 0.1).astype(np.float32)).cuda()
+        norm = torch.cat([torch.zeros(16), torch.ones(16)]).float().cuda()
     model = J.BPModel(params, norm, N)
     nl = J.NeighborList(space, N, LP.SW_RC, 0.3, 64)
     r = torch.from_numpy(si.r).cuda()
@@ -1018,8 +1038,37 @@ def probe_learned_kernels():
     out["us"]["bp_energy_forces_tc"] = t(lambda: J.md_energy_forces(space, model.pot, r, nl.plan, f, None, st))
     J.md_bp_set_tensor_cores(False)
     out["us"]["k_sw"] = t(lambda: J.md_energy_forces(space, sw, r, nl.plan, f, None, st))
+    # partners inside R_c per atom, for the FLOP counts
+    cap = nl.cap
+    n = nl.cnt.clamp(max=cap).long()
+    rows = nl.nbr.long().clamp(max=N - 1)
+    d = r[rows, :3] - r[:, None, :3]
+    d -= float(L) * torch.round(d / float(L))
+    inside = (torch.arange(cap, device="cuda")[None, :] < n[:, None]) & ((d * d).sum(-1) < LP.BP_RC ** 2)
+    m = inside.sum(1).double()
+    pairs, cent, legs = float(m.sum()), float((m * (m - 1) / 2).sum()), float((m * (m - 1)).sum())
+    fp32_pk, _ = fp32_peak()
+    try:
+        bf16_pk = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        bf16_pk = 1800.0
+    us = out["us"]
+    fl = {"k_bp_desc": 44.0 * pairs + 50.0 * cent, "k_mlp_infer_tc": 20480.0 * N,
+          "k_bp_force": 90.0 * pairs + 110.0 * (cent + legs)}
+    pk = {"k_bp_desc": fp32_pk, "k_mlp_infer_tc": bf16_pk, "k_bp_force": fp32_pk}
+    out["roofline"] = {k: {"bound": "tensor" if k == "k_mlp_infer_tc" else "alu",
+                           "achieved_tflops": fl[k] / (us[k] * 1e-6) / 1e12, "peak_tflops": pk[k],
+                           "frac": fl[k] / (us[k] * 1e-6) / 1e12 / pk[k],
+                           "share_of_evaluation": us[k] / (us["k_bp_desc"] + us["k_mlp_infer_tc"] + us["k_bp_force"])}
+                       for k in fl}
+    out["pairs_per_atom"] = pairs / N
+    out["triplets_per_atom"] = {"centred": cent / N, "leg": legs / N}
     out["status"] = J.md_status_poll(st)
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def probe_learned_kernels():
+    print(json.dumps(learned_kernels()), flush=True)
 
 
 def probe_train_step():

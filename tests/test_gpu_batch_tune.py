@@ -1,13 +1,16 @@
 """GPU: the batched engine's tuning knobs change nothing but the time --
 per-class cell multipliers and threads per particle give the same rows (as
 sets), forces and energies to rounding, and the same trajectories to
-rounding; the autotuner returns a configuration no slower than the default
-and caches it."""
+rounding; per-class launches with the default threads per particle give the
+default's bits; a tuned configuration matches the FP64 oracle; the
+autotuner returns a configuration no slower than the default and caches
+it."""
 import numpy as np
 import pytest
 
+import oracle as O
 import workloads as W
-from gpu_helpers import dev, status_word, to_dev
+from gpu_helpers import dev, force_error, status_word, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -124,3 +127,61 @@ def test_autotuner_picks_and_caches(P, tmp_path):
     assert all(m in T.MULTS for m in res["cell_mult"]) and all(t in T.TPPS for t in res["tpp"])
     again = T.tune(descs, r0, v0, probe=10, cache_path=path)
     assert again["cached"] and again["cell_mult"] == res["cell_mult"] and again["tpp"] == res["tpp"]
+
+
+def _run(P, descs, r0, v0, mult, tpp, steps):
+    import torch
+    import paper_1912_04232_b300.batch_tune as T
+    b = P.Batch(T.with_mults(descs, mult), cap=CAP)
+    if tpp is not None:
+        P.md_batch_set_class_tpp(b.plan, T.tpp_per_replica(descs, tpp))
+    r, v = r0.clone(), v0.clone()
+    f = torch.zeros_like(r)
+    st = status_word()
+    P.md_batch_build(b.plan, r, st)
+    P.md_batch_forces(b.plan, r, f, st)
+    f0 = f.cpu().numpy()
+    if steps:
+        P.md_batch_run_nve(b.plan, r, v, f, steps, None, None, True, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    return f0, r.cpu().numpy(), v.cpu().numpy()
+
+
+def test_class_launches_with_default_threads_are_bitwise_default(P):
+    # the per-class force launches (grouped particle list) with 4 threads
+    # per particle everywhere: the same arithmetic per particle as the one
+    # launch, so the same bits after 20 steps
+    specs = [sp for sp in W.replica_plan(R=64, n_max=4096, seed=6) if sp.kind == "lj"]
+    descs = [_desc(P, sp) for sp in specs]
+    r0, v0 = _state(specs)
+    a = _run(P, descs, r0, v0, [1.0, 1.0, 1.0], None, 20)
+    b = _run(P, descs, r0, v0, [1.0, 1.0, 1.0], [4, 4, 4], 20)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_tuned_configuration_matches_oracle(P):
+    # larger cells and other threads per particle on every class: forces of
+    # sampled replicas after the build, and 20-step trajectories of two LJ
+    # replicas, against the FP64 oracle
+    import paper_1912_04232_b300.batch_tune as T
+    specs = [sp for sp in W.replica_plan(R=64, n_max=4096, seed=7) if sp.kind == "lj"]
+    descs = [_desc(P, sp) for sp in specs]
+    states = [W.replica_initial(sp) for sp in specs]
+    import torch
+    r0 = to_dev(np.concatenate([s[0] for s in states]), torch.float32)
+    v0 = to_dev(np.concatenate([s[1] for s in states]), torch.float32)
+    f0, rg, vg = _run(P, descs, r0, v0, [2.0, 1.5, 2.0], [16, 8, 4], 20)
+    offs = np.concatenate([[0], np.cumsum([sp.N for sp in specs])])
+    order = sorted(range(len(specs)), key=lambda k: specs[k].N)
+    for k in (order[0], order[len(order) // 2], order[-1]):
+        sp, (r, v) = specs[k], states[k]
+        a, z = offs[k], offs[k + 1]
+        U, F, e = O.lj(r, sp.L)
+        assert force_error(f0[a:z], F) <= 1e-4, (k, sp.N)
+        ro, vo, _, _ = O.nve(r, v, sp.L, "lj", dt=sp.dt, nsteps=20)
+        d = rg[a:z, :3] - ro
+        d -= sp.L * np.round(d / sp.L)
+        assert np.abs(d).max() < 2e-4, (k, sp.N)
+        assert np.abs(vg[a:z, :3] - vo).max() < 2e-3, (k, sp.N)
