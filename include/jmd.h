@@ -141,10 +141,12 @@ typedef struct {
  * copies from across the box are staged at their periodic image, so a
  * partner's nearest-image vector is the plain difference; between rebuilds
  * positions are not wrapped, so those images stay valid, and they are
- * wrapped at every rebuild and on return.  Membership and the
- * cutoff are decided by the FP32 formula above, so the pair sets are the
- * same as the int32 rows'.  On return md_integrate_nve writes r, v, f, the
- * int32 rows, counts and build positions back in the caller's order.
+ * wrapped at every rebuild and on return.  Membership is decided on those
+ * staged positions (r^2 with FMAs, strict < r_list^2), so the pair sets
+ * equal the int32 rows' except for pairs within an ulp of r_list; the
+ * step's cutoff test takes the same form.  On return md_integrate_nve
+ * writes r, v, f, the int32 rows, counts and build positions back in the
+ * caller's order.
  * Needs dim = 3, at least 3 cells on every axis, r_cut > skin and cap a
  * multiple of 8; a region
  * holds at most about 1.25x its mean count plus 128 particles (denser

@@ -655,16 +655,15 @@ __global__ void __launch_bounds__(TT) k_t_place(TileArgs a)
 // padded with the sentinel index (reg_cap, a far-away position the step
 // kernels place after the region) up to the warp's longest row rounded up
 // to 8, so that the step's thread-per-particle loop, whose warps are these
-// warps, runs without masks.  BND: some particle of the warp has a window
-// across the boundary, so the nearest image takes the comparison form
-// (positions are inside [0, L) at a build).  Needs cap % 8 == 0.
-template <bool BND>
+// warps, runs without masks.  The region is staged with its copies at their
+// periodic image, so a partner is decided on the plain difference of staged
+// positions: r^2 = dz^2 + (dy^2 + dx^2) with FMAs, strict < r_list^2.  This
+// rounds differently from the nearest-image formula of the int32 build only
+// for pairs within an ulp of r_list.  Needs cap % 8 == 0.
 __device__ __forceinline__ int build_thread(const TileArgs &a, const TGeo &g, const TileSm &sm, const float4 *cand,
                                             int k, int loc, int slot, bool valid)
 {
-    const float L0 = a.box.L[0], L1 = a.box.L[1], L2 = a.box.L[2];
-    const float I0 = a.box.Linv[0], I1 = a.box.Linv[1], I2 = a.box.Linv[2];
-    const float wx = L0 / (float)a.H[0], wy = L1 / (float)a.H[1], wz = L2 / (float)a.H[2];
+    const float wx = a.box.L[0] / (float)a.H[0], wy = a.box.L[1] / (float)a.H[1], wz = a.box.L[2] / (float)a.H[2];
     const float lim2 = a.r_list2 * 1.0002f + 1e-4f;
     const float4 ri = valid ? cand[loc] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int xl = 2 + k % g.nx, yl = 2 + (k / g.nx) % g.ny, zl = 2 + k / (g.nx * g.ny);
@@ -699,14 +698,8 @@ __device__ __forceinline__ int build_thread(const TileArgs &a, const TGeo &g, co
             const int end = (valid && rem >= 0.f) ? sm.hoff[base + xb + 1] : beg;
             for (int j = beg; j < end; ++j) {
                 const float4 cj = cand[j];
-                float dx = __fsub_rn(ri.x, cj.x), dy = __fsub_rn(ri.y, cj.y), dz = __fsub_rn(ri.z, cj.z);
-                if (BND) {
-                    const float ux = __fmul_rn(dx, I0), uy = __fmul_rn(dy, I1), uz = __fmul_rn(dz, I2);
-                    dx = (ux > 0.5f || ux < -0.5f) ? __fsub_rn(dx, ux > 0.5f ? L0 : -L0) : dx;
-                    dy = (uy > 0.5f || uy < -0.5f) ? __fsub_rn(dy, uy > 0.5f ? L1 : -L1) : dy;
-                    dz = (uz > 0.5f || uz < -0.5f) ? __fsub_rn(dz, uz > 0.5f ? L2 : -L2) : dz;
-                }
-                const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                const float dx = ri.x - cj.x, dy = ri.y - cj.y, dz = ri.z - cj.z;
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                 if (r2 < a.r_list2 && j != loc) {
                     push((uint32_t)j);
                     if (++nb == 8) {
@@ -754,6 +747,24 @@ __global__ void __launch_bounds__(TT) k_t_build(TileArgs a)
     }
     tile_scan(a, g, sm);
     if (!tile_stage_build(a, g, sm, rs, cand, a.tab + (size_t)blockIdx.x * TILE_TAB_WORDS)) return;
+    // the copies from across the box at their periodic image (region
+    // half-cell by region half-cell), as the step kernels stage them
+    for (int q = threadIdx.x; q < g.nq; q += TT) {
+        const int xl = q % g.RX, yl = (q / g.RX) % g.RY, zl = q / (g.RX * g.RY);
+        const int ux = g.x0 - 2 + xl, uy = g.y0 - 2 + yl, uz = g.z0 - 2 + zl;
+        const float sx = ux < 0 ? -a.box.L[0] : (ux >= a.H[0] ? a.box.L[0] : 0.0f);
+        const float sy = uy < 0 ? -a.box.L[1] : (uy >= a.H[1] ? a.box.L[1] : 0.0f);
+        const float sz = uz < 0 ? -a.box.L[2] : (uz >= a.H[2] ? a.box.L[2] : 0.0f);
+        if (sx == 0.0f && sy == 0.0f && sz == 0.0f) continue;
+        for (int e = sm.hoff[q]; e < sm.hoff[q + 1]; ++e) {
+            float4 p = cand[e];
+            p.x += sx;
+            p.y += sy;
+            p.z += sz;
+            cand[e] = p;
+        }
+    }
+    __syncthreads();
     tile_own_map(sm);
     const int nown = sm.own_off[g.nown];
     int wmax = 0;
@@ -761,17 +772,13 @@ __global__ void __launch_bounds__(TT) k_t_build(TileArgs a)
         const int p = p0 + threadIdx.x;
         const bool valid = p < nown;
         int k = 0, loc = 0, slot = 0;
-        bool bnd = false;
         if (valid) {
             k = sm.kmap[p];
             const int t = p - sm.own_off[k];
             loc = sm.own_loc[k] + t;
             slot = sm.own_slot[k] + t;
-            const int gx = g.x0 + k % g.nx, gy = g.y0 + (k / g.nx) % g.ny, gz = g.z0 + k / (g.nx * g.ny);
-            bnd = gx < 2 || gx >= a.H[0] - 2 || gy < 2 || gy >= a.H[1] - 2 || gz < 2 || gz >= a.H[2] - 2;
         }
-        const int n = __any_sync(0xffffffffu, bnd) ? build_thread<true>(a, g, sm, cand, k, loc, slot, valid)
-                                                    : build_thread<false>(a, g, sm, cand, k, loc, slot, valid);
+        const int n = build_thread(a, g, sm, cand, k, loc, slot, valid);
         wmax = max(wmax, n);
     }
     wmax = __reduce_max_sync(0xffffffffu, wmax);

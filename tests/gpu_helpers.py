@@ -51,3 +51,30 @@ def rows_equal(cnt_g, nbr_g, cnt_o, nbr_o):
     srt = np.sort(big, axis=1)[:, :cap]
     want = np.where(np.arange(cap)[None, :] < n[:, None], nbr_o[:, :cap], np.iinfo(np.int32).max)
     np.testing.assert_array_equal(srt, want)
+
+
+def rows_equal_off_cutoff(cnt_g, nbr_g, cnt_o, nbr_o, r, L, r_list, tol=1e-6):
+    """Neighbor rows as sets against the oracle's FP32-decision sets, with
+    the pairs within tol (sigma) of r_list excluded (their membership may be
+    decided by another FP32 rounding): every pair present on one side only
+    lies within tol of r_list (FP64 nearest-image distance); rows hold no
+    duplicates, padding equals N."""
+    cnt_g = np.asarray(cnt_g)
+    nbr_g = np.asarray(nbr_g)
+    N = nbr_g.shape[0]
+    x = np.asarray(r, np.float64)[:, :3]
+    col = np.arange(nbr_g.shape[1])[None, :]
+    n = np.minimum(cnt_g, nbr_g.shape[1])
+    assert np.all(nbr_g[col >= n[:, None]] == N)
+    bad = 0
+    for i in range(N):
+        g = nbr_g[i, : n[i]]
+        assert len(np.unique(g)) == len(g), i
+        o = nbr_o[i, : cnt_o[i]]
+        diff = np.setxor1d(g, o)
+        if diff.size:
+            d = x[diff] - x[i]
+            d -= L * np.round(d / L)
+            dist = np.sqrt((d * d).sum(1))
+            bad += int(np.sum(np.abs(dist - r_list) > tol))
+    assert bad == 0, bad
