@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--no-flock", action="store_true", help="skip the flocking section")
     ap.add_argument("--no-gnn", action="store_true", help="skip the graph-network potential section")
     ap.add_argument("--no-alu", action="store_true", help="skip the ALU rooflines of k_sw and the rebuild chain")
+    ap.add_argument("--no-tiles-job", action="store_true", help="skip the bench job on the tile engine")
     ap.add_argument("--probe", default=None, choices=["learned-kernels", "train-step"],
                     help="print the per-kernel timings of the learned potential's deployment (64,000 Si atoms) "
                          "or of one BP training step (8 snapshots of 512 atoms) and exit")
@@ -736,6 +737,49 @@ def fire_section():
     return out
 
 
+def tiles_section(reps=3):
+    """The bench job (LJ N = 256,000 from the same seeded start: neighbor
+    build, initial forces, 1,000 velocity-Verlet steps in one graph launch)
+    on the tile engine (MD_NBR_TILES), L2 flushed between repetitions."""
+    import torch
+    import paper_1912_04232_b300 as P
+    import workloads as W
+    dev = torch.device("cuda")
+    c = W.lj_large(seed=0)
+    s = P.md_space_periodic(3, [c.L] * 3)
+    nl = P.NeighborList(s, c.N, c.r_cut, c.skin, 128, tiles=True)
+    pot = P.lj_pot()
+    r0, v0 = torch.from_numpy(c.r).to(dev), torch.from_numpy(c.v).to(dev)
+    r, v, f = r0.clone(), v0.clone(), torch.zeros_like(r0)
+    PE = torch.zeros(c.steps, dtype=torch.float64, device=dev)
+    KE = torch.zeros_like(PE)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def job():
+        r.copy_(r0)
+        v.copy_(v0)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        nl.build(r, st)
+        P.md_energy_forces(s, pot, r, nl.plan, f, None, st)
+        P.md_integrate_nve(s, pot, r, v, f, c.mass, c.dt, c.steps, nl.plan, PE, KE, True, st)
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    job()
+    ms = min(job() for _ in range(reps))
+    b0, _ = nl.stats()
+    e = (PE + KE).cpu().numpy()
+    info = P.md_tiles_info(s, nl.plan)
+    return {"engine": "tiles (MD_NBR_TILES)", "N": c.N, "md_steps": c.steps, "ms_per_job": ms,
+            "particle_steps_per_s": c.N * c.steps / (ms * 1e-3), "builds_since_plan": int(b0),
+            "max_energy_drift_per_particle": float(np.abs(e - e[0]).max() / c.N),
+            "tile": info["tile"], "ntiles": info["ntiles"], "status": P.md_status_poll(st)}
+
+
 def nhc_section(steps=200):
     """Nose-Hoover chain NVT (chain length 3, tau = 100 dt): the N = 256,000
     LJ fluid at T* = 1 and Stillinger-Weber silicon, N = 64,000 atoms at
@@ -1355,6 +1399,8 @@ def main():
         extra["gnn_nvt"] = gnn_section()
     if rank == 0 and not args.no_alu:
         extra["alu_rooflines"] = alu_rooflines_section()
+    if rank == 0 and not args.no_tiles_job and not tiles and args.workload == "lj256k":
+        extra["tiles_engine_job"] = tiles_section()
 
     if rank == 0:
         line = {
