@@ -6,7 +6,7 @@
 //   angular  G_zl = 2^(1-z) sum_{j<k} (1 + l cos theta_jik)^z exp(-eta_a (r_ij^2 + r_ik^2)) f_c f_c,
 //            z in {1, 2, 4, 16}, l in {+1, -1}
 //
-// k_bp_desc   : G [N][16], one warp per atom (pairs and triplets over lanes)
+// k_bp_desc   : G [N][16], four atoms per warp (pairs and triplets over eight lanes)
 // k_bp_force  : F_k = -sum_i sum_m e_im dG_im/dr_k with e = dE/dG from the
 //               network; gather form (self terms, pair terms of the
 //               neighbors, triplets centred on each neighbor with k as a
@@ -254,37 +254,98 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// Descriptors with DESC_GROUP lanes per atom (a silicon atom has about five
+// partners inside R_c, so a whole warp per atom would leave most lanes idle):
+// the group sweeps the atom's row DESC_GROUP entries at a time, compacts the
+// partners inside R_c (group ballot) into its own shared list, then takes
+// the pairs and the triplets (s1 < s2, enumerated without the s1 >= s2
+// slots) over its lanes and sums G over the group.
+constexpr int DESC_GROUP = 8;
+constexpr int DESC_PER_WARP = 32 / DESC_GROUP;
+
 __global__ void __launch_bounds__(BP_WARPS * 32) k_bp_desc(BpArgs a)
 {
     count_launch();
-    __shared__ int nj[BP_WARPS][BP_MAXN];
-    __shared__ float4 nd[BP_WARPS][BP_MAXN];
+    __shared__ float4 nd[BP_WARPS][DESC_PER_WARP][BP_MAXN];
     const BpConst c = bp_const();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = blockIdx.x * BP_WARPS + w; i < a.N; i += gridDim.x * BP_WARPS) {
-        const float4 ri = a.r[i];
-        const int m = gather_within(a, c, i, ri, nj[w], nd[w]);
+    const int grp = lane / DESC_GROUP, gl = lane % DESC_GROUP;
+    const unsigned gmask = ((1u << DESC_GROUP) - 1u) << (grp * DESC_GROUP);
+    const unsigned below = (1u << lane) - 1u;
+    float4 *ndg = nd[w][grp];
+    const int step = gridDim.x * BP_WARPS * DESC_PER_WARP;
+    // every lane runs every trip (group ballots and sums are warp-wide);
+    // atoms past the end carry an empty list
+    for (int i0 = (blockIdx.x * BP_WARPS + w) * DESC_PER_WARP; i0 < a.N; i0 += step) {
+        const int i = i0 + grp;
+        const bool valid = i < a.N;
+        const float4 ri = valid ? a.r[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        int n = 0;
+        const int32_t *row = nullptr;
+        int base = 0;
+        if (valid) {
+            n = min(a.cnt[i], a.cap);
+            row = a.nbr + (size_t)i * a.cap;
+            base = a.sys_n ? (i / a.sys_n) * a.sys_n : 0;
+        }
+        const int nmax = __reduce_max_sync(0xffffffffu, n);
+        int m = 0;
+        for (int k0 = 0; k0 < nmax; k0 += DESC_GROUP) {
+            const int k = k0 + gl;
+            bool in = false;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+            if (k < n) {
+                const float4 rj = __ldg(a.r + row[k] + base);
+                r2 = dist2_rn<3>(rj, ri, a.box, dx, dy, dz);
+                in = r2 < c.rc2;
+            }
+            const unsigned mk = __ballot_sync(0xffffffffu, in) & gmask;
+            const int pos = m + __popc(mk & below);
+            if (in && pos < BP_MAXN) ndg[pos] = make_float4(dx, dy, dz, sqrtf(r2));
+            m += __popc(mk);
+        }
+        if (m > BP_MAXN) {
+            if (gl == 0) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+            m = BP_MAXN;
+        }
+        __syncwarp();
         float G[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) G[q] = 0.0f;
-        for (int s = lane; s < m; s += 32) {
-            float g[8], dg[8];
-            radial8(c, nd[w][s].w, g, dg);
+        const int mmax = __reduce_max_sync(0xffffffffu, m);
+        for (int s0 = 0; s0 < mmax; s0 += DESC_GROUP) {
+            const int s = s0 + gl;
+            if (s < m) {
+                float g[8], dg[8];
+                radial8(c, ndg[s].w, g, dg);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) G[q] += g[q];
+                for (int q = 0; q < 8; ++q) G[q] += g[q];
+            }
         }
-        for (int t = lane; t < m * m; t += 32) {
-            int s1 = t / m, s2 = t - s1 * m;
-            if (s1 >= s2) continue;
-            float4 u = nd[w][s1], v = nd[w][s2];
-            float tt[8], du[8][3], dw[8][3];
-            angular8<false>(c, u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, tt, du, dw);
+        const int nt = m * (m - 1) / 2;
+        const int ntmax = __reduce_max_sync(0xffffffffu, nt);
+        for (int t0 = 0; t0 < ntmax; t0 += DESC_GROUP) {
+            int t = t0 + gl;
+            if (t < nt) {
+                // triplet t of the pairs (s1 < s2) in row-major order
+                int s1 = 0;
+                while (t >= m - 1 - s1) {
+                    t -= m - 1 - s1;
+                    ++s1;
+                }
+                const int s2 = s1 + 1 + t;
+                const float4 u = ndg[s1], v = ndg[s2];
+                float tt[8], du[8][3], dw[8][3];
+                angular8<false>(c, u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, tt, du, dw);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) G[8 + q] += tt[q];
+                for (int q = 0; q < 8; ++q) G[8 + q] += tt[q];
+            }
         }
 #pragma unroll
-        for (int q = 0; q < 16; ++q) G[q] = warp_sum(G[q]);
-        if (lane == 0) {
+        for (int q = 0; q < 16; ++q)
+#pragma unroll
+            for (int o = DESC_GROUP / 2; o > 0; o >>= 1) G[q] += __shfl_xor_sync(0xffffffffu, G[q], o);
+        if (valid && gl == 0) {
             float4 *o = reinterpret_cast<float4 *>(a.G + (size_t)i * 16);
             o[0] = make_float4(G[0], G[1], G[2], G[3]);
             o[1] = make_float4(G[4], G[5], G[6], G[7]);
@@ -541,7 +602,10 @@ static int bp_grid(int N)
     return groups < g ? groups : g;
 }
 
-void enqueue_bp_desc(const BpArgs &a, cudaStream_t st) { k_bp_desc<<<bp_grid(a.N), BP_WARPS * 32, 0, st>>>(a); }
+void enqueue_bp_desc(const BpArgs &a, cudaStream_t st)
+{
+    k_bp_desc<<<bp_grid((a.N + DESC_PER_WARP - 1) / DESC_PER_WARP), BP_WARPS * 32, 0, st>>>(a);
+}
 
 void enqueue_bp_force(const BpArgs &a, int kick, cudaStream_t st)
 {
