@@ -4,7 +4,8 @@
 //   phi3    = lambda eps (cos theta - cos0)^2 g(r_ij) g(r_ik),
 //   g(r)    = exp(gamma sigma / (r - a sigma)),      all for r < a sigma.
 //
-// Gather form, one warp per atom i, no atomics.  F_i collects
+// Gather form, eight lanes per atom i (four atoms per warp), no atomics.
+// F_i collects
 //   (1) the two-body terms of every neighbor j,
 //   (2) the triplets centred on i (legs j < k of i's neighbors), and
 //   (3) the triplets centred on each neighbor j in which i is a leg
@@ -18,7 +19,7 @@
 
 namespace jmd {
 
-constexpr int SW_MAXN = 64;   // neighbors inside a*sigma kept per atom
+constexpr int SW_MAXN = 32;   // neighbors inside a*sigma kept per atom
 constexpr int SW_WARPS = 8;
 
 struct SwP {
@@ -95,14 +96,15 @@ __device__ __forceinline__ float sw_triplet(const SwP &P, float ux, float uy, fl
 // F += dh/du + dh/dw, e += h), or centred on neighbor s with the atom as a
 // leg (k == SW_LEG; the leg from s to the atom is -u, the other leg w' from
 // s: F -= dh(-u, w')/d(-u)).  One code path with selected coefficients, so
-// a warp's mixed queue runs without divergence.
+// a group's mixed queue runs without divergence.  The G lanes of a group
+// (lane gl of the group) evaluate its queue.
 constexpr unsigned char SW_LEG = 0xff;
+template <int G>
 __device__ __forceinline__ void sw_queue_terms(const SwP &P, const float4 *nd, const unsigned char *qs,
-                                               const unsigned char *qk, const float4 *qw, int qn, float &fx,
+                                               const unsigned char *qk, const float4 *qw, int qn, int gl, float &fx,
                                                float &fy, float &fz, float &e)
 {
-    const int lane = threadIdx.x & 31;
-    for (int q = lane; q < qn; q += 32) {
+    for (int q = gl; q < qn; q += G) {
         const int k = qk[q];
         const bool leg = k == SW_LEG;
         const float4 a = nd[qs[q]];
@@ -116,158 +118,176 @@ __device__ __forceinline__ void sw_queue_terms(const SwP &P, const float4 *nd, c
         fz += sg * gu[2] + cw * gw[2];
         e += cw * h;
     }
-    __syncwarp();
 }
 
-constexpr int SW_QMAX = 96;   // queued neighbor-centred triplets per warp
+constexpr int SW_G = 8;                  // lanes per atom
+constexpr int SW_PER_WARP = 32 / SW_G;   // atoms per warp
+constexpr int SW_QG = 32;                // queued triplets per atom between evaluations
 
+// One group of SW_G lanes per atom, SW_PER_WARP atoms per warp (a silicon
+// atom has about five partners inside a*sigma).  Every lane of a warp runs
+// every trip of every loop (group ballots, scans and sums are warp-wide);
+// a queue is evaluated when any group's would overflow.
 template <int KICK>
 __global__ void __launch_bounds__(SW_WARPS * 32) k_sw(PairArgs a)
 {
     count_launch();
-    __shared__ int nj[SW_WARPS][SW_MAXN];
-    __shared__ float4 nd[SW_WARPS][SW_MAXN];   // (ux, uy, uz, r): u = r_j - r_i
-    __shared__ int qpre[SW_WARPS][SW_MAXN + 1];       // neighbors' row offsets in the candidate sweep
-    __shared__ unsigned char qs[SW_WARPS][SW_QMAX];   // queued triplets: first leg
-    __shared__ unsigned char qk[SW_WARPS][SW_QMAX];   // ... second leg of a centred triplet, or SW_LEG
-    __shared__ float4 qw[SW_WARPS][SW_QMAX];          // ... and the other leg (w', |w'|) of a leg triplet
+    __shared__ int nj[SW_WARPS][SW_PER_WARP][SW_MAXN];
+    __shared__ float4 nd[SW_WARPS][SW_PER_WARP][SW_MAXN];   // (ux, uy, uz, r): u = r_j - r_i
+    __shared__ int qpre[SW_WARPS][SW_PER_WARP][SW_MAXN + 1];     // neighbors' row offsets in the candidate sweep
+    __shared__ unsigned char qs[SW_WARPS][SW_PER_WARP][SW_QG];   // queued triplets: first leg
+    __shared__ unsigned char qk[SW_WARPS][SW_PER_WARP][SW_QG];   // ... second leg of a centred triplet, or SW_LEG
+    __shared__ float4 qw[SW_WARPS][SW_PER_WARP][SW_QG];          // ... and the other leg (w', |w'|) of a leg triplet
     const SwP P = sw_params(a);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
+    const int grp = lane / SW_G, gl = lane % SW_G;
+    const unsigned gmask = ((1u << SW_G) - 1u) << (grp * SW_G);
+    const unsigned below = (1u << lane) - 1u;
+    int *njg = nj[w][grp];
+    float4 *ndg = nd[w][grp];
+    int *qp = qpre[w][grp];
+    unsigned char *qsg = qs[w][grp], *qkg = qk[w][grp];
+    float4 *qwg = qw[w][grp];
     float pe_acc = 0.0f, ke_acc = 0.0f;
-    for (int i = blockIdx.x * SW_WARPS + w; i < a.N; i += gridDim.x * SW_WARPS) {
-        const float4 ri = a.r[i];
-        int n = a.cnt[i];
-        n = n < a.cap ? n : a.cap;
-        const int32_t *row = a.nbr + (size_t)i * a.cap;
-        // (0) neighbors inside a*sigma, compacted into shared memory
+    const int step = gridDim.x * SW_WARPS * SW_PER_WARP;
+    for (int i0 = (blockIdx.x * SW_WARPS + w) * SW_PER_WARP; i0 < a.N; i0 += step) {
+        const int i = i0 + grp;
+        const bool valid = i < a.N;
+        const float4 ri = valid ? a.r[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        int n = 0;
+        const int32_t *row = a.nbr + (size_t)(valid ? i : 0) * a.cap;
+        if (valid) n = min(a.cnt[i], a.cap);
+        // (0) neighbors inside a*sigma, compacted into the group's list
+        const int nmax = __reduce_max_sync(0xffffffffu, n);
         int m = 0;
-        for (int k0 = 0; k0 < n; k0 += 32) {
-            int k = k0 + lane;
+        for (int k0 = 0; k0 < nmax; k0 += SW_G) {
+            const int k = k0 + gl;
             bool in = false;
             int j = 0;
             float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
             if (k < n) {
                 j = row[k];
-                float4 rj = __ldg(a.r + j);
+                const float4 rj = __ldg(a.r + j);
                 r2 = dist2_rn<3>(rj, ri, a.box, dx, dy, dz);   // u = r_j - r_i
                 in = r2 < P.rc2;
             }
-            unsigned mk = __ballot_sync(0xffffffffu, in);
-            int pos = m + __popc(mk & lt);
+            const unsigned mk = __ballot_sync(0xffffffffu, in) & gmask;
+            const int pos = m + __popc(mk & below);
             if (in && pos < SW_MAXN) {
-                nj[w][pos] = j;
-                nd[w][pos] = make_float4(dx, dy, dz, sqrtf(r2));
+                njg[pos] = j;
+                ndg[pos] = make_float4(dx, dy, dz, sqrtf(r2));
             }
             m += __popc(mk);
         }
         if (m > SW_MAXN) {
-            if (lane == 0) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+            if (gl == 0) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
             m = SW_MAXN;
         }
         __syncwarp();
         float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
         // (1) two-body: F_i += phi2'(r) u / r
-        for (int s = lane; s < m; s += 32) {
-            float4 u = nd[w][s];
-            float dphi;
-            float ph = sw_phi2(P, u.w, dphi);
-            float fr = dphi / u.w;
-            fx += fr * u.x;
-            fy += fr * u.y;
-            fz += fr * u.z;
-            e += 0.5f * ph;
+        const int mmax = __reduce_max_sync(0xffffffffu, m);
+        for (int s0 = 0; s0 < mmax; s0 += SW_G) {
+            const int s = s0 + gl;
+            if (s < m) {
+                const float4 u = ndg[s];
+                float dphi;
+                const float ph = sw_phi2(P, u.w, dphi);
+                const float fr = dphi / u.w;
+                fx += fr * u.x;
+                fy += fr * u.y;
+                fz += fr * u.z;
+                e += 0.5f * ph;
+            }
         }
         // (2) triplets centred on i: F_i += dh/du + dh/dw, e += h, and
         // (3) triplets centred on neighbor j with i as a leg:
         //     u' = r_i - r_j = -u, w' = r_k - r_j; F_i -= dh/du'.
-        // Both kinds go into one shared-memory queue that is evaluated with
+        // Both kinds go into the group's shared-memory queue, evaluated with
         // every lane busy: the centred pairs (s1 < s2) first, then the leg
-        // candidates (s, k) of all neighbors' rows, swept 32 per step, those
-        // inside a*sigma queued with w'.
-        {
-            int qn = 0;
-            for (int t0 = 0; t0 < m * m; t0 += 32) {
-                const int t = t0 + lane;
-                const int s1 = t / m, s2 = t - s1 * m;
-                const bool in = t < m * m && s1 < s2;
-                const unsigned mk = __ballot_sync(0xffffffffu, in);
-                if (qn + __popc(mk) > SW_QMAX) {
-                    sw_queue_terms(P, nd[w], qs[w], qk[w], qw[w], qn, fx, fy, fz, e);
-                    qn = 0;
-                }
-                const int pos = qn + __popc(mk & lt);
-                if (in) {
-                    qs[w][pos] = (unsigned char)s1;
-                    qk[w][pos] = (unsigned char)s2;
-                }
-                qn += __popc(mk);
+        // candidates (s, k) of all neighbors' rows, swept SW_G per step,
+        // those inside a*sigma queued with w'.
+        int qn = 0;
+        auto enqueue = [&](bool in, int q1, int q2, float4 wv) {
+            const unsigned mk = __ballot_sync(0xffffffffu, in) & gmask;
+            if (__any_sync(0xffffffffu, qn + __popc(mk) > SW_QG)) {   // some group full: evaluate every queue
                 __syncwarp();
-            }
-            int tot = 0;
-            for (int s0 = 0; s0 < m; s0 += 32) {   // exclusive prefix of the neighbors' row lengths
-                const int s = s0 + lane;
-                int nn = 0;
-                if (s < m) {
-                    nn = a.cnt[nj[w][s]];
-                    nn = nn < a.cap ? nn : a.cap;
-                }
-                int incl = nn;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                if (s < m) qpre[w][s] = tot + incl - nn;
-                tot += __shfl_sync(0xffffffffu, incl, 31);
-            }
-            if (lane == 0) qpre[w][m] = tot;
-            __syncwarp();
-            for (int b0 = 0; b0 < tot; b0 += 32) {
-                const int it = b0 + lane;
-                bool in = false;
-                int s = 0;
-                float wx = 0.f, wy = 0.f, wz = 0.f, w2 = 0.f;
-                if (it < tot) {
-                    int lo = 0, hi = m - 1;   // last s with qpre[s] <= it
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (qpre[w][mid] <= it) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    s = lo;
-                    const int j = nj[w][s];
-                    const int kk = a.nbr[(size_t)j * a.cap + (it - qpre[w][s])];
-                    if (kk != i) {
-                        const float4 rj = __ldg(a.r + j), rk = __ldg(a.r + kk);
-                        w2 = dist2_rn<3>(rk, rj, a.box, wx, wy, wz);
-                        in = w2 < P.rc2;
-                    }
-                }
-                const unsigned mk = __ballot_sync(0xffffffffu, in);
-                if (qn + __popc(mk) > SW_QMAX) {   // full: evaluate what is queued
-                    sw_queue_terms(P, nd[w], qs[w], qk[w], qw[w], qn, fx, fy, fz, e);
-                    qn = 0;
-                }
-                const int pos = qn + __popc(mk & lt);
-                if (in) {
-                    qs[w][pos] = (unsigned char)s;
-                    qk[w][pos] = SW_LEG;
-                    qw[w][pos] = make_float4(wx, wy, wz, sqrtf(w2));
-                }
-                qn += __popc(mk);
+                sw_queue_terms<SW_G>(P, ndg, qsg, qkg, qwg, qn, gl, fx, fy, fz, e);
                 __syncwarp();
+                qn = 0;
             }
-            sw_queue_terms(P, nd[w], qs[w], qk[w], qw[w], qn, fx, fy, fz, e);
+            const int pos = qn + __popc(mk & below);
+            if (in) {
+                qsg[pos] = (unsigned char)q1;
+                qkg[pos] = (unsigned char)q2;
+                qwg[pos] = wv;
+            }
+            qn += __popc(mk);
+        };
+        const int nt = m * (m - 1) / 2;
+        const int ntmax = __reduce_max_sync(0xffffffffu, nt);
+        for (int t0 = 0; t0 < ntmax; t0 += SW_G) {
+            int t = t0 + gl, s1 = 0;
+            const bool in = t < nt;
+            if (in)
+                while (t >= m - 1 - s1) {   // pair t of (s1 < s2) in row-major order
+                    t -= m - 1 - s1;
+                    ++s1;
+                }
+            enqueue(in, s1, s1 + 1 + t, make_float4(0.f, 0.f, 0.f, 0.f));
         }
+        int tot = 0;
+        for (int s0 = 0; s0 < mmax; s0 += SW_G) {   // exclusive prefix of the neighbors' row lengths
+            const int s = s0 + gl;
+            int nn = 0;
+            if (s < m) nn = min(a.cnt[njg[s]], a.cap);
+            int incl = nn;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+            for (int o = 1; o < SW_G; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o, SW_G);
+                if (gl >= o) incl += y;
+            }
+            if (s < m) qp[s] = tot + incl - nn;
+            tot += __shfl_sync(0xffffffffu, incl, SW_G - 1, SW_G);
+        }
+        if (gl == 0) qp[m] = tot;
+        __syncwarp();
+        const int totmax = __reduce_max_sync(0xffffffffu, tot);
+        for (int b0 = 0; b0 < totmax; b0 += SW_G) {
+            const int it = b0 + gl;
+            bool in = false;
+            int s = 0;
+            float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (it < tot) {
+                int lo = 0, hi = m - 1;   // last s with qpre[s] <= it
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (qp[mid] <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                s = lo;
+                const int j = njg[s];
+                const int kk = a.nbr[(size_t)j * a.cap + (it - qp[s])];
+                if (kk != i) {
+                    const float4 rj = __ldg(a.r + j), rk = __ldg(a.r + kk);
+                    float wx, wy, wz;
+                    const float w2 = dist2_rn<3>(rk, rj, a.box, wx, wy, wz);
+                    in = w2 < P.rc2;
+                    wv = make_float4(wx, wy, wz, sqrtf(w2));
+                }
+            }
+            enqueue(in, s, SW_LEG, wv);
+        }
+        __syncwarp();
+        sw_queue_terms<SW_G>(P, ndg, qsg, qkg, qwg, qn, gl, fx, fy, fz, e);
+#pragma unroll
+        for (int o = SW_G / 2; o > 0; o >>= 1) {
             fx += __shfl_xor_sync(0xffffffffu, fx, o);
             fy += __shfl_xor_sync(0xffffffffu, fy, o);
             fz += __shfl_xor_sync(0xffffffffu, fz, o);
             e += __shfl_xor_sync(0xffffffffu, e, o);
         }
-        if (lane == 0) {
+        if (valid && gl == 0) {
             a.f[i] = make_float4(fx, fy, fz, e);
             pe_acc += e;
             if (KICK) ke_acc += half_kick<3>(a, i, fx, fy, fz);
@@ -290,7 +310,7 @@ static int sw_grid(int N)
         if (per_sm < 1) per_sm = 1;
         if (sms < 1) sms = 1;
     }
-    int groups = (N + SW_WARPS - 1) / SW_WARPS;
+    int groups = (N + SW_WARPS * SW_PER_WARP - 1) / (SW_WARPS * SW_PER_WARP);
     int g = per_sm * sms;
     return groups < g ? groups : g;
 }
