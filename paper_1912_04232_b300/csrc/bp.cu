@@ -10,7 +10,7 @@
 // k_bp_force  : F_k = -sum_i sum_m e_im dG_im/dr_k with e = dE/dG from the
 //               network; gather form (self terms, pair terms of the
 //               neighbors, triplets centred on each neighbor with k as a
-//               leg), one warp per atom, no atomics
+//               leg), four atoms per warp, eight lanes each, no atomics
 // k_bp_jvp    : v_im = sum_k dG_im/dr_k . dF_k (the descriptor Jacobian
 //               applied to a per-atom vector field): the input of the
 //               force-loss gradient, gathered over the atom's own pairs and
@@ -373,14 +373,15 @@ __device__ __forceinline__ void load16(const float *p, float e[16])
 // F += sum_m e_km (dt/du + dt/dw)), or centred on neighbor j = s with k as a
 // leg (t == BP_LEG; the leg from j to k is -u, the other leg w' from j;
 // F -= sum_m e_jm dt(-u, w')/d(-u)).  One code path with selected
-// coefficients, so a warp's mixed queue runs without divergence.
+// coefficients, so a group's mixed queue runs without divergence.  The G
+// lanes of a group (lane gl of the group) evaluate its queue.
 constexpr unsigned char BP_LEG = 0xff;
+template <int G>
 __device__ __forceinline__ void bp_queue_terms(const BpArgs &a, const BpConst &c, int k, const int *nj,
                                                const float4 *nd, const unsigned char *qs, const unsigned char *qk,
-                                               const float4 *qw, int qn, float &fx, float &fy, float &fz)
+                                               const float4 *qw, int qn, int gl, float &fx, float &fy, float &fz)
 {
-    const int lane = threadIdx.x & 31;
-    for (int q = lane; q < qn; q += 32) {
+    for (int q = gl; q < qn; q += G) {
         const int t = qk[q];
         const bool leg = t == BP_LEG;
         const float4 u = nd[qs[q]];
@@ -397,133 +398,186 @@ __device__ __forceinline__ void bp_queue_terms(const BpArgs &a, const BpConst &c
         fy += sg * gu[1] + cw * gw[1];
         fz += sg * gu[2] + cw * gw[2];
     }
-    __syncwarp();
 }
 
-constexpr int BP_QMAX = 96;   // queued neighbor-centred triplets per warp
+constexpr int BPF_G = 8;                   // lanes per atom of the force gather
+constexpr int BPF_PER_WARP = 32 / BPF_G;   // atoms per warp
+constexpr int BPF_MAXN = BP_MAXN;          // partners inside R_c kept per atom (more: overflow)
+constexpr int BPF_QG = 24;                 // queued triplets per atom between evaluations
 
+// Force gather with BPF_G lanes per atom, BPF_PER_WARP atoms per warp (a
+// silicon atom has about five partners inside R_c).  Every lane of a warp
+// runs every trip of every loop (group ballots, scans and sums are
+// warp-wide); a queue is evaluated when any group's would overflow.
 template <int KICK>
-__global__ void __launch_bounds__(BP_WARPS * 32) k_bp_force(BpArgs a)
+__global__ void __launch_bounds__(BP_WARPS * 32, 4) k_bp_force(BpArgs a)
 {
     count_launch();
-    __shared__ int nj[BP_WARPS][BP_MAXN];
-    __shared__ float4 nd[BP_WARPS][BP_MAXN];
-    __shared__ int qpre[BP_WARPS][BP_MAXN + 1];       // neighbors' row offsets in the candidate sweep
-    __shared__ unsigned char qs[BP_WARPS][BP_QMAX];   // queued triplets: first leg
-    __shared__ unsigned char qk[BP_WARPS][BP_QMAX];   // ... second leg of a centred triplet, or BP_LEG
-    __shared__ float4 qw[BP_WARPS][BP_QMAX];          // ... and the other leg (w', |w'|) of a leg triplet
+    __shared__ int nj[BP_WARPS][BPF_PER_WARP][BPF_MAXN];
+    __shared__ float4 nd[BP_WARPS][BPF_PER_WARP][BPF_MAXN];
+    __shared__ int qpre[BP_WARPS][BPF_PER_WARP][BPF_MAXN + 1];   // neighbors' row offsets in the candidate sweep
+    __shared__ unsigned char qs[BP_WARPS][BPF_PER_WARP][BPF_QG];   // queued triplets: first leg
+    __shared__ unsigned char qk[BP_WARPS][BPF_PER_WARP][BPF_QG];   // ... second leg of a centred triplet, or BP_LEG
+    __shared__ float4 qw[BP_WARPS][BPF_PER_WARP][BPF_QG];          // ... and the other leg (w', |w'|) of a leg triplet
     const BpConst c = bp_const();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / BPF_G, gl = lane % BPF_G;
+    const unsigned gmask = ((1u << BPF_G) - 1u) << (grp * BPF_G);
+    const unsigned below = (1u << lane) - 1u;
+    int *njg = nj[w][grp];
+    float4 *ndg = nd[w][grp];
+    int *qp = qpre[w][grp];
+    unsigned char *qsg = qs[w][grp], *qkg = qk[w][grp];
+    float4 *qwg = qw[w][grp];
     float pe_acc = 0.0f, ke_acc = 0.0f;
-    for (int k = blockIdx.x * BP_WARPS + w; k < a.N; k += gridDim.x * BP_WARPS) {
-        const float4 rk = a.r[k];
-        const int m = gather_within(a, c, k, rk, nj[w], nd[w]);
-        float ek[16];
-        load16(a.dEdG + (size_t)k * 16, ek);
+    const int step = gridDim.x * BP_WARPS * BPF_PER_WARP;
+    for (int k0 = (blockIdx.x * BP_WARPS + w) * BPF_PER_WARP; k0 < a.N; k0 += step) {
+        const int k = k0 + grp;
+        const bool valid = k < a.N;
+        const float4 rk = valid ? a.r[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+        int n = 0, base = 0;
+        const int32_t *row = a.nbr + (size_t)(valid ? k : 0) * a.cap;
+        if (valid) {
+            n = min(a.cnt[k], a.cap);
+            base = a.sys_n ? (k / a.sys_n) * a.sys_n : 0;
+        }
+        // partners inside R_c, compacted into the group's list
+        const int nmax = __reduce_max_sync(0xffffffffu, n);
+        int m = 0;
+        for (int c0 = 0; c0 < nmax; c0 += BPF_G) {
+            const int kk = c0 + gl;
+            bool in = false;
+            int j = 0;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+            if (kk < n) {
+                j = row[kk] + base;
+                const float4 rj = __ldg(a.r + j);
+                r2 = dist2_rn<3>(rj, rk, a.box, dx, dy, dz);
+                in = r2 < c.rc2;
+            }
+            const unsigned mk = __ballot_sync(0xffffffffu, in) & gmask;
+            const int pos = m + __popc(mk & below);
+            if (in && pos < BPF_MAXN) {
+                njg[pos] = j;
+                ndg[pos] = make_float4(dx, dy, dz, sqrtf(r2));
+            }
+            m += __popc(mk);
+        }
+        if (m > BPF_MAXN) {
+            if (gl == 0) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+            m = BPF_MAXN;
+        }
+        __syncwarp();
         float fx = 0.f, fy = 0.f, fz = 0.f;
         // self radial + the neighbor's radial term of the same pair:
         // both give (e_km + e_jm) g'_m(r) u/r with u = r_j - r_k
-        for (int s = lane; s < m; s += 32) {
-            float4 u = nd[w][s];
-            float ej[16];
-            load16(a.dEdG + (size_t)nj[w][s] * 16, ej);
-            float g[8], dg[8];
-            radial8(c, u.w, g, dg);
-            float sc = 0.0f;
+        const int mmax = __reduce_max_sync(0xffffffffu, m);
+        for (int s0 = 0; s0 < mmax; s0 += BPF_G) {
+            const int s = s0 + gl;
+            if (s < m) {
+                const float4 u = ndg[s];
+                float ek[16], ej[16];
+                load16(a.dEdG + (size_t)k * 16, ek);
+                load16(a.dEdG + (size_t)njg[s] * 16, ej);
+                float g[8], dg[8];
+                radial8(c, u.w, g, dg);
+                float sc = 0.0f;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) sc += (ek[q] + ej[q]) * dg[q];
-            sc /= u.w;
-            fx += sc * u.x;
-            fy += sc * u.y;
-            fz += sc * u.z;
+                for (int q = 0; q < 8; ++q) sc += (ek[q] + ej[q]) * dg[q];
+                sc /= u.w;
+                fx += sc * u.x;
+                fy += sc * u.y;
+                fz += sc * u.z;
+            }
         }
         // triplets centred on k: F_k += sum_m e_km (dt/du + dt/dw), and
         // triplets centred on neighbor j with k as leg u' = r_k - r_j:
         // F_k -= sum_m e_jm dt(u', w')/du', w' = r_l - r_j, l in N(j), l != k.
-        // Both kinds go into one shared-memory queue that is evaluated with
+        // Both kinds go into the group's shared-memory queue, evaluated with
         // every lane busy: the centred pairs (s1 < s2) first, then the leg
-        // candidates (s, l) of all neighbors' rows, swept 32 per step, those
-        // inside R_c queued with w'.
-        {
-            int qn = 0;
-            for (int t0 = 0; t0 < m * m; t0 += 32) {
-                const int t = t0 + lane;
-                const int s1 = t / m, s2 = t - s1 * m;
-                const bool in = t < m * m && s1 < s2;
-                const unsigned mk = __ballot_sync(0xffffffffu, in);
-                if (qn + __popc(mk) > BP_QMAX) {
-                    bp_queue_terms(a, c, k, nj[w], nd[w], qs[w], qk[w], qw[w], qn, fx, fy, fz);
-                    qn = 0;
-                }
-                const int pos = qn + __popc(mk & ((1u << lane) - 1u));
-                if (in) {
-                    qs[w][pos] = (unsigned char)s1;
-                    qk[w][pos] = (unsigned char)s2;
-                }
-                qn += __popc(mk);
+        // candidates (s, l) of all neighbors' rows, swept BPF_G per step,
+        // those inside R_c queued with w'.
+        int qn = 0;
+        auto enqueue = [&](bool in, int q1, int q2, float4 wv) {
+            const unsigned mk = __ballot_sync(0xffffffffu, in) & gmask;
+            if (__any_sync(0xffffffffu, qn + __popc(mk) > BPF_QG)) {   // some group full: evaluate every queue
                 __syncwarp();
-            }
-            int tot = 0;
-            for (int s0 = 0; s0 < m; s0 += 32) {   // exclusive prefix of the neighbors' row lengths
-                const int s = s0 + lane;
-                int nn = 0;
-                if (s < m) {
-                    nn = a.cnt[nj[w][s]];
-                    nn = nn < a.cap ? nn : a.cap;
-                }
-                int incl = nn;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                if (s < m) qpre[w][s] = tot + incl - nn;
-                tot += __shfl_sync(0xffffffffu, incl, 31);
-            }
-            if (lane == 0) qpre[w][m] = tot;
-            __syncwarp();
-            for (int b0 = 0; b0 < tot; b0 += 32) {
-                const int it = b0 + lane;
-                bool in = false;
-                int s = 0;
-                float wx = 0.f, wy = 0.f, wz = 0.f, w2 = 0.f;
-                if (it < tot) {
-                    int lo = 0, hi = m - 1;   // last s with qpre[s] <= it
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (qpre[w][mid] <= it) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    s = lo;
-                    const int j = nj[w][s];
-                    const int basej = a.sys_n ? (j / a.sys_n) * a.sys_n : 0;
-                    const int l = a.nbr[(size_t)j * a.cap + (it - qpre[w][s])] + basej;
-                    if (l != k) {
-                        const float4 rj = __ldg(a.r + j), rl = __ldg(a.r + l);
-                        w2 = dist2_rn<3>(rl, rj, a.box, wx, wy, wz);
-                        in = w2 < c.rc2;
-                    }
-                }
-                const unsigned mk = __ballot_sync(0xffffffffu, in);
-                if (qn + __popc(mk) > BP_QMAX) {   // full: evaluate what is queued
-                    bp_queue_terms(a, c, k, nj[w], nd[w], qs[w], qk[w], qw[w], qn, fx, fy, fz);
-                    qn = 0;
-                }
-                const int pos = qn + __popc(mk & ((1u << lane) - 1u));
-                if (in) {
-                    qs[w][pos] = (unsigned char)s;
-                    qk[w][pos] = BP_LEG;
-                    qw[w][pos] = make_float4(wx, wy, wz, sqrtf(w2));
-                }
-                qn += __popc(mk);
+                bp_queue_terms<BPF_G>(a, c, k, njg, ndg, qsg, qkg, qwg, qn, gl, fx, fy, fz);
                 __syncwarp();
+                qn = 0;
             }
-            bp_queue_terms(a, c, k, nj[w], nd[w], qs[w], qk[w], qw[w], qn, fx, fy, fz);
+            const int pos = qn + __popc(mk & below);
+            if (in) {
+                qsg[pos] = (unsigned char)q1;
+                qkg[pos] = (unsigned char)q2;
+                qwg[pos] = wv;
+            }
+            qn += __popc(mk);
+        };
+        const int nt = m * (m - 1) / 2;
+        const int ntmax = __reduce_max_sync(0xffffffffu, nt);
+        for (int t0 = 0; t0 < ntmax; t0 += BPF_G) {
+            int t = t0 + gl, s1 = 0;
+            const bool in = t < nt;
+            if (in)
+                while (t >= m - 1 - s1) {   // pair t of (s1 < s2) in row-major order
+                    t -= m - 1 - s1;
+                    ++s1;
+                }
+            enqueue(in, s1, s1 + 1 + t, make_float4(0.f, 0.f, 0.f, 0.f));
         }
-        fx = warp_sum(fx);
-        fy = warp_sum(fy);
-        fz = warp_sum(fz);
-        if (lane == 0) {
+        int tot = 0;
+        for (int s0 = 0; s0 < mmax; s0 += BPF_G) {   // exclusive prefix of the neighbors' row lengths
+            const int s = s0 + gl;
+            int nn = 0;
+            if (s < m) nn = min(a.cnt[njg[s]], a.cap);
+            int incl = nn;
+#pragma unroll
+            for (int o = 1; o < BPF_G; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o, BPF_G);
+                if (gl >= o) incl += y;
+            }
+            if (s < m) qp[s] = tot + incl - nn;
+            tot += __shfl_sync(0xffffffffu, incl, BPF_G - 1, BPF_G);
+        }
+        if (gl == 0) qp[m] = tot;
+        __syncwarp();
+        const int totmax = __reduce_max_sync(0xffffffffu, tot);
+        for (int b0 = 0; b0 < totmax; b0 += BPF_G) {
+            const int it = b0 + gl;
+            bool in = false;
+            int s = 0;
+            float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (it < tot) {
+                int lo = 0, hi = m - 1;   // last s with qpre[s] <= it
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (qp[mid] <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                s = lo;
+                const int j = njg[s];
+                const int basej = a.sys_n ? (j / a.sys_n) * a.sys_n : 0;
+                const int l = a.nbr[(size_t)j * a.cap + (it - qp[s])] + basej;
+                if (l != k) {
+                    const float4 rj = __ldg(a.r + j), rl = __ldg(a.r + l);
+                    float wx, wy, wz;
+                    const float w2 = dist2_rn<3>(rl, rj, a.box, wx, wy, wz);
+                    in = w2 < c.rc2;
+                    wv = make_float4(wx, wy, wz, sqrtf(w2));
+                }
+            }
+            enqueue(in, s, BP_LEG, wv);
+        }
+        __syncwarp();
+        bp_queue_terms<BPF_G>(a, c, k, njg, ndg, qsg, qkg, qwg, qn, gl, fx, fy, fz);
+#pragma unroll
+        for (int o = BPF_G / 2; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (valid && gl == 0) {
             const float ei = a.Ei ? a.Ei[k] : 0.0f;
             a.pa.f[k] = make_float4(fx, fy, fz, ei);
             pe_acc += ei;
@@ -609,8 +663,9 @@ void enqueue_bp_desc(const BpArgs &a, cudaStream_t st)
 
 void enqueue_bp_force(const BpArgs &a, int kick, cudaStream_t st)
 {
-    if (kick) k_bp_force<1><<<bp_grid(a.N), BP_WARPS * 32, 0, st>>>(a);
-    else k_bp_force<0><<<bp_grid(a.N), BP_WARPS * 32, 0, st>>>(a);
+    const int g = bp_grid((a.N + BPF_PER_WARP - 1) / BPF_PER_WARP);
+    if (kick) k_bp_force<1><<<g, BP_WARPS * 32, 0, st>>>(a);
+    else k_bp_force<0><<<g, BP_WARPS * 32, 0, st>>>(a);
 }
 
 void enqueue_bp_jvp(const BpArgs &a, cudaStream_t st) { k_bp_jvp<<<bp_grid(a.N), BP_WARPS * 32, 0, st>>>(a); }

@@ -129,7 +129,7 @@ constexpr int SW_QG = 32;                // queued triplets per atom between eva
 // every trip of every loop (group ballots, scans and sums are warp-wide);
 // a queue is evaluated when any group's would overflow.
 template <int KICK>
-__global__ void __launch_bounds__(SW_WARPS * 32) k_sw(PairArgs a)
+__global__ void __launch_bounds__(SW_WARPS * 32, 4) k_sw(PairArgs a)
 {
     count_launch();
     __shared__ int nj[SW_WARPS][SW_PER_WARP][SW_MAXN];
