@@ -3,8 +3,10 @@
 // tensor memory): energy E_i and input gradient dE_i/dG_i for tiles of 128
 // atoms (Sec. 4.1 deployment; same network as mlp.cu).
 //
-// Per tile (one CTA of 4 warps; thread t owns row/atom t of the tile, which
-// is TMEM lane t):
+// Per tile (one CTA of 8 warps; two threads per row/atom: thread t owns row
+// t % 128, which is TMEM lane t % 128, and the column half t / 128 of every
+// 64-column accumulator, so that each thread runs half of the element-wise
+// work between the MMA rounds):
 //   MMA1  D1 = X  W1^T        [128 x 16] x [16 x 64]     (a1 = D1 + b1)
 //   MMA2  D2 = H1 W2^T        [128 x 64] x [64 x 64]     (a2 = D2 + b2, E = w3 . silu(a2) + b3)
 //   MMA3  D3 = G2 W2          [128 x 64] x [64 x 64]     (G2 = w3 * silu'(a2))
@@ -66,21 +68,25 @@ __device__ __forceinline__ void tc_row8(unsigned char *sm, uint32_t buf, int row
         make_uint4(tc_pack(v[0], v[1]), tc_pack(v[2], v[3]), tc_pack(v[4], v[5]), tc_pack(v[6], v[7]));
 }
 
+constexpr int TC_THREADS = 2 * TC_M;
+
 struct TcSmallSmem {
     uint64_t bar;
     uint32_t tmem_base;
     uint32_t timeout;
     float b1[64], b2[64], w3[64], mu[16], isd[16];
     float b3;
+    float Eh[TC_M];   // the second column half's part of E
 };
 
-__global__ void __launch_bounds__(128, 4) k_mlp_infer_tc(const float *P, const float *norm, const float *G, int N,
+__global__ void __launch_bounds__(TC_THREADS, 4) k_mlp_infer_tc(const float *P, const float *norm, const float *G, int N,
                                                          float *Ei, float *dEdG, uint32_t *status)
 {
     count_launch();
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ TcSmallSmem S;
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & (TC_M - 1), ch = tid >> 7;   // TMEM lane and column half
     unsigned char *sm = tc_smem;
     const uint32_t sbase = smem_u32(sm);
 
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(128, 4) k_mlp_infer_tc(const float *P, const f
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = S.tmem_base;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;   // a warp reads lanes 32 (warp % 4) + [0, 32)
     const uint32_t row_addr = tmem + lane_base;
     uint32_t phase = 0;
 
@@ -179,28 +185,24 @@ __global__ void __launch_bounds__(128, 4) k_mlp_infer_tc(const float *P, const f
     };
 
     const int ntiles = (N + TC_M - 1) / TC_M;
+    const int c0h = 32 * ch;   // this thread's first column of a 64-column accumulator
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int i = tile * TC_M + tid;
+        const int i = tile * TC_M + row;
         const bool valid = i < N;
-        // X = (G - mu) / sd  (BF16), zeros past the end
+        // X = (G - mu) / sd  (BF16), zeros past the end: features 8 ch + [0, 8)
         {
-            float g[16];
+            float x[8];
             if (valid) {
-                const float4 *gp = reinterpret_cast<const float4 *>(G + (size_t)i * 16);
+                const float4 *gp = reinterpret_cast<const float4 *>(G + (size_t)i * 16 + 8 * ch);
+                const float4 u = __ldg(gp), v = __ldg(gp + 1);
+                const float g[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    float4 v = __ldg(gp + k);
-                    g[4 * k] = v.x;
-                    g[4 * k + 1] = v.y;
-                    g[4 * k + 2] = v.z;
-                    g[4 * k + 3] = v.w;
-                }
+                for (int q = 0; q < 8; ++q) x[q] = (g[q] - S.mu[8 * ch + q]) * S.isd[8 * ch + q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) x[q] = 0.0f;
             }
-            float x[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) x[q] = valid ? (g[q] - S.mu[q]) * S.isd[q] : 0.0f;
-            tc_row8(sm, SM_X, tid, 0, 16, x);
-            tc_row8(sm, SM_X, tid, 8, 16, x + 8);
+            tc_row8(sm, SM_X, row, 8 * ch, 16, x);
         }
         fence_async_smem();
         tc_before_sync();
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(128, 4) k_mlp_infer_tc(const float *P, const f
         wait_mma();
         // h1 = silu(D1 + b1) -> H1
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
+        for (int c0 = c0h; c0 < c0h + 32; c0 += 16) {
             float d[16], h[16];
             tmem_ld16(row_addr + TC_D1 + c0, d);
 #pragma unroll
@@ -217,8 +219,8 @@ __global__ void __launch_bounds__(128, 4) k_mlp_infer_tc(const float *P, const f
                 float a = d[k] + S.b1[c0 + k];
                 h[k] = a * sgm(a);
             }
-            tc_row8(sm, SM_A, tid, c0, 64, h);
-            tc_row8(sm, SM_A, tid, c0 + 8, 64, h + 8);
+            tc_row8(sm, SM_A, row, c0, 64, h);
+            tc_row8(sm, SM_A, row, c0 + 8, 64, h + 8);
         }
         fence_async_smem();
         tc_before_sync();
@@ -226,9 +228,9 @@ __global__ void __launch_bounds__(128, 4) k_mlp_infer_tc(const float *P, const f
         issue(2);
         wait_mma();
         // a2 = D2 + b2; E = w3 . silu(a2) + b3; G2 = w3 * silu'(a2)
-        float E = S.b3;
+        float E = 0.0f;
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
+        for (int c0 = c0h; c0 < c0h + 32; c0 += 16) {
             float d[16], g2[16];
             tmem_ld16(row_addr + TC_D2 + c0, d);
 #pragma unroll
@@ -238,18 +240,19 @@ __global__ void __launch_bounds__(128, 4) k_mlp_infer_tc(const float *P, const f
                 E += S.w3[c0 + k] * a * s;
                 g2[k] = S.w3[c0 + k] * s * (1.0f + a * (1.0f - s));
             }
-            tc_row8(sm, SM_A, tid, c0, 64, g2);
-            tc_row8(sm, SM_A, tid, c0 + 8, 64, g2 + 8);
+            tc_row8(sm, SM_A, row, c0, 64, g2);
+            tc_row8(sm, SM_A, row, c0 + 8, 64, g2 + 8);
         }
-        if (valid) Ei[i] = E;
+        if (ch) S.Eh[row] = E;
         fence_async_smem();
         tc_before_sync();
         __syncthreads();
         issue(3);
+        if (!ch && valid) Ei[i] = S.b3 + E + S.Eh[row];
         wait_mma();
         // G1 = D3 * silu'(D1 + b1)
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
+        for (int c0 = c0h; c0 < c0h + 32; c0 += 16) {
             float d3[16], d1[16], g1[16];
             tmem_ld16(row_addr + TC_D3 + c0, d3);
             tmem_ld16(row_addr + TC_D1 + c0, d1);
@@ -259,24 +262,25 @@ __global__ void __launch_bounds__(128, 4) k_mlp_infer_tc(const float *P, const f
                 float s = sgm(a);
                 g1[k] = d3[k] * s * (1.0f + a * (1.0f - s));
             }
-            tc_row8(sm, SM_A, tid, c0, 64, g1);
-            tc_row8(sm, SM_A, tid, c0 + 8, 64, g1 + 8);
+            tc_row8(sm, SM_A, row, c0, 64, g1);
+            tc_row8(sm, SM_A, row, c0 + 8, 64, g1 + 8);
         }
         fence_async_smem();
         tc_before_sync();
         __syncthreads();
         issue(4);
         wait_mma();
-        // dE/dG = D4 / sd
+        // dE/dG = D4 / sd: features 8 ch + [0, 8) (both halves load the 16
+        // columns: tcgen05.ld is warp-wide)
         {
             float d[16];
             tmem_ld16(row_addr + TC_D4, d);
             if (valid) {
-                float4 *o = reinterpret_cast<float4 *>(dEdG + (size_t)i * 16);
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    o[k] = make_float4(d[4 * k] * S.isd[4 * k], d[4 * k + 1] * S.isd[4 * k + 1],
-                                       d[4 * k + 2] * S.isd[4 * k + 2], d[4 * k + 3] * S.isd[4 * k + 3]);
+                float4 *o = reinterpret_cast<float4 *>(dEdG + (size_t)i * 16 + 8 * ch);
+                const float *dh = d + 8 * ch;
+                const float *sh = S.isd + 8 * ch;
+                o[0] = make_float4(dh[0] * sh[0], dh[1] * sh[1], dh[2] * sh[2], dh[3] * sh[3]);
+                o[1] = make_float4(dh[4] * sh[4], dh[5] * sh[5], dh[6] * sh[6], dh[7] * sh[7]);
             }
         }
         tc_before_sync();
@@ -304,7 +308,7 @@ void enqueue_mlp_infer_tc(const float *P, const float *norm, const float *G, int
     // columns; the grid never exceeds four per SM, so no allocation waits
     int tiles = (N + TC_M - 1) / TC_M;
     int g = tiles < 4 * sms ? tiles : 4 * sms;
-    k_mlp_infer_tc<<<g, 128, SM_LAUNCH, st>>>(P, norm, G, N, Ei, dEdG, status);
+    k_mlp_infer_tc<<<g, TC_THREADS, SM_LAUNCH, st>>>(P, norm, G, N, Ei, dEdG, status);
 }
 
 }  // namespace jmd
