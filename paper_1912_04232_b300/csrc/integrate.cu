@@ -150,24 +150,36 @@ __global__ void __launch_bounds__(1024) k_nhc_begin(const float4 *v, int N, floa
 // The next kick-drift applies both velocity factors (the closing one alone
 // at the end of the loop); the series get the thermostatted state.  The
 // force kernel has already advanced the step counter.
-// The chain works on a shared-memory copy of its state: its dependent FP64
-// updates then read and write shared memory instead of making a round trip
-// to the L2 for every value (the same operations, the same bits).
+// The chain's scalars are held in registers (the chain length is a
+// compile-time constant of the unrolled code) and the reciprocal masses are
+// taken once for both half-steps.
 __global__ void k_nhc_update(double *nhc_g, int M, const uint32_t *ctl, double *KE_out, double *H_out)
 {
     count_launch();
-    __shared__ double nhc[nhc_words(NHC_MAXM)];
-    const int nw = nhc_words(M);
-    for (int k = 0; k < nw; ++k) nhc[k] = nhc_g[k];
-    double *c = nhc + 3 * M;
+    double *c = nhc_g + 3 * M;
     const unsigned step = ctl[CTL_STEP] - 1u;
-    double K = c[NHC_KRAW];
-    c[NHC_SCLOSE] = nhc_half_step(nhc, M, K);
-    c[NHC_K] = K;
-    if (KE_out) KE_out[step] = K;
-    if (H_out) H_out[step] = c[NHC_PE] + K + nhc_energy(nhc, M);
-    c[NHC_SOPEN] = (step + 1u < ctl[CTL_NSTEPS]) ? nhc_half_step(nhc, M, K) : 1.0;
-    for (int k = 0; k < nw; ++k) nhc_g[k] = nhc[k];
+    const double gkT = c[NHC_GKT], kT = c[NHC_KT], dt = c[NHC_DT], pe = c[NHC_PE];
+    const bool more = step + 1u < ctl[CTL_NSTEPS];
+    double K = c[NHC_KRAW], sclose = 1.0, sopen = 1.0, H = 0.0;
+    nhc_dispatch(M, [&](auto m) {
+        constexpr int MM = decltype(m)::value;
+        nhc_with_state<MM>(nhc_g, [&](double *xi, double *w, const double *Q, const double *iQ) {
+            sclose = nhc_half_step_m<MM>(xi, w, Q, iQ, gkT, kT, dt, K);
+            // the extended energy after the closing half-step
+            double e = gkT * xi[0];
+#pragma unroll
+            for (int k = 0; k < MM; ++k) e += 0.5 * Q[k] * w[k] * w[k];
+#pragma unroll
+            for (int k = 1; k < MM; ++k) e += kT * xi[k];
+            H = pe + K + e;
+            if (KE_out) KE_out[step] = K;
+            if (H_out) H_out[step] = H;
+            c[NHC_K] = K;
+            if (more) sopen = nhc_half_step_m<MM>(xi, w, Q, iQ, gkT, kT, dt, K);
+        });
+    });
+    c[NHC_SCLOSE] = sclose;
+    c[NHC_SOPEN] = sopen;
 }
 
 // After the loop: the last step's closing velocity factor.
