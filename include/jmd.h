@@ -262,9 +262,19 @@ typedef struct {
     float alpha;
     /* MD_SW: {eps, sigma, a, lambda, gamma, A, B, p, q, cos0}; cutoff a*sigma. */
     float sw[10];
-    /* MD_BP: pointer to an md_bp_model; MD_GNN: pointer to an md_gnn_model. */
+    /* MD_BP: pointer to an md_bp_model; MD_GNN: pointer to an md_gnn_model.
+     * MD_SW: NULL, or device scratch of md_sw_lists_bytes(N) bytes (256-byte
+     * aligned, caller-owned, contents scratch) for the list's N atoms.  With
+     * it each evaluation first stores every atom's partners inside a*sigma
+     * (at most 32; more raise MD_ERR_NBR_OVERFLOW) and the triplets centred
+     * on a neighbor visit only that neighbor's stored partners; without it
+     * one kernel tests the neighbors' whole rows.  Both give the same terms;
+     * their FP32 sums may differ in the last bits (another summation order). */
     const void *model;
 } md_pot;
+
+/* Bytes of the MD_SW partner-list scratch for N atoms (0 if N < 1). */
+JMD_API size_t md_sw_lists_bytes(int N);
 
 /* Learned potential (MD_BP, Sec. 3.2.4 and 4.1): Behler-Parrinello
  * symmetry functions (8 radial, 8 angular; cutoff 3.77 A) feeding a per-atom

@@ -270,6 +270,24 @@ struct WsLayout {
 
 __host__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Partner lists of the three-body potentials (caller-owned scratch): per
+// atom the count of partners inside the potential's cutoff, their indices
+// and displacement vectors (dx, dy, dz, r) = r_j - r_i, S slots per atom, in
+// the order of the atom's neighbor row.
+struct TbLayout {
+    size_t cnt, idx, vec, bytes;
+};
+__host__ inline TbLayout tb_layout(int N, int S)
+{
+    TbLayout t;
+    size_t o = 0;
+    t.cnt = o;  o = align256(o + sizeof(int32_t) * (size_t)N);
+    t.idx = o;  o = align256(o + sizeof(int32_t) * (size_t)N * S);
+    t.vec = o;  o = align256(o + 4 * sizeof(float) * (size_t)N * S);
+    t.bytes = o;
+    return t;
+}
+
 // Scratch of the tile engine (MD_NBR_TILES), offsets from its own start.
 // nhc = half-cells (2 x 2 x 2 per cell of the list's grid).
 constexpr int TSCAN_ITEMS = 4096;       // half-cells per block of the histogram scan

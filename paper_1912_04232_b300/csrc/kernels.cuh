@@ -47,6 +47,10 @@ struct PairArgs {
     float eps, alpha;
     // Stillinger-Weber {eps, sigma, a, lambda, gamma, A, B, p, q, cos0, rc, rc2}
     float sw[12];
+    // Stillinger-Weber partner lists (tb_layout, SW_MAXN slots; null: the
+    // force kernel tests the neighbors' rows itself)
+    int32_t *tb_cnt, *tb_idx;
+    float4 *tb_vec;
     // learned potential: network and per-atom scratch (device pointers)
     const float *bp_params, *bp_norm;
     float *bp_G, *bp_dEdG, *bp_Ei;
@@ -131,6 +135,8 @@ void enqueue_pair(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st
 // Force evaluation for any supported potential (pair kernels or SW).
 void enqueue_forces(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st);
 void enqueue_sw(const PairArgs &a, int kick, cudaStream_t st);
+constexpr int SW_LIST_SLOTS = 32;   // partners inside a*sigma kept per atom (more: overflow)
+size_t sw_lists_bytes(int N);       // partner-list scratch of N atoms (tb_layout)
 void enqueue_bp_step(const PairArgs &a, int kick, cudaStream_t st);
 void enqueue_gnn_step(const PairArgs &a, int kick, cudaStream_t st);
 bool gnn_model_ok(const md_gnn_model *m, const md_nbr *nb);

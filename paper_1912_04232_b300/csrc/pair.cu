@@ -521,6 +521,14 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
         if (rc > nb->r_list) return false;
         a.sw[10] = rc;
         a.sw[11] = rc * rc;
+        if (p->model) {   // partner-list scratch of md_sw_lists_bytes(N) bytes
+            unsigned char *b = (unsigned char *)p->model;
+            if (((uintptr_t)b & 255u) != 0u) return false;
+            const TbLayout t = tb_layout(nb->N, SW_LIST_SLOTS);
+            a.tb_cnt = (int32_t *)(b + t.cnt);
+            a.tb_idx = (int32_t *)(b + t.idx);
+            a.tb_vec = (float4 *)(b + t.vec);
+        }
     }
     return pair_blocks(a.N, a.tpp) <= w.max_blocks;
 }
@@ -528,6 +536,8 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
 }  // namespace jmd
 
 using namespace jmd;
+
+extern "C" size_t md_sw_lists_bytes(int N) { return N > 0 ? sw_lists_bytes(N) : 0; }
 
 extern "C" md_status md_set_pair_options(int opt)
 {

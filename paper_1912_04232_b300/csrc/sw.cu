@@ -13,13 +13,18 @@
 //       candidates of (3) inside a*sigma are queued in shared memory first
 //       and then evaluated together with every lane busy.
 // e_i = 1/2 sum_j phi2(r_ij) + sum_{j<k} phi3(i; j, k), so sum_i e_i = E.
+// With partner-list scratch (md_sw_lists_bytes), k_sw_lists first stores
+// every atom's partners inside a*sigma (index and r_j - r_i, in row order)
+// and k_sw reads them: for (3) it then visits only the neighbors' partners
+// inside a*sigma instead of testing their whole rows (about a fifth of the
+// entries in silicon at a 0.3 A skin), with the same vectors, bit for bit.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
 
 namespace jmd {
 
-constexpr int SW_MAXN = 32;   // neighbors inside a*sigma kept per atom
+constexpr int SW_MAXN = SW_LIST_SLOTS;   // neighbors inside a*sigma kept per atom
 constexpr int SW_WARPS = 8;
 
 struct SwP {
@@ -128,7 +133,57 @@ constexpr int SW_QG = 32;                // queued triplets per atom between eva
 // atom has about five partners inside a*sigma).  Every lane of a warp runs
 // every trip of every loop (group ballots, scans and sums are warp-wide);
 // a queue is evaluated when any group's would overflow.
-template <int KICK>
+// Partner lists (pass 1 of the two-kernel form): the atom's row entries
+// inside a*sigma, compacted by a group ballot in row order.
+__global__ void __launch_bounds__(SW_WARPS * 32) k_sw_lists(PairArgs a)
+{
+    count_launch();
+    const SwP P = sw_params(a);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / SW_G, gl = lane % SW_G;
+    const unsigned gmask = ((1u << SW_G) - 1u) << (grp * SW_G);
+    const unsigned below = (1u << lane) - 1u;
+    const int step = gridDim.x * SW_WARPS * SW_PER_WARP;
+    for (int i0 = (blockIdx.x * SW_WARPS + w) * SW_PER_WARP; i0 < a.N; i0 += step) {
+        const int i = i0 + grp;
+        const bool valid = i < a.N;
+        const float4 ri = valid ? a.r[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        int n = 0;
+        const int32_t *row = a.nbr + (size_t)(valid ? i : 0) * a.cap;
+        if (valid) n = min(a.cnt[i], a.cap);
+        int32_t *oi = a.tb_idx + (size_t)i * SW_MAXN;
+        float4 *ov = a.tb_vec + (size_t)i * SW_MAXN;
+        const int nmax = __reduce_max_sync(0xffffffffu, n);
+        int m = 0;
+        for (int k0 = 0; k0 < nmax; k0 += SW_G) {
+            const int k = k0 + gl;
+            bool in = false;
+            int j = 0;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+            if (k < n) {
+                j = row[k];
+                const float4 rj = __ldg(a.r + j);
+                r2 = dist2_rn<3>(rj, ri, a.box, dx, dy, dz);   // u = r_j - r_i
+                in = r2 < P.rc2;
+            }
+            const unsigned mk = __ballot_sync(0xffffffffu, in) & gmask;
+            const int pos = m + __popc(mk & below);
+            if (in && pos < SW_MAXN) {
+                oi[pos] = j;
+                ov[pos] = make_float4(dx, dy, dz, sqrtf(r2));
+            }
+            m += __popc(mk);
+        }
+        if (valid && gl == 0) {
+            if (m > SW_MAXN) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
+            a.tb_cnt[i] = min(m, SW_MAXN);
+        }
+    }
+}
+
+// LISTS 1: the partners come from k_sw_lists (this atom's and its
+// neighbors'); LISTS 0: from the neighbor rows, tested here.
+template <int KICK, int LISTS>
 __global__ void __launch_bounds__(SW_WARPS * 32, 4) k_sw(PairArgs a)
 {
     count_launch();
@@ -158,8 +213,15 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 4) k_sw(PairArgs a)
         const int32_t *row = a.nbr + (size_t)(valid ? i : 0) * a.cap;
         if (valid) n = min(a.cnt[i], a.cap);
         // (0) neighbors inside a*sigma, compacted into the group's list
-        const int nmax = __reduce_max_sync(0xffffffffu, n);
+        const int nmax = LISTS ? 0 : __reduce_max_sync(0xffffffffu, n);
         int m = 0;
+        if (LISTS) {
+            if (valid) m = a.tb_cnt[i];
+            for (int s = gl; s < m; s += SW_G) {
+                njg[s] = a.tb_idx[(size_t)i * SW_MAXN + s];
+                ndg[s] = a.tb_vec[(size_t)i * SW_MAXN + s];
+            }
+        }
         for (int k0 = 0; k0 < nmax; k0 += SW_G) {
             const int k = k0 + gl;
             bool in = false;
@@ -240,7 +302,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 4) k_sw(PairArgs a)
         for (int s0 = 0; s0 < mmax; s0 += SW_G) {   // exclusive prefix of the neighbors' row lengths
             const int s = s0 + gl;
             int nn = 0;
-            if (s < m) nn = min(a.cnt[njg[s]], a.cap);
+            if (s < m) nn = LISTS ? a.tb_cnt[njg[s]] : min(a.cnt[njg[s]], a.cap);
             int incl = nn;
 #pragma unroll
             for (int o = 1; o < SW_G; o <<= 1) {
@@ -267,13 +329,22 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 4) k_sw(PairArgs a)
                 }
                 s = lo;
                 const int j = njg[s];
-                const int kk = a.nbr[(size_t)j * a.cap + (it - qp[s])];
-                if (kk != i) {
-                    const float4 rj = __ldg(a.r + j), rk = __ldg(a.r + kk);
-                    float wx, wy, wz;
-                    const float w2 = dist2_rn<3>(rk, rj, a.box, wx, wy, wz);
-                    in = w2 < P.rc2;
-                    wv = make_float4(wx, wy, wz, sqrtf(w2));
+                if (LISTS) {
+                    // j's partner inside a*sigma, with w' = r_k - r_j as k_sw_lists computed it
+                    const size_t e = (size_t)j * SW_MAXN + (it - qp[s]);
+                    if (a.tb_idx[e] != i) {
+                        wv = a.tb_vec[e];
+                        in = true;
+                    }
+                } else {
+                    const int kk = a.nbr[(size_t)j * a.cap + (it - qp[s])];
+                    if (kk != i) {
+                        const float4 rj = __ldg(a.r + j), rk = __ldg(a.r + kk);
+                        float wx, wy, wz;
+                        const float w2 = dist2_rn<3>(rk, rj, a.box, wx, wy, wz);
+                        in = w2 < P.rc2;
+                        wv = make_float4(wx, wy, wz, sqrtf(w2));
+                    }
                 }
             }
             enqueue(in, s, SW_LEG, wv);
@@ -298,27 +369,44 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 4) k_sw(PairArgs a)
     energy_epilogue(pe_acc, ke_acc, a);
 }
 
-template <int KICK>
-static int sw_grid(int N)
+template <class K>
+static int sw_grid(K kern, int N)
 {
-    static int per_sm = 0, sms = 0;
-    if (!per_sm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sw<KICK>, SW_WARPS * 32, 0);
-        if (per_sm < 1) per_sm = 1;
-        if (sms < 1) sms = 1;
-    }
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SW_WARPS * 32, 0);
+    if (per_sm < 1) per_sm = 1;
+    if (sms < 1) sms = 1;
     int groups = (N + SW_WARPS * SW_PER_WARP - 1) / (SW_WARPS * SW_PER_WARP);
     int g = per_sm * sms;
     return groups < g ? groups : g;
 }
 
+template <int KICK, int LISTS>
+static void launch_sw(const PairArgs &a, cudaStream_t st)
+{
+    static int g_full = 0;   // resident CTAs of the whole GPU (occupancy x SMs), first launch
+    if (!g_full) g_full = sw_grid(k_sw<KICK, LISTS>, 1 << 30);
+    const int groups = (a.N + SW_WARPS * SW_PER_WARP - 1) / (SW_WARPS * SW_PER_WARP);
+    k_sw<KICK, LISTS><<<groups < g_full ? groups : g_full, SW_WARPS * 32, 0, st>>>(a);
+}
+
 void enqueue_sw(const PairArgs &a, int kick, cudaStream_t st)
 {
-    if (kick) k_sw<1><<<sw_grid<1>(a.N), SW_WARPS * 32, 0, st>>>(a);
-    else k_sw<0><<<sw_grid<0>(a.N), SW_WARPS * 32, 0, st>>>(a);
+    if (a.tb_cnt) {
+        static int g_lists = 0;
+        if (!g_lists) g_lists = sw_grid(k_sw_lists, 1 << 30);
+        const int groups = (a.N + SW_WARPS * SW_PER_WARP - 1) / (SW_WARPS * SW_PER_WARP);
+        k_sw_lists<<<groups < g_lists ? groups : g_lists, SW_WARPS * 32, 0, st>>>(a);
+        if (kick) launch_sw<1, 1>(a, st);
+        else launch_sw<0, 1>(a, st);
+    } else {
+        if (kick) launch_sw<1, 0>(a, st);
+        else launch_sw<0, 0>(a, st);
+    }
 }
+
+size_t sw_lists_bytes(int N) { return tb_layout(N, SW_MAXN).bytes; }
 
 }  // namespace jmd

@@ -200,6 +200,8 @@ _lib.md_noalloc_scratch_bytes.restype = C.c_size_t
 _lib.md_noalloc_scratch_bytes.argtypes = []
 _lib.md_fire_state_bytes.restype = C.c_size_t
 _lib.md_fire_state_bytes.argtypes = []
+_lib.md_sw_lists_bytes.restype = C.c_size_t
+_lib.md_sw_lists_bytes.argtypes = [C.c_int]
 _lib.md_nhc_state_doubles.restype = C.c_size_t
 _lib.md_nhc_state_doubles.argtypes = [C.c_int]
 _lib.md_gnn_param_count.restype = C.c_size_t
@@ -702,11 +704,23 @@ def soft_pot(eps=1.0, alpha=2.0) -> md_pot:
     return p
 
 
-def sw_pot(params) -> md_pot:
+def md_sw_lists_bytes(N: int) -> int:
+    return int(_lib.md_sw_lists_bytes(int(N)))
+
+
+def sw_pot(params, N=None, device="cuda") -> md_pot:
+    """Stillinger-Weber potential; with N, the partner-list scratch for N
+    atoms is allocated (torch, kept alive by the returned struct) and the
+    two-kernel form is used."""
     p = md_pot()
     p.kind = MD_SW
     for k, v in enumerate(params):
         p.sw[k] = float(v)
+    if N is not None:
+        import torch
+        p._lists = torch.empty(md_sw_lists_bytes(N) + 256, dtype=torch.uint8, device=device)
+        base = p._lists.data_ptr()
+        p.model = (base + 255) // 256 * 256
     return p
 
 

@@ -20,7 +20,7 @@ def P():
     return P
 
 
-def _forces(P, r, L, cap=64):
+def _forces(P, r, L, cap=64, lists=False):
     import torch
     s = P.md_space_periodic(3, [L] * 3)
     nl = P.NeighborList(s, r.shape[0], RC, SKIN, cap)
@@ -29,20 +29,35 @@ def _forces(P, r, L, cap=64):
     nl.build(rd, st)
     f = torch.zeros((r.shape[0], 4), dtype=torch.float32, device=dev())
     E = torch.zeros(1, dtype=torch.float64, device=dev())
-    P.md_energy_forces(s, P.sw_pot(O.SW_SI), rd, nl.plan, f, E, st)
+    pot = P.sw_pot(O.SW_SI, N=r.shape[0]) if lists else P.sw_pot(O.SW_SI)
+    P.md_energy_forces(s, pot, rd, nl.plan, f, E, st)
     torch.cuda.synchronize()
     assert P.md_status_poll(st) == 0
     return f.cpu().numpy(), E.item()
 
 
+@pytest.mark.parametrize("lists", [False, True])
 @pytest.mark.parametrize("n_side,jitter,seed", [(4, 0.15, 1), (4, 0.35, 2), (3, 0.25, 3), (20, 0.2, 4)])
-def test_sw_forces_energy_match_oracle(P, n_side, jitter, seed):
+def test_sw_forces_energy_match_oracle(P, n_side, jitter, seed, lists):
+    # lists: the two-kernel form (partners inside a*sigma stored first)
     si = W.sw_silicon(n_side, T_K=0, jitter=jitter, seed=seed)
-    f, E = _forces(P, si.r, si.L)
+    f, E = _forces(P, si.r, si.L, lists=lists)
     U, F, e = O.sw(si.r, si.L)
     assert force_error(f, F) <= 1e-4
     np.testing.assert_allclose(f[:, 3], e, rtol=0, atol=2e-5 * np.abs(e).max())
     assert abs(E - U) <= 1e-5 * abs(U)
+
+
+def test_sw_partner_lists_give_the_same_terms(P):
+    # the same triplets with the same FP32 vectors: the two forms differ
+    # only by the order in which each atom's terms are summed
+    si = W.sw_silicon(6, T_K=0, jitter=0.3, seed=5)
+    f0, E0 = _forces(P, si.r, si.L, lists=False)
+    f1, E1 = _forces(P, si.r, si.L, lists=True)
+    scale = np.abs(f0[:, :3]).max()
+    assert np.abs(f1[:, :3] - f0[:, :3]).max() <= 2e-6 * scale
+    np.testing.assert_allclose(f1[:, 3], f0[:, 3], rtol=0, atol=2e-6 * np.abs(f0[:, 3]).max())
+    assert abs(E1 - E0) <= 1e-6 * abs(E0)
 
 
 def test_sw_diamond_cohesive_energy(P):
@@ -52,7 +67,8 @@ def test_sw_diamond_cohesive_energy(P):
     assert np.abs(f[:, :3]).max() < 1e-3
 
 
-def test_sw_nve_short_trajectory_matches_oracle(P):
+@pytest.mark.parametrize("lists", [False, True])
+def test_sw_nve_short_trajectory_matches_oracle(P, lists):
     import torch
     si = W.sw_silicon(4, T_K=1500, jitter=0.1, seed=7)
     s = P.md_space_periodic(3, [si.L] * 3)
@@ -61,7 +77,7 @@ def test_sw_nve_short_trajectory_matches_oracle(P):
     vd = to_dev(si.v, torch.float32)
     f = torch.zeros((si.N, 4), dtype=torch.float32, device=dev())
     st = status_word()
-    pot = P.sw_pot(O.SW_SI)
+    pot = P.sw_pot(O.SW_SI, N=si.N) if lists else P.sw_pot(O.SW_SI)
     nl.build(rd, st)
     P.md_energy_forces(s, pot, rd, nl.plan, f, None, st)
     n, dt = 20, 1.0
