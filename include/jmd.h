@@ -287,7 +287,15 @@ typedef struct {
     float *dEdG;          /* [N][16] scratch: network input gradient */
     float *Ei;            /* [N] scratch: per-atom energies */
     int sys_n;            /* 0, or atoms per system for concatenated equal-size systems */
+    void *lists;          /* NULL, or scratch of md_bp_lists_bytes(N) bytes (256-byte aligned): the
+                             descriptor kernel then stores every atom's partners inside R_c (at most
+                             48; more raise MD_ERR_NBR_OVERFLOW) and the force gather visits only the
+                             neighbors' stored partners for the triplets centred on them (the same
+                             terms; FP32 sums may differ in the last bits) */
 } md_bp_model;
+
+/* Bytes of the md_bp_model partner-list scratch for N atoms (0 if N < 1). */
+JMD_API size_t md_bp_lists_bytes(int N);
 
 /* Graph-network potential (MD_GNN; Sec. 3.2.4: GraphNet blocks as in the
  * glass network of Bapst et al.; Sec. 4.1: trained on energies and forces,

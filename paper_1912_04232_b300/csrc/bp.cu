@@ -22,7 +22,7 @@
 
 namespace jmd {
 
-constexpr int BP_MAXN = 48;   // neighbors inside R_c kept per atom
+constexpr int BP_MAXN = BP_LIST_SLOTS;   // neighbors inside R_c kept per atom
 constexpr int BP_WARPS = 8;
 
 struct BpConst {
@@ -259,7 +259,9 @@ __device__ __forceinline__ float warp_sum(float v)
 // the group sweeps the atom's row DESC_GROUP entries at a time, compacts the
 // partners inside R_c (group ballot) into its own shared list, then takes
 // the pairs and the triplets (s1 < s2, enumerated without the s1 >= s2
-// slots) over its lanes and sums G over the group.
+// slots) over its lanes and sums G over the group.  With partner-list
+// scratch it also stores the list (index and r_j - r_i, in row order) for
+// the force kernel.
 constexpr int DESC_GROUP = 8;
 constexpr int DESC_PER_WARP = 32 / DESC_GROUP;
 
@@ -301,13 +303,21 @@ __global__ void __launch_bounds__(BP_WARPS * 32) k_bp_desc(BpArgs a)
             }
             const unsigned mk = __ballot_sync(0xffffffffu, in) & gmask;
             const int pos = m + __popc(mk & below);
-            if (in && pos < BP_MAXN) ndg[pos] = make_float4(dx, dy, dz, sqrtf(r2));
+            if (in && pos < BP_MAXN) {
+                const float4 u = make_float4(dx, dy, dz, sqrtf(r2));
+                ndg[pos] = u;
+                if (a.pa.tb_idx) {   // the partner lists of the force kernel
+                    a.pa.tb_idx[(size_t)i * BP_MAXN + pos] = row[k] + base;
+                    a.pa.tb_vec[(size_t)i * BP_MAXN + pos] = u;
+                }
+            }
             m += __popc(mk);
         }
         if (m > BP_MAXN) {
             if (gl == 0) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
             m = BP_MAXN;
         }
+        if (a.pa.tb_cnt && valid && gl == 0) a.pa.tb_cnt[i] = m;
         __syncwarp();
         float G[16];
 #pragma unroll
@@ -409,7 +419,9 @@ constexpr int BPF_QG = 24;                 // queued triplets per atom between e
 // silicon atom has about five partners inside R_c).  Every lane of a warp
 // runs every trip of every loop (group ballots, scans and sums are
 // warp-wide); a queue is evaluated when any group's would overflow.
-template <int KICK>
+// LISTS 1: the partners come from the lists k_bp_desc stored (this atom's
+// and its neighbors'); LISTS 0: from the neighbor rows, tested here.
+template <int KICK, int LISTS>
 __global__ void __launch_bounds__(BP_WARPS * 32, 4) k_bp_force(BpArgs a)
 {
     count_launch();
@@ -442,8 +454,15 @@ __global__ void __launch_bounds__(BP_WARPS * 32, 4) k_bp_force(BpArgs a)
             base = a.sys_n ? (k / a.sys_n) * a.sys_n : 0;
         }
         // partners inside R_c, compacted into the group's list
-        const int nmax = __reduce_max_sync(0xffffffffu, n);
+        const int nmax = LISTS ? 0 : __reduce_max_sync(0xffffffffu, n);
         int m = 0;
+        if (LISTS) {
+            if (valid) m = a.pa.tb_cnt[k];
+            for (int s = gl; s < m; s += BPF_G) {
+                njg[s] = a.pa.tb_idx[(size_t)k * BP_MAXN + s];
+                ndg[s] = a.pa.tb_vec[(size_t)k * BP_MAXN + s];
+            }
+        }
         for (int c0 = 0; c0 < nmax; c0 += BPF_G) {
             const int kk = c0 + gl;
             bool in = false;
@@ -530,7 +549,7 @@ __global__ void __launch_bounds__(BP_WARPS * 32, 4) k_bp_force(BpArgs a)
         for (int s0 = 0; s0 < mmax; s0 += BPF_G) {   // exclusive prefix of the neighbors' row lengths
             const int s = s0 + gl;
             int nn = 0;
-            if (s < m) nn = min(a.cnt[njg[s]], a.cap);
+            if (s < m) nn = LISTS ? a.pa.tb_cnt[njg[s]] : min(a.cnt[njg[s]], a.cap);
             int incl = nn;
 #pragma unroll
             for (int o = 1; o < BPF_G; o <<= 1) {
@@ -557,14 +576,23 @@ __global__ void __launch_bounds__(BP_WARPS * 32, 4) k_bp_force(BpArgs a)
                 }
                 s = lo;
                 const int j = njg[s];
-                const int basej = a.sys_n ? (j / a.sys_n) * a.sys_n : 0;
-                const int l = a.nbr[(size_t)j * a.cap + (it - qp[s])] + basej;
-                if (l != k) {
-                    const float4 rj = __ldg(a.r + j), rl = __ldg(a.r + l);
-                    float wx, wy, wz;
-                    const float w2 = dist2_rn<3>(rl, rj, a.box, wx, wy, wz);
-                    in = w2 < c.rc2;
-                    wv = make_float4(wx, wy, wz, sqrtf(w2));
+                if (LISTS) {
+                    // j's partner inside R_c, with w' = r_l - r_j as k_bp_desc computed it
+                    const size_t e = (size_t)j * BP_MAXN + (it - qp[s]);
+                    if (a.pa.tb_idx[e] != k) {
+                        wv = a.pa.tb_vec[e];
+                        in = true;
+                    }
+                } else {
+                    const int basej = a.sys_n ? (j / a.sys_n) * a.sys_n : 0;
+                    const int l = a.nbr[(size_t)j * a.cap + (it - qp[s])] + basej;
+                    if (l != k) {
+                        const float4 rj = __ldg(a.r + j), rl = __ldg(a.r + l);
+                        float wx, wy, wz;
+                        const float w2 = dist2_rn<3>(rl, rj, a.box, wx, wy, wz);
+                        in = w2 < c.rc2;
+                        wv = make_float4(wx, wy, wz, sqrtf(w2));
+                    }
                 }
             }
             enqueue(in, s, BP_LEG, wv);
@@ -664,8 +692,13 @@ void enqueue_bp_desc(const BpArgs &a, cudaStream_t st)
 void enqueue_bp_force(const BpArgs &a, int kick, cudaStream_t st)
 {
     const int g = bp_grid((a.N + BPF_PER_WARP - 1) / BPF_PER_WARP);
-    if (kick) k_bp_force<1><<<g, BP_WARPS * 32, 0, st>>>(a);
-    else k_bp_force<0><<<g, BP_WARPS * 32, 0, st>>>(a);
+    if (a.pa.tb_cnt) {
+        if (kick) k_bp_force<1, 1><<<g, BP_WARPS * 32, 0, st>>>(a);
+        else k_bp_force<0, 1><<<g, BP_WARPS * 32, 0, st>>>(a);
+    } else {
+        if (kick) k_bp_force<1, 0><<<g, BP_WARPS * 32, 0, st>>>(a);
+        else k_bp_force<0, 0><<<g, BP_WARPS * 32, 0, st>>>(a);
+    }
 }
 
 void enqueue_bp_jvp(const BpArgs &a, cudaStream_t st) { k_bp_jvp<<<bp_grid(a.N), BP_WARPS * 32, 0, st>>>(a); }

@@ -47,7 +47,8 @@ struct PairArgs {
     float eps, alpha;
     // Stillinger-Weber {eps, sigma, a, lambda, gamma, A, B, p, q, cos0, rc, rc2}
     float sw[12];
-    // Stillinger-Weber partner lists (tb_layout, SW_MAXN slots; null: the
+    // three-body partner lists (tb_layout; SW_LIST_SLOTS slots for
+    // Stillinger-Weber, BP_LIST_SLOTS for the learned potential; null: the
     // force kernel tests the neighbors' rows itself)
     int32_t *tb_cnt, *tb_idx;
     float4 *tb_vec;
@@ -136,6 +137,7 @@ void enqueue_pair(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st
 void enqueue_forces(const PairArgs &a, int dim, int pot, int kick, cudaStream_t st);
 void enqueue_sw(const PairArgs &a, int kick, cudaStream_t st);
 constexpr int SW_LIST_SLOTS = 32;   // partners inside a*sigma kept per atom (more: overflow)
+constexpr int BP_LIST_SLOTS = 48;   // partners inside R_c kept per atom by the learned potential
 size_t sw_lists_bytes(int N);       // partner-list scratch of N atoms (tb_layout)
 void enqueue_bp_step(const PairArgs &a, int kick, cudaStream_t st);
 void enqueue_gnn_step(const PairArgs &a, int kick, cudaStream_t st);

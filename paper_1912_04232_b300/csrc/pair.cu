@@ -515,6 +515,14 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
         a.bp_dEdG = m->dEdG;
         a.bp_Ei = m->Ei;
         a.bp_sys_n = m->sys_n;
+        if (m->lists) {   // partner-list scratch of md_bp_lists_bytes(N) bytes
+            unsigned char *b = (unsigned char *)m->lists;
+            if (((uintptr_t)b & 255u) != 0u) return false;
+            const TbLayout t = tb_layout(nb->N, BP_LIST_SLOTS);
+            a.tb_cnt = (int32_t *)(b + t.cnt);
+            a.tb_idx = (int32_t *)(b + t.idx);
+            a.tb_vec = (float4 *)(b + t.vec);
+        }
     } else {
         for (int k = 0; k < 10; ++k) a.sw[k] = p->sw[k];
         float rc = p->sw[2] * p->sw[1];   // a * sigma
@@ -538,6 +546,8 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
 using namespace jmd;
 
 extern "C" size_t md_sw_lists_bytes(int N) { return N > 0 ? sw_lists_bytes(N) : 0; }
+
+extern "C" size_t md_bp_lists_bytes(int N) { return N > 0 ? tb_layout(N, BP_LIST_SLOTS).bytes : 0; }
 
 extern "C" md_status md_set_pair_options(int opt)
 {

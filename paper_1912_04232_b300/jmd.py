@@ -67,7 +67,7 @@ class md_pot(C.Structure):
 
 class md_bp_model(C.Structure):
     _fields_ = [("params", C.c_void_p), ("norm", C.c_void_p), ("G", C.c_void_p), ("dEdG", C.c_void_p),
-                ("Ei", C.c_void_p), ("sys_n", C.c_int)]
+                ("Ei", C.c_void_p), ("sys_n", C.c_int), ("lists", C.c_void_p)]
 
 
 class md_gnn_model(C.Structure):
@@ -200,6 +200,8 @@ _lib.md_noalloc_scratch_bytes.restype = C.c_size_t
 _lib.md_noalloc_scratch_bytes.argtypes = []
 _lib.md_fire_state_bytes.restype = C.c_size_t
 _lib.md_fire_state_bytes.argtypes = []
+_lib.md_bp_lists_bytes.restype = C.c_size_t
+_lib.md_bp_lists_bytes.argtypes = [C.c_int]
 _lib.md_sw_lists_bytes.restype = C.c_size_t
 _lib.md_sw_lists_bytes.argtypes = [C.c_int]
 _lib.md_nhc_state_doubles.restype = C.c_size_t
@@ -485,14 +487,18 @@ class BPModel:
     points at them (kind MD_BP).  params [5313] and norm [32] are FP32 CUDA
     tensors owned by the caller."""
 
-    def __init__(self, params, norm, N, sys_n=0, device="cuda"):
+    def __init__(self, params, norm, N, sys_n=0, device="cuda", lists=True):
         import torch
         self.params, self.norm = params, norm
         self.G = torch.zeros((N, 16), dtype=torch.float32, device=device)
         self.dEdG = torch.zeros((N, 16), dtype=torch.float32, device=device)
         self.Ei = torch.zeros(N, dtype=torch.float32, device=device)
+        lp = None
+        if lists:   # partner-list scratch: the two-kernel triplet sweep of the force gather
+            self._lists = torch.empty(md_bp_lists_bytes(N) + 256, dtype=torch.uint8, device=device)
+            lp = (self._lists.data_ptr() + 255) // 256 * 256
         self.model = md_bp_model(_ptr(params).value, _ptr(norm).value, _ptr(self.G).value, _ptr(self.dEdG).value,
-                                 _ptr(self.Ei).value, int(sys_n))
+                                 _ptr(self.Ei).value, int(sys_n), lp)
         self.pot = md_pot()
         self.pot.kind = MD_BP
         self.pot.model = C.cast(C.pointer(self.model), C.c_void_p)
@@ -702,6 +708,10 @@ def soft_pot(eps=1.0, alpha=2.0) -> md_pot:
     p.kind = MD_SOFT_SPHERE
     p.eps, p.alpha = eps, alpha
     return p
+
+
+def md_bp_lists_bytes(N: int) -> int:
+    return int(_lib.md_bp_lists_bytes(int(N)))
 
 
 def md_sw_lists_bytes(N: int) -> int:

@@ -89,13 +89,15 @@ def _model(P, r, L, seed=0):
     return p, mu, sd, params, norm
 
 
+@pytest.mark.parametrize("lists", [False, True])
 @pytest.mark.parametrize("n_side,seed", [(2, 2), (4, 3)])
-def test_network_energy_and_forces_match_oracle(P, n_side, seed):
+def test_network_energy_and_forces_match_oracle(P, n_side, seed, lists):
+    # lists: the descriptor kernel stores the partner lists the force gather reads
     import torch
     r, L = _snapshot(n_side, seed)
     s, nl, rd, st = _list(P, r, L)
     p, mu, sd, params, norm = _model(P, r, L, seed)
-    m = P.BPModel(params, norm, r.shape[0])
+    m = P.BPModel(params, norm, r.shape[0], lists=lists)
     f = torch.zeros((r.shape[0], 4), dtype=torch.float32, device=dev())
     E = torch.zeros(1, dtype=torch.float64, device=dev())
     P.md_energy_forces(s, m.pot, rd, nl.plan, f, E, st)
@@ -106,6 +108,27 @@ def test_network_energy_and_forces_match_oracle(P, n_side, seed):
     assert force_error(f.cpu().numpy(), Fo) <= 1e-4
     np.testing.assert_allclose(m.Ei.cpu().numpy(), Eio, rtol=0, atol=1e-5 * np.abs(Eio).max())
     assert abs(E.item() - Eo) <= 1e-5 * abs(Eo)
+
+
+def test_partner_lists_give_the_same_forces(P):
+    # the same triplets with the same FP32 vectors in both forms; only the
+    # order of each atom's sums differs
+    import torch
+    r, L = _snapshot(5, 9, jitter=0.3)
+    s, nl, rd, st = _list(P, r, L)
+    p, mu, sd, params, norm = _model(P, r, L, 9)
+    out = []
+    for lists in (False, True):
+        m = P.BPModel(params, norm, r.shape[0], lists=lists)
+        f = torch.zeros((r.shape[0], 4), dtype=torch.float32, device=dev())
+        E = torch.zeros(1, dtype=torch.float64, device=dev())
+        P.md_energy_forces(s, m.pot, rd, nl.plan, f, E, st)
+        torch.cuda.synchronize()
+        assert P.md_status_poll(st) == 0
+        out.append((f.cpu().numpy(), E.item()))
+    (f0, E0), (f1, E1) = out
+    assert np.abs(f1[:, :3] - f0[:, :3]).max() <= 2e-6 * np.abs(f0[:, :3]).max()
+    assert E1 == E0   # the energies come from the network, before the force gather
 
 
 def test_descriptor_jvp_matches_oracle(P):
