@@ -421,15 +421,14 @@ def alu_rooflines_section():
         return statistics.median(ts)
 
     out = {"peak_tflops": pk, "peak_source": src}
-    # k_sw
-    si = W.sw_silicon(20, T_K=1000.0, seed=0)
+    # SW forces (k_sw_lists + k_sw, the deployed form) on the thermal
+    # configuration after 200 NVE steps from the 1000 K lattice start
+    si, s, r = sw_evolved_64000()
     cap = 64
-    s = P.md_space_periodic(3, [si.L] * 3)
     nl = P.NeighborList(s, si.N, LP.SW_RC, 0.3, cap)
-    r = torch.from_numpy(si.r).to(dev)
     f = torch.zeros_like(r)
     nl.build(r, st)
-    pot = P.sw_pot(LP.SW_SI)
+    pot = P.sw_pot(LP.SW_SI, N=si.N)
     t = timed(lambda: P.md_energy_forces(s, pot, r, nl.plan, f, None, st))
     n = nl.cnt.clamp(max=cap).long()
     rows = nl.nbr.long().clamp(max=si.N - 1)
@@ -439,7 +438,8 @@ def alu_rooflines_section():
     m = inside.sum(1).double()
     pairs, cent, legs = float(m.sum()), float((m * (m - 1) / 2).sum()), float((m * (m - 1)).sum())
     fl = 42.0 * pairs + 102.0 * cent + 107.0 * legs
-    out["k_sw"] = {"N": si.N, "us": t * 1e6, "flops": fl, "pairs_per_atom": pairs / si.N,
+    out["k_sw"] = {"N": si.N, "kernels": "k_sw_lists + k_sw", "configuration": "after 200 NVE steps from 1000 K",
+                   "us": t * 1e6, "flops": fl, "pairs_per_atom": pairs / si.N,
                    "triplets_per_atom": (cent + legs) / si.N,
                    "roofline": {"bound": "alu", "achieved": fl / t / 1e12, "peak": pk, "unit": "TFLOP/s",
                                 "frac": fl / t / 1e12 / pk}}
@@ -823,7 +823,7 @@ def nhc_section(steps=200):
     out["lj256k"] = run(P.md_space_periodic(3, [c.L] * 3), P.lj_pot(), torch.from_numpy(c.r).to(dev),
                         torch.from_numpy(c.v).to(dev), 2.5, 0.3, 128, 1.0, c.dt, 1.0)
     si = W.sw_silicon(20, T_K=1000.0, seed=0)
-    out["sw_si64k_1000K"] = run(P.md_space_periodic(3, [si.L] * 3), P.sw_pot(LP.SW_SI),
+    out["sw_si64k_1000K"] = run(P.md_space_periodic(3, [si.L] * 3), P.sw_pot(LP.SW_SI, N=si.N),
                                 torch.from_numpy(si.r).to(dev), torch.from_numpy(si.v).to(dev), float(LP.SW_RC), 0.5,
                                 64, LP.MASS_SI, 1.0, W.KB_EV * 1000.0)
     out["status"] = P.md_status_poll(st)
@@ -1027,11 +1027,40 @@ def whole_job_rate(n_particles, md_steps, steps, world, ms_max):
     return n_particles * md_steps * steps * world / (ms_max * 1e-3)
 
 
+def sw_evolved_64000(steps=200):
+    """64,000 diamond-silicon atoms after `steps` SW NVE steps (1 fs) from
+    the 1000 K lattice start: the thermal configuration the deployed kernels
+    see (at the lattice start every atom has exactly four partners inside
+    the cutoff; at 1000 K some second neighbors come inside).  Returns the
+    workload, the space and the positions on the GPU."""
+    import torch
+    import paper_1912_04232_b300 as J
+    import paper_1912_04232_b300.learned as LP
+    import workloads as W
+    si = W.sw_silicon(20, T_K=1000.0, seed=0)
+    space = J.md_space_periodic(3, [si.L] * 3)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sw = J.sw_pot(LP.SW_SI, N=si.N)
+    nl = J.NeighborList(space, si.N, LP.SW_RC, 0.3, 64)
+    r = torch.from_numpy(si.r).cuda()
+    v = torch.from_numpy(si.v).cuda()
+    f = torch.zeros_like(r)
+    nl.build(r, st)
+    J.md_energy_forces(space, sw, r, nl.plan, f, None, st)
+    J.md_integrate_nve(space, sw, r, v, f, LP.MASS_SI, 1.0, steps, nl.plan, None, None, True, st)
+    torch.cuda.synchronize()
+    if J.md_status_poll(st):
+        raise RuntimeError("SW NVE for the evolved configuration failed")
+    return si, space, r
+
+
 def learned_kernels(params=None, norm=None):
     """CUDA-event timings of the learned potential's kernels at 64,000 SW
-    silicon atoms (1000 K start): descriptors, the network (tcgen05 and
-    FP32), the force gather, a whole BP force evaluation, and SW forces; and
-    each kernel's fraction of its roofline.  FLOPs (FMA = 2; exp, sin/cos,
+    silicon atoms (after 200 SW NVE steps from the 1000 K start):
+    descriptors, the network (tcgen05 and FP32), the force gather over the
+    neighbor rows, a whole BP force evaluation in both forms (partner lists
+    stored by the descriptor kernel, the deployed form; rows), and SW forces
+    in both forms; and each kernel's fraction of its roofline.  FLOPs (FMA = 2; exp, sin/cos,
     divide = 1): the network 2 (16x64 + 64x64 + 64x64 + 64x16) = 20,480 per
     atom on the tensor cores (BF16 peak of MEASURED_PEAKS.json); the
     descriptors 44 per pair inside R_c (cutoff 4, eight Gaussians 40) and 50
@@ -1043,24 +1072,23 @@ def learned_kernels(params=None, norm=None):
     import torch
     import paper_1912_04232_b300 as J
     import paper_1912_04232_b300.learned as LP
-    import workloads as W
-    si = W.sw_silicon(20, T_K=1000.0, seed=0)
+    si, space, r = sw_evolved_64000()
     N, L = si.N, si.L
-    space = J.md_space_periodic(3, [L] * 3)
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     if params is None:
         rng = np.random.default_rng(0)
         params = torch.from_numpy((rng.normal(size=J.BP_NPARAMS) * 0.1).astype(np.float32)).cuda()
         norm = torch.cat([torch.zeros(16), torch.ones(16)]).float().cuda()
     model = J.BPModel(params, norm, N)
+    model_rows = J.BPModel(params, norm, N, lists=False)
     nl = J.NeighborList(space, N, LP.SW_RC, 0.3, 64)
-    r = torch.from_numpy(si.r).cuda()
     nl.build(r, st)
     G = torch.zeros((N, 16), device="cuda")
     Ei = torch.zeros(N, device="cuda")
     dEdG = torch.zeros((N, 16), device="cuda")
     f = torch.zeros((N, 4), device="cuda")
     sw = J.sw_pot(LP.SW_SI)
+    sw_lists = J.sw_pot(LP.SW_SI, N=N)
 
     def t(fn, K=50):
         for _ in range(5):
@@ -1080,8 +1108,12 @@ def learned_kernels(params=None, norm=None):
         "k_bp_force": t(lambda: J.md_bp_forces(space, r, nl.plan, 0, dEdG, Ei, f, None, st))}}
     J.md_bp_set_tensor_cores(True)
     out["us"]["bp_energy_forces_tc"] = t(lambda: J.md_energy_forces(space, model.pot, r, nl.plan, f, None, st))
+    out["us"]["bp_energy_forces_tc_rows"] = t(lambda: J.md_energy_forces(space, model_rows.pot, r, nl.plan, f, None,
+                                                                           st))
     J.md_bp_set_tensor_cores(False)
     out["us"]["k_sw"] = t(lambda: J.md_energy_forces(space, sw, r, nl.plan, f, None, st))
+    out["us"]["sw_forces_lists"] = t(lambda: J.md_energy_forces(space, sw_lists, r, nl.plan, f, None, st))
+    out["configuration"] = "after 200 SW NVE steps (1 fs) from the 1000 K lattice start"
     # partners inside R_c per atom, for the FLOP counts
     cap = nl.cap
     n = nl.cnt.clamp(max=cap).long()

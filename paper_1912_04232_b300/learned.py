@@ -58,7 +58,7 @@ def generate_sw_dataset(temps, n_snap, stride=20, equil=2000, n_side=4, a=5.431,
     si0 = W.sw_silicon(n_side, a=a, T_K=0.0)
     n, L = si0.N, si0.L
     space = J.md_space_periodic(3, [L] * 3)
-    pot = J.sw_pot(SW_SI)
+    pot = J.sw_pot(SW_SI, N=n, device=device)
     R = torch.zeros((S, n, 4), dtype=torch.float32, device=device)
     F = torch.zeros((S, n, 4), dtype=torch.float32, device=device)
     E = torch.zeros(S, dtype=torch.float64, device=device)
@@ -417,7 +417,7 @@ def deploy_compare(params, norm, n_side=20, T=1000.0, steps=200, warmup=20, dt=1
     st = torch.zeros(1, dtype=torch.int32, device=device)
     out = {"N": N, "T_K": T, "steps": steps, "dt_fs": dt}
     model = J.BPModel(params, norm, N, device=device)
-    sw = J.sw_pot(SW_SI)
+    sw = J.sw_pot(SW_SI, N=N, device=device)
     n = N
     zeros = torch.zeros(n, dtype=torch.float32, device=device)
     cE = torch.zeros(n, dtype=torch.float32, device=device)
