@@ -273,17 +273,20 @@ __host__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Partner lists of the three-body potentials (caller-owned scratch): per
 // atom the count of partners inside the potential's cutoff, their indices
 // and displacement vectors (dx, dy, dz, r) = r_j - r_i, S slots per atom, in
-// the order of the atom's neighbor row.
+// the order of the atom's neighbor row; with AUX (Stillinger-Weber) also
+// each slot's one-leg factors and each atom's two-body force and energy.
 struct TbLayout {
-    size_t cnt, idx, vec, bytes;
+    size_t cnt, idx, vec, aux, f2, bytes;
 };
-__host__ inline TbLayout tb_layout(int N, int S)
+__host__ inline TbLayout tb_layout(int N, int S, bool aux)
 {
     TbLayout t;
     size_t o = 0;
     t.cnt = o;  o = align256(o + sizeof(int32_t) * (size_t)N);
     t.idx = o;  o = align256(o + sizeof(int32_t) * (size_t)N * S);
     t.vec = o;  o = align256(o + 4 * sizeof(float) * (size_t)N * S);
+    t.aux = o;  o = aux ? align256(o + 4 * sizeof(float) * (size_t)N * S) : o;
+    t.f2 = o;   o = aux ? align256(o + 4 * sizeof(float) * (size_t)N) : o;
     t.bytes = o;
     return t;
 }

@@ -52,6 +52,7 @@ struct PairArgs {
     // force kernel tests the neighbors' rows itself)
     int32_t *tb_cnt, *tb_idx;
     float4 *tb_vec;
+    float4 *tb_aux, *tb_f2;   // Stillinger-Weber: (g, g', 1/r) per slot, two-body (F, e) per atom
     // learned potential: network and per-atom scratch (device pointers)
     const float *bp_params, *bp_norm;
     float *bp_G, *bp_dEdG, *bp_Ei;

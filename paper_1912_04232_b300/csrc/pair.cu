@@ -518,7 +518,7 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
         if (m->lists) {   // partner-list scratch of md_bp_lists_bytes(N) bytes
             unsigned char *b = (unsigned char *)m->lists;
             if (((uintptr_t)b & 255u) != 0u) return false;
-            const TbLayout t = tb_layout(nb->N, BP_LIST_SLOTS);
+            const TbLayout t = tb_layout(nb->N, BP_LIST_SLOTS, false);
             a.tb_cnt = (int32_t *)(b + t.cnt);
             a.tb_idx = (int32_t *)(b + t.idx);
             a.tb_vec = (float4 *)(b + t.vec);
@@ -531,11 +531,13 @@ bool make_pair_args(const md_space *s, const md_pot *p, const float *d_r, const 
         a.sw[11] = rc * rc;
         if (p->model) {   // partner-list scratch of md_sw_lists_bytes(N) bytes
             unsigned char *b = (unsigned char *)p->model;
-            if (((uintptr_t)b & 255u) != 0u) return false;
-            const TbLayout t = tb_layout(nb->N, SW_LIST_SLOTS);
+            if (((uintptr_t)b & 255u) != 0u || (size_t)nb->N * SW_LIST_SLOTS >= (size_t)INT32_MAX) return false;
+            const TbLayout t = tb_layout(nb->N, SW_LIST_SLOTS, true);
             a.tb_cnt = (int32_t *)(b + t.cnt);
             a.tb_idx = (int32_t *)(b + t.idx);
             a.tb_vec = (float4 *)(b + t.vec);
+            a.tb_aux = (float4 *)(b + t.aux);
+            a.tb_f2 = (float4 *)(b + t.f2);
         }
     }
     return pair_blocks(a.N, a.tpp) <= w.max_blocks;
@@ -547,7 +549,7 @@ using namespace jmd;
 
 extern "C" size_t md_sw_lists_bytes(int N) { return N > 0 ? sw_lists_bytes(N) : 0; }
 
-extern "C" size_t md_bp_lists_bytes(int N) { return N > 0 ? tb_layout(N, BP_LIST_SLOTS).bytes : 0; }
+extern "C" size_t md_bp_lists_bytes(int N) { return N > 0 ? tb_layout(N, BP_LIST_SLOTS, false).bytes : 0; }
 
 extern "C" md_status md_set_pair_options(int opt)
 {

@@ -14,10 +14,12 @@
 //       and then evaluated together with every lane busy.
 // e_i = 1/2 sum_j phi2(r_ij) + sum_{j<k} phi3(i; j, k), so sum_i e_i = E.
 // With partner-list scratch (md_sw_lists_bytes), k_sw_lists first stores
-// every atom's partners inside a*sigma (index and r_j - r_i, in row order)
-// and k_sw reads them: for (3) it then visits only the neighbors' partners
-// inside a*sigma instead of testing their whole rows (about a fifth of the
-// entries in silicon at a 0.3 A skin), with the same vectors, bit for bit.
+// every atom's partners inside a*sigma (index, r_j - r_i and the one-leg
+// factors g, g', 1/r, in row order) and its two-body terms, and k_sw_pl
+// takes the triplets from those lists: for (3) it visits only the
+// neighbors' partners inside a*sigma instead of testing their whole rows
+// (about a third of the entries in silicon at 1000 K and a 0.3 A skin), and
+// no triplet recomputes an exponential or a division of its legs.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
@@ -133,8 +135,10 @@ constexpr int SW_QG = 32;                // queued triplets per atom between eva
 // atom has about five partners inside a*sigma).  Every lane of a warp runs
 // every trip of every loop (group ballots, scans and sums are warp-wide);
 // a queue is evaluated when any group's would overflow.
-// Partner lists (pass 1 of the two-kernel form): the atom's row entries
-// inside a*sigma, compacted by a group ballot in row order.
+// Two-kernel form, pass 1: the atom's row entries inside a*sigma, compacted
+// by a group ballot in row order, each with its vector u = r_j - r_i and r,
+// and with the one-leg factors of every triplet that has this leg: g(r),
+// g'(r) and 1/r; and the atom's two-body force and energy.
 __global__ void __launch_bounds__(SW_WARPS * 32) k_sw_lists(PairArgs a)
 {
     count_launch();
@@ -151,10 +155,10 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_sw_lists(PairArgs a)
         int n = 0;
         const int32_t *row = a.nbr + (size_t)(valid ? i : 0) * a.cap;
         if (valid) n = min(a.cnt[i], a.cap);
-        int32_t *oi = a.tb_idx + (size_t)i * SW_MAXN;
-        float4 *ov = a.tb_vec + (size_t)i * SW_MAXN;
+        const size_t o = (size_t)(valid ? i : 0) * SW_MAXN;
         const int nmax = __reduce_max_sync(0xffffffffu, n);
         int m = 0;
+        float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
         for (int k0 = 0; k0 < nmax; k0 += SW_G) {
             const int k = k0 + gl;
             bool in = false;
@@ -168,22 +172,214 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_sw_lists(PairArgs a)
             }
             const unsigned mk = __ballot_sync(0xffffffffu, in) & gmask;
             const int pos = m + __popc(mk & below);
-            if (in && pos < SW_MAXN) {
-                oi[pos] = j;
-                ov[pos] = make_float4(dx, dy, dz, sqrtf(r2));
+            if (in) {
+                const float r = sqrtf(r2);
+                float dphi, dg;
+                const float ph = sw_phi2(P, r, dphi);
+                const float fr = dphi / r;
+                fx += fr * dx;
+                fy += fr * dy;
+                fz += fr * dz;
+                e += 0.5f * ph;
+                if (pos < SW_MAXN) {
+                    const float g = sw_g(P, r, dg);
+                    a.tb_idx[o + pos] = j;
+                    a.tb_vec[o + pos] = make_float4(dx, dy, dz, r);
+                    a.tb_aux[o + pos] = make_float4(g, dg, 1.0f / r, 0.f);
+                }
             }
             m += __popc(mk);
+        }
+#pragma unroll
+        for (int q = SW_G / 2; q > 0; q >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, q);
+            fy += __shfl_xor_sync(0xffffffffu, fy, q);
+            fz += __shfl_xor_sync(0xffffffffu, fz, q);
+            e += __shfl_xor_sync(0xffffffffu, e, q);
         }
         if (valid && gl == 0) {
             if (m > SW_MAXN) raise_status(a.status, MD_ERR_NBR_OVERFLOW);
             a.tb_cnt[i] = min(m, SW_MAXN);
+            a.tb_f2[i] = make_float4(fx, fy, fz, e);
         }
     }
 }
 
-// LISTS 1: the partners come from k_sw_lists (this atom's and its
-// neighbors'); LISTS 0: from the neighbor rows, tested here.
-template <int KICK, int LISTS>
+// The triplet of sw_triplet with its one-leg factors given: g, g' and 1/r
+// of each leg (k_sw_lists computed them with the same expressions, so every
+// value is the one sw_triplet computes, bit for bit).
+__device__ __forceinline__ float sw_triplet_pre(const SwP &P, float ux, float uy, float uz, float iu, float g1,
+                                                float dgu, float wx, float wy, float wz, float iw, float g2, float dgw,
+                                                float gu[3], float gw[3])
+{
+    float c = (ux * wx + uy * wy + uz * wz) * iu * iw;
+    float cc = c - P.c0;
+    float le = P.lam * P.eps;
+    float h = le * cc * cc * g1 * g2;
+    float dh_dc = 2.0f * le * cc * g1 * g2;
+    float dh_dru = le * cc * cc * dgu * g2;
+    float dh_drw = le * cc * cc * g1 * dgw;
+    float uu[3] = {ux, uy, uz}, ww[3] = {wx, wy, wz};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float dc_du = ww[q] * iu * iw - c * uu[q] * iu * iu;
+        float dc_dw = uu[q] * iu * iw - c * ww[q] * iw * iw;
+        gu[q] = dh_dc * dc_du + dh_dru * uu[q] * iu;
+        gw[q] = dh_dc * dc_dw + dh_drw * ww[q] * iw;
+    }
+    return h;
+}
+
+// Two-kernel form, pass 2: the triplets, from the stored lists.  Centred
+// triplets take both legs from the atom's own list; a triplet centred on
+// neighbor j with the atom as a leg takes the other leg from j's list
+// (queued as its list entry).  The two-body part comes from pass 1.
+constexpr int SWL_QG = 32;   // queued triplets per atom between evaluations
+
+template <int KICK>
+__global__ void __launch_bounds__(SW_WARPS * 32, 4) k_sw_pl(PairArgs a)
+{
+    count_launch();
+    __shared__ int nj[SW_WARPS][SW_PER_WARP][SW_MAXN];
+    __shared__ float4 nd[SW_WARPS][SW_PER_WARP][SW_MAXN];    // (ux, uy, uz, r)
+    __shared__ float4 na[SW_WARPS][SW_PER_WARP][SW_MAXN];    // (g, g', 1/r)
+    __shared__ int qpre[SW_WARPS][SW_PER_WARP][SW_MAXN + 1];
+    __shared__ unsigned char qs[SW_WARPS][SW_PER_WARP][SWL_QG];   // first leg (own list)
+    __shared__ unsigned char qk[SW_WARPS][SW_PER_WARP][SWL_QG];   // second leg (own list), or SW_LEG
+    __shared__ int qe[SW_WARPS][SW_PER_WARP][SWL_QG];             // ... the other leg's list entry
+    const SwP P = sw_params(a);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / SW_G, gl = lane % SW_G;
+    const unsigned gmask = ((1u << SW_G) - 1u) << (grp * SW_G);
+    const unsigned below = (1u << lane) - 1u;
+    int *njg = nj[w][grp];
+    float4 *ndg = nd[w][grp], *nag = na[w][grp];
+    int *qp = qpre[w][grp];
+    unsigned char *qsg = qs[w][grp], *qkg = qk[w][grp];
+    int *qeg = qe[w][grp];
+    float pe_acc = 0.0f, ke_acc = 0.0f;
+    auto terms = [&](int qn, float &fx, float &fy, float &fz, float &e) {
+        for (int q = gl; q < qn; q += SW_G) {
+            const int k = qkg[q];
+            const bool leg = k == SW_LEG;
+            const float4 u = ndg[qsg[q]], ua = nag[qsg[q]];
+            const float4 v = leg ? a.tb_vec[qeg[q]] : ndg[k];
+            const float4 va = leg ? a.tb_aux[qeg[q]] : nag[k];
+            const float sg = leg ? -1.0f : 1.0f;
+            float gu[3], gw[3];
+            const float h = sw_triplet_pre(P, sg * u.x, sg * u.y, sg * u.z, ua.z, ua.x, ua.y, v.x, v.y, v.z, va.z, va.x,
+                                           va.y, gu, gw);
+            const float cw = leg ? 0.0f : 1.0f;
+            fx += sg * gu[0] + cw * gw[0];
+            fy += sg * gu[1] + cw * gw[1];
+            fz += sg * gu[2] + cw * gw[2];
+            e += cw * h;
+        }
+    };
+    const int step = gridDim.x * SW_WARPS * SW_PER_WARP;
+    for (int i0 = (blockIdx.x * SW_WARPS + w) * SW_PER_WARP; i0 < a.N; i0 += step) {
+        const int i = i0 + grp;
+        const bool valid = i < a.N;
+        const int m = valid ? a.tb_cnt[i] : 0;
+        for (int s = gl; s < m; s += SW_G) {
+            const size_t o = (size_t)i * SW_MAXN + s;
+            njg[s] = a.tb_idx[o];
+            ndg[s] = a.tb_vec[o];
+            nag[s] = a.tb_aux[o];
+        }
+        __syncwarp();
+        float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+        int qn = 0;
+        auto enqueue = [&](bool in, int q1, int q2, int ge) {
+            const unsigned mk = __ballot_sync(0xffffffffu, in) & gmask;
+            if (__any_sync(0xffffffffu, qn + __popc(mk) > SWL_QG)) {   // some group full: evaluate every queue
+                __syncwarp();
+                terms(qn, fx, fy, fz, e);
+                __syncwarp();
+                qn = 0;
+            }
+            const int pos = qn + __popc(mk & below);
+            if (in) {
+                qsg[pos] = (unsigned char)q1;
+                qkg[pos] = (unsigned char)q2;
+                qeg[pos] = ge;
+            }
+            qn += __popc(mk);
+        };
+        // centred pairs (s1 < s2)
+        const int nt = m * (m - 1) / 2;
+        const int ntmax = __reduce_max_sync(0xffffffffu, nt);
+        for (int t0 = 0; t0 < ntmax; t0 += SW_G) {
+            int t = t0 + gl, s1 = 0;
+            const bool in = t < nt;
+            if (in)
+                while (t >= m - 1 - s1) {   // pair t of (s1 < s2) in row-major order
+                    t -= m - 1 - s1;
+                    ++s1;
+                }
+            enqueue(in, s1, s1 + 1 + t, 0);
+        }
+        // the neighbors' partners other than this atom
+        const int mmax = __reduce_max_sync(0xffffffffu, m);
+        int tot = 0;
+        for (int s0 = 0; s0 < mmax; s0 += SW_G) {   // exclusive prefix of the neighbors' list lengths
+            const int s = s0 + gl;
+            const int nn = s < m ? a.tb_cnt[njg[s]] : 0;
+            int incl = nn;
+#pragma unroll
+            for (int o = 1; o < SW_G; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o, SW_G);
+                if (gl >= o) incl += y;
+            }
+            if (s < m) qp[s] = tot + incl - nn;
+            tot += __shfl_sync(0xffffffffu, incl, SW_G - 1, SW_G);
+        }
+        if (gl == 0) qp[m] = tot;
+        __syncwarp();
+        const int totmax = __reduce_max_sync(0xffffffffu, tot);
+        for (int b0 = 0; b0 < totmax; b0 += SW_G) {
+            const int it = b0 + gl;
+            bool in = false;
+            int s = 0, ge = 0;
+            if (it < tot) {
+                int lo = 0, hi = m - 1;   // last s with qpre[s] <= it
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (qp[mid] <= it) lo = mid;
+                    else hi = mid - 1;
+                }
+                s = lo;
+                ge = njg[s] * SW_MAXN + (it - qp[s]);
+                in = a.tb_idx[ge] != i;
+            }
+            enqueue(in, s, SW_LEG, ge);
+        }
+        __syncwarp();
+        terms(qn, fx, fy, fz, e);
+#pragma unroll
+        for (int o = SW_G / 2; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+        }
+        if (valid && gl == 0) {
+            const float4 f2 = a.tb_f2[i];   // two-body part
+            fx += f2.x;
+            fy += f2.y;
+            fz += f2.z;
+            e += f2.w;
+            a.f[i] = make_float4(fx, fy, fz, e);
+            pe_acc += e;
+            if (KICK) ke_acc += half_kick<3>(a, i, fx, fy, fz);
+        }
+        __syncwarp();
+    }
+    if (!a.E_out && !KICK) return;
+    energy_epilogue(pe_acc, ke_acc, a);
+}
+
+template <int KICK>
 __global__ void __launch_bounds__(SW_WARPS * 32, 4) k_sw(PairArgs a)
 {
     count_launch();
@@ -213,15 +409,8 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 4) k_sw(PairArgs a)
         const int32_t *row = a.nbr + (size_t)(valid ? i : 0) * a.cap;
         if (valid) n = min(a.cnt[i], a.cap);
         // (0) neighbors inside a*sigma, compacted into the group's list
-        const int nmax = LISTS ? 0 : __reduce_max_sync(0xffffffffu, n);
+        const int nmax = __reduce_max_sync(0xffffffffu, n);
         int m = 0;
-        if (LISTS) {
-            if (valid) m = a.tb_cnt[i];
-            for (int s = gl; s < m; s += SW_G) {
-                njg[s] = a.tb_idx[(size_t)i * SW_MAXN + s];
-                ndg[s] = a.tb_vec[(size_t)i * SW_MAXN + s];
-            }
-        }
         for (int k0 = 0; k0 < nmax; k0 += SW_G) {
             const int k = k0 + gl;
             bool in = false;
@@ -302,7 +491,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 4) k_sw(PairArgs a)
         for (int s0 = 0; s0 < mmax; s0 += SW_G) {   // exclusive prefix of the neighbors' row lengths
             const int s = s0 + gl;
             int nn = 0;
-            if (s < m) nn = LISTS ? a.tb_cnt[njg[s]] : min(a.cnt[njg[s]], a.cap);
+            if (s < m) nn = min(a.cnt[njg[s]], a.cap);
             int incl = nn;
 #pragma unroll
             for (int o = 1; o < SW_G; o <<= 1) {
@@ -329,22 +518,13 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 4) k_sw(PairArgs a)
                 }
                 s = lo;
                 const int j = njg[s];
-                if (LISTS) {
-                    // j's partner inside a*sigma, with w' = r_k - r_j as k_sw_lists computed it
-                    const size_t e = (size_t)j * SW_MAXN + (it - qp[s]);
-                    if (a.tb_idx[e] != i) {
-                        wv = a.tb_vec[e];
-                        in = true;
-                    }
-                } else {
-                    const int kk = a.nbr[(size_t)j * a.cap + (it - qp[s])];
-                    if (kk != i) {
-                        const float4 rj = __ldg(a.r + j), rk = __ldg(a.r + kk);
-                        float wx, wy, wz;
-                        const float w2 = dist2_rn<3>(rk, rj, a.box, wx, wy, wz);
-                        in = w2 < P.rc2;
-                        wv = make_float4(wx, wy, wz, sqrtf(w2));
-                    }
+                const int kk = a.nbr[(size_t)j * a.cap + (it - qp[s])];
+                if (kk != i) {
+                    const float4 rj = __ldg(a.r + j), rk = __ldg(a.r + kk);
+                    float wx, wy, wz;
+                    const float w2 = dist2_rn<3>(rk, rj, a.box, wx, wy, wz);
+                    in = w2 < P.rc2;
+                    wv = make_float4(wx, wy, wz, sqrtf(w2));
                 }
             }
             enqueue(in, s, SW_LEG, wv);
@@ -383,30 +563,27 @@ static int sw_grid(K kern, int N)
     return groups < g ? groups : g;
 }
 
-template <int KICK, int LISTS>
-static void launch_sw(const PairArgs &a, cudaStream_t st)
+template <class K>
+static void launch_full(K kern, int &g_full, const PairArgs &a, cudaStream_t st)
 {
-    static int g_full = 0;   // resident CTAs of the whole GPU (occupancy x SMs), first launch
-    if (!g_full) g_full = sw_grid(k_sw<KICK, LISTS>, 1 << 30);
+    if (!g_full) g_full = sw_grid(kern, 1 << 30);   // resident CTAs of the whole GPU
     const int groups = (a.N + SW_WARPS * SW_PER_WARP - 1) / (SW_WARPS * SW_PER_WARP);
-    k_sw<KICK, LISTS><<<groups < g_full ? groups : g_full, SW_WARPS * 32, 0, st>>>(a);
+    kern<<<groups < g_full ? groups : g_full, SW_WARPS * 32, 0, st>>>(a);
 }
 
 void enqueue_sw(const PairArgs &a, int kick, cudaStream_t st)
 {
+    static int g0 = 0, g1 = 0, gl = 0, gp0 = 0, gp1 = 0;
     if (a.tb_cnt) {
-        static int g_lists = 0;
-        if (!g_lists) g_lists = sw_grid(k_sw_lists, 1 << 30);
-        const int groups = (a.N + SW_WARPS * SW_PER_WARP - 1) / (SW_WARPS * SW_PER_WARP);
-        k_sw_lists<<<groups < g_lists ? groups : g_lists, SW_WARPS * 32, 0, st>>>(a);
-        if (kick) launch_sw<1, 1>(a, st);
-        else launch_sw<0, 1>(a, st);
+        launch_full(k_sw_lists, gl, a, st);
+        if (kick) launch_full(k_sw_pl<1>, gp1, a, st);
+        else launch_full(k_sw_pl<0>, gp0, a, st);
     } else {
-        if (kick) launch_sw<1, 0>(a, st);
-        else launch_sw<0, 0>(a, st);
+        if (kick) launch_full(k_sw<1>, g1, a, st);
+        else launch_full(k_sw<0>, g0, a, st);
     }
 }
 
-size_t sw_lists_bytes(int N) { return tb_layout(N, SW_MAXN).bytes; }
+size_t sw_lists_bytes(int N) { return tb_layout(N, SW_MAXN, true).bytes; }
 
 }  // namespace jmd
