@@ -257,14 +257,19 @@ def learned_section():
     }
 
 
-def batched_section(steps=500):
+def batched_section(steps=500, rank=0, world=1, dist=None, device=None):
     """512 LJ / soft-sphere replicas (N log-uniform in [64, 8192]) for
-    `steps` NVE steps in one graph launch, against one launch per replica."""
+    `steps` NVE steps in one graph launch, against one launch per replica.
+    With several ranks each runs its share of the replicas
+    (`replicas.split_replicas`); the rates count every rank's particles over
+    the slowest rank's time, the tuning figures are this rank's."""
     import torch
     import paper_1912_04232_b300 as P
     import workloads as W
-    dev = torch.device("cuda")
-    specs = W.replica_plan(R=512, n_max=8192, seed=0)
+    from paper_1912_04232_b300.replicas import split_replicas
+    dev = device if device is not None else torch.device("cuda")
+    specs_all = W.replica_plan(R=512, n_max=8192, seed=0)
+    specs = [specs_all[i] for i in split_replicas([sp.N for sp in specs_all], world)[rank]]
     states = []
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     for sp in specs:
@@ -323,10 +328,12 @@ def batched_section(steps=500):
     b = P.Batch(descs, cap=128)
     ms_default = measure(b)
     scratch = torch.empty((2 * b.plan.N, 4), dtype=torch.float32, device=dev)
-    tpp = P.md_batch_autotune(b.plan, r, v, f, scratch, 20, os.path.join(tempfile.gettempdir(), "jmd_batch_tune.json"))
+    tpp = P.md_batch_autotune(b.plan, r, v, f, scratch, 20,
+                              os.path.join(tempfile.gettempdir(), f"jmd_batch_tune_r{rank}.json"))
     ms_global = measure(b)
     del b
-    tuned = BT.tune(descs, r0, v0, probe=20, cache_path=os.path.join(tempfile.gettempdir(), "jmd_batch_classes.json"))
+    tuned = BT.tune(descs, r0, v0, probe=20,
+                    cache_path=os.path.join(tempfile.gettempdir(), f"jmd_batch_classes_r{rank}.json"))
     b = P.Batch(BT.with_mults(descs, tuned["cell_mult"]), cap=128)
     P.md_batch_set_class_tpp(b.plan, BT.tpp_per_replica(descs, tuned["tpp"]))
     ms_b = measure(b)
@@ -367,7 +374,15 @@ def batched_section(steps=500):
     flop_ps = 35.0 * mean_cnt + 24.0
     pk, src = fp32_peak()
     ach = flop_ps * Ntot * steps / (ms_b * 1e-3) / 1e12
-    return {"replicas": len(specs), "N_total": Ntot, "steps": steps, "tpp_autotuned": tpp,
+    if dist is not None:   # the whole job: every rank's particles, the slowest rank's time
+        t = torch.tensor([float(Ntot)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t)
+        Ntot = int(t.item())
+        ms_b = max_over_ranks(ms_b, dist, dev)
+        ms_s = max_over_ranks(ms_s, dist, dev)
+        ms_default = max_over_ranks(ms_default, dist, dev)
+        ms_global = max_over_ranks(ms_global, dist, dev)
+    return {"replicas": len(specs_all), "ranks": world, "N_total": Ntot, "steps": steps, "tpp_autotuned": tpp,
             "one_launch_particle_steps_per_s": Ntot * steps / (ms_b * 1e-3),
             "per_replica_launches_particle_steps_per_s": Ntot * steps / (ms_s * 1e-3),
             "speedup": ms_s / ms_b, "status": code,
@@ -1413,8 +1428,10 @@ def main():
         extra["fp32_fma_peak"] = {"tflops": pk, "source": src}
     if rank == 0 and not args.no_learned:
         extra["learned_vs_sw"] = learned_section()
-    if rank == 0 and not args.no_batch:
-        extra["batched"] = batched_section()
+    if not args.no_batch and (rank == 0 or world > 1):   # the replicas split over the ranks
+        out = batched_section(rank=rank, world=world, dist=dist, device=dev)
+        if rank == 0:
+            extra["batched"] = out
     if rank == 0 and not args.no_table1:
         extra["table1"] = table1_section()
     if rank == 0 and not args.no_order:
