@@ -34,6 +34,9 @@ struct BpArgs {
 void enqueue_bp_desc(const BpArgs &a, cudaStream_t st);
 void enqueue_bp_force(const BpArgs &a, int kick, cudaStream_t st);
 void enqueue_bp_jvp(const BpArgs &a, cudaStream_t st);
+// descriptors and the tcgen05 network in one kernel (mlp_tc.cu): Ei, dE/dG
+void enqueue_bp_desc_mlp_tc(const BpArgs &b, const float *P, const float *norm, float *Ei, float *dEdG,
+                            uint32_t *status, cudaStream_t st);
 size_t mlp_train_tc_scratch(int N);   // partial gradients of md_bp_mlp_train_tc
 
 }  // namespace jmd

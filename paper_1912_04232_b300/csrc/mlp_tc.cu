@@ -17,9 +17,12 @@
 // weights are staged once per CTA in the same layout.  One elected thread
 // issues the MMAs and commits them to an mbarrier; every wait is bounded
 // and reports MD_ERR_TIMEOUT instead of hanging.
+#include <cstring>
+
 #include <cuda_bf16.h>
 
 #include "bp.cuh"
+#include "bp_terms.cuh"
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -39,13 +42,18 @@ __device__ __forceinline__ float sgm(float x)
 // holds H1, then G2, then G1: each is written only after the MMA that read
 // the previous one has completed.
 constexpr int TC_M = 128;
-constexpr uint32_t SM_W1 = 0;                     // [64 x 16]  B of MMA1 (W1, rows = out units)
+constexpr uint32_t SM_X = 0;                      // [128 x 16]  A of MMA1
+constexpr uint32_t SM_W1 = SM_X + TC_M * 16 * 2;  // [64 x 16]  B of MMA1 (W1, rows = out units)
 constexpr uint32_t SM_W2 = SM_W1 + 64 * 16 * 2;   // [64 x 64]  B of MMA2 (W2)
 constexpr uint32_t SM_W2T = SM_W2 + 64 * 64 * 2;  // [64 x 64]  B of MMA3 (W2^T)
 constexpr uint32_t SM_W1T = SM_W2T + 64 * 64 * 2; // [16 x 64]  B of MMA4 (W1^T)
-constexpr uint32_t SM_X = SM_W1T + 16 * 64 * 2;   // [128 x 16]
-constexpr uint32_t SM_A = SM_X + TC_M * 16 * 2;   // [128 x 64] H1, G2, G1 in turn
+constexpr uint32_t SM_A = SM_W1T + 16 * 64 * 2;   // [128 x 64] H1, G2, G1 in turn
 constexpr uint32_t SM_TOTAL = SM_A + TC_M * 64 * 2;
+// the descriptor phase of the fused kernel keeps its partner lists (eight
+// warps x four atoms x BP_MAXN float4) over the weights and A, which it
+// stages afterwards
+constexpr uint32_t SM_ND = SM_W1;
+static_assert(SM_ND + 8 * 4 * BP_MAXN * 16 <= SM_TOTAL, "the partner lists must fit over the weights");
 // requested per CTA: at least the layout, and enough that a fifth CTA
 // never fits on an SM (its tensor-memory allocation would have to wait)
 constexpr uint32_t SM_LAUNCH = 52 * 1024;
@@ -79,8 +87,16 @@ struct TcSmallSmem {
     float Eh[TC_M];   // the second column half's part of E
 };
 
+// DESC 0: X from the descriptors G in global memory.  DESC 1 (the fused
+// chain of a learned-potential evaluation): each tile first computes its 128
+// atoms' descriptors itself (desc_group, eight lanes per atom, four passes of
+// 32 atoms; the partner lists go to ba's lists when it carries them), writes
+// X straight into shared memory and then stages the weights over the space
+// the descriptor phase used.  G is not written; X has the bits the unfused
+// path gives it.
+template <bool DESC>
 __global__ void __launch_bounds__(TC_THREADS, 4) k_mlp_infer_tc(const float *P, const float *norm, const float *G, int N,
-                                                         float *Ei, float *dEdG, uint32_t *status)
+                                                         float *Ei, float *dEdG, uint32_t *status, BpArgs ba)
 {
     count_launch();
     extern __shared__ __align__(1024) unsigned char tc_smem[];
@@ -93,6 +109,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_mlp_infer_tc(const float *P, 
     // stage weights (BF16, canonical layouts): each thread packs blocks of 8
     // consecutive K elements of a row into one 16-byte store; W1 [h][q] and
     // W2 [h][c] rows are contiguous in P, the transposes read a column
+    auto stage_weights = [&]() {
     for (int b = tid; b < 64 * 2 + 16 * 8 + 64 * 8 * 2; b += blockDim.x) {
         float v[8];
         uint32_t buf;
@@ -119,6 +136,8 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_mlp_infer_tc(const float *P, 
         }
         tc_row8(sm, buf, row, k0, K, v);
     }
+    };
+    if (!DESC) stage_weights();
     if (tid < 64) {
         S.b1[tid] = P[P_B1 + tid];
         S.b2[tid] = P[P_B2 + tid];
@@ -189,8 +208,36 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_mlp_infer_tc(const float *P, 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int i = tile * TC_M + row;
         const bool valid = i < N;
-        // X = (G - mu) / sd  (BF16), zeros past the end: features 8 ch + [0, 8)
-        {
+        if (DESC) {
+            // descriptors of the tile's atoms, eight lanes each: pass p
+            // takes local atoms 32 p + 4 warp + group
+            const BpConst c = bp_const();
+            const int lane = tid & 31, grp = lane >> 3, gl = lane & 7;
+            const unsigned gmask = 0xffu << (grp * 8);
+            const unsigned below = (1u << lane) - 1u;
+            float4 *ndg = reinterpret_cast<float4 *>(sm + SM_ND) + (warp * 4 + grp) * BP_MAXN;
+#pragma unroll 1
+            for (int pass = 0; pass < TC_M / 32; ++pass) {
+                const int loc = pass * 32 + warp * 4 + grp;
+                const int ia = tile * TC_M + loc;
+                const bool va = ia < N;
+                float Gd[16];
+                desc_group<8>(ba, c, ia, va, ndg, gl, gmask, below, Gd);
+                if (gl < 2) {   // lanes 0 and 1 of the group: features 8 gl + [0, 8) of X
+                    float x[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float g = gl ? Gd[8 + q] : Gd[q];
+                        x[q] = va ? (g - S.mu[8 * gl + q]) * S.isd[8 * gl + q] : 0.0f;
+                    }
+                    tc_row8(sm, SM_X, loc, 8 * gl, 16, x);
+                }
+                __syncwarp();
+            }
+            __syncthreads();   // the partner lists are done with: the weights go over them
+            stage_weights();
+        } else {
+            // X = (G - mu) / sd  (BF16), zeros past the end: features 8 ch + [0, 8)
             float x[8];
             if (valid) {
                 const float4 *gp = reinterpret_cast<const float4 *>(G + (size_t)i * 16 + 8 * ch);
@@ -293,8 +340,7 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_mlp_infer_tc(const float *P, 
     if (tid == 0 && S.timeout) raise_status(status, MD_ERR_TIMEOUT);
 }
 
-void enqueue_mlp_infer_tc(const float *P, const float *norm, const float *G, int N, float *Ei, float *dEdG,
-                          uint32_t *status, cudaStream_t st)
+static int tc_grid(int N)
 {
     static int sms = 0;
     if (!sms) {
@@ -302,13 +348,27 @@ void enqueue_mlp_infer_tc(const float *P, const float *norm, const float *G, int
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms < 1) sms = 1;
-        cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_LAUNCH);
+        cudaFuncSetAttribute(k_mlp_infer_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_LAUNCH);
+        cudaFuncSetAttribute(k_mlp_infer_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_LAUNCH);
     }
     // four CTAs per SM: each holds 128 of the SM's 512 tensor-memory
     // columns; the grid never exceeds four per SM, so no allocation waits
     int tiles = (N + TC_M - 1) / TC_M;
-    int g = tiles < 4 * sms ? tiles : 4 * sms;
-    k_mlp_infer_tc<<<g, TC_THREADS, SM_LAUNCH, st>>>(P, norm, G, N, Ei, dEdG, status);
+    return tiles < 4 * sms ? tiles : 4 * sms;
+}
+
+void enqueue_mlp_infer_tc(const float *P, const float *norm, const float *G, int N, float *Ei, float *dEdG,
+                          uint32_t *status, cudaStream_t st)
+{
+    BpArgs none;
+    memset(&none, 0, sizeof(none));
+    k_mlp_infer_tc<false><<<tc_grid(N), TC_THREADS, SM_LAUNCH, st>>>(P, norm, G, N, Ei, dEdG, status, none);
+}
+
+void enqueue_bp_desc_mlp_tc(const BpArgs &b, const float *P, const float *norm, float *Ei, float *dEdG,
+                            uint32_t *status, cudaStream_t st)
+{
+    k_mlp_infer_tc<true><<<tc_grid(b.N), TC_THREADS, SM_LAUNCH, st>>>(P, norm, nullptr, b.N, Ei, dEdG, status, b);
 }
 
 }  // namespace jmd

@@ -309,6 +309,41 @@ def test_tensor_core_network_matches_fp32_network(P, N):
     assert np.corrcoef(etc, e32)[0, 1] > 0.999
 
 
+@pytest.mark.parametrize("n_side,lists", [(5, False), (5, True), (20, True)])
+def test_fused_descriptor_network_kernel_equals_separate_kernels(P, n_side, lists):
+    # on the tensor cores an evaluation computes the descriptors inside the
+    # network kernel; its per-atom energies and input gradients must be the
+    # separate kernels' bit for bit (1,000 atoms: 7 full tiles and a ragged
+    # one; 64,000 atoms: 500 tiles)
+    # (kernel against kernel: the inputs' normalisation comes from the GPU
+    # descriptors, no oracle is needed)
+    import torch
+    r, L = _snapshot(n_side, 21, jitter=0.3)
+    N = r.shape[0]
+    s, nl, rd, st = _list(P, r, L)
+    G0 = torch.zeros((N, 16), dtype=torch.float32, device=dev())
+    P.md_bp_descriptors(s, rd, nl.plan, 0, G0, st)
+    mu, sd = _norm(G0.cpu().numpy().astype(np.float64))
+    params = to_dev(pack(B.init_params(21)), torch.float32)
+    norm = to_dev(np.concatenate([mu, sd]), torch.float32)
+    m = P.BPModel(params, norm, N, lists=lists)
+    f = torch.zeros((N, 4), dtype=torch.float32, device=dev())
+    P.md_bp_set_tensor_cores(True)
+    try:
+        P.md_energy_forces(s, m.pot, rd, nl.plan, f, None, st)
+    finally:
+        P.md_bp_set_tensor_cores(False)
+    G = torch.zeros((N, 16), dtype=torch.float32, device=dev())
+    Ei = torch.zeros(N, dtype=torch.float32, device=dev())
+    D = torch.zeros((N, 16), dtype=torch.float32, device=dev())
+    P.md_bp_descriptors(s, rd, nl.plan, 0, G, st)
+    P.md_bp_mlp_infer_tc(params, norm, G, N, Ei, D, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    assert torch.equal(m.Ei, Ei)
+    assert torch.equal(m.dEdG, D)
+
+
 def test_tensor_core_forces_match_oracle(P):
     import torch
     r, L = _snapshot(4, 8)
