@@ -274,7 +274,7 @@ __device__ __forceinline__ int b_axis_cells(int q, int n, int *out)
 }
 
 constexpr int BB_CMAX = 1024;
-constexpr int BB_WARPS = 8;
+constexpr int BB_WARPS = 4;
 
 // Dense stencil (more candidates than a block stages): row of particle i by
 // one warp straight from the replica's cells, then sorted in the warp's
