@@ -16,7 +16,9 @@
 //                    kinetic energy into f.w and v.w
 //   k_b_energy       block per replica: FP64 sums in fixed order into the
 //                    replica's series; the last block advances the step and
-//                    sets the graph's WHILE condition
+//                    sets the graph's WHILE condition (k_b_step alone when
+//                    no series is asked for; non-finite forces are reported
+//                    by k_b_pair either way)
 // Arithmetic per particle is the single-system arithmetic (same pair term,
 // lane mapping, shuffle order, kick and drift), so a replica advanced here
 // matches the same replica advanced alone with the same tuning, bit for bit.
@@ -557,6 +559,8 @@ __global__ void __launch_bounds__(256) k_b_pair(BatchDev b, const float4 *r, flo
         if (valid && lg == 0) {
             float ei = 0.5f * e;
             f[i] = make_float4(fx, fy, fz, ei);
+            // a blown-up replica is reported here whether or not energies are summed
+            if (!(isfinite(fx) && isfinite(fy) && isfinite(fz) && isfinite(ei))) raise_status(b.status, MD_ERR_NONFINITE);
             if (KICK) {
                 float4 vi = v[i];
                 vi.x += mp->hdm * fx;
@@ -603,6 +607,17 @@ __global__ void __launch_bounds__(256) k_b_energy(BatchDev b, const float4 *v, c
         if (use_cond)
             cudaGraphSetConditional((cudaGraphConditionalHandle)cond_while, (step + 1u < b.ctl[CTL_NSTEPS]) ? 1u : 0u);
     }
+}
+
+// The loop control of a step without energy series: advance the step
+// counter and, in a graph, set the WHILE condition (one thread).
+__global__ void k_b_step(BatchDev b, unsigned long long cond_while, int use_cond)
+{
+    count_launch();
+    const unsigned step = b.ctl[CTL_STEP];
+    b.ctl[CTL_STEP] = step + 1u;
+    if (use_cond)
+        cudaGraphSetConditional((cudaGraphConditionalHandle)cond_while, (step + 1u < b.ctl[CTL_NSTEPS]) ? 1u : 0u);
 }
 
 __global__ void k_b_loop_init(uint32_t *ctl, uint32_t nsteps)
@@ -769,7 +784,8 @@ static md_status b_graph(BatchHost &H, const BatchDev &b0, float4 *r, float4 *v,
     enqueue_b_rebuild(b, r, cs2);
     JMD_CUDA_TRY(cudaStreamEndCapture(cs2, &ibody));
     enqueue_b_pair(b, r, v, f, 1, cs);
-    k_b_energy<<<b.R, 256, 0, cs>>>(b, v, f, PE, KE, len, (unsigned long long)hw, 1);
+    if (PE || KE) k_b_energy<<<b.R, 256, 0, cs>>>(b, v, f, PE, KE, len, (unsigned long long)hw, 1);
+    else k_b_step<<<1, 1, 0, cs>>>(b, (unsigned long long)hw, 1);
     JMD_CUDA_TRY(cudaStreamEndCapture(cs, &body));
     cudaStreamDestroy(cs2);
     cudaStreamDestroy(cs);
@@ -954,7 +970,8 @@ extern "C" md_status md_batch_run_nve(md_batch *bt, float *d_r, float *d_v, floa
             k_b_kick_drift<0><<<gk, 256, 0, st>>>(b, r, v, f, 0ull);
             enqueue_b_rebuild(b, r, st);   // kernels skip replicas with clear flags
             enqueue_b_pair(b, r, v, f, 1, st);
-            k_b_energy<<<b.R, 256, 0, st>>>(b, v, f, d_PE, d_KE, nsteps, 0ull, 0);
+            if (d_PE || d_KE) k_b_energy<<<b.R, 256, 0, st>>>(b, v, f, d_PE, d_KE, nsteps, 0ull, 0);
+            else k_b_step<<<1, 1, 0, st>>>(b, 0ull, 0);
         }
     }
     JMD_CUDA_TRY(cudaGetLastError());
