@@ -74,9 +74,10 @@ def parse():
     ap.add_argument("--no-gnn", action="store_true", help="skip the graph-network potential section")
     ap.add_argument("--no-alu", action="store_true", help="skip the ALU rooflines of k_sw and the rebuild chain")
     ap.add_argument("--no-tiles-job", action="store_true", help="skip the bench job on the tile engine")
-    ap.add_argument("--probe", default=None, choices=["learned-kernels", "train-step"],
-                    help="print the per-kernel timings of the learned potential's deployment (64,000 Si atoms) "
-                         "or of one BP training step (8 snapshots of 512 atoms) and exit")
+    ap.add_argument("--probe", default=None, choices=["learned-kernels", "train-step", "batch-steps"],
+                    help="print the per-kernel timings of the learned potential's deployment (64,000 Si atoms), "
+                         "of one BP training step (8 snapshots of 512 atoms), or the 512-replica batch's NVE "
+                         "steps as host launches, and exit")
     return ap.parse_args()
 
 
@@ -257,21 +258,14 @@ def learned_section():
     }
 
 
-def batched_section(steps=500, rank=0, world=1, dist=None, device=None):
-    """512 LJ / soft-sphere replicas (N log-uniform in [64, 8192]) for
-    `steps` NVE steps in one graph launch, against one launch per replica.
-    With several ranks each runs its share of the replicas
-    (`replicas.split_replicas`); the rates count every rank's particles over
-    the slowest rank's time, the tuning figures are this rank's."""
+def batch_setup(specs, dev, st):
+    """Initial states of replicas (soft-sphere replicas relaxed by 50
+    gradient-descent steps, then wrapped) and their md_replica_desc; the
+    states concatenated on the GPU."""
     import torch
     import paper_1912_04232_b300 as P
     import workloads as W
-    from paper_1912_04232_b300.replicas import split_replicas
-    dev = device if device is not None else torch.device("cuda")
-    specs_all = W.replica_plan(R=512, n_max=8192, seed=0)
-    specs = [specs_all[i] for i in split_replicas([sp.N for sp in specs_all], world)[rank]]
     states = []
-    st = torch.zeros(1, dtype=torch.int32, device=dev)
     for sp in specs:
         r, v = W.replica_initial(sp)
         if sp.kind == "soft":
@@ -298,11 +292,29 @@ def batched_section(steps=500, rank=0, world=1, dist=None, device=None):
         d.skin, d.dt, d.mass = 0.3, sp.dt, 1.0
         return d
 
-    import tempfile
-    import paper_1912_04232_b300.batch_tune as BT
     descs = [desc(sp) for sp in specs]
     r0 = torch.from_numpy(np.concatenate([s[0] for s in states])).to(dev)
     v0 = torch.from_numpy(np.concatenate([s[1] for s in states])).to(dev)
+    return states, descs, r0, v0
+
+
+def batched_section(steps=500, rank=0, world=1, dist=None, device=None):
+    """512 LJ / soft-sphere replicas (N log-uniform in [64, 8192]) for
+    `steps` NVE steps in one graph launch, against one launch per replica.
+    With several ranks each runs its share of the replicas
+    (`replicas.split_replicas`); the rates count every rank's particles over
+    the slowest rank's time, the tuning figures are this rank's."""
+    import torch
+    import paper_1912_04232_b300 as P
+    import workloads as W
+    from paper_1912_04232_b300.replicas import split_replicas
+    dev = device if device is not None else torch.device("cuda")
+    specs_all = W.replica_plan(R=512, n_max=8192, seed=0)
+    specs = [specs_all[i] for i in split_replicas([sp.N for sp in specs_all], world)[rank]]
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    states, descs, r0, v0 = batch_setup(specs, dev, st)
+    import tempfile
+    import paper_1912_04232_b300.batch_tune as BT
     r, v, f = r0.clone(), v0.clone(), torch.zeros_like(r0)
 
     def run_batch(b):
@@ -1158,6 +1170,35 @@ def learned_kernels(params=None, norm=None):
     return out
 
 
+def probe_batch_steps(steps=30):
+    """The 512-replica batch (configuration 4) advanced `steps` NVE steps as
+    host launches, so that a profiler lists every kernel of the step (the
+    graph form hides the kernels of its conditional nodes); prints the
+    CUDA-event time per step and the replica rebuilds."""
+    import torch
+    import paper_1912_04232_b300 as P
+    import workloads as W
+    dev = torch.device("cuda")
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    specs = W.replica_plan(R=512, n_max=8192, seed=0)
+    _, descs, r0, v0 = batch_setup(specs, dev, st)
+    r, v, f = r0.clone(), v0.clone(), torch.zeros_like(r0)
+    b = P.Batch(descs, cap=128)
+    P.md_batch_build(b.plan, r, st)
+    P.md_batch_forces(b.plan, r, f, st)
+    P.md_batch_run_nve(b.plan, r, v, f, 20, None, None, False, st)
+    b0 = sum(P.md_batch_stats(b.plan))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    P.md_batch_run_nve(b.plan, r, v, f, steps, None, None, False, st)
+    e1.record()
+    e1.synchronize()
+    print(json.dumps({"replicas": len(specs), "N": int(b.plan.N), "steps": steps,
+                      "us_per_step": e0.elapsed_time(e1) * 1e3 / steps,
+                      "replica_builds_per_step": (sum(P.md_batch_stats(b.plan)) - b0) / steps,
+                      "status": P.md_status_poll(st)}), flush=True)
+
+
 def probe_learned_kernels():
     print(json.dumps(learned_kernels()), flush=True)
 
@@ -1206,6 +1247,9 @@ def main():
         return
     if args.probe == "train-step":
         probe_train_step()
+        return
+    if args.probe == "batch-steps":
+        probe_batch_steps()
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
