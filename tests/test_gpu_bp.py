@@ -365,3 +365,49 @@ def test_tensor_core_forces_match_oracle(P):
     # the total is a cancelling sum of per-atom terms: judge it on their scale
     np.testing.assert_allclose(m.Ei.cpu().numpy(), Eio, rtol=0, atol=2e-2 * np.abs(Eio).max())
     assert abs(E.item() - Eo) <= 1e-2 * np.abs(Eio).sum()
+
+
+def test_fused_evaluation_on_concatenated_systems_equals_each_alone(P):
+    # equal-size snapshots concatenated (rows local to each, md_bp_model
+    # sys_n) through md_energy_forces on the tensor cores: every atom's
+    # energy, input gradient and force must be the ones of its snapshot
+    # evaluated alone, bit for bit
+    import types
+    import torch
+    import paper_1912_04232_b300.learned as LP
+    S = 3
+    snaps = [W.sw_silicon(3, T_K=0, jitter=0.3, seed=31 + k) for k in range(S)]
+    n, L = snaps[0].N, snaps[0].L
+    ds = types.SimpleNamespace(r=to_dev(np.stack([s.r for s in snaps]), torch.float32), n=n, L=L)
+    LP.build_lists(ds)
+    nb = LP.batch_list_view(ds, 0, S)
+    space = P.md_space_periodic(3, [L] * 3)
+    st = status_word()
+    G0 = torch.zeros((S * n, 16), dtype=torch.float32, device=dev())
+    P.md_bp_descriptors(space, ds.r.reshape(S * n, 4), nb, n, G0, st)
+    mu, sd = _norm(G0.cpu().numpy().astype(np.float64))
+    params = to_dev(pack(B.init_params(31)), torch.float32)
+    norm = to_dev(np.concatenate([mu, sd]), torch.float32)
+    P.md_bp_set_tensor_cores(True)
+    try:
+        m = P.BPModel(params, norm, S * n, sys_n=n)
+        f = torch.zeros((S * n, 4), dtype=torch.float32, device=dev())
+        P.md_energy_forces(space, m.pot, ds.r.reshape(S * n, 4), nb, f, None, st)
+        alone = []
+        for k in range(S):
+            s1, nl1, rd1, st1 = _list(P, snaps[k].r, L)
+            m1 = P.BPModel(params, norm, n)
+            f1 = torch.zeros((n, 4), dtype=torch.float32, device=dev())
+            P.md_energy_forces(s1, m1.pot, rd1, nl1.plan, f1, None, st1)
+            torch.cuda.synchronize()
+            assert P.md_status_poll(st1) == 0
+            alone.append((m1.Ei.clone(), m1.dEdG.clone(), f1.clone()))
+    finally:
+        P.md_bp_set_tensor_cores(False)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    for k, (Ei, D, f1) in enumerate(alone):
+        sl = slice(k * n, (k + 1) * n)
+        assert torch.equal(m.Ei[sl], Ei)
+        assert torch.equal(m.dEdG[sl], D)
+        assert torch.equal(f[sl], f1)
