@@ -411,3 +411,26 @@ def test_fused_evaluation_on_concatenated_systems_equals_each_alone(P):
         assert torch.equal(m.Ei[sl], Ei)
         assert torch.equal(m.dEdG[sl], D)
         assert torch.equal(f[sl], f1)
+
+
+@pytest.mark.parametrize("lists", [False, True])
+def test_more_partners_than_slots_is_reported(P, lists):
+    # 60 atoms within 1.4 A of one point: more than the 48 partners inside
+    # R_c an atom keeps; the list (cap 128) does not overflow
+    import torch
+    si = W.sw_silicon(3, T_K=0, jitter=0.0, seed=0)
+    r = si.r.copy()
+    rng = np.random.default_rng(6)
+    d = rng.normal(size=(60, 3))
+    d *= (1.4 * rng.uniform(0.2, 1.0, size=(60, 1)) ** (1 / 3)) / np.linalg.norm(d, axis=1, keepdims=True)
+    r[:60, :3] = (np.float32(si.L / 2) + d).astype(np.float32)
+    s, nl, rd, st = _list(P, r, si.L, cap=128)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    params = to_dev(pack(B.init_params(3)), torch.float32)
+    norm = to_dev(np.concatenate([np.zeros(16), np.ones(16)]).astype(np.float32), torch.float32)
+    m = P.BPModel(params, norm, si.N, lists=lists)
+    f = torch.zeros((si.N, 4), dtype=torch.float32, device=dev())
+    P.md_energy_forces(s, m.pot, rd, nl.plan, f, None, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) & P.MD_ERR_NBR_OVERFLOW

@@ -136,3 +136,29 @@ def test_langevin_thermalises_to_target_temperature(P):
     r, v, PE, KE = _langevin(P, si, 3000, 0.02, kT, seed=99)
     T_kin = 2.0 * KE[1000:].mean() / (3 * si.N * W.KB_EV)
     assert abs(T_kin - T) < 0.05 * T
+
+
+@pytest.mark.parametrize("lists", [False, True])
+def test_sw_more_partners_than_slots_is_reported(P, lists):
+    # 40 atoms packed within 1.3 A of one point: each has about 39 partners
+    # inside a*sigma, more than the 32 an atom keeps (one-kernel form and
+    # partner lists alike); the list itself (cap 128) does not overflow
+    import torch
+    si = W.sw_silicon(3, T_K=0, jitter=0.0, seed=0)
+    r = si.r.copy()
+    rng = np.random.default_rng(5)
+    d = rng.normal(size=(40, 3))
+    d *= (1.3 * rng.uniform(0.2, 1.0, size=(40, 1)) ** (1 / 3)) / np.linalg.norm(d, axis=1, keepdims=True)
+    r[:40, :3] = (np.float32(si.L / 2) + d).astype(np.float32)
+    s = P.md_space_periodic(3, [si.L] * 3)
+    nl = P.NeighborList(s, si.N, RC, 0.3, 128)
+    rd = to_dev(r, torch.float32)
+    st = status_word()
+    nl.build(rd, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) == 0
+    f = torch.zeros((si.N, 4), dtype=torch.float32, device=dev())
+    pot = P.sw_pot(O.SW_SI, N=si.N) if lists else P.sw_pot(O.SW_SI)
+    P.md_energy_forces(s, pot, rd, nl.plan, f, None, st)
+    torch.cuda.synchronize()
+    assert P.md_status_poll(st) & P.MD_ERR_NBR_OVERFLOW
