@@ -94,15 +94,17 @@ def test_nhc_heavy_thermostat_is_nve(P):
     np.testing.assert_allclose(KE, KEo[1:], rtol=5e-5)
 
 
-def test_nhc_sw_silicon_1000K(P):
-    # the paper's NVT deployment setting (SW silicon, 1000 K, dt = 1 fs)
+@pytest.mark.parametrize("lists", [False, True])
+def test_nhc_sw_silicon_1000K(P, lists):
+    # the paper's NVT deployment setting (SW silicon, 1000 K, dt = 1 fs), in
+    # the one-kernel form and on partner lists
     si = W.sw_silicon(4, T_K=1000.0, jitter=0.05, seed=5)
     mass = O.SW_MASS_AMU * O.AMU_A2_FS2_EV
     kT = W.KB_EV * 1000.0
     rc = float(O.SW_SI[2] * O.SW_SI[1])
     n, tau, M = 50, 100.0, 3
-    x, v, PE, KE, H, th, _ = _nhc_gpu(P, si.r, si.v, si.L, P.sw_pot(O.SW_SI), rc, 0.5, mass, 1.0, kT, tau, M, n,
-                                      cap=64)
+    pot = P.sw_pot(O.SW_SI, N=si.N) if lists else P.sw_pot(O.SW_SI)
+    x, v, PE, KE, H, th, _ = _nhc_gpu(P, si.r, si.v, si.L, pot, rc, 0.5, mass, 1.0, kT, tau, M, n, cap=64)
     xo, vo, PEo, KEo, Ho, (xio, wo) = O.nhc(si.r, si.v, si.L, "sw", mass=mass, dt=1.0, kT=kT, tau=tau, M=M,
                                            nsteps=n)
     np.testing.assert_allclose(PE, PEo[1:], rtol=1e-5)
