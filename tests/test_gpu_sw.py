@@ -94,7 +94,7 @@ def test_sw_nve_short_trajectory_matches_oracle(P, lists):
     np.testing.assert_allclose(KE.cpu().numpy(), KEo[1:], rtol=1e-4)
 
 
-def _langevin(P, si, n, gamma, kT, seed, step0=0):
+def _langevin(P, si, n, gamma, kT, seed, step0=0, lists=False):
     import torch
     s = P.md_space_periodic(3, [si.L] * 3)
     nl = P.NeighborList(s, si.N, RC, SKIN, 64)
@@ -102,7 +102,7 @@ def _langevin(P, si, n, gamma, kT, seed, step0=0):
     vd = to_dev(si.v, torch.float32)
     f = torch.zeros((si.N, 4), dtype=torch.float32, device=dev())
     st = status_word()
-    pot = P.sw_pot(O.SW_SI)
+    pot = P.sw_pot(O.SW_SI, N=si.N) if lists else P.sw_pot(O.SW_SI)
     nl.build(rd, st)
     P.md_energy_forces(s, pot, rd, nl.plan, f, None, st)
     PE = torch.zeros(n, dtype=torch.float64, device=dev())
@@ -113,12 +113,13 @@ def _langevin(P, si, n, gamma, kT, seed, step0=0):
     return rd.cpu().numpy(), vd.cpu().numpy(), PE.cpu().numpy(), KE.cpu().numpy()
 
 
-def test_langevin_trajectory_matches_oracle_noise_bit_for_bit(P):
+@pytest.mark.parametrize("lists", [False, True])
+def test_langevin_trajectory_matches_oracle_noise_bit_for_bit(P, lists):
     # same Philox counters on both sides: the FP32 run follows the FP64 run
     si = W.sw_silicon(4, T_K=1200, jitter=0.1, seed=11)
     kT = W.KB_EV * 1200.0
     n = 20
-    r, v, PE, KE = _langevin(P, si, n, 0.01, kT, seed=1234567, step0=40)
+    r, v, PE, KE = _langevin(P, si, n, 0.01, kT, seed=1234567, step0=40, lists=lists)
     ro, vo, PEo, KEo = O.langevin(si.r, si.v, si.L, "sw", mass=MASS, dt=1.0, gamma=0.01, kT=kT, seed=1234567,
                                   step0=40, nsteps=n)
     d = r[:, :3] - ro
