@@ -362,7 +362,7 @@ def test_tensor_core_forces_match_oracle(P):
     t64 = lambda a: torch.as_tensor(a.astype(np.float64))
     Eo, Fo, Eio, _ = B.energy_forces(r, L, f32_params(p), t64(mu), t64(sd))
     assert force_error(f.cpu().numpy(), Fo) <= 3e-2
-    # the total is a cancelling sum of per-atom terms: judge it on their scale
+    # the total is a cancelling sum of per-atom terms: compare it on their scale
     np.testing.assert_allclose(m.Ei.cpu().numpy(), Eio, rtol=0, atol=2e-2 * np.abs(Eio).max())
     assert abs(E.item() - Eo) <= 1e-2 * np.abs(Eio).sum()
 
