@@ -309,12 +309,12 @@ def test_tensor_core_network_matches_fp32_network(P, N):
     assert np.corrcoef(etc, e32)[0, 1] > 0.999
 
 
-@pytest.mark.parametrize("n_side,lists", [(5, False), (5, True), (20, True)])
+@pytest.mark.parametrize("n_side,lists", [(2, True), (5, False), (5, True), (20, True)])
 def test_fused_descriptor_network_kernel_equals_separate_kernels(P, n_side, lists):
     # on the tensor cores an evaluation computes the descriptors inside the
     # network kernel; its per-atom energies and input gradients must be the
-    # separate kernels' bit for bit (1,000 atoms: 7 full tiles and a ragged
-    # one; 64,000 atoms: 500 tiles)
+    # separate kernels' bit for bit (64 atoms: one partial tile; 1,000 atoms:
+    # 7 full tiles and a ragged one; 64,000 atoms: 500 tiles)
     # (kernel against kernel: the inputs' normalisation comes from the GPU
     # descriptors, no oracle is needed)
     import torch

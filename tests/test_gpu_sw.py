@@ -37,7 +37,7 @@ def _forces(P, r, L, cap=64, lists=False):
 
 
 @pytest.mark.parametrize("lists", [False, True])
-@pytest.mark.parametrize("n_side,jitter,seed", [(4, 0.15, 1), (4, 0.35, 2), (3, 0.25, 3), (20, 0.2, 4)])
+@pytest.mark.parametrize("n_side,jitter,seed", [(2, 0.2, 7), (4, 0.15, 1), (4, 0.35, 2), (3, 0.25, 3), (20, 0.2, 4)])
 def test_sw_forces_energy_match_oracle(P, n_side, jitter, seed, lists):
     # lists: the two-kernel form (partners inside a*sigma stored first)
     si = W.sw_silicon(n_side, T_K=0, jitter=jitter, seed=seed)
